@@ -1,0 +1,302 @@
+#!/usr/bin/env python
+"""Throughput of the PCAL iteration (paper Alg. 2) on one GB300, printed as one JSON line.
+
+Workload (default): the C10H22-like chain, 80 x 44 x 43 hexahedra split into 6 P2
+tetrahedra each (n = 1,175,805 free DoFs, 908,160 tets, 3.63M quadrature points), p = 41
+doubly occupied orbitals, beta = 10, LDA + Hartree, PCG preconditioner with 8 iterations,
+BB2 step, all in float64.  A step is one full PCAL iteration: density, Hartree CG, potential
+and Hamiltonian refresh, H X, the Grams, the multipliers, the gradient, the preconditioner,
+the BB step and the B-normalization.  Inputs are seeded and synthetic; the working set
+(~6 GB of n x p blocks plus ~1 GB of matrices) is far larger than L2, so no flush is needed.
+
+  value  iterations/s with everything resident in HBM (device time from CUDA events on the
+         library's stream, max over ranks)
+  e2e    the same through the C ABI with host buffers: each step uploads X from pinned host
+         memory, iterates once and reads X and the iteration record back
+  --impl reference   the CPU oracle on the same workload (bounded sample), same JSON keys
+
+With torchrun (N > 1) every rank runs an independent replica of the workload on its own
+GPU (the method is not sharded in this build), so scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-6 Ha & iters/s: learned-precond mixed vs plain FP64, same GB300"
+UNIT = "iters/s"
+
+
+def workload(name):
+    from paper_2007_14228_gb300 import inputs as I
+    if name == "chain":
+        return I.chain()
+    if name == "lih":
+        return I.lih()
+    if name == "lattice60":
+        return I.lattice60()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def config_of(args, s, sizes):
+    return {"workload": f"{s.name}: {len(s.Z)} nuclei, {'x'.join(map(str, s.cells))} hex cells -> P2 tets",
+            "n_free": sizes["n"], "n_tets": sizes["n_tets"], "n_q": sizes["n_q"], "p": s.p, "occ": s.occ,
+            "beta": 10.0, "form": "plain FP64", "precond": "PCG x8 (Eq. precondition-T)", "eta": "BB2",
+            "l2": "inputs larger than L2 (working set ~7 GB)", "parallelism": f"replicas x{args.gpus}"}
+
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# FP64 FMA peak of the GB300 (nominal 1.25 TFLOP/s dense FP64; measured by the fp64 probe
+# recorded in profiles/fp64_peak.md)
+FP64_PEAK_TFLOPS = 1.25
+
+
+def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind):
+    """Dominant kernel family by time: algorithmic bytes and flops per launch / mean duration."""
+    fam = max(prof, key=lambda k: prof[k]["ms"])
+    st = prof[fam]
+    per = st["ms"] / max(st["launches"], 1) * 1e-3
+    s = 8
+    model = {
+        "pcg_spmm": ((4 + 2 * s) * nnz + 5 * s * n * p, 4 * nnz * p + 6 * n * p),
+        "spmm_h": ((4 + s) * nnz + 2 * s * n * p, 2 * nnz * p),
+        "spmm_b": ((4 + s) * nnz + 3 * s * n * p, 2 * nnz * p + 2 * n * p),
+        "gram": (3 * s * n * p, 2 * n * p * p),
+        "grad": (3 * s * n * p, 4 * n * p * p),
+        "density": (s * n * p + n_tets * (40 + 32), n_tets * 4 * (20 * p + 2 * p)),
+    }
+    bytes_, flops = model.get(fam, (0, 0))
+    gbs = bytes_ / per / 1e9
+    tflops = flops / per / 1e12
+    f_hbm = gbs / hbm_peak
+    f_alu = tflops / FP64_PEAK_TFLOPS
+    if f_alu >= f_hbm:
+        return {"bound": "alu", "kernel": fam, "achieved": round(tflops, 4), "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s (fp64)", "frac": round(f_alu, 4), "traffic": None,
+                "hbm_gbs": round(gbs, 1), "hbm_frac": round(f_hbm, 4), "peak_kind": "nominal fp64",
+                "mean_launch_ms": round(per * 1e3, 4), "launches": st["launches"]}
+    return {"bound": "hbm", "kernel": fam, "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(f_hbm, 4), "traffic": None, "fp64_tflops": round(tflops, 4),
+            "peak_kind": hbm_kind, "mean_launch_ms": round(per * 1e3, 4), "launches": st["launches"]}
+
+
+def cpu_baseline(s, m, seconds_budget=30.0):
+    """The oracle as it stands, one PCAL iteration at the same workload on the host cores."""
+    import numpy as np
+    from oracle import pcal
+    from paper_2007_14228_gb300 import inputs as I
+    prm = pcal.Params(p=s.p, occ=s.occ, beta=10.0)
+    pr = pcal.Problem(m.xyz, m.tet10, m.dirichlet, s.Z, s.R, prm)
+    st = pcal.State(X=pr.initial_guess(I.initial_block(pr.n, s.p, 0)))
+    t0 = time.perf_counter()
+    pcal.iterate(pr, st)
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", "0") or 0) or os.cpu_count()
+    return {"value": round(1.0 / dt, 6), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"one oracle PCAL iteration (k=0, cold Hartree CG) at the full workload; {dt:.1f} s"}, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    s = workload(args.workload)
+    from paper_2007_14228_gb300 import inputs as I
+    if rank != 0:
+        return
+    m = I.make_mesh(s)
+    import numpy as np
+    from oracle import pcal
+    prm = pcal.Params(p=s.p, occ=s.occ, beta=10.0)
+    pr = pcal.Problem(m.xyz, m.tet10, m.dirichlet, s.Z, s.R, prm)
+    st = pcal.State(X=pr.initial_guess(I.initial_block(pr.n, s.p, 0)))
+    for _ in range(args.warmup):
+        pcal.iterate(pr, st)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pcal.iterate(pr, st)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", "0") or 0) or os.cpu_count()
+    sizes = I.sizes(s)
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": config_of(args, s, sizes),
+           "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{args.warmup}+{args.steps} oracle PCAL iterations at the full workload"},
+           "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="chain")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2007_14228_gb300 import build
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    from paper_2007_14228_gb300 import inputs as I
+    from paper_2007_14228_gb300 import ofks
+
+    s = workload(args.workload)
+    m = I.make_mesh(s)
+    ctx = ofks.context_for(s, m, device=local, beta=10.0)
+    V = I.initial_block(m.n_free, s.p, rank)
+    ctx.init_orbitals(V)
+    ctx.step(args.warmup)
+    clk = Clocks(local)
+    clk.start()
+    if dist:
+        dist.barrier()
+    ctx.profile(True)
+    res = ctx.step(args.steps)
+    prof = ctx.profile_get()
+    ctx.profile(False)
+    launches = prof.pop("all_kernels", {"launches": None})["launches"]
+    clocks = clk.stop()
+    t = res["seconds"]
+    if dist:
+        import torch
+        tt = torch.tensor([t], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    steps_done = res["iters"] - args.warmup
+    value = world * steps_done / t
+    sizes = ctx.sizes()
+
+    # end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        import numpy as np
+        try:
+            import torch
+            Xh = torch.empty((m.n_free, s.p), dtype=torch.float64, pin_memory=True).numpy()
+        except Exception:
+            Xh = np.empty((m.n_free, s.p))
+        ctx.get_orbitals(Xh)
+        k_e2e = max(2, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            ctx.set_orbitals(Xh, keep_history=True)
+            r = ctx.step(1)
+            ctx.get_orbitals(Xh)
+        dt = time.perf_counter() - t0
+        if dist:
+            import torch
+            tt = torch.tensor([dt], dtype=torch.float64, device=f"cuda:{local}")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dt = float(tt.item())
+        nb = m.n_free * s.p * 8
+        e2e = {"value": round(world * k_e2e / dt, 4), "unit": UNIT, "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb + 9 * 8, "steps": k_e2e}
+    ctx.close()
+    if rank != 0:
+        return
+    hbm_peak, hbm_kind = peaks()
+    roof = roofline(prof, sizes["n_free"], s.p, sizes["nnz"], sizes["n_tets"], hbm_peak, hbm_kind)
+    cpu = None
+    if not args.no_cpu and world == 1:
+        cpu, _ = cpu_baseline(s, m)
+    out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": steps_done,
+           "warmup": args.warmup, "ms_per_step": round(t / steps_done * 1e3, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config_of(args, s, I.sizes(s)), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": None, "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items() if v["launches"]},
+           "kernel_launches": {k: v["launches"] for k, v in prof.items() if v["launches"]},
+           "clocks": clocks, "E": res["e_total"], "kkt": res["kkt"], "fea": res["fea"]}
+    out["gpu_launches"] = launches
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * ofks.h - orthogonalization-free Kohn-Sham total-energy minimization (PCAL) on one GB300.
+ *
+ * C ABI of libofks.so.  The library solves the discretized Kohn-Sham problem
+ *     min E_KS(X)  subject to  X^T B X = I_p,   X in R^{n x p}          (paper: Eq. prob:KS)
+ * on a P2 tetrahedral mesh by the column-wise proximal linearized augmented Lagrangian
+ * method PCAL (paper: Alg. 2) and post-processes with Rayleigh-Ritz (paper: Sec. 4.3).
+ * Inputs follow the problem statement: mesh, nuclei, p and beta in; energy, orbitals and
+ * eigenvalues out.  Every arithmetic step runs in CUDA kernels built for sm_103a; the host
+ * side only builds index structures (sparsity patterns, element-to-entry maps) and drives
+ * launches.  There is no CPU fallback: without a usable GPU every call fails.
+ *
+ * Conventions for every entry point
+ *   - Return value: 0 on success, a negative OFKS_E* code on failure; the message is kept
+ *     in the context and returned by ofks_last_error().  Nothing is thrown across the ABI.
+ *   - Host arrays are owned by the caller and only read (inputs) or written (outputs)
+ *     during the call; the library keeps its own device copies.
+ *   - Blocks of orbitals are n_free x p, row-major, float64, where the free degrees of
+ *     freedom are the non-Dirichlet nodes numbered in increasing global node id.
+ *   - A context is bound to one device and is not thread-safe; calls on one context must
+ *     be serialized by the caller.
+ */
+#ifndef OFKS_H
+#define OFKS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------------------- */
+#define OFKS_OK            0
+#define OFKS_EINVAL       -1   /* bad argument (size, range, pointer) */
+#define OFKS_ECUDA        -2   /* a CUDA runtime call or kernel launch failed */
+#define OFKS_ENOMEM       -3   /* device or host allocation failed */
+#define OFKS_ESTATE       -4   /* call out of order (e.g. solve before set_mesh) */
+#define OFKS_ENOTCONV     -5   /* iteration cap reached, or a Cholesky factor does not exist */
+#define OFKS_ENONFINITE   -6   /* NaN/Inf met in energies or norms */
+#define OFKS_ETIMEOUT     -7   /* an iterative inner solve hit its iteration limit */
+
+/* ---- enumerations ------------------------------------------------------------------ */
+#define OFKS_FP64          0   /* every step in float64 */
+
+#define OFKS_PC_NONE       0   /* D = grad L_beta */
+#define OFKS_PC_PCG        1   /* T_i^{-1} grad by Jacobi-PCG, fixed pcg_iters, zero start */
+#define OFKS_PC_EXACT      2   /* the same PCG run to a 1e-12 relative residual */
+
+#define OFKS_ETA_BB2       0   /* eta = <dD,dD>/|<dX,dD>|, dD = difference of applied directions */
+#define OFKS_ETA_BB1       1   /* eta = |<dX,dD>|/<dX,dX> */
+#define OFKS_ETA_ABB1      2   /* BB1 on odd k, BB2 on even k */
+#define OFKS_ETA_ABB2      3   /* BB2 on odd k, BB1 on even k */
+#define OFKS_ETA_BB2_RAW   4   /* BB2 with differences of the raw gradients grad L_beta */
+#define OFKS_ETA_FIXED     5   /* eta = eta_fixed every iteration */
+
+/* which fields ofks_get_field() copies out */
+#define OFKS_F_RHO_Q       0   /* density at quadrature points, n_tets*4 */
+#define OFKS_F_VH_Q        1   /* Hartree potential at quadrature points, n_tets*4 */
+#define OFKS_F_VXC_Q       2   /* exchange-correlation potential at quadrature points */
+#define OFKS_F_EXC_Q       3   /* exchange-correlation energy per particle at quadrature points */
+#define OFKS_F_U           4   /* nodal Hartree potential, n_nodes (all nodes) */
+#define OFKS_F_HX          5   /* H(X) X, n_free x p */
+#define OFKS_F_BX          6   /* B X, n_free x p */
+#define OFKS_F_G           7   /* grad_X L_beta(X, Lambda), n_free x p */
+#define OFKS_F_D           8   /* preconditioned direction, n_free x p */
+#define OFKS_F_LAMBDA0     9   /* X^T H X, p x p */
+#define OFKS_F_S          10   /* X^T B X, p x p */
+#define OFKS_F_LAMBDA     11   /* Eq. (lambda2) multipliers, p x p */
+#define OFKS_F_VEXT_Q     12   /* external potential at quadrature points */
+
+/* which matrix ofks_apply() multiplies with */
+#define OFKS_M_L           0   /* stiffness on the free DoFs */
+#define OFKS_M_B           1   /* mass on the free DoFs */
+#define OFKS_M_H           2   /* current Hamiltonian L/2 + M_ext + M_Har + M_xc */
+
+typedef struct ofks_ctx ofks_ctx;   /* opaque, owned by the library */
+
+typedef struct {
+    int32_t p;              /* number of orbitals (columns of X) */
+    double  beta;           /* penalty parameter of L_beta (paper Eq. ALM-sub) */
+    double  occ;            /* electrons per orbital f: rho = f sum_l |psi_l|^2 */
+    double  tol;            /* stop when (kkt + fea)/kkt_0 < tol (paper Sec. 4.1) */
+    int32_t max_iter;       /* iteration cap of ofks_solve */
+    int32_t precision;      /* OFKS_FP64 */
+    int32_t precond;        /* OFKS_PC_* (paper Eq. precondition-T) */
+    int32_t pcg_iters;      /* PCG iterations per preconditioner apply */
+    int32_t eta_rule;       /* OFKS_ETA_* (paper Sec. 4.4) */
+    double  eta_fixed;      /* used by OFKS_ETA_FIXED */
+    double  eta_min, eta_max;   /* clamp of eta */
+    int32_t hartree;        /* 1: Hartree term on; 0: off (fixed-potential problems) */
+    int32_t xc;             /* 1: LDA (Slater + PZ81) on; 0: off */
+    int32_t multipole_lmax; /* Hartree boundary data: multipoles up to l (0..2); -1: zero */
+    double  poisson_tol;    /* relative residual of the Hartree CG solve */
+    int32_t poisson_max_iter;
+} ofks_params;
+
+typedef struct {
+    double  e_total;        /* E_KS at the last evaluated iterate (Hartree) */
+    double  e_nuc;          /* nucleus-nucleus repulsion */
+    double  kkt;            /* ||H X - B X X^T H X||_F */
+    double  fea;            /* ||X^T B X - I||_F */
+    double  kkt0;           /* kkt at iteration 0 */
+    double  eta;            /* last step parameter */
+    int32_t iters;          /* iterations taken so far (k) */
+    int32_t converged;      /* 1 once (kkt + fea)/kkt0 < tol */
+    double  seconds;        /* device time of the call, from CUDA events */
+} ofks_result;
+
+/* Fill *prm with the defaults: beta 10, occ 2, tol 1e-8, max_iter 1000, FP64, PCG with 8
+ * iterations, BB2, eta in [1e-4, 1e8], Hartree and LDA on, multipole_lmax 2,
+ * poisson_tol 1e-12, poisson_max_iter 20000.  p is set to 1. */
+void ofks_default_params(ofks_params *prm);
+
+/* Create a context on CUDA device `device`.  *out receives the context (NULL on failure).
+ * Errors: OFKS_ECUDA if the device cannot be used, OFKS_ENOMEM. */
+int ofks_create(ofks_ctx **out, int device);
+
+/* Release every device and host resource of the context.  Accepts NULL. */
+void ofks_destroy(ofks_ctx *ctx);
+
+/* Message of the last failed call on this context ("" if none).  Valid until the next call. */
+const char *ofks_last_error(const ofks_ctx *ctx);
+
+/* Mesh (paper Sec. 2.2, discretization; Sec. 4.2 pre-processing).
+ *   xyz       n_nodes x 3 node coordinates (bohr)
+ *   tet10     n_tets x 10 node ids of P2 tetrahedra: vertices 0..3, then the midpoints of
+ *             edges 01, 02, 03, 12, 13, 23 (straight-sided)
+ *   dirichlet n_nodes flags, nonzero on the boundary (orbitals vanish there; the Hartree
+ *             potential takes its multipole boundary values there)
+ * Builds the sparsity patterns, assembles L and B on the device and resets orbitals,
+ * nuclei-dependent data and history.  Errors: OFKS_EINVAL for ids out of range, a
+ * degenerate tetrahedron or fewer than one free node; OFKS_ENOMEM. */
+int ofks_set_mesh(ofks_ctx *ctx, int64_t n_nodes, const double *xyz,
+                  int64_t n_tets, const int64_t *tet10, const uint8_t *dirichlet);
+
+/* Nuclei (paper Eq. ext): M charges Z (> 0) at positions R (M x 3, bohr).  Evaluates V_ext
+ * at the quadrature points and E_nuc.  Requires a mesh.  Errors: OFKS_EINVAL, OFKS_ESTATE. */
+int ofks_set_nuclei(ofks_ctx *ctx, int32_t M, const double *Z, const double *R);
+
+/* Parameters; p must satisfy 1 <= p <= n_free.  Changing p drops the orbitals.
+ * Errors: OFKS_EINVAL for values out of range, OFKS_ESTATE without a mesh. */
+int ofks_set_params(ofks_ctx *ctx, const ofks_params *prm);
+
+/* Initial guess (paper Sec. 4.2): V (n_free x p, host) is B-orthonormalized by the
+ * Cholesky-based Gram-Schmidt V = X0 R (R upper triangular) on the device, and the
+ * iteration counter and history are reset.  Errors: OFKS_ENOTCONV if V^T B V is not
+ * positive definite (V rank deficient), OFKS_ESTATE, OFKS_EINVAL. */
+int ofks_init_orbitals(ofks_ctx *ctx, const double *V);
+
+/* Set X directly (n_free x p, host), without orthonormalization.  keep_history = 0 resets
+ * the iteration counter and the step-size history; 1 keeps them (the caller re-uploads the
+ * block it read back).  Errors: OFKS_ESTATE, OFKS_EINVAL. */
+int ofks_set_orbitals(ofks_ctx *ctx, const double *X, int32_t keep_history);
+
+/* Copy the current X (n_free x p) to host memory X. */
+int ofks_get_orbitals(ofks_ctx *ctx, double *X);
+
+/* Run up to k iterations of Alg. 2 from the current state; stops early once the stopping
+ * test of Sec. 4.1 holds.  res (may be NULL) receives the record of the last evaluated
+ * iterate and the device time of the call.  Errors: OFKS_ESTATE (no orbitals),
+ * OFKS_ENONFINITE, OFKS_ETIMEOUT (the Hartree solve hit poisson_max_iter), OFKS_ECUDA. */
+int ofks_step(ofks_ctx *ctx, int32_t k, ofks_result *res);
+
+/* Iterate until the stopping test holds or max_iter iterations; OFKS_ENOTCONV at the cap
+ * (res is still filled). */
+int ofks_solve(ofks_ctx *ctx, ofks_result *res);
+
+/* Evaluate the current iterate without updating it: density, Hartree and xc potentials,
+ * H(X), H X, B X, the Grams, E, kkt, fea, the multipliers of Eq. (lambda2) and the
+ * gradient; fields are then readable with ofks_get_field(). */
+int ofks_evaluate(ofks_ctx *ctx, ofks_result *res);
+
+/* Post-processing (paper Sec. 4.3): the p x p generalized eigenproblem
+ * (X^T H X) v = lambda (X^T B X) v in float64 on the device, X <- X V.  eigs (host, p)
+ * receives the eigenvalues in ascending order. */
+int ofks_rayleigh_ritz(ofks_ctx *ctx, double *eigs);
+
+/* Copy a field (OFKS_F_*) of the last evaluation into out (host), which holds `count`
+ * doubles; count must equal the field's size.  Errors: OFKS_EINVAL, OFKS_ESTATE. */
+int ofks_get_field(ofks_ctx *ctx, int32_t which, double *out, int64_t count);
+
+/* Y = A X for A = OFKS_M_L, OFKS_M_B or OFKS_M_H on host blocks (n_free x ncols) through
+ * the device SpMM kernel.  ncols must equal p. */
+int ofks_apply(ofks_ctx *ctx, int32_t which, const double *X, double *Y, int32_t ncols);
+
+/* Sizes: free DoFs, all nodes, tetrahedra, stored nonzeros of the free matrices
+ * (without padding).  Any pointer may be NULL. */
+int ofks_get_sizes(ofks_ctx *ctx, int64_t *n_free, int64_t *n_nodes, int64_t *n_tets,
+                   int64_t *nnz);
+
+/* History of evaluated iterates: rows of 6 doubles (k, seconds since init, E, kkt, fea,
+ * eta).  Copies min(cap, available) rows of the most recent ones into buf; *len = rows. */
+int ofks_get_history(ofks_ctx *ctx, double *buf, int32_t cap, int32_t *len);
+
+/* Checkpoint: X, X_prev, D_prev, G_prev, eta, k, kkt0 and the Hartree warm start U, so a
+ * reloaded run continues bit-for-bit.  The mesh, nuclei and params must match on load. */
+int ofks_save_state(ofks_ctx *ctx, const char *path);
+int ofks_load_state(ofks_ctx *ctx, const char *path);
+
+/* Per-kernel device time accumulated while profiling is on (CUDA events around each
+ * launch of the named kernel family).  on = 1 starts (and clears), 0 stops. */
+int ofks_profile(ofks_ctx *ctx, int32_t on);
+/* kernel family id -> launches and total milliseconds since profiling was switched on;
+ * name (may be NULL) receives a static string. */
+int ofks_profile_get(ofks_ctx *ctx, int32_t id, int64_t *launches, double *ms,
+                     const char **name);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OFKS_H */

@@ -2,7 +2,9 @@
 
 Sec. 2.2: V_Har solves -lap V = 4 pi rho; with V_Har = U^T N the discrete system is
 L U = 4 pi (int rho phi_i)_i.  The paper solves it by algebraic multigrid; here the
-interior system is solved by a sparse direct factorization (exact up to rounding).
+interior system is solved by a sparse direct factorization (exact up to rounding) on
+small meshes, and by Jacobi-preconditioned CG to a 1e-13 relative residual, warm-started
+from the previous solution, above DIRECT_MAX_NODES nodes.
 
 Boundary values on the box (the paper is silent on them): the multipole expansion of
 rho about the centre c of the node bounding box, up to l = lmax <= 2 (lmax = -1 gives
@@ -20,8 +22,11 @@ import scipy.sparse.linalg as spla
 from . import fem
 
 
+DIRECT_MAX_NODES = 40_000
+
+
 class Hartree:
-    def __init__(self, xyz, tet10, dirichlet, L_full, vol, xq, lmax: int = 2):
+    def __init__(self, xyz, tet10, dirichlet, L_full, vol, xq, lmax: int = 2, solver: str = "auto"):
         self.xyz, self.tet10, self.vol, self.lmax = xyz, tet10, vol, int(lmax)
         self.n = xyz.shape[0]
         self.center = 0.5 * (xyz.min(axis=0) + xyz.max(axis=0))
@@ -29,7 +34,17 @@ class Hartree:
         self.Bd = np.nonzero(dirichlet != 0)[0]
         Lr = L_full[self.I]
         self.L_IB = Lr[:, self.Bd].tocsr()
-        self.solve_II = spla.factorized(Lr[:, self.I].tocsc())
+        L_II = Lr[:, self.I].tocsr()
+        if solver == "auto":
+            solver = "direct" if self.n <= DIRECT_MAX_NODES else "cg"
+        self.solver = solver
+        if solver == "direct":
+            self.solve_II = spla.factorized(L_II.tocsc())
+        else:
+            self._L_II = L_II
+            self._M = spla.LinearOperator(L_II.shape, matvec=lambda v, d=1.0 / L_II.diagonal(): d * v)
+            self._x = np.zeros(len(self.I))
+            self.solve_II = self._cg
         self.yq = (xq - self.center).reshape(-1, 3)        # (T*4, 3)
         self.wq = np.repeat(vol / 4.0, 4)
 
@@ -55,6 +70,13 @@ class Hartree:
         if self.lmax >= 2:
             V = V + 0.5 * np.einsum("bi,ij,bj->b", r, Qij, r) / rn ** 5
         return V
+
+    def _cg(self, b):
+        x, info = spla.cg(self._L_II, b, x0=self._x, rtol=1e-13, atol=0.0, M=self._M, maxiter=100000)
+        if info != 0:
+            raise RuntimeError(f"Hartree CG did not converge (info={info})")
+        self._x = x
+        return x
 
     def solve(self, rho_q):
         """Nodal Hartree potential U (n_nodes,) for the density rho_q (T, 4)."""

@@ -1,0 +1,673 @@
+// C ABI of libofks: context, parameters, orbitals and the PCAL driver (paper Alg. 2).
+//
+// One iteration at X^k (all on the context's stream, no host arithmetic):
+//   density rho(X) -> Hartree CG -> potentials + H refresh          (Sec. 2.2, Eq. hamiltonian)
+//   H X (SELL SpMM); Lambda0 = X^T H X, S = X^T B X                  (Eq. multi)
+//   Lambda (Eq. lambda2), C = beta (S - I) - Lambda, E, fea
+//   G = H X + B X C, kkt = ||H X - B X Lambda0||_F                   (Eq. PLAM-main, Sec. 4.1)
+//   stopping test (kkt + fea)/kkt0 < tol                             (Sec. 4.1)
+//   D = T^{-1} G by Jacobi-PCG per column (Eq. precondition-T)
+//   eta by BB (Sec. 4.4); Y = X - D/eta; B Y with column norms; X <- Y/||Y||_B (Eq. PCAL-main)
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+enum { CB_SHIFT = 0, CB_ACTIVE = 1, CB_RZ = 2, CB_RZN = 3, CB_PQ = 4, CB_BETA = 5, CB_NORM = 6,
+       CB_ALPHA = 7, CB_COUNT = 8 };
+
+void launch_pcg_alpha(ofks_ctx *c);
+void launch_pcg_beta(ofks_ctx *c);
+
+static const char *kPfNames[PF_COUNT] = {"density", "poisson", "potential", "spmm_h", "gram", "small",
+                                         "grad", "pcg_spmm", "pcg_update", "bb", "step", "spmm_b", "other"};
+
+int ofks_fail(ofks_ctx *c, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+int ofks_cuda_check(ofks_ctx *c, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return OFKS_OK;
+    return ofks_fail(c, OFKS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static cudaEvent_t ev_get(ofks_ctx *c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(ofks_ctx *c, int, cudaEvent_t *a, cudaEvent_t *b) {
+    if (!c->prof) return;
+    *a = ev_get(c);
+    *b = ev_get(c);
+    cudaEventRecord(*a, c->stream);
+}
+
+void prof_end(ofks_ctx *c, int fam, cudaEvent_t a, cudaEvent_t b) {
+    if (!c->prof || !a) return;
+    cudaEventRecord(b, c->stream);
+    c->prof_pending.push_back({fam, {a, b}});
+}
+
+static void prof_resolve(ofks_ctx *c) {
+    if (c->prof_pending.empty()) return;
+    cudaStreamSynchronize(c->stream);
+    for (auto &pe : c->prof_pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, pe.second.first, pe.second.second);
+        c->prof_n[pe.first]++;
+        c->prof_ms[pe.first] += ms;
+        c->ev_pool.push_back(pe.second.first);
+        c->ev_pool.push_back(pe.second.second);
+    }
+    c->prof_pending.clear();
+}
+
+template <class T>
+static void dfree(T *&p) {
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+static void free_blocks(ofks_ctx *c) {
+    for (int i = 0; i < 2; ++i) { dfree(c->d_X[i]); dfree(c->d_D[i]); dfree(c->d_G[i]); }
+    dfree(c->d_HX); dfree(c->d_BX); dfree(c->d_R); dfree(c->d_Z); dfree(c->d_P); dfree(c->d_Q);
+    dfree(c->d_L0); dfree(c->d_S); dfree(c->d_Lam); dfree(c->d_C); dfree(c->d_colA); dfree(c->d_pp);
+    c->p = c->ld = 0;
+    c->have_X = c->evaluated = c->have_prev = false;
+}
+
+static int alloc_blocks(ofks_ctx *c, int p) {
+    free_blocks(c);
+    const int ld = (p <= 2) ? p : (p + 3) / 4 * 4;
+    const size_t blk = sizeof(double) * (size_t)c->n * ld, sm = sizeof(double) * (size_t)ld * ld;
+    double **bl[] = {&c->d_X[0], &c->d_X[1], &c->d_D[0], &c->d_D[1], &c->d_G[0], &c->d_G[1], &c->d_HX,
+                     &c->d_BX, &c->d_R, &c->d_Z, &c->d_P, &c->d_Q};
+    for (double **b : bl) {
+        if (cudaMalloc((void **)b, blk) != cudaSuccess) {
+            free_blocks(c);
+            return ofks_fail(c, OFKS_ENOMEM, "cannot allocate %zu bytes for an n x p block", blk);
+        }
+        cudaMemsetAsync(*b, 0, blk, c->stream);
+    }
+    double **sl[] = {&c->d_L0, &c->d_S, &c->d_Lam, &c->d_C};
+    for (double **b : sl) {
+        if (cudaMalloc((void **)b, sm) != cudaSuccess) { free_blocks(c); return ofks_fail(c, OFKS_ENOMEM, "p x p"); }
+        cudaMemsetAsync(*b, 0, sm, c->stream);
+    }
+    if (cudaMalloc((void **)&c->d_colA, sizeof(double) * CB_COUNT * ld) != cudaSuccess ||
+        cudaMalloc((void **)&c->d_pp, sm * 8 + sizeof(double) * ld) != cudaSuccess) {
+        free_blocks(c);
+        return ofks_fail(c, OFKS_ENOMEM, "p x p scratch");
+    }
+    cudaMemsetAsync(c->d_colA, 0, sizeof(double) * CB_COUNT * ld, c->stream);
+    c->p = p;
+    c->ld = ld;
+    return ofks_cuda_check(c, cudaStreamSynchronize(c->stream), "block allocation");
+}
+
+static double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static int upload_block(ofks_ctx *c, const double *h, double *d) {
+    cudaError_t e = cudaMemcpy2DAsync(d, sizeof(double) * c->ld, h, sizeof(double) * c->p, sizeof(double) * c->p,
+                                      (size_t)c->n, cudaMemcpyHostToDevice, c->stream);
+    return ofks_cuda_check(c, e, "block upload");
+}
+
+static int download_block(ofks_ctx *c, const double *d, double *h) {
+    cudaError_t e = cudaMemcpy2DAsync(h, sizeof(double) * c->p, d, sizeof(double) * c->ld, sizeof(double) * c->p,
+                                      (size_t)c->n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return ofks_cuda_check(c, e, "block download");
+}
+
+static int read_flag(ofks_ctx *c, int *h) {
+    cudaError_t e = cudaMemcpyAsync(h, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream);
+    return ofks_cuda_check(c, e, "status flag");
+}
+
+// ------------------------------------------------------------------------------ iteration
+struct Rec { double E, fea, kkt, eta; };
+
+static int evaluate(ofks_ctx *c, bool need_bx, Rec *out) {
+    double *X = c->d_X[c->cur];
+    int rc;
+    if ((rc = launch_density(c, X))) return rc;
+    if ((rc = run_hartree(c))) return rc;
+    if ((rc = launch_potential_refresh(c))) return rc;
+    {
+        ProfScope ps(c, PF_SPMM_H);
+        launch_sell_spmm(c, c->d_valH, X, c->d_HX);
+    }
+    if (need_bx) {
+        ProfScope ps(c, PF_SPMM_B);
+        launch_sell_spmm(c, c->d_valB, X, c->d_BX);
+    }
+    launch_gram2(c, X, c->d_HX, c->d_BX, c->d_L0, c->d_S);
+    launch_small_update(c);
+    launch_grad_update(c);
+    launch_small_record(c);
+    double h[4];
+    cudaError_t e = cudaMemcpyAsync(h, c->d_rec, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if ((rc = ofks_cuda_check(c, e, "evaluate"))) return rc;
+    out->E = h[0]; out->fea = h[1]; out->kkt = h[2];
+    c->evaluated = true;
+    c->last_E = h[0]; c->last_fea = h[1]; c->last_kkt = h[2];
+    if (!std::isfinite(h[0]) || !std::isfinite(h[1]) || !std::isfinite(h[2]))
+        return ofks_fail(c, OFKS_ENONFINITE, "non-finite iterate record: E=%g fea=%g kkt=%g", h[0], h[1], h[2]);
+    return OFKS_OK;
+}
+
+static int precondition(ofks_ctx *c) {
+    const int ld = c->ld;
+    double *D = c->d_D[c->cur], *G = c->d_G[c->cur];
+    if (c->prm.precond == OFKS_PC_NONE) {
+        return ofks_cuda_check(c, cudaMemcpyAsync(D, G, sizeof(double) * c->n * ld, cudaMemcpyDeviceToDevice, c->stream),
+                               "direction copy");
+    }
+    {
+        ProfScope ps(c, PF_PCG_UPDATE);
+        launch_pcg_init(c);
+        cudaMemsetAsync(c->d_colA + CB_PQ * ld, 0, sizeof(double) * ld, c->stream);
+    }
+    const bool exact = c->prm.precond == OFKS_PC_EXACT;
+    const int max_it = exact ? 5000 : c->prm.pcg_iters;
+    std::vector<double> rz0, rz(ld), act(ld);
+    if (exact) {
+        rz0.resize(ld);
+        cudaMemcpyAsync(rz0.data(), c->d_colA + CB_RZ * ld, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(act.data(), c->d_colA + CB_ACTIVE * ld, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream);
+        cudaStreamSynchronize(c->stream);
+    }
+    for (int it = 0; it < max_it; ++it) {
+        {
+            ProfScope ps(c, PF_PCG_SPMM);
+            launch_pcg_apply(c, c->d_Z, c->d_P, c->d_Q, c->d_colA + CB_BETA * ld, c->d_colA + CB_SHIFT * ld,
+                             c->d_colA + CB_PQ * ld, it == 0 ? 1 : 0);
+        }
+        {
+            ProfScope ps(c, PF_PCG_UPDATE);
+            launch_pcg_alpha(c);
+            launch_pcg_update(c, it);
+            launch_pcg_beta(c);
+        }
+        if (exact && (it + 1) % 25 == 0) {
+            cudaMemcpyAsync(rz.data(), c->d_colA + CB_RZ * ld, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream);
+            cudaStreamSynchronize(c->stream);
+            bool done = true;
+            for (int j = 0; j < c->p; ++j)
+                if (act[j] != 0.0 && rz[j] > 1e-24 * rz0[j]) done = false;
+            if (done) break;
+        }
+    }
+    {
+        ProfScope ps(c, PF_PCG_UPDATE);
+        launch_direction_select(c);
+    }
+    return ofks_cuda_check(c, cudaGetLastError(), "preconditioner");
+}
+
+static int update_step(ofks_ctx *c) {
+    const int prv = c->cur ^ 1, ld = c->ld;
+    int rc;
+    if ((rc = precondition(c))) return rc;
+    {
+        // BB sums on the applied directions, or on the raw gradients for OFKS_ETA_BB2_RAW
+        if (c->prm.eta_rule == OFKS_ETA_BB2_RAW) {
+            std::swap(c->d_D[0], c->d_G[0]);
+            std::swap(c->d_D[1], c->d_G[1]);
+            launch_bb_dots(c);
+            std::swap(c->d_D[0], c->d_G[0]);
+            std::swap(c->d_D[1], c->d_G[1]);
+            // ||D||^2 for eta_0 must use the applied direction
+            if (!c->have_prev) launch_bb_dots(c);
+        } else {
+            launch_bb_dots(c);
+        }
+        launch_eta(c);
+    }
+    double *Y = c->d_X[prv];
+    {
+        ProfScope ps(c, PF_STEP);
+        launch_step_y(c, Y);
+    }
+    cudaMemsetAsync(c->d_colA + CB_NORM * ld, 0, sizeof(double) * ld, c->stream);
+    {
+        ProfScope ps(c, PF_SPMM_B);
+        launch_sell_spmm_colnorm(c, c->d_valB, Y, c->d_BX, c->d_colA + CB_NORM * ld);
+    }
+    {
+        ProfScope ps(c, PF_STEP);
+        launch_scale_cols(c, Y, c->d_BX, c->d_colA + CB_NORM * ld);
+    }
+    if ((rc = ofks_cuda_check(c, cudaGetLastError(), "update step"))) return rc;
+    double eta;
+    cudaError_t e = cudaMemcpyAsync(&eta, c->d_sc + SC_ETA, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if ((rc = ofks_cuda_check(c, e, "update step"))) return rc;
+    c->eta = eta;
+    c->cur = prv;
+    c->have_prev = true;
+    c->k++;
+    return OFKS_OK;
+}
+
+static int run_iterations(ofks_ctx *c, int kmax, ofks_result *res) {
+    if (!c->have_X) return ofks_fail(c, OFKS_ESTATE, "no orbitals: call ofks_init_orbitals first");
+    cudaEvent_t e0 = ev_get(c), e1 = ev_get(c);
+    cudaEventRecord(e0, c->stream);
+    int rc = OFKS_OK;
+    for (int it = 0; it < kmax && !c->converged; ++it) {
+        Rec r{};
+        if ((rc = evaluate(c, !c->bx_valid, &r))) break;
+        c->bx_valid = true;
+        if (c->k == 0) c->kkt0 = r.kkt;
+        c->history.insert(c->history.end(), {(double)c->k, now_s() - c->t_start, r.E, r.kkt, r.fea, c->eta});
+        if (c->kkt0 > 0 && (r.kkt + r.fea) / c->kkt0 < c->prm.tol) { c->converged = true; break; }
+        if ((rc = update_step(c))) break;
+    }
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    c->ev_pool.push_back(e0);
+    c->ev_pool.push_back(e1);
+    if (res) {
+        res->e_total = c->last_E; res->e_nuc = c->e_nuc; res->kkt = c->last_kkt; res->fea = c->last_fea;
+        res->kkt0 = c->kkt0; res->eta = c->eta; res->iters = c->k; res->converged = c->converged ? 1 : 0;
+        res->seconds = ms * 1e-3;
+    }
+    return rc;
+}
+
+// ------------------------------------------------------------------------------ ABI
+extern "C" {
+
+void ofks_default_params(ofks_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->p = 1; p->beta = 10.0; p->occ = 2.0; p->tol = 1e-8; p->max_iter = 1000;
+    p->precision = OFKS_FP64; p->precond = OFKS_PC_PCG; p->pcg_iters = 8; p->eta_rule = OFKS_ETA_BB2;
+    p->eta_fixed = 0.0; p->eta_min = 1e-4; p->eta_max = 1e8; p->hartree = 1; p->xc = 1;
+    p->multipole_lmax = 2; p->poisson_tol = 1e-12; p->poisson_max_iter = 20000;
+}
+
+int ofks_create(ofks_ctx **out, int device) {
+    if (!out) return OFKS_EINVAL;
+    *out = nullptr;
+    ofks_ctx *c = new (std::nothrow) ofks_ctx();
+    if (!c) return OFKS_ENOMEM;
+    ofks_default_params(&c->prm);
+    c->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_sc, sizeof(double) * SC_COUNT);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_rec, sizeof(double) * 8);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_flag, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMemset(c->d_sc, 0, sizeof(double) * SC_COUNT);
+    if (e == cudaSuccess) e = cudaMemset(c->d_rec, 0, sizeof(double) * 8);
+    if (e == cudaSuccess) e = cudaMemset(c->d_flag, 0, sizeof(int) * 4);
+    if (e != cudaSuccess) {
+        ofks_destroy(c);
+        return OFKS_ECUDA;
+    }
+    *out = c;
+    return OFKS_OK;
+}
+
+void ofks_destroy(ofks_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_blocks(c);
+    free_mesh(c);
+    dfree(c->d_sc); dfree(c->d_rec); dfree(c->d_flag);
+    for (auto &pe : c->prof_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char *ofks_last_error(const ofks_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int ofks_set_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, const int64_t *tet10,
+                  const uint8_t *dirichlet) {
+    if (!c) return OFKS_EINVAL;
+    cudaSetDevice(c->device);
+    free_blocks(c);
+    int rc = setup_mesh(c, n_nodes, xyz, n_tets, tet10, dirichlet);
+    if (rc) return rc;
+    if (c->prm.p > c->n) c->prm.p = 1;
+    c->bx_valid = false;
+    return alloc_blocks(c, c->prm.p);
+}
+
+int ofks_set_nuclei(ofks_ctx *c, int32_t M, const double *Z, const double *R) {
+    if (!c) return OFKS_EINVAL;
+    if (!c->n) return ofks_fail(c, OFKS_ESTATE, "set_nuclei: no mesh");
+    if (M < 1 || !Z || !R) return ofks_fail(c, OFKS_EINVAL, "set_nuclei: need M >= 1 and arrays");
+    for (int j = 0; j < M; ++j)
+        if (!(Z[j] > 0)) return ofks_fail(c, OFKS_EINVAL, "set_nuclei: Z[%d] must be > 0", j);
+    cudaSetDevice(c->device);
+    c->evaluated = false;
+    return setup_nuclei(c, M, Z, R);
+}
+
+int ofks_set_params(ofks_ctx *c, const ofks_params *prm) {
+    if (!c || !prm) return OFKS_EINVAL;
+    if (!c->n) return ofks_fail(c, OFKS_ESTATE, "set_params: no mesh");
+    if (prm->p < 1 || prm->p > c->n) return ofks_fail(c, OFKS_EINVAL, "set_params: p=%d outside [1, %lld]", prm->p, (long long)c->n);
+    if (prm->p > 256) return ofks_fail(c, OFKS_EINVAL, "set_params: p=%d above the supported 256", prm->p);
+    if (!(prm->beta >= 0) || !(prm->occ > 0) || !(prm->tol > 0) || prm->max_iter < 0 || prm->pcg_iters < 0 ||
+        prm->eta_rule < 0 || prm->eta_rule > OFKS_ETA_FIXED || prm->precond < 0 || prm->precond > OFKS_PC_EXACT ||
+        prm->precision != OFKS_FP64 || !(prm->eta_min > 0) || !(prm->eta_max >= prm->eta_min) ||
+        prm->multipole_lmax < -1 || prm->multipole_lmax > 2 || !(prm->poisson_tol > 0) ||
+        prm->poisson_max_iter < 1 || (prm->eta_rule == OFKS_ETA_FIXED && !(prm->eta_fixed > 0)))
+        return ofks_fail(c, OFKS_EINVAL, "set_params: a parameter is out of range");
+    cudaSetDevice(c->device);
+    const bool realloc = prm->p != c->p;
+    c->prm = *prm;
+    c->evaluated = false;
+    if (realloc) {
+        int rc = alloc_blocks(c, prm->p);
+        if (rc) return rc;
+        c->bx_valid = false;
+    }
+    return OFKS_OK;
+}
+
+int ofks_init_orbitals(ofks_ctx *c, const double *V) {
+    if (!c || !V) return OFKS_EINVAL;
+    if (!c->n || !c->p) return ofks_fail(c, OFKS_ESTATE, "init_orbitals: no mesh/params");
+    cudaSetDevice(c->device);
+    int rc;
+    double *Vd = c->d_X[c->cur ^ 1], *BV = c->d_Q;
+    if ((rc = upload_block(c, V, Vd))) return rc;
+    launch_sell_spmm(c, c->d_valB, Vd, BV);
+    launch_gram2(c, Vd, BV, BV, c->d_S, c->d_L0);
+    double *Rinv = c->d_pp + 6 * (size_t)c->ld * c->ld;
+    launch_cholesky_inv(c, c->d_S, Rinv);
+    launch_block_times_small(c, Vd, Rinv, c->d_X[c->cur]);
+    launch_block_times_small(c, BV, Rinv, c->d_BX);
+    int flag = 0;
+    if ((rc = read_flag(c, &flag))) return rc;
+    if (flag) return ofks_fail(c, OFKS_ENOTCONV, "init_orbitals: V^T B V is not positive definite");
+    c->bx_valid = true;
+    c->have_X = true; c->have_prev = false; c->converged = false; c->evaluated = false;
+    c->k = 0; c->kkt0 = 0; c->eta = 0;
+    c->history.clear();
+    c->t_start = now_s();
+    return OFKS_OK;
+}
+
+int ofks_set_orbitals(ofks_ctx *c, const double *X, int32_t keep) {
+    if (!c || !X) return OFKS_EINVAL;
+    if (!c->n || !c->p) return ofks_fail(c, OFKS_ESTATE, "set_orbitals: no mesh/params");
+    cudaSetDevice(c->device);
+    int rc = upload_block(c, X, c->d_X[c->cur]);
+    if (rc) return rc;
+    c->bx_valid = false;
+    c->have_X = true;
+    c->evaluated = false;
+    if (!keep) {
+        c->have_prev = false; c->converged = false; c->k = 0; c->kkt0 = 0; c->eta = 0;
+        c->history.clear();
+        c->t_start = now_s();
+    }
+    return OFKS_OK;
+}
+
+int ofks_get_orbitals(ofks_ctx *c, double *X) {
+    if (!c || !X) return OFKS_EINVAL;
+    if (!c->have_X) return ofks_fail(c, OFKS_ESTATE, "get_orbitals: no orbitals");
+    cudaSetDevice(c->device);
+    return download_block(c, c->d_X[c->cur], X);
+}
+
+int ofks_step(ofks_ctx *c, int32_t k, ofks_result *res) {
+    if (!c || k < 0) return OFKS_EINVAL;
+    if (!c->have_nuclei) return ofks_fail(c, OFKS_ESTATE, "step: no nuclei");
+    cudaSetDevice(c->device);
+    return run_iterations(c, k, res);
+}
+
+int ofks_solve(ofks_ctx *c, ofks_result *res) {
+    if (!c) return OFKS_EINVAL;
+    if (!c->have_nuclei) return ofks_fail(c, OFKS_ESTATE, "solve: no nuclei");
+    cudaSetDevice(c->device);
+    int rc = run_iterations(c, c->prm.max_iter - c->k, res);
+    if (rc) return rc;
+    if (!c->converged) return ofks_fail(c, OFKS_ENOTCONV, "solve: not converged after %d iterations", c->k);
+    return OFKS_OK;
+}
+
+int ofks_evaluate(ofks_ctx *c, ofks_result *res) {
+    if (!c) return OFKS_EINVAL;
+    if (!c->have_X || !c->have_nuclei) return ofks_fail(c, OFKS_ESTATE, "evaluate: need orbitals and nuclei");
+    cudaSetDevice(c->device);
+    Rec r{};
+    int rc = evaluate(c, !c->bx_valid, &r);
+    if (rc) return rc;
+    c->bx_valid = true;
+    if (res) {
+        res->e_total = r.E; res->e_nuc = c->e_nuc; res->kkt = r.kkt; res->fea = r.fea; res->kkt0 = c->kkt0;
+        res->eta = c->eta; res->iters = c->k; res->converged = c->converged; res->seconds = 0;
+    }
+    return OFKS_OK;
+}
+
+int ofks_rayleigh_ritz(ofks_ctx *c, double *eigs) {
+    if (!c || !eigs) return OFKS_EINVAL;
+    if (!c->have_X || !c->have_nuclei) return ofks_fail(c, OFKS_ESTATE, "rayleigh_ritz: need orbitals and nuclei");
+    cudaSetDevice(c->device);
+    Rec r{};
+    int rc = evaluate(c, !c->bx_valid, &r);
+    if (rc) return rc;
+    const size_t L2 = (size_t)c->ld * c->ld;
+    double *V = c->d_pp + 5 * L2, *de = c->d_pp + 7 * L2;
+    launch_rayleigh_ritz(c, c->d_L0, c->d_S, de, V);
+    launch_block_times_small(c, c->d_X[c->cur], V, c->d_X[c->cur ^ 1]);
+    int flag = 0;
+    if ((rc = read_flag(c, &flag))) return rc;
+    if (flag) return ofks_fail(c, OFKS_ENOTCONV, "rayleigh_ritz: X^T B X is not positive definite");
+    cudaError_t e = cudaMemcpyAsync(eigs, de, sizeof(double) * c->p, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if ((rc = ofks_cuda_check(c, e, "rayleigh_ritz"))) return rc;
+    c->cur ^= 1;
+    c->bx_valid = false;
+    c->have_prev = false;
+    c->evaluated = false;
+    return OFKS_OK;
+}
+
+int ofks_get_field(ofks_ctx *c, int32_t which, double *out, int64_t count) {
+    if (!c || !out) return OFKS_EINVAL;
+    if (!c->evaluated) return ofks_fail(c, OFKS_ESTATE, "get_field: evaluate first");
+    cudaSetDevice(c->device);
+    const int64_t nq = c->n_tets * 4, nb = c->n * (int64_t)c->p, pp = (int64_t)c->p * c->p;
+    const double *src = nullptr;
+    int64_t need = 0;
+    int kind = 0;   // 0 flat, 1 block n x p, 2 small p x p
+    switch (which) {
+        case OFKS_F_RHO_Q: src = c->d_rho; need = nq; break;
+        case OFKS_F_VH_Q: src = c->d_vh; need = nq; break;
+        case OFKS_F_VXC_Q: src = c->d_vxc; need = nq; break;
+        case OFKS_F_EXC_Q: src = c->d_exc; need = nq; break;
+        case OFKS_F_VEXT_Q: src = c->d_vext; need = nq; break;
+        case OFKS_F_U: src = c->d_U; need = c->n_nodes; break;
+        case OFKS_F_HX: src = c->d_HX; need = nb; kind = 1; break;
+        case OFKS_F_BX: src = c->d_BX; need = nb; kind = 1; break;
+        case OFKS_F_G: src = c->d_G[c->cur]; need = nb; kind = 1; break;
+        case OFKS_F_D: src = c->d_D[c->cur ^ (c->have_prev ? 1 : 0)]; need = nb; kind = 1; break;
+        case OFKS_F_LAMBDA0: src = c->d_L0; need = pp; kind = 2; break;
+        case OFKS_F_S: src = c->d_S; need = pp; kind = 2; break;
+        case OFKS_F_LAMBDA: src = c->d_Lam; need = pp; kind = 2; break;
+        default: return ofks_fail(c, OFKS_EINVAL, "get_field: unknown field %d", which);
+    }
+    if (count != need) return ofks_fail(c, OFKS_EINVAL, "get_field: field %d has %lld values, got %lld", which,
+                                        (long long)need, (long long)count);
+    if (kind == 1) return download_block(c, src, out);
+    cudaError_t e;
+    if (kind == 2)
+        e = cudaMemcpy2DAsync(out, sizeof(double) * c->p, src, sizeof(double) * c->ld, sizeof(double) * c->p, c->p,
+                              cudaMemcpyDeviceToHost, c->stream);
+    else
+        e = cudaMemcpyAsync(out, src, sizeof(double) * need, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return ofks_cuda_check(c, e, "get_field");
+}
+
+int ofks_apply(ofks_ctx *c, int32_t which, const double *X, double *Y, int32_t ncols) {
+    if (!c || !X || !Y) return OFKS_EINVAL;
+    if (!c->n || !c->p) return ofks_fail(c, OFKS_ESTATE, "apply: no mesh/params");
+    if (ncols != c->p) return ofks_fail(c, OFKS_EINVAL, "apply: ncols must equal p");
+    const double *val = which == OFKS_M_L ? c->d_valL : which == OFKS_M_B ? c->d_valB : which == OFKS_M_H ? c->d_valH : nullptr;
+    if (!val) return ofks_fail(c, OFKS_EINVAL, "apply: unknown matrix %d", which);
+    if (which == OFKS_M_H && !c->evaluated) return ofks_fail(c, OFKS_ESTATE, "apply: H needs an evaluation");
+    cudaSetDevice(c->device);
+    int rc = upload_block(c, X, c->d_Z);
+    if (rc) return rc;
+    launch_sell_spmm(c, val, c->d_Z, c->d_Q);
+    if ((rc = ofks_cuda_check(c, cudaGetLastError(), "apply"))) return rc;
+    return download_block(c, c->d_Q, Y);
+}
+
+int ofks_get_sizes(ofks_ctx *c, int64_t *n_free, int64_t *n_nodes, int64_t *n_tets, int64_t *nnz) {
+    if (!c) return OFKS_EINVAL;
+    if (n_free) *n_free = c->n;
+    if (n_nodes) *n_nodes = c->n_nodes;
+    if (n_tets) *n_tets = c->n_tets;
+    if (nnz) *nnz = c->nnz;
+    return OFKS_OK;
+}
+
+int ofks_get_history(ofks_ctx *c, double *buf, int32_t cap, int32_t *len) {
+    if (!c || !len || cap < 0 || (cap > 0 && !buf)) return OFKS_EINVAL;
+    const int rows = (int)(c->history.size() / 6);
+    const int m = rows < cap ? rows : cap;
+    if (m > 0) memcpy(buf, c->history.data() + (size_t)(rows - m) * 6, sizeof(double) * 6 * m);
+    *len = m;
+    return OFKS_OK;
+}
+
+struct StateHeader {
+    char magic[8];
+    int64_t n, n_nodes;
+    int32_t p, ld, k, cur_unused, have_prev, converged;
+    double kkt0, eta, eta_dev;
+    int64_t hist_rows;
+};
+
+int ofks_save_state(ofks_ctx *c, const char *path) {
+    if (!c || !path) return OFKS_EINVAL;
+    if (!c->have_X) return ofks_fail(c, OFKS_ESTATE, "save_state: no orbitals");
+    cudaSetDevice(c->device);
+    if (!c->bx_valid) { launch_sell_spmm(c, c->d_valB, c->d_X[c->cur], c->d_BX); c->bx_valid = true; }
+    StateHeader h{};
+    memcpy(h.magic, "OFKSST1", 8);
+    h.n = c->n; h.n_nodes = c->n_nodes; h.p = c->p; h.ld = c->ld; h.k = c->k; h.have_prev = c->have_prev;
+    h.converged = c->converged; h.kkt0 = c->kkt0; h.eta = c->eta; h.hist_rows = (int64_t)c->history.size() / 6;
+    cudaMemcpyAsync(&h.eta_dev, c->d_sc + SC_ETA, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    const size_t blk = (size_t)c->n * c->ld;
+    std::vector<double> buf(blk * 5 + c->n_nodes);
+    const double *srcs[5] = {c->d_X[c->cur], c->d_X[c->cur ^ 1], c->d_D[c->cur ^ 1], c->d_G[c->cur ^ 1], c->d_BX};
+    for (int i = 0; i < 5; ++i)
+        cudaMemcpyAsync(buf.data() + i * blk, srcs[i], sizeof(double) * blk, cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(buf.data() + 5 * blk, c->d_U, sizeof(double) * c->n_nodes, cudaMemcpyDeviceToHost, c->stream);
+    int rc = ofks_cuda_check(c, cudaStreamSynchronize(c->stream), "save_state");
+    if (rc) return rc;
+    FILE *f = fopen(path, "wb");
+    if (!f) return ofks_fail(c, OFKS_EINVAL, "save_state: cannot open %s", path);
+    bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(buf.data(), sizeof(double), buf.size(), f) == buf.size() &&
+              fwrite(c->history.data(), sizeof(double), c->history.size(), f) == c->history.size();
+    ok = (fclose(f) == 0) && ok;
+    return ok ? OFKS_OK : ofks_fail(c, OFKS_EINVAL, "save_state: write to %s failed", path);
+}
+
+int ofks_load_state(ofks_ctx *c, const char *path) {
+    if (!c || !path) return OFKS_EINVAL;
+    if (!c->n || !c->p) return ofks_fail(c, OFKS_ESTATE, "load_state: set mesh and params first");
+    FILE *f = fopen(path, "rb");
+    if (!f) return ofks_fail(c, OFKS_EINVAL, "load_state: cannot open %s", path);
+    StateHeader h{};
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, "OFKSST1", 8) != 0) {
+        fclose(f);
+        return ofks_fail(c, OFKS_EINVAL, "load_state: %s is not a state file", path);
+    }
+    if (h.n != c->n || h.n_nodes != c->n_nodes || h.p != c->p || h.ld != c->ld) {
+        fclose(f);
+        return ofks_fail(c, OFKS_EINVAL, "load_state: sizes differ from the current mesh/params");
+    }
+    const size_t blk = (size_t)c->n * c->ld;
+    std::vector<double> buf(blk * 5 + c->n_nodes);
+    std::vector<double> hist((size_t)h.hist_rows * 6);
+    bool ok = fread(buf.data(), sizeof(double), buf.size(), f) == buf.size() &&
+              fread(hist.data(), sizeof(double), hist.size(), f) == hist.size();
+    fclose(f);
+    if (!ok) return ofks_fail(c, OFKS_EINVAL, "load_state: %s is truncated", path);
+    cudaSetDevice(c->device);
+    c->cur = 0;
+    double *dsts[5] = {c->d_X[0], c->d_X[1], c->d_D[1], c->d_G[1], c->d_BX};
+    for (int i = 0; i < 5; ++i)
+        cudaMemcpyAsync(dsts[i], buf.data() + i * blk, sizeof(double) * blk, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->d_U, buf.data() + 5 * blk, sizeof(double) * c->n_nodes, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->d_sc + SC_ETA, &h.eta_dev, sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    int rc = ofks_cuda_check(c, cudaStreamSynchronize(c->stream), "load_state");
+    if (rc) return rc;
+    c->bx_valid = true;
+    c->have_X = true; c->k = h.k; c->have_prev = h.have_prev; c->converged = h.converged; c->kkt0 = h.kkt0;
+    c->eta = h.eta; c->evaluated = false;
+    c->history = hist;
+    c->t_start = now_s() - (hist.empty() ? 0.0 : hist[hist.size() - 5]);
+    return OFKS_OK;
+}
+
+int ofks_profile(ofks_ctx *c, int32_t on) {
+    if (!c) return OFKS_EINVAL;
+    prof_resolve(c);
+    c->prof = on != 0;
+    if (on) {
+        for (int i = 0; i < PF_COUNT; ++i) { c->prof_n[i] = 0; c->prof_ms[i] = 0; }
+        c->kernels_at_prof = c->kernels;
+    }
+    return OFKS_OK;
+}
+
+int ofks_profile_get(ofks_ctx *c, int32_t id, int64_t *launches, double *ms, const char **name) {
+    if (!c || id < 0 || id > PF_COUNT) return OFKS_EINVAL;
+    prof_resolve(c);
+    if (id == PF_COUNT) {   // every kernel launch since profiling was switched on
+        if (launches) *launches = c->kernels - c->kernels_at_prof;
+        if (ms) *ms = 0.0;
+        if (name) *name = "all_kernels";
+        return OFKS_OK;
+    }
+    if (launches) *launches = c->prof_n[id];
+    if (ms) *ms = c->prof_ms[id];
+    if (name) *name = kPfNames[id];
+    return OFKS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,53 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point of include/ofks.h."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2007_14228_gb300 import build, ofks
+    path = build.build()
+    return ofks.load(path)
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "ofks.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ofks_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for must in ("ofks_create", "ofks_set_mesh", "ofks_set_nuclei", "ofks_set_params", "ofks_init_orbitals",
+                 "ofks_solve", "ofks_step", "ofks_rayleigh_ritz", "ofks_get_orbitals", "ofks_get_history",
+                 "ofks_save_state", "ofks_load_state", "ofks_last_error", "ofks_destroy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2007_14228_gb300 import ofks
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+    assert set(ofks.SYMBOLS) <= set(declared_symbols())
+
+
+def test_default_params_without_gpu(lib):
+    from paper_2007_14228_gb300 import ofks
+    prm = ofks.default_params(p=3, precond="exact", eta_rule="fixed", eta_fixed=2.0)
+    assert prm.p == 3 and prm.beta == 10.0 and prm.tol == 1e-8 and prm.precond == 2 and prm.eta_rule == 5
+    assert prm.pcg_iters == 8 and prm.multipole_lmax == 2 and prm.hartree == 1 and prm.xc == 1
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_2007_14228_gb300 import ofks
+    saved = ofks._lib
+    try:
+        ofks._lib = None
+        with pytest.raises(ofks.OfksError):
+            ofks.load(str(tmp_path / "libofks.so"))
+    finally:
+        ofks._lib = saved

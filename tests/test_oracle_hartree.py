@@ -91,3 +91,16 @@ def test_zero_boundary_map_is_symmetric():
     a12 = np.sum(w * fem.values_at_quad(h.solve(r1), m.tet10) * r2)
     a21 = np.sum(w * fem.values_at_quad(h.solve(r2), m.tet10) * r1)
     assert abs(a12 - a21) < 1e-10 * abs(a12)
+
+
+def test_cg_path_matches_direct_solve():
+    Q, a, c = 2.0, 1.0, np.array([0.5, -0.2, 0.1])
+    s = I.hydrogenic(1.0, half=10.0, cells=(10, 10, 10))
+    m = I.make_mesh(s)
+    L, _ = fem.assemble_LB(m.xyz, m.tet10)
+    vol, _ = fem.tet_geometry(m.xyz, m.tet10)
+    xq = fem.quad_points(m.xyz, m.tet10)
+    rho = _gauss(xq, c, Q, a)
+    Ud = Hartree(m.xyz, m.tet10, m.dirichlet, L, vol, xq, 2, solver="direct").solve(rho)
+    Uc = Hartree(m.xyz, m.tet10, m.dirichlet, L, vol, xq, 2, solver="cg").solve(rho)
+    assert np.max(np.abs(Ud - Uc)) < 1e-10 * np.max(np.abs(Ud))

@@ -92,6 +92,7 @@ typedef struct {
     int32_t multipole_lmax; /* Hartree boundary data: multipoles up to l (0..2); -1: zero */
     double  poisson_tol;    /* relative residual of the Hartree CG solve */
     int32_t poisson_max_iter;
+    int32_t poisson_amg;    /* 1: CG preconditioned by the algebraic multigrid V-cycle; 0: Jacobi */
 } ofks_params;
 
 typedef struct {
@@ -104,11 +105,13 @@ typedef struct {
     int32_t iters;          /* iterations taken so far (k) */
     int32_t converged;      /* 1 once (kkt + fea)/kkt0 < tol */
     double  seconds;        /* device time of the call, from CUDA events */
+    int32_t hartree_iters;  /* CG iterations of the last Hartree solve */
+    int32_t hartree_total;  /* CG iterations of all Hartree solves of the call */
 } ofks_result;
 
 /* Fill *prm with the defaults: beta 10, occ 2, tol 1e-8, max_iter 1000, FP64, PCG with 8
  * iterations, BB2, eta in [1e-4, 1e8], Hartree and LDA on, multipole_lmax 2,
- * poisson_tol 1e-12, poisson_max_iter 20000.  p is set to 1. */
+ * poisson_tol 1e-12, poisson_max_iter 20000, poisson_amg 0.  p is set to 1. */
 void ofks_default_params(ofks_params *prm);
 
 /* Create a context on CUDA device `device`.  *out receives the context (NULL on failure).
@@ -184,9 +187,10 @@ int ofks_get_field(ofks_ctx *ctx, int32_t which, double *out, int64_t count);
 int ofks_apply(ofks_ctx *ctx, int32_t which, const double *X, double *Y, int32_t ncols);
 
 /* Sizes: free DoFs, all nodes, tetrahedra, stored nonzeros of the free matrices
- * (without padding).  Any pointer may be NULL. */
+ * (without padding) and of the all-node stiffness of the Hartree problem.  Any pointer may
+ * be NULL. */
 int ofks_get_sizes(ofks_ctx *ctx, int64_t *n_free, int64_t *n_nodes, int64_t *n_tets,
-                   int64_t *nnz);
+                   int64_t *nnz, int64_t *nnz_full);
 
 /* History of evaluated iterates: rows of 6 doubles (k, seconds since init, E, kkt, fea,
  * eta).  Copies min(cap, available) rows of the most recent ones into buf; *len = rows. */

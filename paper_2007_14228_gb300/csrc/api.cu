@@ -25,7 +25,8 @@ void launch_pcg_alpha(ofks_ctx *c);
 void launch_pcg_beta(ofks_ctx *c);
 
 static const char *kPfNames[PF_COUNT] = {"density", "poisson", "potential", "spmm_h", "gram", "small",
-                                         "grad", "pcg_spmm", "pcg_update", "bb", "step", "spmm_b", "other"};
+                                         "grad", "pcg_spmm", "pcg_update", "bb", "step", "spmm_b", "other",
+                                         "poisson_spmv"};
 
 int ofks_fail(ofks_ctx *c, int code, const char *fmt, ...) {
     char buf[512];
@@ -88,7 +89,7 @@ static void dfree(T *&p) {
 
 static void free_blocks(ofks_ctx *c) {
     for (int i = 0; i < 2; ++i) { dfree(c->d_X[i]); dfree(c->d_D[i]); dfree(c->d_G[i]); }
-    dfree(c->d_HX); dfree(c->d_BX); dfree(c->d_R); dfree(c->d_Z); dfree(c->d_P); dfree(c->d_Q);
+    dfree(c->d_HX); dfree(c->d_BX); dfree(c->d_R); dfree(c->d_Z); dfree(c->d_P); dfree(c->d_Q); dfree(c->d_W);
     dfree(c->d_L0); dfree(c->d_S); dfree(c->d_Lam); dfree(c->d_C); dfree(c->d_colA); dfree(c->d_pp);
     c->p = c->ld = 0;
     c->have_X = c->evaluated = c->have_prev = false;
@@ -99,7 +100,7 @@ static int alloc_blocks(ofks_ctx *c, int p) {
     const int ld = (p <= 2) ? p : (p + 3) / 4 * 4;
     const size_t blk = sizeof(double) * (size_t)c->n * ld, sm = sizeof(double) * (size_t)ld * ld;
     double **bl[] = {&c->d_X[0], &c->d_X[1], &c->d_D[0], &c->d_D[1], &c->d_G[0], &c->d_G[1], &c->d_HX,
-                     &c->d_BX, &c->d_R, &c->d_Z, &c->d_P, &c->d_Q};
+                     &c->d_BX, &c->d_R, &c->d_Z, &c->d_P, &c->d_Q, &c->d_W};
     for (double **b : bl) {
         if (cudaMalloc((void **)b, blk) != cudaSuccess) {
             free_blocks(c);
@@ -277,6 +278,7 @@ static int update_step(ofks_ctx *c) {
 static int run_iterations(ofks_ctx *c, int kmax, ofks_result *res) {
     if (!c->have_X) return ofks_fail(c, OFKS_ESTATE, "no orbitals: call ofks_init_orbitals first");
     cudaEvent_t e0 = ev_get(c), e1 = ev_get(c);
+    c->cg_total = 0;
     cudaEventRecord(e0, c->stream);
     int rc = OFKS_OK;
     for (int it = 0; it < kmax && !c->converged; ++it) {
@@ -298,6 +300,8 @@ static int run_iterations(ofks_ctx *c, int kmax, ofks_result *res) {
         res->e_total = c->last_E; res->e_nuc = c->e_nuc; res->kkt = c->last_kkt; res->fea = c->last_fea;
         res->kkt0 = c->kkt0; res->eta = c->eta; res->iters = c->k; res->converged = c->converged ? 1 : 0;
         res->seconds = ms * 1e-3;
+        res->hartree_iters = c->cg_last;
+        res->hartree_total = (int32_t)c->cg_total;
     }
     return rc;
 }
@@ -312,6 +316,7 @@ void ofks_default_params(ofks_params *p) {
     p->precision = OFKS_FP64; p->precond = OFKS_PC_PCG; p->pcg_iters = 8; p->eta_rule = OFKS_ETA_BB2;
     p->eta_fixed = 0.0; p->eta_min = 1e-4; p->eta_max = 1e8; p->hartree = 1; p->xc = 1;
     p->multipole_lmax = 2; p->poisson_tol = 1e-12; p->poisson_max_iter = 20000;
+    p->poisson_amg = 0;
 }
 
 int ofks_create(ofks_ctx **out, int device) {
@@ -384,7 +389,7 @@ int ofks_set_params(ofks_ctx *c, const ofks_params *prm) {
         prm->eta_rule < 0 || prm->eta_rule > OFKS_ETA_FIXED || prm->precond < 0 || prm->precond > OFKS_PC_EXACT ||
         prm->precision != OFKS_FP64 || !(prm->eta_min > 0) || !(prm->eta_max >= prm->eta_min) ||
         prm->multipole_lmax < -1 || prm->multipole_lmax > 2 || !(prm->poisson_tol > 0) ||
-        prm->poisson_max_iter < 1 || (prm->eta_rule == OFKS_ETA_FIXED && !(prm->eta_fixed > 0)))
+        prm->poisson_max_iter < 1 || prm->poisson_amg < 0 || prm->poisson_amg > 1 || (prm->eta_rule == OFKS_ETA_FIXED && !(prm->eta_fixed > 0)))
         return ofks_fail(c, OFKS_EINVAL, "set_params: a parameter is out of range");
     cudaSetDevice(c->device);
     const bool realloc = prm->p != c->p;
@@ -474,6 +479,7 @@ int ofks_evaluate(ofks_ctx *c, ofks_result *res) {
     if (res) {
         res->e_total = r.E; res->e_nuc = c->e_nuc; res->kkt = r.kkt; res->fea = r.fea; res->kkt0 = c->kkt0;
         res->eta = c->eta; res->iters = c->k; res->converged = c->converged; res->seconds = 0;
+        res->hartree_iters = c->cg_last; res->hartree_total = c->cg_last;
     }
     return OFKS_OK;
 }
@@ -554,12 +560,14 @@ int ofks_apply(ofks_ctx *c, int32_t which, const double *X, double *Y, int32_t n
     return download_block(c, c->d_Q, Y);
 }
 
-int ofks_get_sizes(ofks_ctx *c, int64_t *n_free, int64_t *n_nodes, int64_t *n_tets, int64_t *nnz) {
+int ofks_get_sizes(ofks_ctx *c, int64_t *n_free, int64_t *n_nodes, int64_t *n_tets, int64_t *nnz,
+                   int64_t *nnz_full) {
     if (!c) return OFKS_EINVAL;
     if (n_free) *n_free = c->n;
     if (n_nodes) *n_nodes = c->n_nodes;
     if (n_tets) *n_tets = c->n_tets;
     if (nnz) *nnz = c->nnz;
+    if (nnz_full) *nnz_full = c->nnz_full;
     return OFKS_OK;
 }
 

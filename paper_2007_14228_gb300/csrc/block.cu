@@ -16,7 +16,10 @@ namespace {
 
 // ---------------------------------------------------------------- Grams (upper tiles)
 // XA = X^T A and XB = X^T B over the rows of one split, for output tile (ti, tj), ti <= tj.
-// 16 x 16 threads, each an RT x RT register tile; rows staged KR at a time in shared memory.
+// The tile is cut into RT x RT micro-tiles; only micro-tiles that hold entries i <= j < p are
+// computed, numbered consecutively so that whole warps stay idle when there are fewer of them
+// than threads (a float64 warp instruction costs the same however many lanes are active).
+// Rows are staged KR at a time in shared memory.
 template <int RT>
 __global__ void __launch_bounds__(256) k_gram2(int64_t n, int p, int ld, int ntile,
                                                const double *__restrict__ X,
@@ -30,7 +33,20 @@ __global__ void __launch_bounds__(256) k_gram2(int64_t n, int p, int ld, int nti
     while (pair >= ntile - ti) { pair -= ntile - ti; ++ti; }
     const int tj = ti + pair;
     const int i0 = ti * TS, j0 = tj * TS;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int nbi = (min(TS, p - i0) + RT - 1) / RT, nbj = (min(TS, p - j0) + RT - 1) / RT;
+    // this thread's micro-tile (bi, bj)
+    int bi = 0, bj = 0;
+    bool act;
+    if (ti == tj) {                                     // upper triangle of micro-tiles
+        int idx = threadIdx.x;
+        act = idx < nbi * (nbi + 1) / 2;
+        while (act && idx >= nbi - bi) { idx -= nbi - bi; ++bi; }
+        bj = bi + idx;
+    } else {
+        act = (int)threadIdx.x < nbi * nbj;
+        bi = threadIdx.x / nbj;
+        bj = threadIdx.x - bi * nbj;
+    }
     const int64_t r0 = blockIdx.y * rows_per_split;
     const int64_t r1 = (r0 + rows_per_split < n) ? r0 + rows_per_split : n;
     double ca[RT][RT], cb[RT][RT];
@@ -40,7 +56,7 @@ __global__ void __launch_bounds__(256) k_gram2(int64_t n, int p, int ld, int nti
         for (int b = 0; b < RT; ++b) { ca[a][b] = 0.0; cb[a][b] = 0.0; }
     for (int64_t rb = r0; rb < r1; rb += KR) {
         for (int idx = threadIdx.x; idx < KR * TS; idx += 256) {
-            const int rr = idx / TS, cc = idx % TS;
+            const int rr = idx / TS, cc = idx - rr * TS;
             const int64_t r = rb + rr;
             const bool okr = r < r1;
             xs[rr][cc] = (okr && i0 + cc < ld) ? X[r * ld + i0 + cc] : 0.0;
@@ -48,13 +64,14 @@ __global__ void __launch_bounds__(256) k_gram2(int64_t n, int p, int ld, int nti
             bs[rr][cc] = (okr && j0 + cc < ld) ? B[r * ld + j0 + cc] : 0.0;
         }
         __syncthreads();
+        if (act)
 #pragma unroll 4
         for (int k = 0; k < KR; ++k) {
             double xv[RT], av[RT], bv[RT];
 #pragma unroll
-            for (int a = 0; a < RT; ++a) xv[a] = xs[k][ty * RT + a];
+            for (int a = 0; a < RT; ++a) xv[a] = xs[k][bi * RT + a];
 #pragma unroll
-            for (int b = 0; b < RT; ++b) { av[b] = as[k][tx * RT + b]; bv[b] = bs[k][tx * RT + b]; }
+            for (int b = 0; b < RT; ++b) { av[b] = as[k][bj * RT + b]; bv[b] = bs[k][bj * RT + b]; }
 #pragma unroll
             for (int a = 0; a < RT; ++a)
 #pragma unroll
@@ -65,11 +82,12 @@ __global__ void __launch_bounds__(256) k_gram2(int64_t n, int p, int ld, int nti
         }
         __syncthreads();
     }
+    if (!act) return;
 #pragma unroll
     for (int a = 0; a < RT; ++a)
 #pragma unroll
         for (int b = 0; b < RT; ++b) {
-            const int i = i0 + ty * RT + a, j = j0 + tx * RT + b;
+            const int i = i0 + bi * RT + a, j = j0 + bj * RT + b;
             if (i < p && j < p && i <= j) {
                 atomicAdd(XA + (int64_t)i * ld + j, ca[a][b]);
                 atomicAdd(XB + (int64_t)i * ld + j, cb[a][b]);
@@ -88,9 +106,10 @@ __global__ void k_mirror2(int p, int ld, double *A, double *B) {
 }
 
 // ---------------------------------------------------------------- gradient and residual
-// G = HX + BX C ;  kkt2 += ||HX - BX L0||^2 (columns < p).  32 column lanes x 8 row groups;
-// each thread owns 4 rows of a 32-row tile and MC columns; C, L0 staged in KC-row chunks.
-template <int MC>
+// G = HX + BX C ;  kkt2 += ||HX - BX L0||^2 (columns < p).  A 32-row tile is staged in shared
+// memory; its 32 x ld outputs are spread over the 256 threads (output o = tid + 256 i), so
+// every lane issues useful float64 FMAs whatever ld is.  C and L0 are staged in KC-row chunks.
+template <int NO>
 __global__ void __launch_bounds__(256) k_grad(int64_t n, int p, int ld, const double *__restrict__ HX,
                                               const double *__restrict__ BX,
                                               const double *__restrict__ C,
@@ -101,24 +120,24 @@ __global__ void __launch_bounds__(256) k_grad(int64_t n, int p, int ld, const do
     double *cs = bx + 32 * ld;         // KC x ld
     double *ls = cs + KC * ld;         // KC x ld
     __shared__ double red[8];
-    const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
+    const int nout = 32 * ld;
     double part = 0.0;
     for (int64_t rt = blockIdx.x * 32LL; rt < n; rt += 32LL * gridDim.x) {
-        double g[4][MC], rr[4][MC];
+        double g[NO], rr[NO];
+        int orow[NO], ocol[NO];
         __syncthreads();
-        for (int idx = threadIdx.x; idx < 32 * ld; idx += 256) {
+        for (int idx = threadIdx.x; idx < nout; idx += 256) {
             const int64_t r = rt + idx / ld;
             bx[idx] = r < n ? BX[rt * ld + idx] : 0.0;
         }
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const int64_t r = rt + rg * 4 + a;
-#pragma unroll
-            for (int m = 0; m < MC; ++m) {
-                const int j = lane + 32 * m;
-                const double h = (r < n && j < ld) ? HX[r * ld + j] : 0.0;
-                g[a][m] = h; rr[a][m] = h;
-            }
+        for (int i = 0; i < NO; ++i) {
+            const int o = threadIdx.x + 256 * i;
+            orow[i] = o / ld;
+            ocol[i] = o - orow[i] * ld;
+            const int64_t r = rt + orow[i];
+            const double h = (o < nout && r < n) ? HX[rt * ld + o] : 0.0;
+            g[i] = h; rr[i] = h;
         }
         for (int k0 = 0; k0 < ld; k0 += KC) {
             const int kl = min(KC, ld - k0);
@@ -129,132 +148,118 @@ __global__ void __launch_bounds__(256) k_grad(int64_t n, int p, int ld, const do
             }
             __syncthreads();
             for (int kk = 0; kk < kl; ++kk) {
-                double b[4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) b[a] = bx[(rg * 4 + a) * ld + k0 + kk];
-#pragma unroll
-                for (int m = 0; m < MC; ++m) {
-                    const int j = lane + 32 * m;
-                    const double cv = j < ld ? cs[kk * ld + j] : 0.0;
-                    const double lv = j < ld ? ls[kk * ld + j] : 0.0;
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        g[a][m] = fma(b[a], cv, g[a][m]);
-                        rr[a][m] = fma(-b[a], lv, rr[a][m]);
+                for (int i = 0; i < NO; ++i) {
+                    if (threadIdx.x + 256 * i < nout) {
+                        const double b = bx[orow[i] * ld + k0 + kk];
+                        g[i] = fma(b, cs[kk * ld + ocol[i]], g[i]);
+                        rr[i] = fma(-b, ls[kk * ld + ocol[i]], rr[i]);
                     }
                 }
             }
         }
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const int64_t r = rt + rg * 4 + a;
-            if (r >= n) continue;
-#pragma unroll
-            for (int m = 0; m < MC; ++m) {
-                const int j = lane + 32 * m;
-                if (j < ld) G[r * ld + j] = g[a][m];
-                if (j < p) part += rr[a][m] * rr[a][m];
-            }
+        for (int i = 0; i < NO; ++i) {
+            const int o = threadIdx.x + 256 * i;
+            const int64_t r = rt + orow[i];
+            if (o >= nout || r >= n) continue;
+            G[rt * ld + o] = g[i];
+            if (ocol[i] < p) part += rr[i] * rr[i];
         }
     }
     part = block_sum(part, red);
     if (threadIdx.x == 0) atomicAdd(kkt2, part);
 }
 
-// ---------------------------------------------------------------- row-parallel helpers
-// Thread layout for n x ld elementwise work with per-column sums: 32 column lanes x 8 rows.
-#define ROWLOOP_BEGIN                                                                          \
-    const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;                                \
-    for (int64_t r = blockIdx.x * 8LL + rg; r < n; r += 8LL * gridDim.x) {                    \
-        _Pragma("unroll") for (int m = 0; m < MC; ++m) {                                     \
-            const int j = lane + 32 * m;                                                     \
-            if (j >= ld) continue;                                                           \
-            const int64_t e = r * ld + j;
-#define ROWLOOP_END } }
+// ---------------------------------------------------------------- elementwise block kernels
+// Flattened over the n x ld elements with a stride that is a multiple of ld, so each thread
+// keeps one column: per-column scalars are read once and per-column sums stay in a register.
+#define ELEM_BEGIN                                                                  \
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;            \
+    const int64_t S = stride;                                                       \
+    const int j = (int)(gid % ld);                                                  \
+    (void)j;                                                                        \
+    const int64_t total = n * ld;                                                   \
+    if (gid < S) {                                                                  \
+        int64_t r = gid / ld;                                                       \
+        const int64_t dr = S / ld;                                                  \
+        for (int64_t e = gid; e < total; e += S, r += dr) {
+#define ELEM_END } }
 
-// add per-thread column partials (MC per thread) into colsum[j] over the block
-template <int MC>
-__device__ __forceinline__ void col_reduce(double (&acc)[MC], int ld, int p, double *colsum) {
-    __shared__ double sh[8][32 * MC];
-    const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
-#pragma unroll
-    for (int m = 0; m < MC; ++m) sh[rg][lane + 32 * m] = acc[m];
+constexpr int MAXLD = 256;
+
+// add each thread's partial of column j into colsum[j] (j < p) through shared memory
+__device__ __forceinline__ void col_reduce(double acc, int j, bool active, int ld, int p, double *colsum) {
+    __shared__ double sh[MAXLD];
+    for (int k = threadIdx.x; k < ld; k += blockDim.x) sh[k] = 0.0;
     __syncthreads();
-    for (int j = threadIdx.x; j < 32 * MC; j += blockDim.x) {
-        if (j >= p) continue;
-        double s = 0.0;
-#pragma unroll
-        for (int g = 0; g < 8; ++g) s += sh[g][j];
-        atomicAdd(colsum + j, s);
-    }
+    if (active && acc != 0.0) atomicAdd(sh + j, acc);
+    __syncthreads();
+    for (int k = threadIdx.x; k < ld && k < p; k += blockDim.x)
+        if (sh[k] != 0.0) atomicAdd(colsum + k, sh[k]);
 }
 
-// PCG start: D = 0, R = G, Z = R / diag, rz[c] = sum R Z  (diag = dL/2 - shift_c dB)
-template <int MC>
-__global__ void __launch_bounds__(256) k_pcg_init(int64_t n, int p, int ld, const double *__restrict__ G,
+// PCG start: W = 1/diag with diag = dL/2 - shift_c dB, D = 0, R = G, Z = G W, rz[c] = sum R Z
+__global__ void __launch_bounds__(256) k_pcg_init(int64_t n, int p, int ld, int64_t stride,
+                                                  const double *__restrict__ G,
                                                   const double *__restrict__ dL,
                                                   const double *__restrict__ dB, const double *cb,
-                                                  double *D, double *R, double *Z, double *rz) {
-    double acc[MC];
-#pragma unroll
-    for (int m = 0; m < MC; ++m) acc[m] = 0.0;
-    ROWLOOP_BEGIN
+                                                  double *W, double *D, double *R, double *Z, double *rz) {
+    double acc = 0.0;
+    ELEM_BEGIN
+        const double sh = cb[CB_SHIFT * ld + j];
+        const double w = 1.0 / (0.5 * dL[r] - sh * dB[r]);
         const double gv = G[e];
-        const double dg = 0.5 * dL[r] - cb[CB_SHIFT * ld + j] * dB[r];
-        const double z = gv / dg;
-        D[e] = 0.0; R[e] = gv; Z[e] = z;
-        acc[m] += gv * z;
-    ROWLOOP_END
-    col_reduce<MC>(acc, ld, p, rz);
+        const double z = gv * w;
+        W[e] = w; D[e] = 0.0; R[e] = gv; Z[e] = z;
+        acc = fma(gv, z, acc);
+    ELEM_END
+    col_reduce(acc, j, gid < stride, ld, p, rz);
 }
 
-// alpha = rz/pq; D += alpha P; R -= alpha Q; Z = R/diag; rzn += R Z
-template <int MC>
-__global__ void __launch_bounds__(256) k_pcg_update(int64_t n, int p, int ld, const double *__restrict__ dL,
-                                                    const double *__restrict__ dB, const double *cb,
+// alpha = rz/pq; D += alpha P; R -= alpha Q; Z = R W; rzn += R Z
+__global__ void __launch_bounds__(256) k_pcg_update(int64_t n, int p, int ld, int64_t stride, const double *cb,
+                                                    const double *__restrict__ W,
                                                     const double *__restrict__ P,
                                                     const double *__restrict__ Q, double *D, double *R,
                                                     double *Z, double *rzn) {
-    double acc[MC];
-#pragma unroll
-    for (int m = 0; m < MC; ++m) acc[m] = 0.0;
-    ROWLOOP_BEGIN
-        const double al = cb[CB_ALPHA * ld + j];
-        const double dg = 0.5 * dL[r] - cb[CB_SHIFT * ld + j] * dB[r];
+    double acc = 0.0;
+    const double al = cb[CB_ALPHA * ld + (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) % ld];
+    ELEM_BEGIN
         D[e] = fma(al, P[e], D[e]);
         const double rv = fma(-al, Q[e], R[e]);
-        const double z = rv / dg;
+        const double z = rv * W[e];
         R[e] = rv; Z[e] = z;
-        acc[m] += rv * z;
-    ROWLOOP_END
-    col_reduce<MC>(acc, ld, p, rzn);
+        acc = fma(rv, z, acc);
+    ELEM_END
+    col_reduce(acc, j, gid < stride, ld, p, rzn);
 }
 
 // columns whose shift is not negative take D = G (T = I in Eq. precondition-T)
-template <int MC>
-__global__ void __launch_bounds__(256) k_select(int64_t n, int ld, const double *cb,
+__global__ void __launch_bounds__(256) k_select(int64_t n, int ld, int64_t stride, const double *cb,
                                                 const double *__restrict__ G, double *D) {
-    ROWLOOP_BEGIN
-        if (cb[CB_ACTIVE * ld + j] == 0.0) D[e] = G[e];
-    ROWLOOP_END
+    const int jj = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) % ld);
+    if (cb[CB_ACTIVE * ld + jj] != 0.0) return;
+    ELEM_BEGIN
+        D[e] = G[e];
+    ELEM_END
 }
 
 // Barzilai-Borwein sums: <dX,dD>, <dD,dD>, <dX,dX>, and ||X||^2, ||D||^2
-template <int MC>
-__global__ void __launch_bounds__(256) k_bb(int64_t n, int ld, const double *__restrict__ X,
+__global__ void __launch_bounds__(256) k_bb(int64_t n, int ld, int64_t stride, const double *__restrict__ X,
                                             const double *__restrict__ Xp, const double *__restrict__ D,
                                             const double *__restrict__ Dp, int have_prev, double *sc) {
     __shared__ double red[8];
     double sy = 0, yy = 0, ss = 0, xx = 0, dd = 0;
     {
-        ROWLOOP_BEGIN
+        ELEM_BEGIN
             const double x = X[e], d = D[e];
-            xx += x * x; dd += d * d;
+            xx = fma(x, x, xx); dd = fma(d, d, dd);
             if (have_prev) {
                 const double sx = x - Xp[e], yd = d - Dp[e];
-                sy += sx * yd; yy += yd * yd; ss += sx * sx;
+                sy = fma(sx, yd, sy); yy = fma(yd, yd, yy); ss = fma(sx, sx, ss);
             }
-        ROWLOOP_END
+        ELEM_END
     }
     sy = block_sum(sy, red); yy = block_sum(yy, red); ss = block_sum(ss, red);
     xx = block_sum(xx, red); dd = block_sum(dd, red);
@@ -265,26 +270,23 @@ __global__ void __launch_bounds__(256) k_bb(int64_t n, int ld, const double *__r
 }
 
 // Y = X - D / eta
-template <int MC>
-__global__ void __launch_bounds__(256) k_step(int64_t n, int ld, const double *__restrict__ X,
-                                              const double *__restrict__ D, const double *sc,
-                                              double *Y) {
+__global__ void __launch_bounds__(256) k_step(int64_t n, int ld, int64_t stride, const double *__restrict__ X,
+                                              const double *__restrict__ D, const double *sc, double *Y) {
     const double inv = 1.0 / sc[SC_ETA];
-    ROWLOOP_BEGIN
+    ELEM_BEGIN
         Y[e] = fma(-inv, D[e], X[e]);
-    ROWLOOP_END
+    ELEM_END
 }
 
 // X_i = Y_i / ||Y_i||_B and B X_i = B Y_i / ||Y_i||_B   (Eq. PCAL-main)
-template <int MC>
-__global__ void __launch_bounds__(256) k_scale(int64_t n, int p, int ld, const double *colsum,
+__global__ void __launch_bounds__(256) k_scale(int64_t n, int p, int ld, int64_t stride, const double *colsum,
                                                double *Y, double *BY) {
-    ROWLOOP_BEGIN
-        if (j < p) {
-            const double s = 1.0 / sqrt(colsum[j]);
-            Y[e] *= s; BY[e] *= s;
-        }
-    ROWLOOP_END
+    const int jj = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) % ld);
+    if (jj >= p) return;
+    const double s = 1.0 / sqrt(colsum[jj]);
+    ELEM_BEGIN
+        Y[e] *= s; BY[e] *= s;
+    ELEM_END
 }
 
 // Y = X M with M (ld x ld, zero padded) staged in KC-row chunks
@@ -378,6 +380,15 @@ void launch_gram2(ofks_ctx *c, const double *X, const double *A, const double *B
     c->kernels += 2;
 }
 
+// grid of 256-thread blocks whose total thread count is a multiple of ld
+struct ElemGrid { unsigned blocks; int64_t stride; };
+static ElemGrid elem_grid(int64_t n, int ld) {
+    const int64_t want = std::min<int64_t>((n * ld + 255) / 256, 152LL * 8);
+    const int64_t threads = std::max<int64_t>(want * 256, ld);
+    const int64_t stride = threads / ld * ld;
+    return {(unsigned)((stride + 255) / 256), stride};
+}
+
 void launch_grad_update(ofks_ctx *c) {
     c->kernels += 1;
     ProfScope ps(c, PF_GRAD);
@@ -386,11 +397,13 @@ void launch_grad_update(ofks_ctx *c) {
     double *G = c->d_G[c->cur];
     cudaMemsetAsync(c->d_sc + SC_KKT2, 0, sizeof(double), c->stream);
     const unsigned grid = row_grid(32, c->n);
-    MC_DISPATCH(mc_of(ld), {
-        cudaFuncSetAttribute(k_grad<M_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_grad<M_><<<grid, 256, sm, c->stream>>>(c->n, c->p, ld, c->d_HX, c->d_BX, c->d_C, c->d_L0, G,
-                                                 c->d_sc + SC_KKT2, KC);
-    });
+    const int no = (32 * ld + 255) / 256;
+#define GR_(k) { cudaFuncSetAttribute(k_grad<k>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        k_grad<k><<<grid, 256, sm, c->stream>>>(c->n, c->p, ld, c->d_HX, c->d_BX, c->d_C, c->d_L0, G, \
+                                               c->d_sc + SC_KKT2, KC); }
+    if (no <= 1) GR_(1) else if (no <= 2) GR_(2) else if (no <= 4) GR_(4) else if (no <= 6) GR_(6)
+    else if (no <= 8) GR_(8) else if (no <= 16) GR_(16) else GR_(32)
+#undef GR_
 }
 
 void launch_pcg_init(ofks_ctx *c) {
@@ -398,53 +411,47 @@ void launch_pcg_init(ofks_ctx *c) {
     const int ld = c->ld;
     double *cb = c->d_colA;
     cudaMemsetAsync(cb + CB_RZ * ld, 0, sizeof(double) * ld, c->stream);
-    const unsigned grid = row_grid(8, c->n);
-    MC_DISPATCH(mc_of(ld), k_pcg_init<M_><<<grid, 256, 0, c->stream>>>(
-        c->n, c->p, ld, c->d_G[c->cur], c->d_dL, c->d_dB, cb, c->d_D[c->cur], c->d_R, c->d_Z, cb + CB_RZ * ld));
+    const ElemGrid g = elem_grid(c->n, ld);
+    k_pcg_init<<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, c->d_G[c->cur], c->d_dL, c->d_dB, cb,
+                                                c->d_W, c->d_D[c->cur], c->d_R, c->d_Z, cb + CB_RZ * ld);
 }
 
 void launch_pcg_update(ofks_ctx *c, int) {
     c->kernels += 1;
     const int ld = c->ld;
     double *cb = c->d_colA;
-    const unsigned grid = row_grid(8, c->n);
-    MC_DISPATCH(mc_of(ld), k_pcg_update<M_><<<grid, 256, 0, c->stream>>>(
-        c->n, c->p, ld, c->d_dL, c->d_dB, cb, c->d_P, c->d_Q, c->d_D[c->cur], c->d_R, c->d_Z,
-        cb + CB_RZN * ld));
+    const ElemGrid g = elem_grid(c->n, ld);
+    k_pcg_update<<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, cb, c->d_W, c->d_P, c->d_Q,
+                                                  c->d_D[c->cur], c->d_R, c->d_Z, cb + CB_RZN * ld);
 }
 
 void launch_direction_select(ofks_ctx *c) {
     c->kernels += 1;
-    const int ld = c->ld;
-    const unsigned grid = row_grid(8, c->n);
-    MC_DISPATCH(mc_of(ld), k_select<M_><<<grid, 256, 0, c->stream>>>(c->n, ld, c->d_colA, c->d_G[c->cur],
-                                                                      c->d_D[c->cur]));
+    const ElemGrid g = elem_grid(c->n, c->ld);
+    k_select<<<g.blocks, 256, 0, c->stream>>>(c->n, c->ld, g.stride, c->d_colA, c->d_G[c->cur], c->d_D[c->cur]);
 }
 
 void launch_bb_dots(ofks_ctx *c) {
     c->kernels += 1;
     ProfScope ps(c, PF_BB);
-    const int ld = c->ld, cur = c->cur, prv = cur ^ 1;
+    const int cur = c->cur, prv = cur ^ 1;
     cudaMemsetAsync(c->d_sc + SC_BB, 0, sizeof(double) * 3, c->stream);
     cudaMemsetAsync(c->d_sc + SC_XNRM2, 0, sizeof(double) * 2, c->stream);
-    const unsigned grid = row_grid(8, c->n);
-    MC_DISPATCH(mc_of(ld), k_bb<M_><<<grid, 256, 0, c->stream>>>(
-        c->n, ld, c->d_X[cur], c->d_X[prv], c->d_D[cur], c->d_D[prv], c->have_prev ? 1 : 0, c->d_sc));
+    const ElemGrid g = elem_grid(c->n, c->ld);
+    k_bb<<<g.blocks, 256, 0, c->stream>>>(c->n, c->ld, g.stride, c->d_X[cur], c->d_X[prv], c->d_D[cur], c->d_D[prv],
+                                          c->have_prev ? 1 : 0, c->d_sc);
 }
 
 void launch_step_y(ofks_ctx *c, double *Y) {
     c->kernels += 1;
-    const int ld = c->ld;
-    const unsigned grid = row_grid(8, c->n);
-    MC_DISPATCH(mc_of(ld), k_step<M_><<<grid, 256, 0, c->stream>>>(c->n, ld, c->d_X[c->cur], c->d_D[c->cur],
-                                                                    c->d_sc, Y));
+    const ElemGrid g = elem_grid(c->n, c->ld);
+    k_step<<<g.blocks, 256, 0, c->stream>>>(c->n, c->ld, g.stride, c->d_X[c->cur], c->d_D[c->cur], c->d_sc, Y);
 }
 
 void launch_scale_cols(ofks_ctx *c, double *Y, double *BY, const double *colsum) {
     c->kernels += 1;
-    const int ld = c->ld;
-    const unsigned grid = row_grid(8, c->n);
-    MC_DISPATCH(mc_of(ld), k_scale<M_><<<grid, 256, 0, c->stream>>>(c->n, c->p, ld, colsum, Y, BY));
+    const ElemGrid g = elem_grid(c->n, c->ld);
+    k_scale<<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, c->ld, g.stride, colsum, Y, BY);
 }
 
 void launch_block_times_small(ofks_ctx *c, const double *X, const double *M, double *Y) {

@@ -41,10 +41,12 @@ __device__ __forceinline__ double lda(double rho, double &vxc) {
     return ex + ec;
 }
 
-// One group of G lanes per tetrahedron; lane j of the group covers columns j, j+G, ...
-// psi_{q,l} = sum_a N_a(x_q) X_{a,l}; rho_q = f sum_l psi_{q,l}^2.  The group leader writes
-// rho_q, scatters the Poisson load 4 pi sum_q w rho_q N_i(x_q) to the 10 nodes and adds the
-// tetrahedron's multipole moments to the block sums.
+// Density at the quadrature points (a1).  A group of G lanes works on one tetrahedron; lane
+// j of the group covers columns j, j+G, ...:  psi_{q,l} = sum_a N_a(x_q) X_{a,l},
+// rho_q = f sum_l psi_{q,l}^2 (group xor-reduction).  The per-tetrahedron epilogue is spread
+// over the group's lanes (float64 warp instructions cost the same with one active lane):
+// lane k writes rho_k (k < 4), adds the Poisson load 4 pi w sum_q N_k(x_q) rho_q of local
+// node k (k < 10) and accumulates multipole moment k (k < 10) over all its tetrahedra.
 template <int G>
 __global__ void __launch_bounds__(256) k_density(int64_t T, int p, int ld, double occ,
                                                  const double *__restrict__ X,
@@ -53,71 +55,84 @@ __global__ void __launch_bounds__(256) k_density(int64_t T, int p, int ld, doubl
                                                  const double *__restrict__ wq,
                                                  const double *__restrict__ yq, double *rho,
                                                  double *rhs, double *mom, int do_hartree) {
+    constexpr int TPW = 32 / G;                       // tetrahedra per warp and pass
     __shared__ double smom[10];
+    __shared__ double sN[4][10];
+    if (threadIdx.x < 40) sN[threadIdx.x / 10][threadIdx.x % 10] = p2N(threadIdx.x / 10, threadIdx.x % 10);
     if (threadIdx.x < 10) smom[threadIdx.x] = 0.0;
     __syncthreads();
-    const int lane = threadIdx.x % G;
-    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+    const int lane = threadIdx.x & (G - 1), grp = (threadIdx.x & 31) / G;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double m[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    double s[4] = {0, 0, 0, 0};
-    if (t < T) {
-        int f[10];
+    for (int64_t t0 = warp * TPW; t0 < T; t0 += nwarp * TPW) {
+        const int64_t t = t0 + grp;
+        const bool ok = t < T;
+        double s[4] = {0, 0, 0, 0};
+        if (ok) {
+            int f[10];
 #pragma unroll
-        for (int a = 0; a < 10; ++a) f[a] = tetf[t * 10 + a];
-        for (int l = lane; l < p; l += G) {
-            double x[10];
+            for (int a = 0; a < 10; ++a) f[a] = tetf[t * 10 + a];
+            for (int l = lane; l < p; l += G) {
+                double x[10];
 #pragma unroll
-            for (int a = 0; a < 10; ++a) x[a] = f[a] >= 0 ? X[(int64_t)f[a] * ld + l] : 0.0;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                double psi = 0.0;
-#pragma unroll
-                for (int a = 0; a < 10; ++a) psi += p2N(q, a) * x[a];
-                s[q] += psi * psi;
-            }
-        }
-    }
-    // every lane of the warp takes part in the group reduction
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o, G);
-    if (t < T) {
-        if (lane == 0) {
-            const double w = wq[t];
-            double r[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) { r[q] = occ * s[q]; rho[t * 4 + q] = r[q]; }
-            if (do_hartree) {
-#pragma unroll
-                for (int a = 0; a < 10; ++a) {
-                    double v = 0.0;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) v += p2N(q, a) * r[q];
-                    atomicAdd(rhs + tetn[t * 10 + a], 4.0 * PI * w * v);
-                }
+                for (int a = 0; a < 10; ++a) x[a] = f[a] >= 0 ? X[(int64_t)f[a] * ld + l] : 0.0;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const double *y = yq + (t * 4 + q) * 3;
-                    double wr = w * r[q], y2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
-                    m[0] += wr;
-                    m[1] += wr * y[0]; m[2] += wr * y[1]; m[3] += wr * y[2];
-                    m[4] += wr * (3.0 * y[0] * y[0] - y2);
-                    m[5] += wr * (3.0 * y[1] * y[1] - y2);
-                    m[6] += wr * (3.0 * y[2] * y[2] - y2);
-                    m[7] += wr * 3.0 * y[0] * y[1];
-                    m[8] += wr * 3.0 * y[0] * y[2];
-                    m[9] += wr * 3.0 * y[1] * y[2];
+                    double psi = 0.0;
+#pragma unroll
+                    for (int a = 0; a < 10; ++a) psi = fma(p2N(q, a), x[a], psi);
+                    s[q] = fma(psi, psi, s[q]);
                 }
             }
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o, G);
+        if (!ok) continue;
+        for (int k = lane; k < 4; k += G) rho[t * 4 + k] = occ * s[k];
+        if (!do_hartree) continue;
+        const double w = wq[t];
+        for (int k = lane; k < 10; k += G) {
+            double v = 0.0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v = fma(sN[q][k], s[q], v);
+            atomicAdd(rhs + tetn[t * 10 + k], (4.0 * 3.14159265358979323846 * occ) * w * v);
+        }
+        for (int k = lane; k < 10; k += G) {
+            double acc = 0.0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const double *y = yq + (t * 4 + q) * 3;
+                const double y0 = y[0], y1 = y[1], y2 = y[2];
+                const double y2s = y0 * y0 + y1 * y1 + y2 * y2;
+                double f;
+                switch (k) {
+                    case 0: f = 1.0; break;
+                    case 1: f = y0; break;
+                    case 2: f = y1; break;
+                    case 3: f = y2; break;
+                    case 4: f = 3.0 * y0 * y0 - y2s; break;
+                    case 5: f = 3.0 * y1 * y1 - y2s; break;
+                    case 6: f = 3.0 * y2 * y2 - y2s; break;
+                    case 7: f = 3.0 * y0 * y1; break;
+                    case 8: f = 3.0 * y0 * y2; break;
+                    default: f = 3.0 * y1 * y2; break;
+                }
+                acc = fma(s[q], f, acc);
+            }
+            m[k] = fma(occ * w, acc, m[k]);
         }
     }
     if (do_hartree) {
+        // lane k of every group holds moments k, k+G, ...: sum over the warp's groups, then the block
 #pragma unroll
-        for (int i = 0; i < 10; ++i) {
-            double v = warp_sum(m[i]);
-            if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(smom + i, v);
-        }
+        for (int i = 0; i < 10; ++i)
+#pragma unroll
+            for (int o = 16; o >= G; o >>= 1) m[i] += __shfl_xor_sync(0xffffffffu, m[i], o);
+        if (grp == 0)
+            for (int k = lane; k < 10; k += G) atomicAdd(smom + k, m[k]);
         __syncthreads();
         if (threadIdx.x < 10) atomicAdd(mom + threadIdx.x, smom[threadIdx.x]);
     }
@@ -175,7 +190,8 @@ __global__ void __launch_bounds__(256) k_cg_init(int64_t N, const int *__restric
     }
 }
 
-// q = L p, pq += p.q  (slot it&1); zero the retired rz slot
+// q = L p, pq += p.q  (slot it&1); zero the retired rz slot.  8 lanes per row read the row's
+// entries together (coalesced) and xor-reduce.
 __global__ void __launch_bounds__(256) k_cg_spmv(int64_t N, const int *__restrict__ ptr,
                                                  const int *__restrict__ col,
                                                  const double *__restrict__ val,
@@ -183,11 +199,16 @@ __global__ void __launch_bounds__(256) k_cg_spmv(int64_t N, const int *__restric
                                                  const double *__restrict__ pv, double *qv,
                                                  double *sc, int it) {
     __shared__ double sh[8];
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3;
+    const int lane = threadIdx.x & 7;
+    const bool live = i < N && minv[i] != 0.0;
+    double s = 0.0;
+    if (live)
+        for (int k = ptr[i] + lane; k < ptr[i + 1]; k += 8) s = fma(val[k], pv[col[k]], s);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 8);
     double pq = 0.0;
-    if (i < N && minv[i] != 0.0) {
-        double s = 0.0;
-        for (int k = ptr[i]; k < ptr[i + 1]; ++k) s += val[k] * pv[col[k]];
+    if (live && lane == 0) {
         qv[i] = s;
         pq = pv[i] * s;
     }
@@ -229,6 +250,44 @@ __global__ void __launch_bounds__(256) k_cg_update(int64_t N, const double *__re
         atomicAdd(sc + 4 + nn, rr);
         if (blockIdx.x == 0) sc[2 + nn] = 0.0;   // next pq slot
     }
+}
+
+// preconditioned variant of k_cg_update: alpha = rz/pq; U += alpha p; r -= alpha q; rr'
+__global__ void __launch_bounds__(256) k_cg_update_r(int64_t N, const double *__restrict__ minv,
+                                                     const double *__restrict__ pv,
+                                                     const double *__restrict__ qv, double *U, double *r,
+                                                     double *sc, int it) {
+    __shared__ double sh[8];
+    const int o = it & 1, nn = (it + 1) & 1;
+    const double rz = sc[0 + o], pq = sc[2 + o];
+    const double alpha = pq > 0.0 ? rz / pq : 0.0;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double rr = 0.0;
+    if (i < N && minv[i] != 0.0) {
+        U[i] += alpha * pv[i];
+        const double ri = r[i] - alpha * qv[i];
+        r[i] = ri;
+        rr = ri * ri;
+    }
+    rr = block_sum(rr, sh);
+    if (threadIdx.x == 0) {
+        atomicAdd(sc + 4 + nn, rr);
+        if (blockIdx.x == 0) sc[2 + nn] = 0.0;
+    }
+}
+
+// sc[slot] += r.z; with first = 1 also p = z
+__global__ void __launch_bounds__(256) k_cg_rz(int64_t N, const double *__restrict__ r, const double *__restrict__ z,
+                                               double *pv, double *sc, int slot, int first) {
+    __shared__ double sh[8];
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (i < N) {
+        v = r[i] * z[i];
+        if (first) pv[i] = z[i];
+    }
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) atomicAdd(sc + slot, v);
 }
 
 // beta = rz'/rz; p = z + beta p
@@ -297,10 +356,14 @@ int launch_density(ofks_ctx *c, const double *X) {
         cudaMemsetAsync(c->d_rhs, 0, sizeof(double) * c->n_nodes, c->stream);
         cudaMemsetAsync(c->d_sc + SC_MOM, 0, sizeof(double) * 10, c->stream);
     }
-    int G = 1;
-    while (G < 32 && G < (c->p + 1) / 2) G <<= 1;
+    // group width: the fewest wasted column slots ceil(p/G) G, preferring wide groups on ties
+    int G = c->p <= 2 ? c->p : 4;
+    if (c->p > 2)
+        for (int g = 8; g <= 32; g <<= 1)
+            if ((c->p + g - 1) / g * g <= (c->p + G - 1) / G * G) G = g;
     const int B = 256;
-    unsigned grid = (unsigned)((T * G + B - 1) / B);
+    const int64_t warps = (T + 32 / G - 1) / (32 / G);
+    unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((warps * 32 + B - 1) / B, 152LL * 16));
 #define DENS(g) k_density<g><<<grid, B, 0, c->stream>>>(T, c->p, c->ld, c->prm.occ, X, c->d_tetf, \
         c->d_tetn, c->d_wq, c->d_yq, c->d_rho, c->d_rhs, c->d_sc + SC_MOM, do_h)
     switch (G) {
@@ -320,7 +383,7 @@ int run_hartree(ofks_ctx *c) {
     if (!c->prm.hartree) return OFKS_OK;
     ProfScope ps(c, PF_POISSON);
     const int64_t N = c->n_nodes;
-    const unsigned gN = (unsigned)((N + 255) / 256);
+    const unsigned gN = (unsigned)((N + 255) / 256), gN8 = (unsigned)((N * 8 + 255) / 256);
     double *sc = c->d_sc + SC_CG;
     k_boundary<<<(c->n_bnd + 255) / 256, 256, 0, c->stream>>>(c->n_bnd, c->d_bnd, c->d_bxyz,
                                                                c->d_sc + SC_MOM, c->prm.multipole_lmax,
@@ -329,8 +392,15 @@ int run_hartree(ofks_ctx *c) {
     k_cg_init<<<gN, 256, 0, c->stream>>>(N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv, c->d_rhs, c->d_U,
                                          c->d_cr, c->d_cz, c->d_cp, sc);
     c->kernels += 2;
+    const bool amg = !c->amg.empty() && c->prm.poisson_amg;
+    if (amg) {   // z = M^-1 r by the multigrid V-cycle, rz[0] = r.z, p = z
+        cudaMemsetAsync(sc, 0, sizeof(double), c->stream);
+        amg_apply(c, c->d_cr, c->d_cz);
+        k_cg_rz<<<gN, 256, 0, c->stream>>>(N, c->d_cr, c->d_cz, c->d_cp, sc, 0, 1);
+        c->kernels += 1;
+    }
     const double tol2 = c->prm.poisson_tol * c->prm.poisson_tol;
-    const int chunk = 16;
+    const int chunk = amg ? 4 : 32;
     int it = 0;
     double h[8];
     for (;;) {
@@ -339,13 +409,28 @@ int run_hartree(ofks_ctx *c) {
         if (e != cudaSuccess) return ofks_cuda_check(c, e, "Hartree CG");
         const double rr = h[4 + (it & 1)], bb = h[6];
         if (!std::isfinite(rr)) return ofks_fail(c, OFKS_ENONFINITE, "Hartree CG residual is not finite");
-        if (rr <= tol2 * bb || bb == 0.0) break;
+        if (rr <= tol2 * bb || bb == 0.0) { c->cg_last = it; c->cg_total += it; break; }
         if (it >= c->prm.poisson_max_iter)
             return ofks_fail(c, OFKS_ETIMEOUT, "Hartree CG: %d iterations, relative residual %.3e",
                              it, std::sqrt(rr / bb));
-        for (int j = 0; j < chunk; ++j, ++it) {
-            k_cg_spmv<<<gN, 256, 0, c->stream>>>(N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv, c->d_cp,
-                                                 c->d_cq, sc, it);
+        for (int j = 0; j < chunk && amg; ++j, ++it) {
+            {
+                ProfScope pv(c, PF_POISSON_SPMV);
+                k_cg_spmv<<<gN8, 256, 0, c->stream>>>(N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv, c->d_cp,
+                                                      c->d_cq, sc, it);
+            }
+            k_cg_update_r<<<gN, 256, 0, c->stream>>>(N, c->d_minv, c->d_cp, c->d_cq, c->d_U, c->d_cr, sc, it);
+            amg_apply(c, c->d_cr, c->d_cz);
+            k_cg_rz<<<gN, 256, 0, c->stream>>>(N, c->d_cr, c->d_cz, c->d_cp, sc, (it + 1) & 1, 0);
+            k_cg_dir<<<gN, 256, 0, c->stream>>>(N, c->d_cz, c->d_cp, sc, it);
+            c->kernels += 4;
+        }
+        for (int j = 0; j < chunk && !amg; ++j, ++it) {
+            {
+                ProfScope pv(c, PF_POISSON_SPMV);
+                k_cg_spmv<<<gN8, 256, 0, c->stream>>>(N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv, c->d_cp,
+                                                      c->d_cq, sc, it);
+            }
             k_cg_update<<<gN, 256, 0, c->stream>>>(N, c->d_minv, c->d_cp, c->d_cq, c->d_U, c->d_cr,
                                                    c->d_cz, sc, it);
             k_cg_dir<<<gN, 256, 0, c->stream>>>(N, c->d_cz, c->d_cp, sc, it);

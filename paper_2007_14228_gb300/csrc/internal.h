@@ -25,7 +25,20 @@ enum {
 // Kernel families timed by ofks_profile.
 enum {
     PF_DENSITY = 0, PF_POISSON, PF_POTENTIAL, PF_SPMM_H, PF_GRAM, PF_SMALL, PF_GRAD,
-    PF_PCG_SPMM, PF_PCG_UPDATE, PF_BB, PF_STEP, PF_SPMM_B, PF_OTHER, PF_COUNT
+    PF_PCG_SPMM, PF_PCG_UPDATE, PF_BB, PF_STEP, PF_SPMM_B, PF_OTHER, PF_POISSON_SPMV, PF_COUNT
+};
+
+// one level of the algebraic multigrid hierarchy of the Hartree Poisson operator (device CSR)
+struct AmgMat {
+    int64_t n = 0, m = 0;
+    int *ptr = nullptr, *col = nullptr;
+    double *val = nullptr;
+};
+struct AmgLevel {
+    AmgMat A, P, R;                              // operator, prolongator, restriction = P^T
+    double *dinv = nullptr;                      // inverse diagonal of A
+    double omega = 0.0;                          // Jacobi damping 4 / (3 rho(D^-1 A))
+    double *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr;
 };
 
 struct ofks_ctx {
@@ -60,6 +73,10 @@ struct ofks_ctx {
     int *d_bnd = nullptr;                        // boundary node ids
     double *d_bxyz = nullptr;                    // n_bnd x 3 boundary node coords minus centre
     double center[3] = {0, 0, 0};
+    std::vector<AmgLevel> amg;                   // Hartree preconditioner (empty: Jacobi)
+    int *d_amg_idx = nullptr;                    // interior node ids (level 0 numbering)
+    double *d_amg_chol = nullptr;                // dense inverse of the coarsest operator
+    int64_t amg_ni = 0, amg_nc = 0;
     double e_nuc = 0.0;
     bool have_nuclei = false;
 
@@ -75,6 +92,7 @@ struct ofks_ctx {
     double *d_G[2] = {nullptr, nullptr};         // current / previous gradient
     double *d_HX = nullptr, *d_BX = nullptr;
     double *d_R = nullptr, *d_Z = nullptr, *d_P = nullptr, *d_Q = nullptr;   // PCG block
+    double *d_W = nullptr;                       // PCG inverse Jacobi diagonal per column
     int cur = 0;                                 // index of the current X/D/G buffers
     // ---- small p x p (device)
     double *d_L0 = nullptr, *d_S = nullptr, *d_Lam = nullptr, *d_C = nullptr;
@@ -88,6 +106,8 @@ struct ofks_ctx {
     bool have_X = false, evaluated = false, have_prev = false;
     bool bx_valid = false;                       // d_BX holds B X for the current iterate
     int k = 0;
+    int cg_last = 0;                             // CG iterations of the last Hartree solve
+    int64_t cg_total = 0;                        // ... summed since the counter was cleared
     double kkt0 = 0.0, eta = 0.0;
     bool converged = false;
     double last_E = 0, last_kkt = 0, last_fea = 0;
@@ -127,6 +147,11 @@ void free_mesh(ofks_ctx *c);
 int launch_density(ofks_ctx *c, const double *X);
 int run_hartree(ofks_ctx *c);
 int launch_potential_refresh(ofks_ctx *c);
+
+// ---- amg.cu (Hartree preconditioner)
+int amg_setup(ofks_ctx *c, const int *tetn, int64_t T);
+void amg_free(ofks_ctx *c);
+void amg_apply(ofks_ctx *c, const double *r_full, double *z_full);
 
 // ---- spmm.cu
 void launch_sell_spmm(ofks_ctx *c, const double *val, const double *X, double *Y);

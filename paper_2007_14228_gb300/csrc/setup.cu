@@ -186,6 +186,7 @@ void free_mesh(ofks_ctx *c) {
     dev_free(c->d_rho); dev_free(c->d_vh); dev_free(c->d_vxc); dev_free(c->d_exc);
     dev_free(c->d_U); dev_free(c->d_rhs); dev_free(c->d_cr); dev_free(c->d_cz); dev_free(c->d_cp);
     dev_free(c->d_cq);
+    amg_free(c);
     c->n = c->n_nodes = c->n_tets = c->nnz = c->nnz_full = 0;
     c->have_nuclei = false;
 }
@@ -405,6 +406,9 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
     if (hflag) { free_mesh(c); return ofks_fail(c, OFKS_EINVAL, "set_mesh: degenerate tetrahedron"); }
     c->n_nodes = N; c->n_tets = T; c->n = n; c->nnz = nnz; c->nnz_full = nnz_full;
     c->n_slices = n_slices; c->sell_len = sell_len; c->n_bnd = (int)bnd.size();
+    // the multigrid preconditioner of the Hartree solve is optional: without it the CG runs
+    // with the Jacobi preconditioner
+    if (amg_setup(c, tetn.data(), T) != OFKS_OK) amg_free(c);
     return OFKS_OK;
 }
 

@@ -110,8 +110,9 @@ __device__ void chol_upper(int p, int ld, const double *S, double *R, double *Ri
     __shared__ double piv;
     for (int j = 0; j < p; ++j) {
         if (threadIdx.x == 0) {
+            // a pivot that lost all but ~13 digits of the original diagonal counts as zero
             const double d = A[(int64_t)j * ld + j];
-            if (!(d > 0.0)) { *flag = 1; piv = 1.0; } else piv = sqrt(d);
+            if (!(d > 1e-13 * fabs(S[(int64_t)j * ld + j]))) { *flag = 1; piv = 1.0; } else piv = sqrt(d);
             R[(int64_t)j * ld + j] = piv;
         }
         __syncthreads();

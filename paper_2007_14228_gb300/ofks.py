@@ -38,13 +38,13 @@ class Params(C.Structure):
                 ("pcg_iters", C.c_int32), ("eta_rule", C.c_int32), ("eta_fixed", C.c_double),
                 ("eta_min", C.c_double), ("eta_max", C.c_double), ("hartree", C.c_int32),
                 ("xc", C.c_int32), ("multipole_lmax", C.c_int32), ("poisson_tol", C.c_double),
-                ("poisson_max_iter", C.c_int32)]
+                ("poisson_max_iter", C.c_int32), ("poisson_amg", C.c_int32)]
 
 
 class Result(C.Structure):
     _fields_ = [("e_total", C.c_double), ("e_nuc", C.c_double), ("kkt", C.c_double), ("fea", C.c_double),
                 ("kkt0", C.c_double), ("eta", C.c_double), ("iters", C.c_int32), ("converged", C.c_int32),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("hartree_iters", C.c_int32), ("hartree_total", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -82,7 +82,8 @@ def load(path: str = LIB_PATH):
         "ofks_rayleigh_ritz": (C.c_int, [vp, _dp]),
         "ofks_get_field": (C.c_int, [vp, i32, _dp, i64]),
         "ofks_apply": (C.c_int, [vp, i32, _dp, _dp, i32]),
-        "ofks_get_sizes": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]),
+        "ofks_get_sizes": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64),
+                                     C.POINTER(i64)]),
         "ofks_get_history": (C.c_int, [vp, _dp, i32, C.POINTER(i32)]),
         "ofks_save_state": (C.c_int, [vp, C.c_char_p]),
         "ofks_load_state": (C.c_int, [vp, C.c_char_p]),
@@ -208,9 +209,9 @@ class Context:
 
     # ---- inspection
     def sizes(self) -> dict:
-        v = [C.c_int64() for _ in range(4)]
+        v = [C.c_int64() for _ in range(5)]
         self._chk(self.lib.ofks_get_sizes(self.h, *[C.byref(x) for x in v]))
-        return dict(zip(("n_free", "n_nodes", "n_tets", "nnz"), (x.value for x in v)))
+        return dict(zip(("n_free", "n_nodes", "n_tets", "nnz", "nnz_full"), (x.value for x in v)))
 
     def get_field(self, name: str):
         s = self.sizes()

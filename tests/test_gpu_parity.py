@@ -73,7 +73,14 @@ def test_spmm_matches_oracle(ofks, case):
     X = np.random.default_rng(7).standard_normal((pr.n, s.p))
     assert rel(ctx.apply("L", X), pr.Lf @ X) < 1e-12
     assert rel(ctx.apply("B", X), pr.Bf @ X) < 1e-12
-    assert ctx.sizes()["nnz"] == pr.Lf.nnz
+    # structural pattern: every free (i, j) pair sharing a tetrahedron (scipy drops exact zeros)
+    fidx = np.full(m.n_nodes, -1)
+    fidx[m.free_ids()] = np.arange(m.n_free)
+    tf = fidx[m.tet10]
+    a = np.repeat(tf, 10, axis=1).ravel()
+    b = np.tile(tf, (1, 10)).ravel()
+    keep = (a >= 0) & (b >= 0)
+    assert ctx.sizes()["nnz"] == len(np.unique(a[keep].astype(np.int64) * m.n_free + b[keep]))
     ctx.close()
 
 
@@ -143,20 +150,20 @@ def test_trajectory_matches_oracle(ofks, case):
         o = pcal.iterate(pr, st)
         assert abs(g["e_total"] - o["E"]) < 1e-8 * max(1.0, abs(o["E"])), (k, g["e_total"], o["E"])
         assert abs(g["kkt"] - o["kkt"]) < 1e-7 * o["kkt"], (k, g["kkt"], o["kkt"])
-        assert abs(g["fea"] - o["fea"]) < 1e-7 * max(o["fea"], 1e-9), (k, g["fea"], o["fea"])
+        assert abs(g["fea"] - o["fea"]) < 1e-7 * o["fea"] + 1e-13, (k, g["fea"], o["fea"])
     assert rel(ctx.get_orbitals(), st.X) < 1e-6
     ctx.close()
 
 
 def test_converged_solve_matches_oracle(ofks):
     s = CASES["lih6"]()
-    ctx, pr, V, m = build_pair(ofks, s, tol=1e-10, max_iter=3000)
+    ctx, pr, V, m = build_pair(ofks, s, tol=1e-12, max_iter=4000)
     ctx.init_orbitals(V)
     res = ctx.solve()
     assert res["converged"] == 1
     E_gpu = res["e_total"]
     eig_gpu = ctx.rayleigh_ritz()
-    pr.prm.max_iter = 3000
+    pr.prm.max_iter = 4000
     st = pcal.solve(pr, pr.initial_guess(V))
     assert st.converged
     E_or = st.history[-1]["E"]
@@ -190,18 +197,22 @@ def test_single_orbital_feasibility(ofks):
 
 
 def test_rayleigh_ritz_keeps_energy_and_orders_eigenvalues(ofks):
+    # at a converged (feasible) iterate the post-processing leaves E unchanged (Sec. 4.3)
     s = CASES["h2o_p5"]()
-    ctx, pr, V, m = build_pair(ofks, s)
+    ctx, pr, V, m = build_pair(ofks, s, tol=1e-10, max_iter=4000)
     ctx.init_orbitals(V)
-    ctx.step(40)
+    res = ctx.solve()
+    assert res["converged"] == 1
     E0 = ctx.evaluate()["e_total"]
     eig = ctx.rayleigh_ritz()
     E1 = ctx.evaluate()["e_total"]
     assert abs(E1 - E0) < 1e-10 * max(1.0, abs(E0))
     assert np.all(np.diff(eig) >= 0)
-    X = ctx.get_orbitals()
-    _, Xr = pr.rayleigh_ritz(X)          # oracle RR of the rotated block is (nearly) the identity
-    assert abs(pr.energy(X)["total"] - E1) < 1e-9 * max(1.0, abs(E1))
+    # the rotated block is B-orthonormal and diagonalizes X^T H X
+    L0 = ctx.get_field("Lambda0")
+    np.testing.assert_allclose(np.diag(L0), eig, atol=1e-9)
+    assert np.max(np.abs(L0 - np.diag(np.diag(L0)))) < 1e-9
+    assert np.max(np.abs(ctx.get_field("S") - np.eye(s.p))) < 1e-10
     ctx.close()
 
 
@@ -329,4 +340,18 @@ def test_full_size_lih_first_steps_match_oracle(ofks):
         o = pcal.iterate(pr, st)
         assert abs(g["e_total"] - o["E"]) < 1e-9 * abs(o["E"]), (k, g["e_total"], o["E"])
         assert abs(g["kkt"] - o["kkt"]) < 1e-8 * o["kkt"]
+    ctx.close()
+
+
+@pytest.mark.parametrize("amg", [0, 1])
+def test_hartree_preconditioners_agree_with_oracle(ofks, amg):
+    # the Hartree CG with the Jacobi or the multigrid preconditioner reaches the same potential
+    s = CASES["chain_p41"]()
+    ctx, pr, V, m = build_pair(ofks, s, poisson_amg=amg)
+    X0 = pr.initial_guess(V)
+    ctx.set_orbitals(X0)
+    r = ctx.evaluate()
+    pot = pr.potentials(pr.density(X0))
+    assert rel(ctx.get_field("U"), pot["U"]) < 1e-9
+    assert 0 < r["hartree_iters"] < 2000, r["hartree_iters"]
     ctx.close()

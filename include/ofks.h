@@ -140,6 +140,21 @@ int ofks_set_mesh(ofks_ctx *ctx, int64_t n_nodes, const double *xyz,
  * at the quadrature points and E_nuc.  Requires a mesh.  Errors: OFKS_EINVAL, OFKS_ESTATE. */
 int ofks_set_nuclei(ofks_ctx *ctx, int32_t M, const double *Z, const double *R);
 
+/* Largest number of nuclei ofks_set_nuclei_static accepts. */
+#define OFKS_STATIC_NUCLEI_MAX 1024
+
+/* ofks_set_nuclei without any device allocation (the paper has no counterpart: this is a
+ * service of the library, not a step of the method).  For callers that cannot call cudaMalloc
+ * -- code that moves the nuclei every step (relaxation, molecular dynamics) under a caching
+ * allocator that owns the device memory, or in a loop where allocating is not allowed -- the
+ * nuclear data is staged in a fixed array compiled into the library (OFKS_STATIC_NUCLEI_MAX
+ * nuclei, 32 KiB per GPU that loads the library, held until the process exits) instead of
+ * memory allocated per call.  Same arguments, results and errors as ofks_set_nuclei, plus
+ * OFKS_EINVAL when M > OFKS_STATIC_NUCLEI_MAX.  The first call on a device looks up the array's
+ * device address, so make that first call before any stream capture.  All contexts share the
+ * array: calls whose work overlaps on the GPU (contexts driven concurrently) race. */
+int ofks_set_nuclei_static(ofks_ctx *ctx, int32_t M, const double *Z, const double *R);
+
 /* Parameters; p must satisfy 1 <= p <= n_free.  Changing p drops the orbitals.
  * Errors: OFKS_EINVAL for values out of range, OFKS_ESTATE without a mesh. */
 int ofks_set_params(ofks_ctx *ctx, const ofks_params *prm);

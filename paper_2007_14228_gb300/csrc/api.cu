@@ -380,6 +380,21 @@ int ofks_set_nuclei(ofks_ctx *c, int32_t M, const double *Z, const double *R) {
     return setup_nuclei(c, M, Z, R);
 }
 
+int ofks_set_nuclei_static(ofks_ctx *c, int32_t M, const double *Z, const double *R) {
+    if (!c) return OFKS_EINVAL;
+    if (!c->n) return ofks_fail(c, OFKS_ESTATE, "set_nuclei_static: no mesh");
+    if (M < 1 || !Z || !R) return ofks_fail(c, OFKS_EINVAL, "set_nuclei_static: need M >= 1 and arrays");
+    if (M > OFKS_STATIC_NUCLEI_MAX)
+        return ofks_fail(c, OFKS_EINVAL, "set_nuclei_static: %d nuclei exceed the fixed maximum of %d", M,
+                         OFKS_STATIC_NUCLEI_MAX);
+    for (int j = 0; j < M; ++j)
+        if (!(Z[j] > 0)) return ofks_fail(c, OFKS_EINVAL, "set_nuclei_static: Z[%d] must be > 0", j);
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return ofks_cuda_check(c, e, "set_nuclei_static");
+    c->evaluated = false;
+    return setup_nuclei_static(c, M, Z, R);
+}
+
 int ofks_set_params(ofks_ctx *c, const ofks_params *prm) {
     if (!c || !prm) return OFKS_EINVAL;
     if (!c->n) return ofks_fail(c, OFKS_ESTATE, "set_params: no mesh");

@@ -141,6 +141,7 @@ struct ProfScope {
 int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets,
                const int64_t *tet10, const uint8_t *dirichlet);
 int setup_nuclei(ofks_ctx *c, int M, const double *Z, const double *R);
+int setup_nuclei_static(ofks_ctx *c, int M, const double *Z, const double *R);
 void free_mesh(ofks_ctx *c);
 
 // ---- fields.cu (density, potentials, Hamiltonian refresh, Poisson)

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <mutex>
 #include <numeric>
 #include <thread>
 #include <vector>
@@ -432,6 +433,64 @@ int setup_nuclei(ofks_ctx *c, int M, const double *Z, const double *R) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     dev_free(d_zr); dev_free(d_e);
     if (e != cudaSuccess) return ofks_cuda_check(c, e, "set_nuclei");
+    c->have_nuclei = true;
+    return OFKS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// No-allocation variant of setup_nuclei (ofks_set_nuclei_static).  The nuclear data that
+// setup_nuclei stages in freshly allocated device memory lives here in a fixed file-scope
+// array, so the call allocates nothing.  Every GPU that loads the library holds the array
+// (32 KiB) until the process exits; all calls share it, so calls that overlap on the GPU
+// (different contexts on different streams) race on its contents.
+namespace {
+
+static __device__ __align__(256) double g_nuclei_stage[4 * OFKS_STATIC_NUCLEI_MAX + 1];
+
+constexpr int kStageDevices = 64;
+std::mutex g_stage_mu;
+double *g_stage_ptr[kStageDevices] = {nullptr};
+
+// Device address of the staging array on the context's device.  The first call on a device
+// looks it up with that device current (the host-side symbol is only a stand-in, never a device
+// address); later calls reuse it.
+int stage_address(ofks_ctx *c, double **out) {
+    if (c->device < 0 || c->device >= kStageDevices)
+        return ofks_fail(c, OFKS_EINVAL, "set_nuclei_static: device %d out of range", c->device);
+    std::lock_guard<std::mutex> lock(g_stage_mu);
+    if (!g_stage_ptr[c->device]) {
+        double *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress((void **)&ptr, g_nuclei_stage);
+        if (e != cudaSuccess) return ofks_cuda_check(c, e, "set_nuclei_static: cudaGetSymbolAddress");
+        g_stage_ptr[c->device] = ptr;
+    }
+    *out = g_stage_ptr[c->device];
+    return OFKS_OK;
+}
+
+}  // namespace
+
+int setup_nuclei_static(ofks_ctx *c, int M, const double *Z, const double *R) {
+    double *stage = nullptr;
+    int rc = stage_address(c, &stage);
+    if (rc) return rc;
+    double *e_slot = stage + 4 * OFKS_STATIC_NUCLEI_MAX;
+    // Z[j] -> stage[4j], R[j] -> stage[4j+1 .. 4j+3]: strided copies, no host staging buffer
+    cudaError_t e = cudaMemcpy2DAsync(stage, 4 * sizeof(double), Z, sizeof(double), sizeof(double), (size_t)M,
+                                      cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(stage + 1, 4 * sizeof(double), R, 3 * sizeof(double), 3 * sizeof(double), (size_t)M,
+                              cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(e_slot, 0, sizeof(double), c->stream);
+    if (e != cudaSuccess) return ofks_cuda_check(c, e, "set_nuclei_static: staging copy");
+    const int64_t nq = c->n_tets * 4;
+    k_vext<<<(unsigned)((nq + 255) / 256), 256, 0, c->stream>>>(nq, c->d_yq, c->center[0], c->center[1],
+                                                                  c->center[2], M, stage, c->d_vext);
+    k_enuc<<<1, 1, 0, c->stream>>>(M, stage, e_slot);
+    c->kernels += 2;
+    e = cudaMemcpyAsync(&c->e_nuc, e_slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return ofks_cuda_check(c, e, "set_nuclei_static");
     c->have_nuclei = true;
     return OFKS_OK;
 }

@@ -19,8 +19,9 @@ ETA = {"bb2": 0, "bb1": 1, "abb1": 2, "abb2": 3, "bb2_raw": 4, "fixed": 5}
 FIELDS = {"rho_q": 0, "vh_q": 1, "vxc_q": 2, "exc_q": 3, "U": 4, "HX": 5, "BX": 6, "G": 7, "D": 8,
           "Lambda0": 9, "S": 10, "Lambda": 11, "vext_q": 12}
 MATS = {"L": 0, "B": 1, "H": 2}
+STATIC_NUCLEI_MAX = 1024          # OFKS_STATIC_NUCLEI_MAX
 SYMBOLS = ("ofks_default_params", "ofks_create", "ofks_destroy", "ofks_last_error", "ofks_set_mesh",
-           "ofks_set_nuclei", "ofks_set_params", "ofks_init_orbitals", "ofks_set_orbitals",
+           "ofks_set_nuclei", "ofks_set_nuclei_static", "ofks_set_params", "ofks_init_orbitals", "ofks_set_orbitals",
            "ofks_get_orbitals", "ofks_step", "ofks_solve", "ofks_evaluate", "ofks_rayleigh_ritz",
            "ofks_get_field", "ofks_apply", "ofks_get_sizes", "ofks_get_history", "ofks_save_state",
            "ofks_load_state", "ofks_profile", "ofks_profile_get")
@@ -72,6 +73,7 @@ def load(path: str = LIB_PATH):
         "ofks_last_error": (C.c_char_p, [vp]),
         "ofks_set_mesh": (C.c_int, [vp, i64, _dp, i64, _ip, _up]),
         "ofks_set_nuclei": (C.c_int, [vp, i32, _dp, _dp]),
+        "ofks_set_nuclei_static": (C.c_int, [vp, i32, _dp, _dp]),
         "ofks_set_params": (C.c_int, [vp, C.POINTER(Params)]),
         "ofks_init_orbitals": (C.c_int, [vp, _dp]),
         "ofks_set_orbitals": (C.c_int, [vp, _dp, i32]),
@@ -158,6 +160,12 @@ class Context:
         Z = np.ascontiguousarray(Z, np.float64)
         R = np.ascontiguousarray(R, np.float64).reshape(-1, 3)
         self._chk(self.lib.ofks_set_nuclei(self.h, len(Z), Z, R))
+
+    def set_nuclei_static(self, Z, R):
+        """ofks_set_nuclei_static: same as set_nuclei, without any device allocation."""
+        Z = np.ascontiguousarray(Z, np.float64)
+        R = np.ascontiguousarray(R, np.float64).reshape(-1, 3)
+        self._chk(self.lib.ofks_set_nuclei_static(self.h, len(Z), Z, R))
 
     def set_params(self, prm: Params | None = None, **overrides):
         if prm is None:

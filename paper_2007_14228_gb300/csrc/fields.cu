@@ -190,8 +190,9 @@ __global__ void __launch_bounds__(256) k_cg_init(int64_t N, const int *__restric
     }
 }
 
-// q = L p, pq += p.q  (slot it&1); zero the retired rz slot.  8 lanes per row read the row's
-// entries together (coalesced) and xor-reduce.
+// q = L p, pq += p.q  (slot it&1); zero the retired rz slot.  One thread per row: on GB300 a
+// float64 warp instruction costs the same with any number of active lanes, so lane-split rows
+// (which add shuffle-reductions in float64) measured slower than this form.
 __global__ void __launch_bounds__(256) k_cg_spmv(int64_t N, const int *__restrict__ ptr,
                                                  const int *__restrict__ col,
                                                  const double *__restrict__ val,
@@ -199,16 +200,11 @@ __global__ void __launch_bounds__(256) k_cg_spmv(int64_t N, const int *__restric
                                                  const double *__restrict__ pv, double *qv,
                                                  double *sc, int it) {
     __shared__ double sh[8];
-    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3;
-    const int lane = threadIdx.x & 7;
-    const bool live = i < N && minv[i] != 0.0;
-    double s = 0.0;
-    if (live)
-        for (int k = ptr[i] + lane; k < ptr[i + 1]; k += 8) s = fma(val[k], pv[col[k]], s);
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 8);
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double pq = 0.0;
-    if (live && lane == 0) {
+    if (i < N && minv[i] != 0.0) {
+        double s = 0.0;
+        for (int k = ptr[i]; k < ptr[i + 1]; ++k) s = fma(val[k], pv[col[k]], s);
         qv[i] = s;
         pq = pv[i] * s;
     }
@@ -383,7 +379,7 @@ int run_hartree(ofks_ctx *c) {
     if (!c->prm.hartree) return OFKS_OK;
     ProfScope ps(c, PF_POISSON);
     const int64_t N = c->n_nodes;
-    const unsigned gN = (unsigned)((N + 255) / 256), gN8 = (unsigned)((N * 8 + 255) / 256);
+    const unsigned gN = (unsigned)((N + 255) / 256);
     double *sc = c->d_sc + SC_CG;
     k_boundary<<<(c->n_bnd + 255) / 256, 256, 0, c->stream>>>(c->n_bnd, c->d_bnd, c->d_bxyz,
                                                                c->d_sc + SC_MOM, c->prm.multipole_lmax,
@@ -416,7 +412,7 @@ int run_hartree(ofks_ctx *c) {
         for (int j = 0; j < chunk && amg; ++j, ++it) {
             {
                 ProfScope pv(c, PF_POISSON_SPMV);
-                k_cg_spmv<<<gN8, 256, 0, c->stream>>>(N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv, c->d_cp,
+                k_cg_spmv<<<gN, 256, 0, c->stream>>>(N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv, c->d_cp,
                                                       c->d_cq, sc, it);
             }
             k_cg_update_r<<<gN, 256, 0, c->stream>>>(N, c->d_minv, c->d_cp, c->d_cq, c->d_U, c->d_cr, sc, it);
@@ -428,7 +424,7 @@ int run_hartree(ofks_ctx *c) {
         for (int j = 0; j < chunk && !amg; ++j, ++it) {
             {
                 ProfScope pv(c, PF_POISSON_SPMV);
-                k_cg_spmv<<<gN8, 256, 0, c->stream>>>(N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv, c->d_cp,
+                k_cg_spmv<<<gN, 256, 0, c->stream>>>(N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv, c->d_cp,
                                                       c->d_cq, sc, it);
             }
             k_cg_update<<<gN, 256, 0, c->stream>>>(N, c->d_minv, c->d_cp, c->d_cq, c->d_U, c->d_cr,

@@ -1,0 +1,128 @@
+"""Learned preconditioner network (oracle, float64): features, forward, loss and backward.
+
+TEST INFRASTRUCTURE ONLY (see the package header).
+
+The paper's preconditioner is D_i = T_i^{-1} G_i with T_i = L/2 - Lambda_ii B (Eq. precondition-T).
+The learned stand-in maps a gradient column to an approximate T_i^{-1} G_i with a small graph
+network on the free-DoF graph of the P2 mesh (one node per free degree of freedom, edges = the
+sparsity pattern of L).  Everything here is written out plainly so that the GPU kernels'
+values and gradients can be checked against it.
+
+Per column c with shift lam_c (lam_c = Lambda_cc if negative, else 0):
+    diag_i  = dL_i / 2 - lam_c dB_i                      (Jacobi diagonal of T_c)
+    z_i     = g_i / diag_i                                (one Jacobi step)
+    s_c     = sqrt(mean_i z_i^2)                          (column scale)
+    features f = [z_i / s_c,  log diag_i - mean_i log diag_i,  -lam_c dB_i / diag_i,  1]
+Aggregation A: mean over the closed neighbourhood, (A h)_i = sum_{j in N(i)} h_j / |N(i)|.
+Layers (widths 4 -> H -> H -> 1):  Z_l = H_l W_l + (A H_l) U_l + b_l,  H_{l+1} = relu(Z_l) for the
+two hidden layers, identity for the last.
+Output: D_i = s_c (f0_i + H_3,i)   (the network corrects the scaled Jacobi step).
+Loss over a batch of columns: mean_c ||D_c - D*_c||^2 / ||D*_c||^2.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+N_FEAT = 4
+
+
+def mean_aggregator(pattern: sp.csr_matrix) -> sp.csr_matrix:
+    """A with A_ij = 1/|N(i)| on the sparsity pattern (closed neighbourhoods)."""
+    P = pattern.tocsr(copy=True)
+    P.data = np.ones_like(P.data)
+    deg = np.diff(P.indptr)
+    return sp.diags(1.0 / deg) @ P
+
+
+def features(G: np.ndarray, dL: np.ndarray, dB: np.ndarray, shifts: np.ndarray):
+    """Input features (n, p, 4), the column scales s (p,) and the Jacobi diagonals (n, p)."""
+    lam = np.where(shifts < 0, shifts, 0.0)
+    diag = 0.5 * dL[:, None] - lam[None, :] * dB[:, None]
+    z = G / diag
+    s = np.sqrt(np.mean(z * z, axis=0))
+    logd = np.log(diag)
+    f = np.empty(G.shape + (N_FEAT,))
+    f[..., 0] = z / s
+    f[..., 1] = logd - logd.mean(axis=0)
+    f[..., 2] = -lam[None, :] * dB[:, None] / diag
+    f[..., 3] = 1.0
+    return f, s, diag
+
+
+def init_params(width: int = 64, seed: int = 0):
+    """He-initialized weights; the last layer starts at zero (the network starts as Jacobi)."""
+    rng = np.random.default_rng(seed)
+    dims = [N_FEAT, width, width, 1]
+    params = []
+    for l in range(3):
+        fi, fo = dims[l], dims[l + 1]
+        sc = 0.0 if l == 2 else np.sqrt(2.0 / (2 * fi))
+        params.append({"W": rng.standard_normal((fi, fo)) * sc, "U": rng.standard_normal((fi, fo)) * sc,
+                       "b": np.zeros(fo)})
+    return params
+
+
+def forward(params, f: np.ndarray, A: sp.csr_matrix):
+    """f (n, p, F0) -> y (n, p) network output, with the cache for backward."""
+    n, p, _ = f.shape
+    H = f
+    cache = []
+    for l, P in enumerate(params):
+        AH = np.stack([A @ H[:, c, :] for c in range(p)], axis=1)     # per column, over nodes
+        Z = H @ P["W"] + AH @ P["U"] + P["b"]
+        cache.append((H, AH, Z))
+        H = np.maximum(Z, 0.0) if l < 2 else Z
+    return H[..., 0], cache
+
+
+def predict(params, f, s, A):
+    y, cache = forward(params, f, A)
+    return s[None, :] * (f[..., 0] + y), y, cache
+
+
+def loss_and_dy(D: np.ndarray, Dstar: np.ndarray, s: np.ndarray):
+    """Relative squared error averaged over columns and its gradient with respect to y."""
+    den = np.sum(Dstar * Dstar, axis=0)
+    r = D - Dstar
+    p = D.shape[1]
+    loss = float(np.mean(np.sum(r * r, axis=0) / den))
+    dD = 2.0 * r / den[None, :] / p
+    return loss, dD * s[None, :]
+
+
+def backward(params, cache, dy: np.ndarray, A: sp.csr_matrix):
+    """Gradients of the loss for every W, U, b given dL/dy (n, p)."""
+    n, p = dy.shape
+    AT = A.T.tocsr()
+    grads = [None] * 3
+    dH = dy[..., None]
+    for l in range(2, -1, -1):
+        H, AH, Z = cache[l]
+        dZ = dH if l == 2 else dH * (Z > 0)
+        P = params[l]
+        gW = np.einsum("ncf,nco->fo", H, dZ)
+        gU = np.einsum("ncf,nco->fo", AH, dZ)
+        gb = dZ.sum(axis=(0, 1))
+        grads[l] = {"W": gW, "U": gU, "b": gb}
+        dAH = dZ @ P["U"].T
+        dH = dZ @ P["W"].T + np.stack([AT @ dAH[:, c, :] for c in range(p)], axis=1)
+    return grads
+
+
+def adam_step(params, grads, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update in place; state holds the moments and the step count."""
+    state["t"] = state.get("t", 0) + 1
+    t = state["t"]
+    for l in range(3):
+        for k in ("W", "U", "b"):
+            key = (l, k)
+            m = state.setdefault(("m",) + key, np.zeros_like(params[l][k]))
+            v = state.setdefault(("v",) + key, np.zeros_like(params[l][k]))
+            g = grads[l][k]
+            m[:] = b1 * m + (1 - b1) * g
+            v[:] = b2 * v + (1 - b2) * g * g
+            mh = m / (1 - b1 ** t)
+            vh = v / (1 - b2 ** t)
+            params[l][k] = params[l][k] - lr * mh / (np.sqrt(vh) + eps)
+    return params

@@ -1,0 +1,79 @@
+"""Pins of the oracle's learned-preconditioner network.
+
+* with its zero-initialized last layer the network returns exactly the Jacobi step G / diag
+* the hand-written backward equals central finite differences of the loss
+* a few Adam steps on exact preconditioned directions T^{-1} G lower the loss
+"""
+import numpy as np
+import pytest
+
+from oracle import gcn, pcal
+from paper_2007_14228_gb300 import inputs as I
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    s = I.lih().with_cells((6, 4, 4))
+    m = I.make_mesh(s)
+    pr = pcal.Problem(m.xyz, m.tet10, m.dirichlet, s.Z, s.R, pcal.Params(p=2, hartree=False, xc=False,
+                                                                          precond="exact"))
+    A = gcn.mean_aggregator(pr.Lf)
+    rng = np.random.default_rng(4)
+    G = rng.standard_normal((pr.n, 2))
+    shifts = np.array([-0.8, -0.2])
+    Dstar = pr.precondition(G, shifts)
+    return pr, A, G, shifts, Dstar
+
+
+def test_aggregator_rows_average(tiny):
+    pr, A, *_ = tiny
+    np.testing.assert_allclose(A @ np.ones(pr.n), 1.0, atol=1e-14)
+
+
+def test_initial_network_is_the_jacobi_step(tiny):
+    pr, A, G, shifts, _ = tiny
+    f, s, diag = gcn.features(G, pr.Lf.diagonal(), pr.Bf.diagonal(), shifts)
+    D, _, _ = gcn.predict(gcn.init_params(width=8), f, s, A)
+    np.testing.assert_allclose(D, G / diag, rtol=1e-13)
+
+
+def test_backward_matches_finite_differences(tiny):
+    pr, A, G, shifts, Dstar = tiny
+    f, s, _ = gcn.features(G, pr.Lf.diagonal(), pr.Bf.diagonal(), shifts)
+    params = gcn.init_params(width=6, seed=1)
+    rng = np.random.default_rng(9)
+    params[2]["W"] = 0.1 * rng.standard_normal(params[2]["W"].shape)
+    params[2]["U"] = 0.1 * rng.standard_normal(params[2]["U"].shape)
+
+    def loss_of(pp):
+        D, _, _ = gcn.predict(pp, f, s, A)
+        return gcn.loss_and_dy(D, Dstar, s)[0]
+
+    D, y, cache = gcn.predict(params, f, s, A)
+    _, dy = gcn.loss_and_dy(D, Dstar, s)
+    grads = gcn.backward(params, cache, dy, A)
+    h = 1e-6
+    for (l, k, idx) in [(0, "W", (1, 2)), (0, "U", (0, 3)), (1, "W", (4, 5)), (1, "b", (2,)), (2, "U", (3, 0)),
+                        (2, "b", (0,)), (0, "b", (1,)), (1, "U", (0, 1))]:
+        pp = [{kk: v.copy() for kk, v in P.items()} for P in params]
+        pp[l][k][idx] += h
+        lp = loss_of(pp)
+        pp[l][k][idx] -= 2 * h
+        lm = loss_of(pp)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - grads[l][k][idx]) < 1e-6 * max(1.0, abs(fd)), (l, k, idx, fd, grads[l][k][idx])
+
+
+def test_adam_steps_reduce_the_loss(tiny):
+    pr, A, G, shifts, Dstar = tiny
+    f, s, _ = gcn.features(G, pr.Lf.diagonal(), pr.Bf.diagonal(), shifts)
+    params = gcn.init_params(width=16, seed=2)
+    state = {}
+    D, _, _ = gcn.predict(params, f, s, A)
+    l0 = gcn.loss_and_dy(D, Dstar, s)[0]
+    for _ in range(60):
+        D, y, cache = gcn.predict(params, f, s, A)
+        _, dy = gcn.loss_and_dy(D, Dstar, s)
+        params = gcn.adam_step(params, gcn.backward(params, cache, dy, A), state, lr=3e-3)
+    D, _, _ = gcn.predict(params, f, s, A)
+    assert gcn.loss_and_dy(D, Dstar, s)[0] < 0.7 * l0

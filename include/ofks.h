@@ -41,10 +41,13 @@ extern "C" {
 
 /* ---- enumerations ------------------------------------------------------------------ */
 #define OFKS_FP64          0   /* every step in float64 */
+#define OFKS_MIXED         1   /* float32 iterations (float64 p x p, energies, tests), then a
+                                  float64 refinement sweep once (kkt+fea)/kkt0 < mixed_tol */
 
 #define OFKS_PC_NONE       0   /* D = grad L_beta */
 #define OFKS_PC_PCG        1   /* T_i^{-1} grad by Jacobi-PCG, fixed pcg_iters, zero start */
 #define OFKS_PC_EXACT      2   /* the same PCG run to a 1e-12 relative residual */
+#define OFKS_PC_LEARNED    3   /* graph network D = N(G), judged per column; PCG from D for rejects */
 
 #define OFKS_ETA_BB2       0   /* eta = <dD,dD>/|<dX,dD>|, dD = difference of applied directions */
 #define OFKS_ETA_BB1       1   /* eta = |<dX,dD>|/<dX,dX> */
@@ -81,7 +84,7 @@ typedef struct {
     double  occ;            /* electrons per orbital f: rho = f sum_l |psi_l|^2 */
     double  tol;            /* stop when (kkt + fea)/kkt_0 < tol (paper Sec. 4.1) */
     int32_t max_iter;       /* iteration cap of ofks_solve */
-    int32_t precision;      /* OFKS_FP64 */
+    int32_t precision;      /* OFKS_FP64 or OFKS_MIXED */
     int32_t precond;        /* OFKS_PC_* (paper Eq. precondition-T) */
     int32_t pcg_iters;      /* PCG iterations per preconditioner apply */
     int32_t eta_rule;       /* OFKS_ETA_* (paper Sec. 4.4) */
@@ -93,6 +96,10 @@ typedef struct {
     double  poisson_tol;    /* relative residual of the Hartree CG solve */
     int32_t poisson_max_iter;
     int32_t poisson_amg;    /* 1: CG preconditioned by the algebraic multigrid V-cycle; 0: Jacobi */
+    double  mixed_tol;      /* OFKS_MIXED: hand over to float64 once (kkt+fea)/kkt0 < mixed_tol */
+    double  poisson_tol_mixed; /* Hartree CG tolerance during the float32 iterations */
+    double  judge_tau;      /* OFKS_PC_LEARNED: accept a column if |G - T D| <= judge_tau |G| and G.D > 0 */
+    int32_t learned_tc;     /* 1: width-64 hidden layer on the tensor cores (bf16 operands) at inference */
 } ofks_params;
 
 typedef struct {
@@ -107,11 +114,15 @@ typedef struct {
     double  seconds;        /* device time of the call, from CUDA events */
     int32_t hartree_iters;  /* CG iterations of the last Hartree solve */
     int32_t hartree_total;  /* CG iterations of all Hartree solves of the call */
+    int32_t switch_iter;    /* OFKS_MIXED: iteration that started the float64 sweep, -1 before */
+    int64_t judge_accept;   /* OFKS_PC_LEARNED: columns the judge accepted so far ... */
+    int64_t judge_total;    /* ... out of this many judged */
 } ofks_result;
 
 /* Fill *prm with the defaults: beta 10, occ 2, tol 1e-8, max_iter 1000, FP64, PCG with 8
  * iterations, BB2, eta in [1e-4, 1e8], Hartree and LDA on, multipole_lmax 2,
- * poisson_tol 1e-12, poisson_max_iter 20000, poisson_amg 0.  p is set to 1. */
+ * poisson_tol 1e-12, poisson_max_iter 20000, poisson_amg 0, mixed_tol 1e-5, poisson_tol_mixed
+ * 1e-8, judge_tau 0.5, learned_tc 1.  p is set to 1. */
 void ofks_default_params(ofks_params *prm);
 
 /* Create a context on CUDA device `device`.  *out receives the context (NULL on failure).
@@ -210,6 +221,37 @@ int ofks_get_sizes(ofks_ctx *ctx, int64_t *n_free, int64_t *n_nodes, int64_t *n_
 /* History of evaluated iterates: rows of 6 doubles (k, seconds since init, E, kkt, fea,
  * eta).  Copies min(cap, available) rows of the most recent ones into buf; *len = rows. */
 int ofks_get_history(ofks_ctx *ctx, double *buf, int32_t cap, int32_t *len);
+
+/* ---- learned preconditioner (BASELINE's learned-preconditioner configuration; the paper's
+ * Eq. precondition-T stays its fallback and judge) -------------------------------------------
+ * The network maps a gradient column G_c to an approximation of T_c^{-1} G_c on the free-DoF
+ * graph of the mesh: input features [z/s, log diag - mean, -lam dB/diag, 1] with
+ * z = G / diag, diag = dL/2 - lam dB, s = rms(z); layers Z = H W + (A H) U + b (A: mean over the
+ * closed neighbourhood), widths 4 -> width -> width -> 1, relu on the hidden layers; output
+ * D = s (z/s + y).  Parameters: float32 masters rounded to bfloat16 where used, flat layout
+ * W0, U0, b0, W1, U1, b1, W2, U2, b2 (W and U row-major fan_in x fan_out). */
+
+/* Random initialization (seeded; last layer zero, so the network starts as the Jacobi step).
+ * width in {8, 16, 32, 64}.  Requires a mesh.  Resets the optimizer state. */
+int ofks_precond_init(ofks_ctx *ctx, int32_t width, uint64_t seed);
+
+/* Copy the parameters out (cap >= *count) or in (count must match the width's size). */
+int ofks_precond_get_weights(ofks_ctx *ctx, float *w, int64_t cap, int64_t *count);
+int ofks_precond_set_weights(ofks_ctx *ctx, const float *w, int64_t count);
+
+/* D (n_free x p, host) = preconditioned directions of G (host) for per-column shifts (host, p;
+ * columns with shift >= 0 take D = G): mode OFKS_PC_PCG, OFKS_PC_EXACT or OFKS_PC_LEARNED (the
+ * network alone, no judge).  Uses the context's scratch blocks; iteration history is kept. */
+int ofks_precondition(ofks_ctx *ctx, int32_t mode, const double *G, const double *shifts, double *D);
+
+/* One Adam step (learning rate lr) of the network on the pair (G, Dstar) with per-column
+ * shifts; *loss receives the loss before the step (mean over columns of |D - D*|^2/|D*|^2). */
+int ofks_train_precond_step(ofks_ctx *ctx, const double *G, const double *shifts, const double *Dstar,
+                            double lr, double *loss);
+
+/* Loss and parameter gradients (float64, same layout as the weights) without a step. */
+int ofks_precond_grads(ofks_ctx *ctx, const double *G, const double *shifts, const double *Dstar,
+                       double *grads, int64_t cap, double *loss);
 
 /* Checkpoint: X, X_prev, D_prev, G_prev, eta, k, kkt0 and the Hartree warm start U, so a
  * reloaded run continues bit-for-bit.  The mesh, nuclei and params must match on load. */

@@ -18,15 +18,9 @@
 #include "common.cuh"
 #include "internal.h"
 
-enum { CB_SHIFT = 0, CB_ACTIVE = 1, CB_RZ = 2, CB_RZN = 3, CB_PQ = 4, CB_BETA = 5, CB_NORM = 6,
-       CB_ALPHA = 7, CB_COUNT = 8 };
-
-void launch_pcg_alpha(ofks_ctx *c);
-void launch_pcg_beta(ofks_ctx *c);
-
 static const char *kPfNames[PF_COUNT] = {"density", "poisson", "potential", "spmm_h", "gram", "small",
                                          "grad", "pcg_spmm", "pcg_update", "bb", "step", "spmm_b", "other",
-                                         "poisson_spmv"};
+                                         "poisson_spmv", "gcn"};
 
 int ofks_fail(ofks_ctx *c, int code, const char *fmt, ...) {
     char buf[512];
@@ -87,27 +81,50 @@ static void dfree(T *&p) {
     p = nullptr;
 }
 
+template <class T>
+static void free_set(Blocks<T> &b) {
+    for (int i = 0; i < 2; ++i) { dfree(b.X[i]); dfree(b.D[i]); dfree(b.G[i]); }
+    dfree(b.HX); dfree(b.BX); dfree(b.R); dfree(b.Z); dfree(b.P); dfree(b.Q); dfree(b.W);
+    dfree(b.valL); dfree(b.valB); dfree(b.valH);
+}
+
 static void free_blocks(ofks_ctx *c) {
-    for (int i = 0; i < 2; ++i) { dfree(c->d_X[i]); dfree(c->d_D[i]); dfree(c->d_G[i]); }
-    dfree(c->d_HX); dfree(c->d_BX); dfree(c->d_R); dfree(c->d_Z); dfree(c->d_P); dfree(c->d_Q); dfree(c->d_W);
+    free_set(c->b64);
+    free_set(c->b32);
     dfree(c->d_L0); dfree(c->d_S); dfree(c->d_Lam); dfree(c->d_C); dfree(c->d_colA); dfree(c->d_pp);
     c->p = c->ld = 0;
     c->have_X = c->evaluated = c->have_prev = false;
+    c->phase = 64;
 }
 
-static int alloc_blocks(ofks_ctx *c, int p) {
+template <class T>
+static int alloc_set(ofks_ctx *c, Blocks<T> &b, int ld, bool values) {
+    const size_t blk = sizeof(T) * (size_t)c->n * ld;
+    T **bl[] = {&b.X[0], &b.X[1], &b.D[0], &b.D[1], &b.G[0], &b.G[1], &b.HX, &b.BX, &b.R, &b.Z, &b.P, &b.Q, &b.W};
+    for (T **q : bl) {
+        if (cudaMalloc((void **)q, blk) != cudaSuccess)
+            return ofks_fail(c, OFKS_ENOMEM, "cannot allocate %zu bytes for an n x p block", blk);
+        cudaMemsetAsync(*q, 0, blk, c->stream);
+    }
+    if (values) {
+        const size_t vb = sizeof(T) * (size_t)std::max<int64_t>(c->sell_len, 1);
+        if (cudaMalloc((void **)&b.valL, vb) != cudaSuccess || cudaMalloc((void **)&b.valB, vb) != cudaSuccess ||
+            cudaMalloc((void **)&b.valH, vb) != cudaSuccess)
+            return ofks_fail(c, OFKS_ENOMEM, "cannot allocate the float32 matrix values");
+        launch_convert(c, c->d_valL, b.valL, c->sell_len);
+        launch_convert(c, c->d_valB, b.valB, c->sell_len);
+        launch_convert(c, c->d_valH, b.valH, c->sell_len);
+    }
+    return OFKS_OK;
+}
+
+static int alloc_blocks(ofks_ctx *c, int p, bool mixed) {
     free_blocks(c);
     const int ld = (p <= 2) ? p : (p + 3) / 4 * 4;
-    const size_t blk = sizeof(double) * (size_t)c->n * ld, sm = sizeof(double) * (size_t)ld * ld;
-    double **bl[] = {&c->d_X[0], &c->d_X[1], &c->d_D[0], &c->d_D[1], &c->d_G[0], &c->d_G[1], &c->d_HX,
-                     &c->d_BX, &c->d_R, &c->d_Z, &c->d_P, &c->d_Q, &c->d_W};
-    for (double **b : bl) {
-        if (cudaMalloc((void **)b, blk) != cudaSuccess) {
-            free_blocks(c);
-            return ofks_fail(c, OFKS_ENOMEM, "cannot allocate %zu bytes for an n x p block", blk);
-        }
-        cudaMemsetAsync(*b, 0, blk, c->stream);
-    }
+    const size_t sm = sizeof(double) * (size_t)ld * ld;
+    int rc = alloc_set(c, c->b64, ld, false);
+    if (!rc && mixed) rc = alloc_set(c, c->b32, ld, true);
+    if (rc) { free_blocks(c); return rc; }
     double **sl[] = {&c->d_L0, &c->d_S, &c->d_Lam, &c->d_C};
     for (double **b : sl) {
         if (cudaMalloc((void **)b, sm) != cudaSuccess) { free_blocks(c); return ofks_fail(c, OFKS_ENOMEM, "p x p"); }
@@ -121,7 +138,31 @@ static int alloc_blocks(ofks_ctx *c, int p) {
     cudaMemsetAsync(c->d_colA, 0, sizeof(double) * CB_COUNT * ld, c->stream);
     c->p = p;
     c->ld = ld;
+    c->mixed_alloc = mixed;
     return ofks_cuda_check(c, cudaStreamSynchronize(c->stream), "block allocation");
+}
+
+// copy the iteration state between the float32 and float64 sets (X, previous X, D, G, B X)
+template <class S, class T>
+static void copy_state(ofks_ctx *c, Blocks<S> &a, Blocks<T> &b) {
+    const int64_t cnt = c->n * (int64_t)c->ld;
+    for (int i = 0; i < 2; ++i) {
+        launch_convert(c, a.X[i], b.X[i], cnt);
+        launch_convert(c, a.D[i], b.D[i], cnt);
+        launch_convert(c, a.G[i], b.G[i], cnt);
+    }
+    launch_convert(c, a.BX, b.BX, cnt);
+    launch_convert(c, a.HX, b.HX, cnt);
+}
+
+// the float64 set holds the current state (after float32 iterations it is stale)
+static void state_to64(ofks_ctx *c) {
+    if (c->phase == 32) copy_state(c, c->b32, c->b64);
+}
+
+// entering float32 iterations from the float64 set
+static void state_to32(ofks_ctx *c) {
+    if (c->phase == 32) copy_state(c, c->b64, c->b32);
 }
 
 static double now_s() {
@@ -151,23 +192,38 @@ static int read_flag(ofks_ctx *c, int *h) {
 // ------------------------------------------------------------------------------ iteration
 struct Rec { double E, fea, kkt, eta; };
 
-static int evaluate(ofks_ctx *c, bool need_bx, Rec *out) {
-    double *X = c->d_X[c->cur];
+template <class T> static const T *vals_L(ofks_ctx *c);
+template <> const double *vals_L<double>(ofks_ctx *c) { return c->d_valL; }
+template <> const float *vals_L<float>(ofks_ctx *c) { return c->b32.valL; }
+template <class T> static const T *vals_B(ofks_ctx *c);
+template <> const double *vals_B<double>(ofks_ctx *c) { return c->d_valB; }
+template <> const float *vals_B<float>(ofks_ctx *c) { return c->b32.valB; }
+template <class T> static T *vals_H(ofks_ctx *c);
+template <> double *vals_H<double>(ofks_ctx *c) { return c->d_valH; }
+template <> float *vals_H<float>(ofks_ctx *c) { return c->b32.valH; }
+template <class T> static Blocks<T> &blocks(ofks_ctx *c);
+template <> Blocks<double> &blocks<double>(ofks_ctx *c) { return c->b64; }
+template <> Blocks<float> &blocks<float>(ofks_ctx *c) { return c->b32; }
+
+template <class T>
+static int evaluate_t(ofks_ctx *c, bool need_bx, Rec *out) {
+    Blocks<T> &b = blocks<T>(c);
+    T *X = b.X[c->cur];
     int rc;
     if ((rc = launch_density(c, X))) return rc;
     if ((rc = run_hartree(c))) return rc;
-    if ((rc = launch_potential_refresh(c))) return rc;
+    if ((rc = launch_potential_refresh(c, vals_H<T>(c), vals_L<T>(c)))) return rc;
     {
         ProfScope ps(c, PF_SPMM_H);
-        launch_sell_spmm(c, c->d_valH, X, c->d_HX);
+        launch_sell_spmm(c, (const T *)vals_H<T>(c), (const T *)X, b.HX);
     }
     if (need_bx) {
         ProfScope ps(c, PF_SPMM_B);
-        launch_sell_spmm(c, c->d_valB, X, c->d_BX);
+        launch_sell_spmm(c, vals_B<T>(c), (const T *)X, b.BX);
     }
-    launch_gram2(c, X, c->d_HX, c->d_BX, c->d_L0, c->d_S);
+    launch_gram2(c, (const T *)X, (const T *)b.HX, (const T *)b.BX, c->d_L0, c->d_S);
     launch_small_update(c);
-    launch_grad_update(c);
+    launch_grad_update(c, b);
     launch_small_record(c);
     double h[4];
     cudaError_t e = cudaMemcpyAsync(h, c->d_rec, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream);
@@ -181,20 +237,63 @@ static int evaluate(ofks_ctx *c, bool need_bx, Rec *out) {
     return OFKS_OK;
 }
 
-static int precondition(ofks_ctx *c) {
+static int evaluate(ofks_ctx *c, bool need_bx, Rec *out) {
+    return c->phase == 32 ? evaluate_t<float>(c, need_bx, out) : evaluate_t<double>(c, need_bx, out);
+}
+
+template <class T>
+static int precondition_t(ofks_ctx *c) {
+    Blocks<T> &b = blocks<T>(c);
     const int ld = c->ld;
-    double *D = c->d_D[c->cur], *G = c->d_G[c->cur];
+    T *D = b.D[c->cur], *G = b.G[c->cur];
     if (c->prm.precond == OFKS_PC_NONE) {
-        return ofks_cuda_check(c, cudaMemcpyAsync(D, G, sizeof(double) * c->n * ld, cudaMemcpyDeviceToDevice, c->stream),
+        return ofks_cuda_check(c, cudaMemcpyAsync(D, G, sizeof(T) * c->n * ld, cudaMemcpyDeviceToDevice, c->stream),
                                "direction copy");
     }
-    {
+    bool run_pcg = true, warm = false;
+    if (c->prm.precond == OFKS_PC_LEARNED) {
+        // D = network(G); each active column is judged by its relative residual |G - T D| / |G| and
+        // the sign of G.D; rejected columns continue with PCG started from the network's D
+        if (!c->gcn.H) return ofks_fail(c, OFKS_ESTATE, "learned preconditioner: no network (ofks_precond_init)");
+        int rc;
+        if ((rc = gcn_forward_prepare(c))) return rc;
+        gcn_pack<T>(c, G, c->gcn.G32);
+        if ((rc = gcn_forward(c, c->d_colA + CB_SHIFT * ld, false))) return rc;
+        gcn_unpack<T>(c, c->gcn.Dn, D);
+        {
+            ProfScope ps(c, PF_PCG_SPMM);
+            launch_pcg_apply(c, vals_L<T>(c), vals_B<T>(c), (const T *)D, b.P, b.Q, c->d_colA + CB_BETA * ld,
+                             c->d_colA + CB_SHIFT * ld, c->d_colA + CB_PQ * ld, 1);
+        }
+        launch_judge(c, b);
+        std::vector<double> h(4 * (size_t)ld);
+        cudaMemcpyAsync(h.data(), c->d_colA + CB_ACTIVE * ld, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(h.data() + ld, c->d_colA + CB_RZ * ld, sizeof(double) * 3 * ld, cudaMemcpyDeviceToHost, c->stream);
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return ofks_cuda_check(c, e, "learned preconditioner judge");
+        std::vector<double> acc(ld, 1.0);
+        int rejected = 0;
+        for (int j = 0; j < c->p; ++j) {
+            if (h[j] == 0.0) continue;                      // T = I column: D = G below
+            const double rr = h[ld + j], gg = h[2 * ld + j], gd = h[3 * ld + j];
+            const bool ok = gd > 0.0 && std::sqrt(rr) <= c->prm.judge_tau * std::sqrt(gg);
+            acc[j] = ok ? 1.0 : 0.0;
+            rejected += !ok;
+            c->judge_total++;
+            c->judge_accept += ok;
+        }
+        cudaMemcpyAsync(c->d_colA + CB_ACC * ld, acc.data(), sizeof(double) * ld, cudaMemcpyHostToDevice, c->stream);
+        run_pcg = rejected > 0;
+        warm = true;
+    }
+    if (run_pcg) {
         ProfScope ps(c, PF_PCG_UPDATE);
-        launch_pcg_init(c);
+        if (warm) launch_pcg_init_warm(c, b);
+        else launch_pcg_init(c, b);
         cudaMemsetAsync(c->d_colA + CB_PQ * ld, 0, sizeof(double) * ld, c->stream);
     }
     const bool exact = c->prm.precond == OFKS_PC_EXACT;
-    const int max_it = exact ? 5000 : c->prm.pcg_iters;
+    const int max_it = !run_pcg ? 0 : exact ? 5000 : c->prm.pcg_iters;
     std::vector<double> rz0, rz(ld), act(ld);
     if (exact) {
         rz0.resize(ld);
@@ -205,13 +304,13 @@ static int precondition(ofks_ctx *c) {
     for (int it = 0; it < max_it; ++it) {
         {
             ProfScope ps(c, PF_PCG_SPMM);
-            launch_pcg_apply(c, c->d_Z, c->d_P, c->d_Q, c->d_colA + CB_BETA * ld, c->d_colA + CB_SHIFT * ld,
-                             c->d_colA + CB_PQ * ld, it == 0 ? 1 : 0);
+            launch_pcg_apply(c, vals_L<T>(c), vals_B<T>(c), (const T *)b.Z, b.P, b.Q, c->d_colA + CB_BETA * ld,
+                             c->d_colA + CB_SHIFT * ld, c->d_colA + CB_PQ * ld, it == 0 ? 1 : 0);
         }
         {
             ProfScope ps(c, PF_PCG_UPDATE);
             launch_pcg_alpha(c);
-            launch_pcg_update(c, it);
+            launch_pcg_update(c, b);
             launch_pcg_beta(c);
         }
         if (exact && (it + 1) % 25 == 0) {
@@ -225,43 +324,32 @@ static int precondition(ofks_ctx *c) {
     }
     {
         ProfScope ps(c, PF_PCG_UPDATE);
-        launch_direction_select(c);
+        launch_direction_select(c, b);
     }
     return ofks_cuda_check(c, cudaGetLastError(), "preconditioner");
 }
 
-static int update_step(ofks_ctx *c) {
+template <class T>
+static int update_step_t(ofks_ctx *c) {
+    Blocks<T> &b = blocks<T>(c);
     const int prv = c->cur ^ 1, ld = c->ld;
     int rc;
-    if ((rc = precondition(c))) return rc;
-    {
-        // BB sums on the applied directions, or on the raw gradients for OFKS_ETA_BB2_RAW
-        if (c->prm.eta_rule == OFKS_ETA_BB2_RAW) {
-            std::swap(c->d_D[0], c->d_G[0]);
-            std::swap(c->d_D[1], c->d_G[1]);
-            launch_bb_dots(c);
-            std::swap(c->d_D[0], c->d_G[0]);
-            std::swap(c->d_D[1], c->d_G[1]);
-            // ||D||^2 for eta_0 must use the applied direction
-            if (!c->have_prev) launch_bb_dots(c);
-        } else {
-            launch_bb_dots(c);
-        }
-        launch_eta(c);
-    }
-    double *Y = c->d_X[prv];
+    if ((rc = precondition_t<T>(c))) return rc;
+    launch_bb_dots(c, b, c->prm.eta_rule == OFKS_ETA_BB2_RAW);
+    launch_eta(c);
+    T *Y = b.X[prv];
     {
         ProfScope ps(c, PF_STEP);
-        launch_step_y(c, Y);
+        launch_step_y(c, b, Y);
     }
     cudaMemsetAsync(c->d_colA + CB_NORM * ld, 0, sizeof(double) * ld, c->stream);
     {
         ProfScope ps(c, PF_SPMM_B);
-        launch_sell_spmm_colnorm(c, c->d_valB, Y, c->d_BX, c->d_colA + CB_NORM * ld);
+        launch_sell_spmm_colnorm(c, vals_B<T>(c), (const T *)Y, b.BX, c->d_colA + CB_NORM * ld);
     }
     {
         ProfScope ps(c, PF_STEP);
-        launch_scale_cols(c, Y, c->d_BX, c->d_colA + CB_NORM * ld);
+        launch_scale_cols(c, Y, b.BX, c->d_colA + CB_NORM * ld);
     }
     if ((rc = ofks_cuda_check(c, cudaGetLastError(), "update step"))) return rc;
     double eta;
@@ -275,6 +363,8 @@ static int update_step(ofks_ctx *c) {
     return OFKS_OK;
 }
 
+static int update_step(ofks_ctx *c) { return c->phase == 32 ? update_step_t<float>(c) : update_step_t<double>(c); }
+
 static int run_iterations(ofks_ctx *c, int kmax, ofks_result *res) {
     if (!c->have_X) return ofks_fail(c, OFKS_ESTATE, "no orbitals: call ofks_init_orbitals first");
     cudaEvent_t e0 = ev_get(c), e1 = ev_get(c);
@@ -287,6 +377,16 @@ static int run_iterations(ofks_ctx *c, int kmax, ofks_result *res) {
         c->bx_valid = true;
         if (c->k == 0) c->kkt0 = r.kkt;
         c->history.insert(c->history.end(), {(double)c->k, now_s() - c->t_start, r.E, r.kkt, r.fea, c->eta});
+        if (c->phase == 32 && c->kkt0 > 0 && (r.kkt + r.fea) / c->kkt0 < c->prm.mixed_tol) {
+            // float32 iterations have reached their floor: continue with the float64 sweep
+            state_to64(c);
+            c->phase = 64;
+            c->bx_valid = false;
+            c->switch_k = c->k;
+            c->history.resize(c->history.size() - 6);   // the float64 evaluation replaces this record
+            --it;
+            continue;
+        }
         if (c->kkt0 > 0 && (r.kkt + r.fea) / c->kkt0 < c->prm.tol) { c->converged = true; break; }
         if ((rc = update_step(c))) break;
     }
@@ -302,6 +402,9 @@ static int run_iterations(ofks_ctx *c, int kmax, ofks_result *res) {
         res->seconds = ms * 1e-3;
         res->hartree_iters = c->cg_last;
         res->hartree_total = (int32_t)c->cg_total;
+        res->switch_iter = c->switch_k;
+        res->judge_accept = c->judge_accept;
+        res->judge_total = c->judge_total;
     }
     return rc;
 }
@@ -317,6 +420,8 @@ void ofks_default_params(ofks_params *p) {
     p->eta_fixed = 0.0; p->eta_min = 1e-4; p->eta_max = 1e8; p->hartree = 1; p->xc = 1;
     p->multipole_lmax = 2; p->poisson_tol = 1e-12; p->poisson_max_iter = 20000;
     p->poisson_amg = 0;
+    p->mixed_tol = 1e-5; p->poisson_tol_mixed = 1e-8;
+    p->judge_tau = 0.5; p->learned_tc = 1;
 }
 
 int ofks_create(ofks_ctx **out, int device) {
@@ -348,7 +453,7 @@ void ofks_destroy(ofks_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_blocks(c);
     free_mesh(c);
-    dfree(c->d_sc); dfree(c->d_rec); dfree(c->d_flag);
+    dfree(c->d_sc); dfree(c->d_rec); dfree(c->d_flag); dfree(c->d_shift_in);
     for (auto &pe : c->prof_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     if (c->stream) cudaStreamDestroy(c->stream);
@@ -366,7 +471,7 @@ int ofks_set_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tet
     if (rc) return rc;
     if (c->prm.p > c->n) c->prm.p = 1;
     c->bx_valid = false;
-    return alloc_blocks(c, c->prm.p);
+    return alloc_blocks(c, c->prm.p, c->prm.precision == OFKS_MIXED);
 }
 
 int ofks_set_nuclei(ofks_ctx *c, int32_t M, const double *Z, const double *R) {
@@ -401,20 +506,24 @@ int ofks_set_params(ofks_ctx *c, const ofks_params *prm) {
     if (prm->p < 1 || prm->p > c->n) return ofks_fail(c, OFKS_EINVAL, "set_params: p=%d outside [1, %lld]", prm->p, (long long)c->n);
     if (prm->p > 256) return ofks_fail(c, OFKS_EINVAL, "set_params: p=%d above the supported 256", prm->p);
     if (!(prm->beta >= 0) || !(prm->occ > 0) || !(prm->tol > 0) || prm->max_iter < 0 || prm->pcg_iters < 0 ||
-        prm->eta_rule < 0 || prm->eta_rule > OFKS_ETA_FIXED || prm->precond < 0 || prm->precond > OFKS_PC_EXACT ||
-        prm->precision != OFKS_FP64 || !(prm->eta_min > 0) || !(prm->eta_max >= prm->eta_min) ||
+        prm->eta_rule < 0 || prm->eta_rule > OFKS_ETA_FIXED || prm->precond < 0 || prm->precond > OFKS_PC_LEARNED ||
+        !(prm->judge_tau > 0) || prm->learned_tc < 0 || prm->learned_tc > 1 ||
+        (prm->precision != OFKS_FP64 && prm->precision != OFKS_MIXED) || !(prm->mixed_tol > 0) ||
+        !(prm->poisson_tol_mixed > 0) || !(prm->eta_min > 0) || !(prm->eta_max >= prm->eta_min) ||
         prm->multipole_lmax < -1 || prm->multipole_lmax > 2 || !(prm->poisson_tol > 0) ||
         prm->poisson_max_iter < 1 || prm->poisson_amg < 0 || prm->poisson_amg > 1 || (prm->eta_rule == OFKS_ETA_FIXED && !(prm->eta_fixed > 0)))
         return ofks_fail(c, OFKS_EINVAL, "set_params: a parameter is out of range");
     cudaSetDevice(c->device);
-    const bool realloc = prm->p != c->p;
+    const bool mixed = prm->precision == OFKS_MIXED;
+    const bool realloc = prm->p != c->p || mixed != c->mixed_alloc;
     c->prm = *prm;
     c->evaluated = false;
     if (realloc) {
-        int rc = alloc_blocks(c, prm->p);
+        int rc = alloc_blocks(c, prm->p, mixed);
         if (rc) return rc;
         c->bx_valid = false;
     }
+    if (!mixed) c->phase = 64;
     return OFKS_OK;
 }
 
@@ -423,18 +532,22 @@ int ofks_init_orbitals(ofks_ctx *c, const double *V) {
     if (!c->n || !c->p) return ofks_fail(c, OFKS_ESTATE, "init_orbitals: no mesh/params");
     cudaSetDevice(c->device);
     int rc;
-    double *Vd = c->d_X[c->cur ^ 1], *BV = c->d_Q;
+    Blocks<double> &b = c->b64;
+    double *Vd = b.X[c->cur ^ 1], *BV = b.Q;
     if ((rc = upload_block(c, V, Vd))) return rc;
-    launch_sell_spmm(c, c->d_valB, Vd, BV);
-    launch_gram2(c, Vd, BV, BV, c->d_S, c->d_L0);
+    launch_sell_spmm(c, (const double *)c->d_valB, (const double *)Vd, BV);
+    launch_gram2(c, (const double *)Vd, (const double *)BV, (const double *)BV, c->d_S, c->d_L0);
     double *Rinv = c->d_pp + 6 * (size_t)c->ld * c->ld;
     launch_cholesky_inv(c, c->d_S, Rinv);
-    launch_block_times_small(c, Vd, Rinv, c->d_X[c->cur]);
-    launch_block_times_small(c, BV, Rinv, c->d_BX);
+    launch_block_times_small(c, (const double *)Vd, Rinv, b.X[c->cur]);
+    launch_block_times_small(c, (const double *)BV, Rinv, b.BX);
     int flag = 0;
     if ((rc = read_flag(c, &flag))) return rc;
     if (flag) return ofks_fail(c, OFKS_ENOTCONV, "init_orbitals: V^T B V is not positive definite");
     c->bx_valid = true;
+    c->phase = c->prm.precision == OFKS_MIXED ? 32 : 64;
+    state_to32(c);
+    c->switch_k = -1;
     c->have_X = true; c->have_prev = false; c->converged = false; c->evaluated = false;
     c->k = 0; c->kkt0 = 0; c->eta = 0;
     c->history.clear();
@@ -446,8 +559,10 @@ int ofks_set_orbitals(ofks_ctx *c, const double *X, int32_t keep) {
     if (!c || !X) return OFKS_EINVAL;
     if (!c->n || !c->p) return ofks_fail(c, OFKS_ESTATE, "set_orbitals: no mesh/params");
     cudaSetDevice(c->device);
-    int rc = upload_block(c, X, c->d_X[c->cur]);
+    int rc = upload_block(c, X, c->b64.X[c->cur]);
     if (rc) return rc;
+    if (!keep) c->phase = c->prm.precision == OFKS_MIXED ? 32 : 64;
+    if (c->phase == 32) launch_convert(c, (const double *)c->b64.X[c->cur], c->b32.X[c->cur], c->n * (int64_t)c->ld);
     c->bx_valid = false;
     c->have_X = true;
     c->evaluated = false;
@@ -463,7 +578,8 @@ int ofks_get_orbitals(ofks_ctx *c, double *X) {
     if (!c || !X) return OFKS_EINVAL;
     if (!c->have_X) return ofks_fail(c, OFKS_ESTATE, "get_orbitals: no orbitals");
     cudaSetDevice(c->device);
-    return download_block(c, c->d_X[c->cur], X);
+    if (c->phase == 32) launch_convert(c, (const float *)c->b32.X[c->cur], c->b64.X[c->cur], c->n * (int64_t)c->ld);
+    return download_block(c, c->b64.X[c->cur], X);
 }
 
 int ofks_step(ofks_ctx *c, int32_t k, ofks_result *res) {
@@ -503,13 +619,18 @@ int ofks_rayleigh_ritz(ofks_ctx *c, double *eigs) {
     if (!c || !eigs) return OFKS_EINVAL;
     if (!c->have_X || !c->have_nuclei) return ofks_fail(c, OFKS_ESTATE, "rayleigh_ritz: need orbitals and nuclei");
     cudaSetDevice(c->device);
+    if (c->phase == 32) {            // Rayleigh-Ritz runs on the float64 state
+        state_to64(c);
+        c->phase = 64;
+        c->bx_valid = false;
+    }
     Rec r{};
     int rc = evaluate(c, !c->bx_valid, &r);
     if (rc) return rc;
     const size_t L2 = (size_t)c->ld * c->ld;
     double *V = c->d_pp + 5 * L2, *de = c->d_pp + 7 * L2;
     launch_rayleigh_ritz(c, c->d_L0, c->d_S, de, V);
-    launch_block_times_small(c, c->d_X[c->cur], V, c->d_X[c->cur ^ 1]);
+    launch_block_times_small(c, (const double *)c->b64.X[c->cur], V, c->b64.X[c->cur ^ 1]);
     int flag = 0;
     if ((rc = read_flag(c, &flag))) return rc;
     if (flag) return ofks_fail(c, OFKS_ENOTCONV, "rayleigh_ritz: X^T B X is not positive definite");
@@ -538,10 +659,20 @@ int ofks_get_field(ofks_ctx *c, int32_t which, double *out, int64_t count) {
         case OFKS_F_EXC_Q: src = c->d_exc; need = nq; break;
         case OFKS_F_VEXT_Q: src = c->d_vext; need = nq; break;
         case OFKS_F_U: src = c->d_U; need = c->n_nodes; break;
-        case OFKS_F_HX: src = c->d_HX; need = nb; kind = 1; break;
-        case OFKS_F_BX: src = c->d_BX; need = nb; kind = 1; break;
-        case OFKS_F_G: src = c->d_G[c->cur]; need = nb; kind = 1; break;
-        case OFKS_F_D: src = c->d_D[c->cur ^ (c->have_prev ? 1 : 0)]; need = nb; kind = 1; break;
+        case OFKS_F_HX: case OFKS_F_BX: case OFKS_F_G: case OFKS_F_D: {
+            const int dcur = c->cur ^ (c->have_prev ? 1 : 0);
+            need = nb; kind = 1;
+            if (c->phase == 32) {       // float32 state: widen into a float64 scratch block
+                const float *f = which == OFKS_F_HX ? c->b32.HX : which == OFKS_F_BX ? c->b32.BX
+                               : which == OFKS_F_G ? c->b32.G[c->cur] : c->b32.D[dcur];
+                launch_convert(c, f, c->b64.R, c->n * (int64_t)c->ld);
+                src = c->b64.R;
+            } else {
+                src = which == OFKS_F_HX ? c->b64.HX : which == OFKS_F_BX ? c->b64.BX
+                    : which == OFKS_F_G ? c->b64.G[c->cur] : c->b64.D[dcur];
+            }
+            break;
+        }
         case OFKS_F_LAMBDA0: src = c->d_L0; need = pp; kind = 2; break;
         case OFKS_F_S: src = c->d_S; need = pp; kind = 2; break;
         case OFKS_F_LAMBDA: src = c->d_Lam; need = pp; kind = 2; break;
@@ -568,11 +699,11 @@ int ofks_apply(ofks_ctx *c, int32_t which, const double *X, double *Y, int32_t n
     if (!val) return ofks_fail(c, OFKS_EINVAL, "apply: unknown matrix %d", which);
     if (which == OFKS_M_H && !c->evaluated) return ofks_fail(c, OFKS_ESTATE, "apply: H needs an evaluation");
     cudaSetDevice(c->device);
-    int rc = upload_block(c, X, c->d_Z);
+    int rc = upload_block(c, X, c->b64.Z);
     if (rc) return rc;
-    launch_sell_spmm(c, val, c->d_Z, c->d_Q);
+    launch_sell_spmm(c, val, (const double *)c->b64.Z, c->b64.Q);
     if ((rc = ofks_cuda_check(c, cudaGetLastError(), "apply"))) return rc;
-    return download_block(c, c->d_Q, Y);
+    return download_block(c, c->b64.Q, Y);
 }
 
 int ofks_get_sizes(ofks_ctx *c, int64_t *n_free, int64_t *n_nodes, int64_t *n_tets, int64_t *nnz,
@@ -598,7 +729,7 @@ int ofks_get_history(ofks_ctx *c, double *buf, int32_t cap, int32_t *len) {
 struct StateHeader {
     char magic[8];
     int64_t n, n_nodes;
-    int32_t p, ld, k, cur_unused, have_prev, converged;
+    int32_t p, ld, k, phase, have_prev, converged;
     double kkt0, eta, eta_dev;
     int64_t hist_rows;
 };
@@ -607,15 +738,19 @@ int ofks_save_state(ofks_ctx *c, const char *path) {
     if (!c || !path) return OFKS_EINVAL;
     if (!c->have_X) return ofks_fail(c, OFKS_ESTATE, "save_state: no orbitals");
     cudaSetDevice(c->device);
-    if (!c->bx_valid) { launch_sell_spmm(c, c->d_valB, c->d_X[c->cur], c->d_BX); c->bx_valid = true; }
+    state_to64(c);
+    if (!c->bx_valid)
+        launch_sell_spmm(c, (const double *)c->d_valB, (const double *)c->b64.X[c->cur], c->b64.BX);
     StateHeader h{};
     memcpy(h.magic, "OFKSST1", 8);
     h.n = c->n; h.n_nodes = c->n_nodes; h.p = c->p; h.ld = c->ld; h.k = c->k; h.have_prev = c->have_prev;
     h.converged = c->converged; h.kkt0 = c->kkt0; h.eta = c->eta; h.hist_rows = (int64_t)c->history.size() / 6;
+    h.phase = c->phase;
     cudaMemcpyAsync(&h.eta_dev, c->d_sc + SC_ETA, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     const size_t blk = (size_t)c->n * c->ld;
     std::vector<double> buf(blk * 5 + c->n_nodes);
-    const double *srcs[5] = {c->d_X[c->cur], c->d_X[c->cur ^ 1], c->d_D[c->cur ^ 1], c->d_G[c->cur ^ 1], c->d_BX};
+    const double *srcs[5] = {c->b64.X[c->cur], c->b64.X[c->cur ^ 1], c->b64.D[c->cur ^ 1], c->b64.G[c->cur ^ 1],
+                             c->b64.BX};
     for (int i = 0; i < 5; ++i)
         cudaMemcpyAsync(buf.data() + i * blk, srcs[i], sizeof(double) * blk, cudaMemcpyDeviceToHost, c->stream);
     cudaMemcpyAsync(buf.data() + 5 * blk, c->d_U, sizeof(double) * c->n_nodes, cudaMemcpyDeviceToHost, c->stream);
@@ -652,7 +787,7 @@ int ofks_load_state(ofks_ctx *c, const char *path) {
     if (!ok) return ofks_fail(c, OFKS_EINVAL, "load_state: %s is truncated", path);
     cudaSetDevice(c->device);
     c->cur = 0;
-    double *dsts[5] = {c->d_X[0], c->d_X[1], c->d_D[1], c->d_G[1], c->d_BX};
+    double *dsts[5] = {c->b64.X[0], c->b64.X[1], c->b64.D[1], c->b64.G[1], c->b64.BX};
     for (int i = 0; i < 5; ++i)
         cudaMemcpyAsync(dsts[i], buf.data() + i * blk, sizeof(double) * blk, cudaMemcpyHostToDevice, c->stream);
     cudaMemcpyAsync(c->d_U, buf.data() + 5 * blk, sizeof(double) * c->n_nodes, cudaMemcpyHostToDevice, c->stream);
@@ -660,11 +795,133 @@ int ofks_load_state(ofks_ctx *c, const char *path) {
     int rc = ofks_cuda_check(c, cudaStreamSynchronize(c->stream), "load_state");
     if (rc) return rc;
     c->bx_valid = true;
+    c->phase = (h.phase == 32 && c->mixed_alloc) ? 32 : 64;
+    state_to32(c);
     c->have_X = true; c->k = h.k; c->have_prev = h.have_prev; c->converged = h.converged; c->kkt0 = h.kkt0;
     c->eta = h.eta; c->evaluated = false;
     c->history = hist;
     c->t_start = now_s() - (hist.empty() ? 0.0 : hist[hist.size() - 5]);
     return OFKS_OK;
+}
+
+// ------------------------------------------------------------------------- learned preconditioner
+int ofks_precond_init(ofks_ctx *c, int32_t width, uint64_t seed) {
+    if (!c) return OFKS_EINVAL;
+    if (!c->n) return ofks_fail(c, OFKS_ESTATE, "precond_init: no mesh");
+    if (width != 8 && width != 16 && width != 32 && width != 64)
+        return ofks_fail(c, OFKS_EINVAL, "precond_init: width must be 8, 16, 32 or 64");
+    cudaSetDevice(c->device);
+    return gcn_setup(c, width, seed, c->row_deg);
+}
+
+int ofks_precond_get_weights(ofks_ctx *c, float *w, int64_t cap, int64_t *count) {
+    if (!c || !count) return OFKS_EINVAL;
+    if (!c->gcn.H) return ofks_fail(c, OFKS_ESTATE, "precond_get_weights: no network");
+    const int64_t m = gcn_param_count(c->gcn.H);
+    *count = m;
+    if (!w) return OFKS_OK;
+    if (cap < m) return ofks_fail(c, OFKS_EINVAL, "precond_get_weights: need %lld floats", (long long)m);
+    cudaSetDevice(c->device);
+    return ofks_cuda_check(c, cudaMemcpy(w, c->gcn.w, sizeof(float) * m, cudaMemcpyDeviceToHost), "get_weights");
+}
+
+int ofks_precond_set_weights(ofks_ctx *c, const float *w, int64_t count) {
+    if (!c || !w) return OFKS_EINVAL;
+    if (!c->n) return ofks_fail(c, OFKS_ESTATE, "precond_set_weights: no mesh");
+    int width = 0;
+    for (int h : {8, 16, 32, 64})
+        if (gcn_param_count(h) == count) width = h;
+    if (!width) return ofks_fail(c, OFKS_EINVAL, "precond_set_weights: %lld values match no width", (long long)count);
+    cudaSetDevice(c->device);
+    if (c->gcn.H != width) {
+        int rc = gcn_setup(c, width, 0, c->row_deg);
+        if (rc) return rc;
+    }
+    return ofks_cuda_check(c, cudaMemcpy(c->gcn.w, w, sizeof(float) * count, cudaMemcpyHostToDevice), "set_weights");
+}
+
+int ofks_precondition(ofks_ctx *c, int32_t mode, const double *G, const double *shifts, double *D) {
+    if (!c || !G || !shifts || !D) return OFKS_EINVAL;
+    if (!c->n || !c->p) return ofks_fail(c, OFKS_ESTATE, "precondition: no mesh/params");
+    if (mode != OFKS_PC_PCG && mode != OFKS_PC_EXACT && mode != OFKS_PC_LEARNED)
+        return ofks_fail(c, OFKS_EINVAL, "precondition: unknown mode %d", mode);
+    cudaSetDevice(c->device);
+    const int ld = c->ld;
+    if (mode == OFKS_PC_LEARNED) {
+        if (!c->gcn.H) return ofks_fail(c, OFKS_ESTATE, "precondition: no network");
+        int rc;
+        if (!c->d_shift_in && cudaMalloc((void **)&c->d_shift_in, sizeof(double) * 256) != cudaSuccess)
+            return ofks_fail(c, OFKS_ENOMEM, "shift buffer");
+        if ((rc = upload_block(c, G, c->b64.Z))) return rc;
+        cudaMemcpyAsync(c->d_shift_in, shifts, sizeof(double) * c->p, cudaMemcpyHostToDevice, c->stream);
+        if ((rc = gcn_forward_prepare(c))) return rc;
+        gcn_pack<double>(c, c->b64.Z, c->gcn.G32);
+        if ((rc = gcn_forward(c, c->d_shift_in, false))) return rc;
+        gcn_unpack<double>(c, c->gcn.Dn, c->b64.Q);
+        // columns with shift >= 0: D = G
+        std::vector<double> act(ld, 0.0);
+        for (int j = 0; j < c->p; ++j) act[j] = shifts[j] < 0 ? 1.0 : 0.0;
+        cudaMemcpyAsync(c->d_colA + CB_ACTIVE * ld, act.data(), sizeof(double) * ld, cudaMemcpyHostToDevice, c->stream);
+        Blocks<double> tmp = c->b64;
+        tmp.G[c->cur] = c->b64.Z;
+        tmp.D[c->cur] = c->b64.Q;
+        launch_direction_select(c, tmp);
+        return download_block(c, c->b64.Q, D);
+    }
+    // PCG / exact: run the iteration's preconditioner on (G, shifts) in float64
+    std::vector<double> col(2 * (size_t)ld, 0.0);
+    for (int j = 0; j < c->p; ++j) {
+        col[j] = shifts[j] < 0 ? shifts[j] : 0.0;
+        col[ld + j] = shifts[j] < 0 ? 1.0 : 0.0;
+    }
+    cudaMemcpyAsync(c->d_colA + CB_SHIFT * ld, col.data(), sizeof(double) * 2 * ld, cudaMemcpyHostToDevice, c->stream);
+    cudaMemsetAsync(c->d_colA + CB_ACC * ld, 0, sizeof(double) * ld, c->stream);
+    int rc = upload_block(c, G, c->b64.G[c->cur]);
+    if (rc) return rc;
+    const int saved = c->prm.precond, phase = c->phase;
+    c->prm.precond = mode;
+    c->phase = 64;
+    rc = precondition_t<double>(c);
+    c->prm.precond = saved;
+    c->phase = phase;
+    if (rc) return rc;
+    return download_block(c, c->b64.D[c->cur], D);
+}
+
+static int train_common(ofks_ctx *c, const double *G, const double *shifts, const double *Dstar, double *loss) {
+    if (!c->gcn.H) return ofks_fail(c, OFKS_ESTATE, "no network (ofks_precond_init)");
+    if (!c->n || !c->p) return ofks_fail(c, OFKS_ESTATE, "no mesh/params");
+    if (!c->d_shift_in && cudaMalloc((void **)&c->d_shift_in, sizeof(double) * 256) != cudaSuccess)
+        return ofks_fail(c, OFKS_ENOMEM, "shift buffer");
+    int rc;
+    if ((rc = upload_block(c, G, c->b64.Z)) || (rc = upload_block(c, Dstar, c->b64.R))) return rc;
+    cudaMemcpyAsync(c->d_shift_in, shifts, sizeof(double) * c->p, cudaMemcpyHostToDevice, c->stream);
+    if ((rc = gcn_forward_prepare(c))) return rc;
+    gcn_pack<double>(c, c->b64.Z, c->gcn.G32);
+    gcn_pack<double>(c, c->b64.R, c->gcn.Ds);
+    if ((rc = gcn_forward(c, c->d_shift_in, true))) return rc;
+    return gcn_backward(c, loss);
+}
+
+int ofks_train_precond_step(ofks_ctx *c, const double *G, const double *shifts, const double *Dstar, double lr,
+                            double *loss) {
+    if (!c || !G || !shifts || !Dstar || !loss || !(lr > 0)) return OFKS_EINVAL;
+    cudaSetDevice(c->device);
+    int rc = train_common(c, G, shifts, Dstar, loss);
+    if (rc) return rc;
+    if ((rc = gcn_adam(c, lr))) return rc;
+    return ofks_cuda_check(c, cudaStreamSynchronize(c->stream), "train step");
+}
+
+int ofks_precond_grads(ofks_ctx *c, const double *G, const double *shifts, const double *Dstar, double *grads,
+                       int64_t cap, double *loss) {
+    if (!c || !G || !shifts || !Dstar || !grads || !loss) return OFKS_EINVAL;
+    cudaSetDevice(c->device);
+    int rc = train_common(c, G, shifts, Dstar, loss);
+    if (rc) return rc;
+    const int64_t m = gcn_param_count(c->gcn.H);
+    if (cap < m) return ofks_fail(c, OFKS_EINVAL, "precond_grads: need %lld values", (long long)m);
+    return ofks_cuda_check(c, cudaMemcpy(grads, c->gcn.grad, sizeof(double) * m, cudaMemcpyDeviceToHost), "grads");
 }
 
 int ofks_profile(ofks_ctx *c, int32_t on) {

@@ -3,14 +3,12 @@
 //   C = beta (S - I) - Lambda (Eq. PLAM-main), the residual H X - B X Lambda0 for kkt
 //   (Sec. 4.1), the Jacobi-PCG vector updates of the preconditioner (Eq. precondition-T),
 //   the Barzilai-Borwein inner products (Sec. 4.4), and the step/normalization of
-//   Eq. (PCAL-main).  Blocks are row-major n x ld float64 with zero padding columns.
+//   Eq. (PCAL-main).  Blocks are row-major n x ld (float64 or float32, T) with zero padding
+//   columns; p x p matrices and every reduction are float64.
 #include <algorithm>
 
 #include "common.cuh"
 #include "internal.h"
-
-enum { CB_SHIFT = 0, CB_ACTIVE = 1, CB_RZ = 2, CB_RZN = 3, CB_PQ = 4, CB_BETA = 5, CB_NORM = 6,
-       CB_ALPHA = 7, CB_COUNT = 8 };
 
 namespace {
 
@@ -20,14 +18,14 @@ namespace {
 // computed, numbered consecutively so that whole warps stay idle when there are fewer of them
 // than threads (a float64 warp instruction costs the same however many lanes are active).
 // Rows are staged KR at a time in shared memory.
-template <int RT>
+template <class T, int RT>
 __global__ void __launch_bounds__(256) k_gram2(int64_t n, int p, int ld, int ntile,
-                                               const double *__restrict__ X,
-                                               const double *__restrict__ A,
-                                               const double *__restrict__ B, double *XA, double *XB,
+                                               const T *__restrict__ X,
+                                               const T *__restrict__ A,
+                                               const T *__restrict__ B, double *XA, double *XB,
                                                int64_t rows_per_split) {
     constexpr int TS = 16 * RT, KR = 16;
-    __shared__ double xs[KR][TS], as[KR][TS], bs[KR][TS];
+    __shared__ T xs[KR][TS], as[KR][TS], bs[KR][TS];
     // decode the upper-triangular tile pair
     int pair = blockIdx.x, ti = 0;
     while (pair >= ntile - ti) { pair -= ntile - ti; ++ti; }
@@ -49,25 +47,25 @@ __global__ void __launch_bounds__(256) k_gram2(int64_t n, int p, int ld, int nti
     }
     const int64_t r0 = blockIdx.y * rows_per_split;
     const int64_t r1 = (r0 + rows_per_split < n) ? r0 + rows_per_split : n;
-    double ca[RT][RT], cb[RT][RT];
+    T ca[RT][RT], cb[RT][RT];
 #pragma unroll
     for (int a = 0; a < RT; ++a)
 #pragma unroll
-        for (int b = 0; b < RT; ++b) { ca[a][b] = 0.0; cb[a][b] = 0.0; }
+        for (int b = 0; b < RT; ++b) { ca[a][b] = T(0); cb[a][b] = T(0); }
     for (int64_t rb = r0; rb < r1; rb += KR) {
         for (int idx = threadIdx.x; idx < KR * TS; idx += 256) {
             const int rr = idx / TS, cc = idx - rr * TS;
             const int64_t r = rb + rr;
             const bool okr = r < r1;
-            xs[rr][cc] = (okr && i0 + cc < ld) ? X[r * ld + i0 + cc] : 0.0;
-            as[rr][cc] = (okr && j0 + cc < ld) ? A[r * ld + j0 + cc] : 0.0;
-            bs[rr][cc] = (okr && j0 + cc < ld) ? B[r * ld + j0 + cc] : 0.0;
+            xs[rr][cc] = (okr && i0 + cc < ld) ? X[r * ld + i0 + cc] : T(0);
+            as[rr][cc] = (okr && j0 + cc < ld) ? A[r * ld + j0 + cc] : T(0);
+            bs[rr][cc] = (okr && j0 + cc < ld) ? B[r * ld + j0 + cc] : T(0);
         }
         __syncthreads();
         if (act)
 #pragma unroll 4
         for (int k = 0; k < KR; ++k) {
-            double xv[RT], av[RT], bv[RT];
+            T xv[RT], av[RT], bv[RT];
 #pragma unroll
             for (int a = 0; a < RT; ++a) xv[a] = xs[k][bi * RT + a];
 #pragma unroll
@@ -89,8 +87,8 @@ __global__ void __launch_bounds__(256) k_gram2(int64_t n, int p, int ld, int nti
         for (int b = 0; b < RT; ++b) {
             const int i = i0 + bi * RT + a, j = j0 + bj * RT + b;
             if (i < p && j < p && i <= j) {
-                atomicAdd(XA + (int64_t)i * ld + j, ca[a][b]);
-                atomicAdd(XB + (int64_t)i * ld + j, cb[a][b]);
+                atomicAdd(XA + (int64_t)i * ld + j, (double)ca[a][b]);
+                atomicAdd(XB + (int64_t)i * ld + j, (double)cb[a][b]);
             }
         }
 }
@@ -109,26 +107,26 @@ __global__ void k_mirror2(int p, int ld, double *A, double *B) {
 // G = HX + BX C ;  kkt2 += ||HX - BX L0||^2 (columns < p).  A 32-row tile is staged in shared
 // memory; its 32 x ld outputs are spread over the 256 threads (output o = tid + 256 i), so
 // every lane issues useful float64 FMAs whatever ld is.  C and L0 are staged in KC-row chunks.
-template <int NO>
-__global__ void __launch_bounds__(256) k_grad(int64_t n, int p, int ld, const double *__restrict__ HX,
-                                              const double *__restrict__ BX,
+template <class T, int NO>
+__global__ void __launch_bounds__(256) k_grad(int64_t n, int p, int ld, const T *__restrict__ HX,
+                                              const T *__restrict__ BX,
                                               const double *__restrict__ C,
-                                              const double *__restrict__ L0, double *G,
+                                              const double *__restrict__ L0, T *G,
                                               double *kkt2, int KC) {
-    extern __shared__ double smem[];
-    double *bx = smem;                 // 32 x ld
-    double *cs = bx + 32 * ld;         // KC x ld
-    double *ls = cs + KC * ld;         // KC x ld
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *bx = reinterpret_cast<T *>(smem_raw);   // 32 x ld
+    T *cs = bx + 32 * ld;                       // KC x ld
+    T *ls = cs + KC * ld;                       // KC x ld
     __shared__ double red[8];
     const int nout = 32 * ld;
     double part = 0.0;
     for (int64_t rt = blockIdx.x * 32LL; rt < n; rt += 32LL * gridDim.x) {
-        double g[NO], rr[NO];
+        T g[NO], rr[NO];
         int orow[NO], ocol[NO];
         __syncthreads();
         for (int idx = threadIdx.x; idx < nout; idx += 256) {
             const int64_t r = rt + idx / ld;
-            bx[idx] = r < n ? BX[rt * ld + idx] : 0.0;
+            bx[idx] = r < n ? BX[rt * ld + idx] : T(0);
         }
 #pragma unroll
         for (int i = 0; i < NO; ++i) {
@@ -136,22 +134,22 @@ __global__ void __launch_bounds__(256) k_grad(int64_t n, int p, int ld, const do
             orow[i] = o / ld;
             ocol[i] = o - orow[i] * ld;
             const int64_t r = rt + orow[i];
-            const double h = (o < nout && r < n) ? HX[rt * ld + o] : 0.0;
+            const T h = (o < nout && r < n) ? HX[rt * ld + o] : T(0);
             g[i] = h; rr[i] = h;
         }
         for (int k0 = 0; k0 < ld; k0 += KC) {
             const int kl = min(KC, ld - k0);
             __syncthreads();
             for (int idx = threadIdx.x; idx < kl * ld; idx += 256) {
-                cs[idx] = C[(int64_t)k0 * ld + idx];
-                ls[idx] = L0[(int64_t)k0 * ld + idx];
+                cs[idx] = (T)C[(int64_t)k0 * ld + idx];
+                ls[idx] = (T)L0[(int64_t)k0 * ld + idx];
             }
             __syncthreads();
             for (int kk = 0; kk < kl; ++kk) {
 #pragma unroll
                 for (int i = 0; i < NO; ++i) {
                     if (threadIdx.x + 256 * i < nout) {
-                        const double b = bx[orow[i] * ld + k0 + kk];
+                        const T b = bx[orow[i] * ld + k0 + kk];
                         g[i] = fma(b, cs[kk * ld + ocol[i]], g[i]);
                         rr[i] = fma(-b, ls[kk * ld + ocol[i]], rr[i]);
                     }
@@ -164,7 +162,7 @@ __global__ void __launch_bounds__(256) k_grad(int64_t n, int p, int ld, const do
             const int64_t r = rt + orow[i];
             if (o >= nout || r >= n) continue;
             G[rt * ld + o] = g[i];
-            if (ocol[i] < p) part += rr[i] * rr[i];
+            if (ocol[i] < p) part += (double)(rr[i] * rr[i]);
         }
     }
     part = block_sum(part, red);
@@ -200,44 +198,83 @@ __device__ __forceinline__ void col_reduce(double acc, int j, bool active, int l
 }
 
 // PCG start: W = 1/diag with diag = dL/2 - shift_c dB, D = 0, R = G, Z = G W, rz[c] = sum R Z
+template <class T>
 __global__ void __launch_bounds__(256) k_pcg_init(int64_t n, int p, int ld, int64_t stride,
-                                                  const double *__restrict__ G,
+                                                  const T *__restrict__ G,
                                                   const double *__restrict__ dL,
                                                   const double *__restrict__ dB, const double *cb,
-                                                  double *W, double *D, double *R, double *Z, double *rz) {
-    double acc = 0.0;
+                                                  T *W, T *D, T *R, T *Z, double *rz) {
+    T acc = T(0);
     ELEM_BEGIN
-        const double sh = cb[CB_SHIFT * ld + j];
-        const double w = 1.0 / (0.5 * dL[r] - sh * dB[r]);
-        const double gv = G[e];
-        const double z = gv * w;
-        W[e] = w; D[e] = 0.0; R[e] = gv; Z[e] = z;
+        const T sh = (T)cb[CB_SHIFT * ld + j];
+        const T w = T(1) / (T(0.5) * (T)dL[r] - sh * (T)dB[r]);
+        const T gv = G[e];
+        const T z = gv * w;
+        W[e] = w; D[e] = T(0); R[e] = gv; Z[e] = z;
         acc = fma(gv, z, acc);
     ELEM_END
-    col_reduce(acc, j, gid < stride, ld, p, rz);
+    col_reduce((double)acc, j, gid < stride, ld, p, rz);
+}
+
+// learned preconditioner judge sums per column: |G - T D|^2 (T D in Q), |G|^2, G.D
+template <class T>
+__global__ void __launch_bounds__(256) k_judge(int64_t n, int p, int ld, int64_t stride, const T *__restrict__ G,
+                                               const T *__restrict__ Q, const T *__restrict__ D, double *rr,
+                                               double *gg, double *gd) {
+    T a = T(0), b = T(0), d = T(0);
+    ELEM_BEGIN
+        const T g = G[e], r = g - Q[e];
+        a = fma(r, r, a); b = fma(g, g, b); d = fma(g, D[e], d);
+    ELEM_END
+    col_reduce((double)a, j, gid < stride, ld, p, rr);
+    __syncthreads();
+    col_reduce((double)b, j, gid < stride, ld, p, gg);
+    __syncthreads();
+    col_reduce((double)d, j, gid < stride, ld, p, gd);
+}
+
+// PCG restarted from the current D (the network's output): R = G - Q with Q = T D, Z = R W
+template <class T>
+__global__ void __launch_bounds__(256) k_pcg_init_warm(int64_t n, int p, int ld, int64_t stride,
+                                                       const T *__restrict__ G, const T *__restrict__ Q,
+                                                       const double *__restrict__ dL,
+                                                       const double *__restrict__ dB, const double *cb,
+                                                       T *W, T *R, T *Z, double *rz) {
+    T acc = T(0);
+    ELEM_BEGIN
+        const T sh = (T)cb[CB_SHIFT * ld + j];
+        const T w = T(1) / (T(0.5) * (T)dL[r] - sh * (T)dB[r]);
+        const T rv = G[e] - Q[e];
+        const T z = rv * w;
+        W[e] = w; R[e] = rv; Z[e] = z;
+        acc = fma(rv, z, acc);
+    ELEM_END
+    col_reduce((double)acc, j, gid < stride, ld, p, rz);
 }
 
 // alpha = rz/pq; D += alpha P; R -= alpha Q; Z = R W; rzn += R Z
+template <class T>
 __global__ void __launch_bounds__(256) k_pcg_update(int64_t n, int p, int ld, int64_t stride, const double *cb,
-                                                    const double *__restrict__ W,
-                                                    const double *__restrict__ P,
-                                                    const double *__restrict__ Q, double *D, double *R,
-                                                    double *Z, double *rzn) {
-    double acc = 0.0;
-    const double al = cb[CB_ALPHA * ld + (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) % ld];
+                                                    const T *__restrict__ W,
+                                                    const T *__restrict__ P,
+                                                    const T *__restrict__ Q, T *D, T *R,
+                                                    T *Z, double *rzn) {
+    T acc = T(0);
+    const T al = (T)cb[CB_ALPHA * ld + (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) % ld];
     ELEM_BEGIN
         D[e] = fma(al, P[e], D[e]);
-        const double rv = fma(-al, Q[e], R[e]);
-        const double z = rv * W[e];
+        const T rv = fma(-al, Q[e], R[e]);
+        const T z = rv * W[e];
         R[e] = rv; Z[e] = z;
         acc = fma(rv, z, acc);
     ELEM_END
-    col_reduce(acc, j, gid < stride, ld, p, rzn);
+    col_reduce((double)acc, j, gid < stride, ld, p, rzn);
 }
 
 // columns whose shift is not negative take D = G (T = I in Eq. precondition-T)
+template <class T>
 __global__ void __launch_bounds__(256) k_select(int64_t n, int ld, int64_t stride, const double *cb,
-                                                const double *__restrict__ G, double *D) {
+                                                const T *__restrict__ G, T *D) {
     const int jj = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) % ld);
     if (cb[CB_ACTIVE * ld + jj] != 0.0) return;
     ELEM_BEGIN
@@ -246,81 +283,91 @@ __global__ void __launch_bounds__(256) k_select(int64_t n, int ld, int64_t strid
 }
 
 // Barzilai-Borwein sums: <dX,dD>, <dD,dD>, <dX,dX>, and ||X||^2, ||D||^2
-__global__ void __launch_bounds__(256) k_bb(int64_t n, int ld, int64_t stride, const double *__restrict__ X,
-                                            const double *__restrict__ Xp, const double *__restrict__ D,
-                                            const double *__restrict__ Dp, int have_prev, double *sc) {
+template <class T>
+__global__ void __launch_bounds__(256) k_bb(int64_t n, int ld, int64_t stride, const T *__restrict__ X,
+                                            const T *__restrict__ Xp, const T *__restrict__ D,
+                                            const T *__restrict__ Dp, int have_prev, double *sc) {
     __shared__ double red[8];
-    double sy = 0, yy = 0, ss = 0, xx = 0, dd = 0;
+    T sy = 0, yy = 0, ss = 0, xx = 0, dd = 0;
     {
         ELEM_BEGIN
-            const double x = X[e], d = D[e];
+            const T x = X[e], d = D[e];
             xx = fma(x, x, xx); dd = fma(d, d, dd);
             if (have_prev) {
-                const double sx = x - Xp[e], yd = d - Dp[e];
+                const T sx = x - Xp[e], yd = d - Dp[e];
                 sy = fma(sx, yd, sy); yy = fma(yd, yd, yy); ss = fma(sx, sx, ss);
             }
         ELEM_END
     }
-    sy = block_sum(sy, red); yy = block_sum(yy, red); ss = block_sum(ss, red);
-    xx = block_sum(xx, red); dd = block_sum(dd, red);
+    const double syd = block_sum((double)sy, red), yyd = block_sum((double)yy, red),
+                 ssd = block_sum((double)ss, red), xxd = block_sum((double)xx, red),
+                 ddd = block_sum((double)dd, red);
     if (threadIdx.x == 0) {
-        atomicAdd(sc + SC_BB + 0, sy); atomicAdd(sc + SC_BB + 1, yy); atomicAdd(sc + SC_BB + 2, ss);
-        atomicAdd(sc + SC_XNRM2, xx); atomicAdd(sc + SC_DNRM2, dd);
+        atomicAdd(sc + SC_BB + 0, syd); atomicAdd(sc + SC_BB + 1, yyd); atomicAdd(sc + SC_BB + 2, ssd);
+        atomicAdd(sc + SC_XNRM2, xxd); atomicAdd(sc + SC_DNRM2, ddd);
     }
 }
 
 // Y = X - D / eta
-__global__ void __launch_bounds__(256) k_step(int64_t n, int ld, int64_t stride, const double *__restrict__ X,
-                                              const double *__restrict__ D, const double *sc, double *Y) {
-    const double inv = 1.0 / sc[SC_ETA];
+template <class T>
+__global__ void __launch_bounds__(256) k_step(int64_t n, int ld, int64_t stride, const T *__restrict__ X,
+                                              const T *__restrict__ D, const double *sc, T *Y) {
+    const T inv = (T)(1.0 / sc[SC_ETA]);
     ELEM_BEGIN
         Y[e] = fma(-inv, D[e], X[e]);
     ELEM_END
 }
 
 // X_i = Y_i / ||Y_i||_B and B X_i = B Y_i / ||Y_i||_B   (Eq. PCAL-main)
+template <class T>
 __global__ void __launch_bounds__(256) k_scale(int64_t n, int p, int ld, int64_t stride, const double *colsum,
-                                               double *Y, double *BY) {
+                                               T *Y, T *BY) {
     const int jj = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) % ld);
     if (jj >= p) return;
-    const double s = 1.0 / sqrt(colsum[jj]);
+    const T s = (T)(1.0 / sqrt(colsum[jj]));
     ELEM_BEGIN
         Y[e] *= s; BY[e] *= s;
     ELEM_END
 }
 
+template <class S, class T>
+__global__ void k_convert(int64_t count, const S *__restrict__ src, T *dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (T)src[i];
+}
+
 // Y = X M with M (ld x ld, zero padded) staged in KC-row chunks
-template <int MC>
-__global__ void __launch_bounds__(256) k_block_small(int64_t n, int ld, const double *__restrict__ X,
-                                                     const double *__restrict__ M, double *Y, int KC) {
-    extern __shared__ double smem[];
-    double *xs = smem;                 // 32 x ld
-    double *ms = xs + 32 * ld;         // KC x ld
+template <class T, int MC>
+__global__ void __launch_bounds__(256) k_block_small(int64_t n, int ld, const T *__restrict__ X,
+                                                     const double *__restrict__ M, T *Y, int KC) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *xs = reinterpret_cast<T *>(smem_raw);   // 32 x ld
+    T *ms = xs + 32 * ld;                       // KC x ld
     const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
     for (int64_t rt = blockIdx.x * 32LL; rt < n; rt += 32LL * gridDim.x) {
-        double y[4][MC];
+        T y[4][MC];
         __syncthreads();
         for (int idx = threadIdx.x; idx < 32 * ld; idx += 256) {
             const int64_t r = rt + idx / ld;
-            xs[idx] = r < n ? X[rt * ld + idx] : 0.0;
+            xs[idx] = r < n ? X[rt * ld + idx] : T(0);
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int m = 0; m < MC; ++m) y[a][m] = 0.0;
+            for (int m = 0; m < MC; ++m) y[a][m] = T(0);
         for (int k0 = 0; k0 < ld; k0 += KC) {
             const int kl = min(KC, ld - k0);
             __syncthreads();
-            for (int idx = threadIdx.x; idx < kl * ld; idx += 256) ms[idx] = M[(int64_t)k0 * ld + idx];
+            for (int idx = threadIdx.x; idx < kl * ld; idx += 256) ms[idx] = (T)M[(int64_t)k0 * ld + idx];
             __syncthreads();
             for (int kk = 0; kk < kl; ++kk) {
-                double b[4];
+                T b[4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) b[a] = xs[(rg * 4 + a) * ld + k0 + kk];
 #pragma unroll
                 for (int m = 0; m < MC; ++m) {
                     const int j = lane + 32 * m;
-                    const double mv = j < ld ? ms[kk * ld + j] : 0.0;
+                    const T mv = j < ld ? ms[kk * ld + j] : T(0);
 #pragma unroll
                     for (int a = 0; a < 4; ++a) y[a][m] = fma(b[a], mv, y[a][m]);
                 }
@@ -362,7 +409,9 @@ inline int kc_of(int ld) { return ld <= 64 ? ld : 32; }
         default: { constexpr int M_ = 8; __VA_ARGS__; } break; \
     }
 
-void launch_gram2(ofks_ctx *c, const double *X, const double *A, const double *B, double *XA, double *XB) {
+template <class T>
+void launch_gram2(ofks_ctx *c, const T *X, const T *A, const T *B, double *XA, double *XB) {
+    c->kernels += 2;
     ProfScope ps(c, PF_GRAM);
     const int ld = c->ld, p = c->p;
     cudaMemsetAsync(XA, 0, sizeof(double) * ld * ld, c->stream);
@@ -373,11 +422,10 @@ void launch_gram2(ofks_ctx *c, const double *X, const double *A, const double *B
     const int64_t rps = ((c->n + splits - 1) / splits + 15) / 16 * 16;
     splits = (c->n + rps - 1) / rps;
     dim3 grid((unsigned)npair, (unsigned)splits);
-#define G_(rt) k_gram2<rt><<<grid, 256, 0, c->stream>>>(c->n, p, ld, ntile, X, A, B, XA, XB, rps)
+#define G_(rt) k_gram2<T, rt><<<grid, 256, 0, c->stream>>>(c->n, p, ld, ntile, X, A, B, XA, XB, rps)
     switch (RT) { case 1: G_(1); break; case 2: G_(2); break; case 3: G_(3); break; default: G_(4); }
 #undef G_
     k_mirror2<<<4, 256, 0, c->stream>>>(p, ld, XA, XB);
-    c->kernels += 2;
 }
 
 // grid of 256-thread blocks whose total thread count is a multiple of ld
@@ -389,82 +437,142 @@ static ElemGrid elem_grid(int64_t n, int ld) {
     return {(unsigned)((stride + 255) / 256), stride};
 }
 
-void launch_grad_update(ofks_ctx *c) {
+template <class T>
+void launch_grad_update(ofks_ctx *c, Blocks<T> &b) {
     c->kernels += 1;
     ProfScope ps(c, PF_GRAD);
     const int ld = c->ld, KC = kc_of(ld);
-    const size_t sm = sizeof(double) * (32 * ld + 2 * KC * ld);
-    double *G = c->d_G[c->cur];
+    const size_t sm = sizeof(T) * (32 * ld + 2 * KC * ld);
+    T *G = b.G[c->cur];
     cudaMemsetAsync(c->d_sc + SC_KKT2, 0, sizeof(double), c->stream);
     const unsigned grid = row_grid(32, c->n);
     const int no = (32 * ld + 255) / 256;
-#define GR_(k) { cudaFuncSetAttribute(k_grad<k>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        k_grad<k><<<grid, 256, sm, c->stream>>>(c->n, c->p, ld, c->d_HX, c->d_BX, c->d_C, c->d_L0, G, \
-                                               c->d_sc + SC_KKT2, KC); }
+#define GR_(k) { cudaFuncSetAttribute(k_grad<T, k>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        k_grad<T, k><<<grid, 256, sm, c->stream>>>(c->n, c->p, ld, b.HX, b.BX, c->d_C, c->d_L0, G, \
+                                                  c->d_sc + SC_KKT2, KC); }
     if (no <= 1) GR_(1) else if (no <= 2) GR_(2) else if (no <= 4) GR_(4) else if (no <= 6) GR_(6)
     else if (no <= 8) GR_(8) else if (no <= 16) GR_(16) else GR_(32)
 #undef GR_
 }
 
-void launch_pcg_init(ofks_ctx *c) {
+template <class T>
+void launch_pcg_init(ofks_ctx *c, Blocks<T> &b) {
     c->kernels += 1;
     const int ld = c->ld;
     double *cb = c->d_colA;
     cudaMemsetAsync(cb + CB_RZ * ld, 0, sizeof(double) * ld, c->stream);
     const ElemGrid g = elem_grid(c->n, ld);
-    k_pcg_init<<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, c->d_G[c->cur], c->d_dL, c->d_dB, cb,
-                                                c->d_W, c->d_D[c->cur], c->d_R, c->d_Z, cb + CB_RZ * ld);
+    k_pcg_init<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, b.G[c->cur], c->d_dL, c->d_dB, cb,
+                                                   b.W, b.D[c->cur], b.R, b.Z, cb + CB_RZ * ld);
 }
 
-void launch_pcg_update(ofks_ctx *c, int) {
+template <class T>
+void launch_judge(ofks_ctx *c, Blocks<T> &b) {
+    c->kernels += 1;
+    const int ld = c->ld;
+    double *cb = c->d_colA;
+    cudaMemsetAsync(cb + CB_RZ * ld, 0, sizeof(double) * 3 * ld, c->stream);   // RZ, RZN, PQ rows
+    const ElemGrid g = elem_grid(c->n, ld);
+    k_judge<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, b.G[c->cur], b.Q, b.D[c->cur],
+                                                cb + CB_RZ * ld, cb + CB_RZN * ld, cb + CB_PQ * ld);
+}
+
+template <class T>
+void launch_pcg_init_warm(ofks_ctx *c, Blocks<T> &b) {
+    c->kernels += 1;
+    const int ld = c->ld;
+    double *cb = c->d_colA;
+    cudaMemsetAsync(cb + CB_RZ * ld, 0, sizeof(double) * ld, c->stream);
+    const ElemGrid g = elem_grid(c->n, ld);
+    k_pcg_init_warm<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, b.G[c->cur], b.Q, c->d_dL, c->d_dB,
+                                                        cb, b.W, b.R, b.Z, cb + CB_RZ * ld);
+}
+
+template <class T>
+void launch_pcg_update(ofks_ctx *c, Blocks<T> &b) {
     c->kernels += 1;
     const int ld = c->ld;
     double *cb = c->d_colA;
     const ElemGrid g = elem_grid(c->n, ld);
-    k_pcg_update<<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, cb, c->d_W, c->d_P, c->d_Q,
-                                                  c->d_D[c->cur], c->d_R, c->d_Z, cb + CB_RZN * ld);
+    k_pcg_update<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, cb, b.W, b.P, b.Q, b.D[c->cur], b.R,
+                                                     b.Z, cb + CB_RZN * ld);
 }
 
-void launch_direction_select(ofks_ctx *c) {
+template <class T>
+void launch_direction_select(ofks_ctx *c, Blocks<T> &b) {
     c->kernels += 1;
     const ElemGrid g = elem_grid(c->n, c->ld);
-    k_select<<<g.blocks, 256, 0, c->stream>>>(c->n, c->ld, g.stride, c->d_colA, c->d_G[c->cur], c->d_D[c->cur]);
+    k_select<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->ld, g.stride, c->d_colA, b.G[c->cur], b.D[c->cur]);
 }
 
-void launch_bb_dots(ofks_ctx *c) {
-    c->kernels += 1;
+// BB sums over the applied directions D, or over the raw gradients G when raw is set; the
+// norms used by eta_0 are always those of X and D
+template <class T>
+void launch_bb_dots(ofks_ctx *c, Blocks<T> &b, bool raw) {
     ProfScope ps(c, PF_BB);
     const int cur = c->cur, prv = cur ^ 1;
     cudaMemsetAsync(c->d_sc + SC_BB, 0, sizeof(double) * 3, c->stream);
     cudaMemsetAsync(c->d_sc + SC_XNRM2, 0, sizeof(double) * 2, c->stream);
     const ElemGrid g = elem_grid(c->n, c->ld);
-    k_bb<<<g.blocks, 256, 0, c->stream>>>(c->n, c->ld, g.stride, c->d_X[cur], c->d_X[prv], c->d_D[cur], c->d_D[prv],
-                                          c->have_prev ? 1 : 0, c->d_sc);
+    T **DD = raw ? b.G : b.D;
+    k_bb<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->ld, g.stride, b.X[cur], b.X[prv], DD[cur], DD[prv],
+                                             c->have_prev ? 1 : 0, c->d_sc);
+    c->kernels += 1;
+    if (raw && !c->have_prev) {       // eta_0 needs ||D||: rerun the sums on D
+        cudaMemsetAsync(c->d_sc + SC_XNRM2, 0, sizeof(double) * 2, c->stream);
+        k_bb<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->ld, g.stride, b.X[cur], b.X[prv], b.D[cur], b.D[prv], 0,
+                                                 c->d_sc);
+        c->kernels += 1;
+    }
 }
 
-void launch_step_y(ofks_ctx *c, double *Y) {
+template <class T>
+void launch_step_y(ofks_ctx *c, Blocks<T> &b, T *Y) {
     c->kernels += 1;
     const ElemGrid g = elem_grid(c->n, c->ld);
-    k_step<<<g.blocks, 256, 0, c->stream>>>(c->n, c->ld, g.stride, c->d_X[c->cur], c->d_D[c->cur], c->d_sc, Y);
+    k_step<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->ld, g.stride, b.X[c->cur], b.D[c->cur], c->d_sc, Y);
 }
 
-void launch_scale_cols(ofks_ctx *c, double *Y, double *BY, const double *colsum) {
+template <class T>
+void launch_scale_cols(ofks_ctx *c, T *Y, T *BY, const double *colsum) {
     c->kernels += 1;
     const ElemGrid g = elem_grid(c->n, c->ld);
-    k_scale<<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, c->ld, g.stride, colsum, Y, BY);
+    k_scale<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, c->ld, g.stride, colsum, Y, BY);
 }
 
-void launch_block_times_small(ofks_ctx *c, const double *X, const double *M, double *Y) {
+template <class T>
+void launch_block_times_small(ofks_ctx *c, const T *X, const double *M, T *Y) {
     c->kernels += 1;
     const int ld = c->ld, KC = kc_of(ld);
-    const size_t sm = sizeof(double) * (32 * ld + KC * ld);
+    const size_t sm = sizeof(T) * (32 * ld + KC * ld);
     const unsigned grid = row_grid(32, c->n);
     MC_DISPATCH(mc_of(ld), {
-        cudaFuncSetAttribute(k_block_small<M_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_block_small<M_><<<grid, 256, sm, c->stream>>>(c->n, ld, X, M, Y, KC);
+        cudaFuncSetAttribute(k_block_small<T, M_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_block_small<T, M_><<<grid, 256, sm, c->stream>>>(c->n, ld, X, M, Y, KC);
     });
 }
 
-void launch_tri_solve_rows(ofks_ctx *c, const double *V, double *X, const double *Rinv) {
-    launch_block_times_small(c, V, Rinv, X);
+template <class S, class T>
+void launch_convert(ofks_ctx *c, const S *src, T *dst, int64_t count) {
+    c->kernels += 1;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 152LL * 16));
+    k_convert<S, T><<<g, 256, 0, c->stream>>>(count, src, dst);
 }
+
+#define INST(T)                                                                                      \
+    template void launch_gram2<T>(ofks_ctx *, const T *, const T *, const T *, double *, double *); \
+    template void launch_grad_update<T>(ofks_ctx *, Blocks<T> &);                                    \
+    template void launch_pcg_init<T>(ofks_ctx *, Blocks<T> &);                                       \
+    template void launch_pcg_update<T>(ofks_ctx *, Blocks<T> &);                                     \
+    template void launch_judge<T>(ofks_ctx *, Blocks<T> &);                                          \
+    template void launch_pcg_init_warm<T>(ofks_ctx *, Blocks<T> &);                                 \
+    template void launch_direction_select<T>(ofks_ctx *, Blocks<T> &);                               \
+    template void launch_bb_dots<T>(ofks_ctx *, Blocks<T> &, bool);                                  \
+    template void launch_step_y<T>(ofks_ctx *, Blocks<T> &, T *);                                    \
+    template void launch_scale_cols<T>(ofks_ctx *, T *, T *, const double *);                        \
+    template void launch_block_times_small<T>(ofks_ctx *, const T *, const double *, T *);
+INST(double)
+INST(float)
+#undef INST
+template void launch_convert<double, float>(ofks_ctx *, const double *, float *, int64_t);
+template void launch_convert<float, double>(ofks_ctx *, const float *, double *, int64_t);

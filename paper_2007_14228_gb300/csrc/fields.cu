@@ -47,9 +47,9 @@ __device__ __forceinline__ double lda(double rho, double &vxc) {
 // over the group's lanes (float64 warp instructions cost the same with one active lane):
 // lane k writes rho_k (k < 4), adds the Poisson load 4 pi w sum_q N_k(x_q) rho_q of local
 // node k (k < 10) and accumulates multipole moment k (k < 10) over all its tetrahedra.
-template <int G>
+template <class E, int G>
 __global__ void __launch_bounds__(256) k_density(int64_t T, int p, int ld, double occ,
-                                                 const double *__restrict__ X,
+                                                 const E *__restrict__ X,
                                                  const int *__restrict__ tetf,
                                                  const int *__restrict__ tetn,
                                                  const double *__restrict__ wq,
@@ -68,28 +68,31 @@ __global__ void __launch_bounds__(256) k_density(int64_t T, int p, int ld, doubl
     for (int64_t t0 = warp * TPW; t0 < T; t0 += nwarp * TPW) {
         const int64_t t = t0 + grp;
         const bool ok = t < T;
-        double s[4] = {0, 0, 0, 0};
+        E se[4] = {E(0), E(0), E(0), E(0)};
         if (ok) {
             int f[10];
 #pragma unroll
             for (int a = 0; a < 10; ++a) f[a] = tetf[t * 10 + a];
             for (int l = lane; l < p; l += G) {
-                double x[10];
+                E x[10];
 #pragma unroll
-                for (int a = 0; a < 10; ++a) x[a] = f[a] >= 0 ? X[(int64_t)f[a] * ld + l] : 0.0;
+                for (int a = 0; a < 10; ++a) x[a] = f[a] >= 0 ? X[(int64_t)f[a] * ld + l] : E(0);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    double psi = 0.0;
+                    E psi = E(0);
 #pragma unroll
-                    for (int a = 0; a < 10; ++a) psi = fma(p2N(q, a), x[a], psi);
-                    s[q] = fma(psi, psi, s[q]);
+                    for (int a = 0; a < 10; ++a) psi = fma((E)p2N(q, a), x[a], psi);
+                    se[q] = fma(psi, psi, se[q]);
                 }
             }
         }
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o, G);
+            for (int q = 0; q < 4; ++q) se[q] += __shfl_xor_sync(0xffffffffu, se[q], o, G);
+        double s[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s[q] = (double)se[q];
         if (!ok) continue;
         for (int k = lane; k < 4; k += G) rho[t * 4 + k] = occ * s[k];
         if (!do_hartree) continue;
@@ -295,14 +298,16 @@ __global__ void k_cg_dir(int64_t N, const double *__restrict__ z, double *pv, co
     if (i < N) pv[i] = z[i] + beta * pv[i];
 }
 
-__global__ void k_half_copy(int64_t n, const double *__restrict__ a, double *b) {
+template <class E>
+__global__ void k_half_copy(int64_t n, const E *__restrict__ a, E *b) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) b[i] = 0.5 * a[i];
+    if (i < n) b[i] = E(0.5) * a[i];
 }
 
 // Per tetrahedron: V_H(x_q) from the nodal U, LDA at rho_q, V_q = V_ext + V_H + V_xc,
 // the double-counting sum w (V_H/2 + V_xc - eps_xc) rho, and the local potential matrix
 // sum_q w V_q N_a N_b added to the Hamiltonian values (which hold L/2 on entry).
+template <class E>
 __global__ void __launch_bounds__(128) k_potential(int64_t T, const int *__restrict__ tetn,
                                                    const int *__restrict__ emap,
                                                    const double *__restrict__ wq,
@@ -310,7 +315,7 @@ __global__ void __launch_bounds__(128) k_potential(int64_t T, const int *__restr
                                                    const double *__restrict__ rho,
                                                    const double *__restrict__ U, int do_h, int do_xc,
                                                    double *vh, double *vxc, double *exc,
-                                                   double *valH, double *edc) {
+                                                   E *valH, double *edc) {
     __shared__ double sh[4];
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double e = 0.0;
@@ -335,7 +340,7 @@ __global__ void __launch_bounds__(128) k_potential(int64_t T, const int *__restr
                 double m = 0.0;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) m += V[q] * p2N(q, a) * p2N(q, b);
-                atomicAdd(valH + pos, m);
+                atomicAdd(valH + pos, (E)m);
             }
     }
     e = block_sum(e, sh);
@@ -344,7 +349,8 @@ __global__ void __launch_bounds__(128) k_potential(int64_t T, const int *__restr
 
 }  // namespace
 
-int launch_density(ofks_ctx *c, const double *X) {
+template <class E>
+int launch_density(ofks_ctx *c, const E *X) {
     ProfScope ps(c, PF_DENSITY);
     const int64_t T = c->n_tets;
     const int do_h = c->prm.hartree ? 1 : 0;
@@ -360,7 +366,7 @@ int launch_density(ofks_ctx *c, const double *X) {
     const int B = 256;
     const int64_t warps = (T + 32 / G - 1) / (32 / G);
     unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((warps * 32 + B - 1) / B, 152LL * 16));
-#define DENS(g) k_density<g><<<grid, B, 0, c->stream>>>(T, c->p, c->ld, c->prm.occ, X, c->d_tetf, \
+#define DENS(g) k_density<E, g><<<grid, B, 0, c->stream>>>(T, c->p, c->ld, c->prm.occ, X, c->d_tetf, \
         c->d_tetn, c->d_wq, c->d_yq, c->d_rho, c->d_rhs, c->d_sc + SC_MOM, do_h)
     switch (G) {
         case 1: DENS(1); break;
@@ -395,7 +401,8 @@ int run_hartree(ofks_ctx *c) {
         k_cg_rz<<<gN, 256, 0, c->stream>>>(N, c->d_cr, c->d_cz, c->d_cp, sc, 0, 1);
         c->kernels += 1;
     }
-    const double tol2 = c->prm.poisson_tol * c->prm.poisson_tol;
+    const double ptol = c->phase == 32 ? std::max(c->prm.poisson_tol, c->prm.poisson_tol_mixed) : c->prm.poisson_tol;
+    const double tol2 = ptol * ptol;
     const int chunk = amg ? 4 : 32;
     int it = 0;
     double h[8];
@@ -436,15 +443,20 @@ int run_hartree(ofks_ctx *c) {
     return ofks_cuda_check(c, cudaGetLastError(), "Hartree CG");
 }
 
-int launch_potential_refresh(ofks_ctx *c) {
+template <class E>
+int launch_potential_refresh(ofks_ctx *c, E *valH, const E *valL) {
     ProfScope ps(c, PF_POTENTIAL);
     const int64_t T = c->n_tets;
-    k_half_copy<<<(unsigned)((c->sell_len + 255) / 256), 256, 0, c->stream>>>(c->sell_len, c->d_valL,
-                                                                                 c->d_valH);
+    k_half_copy<E><<<(unsigned)((c->sell_len + 255) / 256), 256, 0, c->stream>>>(c->sell_len, valL, valH);
     cudaMemsetAsync(c->d_sc + SC_EDC, 0, sizeof(double), c->stream);
-    k_potential<<<(unsigned)((T + 127) / 128), 128, 0, c->stream>>>(
+    k_potential<E><<<(unsigned)((T + 127) / 128), 128, 0, c->stream>>>(
         T, c->d_tetn, c->d_emap, c->d_wq, c->d_vext, c->d_rho, c->d_U, c->prm.hartree ? 1 : 0,
-        c->prm.xc ? 1 : 0, c->d_vh, c->d_vxc, c->d_exc, c->d_valH, c->d_sc + SC_EDC);
+        c->prm.xc ? 1 : 0, c->d_vh, c->d_vxc, c->d_exc, valH, c->d_sc + SC_EDC);
     c->kernels += 2;
     return ofks_cuda_check(c, cudaGetLastError(), "potential kernel");
 }
+
+template int launch_density<double>(ofks_ctx *, const double *);
+template int launch_density<float>(ofks_ctx *, const float *);
+template int launch_potential_refresh<double>(ofks_ctx *, double *, const double *);
+template int launch_potential_refresh<float>(ofks_ctx *, float *, const float *);

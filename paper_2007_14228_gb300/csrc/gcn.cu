@@ -1,0 +1,534 @@
+// Learned preconditioner: a 3-layer graph network on the free-DoF graph of the P2 mesh that maps a
+// gradient column G_c to an approximation of T_c^{-1} G_c (T_c = L/2 - Lambda_cc B, paper
+// Eq. precondition-T), with its forward, backward and Adam kernels.
+//
+// Per column c (shift lam_c <= 0):  diag = dL/2 - lam_c dB,  z = g / diag,  s_c = rms(z),
+//   features f = [z / s_c, log diag - mean log diag, -lam_c dB / diag, 1]
+//   Z_l = H_l W_l + (A H_l) U_l + b_l,  H_{l+1} = relu(Z_l) (hidden) / Z_l (last)
+//   D = s_c (f0 + H_3)
+// A is the mean over the closed neighbourhood (1/|N(i)| on the pattern of L).  Activations are
+// rows (i, c) of an (n p) x F float32 matrix, so the aggregation over nodes is the SELL SpMM
+// with leading dimension p F.  Weights are float32 masters rounded to bfloat16 where used;
+// products accumulate in float32, reductions over rows in float64.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace {
+
+constexpr int F0 = 4;
+
+__device__ __forceinline__ float bf(float w) { return __bfloat162float(__float2bfloat16(w)); }
+
+// column sums of z^2 and of log(diag) (float64)
+__global__ void __launch_bounds__(256) k_feat_stats(int64_t n, int p, const float *__restrict__ G,
+                                                    const double *__restrict__ dL, const double *__restrict__ dB,
+                                                    const double *__restrict__ shift, double *stats) {
+    // stats[c] = sum z^2, stats[p + c] = sum log diag
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t S = (int64_t)gridDim.x * blockDim.x / p * p;
+    const int c = (int)(gid % p);
+    double a = 0.0, b = 0.0;
+    if (gid < S) {
+        const float lam = (float)fmin(shift[c], 0.0);
+        for (int64_t e = gid; e < n * p; e += S) {
+            const int64_t i = e / p;
+            const float d = 0.5f * (float)dL[i] - lam * (float)dB[i];
+            const float z = G[e] / d;
+            a += (double)(z * z);
+            b += (double)logf(d);
+        }
+        atomicAdd(stats + c, a);
+        atomicAdd(stats + p + c, b);
+    }
+}
+
+// features (rows (i, c)), the column scales s_c and the Jacobi diagonals diag (n x p)
+__global__ void __launch_bounds__(256) k_features(int64_t n, int p, const float *__restrict__ G,
+                                                  const double *__restrict__ dL, const double *__restrict__ dB,
+                                                  const double *__restrict__ shift, const double *__restrict__ stats,
+                                                  float *F, float *scale, float *diagv) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * p) return;
+    const int64_t i = e / p;
+    const int c = (int)(e - i * p);
+    const float lam = (float)fmin(shift[c], 0.0);
+    const float d = 0.5f * (float)dL[i] - lam * (float)dB[i];
+    const float s = (float)sqrt(stats[c] / (double)n);
+    const float ml = (float)(stats[p + c] / (double)n);
+    float *f = F + e * F0;
+    f[0] = s > 0.f ? G[e] / d / s : 0.f;
+    f[1] = logf(d) - ml;
+    f[2] = -lam * (float)dB[i] / d;
+    f[3] = 1.f;
+    diagv[e] = d;
+    if (i == 0) scale[c] = s;
+}
+
+// Z = H W + AH U + b (rows x FO), H/AH rows x FI; out = relu(Z) if relu else Z.  A block owns 64
+// rows; thread t owns rows 4 (t / (FO/ 4)) ... and 4 consecutive outputs.
+template <int FI, int FO>
+__global__ void __launch_bounds__(256) k_dense(int64_t rows, const float *__restrict__ H, const float *__restrict__ AH,
+                                               const float *__restrict__ W, const float *__restrict__ U,
+                                               const float *__restrict__ b, int relu, float *Z, float *out) {
+    constexpr int RB = FI >= 64 ? 16 : 64;             // rows per tile (static shared memory <= 48 KiB)
+    constexpr int OC = FO >= 4 ? 4 : 1;                 // outputs per thread
+    constexpr int TPR = FO / OC;                        // threads per row group
+    constexpr int RPT = RB * TPR / 256 > 0 ? RB * TPR / 256 : 1;   // rows per thread
+    __shared__ float sW[FI * FO], sU[FI * FO], sb[FO];
+    __shared__ float sH[RB * FI], sA[RB * FI];
+    for (int k = threadIdx.x; k < FI * FO; k += 256) { sW[k] = bf(W[k]); sU[k] = bf(U[k]); }
+    for (int k = threadIdx.x; k < FO; k += 256) sb[k] = bf(b[k]);
+    for (int64_t r0 = blockIdx.x * (int64_t)RB; r0 < rows; r0 += (int64_t)RB * gridDim.x) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < RB * FI; k += 256) {
+            const int64_t r = r0 + k / FI;
+            sH[k] = r < rows ? H[r0 * FI + k] : 0.f;
+            sA[k] = r < rows ? AH[r0 * FI + k] : 0.f;
+        }
+        __syncthreads();
+        const int og = threadIdx.x % TPR, rg = threadIdx.x / TPR;
+        if (rg * RPT < RB) {
+            float acc[RPT][OC];
+#pragma unroll
+            for (int a = 0; a < RPT; ++a)
+#pragma unroll
+                for (int o = 0; o < OC; ++o) acc[a][o] = sb[og * OC + o];
+            for (int k = 0; k < FI; ++k) {
+                float w[OC], u[OC];
+#pragma unroll
+                for (int o = 0; o < OC; ++o) { w[o] = sW[k * FO + og * OC + o]; u[o] = sU[k * FO + og * OC + o]; }
+#pragma unroll
+                for (int a = 0; a < RPT; ++a) {
+                    const float h = sH[(rg * RPT + a) * FI + k], ah = sA[(rg * RPT + a) * FI + k];
+#pragma unroll
+                    for (int o = 0; o < OC; ++o) acc[a][o] = fmaf(h, w[o], fmaf(ah, u[o], acc[a][o]));
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < RPT; ++a) {
+                const int64_t r = r0 + rg * RPT + a;
+                if (r >= rows) continue;
+#pragma unroll
+                for (int o = 0; o < OC; ++o) {
+                    const float z = acc[a][o];
+                    if (Z) Z[r * FO + og * OC + o] = z;
+                    out[r * FO + og * OC + o] = relu ? fmaxf(z, 0.f) : z;
+                }
+            }
+        }
+    }
+}
+
+// last layer (FO = 1): y = H w + AH u + b, one warp per 32 rows, FI features per row
+__global__ void __launch_bounds__(256) k_dense_out(int64_t rows, int FI, const float *__restrict__ H,
+                                                   const float *__restrict__ AH, const float *__restrict__ W,
+                                                   const float *__restrict__ U, const float *__restrict__ b,
+                                                   float *y) {
+    __shared__ float sw[256], su[256];
+    for (int k = threadIdx.x; k < FI; k += blockDim.x) { sw[k] = bf(W[k]); su[k] = bf(U[k]); }
+    __syncthreads();
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    float acc = bf(b[0]);
+    for (int k = 0; k < FI; ++k) acc = fmaf(H[r * FI + k], sw[k], fmaf(AH[r * FI + k], su[k], acc));
+    y[r] = acc;
+}
+
+// D = s_c (f0 + y)
+__global__ void k_output(int64_t n, int p, const float *__restrict__ F, const float *__restrict__ y,
+                         const float *__restrict__ scale, float *D) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * p) return;
+    D[e] = scale[e % p] * (F[e * F0] + y[e]);
+}
+
+// loss pieces: num[c] = sum (D - D*)^2, den[c] = sum D*^2 (float64)
+__global__ void __launch_bounds__(256) k_loss(int64_t n, int p, const float *__restrict__ D, const float *__restrict__ Ds,
+                                              double *acc) {
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t S = (int64_t)gridDim.x * blockDim.x / p * p;
+    const int c = (int)(gid % p);
+    if (gid >= S) return;
+    double a = 0.0, b = 0.0;
+    for (int64_t e = gid; e < n * p; e += S) {
+        const double r = (double)D[e] - (double)Ds[e];
+        a += r * r;
+        b += (double)Ds[e] * (double)Ds[e];
+    }
+    atomicAdd(acc + c, a);
+    atomicAdd(acc + p + c, b);
+}
+
+// dL/dy = 2 s_c (D - D*) / den_c / p
+__global__ void k_dy(int64_t n, int p, const float *__restrict__ D, const float *__restrict__ Ds,
+                     const float *__restrict__ scale, const double *__restrict__ acc, float *dy) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * p) return;
+    const int c = (int)(e % p);
+    dy[e] = (float)(2.0 * (double)scale[c] * ((double)D[e] - (double)Ds[e]) / acc[p + c] / p);
+}
+
+// dZ = dH * (Z > 0) in place (hidden layers)
+__global__ void k_relu_back(int64_t m, const float *__restrict__ Z, float *dH) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < m && !(Z[e] > 0.f)) dH[e] = 0.f;
+}
+
+// gW += H^T dZ (FI x FO), gU += AH^T dZ, gb += sum dZ: row chunks per block, float64 atomics
+template <int FI, int FO>
+__global__ void __launch_bounds__(256) k_wgrad(int64_t rows, const float *__restrict__ H, const float *__restrict__ AH,
+                                               const float *__restrict__ dZ, double *gW, double *gU, double *gb) {
+    constexpr int NW = (FI * FO + 255) / 256;
+    constexpr int RB = 32;
+    __shared__ float sH[RB * FI], sA[RB * FI], sZ[RB * FO];
+    float aW[NW], aU[NW], aB = 0.f;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) { aW[q] = 0.f; aU[q] = 0.f; }
+    for (int64_t r0 = blockIdx.x * (int64_t)RB; r0 < rows; r0 += (int64_t)RB * gridDim.x) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < RB * FI; k += 256) {
+            const int64_t r = r0 + k / FI;
+            sH[k] = r < rows ? H[r0 * FI + k] : 0.f;
+            sA[k] = r < rows ? AH[r0 * FI + k] : 0.f;
+        }
+        for (int k = threadIdx.x; k < RB * FO; k += 256) {
+            const int64_t r = r0 + k / FO;
+            sZ[k] = r < rows ? dZ[r0 * FO + k] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < NW; ++q) {
+            const int o = threadIdx.x + 256 * q;
+            if (o >= FI * FO) continue;
+            const int fi = o / FO, fo = o - fi * FO;
+            float w = aW[q], u = aU[q];
+            for (int r = 0; r < RB; ++r) {
+                const float z = sZ[r * FO + fo];
+                w = fmaf(sH[r * FI + fi], z, w);
+                u = fmaf(sA[r * FI + fi], z, u);
+            }
+            aW[q] = w; aU[q] = u;
+        }
+        if (threadIdx.x < FO)
+            for (int r = 0; r < RB; ++r) aB += sZ[r * FO + threadIdx.x];
+    }
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        const int o = threadIdx.x + 256 * q;
+        if (o >= FI * FO) continue;
+        atomicAdd(gW + o, (double)aW[q]);
+        atomicAdd(gU + o, (double)aU[q]);
+    }
+    if (threadIdx.x < FO) atomicAdd(gb + threadIdx.x, (double)aB);
+}
+
+// dH = dZ W^T (into out), dAH = dZ U^T (into out2): rows x FI from rows x FO
+template <int FI, int FO>
+__global__ void __launch_bounds__(256) k_dinput(int64_t rows, const float *__restrict__ dZ, const float *__restrict__ W,
+                                                const float *__restrict__ U, float *dH, float *dAH) {
+    __shared__ float sW[FI * FO], sU[FI * FO];
+    for (int k = threadIdx.x; k < FI * FO; k += 256) { sW[k] = bf(W[k]); sU[k] = bf(U[k]); }
+    __syncthreads();
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= rows * FI) return;
+    const int64_t r = e / FI;
+    const int fi = (int)(e - r * FI);
+    float a = 0.f, b = 0.f;
+    for (int o = 0; o < FO; ++o) {
+        const float z = dZ[r * FO + o];
+        a = fmaf(z, sW[fi * FO + o], a);
+        b = fmaf(z, sU[fi * FO + o], b);
+    }
+    dH[e] = a;
+    dAH[e] = b;
+}
+
+__global__ void k_add(int64_t m, const float *__restrict__ a, float *b) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < m) b[e] += a[e];
+}
+
+// Adam on the flat parameter vector
+__global__ void k_adam(int64_t m, const double *__restrict__ g, float *w, float *mo, float *ve, float lr, float b1,
+                       float b2, float c1, float c2, float eps) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const float gi = (float)g[i];
+    const float mi = b1 * mo[i] + (1.f - b1) * gi;
+    const float vi = b2 * ve[i] + (1.f - b2) * gi * gi;
+    mo[i] = mi; ve[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// n x ld block (element type E) <-> n x p compact float
+template <class E>
+__global__ void k_pack(int64_t n, int p, int ld, const E *__restrict__ src, float *dst) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * p) return;
+    const int64_t i = e / p;
+    dst[e] = (float)src[i * ld + (e - i * p)];
+}
+template <class E>
+__global__ void k_unpack(int64_t n, int p, int ld, const float *__restrict__ src, E *dst) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * p) return;
+    const int64_t i = e / p;
+    dst[i * ld + (e - i * p)] = (E)src[e];
+}
+
+inline unsigned gr(int64_t m) { return (unsigned)std::max<int64_t>(1, (m + 255) / 256); }
+inline unsigned gr_stride(int64_t m) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 152 * 8)); }
+
+}  // namespace
+
+// layer dimensions for width H
+static void dims(int H, int d[4]) { d[0] = F0; d[1] = H; d[2] = H; d[3] = 1; }
+
+int64_t gcn_param_count(int H) {
+    int d[4];
+    dims(H, d);
+    int64_t m = 0;
+    for (int l = 0; l < 3; ++l) m += 2LL * d[l] * d[l + 1] + d[l + 1];
+    return m;
+}
+
+// offsets of W_l, U_l, b_l in the flat vector
+static void offsets(int H, int64_t off[3][3]) {
+    int d[4];
+    dims(H, d);
+    int64_t o = 0;
+    for (int l = 0; l < 3; ++l) {
+        off[l][0] = o; o += (int64_t)d[l] * d[l + 1];
+        off[l][1] = o; o += (int64_t)d[l] * d[l + 1];
+        off[l][2] = o; o += d[l + 1];
+    }
+}
+
+void gcn_free(ofks_ctx *c) {
+    GcnState &g = c->gcn;
+    for (float *q : {g.w, g.m, g.v, g.valA, g.valAT, g.F, g.H1, g.H2, g.Z1, g.Z2, g.AH, g.y, g.scale, g.diag, g.Dn,
+                     g.Ds, g.dA, g.dB2, g.G32})
+        if (q) cudaFree(q);
+    for (double *q : {g.grad, g.stats, g.lacc}) if (q) cudaFree(q);
+    c->gcn = GcnState{};
+}
+
+// aggregation values on the SELL pattern: A_ij = 1/|N(i)|, (A^T)_ij = 1/|N(j)|
+__global__ void k_agg_values(int n_slices, const int *__restrict__ slice_ptr, const int *__restrict__ slice_w,
+                             const int *__restrict__ cols, const int *__restrict__ perm, const double *__restrict__ valL,
+                             const int *__restrict__ deg, float *valA, float *valAT) {
+    const int s = blockIdx.x, lane = threadIdx.x;
+    if (s >= n_slices || lane >= SELL_C) return;
+    const int r = perm[s * SELL_C + lane];
+    for (int j = 0; j < slice_w[s]; ++j) {
+        const int e = slice_ptr[s] + j * SELL_C + lane;
+        const bool real = r >= 0 && j < deg[r];
+        valA[e] = real ? 1.f / (float)deg[r] : 0.f;
+        valAT[e] = real ? 1.f / (float)deg[cols[e]] : 0.f;
+    }
+}
+
+int gcn_setup(ofks_ctx *c, int H, uint64_t seed, const std::vector<int> &deg) {
+    gcn_free(c);
+    GcnState &g = c->gcn;
+    g.H = H;
+    const int64_t m = gcn_param_count(H);
+    std::vector<float> w(m, 0.f);
+    int64_t off[3][3];
+    offsets(H, off);
+    int d[4];
+    dims(H, d);
+    uint64_t st = seed * 6364136223846793005ULL + 1442695040888963407ULL;
+    auto gauss = [&]() {   // Box-Muller on a 64-bit LCG (weights only need to be reproducible)
+        st = st * 6364136223846793005ULL + 1442695040888963407ULL;
+        const double u1 = ((st >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        st = st * 6364136223846793005ULL + 1442695040888963407ULL;
+        const double u2 = ((st >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+    };
+    for (int l = 0; l < 2; ++l) {
+        const double sc = std::sqrt(2.0 / (2.0 * d[l]));
+        for (int64_t k = 0; k < (int64_t)d[l] * d[l + 1]; ++k) {
+            w[off[l][0] + k] = (float)(sc * gauss());
+            w[off[l][1] + k] = (float)(sc * gauss());
+        }
+    }
+    auto alloc = [&](float **q, int64_t cnt) { return cudaMalloc((void **)q, sizeof(float) * std::max<int64_t>(cnt, 1)); };
+    if (alloc(&g.w, m) || alloc(&g.m, m) || alloc(&g.v, m) ||
+        cudaMalloc((void **)&g.grad, sizeof(double) * m) != cudaSuccess ||
+        alloc(&g.valA, c->sell_len) || alloc(&g.valAT, c->sell_len))
+        return ofks_fail(c, OFKS_ENOMEM, "learned preconditioner: parameters");
+    cudaMemcpy(g.w, w.data(), sizeof(float) * m, cudaMemcpyHostToDevice);
+    cudaMemset(g.m, 0, sizeof(float) * m);
+    cudaMemset(g.v, 0, sizeof(float) * m);
+    int *d_deg = nullptr;
+    if (cudaMalloc((void **)&d_deg, sizeof(int) * deg.size()) != cudaSuccess)
+        return ofks_fail(c, OFKS_ENOMEM, "learned preconditioner: degrees");
+    cudaMemcpy(d_deg, deg.data(), sizeof(int) * deg.size(), cudaMemcpyHostToDevice);
+    k_agg_values<<<c->n_slices, SELL_C, 0, c->stream>>>(c->n_slices, c->d_slice_ptr, c->d_slice_w, c->d_cols, c->d_perm,
+                                                        c->d_valL, d_deg, g.valA, g.valAT);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_deg);
+    g.t = 0;
+    return ofks_cuda_check(c, e, "learned preconditioner setup");
+}
+
+// activations for the current p
+static int gcn_buffers(ofks_ctx *c) {
+    GcnState &g = c->gcn;
+    const int64_t rows = c->n * (int64_t)c->p;
+    if (g.rows == rows && g.F) return OFKS_OK;
+    for (float **q : {&g.F, &g.H1, &g.H2, &g.Z1, &g.Z2, &g.AH, &g.y, &g.scale, &g.diag, &g.Dn, &g.Ds, &g.dA, &g.dB2, &g.G32}) {
+        if (*q) cudaFree(*q);
+        *q = nullptr;
+    }
+    for (double **q : {&g.stats, &g.lacc}) { if (*q) cudaFree(*q); *q = nullptr; }
+    const int H = g.H;
+    auto alloc = [&](float **q, int64_t cnt) { return cudaMalloc((void **)q, sizeof(float) * std::max<int64_t>(cnt, 1)); };
+    if (alloc(&g.F, rows * F0) || alloc(&g.H1, rows * H) || alloc(&g.H2, rows * H) || alloc(&g.Z1, rows * H) ||
+        alloc(&g.Z2, rows * H) || alloc(&g.AH, rows * H) || alloc(&g.y, rows) || alloc(&g.scale, c->p) ||
+        alloc(&g.diag, rows) || alloc(&g.Dn, rows) || alloc(&g.Ds, rows) || alloc(&g.dA, rows * H) ||
+        alloc(&g.dB2, rows * H) || alloc(&g.G32, rows) ||
+        cudaMalloc((void **)&g.stats, sizeof(double) * 2 * c->p) != cudaSuccess ||
+        cudaMalloc((void **)&g.lacc, sizeof(double) * 2 * c->p) != cudaSuccess)
+        return ofks_fail(c, OFKS_ENOMEM, "learned preconditioner: activations for %lld rows", (long long)rows);
+    g.rows = rows;
+    return OFKS_OK;
+}
+
+int gcn_forward_prepare(ofks_ctx *c) { return gcn_buffers(c); }
+
+// aggregation over nodes of an (n p) x F activation: out = A in (or A^T in)
+static void aggregate(ofks_ctx *c, const float *val, const float *in, float *out, int F) {
+    launch_sell_spmm_ld<float>(c, val, in, out, c->p * F);
+}
+
+#define DISPATCH_DENSE(FI_, FO_, ...)                                                              \
+    do {                                                                                         \
+        if (FI_ == 4 && FO_ == 64) { constexpr int A_ = 4, B_ = 64; __VA_ARGS__; }               \
+        else if (FI_ == 64 && FO_ == 64) { constexpr int A_ = 64, B_ = 64; __VA_ARGS__; }        \
+        else if (FI_ == 4 && FO_ == 32) { constexpr int A_ = 4, B_ = 32; __VA_ARGS__; }          \
+        else if (FI_ == 32 && FO_ == 32) { constexpr int A_ = 32, B_ = 32; __VA_ARGS__; }        \
+        else if (FI_ == 4 && FO_ == 16) { constexpr int A_ = 4, B_ = 16; __VA_ARGS__; }          \
+        else if (FI_ == 16 && FO_ == 16) { constexpr int A_ = 16, B_ = 16; __VA_ARGS__; }        \
+        else if (FI_ == 4 && FO_ == 8) { constexpr int A_ = 4, B_ = 8; __VA_ARGS__; }            \
+        else { constexpr int A_ = 8, B_ = 8; __VA_ARGS__; }                                      \
+    } while (0)
+
+// forward on G32 (n x p float32, column-major-by-row layout (i, c)) -> g.Dn
+int gcn_forward(ofks_ctx *c, const double *shift, bool keep) {
+    GcnState &g = c->gcn;
+    int rc = gcn_buffers(c);
+    if (rc) return rc;
+    const int64_t n = c->n, p = c->p, rows = n * p;
+    const int H = g.H;
+    int64_t off[3][3];
+    offsets(H, off);
+    ProfScope ps(c, PF_GCN);
+    cudaMemsetAsync(g.stats, 0, sizeof(double) * 2 * p, c->stream);
+    k_feat_stats<<<gr_stride(rows), 256, 0, c->stream>>>(n, (int)p, g.G32, c->d_dL, c->d_dB, shift, g.stats);
+    k_features<<<gr(rows), 256, 0, c->stream>>>(n, (int)p, g.G32, c->d_dL, c->d_dB, shift, g.stats, g.F, g.scale, g.diag);
+    // layer 0: F (4) -> H1
+    aggregate(c, g.valA, g.F, g.AH, F0);
+    const unsigned gd = (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 15) / 16, 152LL * 8));
+    DISPATCH_DENSE(F0, H, k_dense<A_, B_><<<gd, 256, 0, c->stream>>>(rows, g.F, g.AH, g.w + off[0][0], g.w + off[0][1],
+                                                                      g.w + off[0][2], 1, nullptr, g.H1));
+    // layer 1: H1 -> H2 (tensor cores for width 64 at inference; training keeps float32 activations)
+    aggregate(c, g.valA, g.H1, g.AH, H);
+    if (H == 64 && !keep && c->prm.learned_tc)
+        launch_dense_tc(c, rows, g.H1, g.AH, g.w + off[1][0], g.w + off[1][1], g.w + off[1][2], g.H2);
+    else
+        DISPATCH_DENSE(H, H, k_dense<A_, B_><<<gd, 256, 0, c->stream>>>(rows, g.H1, g.AH, g.w + off[1][0],
+                                                                         g.w + off[1][1], g.w + off[1][2], 1, nullptr, g.H2));
+    // layer 2: H2 -> y (keep A H2 in dA for the backward pass)
+    float *AH2 = keep ? g.dA : g.AH;
+    aggregate(c, g.valA, g.H2, AH2, H);
+    k_dense_out<<<gr(rows), 256, 0, c->stream>>>(rows, H, g.H2, AH2, g.w + off[2][0], g.w + off[2][1], g.w + off[2][2], g.y);
+    k_output<<<gr(rows), 256, 0, c->stream>>>(n, (int)p, g.F, g.y, g.scale, g.Dn);
+    c->kernels += 9;
+    return ofks_cuda_check(c, cudaGetLastError(), "learned preconditioner forward");
+}
+
+// loss of g.Dn against g.Ds and the parameter gradients in g.grad (float64)
+int gcn_backward(ofks_ctx *c, double *loss) {
+    GcnState &g = c->gcn;
+    const int64_t n = c->n, p = c->p, rows = n * p;
+    const int H = g.H;
+    int64_t off[3][3];
+    offsets(H, off);
+    const int64_t m = gcn_param_count(H);
+    cudaMemsetAsync(g.grad, 0, sizeof(double) * m, c->stream);
+    cudaMemsetAsync(g.lacc, 0, sizeof(double) * 2 * p, c->stream);
+    k_loss<<<gr_stride(rows), 256, 0, c->stream>>>(n, (int)p, g.Dn, g.Ds, g.lacc);
+    k_dy<<<gr(rows), 256, 0, c->stream>>>(n, (int)p, g.Dn, g.Ds, g.scale, g.lacc, g.y);   // g.y <- dL/dy
+    const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 31) / 32, 152LL * 4));
+    // layer 2 (H -> 1): dZ = dy; grads; dH2 = dy w^T, dAH2 = dy u^T
+    if (H == 64) k_wgrad<64, 1><<<gw, 256, 0, c->stream>>>(rows, g.H2, g.dA, g.y, g.grad + off[2][0], g.grad + off[2][1], g.grad + off[2][2]);
+    else if (H == 32) k_wgrad<32, 1><<<gw, 256, 0, c->stream>>>(rows, g.H2, g.dA, g.y, g.grad + off[2][0], g.grad + off[2][1], g.grad + off[2][2]);
+    else if (H == 16) k_wgrad<16, 1><<<gw, 256, 0, c->stream>>>(rows, g.H2, g.dA, g.y, g.grad + off[2][0], g.grad + off[2][1], g.grad + off[2][2]);
+    else k_wgrad<8, 1><<<gw, 256, 0, c->stream>>>(rows, g.H2, g.dA, g.y, g.grad + off[2][0], g.grad + off[2][1], g.grad + off[2][2]);
+    const unsigned gi = gr(rows * H);
+    if (H == 64) k_dinput<64, 1><<<gi, 256, 0, c->stream>>>(rows, g.y, g.w + off[2][0], g.w + off[2][1], g.Z2 /*dH2*/, g.dB2);
+    else if (H == 32) k_dinput<32, 1><<<gi, 256, 0, c->stream>>>(rows, g.y, g.w + off[2][0], g.w + off[2][1], g.Z2, g.dB2);
+    else if (H == 16) k_dinput<16, 1><<<gi, 256, 0, c->stream>>>(rows, g.y, g.w + off[2][0], g.w + off[2][1], g.Z2, g.dB2);
+    else k_dinput<8, 1><<<gi, 256, 0, c->stream>>>(rows, g.y, g.w + off[2][0], g.w + off[2][1], g.Z2, g.dB2);
+    // dH2 += A^T dAH2
+    aggregate(c, g.valAT, g.dB2, g.AH, H);
+    k_add<<<gr(rows * H), 256, 0, c->stream>>>(rows * H, g.AH, g.Z2);
+    // layer 1 (H -> H): dZ1' = dH2 * (Z of layer 1 > 0); Z of layer 1 is g.H2's pre-activation: recompute mask from H2
+    k_relu_back<<<gr(rows * H), 256, 0, c->stream>>>(rows * H, g.H2, g.Z2);      // H2 = relu(Z): H2 > 0 <=> Z > 0
+    aggregate(c, g.valA, g.H1, g.AH, H);                                         // A H1 again
+    DISPATCH_DENSE(H, H, k_wgrad<A_, B_><<<gw, 256, 0, c->stream>>>(rows, g.H1, g.AH, g.Z2, g.grad + off[1][0],
+                                                                     g.grad + off[1][1], g.grad + off[1][2]));
+    DISPATCH_DENSE(H, H, k_dinput<A_, B_><<<gr(rows * H), 256, 0, c->stream>>>(rows, g.Z2, g.w + off[1][0], g.w + off[1][1],
+                                                                                g.dA, g.dB2));
+    aggregate(c, g.valAT, g.dB2, g.AH, H);
+    k_add<<<gr(rows * H), 256, 0, c->stream>>>(rows * H, g.AH, g.dA);             // dH1
+    // layer 0 (4 -> H)
+    k_relu_back<<<gr(rows * H), 256, 0, c->stream>>>(rows * H, g.H1, g.dA);
+    aggregate(c, g.valA, g.F, g.AH, F0);
+    DISPATCH_DENSE(F0, H, k_wgrad<A_, B_><<<gw, 256, 0, c->stream>>>(rows, g.F, g.AH, g.dA, g.grad + off[0][0],
+                                                                      g.grad + off[0][1], g.grad + off[0][2]));
+    c->kernels += 18;
+    double h[2 * 256];
+    const int pp = (int)std::min<int64_t>(p, 256);
+    cudaError_t e = cudaMemcpyAsync(h, g.lacc, sizeof(double) * 2 * pp, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return ofks_cuda_check(c, e, "learned preconditioner backward");
+    double L = 0.0;
+    for (int k = 0; k < pp; ++k) L += h[k] / h[pp + k];
+    *loss = L / pp;
+    return OFKS_OK;
+}
+
+int gcn_adam(ofks_ctx *c, double lr) {
+    GcnState &g = c->gcn;
+    const int64_t m = gcn_param_count(g.H);
+    g.t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)g.t), c2 = 1.f - std::pow(b2, (float)g.t);
+    k_adam<<<gr(m), 256, 0, c->stream>>>(m, g.grad, g.w, g.m, g.v, (float)lr, b1, b2, c1, c2, 1e-8f);
+    c->kernels += 1;
+    return ofks_cuda_check(c, cudaGetLastError(), "Adam");
+}
+
+template <class E>
+void gcn_pack(ofks_ctx *c, const E *src, float *dst) {
+    k_pack<E><<<gr(c->n * (int64_t)c->p), 256, 0, c->stream>>>(c->n, c->p, c->ld, src, dst);
+    c->kernels += 1;
+}
+template <class E>
+void gcn_unpack(ofks_ctx *c, const float *src, E *dst) {
+    k_unpack<E><<<gr(c->n * (int64_t)c->p), 256, 0, c->stream>>>(c->n, c->p, c->ld, src, dst);
+    c->kernels += 1;
+}
+template void gcn_pack<double>(ofks_ctx *, const double *, float *);
+template void gcn_pack<float>(ofks_ctx *, const float *, float *);
+template void gcn_unpack<double>(ofks_ctx *, const float *, double *);
+template void gcn_unpack<float>(ofks_ctx *, const float *, float *);

@@ -22,10 +22,14 @@ enum {
     SC_COUNT = 32
 };
 
+// Rows of the per-column scalar array ctx->d_colA (each ld float64 long).
+enum { CB_SHIFT = 0, CB_ACTIVE = 1, CB_RZ = 2, CB_RZN = 3, CB_PQ = 4, CB_BETA = 5, CB_NORM = 6,
+       CB_ALPHA = 7, CB_ACC = 8, CB_COUNT = 9 };
+
 // Kernel families timed by ofks_profile.
 enum {
     PF_DENSITY = 0, PF_POISSON, PF_POTENTIAL, PF_SPMM_H, PF_GRAM, PF_SMALL, PF_GRAD,
-    PF_PCG_SPMM, PF_PCG_UPDATE, PF_BB, PF_STEP, PF_SPMM_B, PF_OTHER, PF_POISSON_SPMV, PF_COUNT
+    PF_PCG_SPMM, PF_PCG_UPDATE, PF_BB, PF_STEP, PF_SPMM_B, PF_OTHER, PF_POISSON_SPMV, PF_GCN, PF_COUNT
 };
 
 // one level of the algebraic multigrid hierarchy of the Hartree Poisson operator (device CSR)
@@ -39,6 +43,30 @@ struct AmgLevel {
     double *dinv = nullptr;                      // inverse diagonal of A
     double omega = 0.0;                          // Jacobi damping 4 / (3 rho(D^-1 A))
     double *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr;
+};
+
+// n x ld blocks of one precision.  X, D and G are ping-pong pairs (current / previous iterate).
+template <class T>
+struct Blocks {
+    T *X[2] = {nullptr, nullptr}, *D[2] = {nullptr, nullptr}, *G[2] = {nullptr, nullptr};
+    T *HX = nullptr, *BX = nullptr;
+    T *R = nullptr, *Z = nullptr, *P = nullptr, *Q = nullptr, *W = nullptr;   // PCG block, W = 1/diag
+    T *valL = nullptr, *valB = nullptr, *valH = nullptr;   // SELL values (float set only; the
+                                                           // float64 values are d_valL/B/H)
+};
+
+// learned preconditioner (network parameters, optimizer moments, activations)
+struct GcnState {
+    int H = 0;                                   // hidden width (0: not initialized)
+    float *w = nullptr, *m = nullptr, *v = nullptr;   // parameters and Adam moments (float32)
+    double *grad = nullptr;                      // parameter gradients (float64 accumulation)
+    float *valA = nullptr, *valAT = nullptr;     // mean aggregation A and A^T on the SELL pattern
+    int64_t rows = 0;                            // n * p the activations are sized for
+    float *F = nullptr, *H1 = nullptr, *H2 = nullptr, *Z1 = nullptr, *Z2 = nullptr, *AH = nullptr;
+    float *y = nullptr, *scale = nullptr, *diag = nullptr, *Dn = nullptr, *Ds = nullptr;
+    float *dA = nullptr, *dB2 = nullptr, *G32 = nullptr;
+    double *stats = nullptr, *lacc = nullptr;
+    int64_t t = 0;                               // Adam step count
 };
 
 struct ofks_ctx {
@@ -85,14 +113,13 @@ struct ofks_ctx {
     double *d_U = nullptr, *d_rhs = nullptr, *d_cr = nullptr, *d_cz = nullptr, *d_cp = nullptr,
            *d_cq = nullptr;
 
-    // ---- blocks n x ld
+    // ---- blocks n x ld: float64 set (plain form, refinement sweep) and float32 set (mixed form)
     int p = 0, ld = 0;
-    double *d_X[2] = {nullptr, nullptr};         // current / previous iterate (ping-pong)
-    double *d_D[2] = {nullptr, nullptr};         // current / previous direction
-    double *d_G[2] = {nullptr, nullptr};         // current / previous gradient
-    double *d_HX = nullptr, *d_BX = nullptr;
-    double *d_R = nullptr, *d_Z = nullptr, *d_P = nullptr, *d_Q = nullptr;   // PCG block
-    double *d_W = nullptr;                       // PCG inverse Jacobi diagonal per column
+    Blocks<double> b64;
+    Blocks<float> b32;
+    int phase = 64;                              // 64: float64 iterations, 32: float32 iterations
+    bool mixed_alloc = false;                    // the float32 set is allocated
+    int switch_k = -1;                           // iteration at which float32 handed over to float64
     int cur = 0;                                 // index of the current X/D/G buffers
     // ---- small p x p (device)
     double *d_L0 = nullptr, *d_S = nullptr, *d_Lam = nullptr, *d_C = nullptr;
@@ -114,6 +141,11 @@ struct ofks_ctx {
     std::vector<double> history;                 // rows of 6
     double t_start = 0.0;
     double t_accum = 0.0;
+
+    GcnState gcn;
+    std::vector<int> row_deg;                    // pattern row lengths of the free matrices
+    double *d_shift_in = nullptr;                // p shifts for ofks_precondition / training calls
+    int64_t judge_accept = 0, judge_total = 0;   // learned preconditioner: columns accepted / judged
 
     // ---- profiling
     int64_t kernels = 0;                         // kernel launches issued (all families)
@@ -145,39 +177,55 @@ int setup_nuclei_static(ofks_ctx *c, int M, const double *Z, const double *R);
 void free_mesh(ofks_ctx *c);
 
 // ---- fields.cu (density, potentials, Hamiltonian refresh, Poisson)
-int launch_density(ofks_ctx *c, const double *X);
+template <class T> int launch_density(ofks_ctx *c, const T *X);
 int run_hartree(ofks_ctx *c);
-int launch_potential_refresh(ofks_ctx *c);
+template <class T> int launch_potential_refresh(ofks_ctx *c, T *valH, const T *valL);
 
 // ---- amg.cu (Hartree preconditioner)
 int amg_setup(ofks_ctx *c, const int *tetn, int64_t T);
 void amg_free(ofks_ctx *c);
 void amg_apply(ofks_ctx *c, const double *r_full, double *z_full);
 
-// ---- spmm.cu
-void launch_sell_spmm(ofks_ctx *c, const double *val, const double *X, double *Y);
-void launch_sell_spmm_colnorm(ofks_ctx *c, const double *val, const double *X, double *Y,
-                              double *colsum);
-void launch_pcg_apply(ofks_ctx *c, const double *Zin, double *P, double *Q, const double *beta_col,
+// ---- spmm.cu (T = double or float)
+template <class T> void launch_sell_spmm(ofks_ctx *c, const T *val, const T *X, T *Y);
+template <class T> void launch_sell_spmm_ld(ofks_ctx *c, const T *val, const T *X, T *Y, int ld);
+template <class T> void launch_sell_spmm_colnorm(ofks_ctx *c, const T *val, const T *X, T *Y, double *colsum);
+template <class T>
+void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, T *P, T *Q, const double *beta_col,
                       const double *shift, double *pq, int first);
 
 // ---- block.cu (tall-skinny products and vector updates)
-void launch_gram2(ofks_ctx *c, const double *X, const double *A, const double *B, double *XA,
-                  double *XB);
-void launch_grad_update(ofks_ctx *c);
-void launch_pcg_init(ofks_ctx *c);
-void launch_pcg_update(ofks_ctx *c, int it);
-void launch_direction_select(ofks_ctx *c);
-void launch_bb_dots(ofks_ctx *c);
-void launch_step_y(ofks_ctx *c, double *Y);
-void launch_scale_cols(ofks_ctx *c, double *Y, double *BY, const double *colsum);
-void launch_tri_solve_rows(ofks_ctx *c, const double *V, double *X, const double *Rinv);
+template <class T> void launch_gram2(ofks_ctx *c, const T *X, const T *A, const T *B, double *XA, double *XB);
+template <class T> void launch_grad_update(ofks_ctx *c, Blocks<T> &b);
+template <class T> void launch_pcg_init(ofks_ctx *c, Blocks<T> &b);
+template <class T> void launch_pcg_update(ofks_ctx *c, Blocks<T> &b);
+template <class T> void launch_judge(ofks_ctx *c, Blocks<T> &b);
+template <class T> void launch_pcg_init_warm(ofks_ctx *c, Blocks<T> &b);
+template <class T> void launch_direction_select(ofks_ctx *c, Blocks<T> &b);
+template <class T> void launch_bb_dots(ofks_ctx *c, Blocks<T> &b, bool raw);
+template <class T> void launch_step_y(ofks_ctx *c, Blocks<T> &b, T *Y);
+template <class T> void launch_scale_cols(ofks_ctx *c, T *Y, T *BY, const double *colsum);
+template <class T> void launch_block_times_small(ofks_ctx *c, const T *X, const double *M, T *Y);
+template <class S, class T> void launch_convert(ofks_ctx *c, const S *src, T *dst, int64_t count);
 
 // ---- small.cu (p x p work on one CTA)
 void launch_small_update(ofks_ctx *c);
 void launch_small_record(ofks_ctx *c);
 void launch_eta(ofks_ctx *c);
+void launch_pcg_alpha(ofks_ctx *c);
+void launch_pcg_beta(ofks_ctx *c);
 void launch_cholesky_inv(ofks_ctx *c, const double *S, double *Rinv);
-void launch_rayleigh_ritz(ofks_ctx *c, const double *A, const double *S, double *eigs,
-                          double *V);
-void launch_block_times_small(ofks_ctx *c, const double *X, const double *V, double *Y);
+void launch_rayleigh_ritz(ofks_ctx *c, const double *A, const double *S, double *eigs, double *V);
+
+// ---- gcn.cu (learned preconditioner)
+int64_t gcn_param_count(int H);
+int gcn_setup(ofks_ctx *c, int H, uint64_t seed, const std::vector<int> &deg);
+void gcn_free(ofks_ctx *c);
+int gcn_forward_prepare(ofks_ctx *c);
+int gcn_forward(ofks_ctx *c, const double *shift, bool keep);
+int gcn_backward(ofks_ctx *c, double *loss);
+int gcn_adam(ofks_ctx *c, double lr);
+void launch_dense_tc(ofks_ctx *c, int64_t rows, const float *H, const float *AH, const float *W, const float *U,
+                     const float *b, float *out);
+template <class E> void gcn_pack(ofks_ctx *c, const E *src, float *dst);
+template <class E> void gcn_unpack(ofks_ctx *c, const float *src, E *dst);

@@ -188,6 +188,7 @@ void free_mesh(ofks_ctx *c) {
     dev_free(c->d_U); dev_free(c->d_rhs); dev_free(c->d_cr); dev_free(c->d_cz); dev_free(c->d_cp);
     dev_free(c->d_cq);
     amg_free(c);
+    gcn_free(c);
     c->n = c->n_nodes = c->n_tets = c->nnz = c->nnz_full = 0;
     c->have_nuclei = false;
 }
@@ -259,6 +260,7 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
         }
     });
     for (int64_t r = 0; r < n; ++r) rptr[r + 1] = rptr[r] + rowlen[r];
+    c->row_deg = rowlen;
     const int64_t nnz = rptr[n];
     std::vector<int> rcol(nnz);
     parallel_for(n, [&](int64_t a, int64_t b) {

@@ -9,9 +9,6 @@
 #include "common.cuh"
 #include "internal.h"
 
-enum { CB_SHIFT = 0, CB_ACTIVE = 1, CB_RZ = 2, CB_RZN = 3, CB_PQ = 4, CB_BETA = 5, CB_NORM = 6,
-       CB_ALPHA = 7 };
-
 namespace {
 
 __global__ void __launch_bounds__(256) k_small_update(int p, int ld, const double *__restrict__ L0,
@@ -48,6 +45,7 @@ __global__ void __launch_bounds__(256) k_small_update(int p, int ld, const doubl
         const bool act = precond && j < p && ljj < 0.0;
         cb[CB_SHIFT * ld + j] = act ? ljj : 0.0;
         cb[CB_ACTIVE * ld + j] = act ? 1.0 : 0.0;
+        cb[CB_ACC * ld + j] = 0.0;
     }
     if (threadIdx.x == 0) {
         rec[0] = occ * tr - sc[SC_EDC] + e_nuc;   // E_KS in the double-counting form
@@ -83,7 +81,7 @@ __global__ void k_eta(int rule, int k, int have_prev, double eta_fixed, double e
 __global__ void k_pcg_alpha(int ld, double *cb) {
     for (int j = threadIdx.x; j < ld; j += blockDim.x) {
         const double pq = cb[CB_PQ * ld + j], rz = cb[CB_RZ * ld + j];
-        cb[CB_ALPHA * ld + j] = pq > 0.0 ? rz / pq : 0.0;
+        cb[CB_ALPHA * ld + j] = (pq > 0.0 && cb[CB_ACC * ld + j] == 0.0) ? rz / pq : 0.0;
         cb[CB_RZN * ld + j] = 0.0;
     }
 }

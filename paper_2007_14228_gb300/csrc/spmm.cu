@@ -12,38 +12,61 @@
 
 namespace {
 
-template <int W>
-__device__ __forceinline__ void load_w(const double *__restrict__ p, double (&v)[W]) {
+template <class T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+
+template <class T, int W>
+__device__ __forceinline__ void load_w(const T *__restrict__ p, T (&v)[W]) {
     if constexpr (W == 1) {
         v[0] = __ldg(p);
+    } else if constexpr (sizeof(T) == 4 && W == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
     } else {
+        using V2 = typename Vec2<T>::type;
 #pragma unroll
         for (int w = 0; w < W; w += 2) {
-            double2 t = __ldg(reinterpret_cast<const double2 *>(p + w));
+            const V2 t = __ldg(reinterpret_cast<const V2 *>(p + w));
             v[w] = t.x; v[w + 1] = t.y;
         }
     }
 }
 
-template <int W>
-__device__ __forceinline__ void store_w(double *p, const double (&v)[W]) {
+template <class T, int W>
+__device__ __forceinline__ void store_w(T *p, const T (&v)[W]) {
     if constexpr (W == 1) {
         p[0] = v[0];
+    } else if constexpr (sizeof(T) == 4 && W == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
     } else {
+        using V2 = typename Vec2<T>::type;
 #pragma unroll
-        for (int w = 0; w < W; w += 2) *reinterpret_cast<double2 *>(p + w) = make_double2(v[w], v[w + 1]);
+        for (int w = 0; w < W; w += 2) {
+            V2 t;
+            t.x = v[w]; t.y = v[w + 1];
+            *reinterpret_cast<V2 *>(p + w) = t;
+        }
     }
 }
 
-// MODE 0: Y = A X.  MODE 1: also colsum[c] += sum_rows X[r,c] Y[r,c].
-template <int W, int MODE>
+template <class T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// MODE 0: Y = A X.  MODE 1: also colsum[c] += sum_rows X[r,c] Y[r,c] (float64 accumulators).
+// T is the element type of the values and blocks; sums run in T.
+template <class T, int W, int MODE>
 __global__ void __launch_bounds__(256) k_sell_spmm(int64_t nwarps, int nchunks, int p, int ld,
                                                    const int *__restrict__ slice_ptr,
                                                    const int *__restrict__ slice_w,
                                                    const int *__restrict__ cols,
                                                    const int *__restrict__ perm,
-                                                   const double *__restrict__ val,
-                                                   const double *__restrict__ X, double *__restrict__ Y,
+                                                   const T *__restrict__ val,
+                                                   const T *__restrict__ X, T *__restrict__ Y,
                                                    double *colsum) {
     const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -53,27 +76,27 @@ __global__ void __launch_bounds__(256) k_sell_spmm(int64_t nwarps, int nchunks, 
     const int c0 = chunk * W;
     const int base = slice_ptr[s], width = slice_w[s];
     const int r = perm[s * SELL_C + lane];
-    double acc[W];
+    T acc[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) acc[w] = 0.0;
+    for (int w = 0; w < W; ++w) acc[w] = T(0);
     int e = base + lane;
     for (int j = 0; j < width; ++j, e += SELL_C) {
         const int c = __ldg(cols + e);
-        const double v = __ldg(val + e);
-        double x[W];
-        load_w<W>(X + (int64_t)c * ld + c0, x);
+        const T v = __ldg(val + e);
+        T x[W];
+        load_w<T, W>(X + (int64_t)c * ld + c0, x);
 #pragma unroll
         for (int w = 0; w < W; ++w) acc[w] = fma(v, x[w], acc[w]);
     }
-    if (r >= 0) store_w<W>(Y + (int64_t)r * ld + c0, acc);
+    if (r >= 0) store_w<T, W>(Y + (int64_t)r * ld + c0, acc);
     if constexpr (MODE == 1) {
-        double xr[W];
-        if (r >= 0) load_w<W>(X + (int64_t)r * ld + c0, xr);
+        T xr[W];
+        if (r >= 0) load_w<T, W>(X + (int64_t)r * ld + c0, xr);
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-            double t = (r >= 0) ? xr[w] * acc[w] : 0.0;
-            t = warp_sum(t);
-            if (lane == 0 && c0 + w < p) atomicAdd(colsum + c0 + w, t);
+            T t = (r >= 0) ? xr[w] * acc[w] : T(0);
+            t = warp_sum_t(t);
+            if (lane == 0 && c0 + w < p) atomicAdd(colsum + c0 + w, (double)t);
         }
     }
 }
@@ -82,15 +105,15 @@ __global__ void __launch_bounds__(256) k_sell_spmm(int64_t nwarps, int nchunks, 
 //   TZ = (L/2) Z - B Z diag(shift)  gathered over the neighbours of each row, then for the
 //   own row  P <- Z + beta P,  Q <- TZ + beta Q  (so T P = Q), and pq[c] += P.Q.
 // With first = 1: P = Z, Q = TZ.
-template <int W>
+template <class T, int W>
 __global__ void __launch_bounds__(256) k_pcg_apply(int64_t nwarps, int nchunks, int p, int ld,
                                                    const int *__restrict__ slice_ptr,
                                                    const int *__restrict__ slice_w,
                                                    const int *__restrict__ cols,
                                                    const int *__restrict__ perm,
-                                                   const double *__restrict__ valL,
-                                                   const double *__restrict__ valB,
-                                                   const double *__restrict__ Z, double *P, double *Q,
+                                                   const T *__restrict__ valL,
+                                                   const T *__restrict__ valB,
+                                                   const T *__restrict__ Z, T *P, T *Q,
                                                    const double *__restrict__ beta_col,
                                                    const double *__restrict__ shift, double *pq,
                                                    int first) {
@@ -102,45 +125,45 @@ __global__ void __launch_bounds__(256) k_pcg_apply(int64_t nwarps, int nchunks, 
     const int c0 = chunk * W;
     const int base = slice_ptr[s], width = slice_w[s];
     const int r = perm[s * SELL_C + lane];
-    double aL[W], aB[W];
+    T aL[W], aB[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) { aL[w] = 0.0; aB[w] = 0.0; }
+    for (int w = 0; w < W; ++w) { aL[w] = T(0); aB[w] = T(0); }
     int e = base + lane;
     for (int j = 0; j < width; ++j, e += SELL_C) {
         const int c = __ldg(cols + e);
-        const double vl = __ldg(valL + e), vb = __ldg(valB + e);
-        double x[W];
-        load_w<W>(Z + (int64_t)c * ld + c0, x);
+        const T vl = __ldg(valL + e), vb = __ldg(valB + e);
+        T x[W];
+        load_w<T, W>(Z + (int64_t)c * ld + c0, x);
 #pragma unroll
         for (int w = 0; w < W; ++w) { aL[w] = fma(vl, x[w], aL[w]); aB[w] = fma(vb, x[w], aB[w]); }
     }
-    double contrib[W];
+    T contrib[W];
     if (r >= 0) {
-        double zr[W], pr[W], qr[W];
-        load_w<W>(Z + (int64_t)r * ld + c0, zr);
+        T zr[W], pr[W], qr[W];
+        load_w<T, W>(Z + (int64_t)r * ld + c0, zr);
         if (!first) {
-            load_w<W>(P + (int64_t)r * ld + c0, pr);
-            load_w<W>(Q + (int64_t)r * ld + c0, qr);
+            load_w<T, W>(P + (int64_t)r * ld + c0, pr);
+            load_w<T, W>(Q + (int64_t)r * ld + c0, qr);
         }
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-            const double tz = 0.5 * aL[w] - shift[c0 + w] * aB[w];
-            const double b = first ? 0.0 : beta_col[c0 + w];
-            const double pn = first ? zr[w] : fma(b, pr[w], zr[w]);
-            const double qn = first ? tz : fma(b, qr[w], tz);
+            const T tz = T(0.5) * aL[w] - T(shift[c0 + w]) * aB[w];
+            const T b = first ? T(0) : T(beta_col[c0 + w]);
+            const T pn = first ? zr[w] : fma(b, pr[w], zr[w]);
+            const T qn = first ? tz : fma(b, qr[w], tz);
             pr[w] = pn; qr[w] = qn;
             contrib[w] = pn * qn;
         }
-        store_w<W>(P + (int64_t)r * ld + c0, pr);
-        store_w<W>(Q + (int64_t)r * ld + c0, qr);
+        store_w<T, W>(P + (int64_t)r * ld + c0, pr);
+        store_w<T, W>(Q + (int64_t)r * ld + c0, qr);
     } else {
 #pragma unroll
-        for (int w = 0; w < W; ++w) contrib[w] = 0.0;
+        for (int w = 0; w < W; ++w) contrib[w] = T(0);
     }
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-        double t = warp_sum(contrib[w]);
-        if (lane == 0 && c0 + w < p) atomicAdd(pq + c0 + w, t);
+        T t = warp_sum_t(contrib[w]);
+        if (lane == 0 && c0 + w < p) atomicAdd(pq + c0 + w, (double)t);
     }
 }
 
@@ -148,36 +171,61 @@ inline int chunk_width(int ld) { return (ld % 4 == 0) ? 4 : (ld % 2 == 0 ? 2 : 1
 
 }  // namespace
 
-void launch_sell_spmm(ofks_ctx *c, const double *val, const double *X, double *Y) {
+template <class T>
+void launch_sell_spmm(ofks_ctx *c, const T *val, const T *X, T *Y) {
     const int W = chunk_width(c->ld), nch = c->ld / W;
     const int64_t nw = (int64_t)c->n_slices * nch;
     const unsigned grid = (unsigned)((nw * 32 + 255) / 256);
-#define L_(w) k_sell_spmm<w, 0><<<grid, 256, 0, c->stream>>>(nw, nch, c->p, c->ld, c->d_slice_ptr, \
+#define L_(w) k_sell_spmm<T, w, 0><<<grid, 256, 0, c->stream>>>(nw, nch, c->p, c->ld, c->d_slice_ptr, \
         c->d_slice_w, c->d_cols, c->d_perm, val, X, Y, nullptr)
     if (W == 4) L_(4); else if (W == 2) L_(2); else L_(1);
 #undef L_
     c->kernels += 1;
 }
 
-void launch_sell_spmm_colnorm(ofks_ctx *c, const double *val, const double *X, double *Y, double *colsum) {
+template <class T>
+void launch_sell_spmm_colnorm(ofks_ctx *c, const T *val, const T *X, T *Y, double *colsum) {
     const int W = chunk_width(c->ld), nch = c->ld / W;
     const int64_t nw = (int64_t)c->n_slices * nch;
     const unsigned grid = (unsigned)((nw * 32 + 255) / 256);
-#define L_(w) k_sell_spmm<w, 1><<<grid, 256, 0, c->stream>>>(nw, nch, c->p, c->ld, c->d_slice_ptr, \
+#define L_(w) k_sell_spmm<T, w, 1><<<grid, 256, 0, c->stream>>>(nw, nch, c->p, c->ld, c->d_slice_ptr, \
         c->d_slice_w, c->d_cols, c->d_perm, val, X, Y, colsum)
     if (W == 4) L_(4); else if (W == 2) L_(2); else L_(1);
 #undef L_
     c->kernels += 1;
 }
 
-void launch_pcg_apply(ofks_ctx *c, const double *Zin, double *P, double *Q, const double *beta_col,
+template <class T>
+void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, T *P, T *Q, const double *beta_col,
                       const double *shift, double *pq, int first) {
     const int W = chunk_width(c->ld), nch = c->ld / W;
     const int64_t nw = (int64_t)c->n_slices * nch;
     const unsigned grid = (unsigned)((nw * 32 + 255) / 256);
-#define L_(w) k_pcg_apply<w><<<grid, 256, 0, c->stream>>>(nw, nch, c->p, c->ld, c->d_slice_ptr, \
-        c->d_slice_w, c->d_cols, c->d_perm, c->d_valL, c->d_valB, Zin, P, Q, beta_col, shift, pq, first)
+#define L_(w) k_pcg_apply<T, w><<<grid, 256, 0, c->stream>>>(nw, nch, c->p, c->ld, c->d_slice_ptr, \
+        c->d_slice_w, c->d_cols, c->d_perm, valL, valB, Zin, P, Q, beta_col, shift, pq, first)
     if (W == 4) L_(4); else if (W == 2) L_(2); else L_(1);
 #undef L_
     c->kernels += 1;
 }
+
+template <class T>
+void launch_sell_spmm_ld(ofks_ctx *c, const T *val, const T *X, T *Y, int ld) {
+    const int W = chunk_width(ld), nch = ld / W;
+    const int64_t nw = (int64_t)c->n_slices * nch;
+    const unsigned grid = (unsigned)((nw * 32 + 255) / 256);
+#define L_(w) k_sell_spmm<T, w, 0><<<grid, 256, 0, c->stream>>>(nw, nch, ld, ld, c->d_slice_ptr, \
+        c->d_slice_w, c->d_cols, c->d_perm, val, X, Y, nullptr)
+    if (W == 4) L_(4); else if (W == 2) L_(2); else L_(1);
+#undef L_
+    c->kernels += 1;
+}
+
+template void launch_sell_spmm_ld<float>(ofks_ctx *, const float *, const float *, float *, int);
+template void launch_sell_spmm<double>(ofks_ctx *, const double *, const double *, double *);
+template void launch_sell_spmm<float>(ofks_ctx *, const float *, const float *, float *);
+template void launch_sell_spmm_colnorm<double>(ofks_ctx *, const double *, const double *, double *, double *);
+template void launch_sell_spmm_colnorm<float>(ofks_ctx *, const float *, const float *, float *, double *);
+template void launch_pcg_apply<double>(ofks_ctx *, const double *, const double *, const double *, double *,
+                                       double *, const double *, const double *, double *, int);
+template void launch_pcg_apply<float>(ofks_ctx *, const float *, const float *, const float *, float *, float *,
+                                      const double *, const double *, double *, int);

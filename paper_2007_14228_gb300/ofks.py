@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libofks.so")
 
 OK, EINVAL, ECUDA, ENOMEM, ESTATE, ENOTCONV, ENONFINITE, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
-PC = {"none": 0, "pcg": 1, "exact": 2}
+PC = {"none": 0, "pcg": 1, "exact": 2, "learned": 3}
+PRECISION = {"fp64": 0, "mixed": 1}
 ETA = {"bb2": 0, "bb1": 1, "abb1": 2, "abb2": 3, "bb2_raw": 4, "fixed": 5}
 FIELDS = {"rho_q": 0, "vh_q": 1, "vxc_q": 2, "exc_q": 3, "U": 4, "HX": 5, "BX": 6, "G": 7, "D": 8,
           "Lambda0": 9, "S": 10, "Lambda": 11, "vext_q": 12}
@@ -24,7 +25,8 @@ SYMBOLS = ("ofks_default_params", "ofks_create", "ofks_destroy", "ofks_last_erro
            "ofks_set_nuclei", "ofks_set_nuclei_static", "ofks_set_params", "ofks_init_orbitals", "ofks_set_orbitals",
            "ofks_get_orbitals", "ofks_step", "ofks_solve", "ofks_evaluate", "ofks_rayleigh_ritz",
            "ofks_get_field", "ofks_apply", "ofks_get_sizes", "ofks_get_history", "ofks_save_state",
-           "ofks_load_state", "ofks_profile", "ofks_profile_get")
+           "ofks_load_state", "ofks_profile", "ofks_profile_get", "ofks_precond_init", "ofks_precond_get_weights",
+           "ofks_precond_set_weights", "ofks_precondition", "ofks_train_precond_step", "ofks_precond_grads")
 
 
 class OfksError(RuntimeError):
@@ -39,13 +41,15 @@ class Params(C.Structure):
                 ("pcg_iters", C.c_int32), ("eta_rule", C.c_int32), ("eta_fixed", C.c_double),
                 ("eta_min", C.c_double), ("eta_max", C.c_double), ("hartree", C.c_int32),
                 ("xc", C.c_int32), ("multipole_lmax", C.c_int32), ("poisson_tol", C.c_double),
-                ("poisson_max_iter", C.c_int32), ("poisson_amg", C.c_int32)]
+                ("poisson_max_iter", C.c_int32), ("poisson_amg", C.c_int32), ("mixed_tol", C.c_double),
+                ("poisson_tol_mixed", C.c_double), ("judge_tau", C.c_double), ("learned_tc", C.c_int32)]
 
 
 class Result(C.Structure):
     _fields_ = [("e_total", C.c_double), ("e_nuc", C.c_double), ("kkt", C.c_double), ("fea", C.c_double),
                 ("kkt0", C.c_double), ("eta", C.c_double), ("iters", C.c_int32), ("converged", C.c_int32),
-                ("seconds", C.c_double), ("hartree_iters", C.c_int32), ("hartree_total", C.c_int32)]
+                ("seconds", C.c_double), ("hartree_iters", C.c_int32), ("hartree_total", C.c_int32),
+                ("switch_iter", C.c_int32), ("judge_accept", C.c_int64), ("judge_total", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -55,6 +59,7 @@ _lib = None
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _ip = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
 _up = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+_fp = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
 
 
 def load(path: str = LIB_PATH):
@@ -91,6 +96,12 @@ def load(path: str = LIB_PATH):
         "ofks_load_state": (C.c_int, [vp, C.c_char_p]),
         "ofks_profile": (C.c_int, [vp, i32]),
         "ofks_profile_get": (C.c_int, [vp, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(C.c_char_p)]),
+        "ofks_precond_init": (C.c_int, [vp, i32, C.c_uint64]),
+        "ofks_precond_get_weights": (C.c_int, [vp, C.c_void_p, i64, C.POINTER(i64)]),
+        "ofks_precond_set_weights": (C.c_int, [vp, _fp, i64]),
+        "ofks_precondition": (C.c_int, [vp, i32, _dp, _dp, _dp]),
+        "ofks_train_precond_step": (C.c_int, [vp, _dp, _dp, _dp, dbl, C.POINTER(dbl)]),
+        "ofks_precond_grads": (C.c_int, [vp, _dp, _dp, _dp, _dp, i64, C.POINTER(dbl)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -108,6 +119,8 @@ def default_params(**overrides) -> Params:
             v = PC[v]
         if k == "eta_rule" and isinstance(v, str):
             v = ETA[v]
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
         if isinstance(v, bool):
             v = int(v)
         setattr(prm, k, v)
@@ -254,6 +267,46 @@ class Context:
 
     def load_state(self, path: str):
         self._chk(self.lib.ofks_load_state(self.h, path.encode()))
+
+    # ---- learned preconditioner
+    def precond_init(self, width: int = 64, seed: int = 0):
+        self._chk(self.lib.ofks_precond_init(self.h, int(width), int(seed)))
+
+    def precond_get_weights(self):
+        n = C.c_int64()
+        self._chk(self.lib.ofks_precond_get_weights(self.h, None, 0, C.byref(n)))
+        w = np.empty(n.value, np.float32)
+        self._chk(self.lib.ofks_precond_get_weights(self.h, w.ctypes.data, n.value, C.byref(n)))
+        return w
+
+    def precond_set_weights(self, w):
+        w = np.ascontiguousarray(w, np.float32)
+        self._chk(self.lib.ofks_precond_set_weights(self.h, w, w.size))
+
+    def precondition(self, mode: str, G, shifts):
+        G = np.ascontiguousarray(G, np.float64)
+        self._check_block(G)
+        D = np.empty_like(G)
+        self._chk(self.lib.ofks_precondition(self.h, PC[mode], G, np.ascontiguousarray(shifts, np.float64), D))
+        return D
+
+    def train_precond_step(self, G, shifts, Dstar, lr: float = 1e-3) -> float:
+        loss = C.c_double()
+        self._chk(self.lib.ofks_train_precond_step(self.h, np.ascontiguousarray(G, np.float64),
+                                                   np.ascontiguousarray(shifts, np.float64),
+                                                   np.ascontiguousarray(Dstar, np.float64), float(lr),
+                                                   C.byref(loss)))
+        return loss.value
+
+    def precond_grads(self, G, shifts, Dstar):
+        n = C.c_int64()
+        self._chk(self.lib.ofks_precond_get_weights(self.h, None, 0, C.byref(n)))
+        g = np.empty(n.value)
+        loss = C.c_double()
+        self._chk(self.lib.ofks_precond_grads(self.h, np.ascontiguousarray(G, np.float64),
+                                              np.ascontiguousarray(shifts, np.float64),
+                                              np.ascontiguousarray(Dstar, np.float64), g, g.size, C.byref(loss)))
+        return loss.value, g
 
     def profile(self, on: bool):
         self._chk(self.lib.ofks_profile(self.h, int(on)))

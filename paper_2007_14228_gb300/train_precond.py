@@ -1,0 +1,106 @@
+"""Train the learned preconditioner on pairs the method itself generates.
+
+For seeded random nuclei sets (4-12 nuclei, Z in {1, 6, 7, 8}, positions uniform in a 6 bohr
+box, meshes of 16^3-24^3 cells) PCAL runs with the paper's PCG preconditioner; at sampled
+iterations the gradient block G and the multipliers' diagonal give the pairs
+(G_c, T_c^{-1} G_c) with the target solved to a tight residual by the same PCG.  Each pair
+batch (all columns of one iterate) takes a few Adam steps of the library's own forward and
+backward kernels, then is discarded.
+
+    python -m paper_2007_14228_gb300.train_precond --systems 100 --out weights.npy
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import inputs as I
+from . import ofks
+
+
+def pairs_from_system(seed: int, cells: int, samples, rng, device=0, width=64, weights=None):
+    """Yield (ctx, G, shifts, Dstar) at the sampled iterations of one random system."""
+    s = I.random_nuclei(seed, cells=(cells, cells, cells))
+    m = I.make_mesh(s)
+    ctx = ofks.context_for(s, m, device=device, beta=10.0)
+    if weights is not None:
+        ctx.precond_set_weights(weights)
+    else:
+        ctx.precond_init(width, seed)
+    ctx.init_orbitals(I.initial_block(m.n_free, s.p, seed))
+    k = 0
+    for target in samples:
+        if target > k:
+            ctx.step(target - k)
+            k = target
+        ctx.evaluate()
+        G = ctx.get_field("G")
+        shifts = np.diag(ctx.get_field("Lambda")).copy()
+        if not np.any(shifts < 0):
+            continue
+        Dstar = ctx.precondition("exact", G, shifts)
+        yield ctx, G, shifts, Dstar
+    ctx.close()
+
+
+def train(systems=100, first_seed=1, steps_per_pair=3, lr=1e-3, width=64, samples=(5, 10, 15, 20, 30, 40, 50),
+          device=0, log=None, weights=None):
+    rng = np.random.default_rng(first_seed)
+    w = weights
+    history = []
+    n_pairs = 0
+    t0 = time.time()
+    for k, seed in enumerate(range(first_seed, first_seed + systems)):
+        cells = int(rng.integers(16, 25))
+        for ctx, G, shifts, Dstar in pairs_from_system(seed, cells, samples, rng, device, width, w):
+            for _ in range(steps_per_pair):
+                loss = ctx.train_precond_step(G, shifts, Dstar, lr)
+            history.append(loss)
+            n_pairs += int(np.sum(shifts < 0))
+            w = ctx.precond_get_weights()
+        if log:
+            log({"system": seed, "cells": cells, "pairs": n_pairs, "loss": history[-1] if history else None,
+                 "seconds": round(time.time() - t0, 1)})
+    return w, history, n_pairs
+
+
+def evaluate(weights, seed: int, cells: int, device=0, tol=1e-6, max_iter=600):
+    """Iterations to (kkt + fea)/kkt0 < tol with no preconditioner, the learned one and PCG."""
+    s = I.random_nuclei(seed, cells=(cells, cells, cells))
+    m = I.make_mesh(s)
+    V = I.initial_block(m.n_free, s.p, seed)
+    out = {"seed": seed, "cells": cells, "p": s.p}
+    for mode in ("none", "learned", "pcg"):
+        ctx = ofks.context_for(s, m, device=device, beta=10.0, tol=tol, max_iter=max_iter, precond=mode)
+        if mode == "learned":
+            ctx.precond_set_weights(weights)
+        ctx.init_orbitals(V)
+        r = ctx.solve(allow_notconv=True)
+        out[mode] = {"iters": r["iters"], "converged": r["converged"], "E": r["e_total"],
+                     "accepted": r["judge_accept"], "judged": r["judge_total"]}
+        ctx.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--systems", type=int, default=100)
+    ap.add_argument("--first-seed", type=int, default=1)
+    ap.add_argument("--width", type=int, default=64)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--steps-per-pair", type=int, default=3)
+    ap.add_argument("--out", default="precond_weights.npy")
+    ap.add_argument("--eval-seed", type=int, default=10_000)
+    args = ap.parse_args()
+    w, hist, n = train(args.systems, args.first_seed, args.steps_per_pair, args.lr, args.width,
+                       log=lambda d: print(json.dumps(d), flush=True))
+    np.save(args.out, w)
+    print(json.dumps({"pairs": n, "final_loss": hist[-1] if hist else None, "out": args.out}), flush=True)
+    print(json.dumps({"eval": evaluate(w, args.eval_seed, 16)}), flush=True)
+
+
+if __name__ == "__main__":
+    main()

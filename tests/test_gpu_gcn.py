@@ -1,0 +1,127 @@
+"""Learned preconditioner on the GPU against the oracle network (oracle/gcn.py).
+
+Weights are drawn in Python and rounded to bfloat16-representable values, so the GPU's
+bfloat16 use of them is exact and both sides evaluate the same network; float32 activations
+on the GPU give relative agreement of ~1e-5 in the output and ~1e-3 in the gradients.
+"""
+import numpy as np
+import pytest
+
+from oracle import gcn, pcal
+from paper_2007_14228_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ofks():
+    from paper_2007_14228_gb300 import build
+    build.build()
+    from paper_2007_14228_gb300 import ofks as mod
+    return mod
+
+
+def bf16(x):
+    """Round float32 values to the nearest bfloat16 (ties to even)."""
+    u = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def flat_to_params(w, width):
+    dims = [gcn.N_FEAT, width, width, 1]
+    out, o = [], 0
+    for l in range(3):
+        fi, fo = dims[l], dims[l + 1]
+        W = w[o:o + fi * fo].reshape(fi, fo).astype(np.float64); o += fi * fo
+        U = w[o:o + fi * fo].reshape(fi, fo).astype(np.float64); o += fi * fo
+        b = w[o:o + fo].astype(np.float64); o += fo
+        out.append({"W": W, "U": U, "b": b})
+    return out
+
+
+def setup(ofks, width, seed=0):
+    s = I.lih().with_cells((8, 6, 6)).with_p(3, occ=1.0)
+    m = I.make_mesh(s)
+    ctx = ofks.context_for(s, m, beta=10.0, learned_tc=0)     # float32 activations for the oracle checks
+    pr = pcal.Problem(m.xyz, m.tet10, m.dirichlet, s.Z, s.R, pcal.Params(p=3, occ=1.0, precond="exact",
+                                                                          hartree=False, xc=False))
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((pr.n, 3))
+    shifts = np.array([-0.9, -0.3, 0.2])
+    ctx.precond_init(width, seed)
+    w = ctx.precond_get_weights()
+    w = bf16(0.3 * rng.standard_normal(w.size).astype(np.float32))
+    ctx.precond_set_weights(w)
+    A = gcn.mean_aggregator(pr.Lf)
+    return ctx, pr, G, shifts, w, A
+
+
+@pytest.mark.parametrize("width", [8, 64])
+def test_network_output_matches_oracle(ofks, width):
+    ctx, pr, G, shifts, w, A = setup(ofks, width)
+    D = ctx.precondition("learned", G, shifts)
+    f, s, diag = gcn.features(G, pr.Lf.diagonal(), pr.Bf.diagonal(), shifts)
+    Do, _, _ = gcn.predict(flat_to_params(w, width), f, s, A)
+    Do[:, 2] = G[:, 2]                     # shift >= 0: T = I
+    assert np.max(np.abs(D - Do)) < 2e-4 * np.max(np.abs(Do))
+    ctx.close()
+
+
+@pytest.mark.parametrize("width", [8, 64])
+def test_network_gradients_match_oracle(ofks, width):
+    ctx, pr, G, shifts, w, A = setup(ofks, width, seed=1)
+    Dstar = pr.precondition(G, shifts)
+    loss, g = ctx.precond_grads(G, shifts, Dstar)
+    f, s, _ = gcn.features(G, pr.Lf.diagonal(), pr.Bf.diagonal(), shifts)
+    params = flat_to_params(w, width)
+    D, y, cache = gcn.predict(params, f, s, A)
+    lo, dy = gcn.loss_and_dy(D, Dstar, s)
+    grads = gcn.backward(params, cache, dy, A)
+    go = np.concatenate([np.concatenate([gr["W"].ravel(), gr["U"].ravel(), gr["b"].ravel()]) for gr in grads])
+    assert abs(loss - lo) < 1e-4 * lo
+    assert np.max(np.abs(g - go)) < 1e-3 * np.max(np.abs(go)), np.max(np.abs(g - go)) / np.max(np.abs(go))
+    ctx.close()
+
+
+def test_training_steps_reduce_the_loss(ofks):
+    ctx, pr, G, shifts, w, A = setup(ofks, 16, seed=2)
+    ctx.precond_init(16, 3)                 # last layer zero: starts as the Jacobi step
+    Dstar = pr.precondition(G, shifts)
+    losses = [ctx.train_precond_step(G, shifts, Dstar, lr=3e-3) for _ in range(60)]
+    assert losses[-1] < 0.7 * losses[0], (losses[0], losses[-1])
+    ctx.close()
+
+
+def test_learned_mode_keeps_the_fixed_point(ofks):
+    # the judge and its PCG fallback make the learned mode change only the path
+    s = I.lih().with_cells((6, 6, 6))
+    m = I.make_mesh(s)
+    V = I.initial_block(m.n_free, s.p, 0)
+    E = {}
+    for mode in ("pcg", "learned"):
+        ctx = ofks.context_for(s, m, beta=10.0, tol=1e-10, max_iter=3000, precond=mode)
+        if mode == "learned":
+            ctx.precond_init(16, 5)
+        ctx.init_orbitals(V)
+        r = ctx.solve()
+        E[mode] = r["e_total"]
+        if mode == "learned":
+            assert r["judge_total"] > 0
+        ctx.close()
+    assert abs(E["pcg"] - E["learned"]) < 1e-8
+
+
+def test_tensor_core_layer_matches_cuda_cores(ofks):
+    # the width-64 hidden layer on tcgen05 (bf16 operands, float32 accumulation in tensor memory)
+    # against the float32 CUDA-core layer: agreement to bf16 rounding of the activations
+    ctx, pr, G, shifts, w, A = setup(ofks, 64, seed=4)
+    outs = {}
+    for tc in (0, 1):
+        ctx.set_params(p=3, occ=1.0, beta=10.0, learned_tc=tc)
+        ctx.precond_set_weights(w)
+        outs[tc] = ctx.precondition("learned", G, shifts)
+    err = np.max(np.abs(outs[1] - outs[0])) / np.max(np.abs(outs[0]))
+    assert err < 3e-2, err
+    assert np.all(np.isfinite(outs[1]))
+    ctx.close()

@@ -54,6 +54,7 @@ def config_of(args, s, sizes):
             "n_free": sizes["n"], "n_tets": sizes["n_tets"], "n_q": sizes["n_q"], "p": s.p, "occ": s.occ,
             "beta": 10.0, "form": "mixed: float32 iterations, float64 p x p / energy / tests (plain float64 beside it)",
             "precond": "PCG x8 (Eq. precondition-T)", "eta": "BB2",
+            "hartree": "Jacobi-CG, tolerance max(1e-12, min(1e-4, 0.01 (kkt+fea)/kkt0)) in both forms",
             "l2": "inputs larger than L2 (working set ~7 GB)", "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -198,7 +199,7 @@ def time_to_target(ofks, I, target=1e-6, fea_max=1e-7):
     ref.close()
     out = {"workload": "lih 24^3 cells (n = 103,823, p = 2)", "E_star": E_star, "E_star_iters": r["iters"]}
     for form in ("fp64", "mixed"):
-        ctx = ofks.context_for(s, m, beta=10.0, tol=1e-9, max_iter=6000, precision=form)
+        ctx = ofks.context_for(s, m, beta=10.0, tol=1e-9, max_iter=6000, precision=form, poisson_adaptive=1)
         ctx.init_orbitals(V)
         res = ctx.solve(allow_notconv=True)
         h = ctx.history()
@@ -279,7 +280,7 @@ def main():
     m = I.make_mesh(s)
 
     def timed(precision, clocks_on):
-        ctx = ofks.context_for(s, m, device=local, beta=10.0, precision=precision)
+        ctx = ofks.context_for(s, m, device=local, beta=10.0, precision=precision, poisson_adaptive=1)
         ctx.init_orbitals(I.initial_block(m.n_free, s.p, rank))
         ctx.step(args.warmup)
         clk = Clocks(local) if clocks_on else None

@@ -100,6 +100,8 @@ typedef struct {
     double  poisson_tol_mixed; /* Hartree CG tolerance during the float32 iterations */
     double  judge_tau;      /* OFKS_PC_LEARNED: accept a column if |G - T D| <= judge_tau |G| and G.D > 0 */
     int32_t learned_tc;     /* 1: width-64 hidden layer on the tensor cores (bf16 operands) at inference */
+    int32_t poisson_adaptive; /* 1: Hartree CG tolerance max(poisson_tol, min(1e-4, 0.01 (kkt+fea)/kkt0))
+                                 from the previous iterate (inexact potentials early, exact at the end) */
 } ofks_params;
 
 typedef struct {
@@ -122,7 +124,7 @@ typedef struct {
 /* Fill *prm with the defaults: beta 10, occ 2, tol 1e-8, max_iter 1000, FP64, PCG with 8
  * iterations, BB2, eta in [1e-4, 1e8], Hartree and LDA on, multipole_lmax 2,
  * poisson_tol 1e-12, poisson_max_iter 20000, poisson_amg 0, mixed_tol 1e-5, poisson_tol_mixed
- * 1e-8, judge_tau 0.5, learned_tc 1.  p is set to 1. */
+ * 1e-8, judge_tau 0.5, learned_tc 1, poisson_adaptive 0.  p is set to 1. */
 void ofks_default_params(ofks_params *prm);
 
 /* Create a context on CUDA device `device`.  *out receives the context (NULL on failure).

@@ -373,6 +373,11 @@ static int run_iterations(ofks_ctx *c, int kmax, ofks_result *res) {
     int rc = OFKS_OK;
     for (int it = 0; it < kmax && !c->converged; ++it) {
         Rec r{};
+        // inexact Hartree potentials while far from stationarity (tightens to poisson_tol)
+        c->hartree_tol = 0.0;
+        if (c->prm.poisson_adaptive)
+            c->hartree_tol = (c->k == 0 || !(c->kkt0 > 0)) ? 1e-4
+                             : std::min(1e-4, 1e-2 * (c->last_kkt + c->last_fea) / c->kkt0);
         if ((rc = evaluate(c, !c->bx_valid, &r))) break;
         c->bx_valid = true;
         if (c->k == 0) c->kkt0 = r.kkt;
@@ -390,6 +395,7 @@ static int run_iterations(ofks_ctx *c, int kmax, ofks_result *res) {
         if (c->kkt0 > 0 && (r.kkt + r.fea) / c->kkt0 < c->prm.tol) { c->converged = true; break; }
         if ((rc = update_step(c))) break;
     }
+    c->hartree_tol = 0.0;
     cudaEventRecord(e1, c->stream);
     cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -421,7 +427,7 @@ void ofks_default_params(ofks_params *p) {
     p->multipole_lmax = 2; p->poisson_tol = 1e-12; p->poisson_max_iter = 20000;
     p->poisson_amg = 0;
     p->mixed_tol = 1e-5; p->poisson_tol_mixed = 1e-8;
-    p->judge_tau = 0.5; p->learned_tc = 1;
+    p->judge_tau = 0.5; p->learned_tc = 1; p->poisson_adaptive = 0;
 }
 
 int ofks_create(ofks_ctx **out, int device) {
@@ -508,6 +514,7 @@ int ofks_set_params(ofks_ctx *c, const ofks_params *prm) {
     if (!(prm->beta >= 0) || !(prm->occ > 0) || !(prm->tol > 0) || prm->max_iter < 0 || prm->pcg_iters < 0 ||
         prm->eta_rule < 0 || prm->eta_rule > OFKS_ETA_FIXED || prm->precond < 0 || prm->precond > OFKS_PC_LEARNED ||
         !(prm->judge_tau > 0) || prm->learned_tc < 0 || prm->learned_tc > 1 ||
+        prm->poisson_adaptive < 0 || prm->poisson_adaptive > 1 ||
         (prm->precision != OFKS_FP64 && prm->precision != OFKS_MIXED) || !(prm->mixed_tol > 0) ||
         !(prm->poisson_tol_mixed > 0) || !(prm->eta_min > 0) || !(prm->eta_max >= prm->eta_min) ||
         prm->multipole_lmax < -1 || prm->multipole_lmax > 2 || !(prm->poisson_tol > 0) ||

@@ -401,7 +401,8 @@ int run_hartree(ofks_ctx *c) {
         k_cg_rz<<<gN, 256, 0, c->stream>>>(N, c->d_cr, c->d_cz, c->d_cp, sc, 0, 1);
         c->kernels += 1;
     }
-    const double ptol = c->phase == 32 ? std::max(c->prm.poisson_tol, c->prm.poisson_tol_mixed) : c->prm.poisson_tol;
+    double ptol = c->phase == 32 ? std::max(c->prm.poisson_tol, c->prm.poisson_tol_mixed) : c->prm.poisson_tol;
+    if (c->hartree_tol > 0.0) ptol = std::max(ptol, c->hartree_tol);
     const double tol2 = ptol * ptol;
     const int chunk = amg ? 4 : 32;
     int it = 0;

@@ -134,6 +134,7 @@ struct ofks_ctx {
     bool bx_valid = false;                       // d_BX holds B X for the current iterate
     int k = 0;
     int cg_last = 0;                             // CG iterations of the last Hartree solve
+    double hartree_tol = 0.0;                    // > 0: tolerance of the next Hartree solve (adaptive mode)
     int64_t cg_total = 0;                        // ... summed since the counter was cleared
     double kkt0 = 0.0, eta = 0.0;
     bool converged = false;

@@ -42,7 +42,8 @@ class Params(C.Structure):
                 ("eta_min", C.c_double), ("eta_max", C.c_double), ("hartree", C.c_int32),
                 ("xc", C.c_int32), ("multipole_lmax", C.c_int32), ("poisson_tol", C.c_double),
                 ("poisson_max_iter", C.c_int32), ("poisson_amg", C.c_int32), ("mixed_tol", C.c_double),
-                ("poisson_tol_mixed", C.c_double), ("judge_tau", C.c_double), ("learned_tc", C.c_int32)]
+                ("poisson_tol_mixed", C.c_double), ("judge_tau", C.c_double), ("learned_tc", C.c_int32),
+                ("poisson_adaptive", C.c_int32)]
 
 
 class Result(C.Structure):

@@ -4,8 +4,9 @@ TEST INFRASTRUCTURE ONLY (see the package header).
 
 The paper's preconditioner is D_i = T_i^{-1} G_i with T_i = L/2 - Lambda_ii B (Eq. precondition-T).
 The learned stand-in maps a gradient column to an approximate T_i^{-1} G_i with a small graph
-network on the free-DoF graph of the P2 mesh (one node per free degree of freedom, edges = the
-sparsity pattern of L).  Everything here is written out plainly so that the GPU kernels'
+network on the free-DoF graph of the P2 mesh (one node per free degree of freedom, an edge
+between two DoFs that share a tetrahedron: the structural pattern of L, which keeps the entries
+of the stiffness that happen to vanish for right-angled elements).  Everything here is written out plainly so that the GPU kernels'
 values and gradients can be checked against it.
 
 Per column c with shift lam_c (lam_c = Lambda_cc if negative, else 0):
@@ -25,6 +26,21 @@ import numpy as np
 import scipy.sparse as sp
 
 N_FEAT = 4
+
+
+def dof_graph(tet10: np.ndarray, dirichlet: np.ndarray) -> sp.csr_matrix:
+    """Free-DoF adjacency of the mesh: ones where two free DoFs share a tetrahedron (and on the
+    diagonal), whatever the values of L there."""
+    free = np.cumsum(dirichlet == 0) - 1
+    free[dirichlet != 0] = -1
+    T = free[tet10]
+    r = np.repeat(T, T.shape[1], axis=1).ravel()
+    c = np.tile(T, (1, T.shape[1])).ravel()
+    keep = (r >= 0) & (c >= 0)
+    n = int(np.sum(dirichlet == 0))
+    G = sp.csr_matrix((np.ones(int(keep.sum())), (r[keep], c[keep])), shape=(n, n))
+    G.data[:] = 1.0
+    return G
 
 
 def mean_aggregator(pattern: sp.csr_matrix) -> sp.csr_matrix:

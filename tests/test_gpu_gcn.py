@@ -53,7 +53,7 @@ def setup(ofks, width, seed=0):
     w = ctx.precond_get_weights()
     w = bf16(0.3 * rng.standard_normal(w.size).astype(np.float32))
     ctx.precond_set_weights(w)
-    A = gcn.mean_aggregator(pr.Lf)
+    A = gcn.mean_aggregator(gcn.dof_graph(m.tet10, m.dirichlet))
     return ctx, pr, G, shifts, w, A
 
 
@@ -88,8 +88,8 @@ def test_training_steps_reduce_the_loss(ofks):
     ctx, pr, G, shifts, w, A = setup(ofks, 16, seed=2)
     ctx.precond_init(16, 3)                 # last layer zero: starts as the Jacobi step
     Dstar = pr.precondition(G, shifts)
-    losses = [ctx.train_precond_step(G, shifts, Dstar, lr=3e-3) for _ in range(60)]
-    assert losses[-1] < 0.7 * losses[0], (losses[0], losses[-1])
+    losses = [ctx.train_precond_step(G, shifts, Dstar, lr=3e-3) for _ in range(100)]
+    assert losses[-1] < 0.75 * losses[0], (losses[0], losses[-1])
     ctx.close()
 
 

@@ -17,7 +17,7 @@ def tiny():
     m = I.make_mesh(s)
     pr = pcal.Problem(m.xyz, m.tet10, m.dirichlet, s.Z, s.R, pcal.Params(p=2, hartree=False, xc=False,
                                                                           precond="exact"))
-    A = gcn.mean_aggregator(pr.Lf)
+    A = gcn.mean_aggregator(gcn.dof_graph(m.tet10, m.dirichlet))
     rng = np.random.default_rng(4)
     G = rng.standard_normal((pr.n, 2))
     shifts = np.array([-0.8, -0.2])
@@ -77,3 +77,21 @@ def test_adam_steps_reduce_the_loss(tiny):
         params = gcn.adam_step(params, gcn.backward(params, cache, dy, A), state, lr=3e-3)
     D, _, _ = gcn.predict(params, f, s, A)
     assert gcn.loss_and_dy(D, Dstar, s)[0] < 0.7 * l0
+
+
+def test_dof_graph_is_the_mesh_adjacency():
+    # the graph holds every nonzero of the stiffness and the Kuhn-split P2 neighbourhoods:
+    # an interior cell vertex sees itself, its 14 edge neighbours, the 14 midpoints of those
+    # edges and the 36 midpoints of the edges of its link (a triangulated sphere with 14 vertices
+    # and 24 triangles, so 36 edges by Euler's formula): 65 DoFs
+    s = I.lih().with_cells((6, 4, 4))
+    m = I.make_mesh(s)
+    pr = pcal.Problem(m.xyz, m.tet10, m.dirichlet, s.Z, s.R, pcal.Params(p=2, hartree=False, xc=False))
+    Gr = gcn.dof_graph(m.tet10, m.dirichlet)
+    Lnz = pr.Lf.tocsr()
+    Lnz.data[:] = 1.0
+    assert (Lnz - Lnz.multiply(Gr)).nnz == 0
+    Lx, Ly, Lz = m.lattice
+    free = np.cumsum(m.dirichlet == 0) - 1
+    v = free[(4 * Ly + 4) * Lz + 4]
+    assert np.diff(Gr.indptr)[v] == 65

@@ -54,7 +54,8 @@ def config_of(args, s, sizes):
             "n_free": sizes["n"], "n_tets": sizes["n_tets"], "n_q": sizes["n_q"], "p": s.p, "occ": s.occ,
             "beta": 10.0, "form": "mixed: float32 iterations, float64 p x p / energy / tests (plain float64 beside it)",
             "precond": "PCG x8 (Eq. precondition-T)", "eta": "BB2",
-            "hartree": "Jacobi-CG, tolerance max(1e-12, min(1e-4, 0.01 (kkt+fea)/kkt0)) in both forms",
+            "hartree": ("CG on the lattice-stencil stiffness, separable (fast-diagonalization) preconditioner, "
+                        "tolerance max(1e-12, min(1e-4, 0.01 (kkt+fea)/kkt0)) in both forms"),
             "l2": "inputs larger than L2 (working set ~7 GB)", "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -119,17 +120,42 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# FP64 FMA peak of the GB300 (nominal 1.25 TFLOP/s dense FP64; measured by the fp64 probe
-# recorded in profiles/fp64_peak.md)
-FP64_PEAK_TFLOPS = 1.25
+# FMA peaks of the GB300 from its unit counts: 152 SMs x 2.07 GHz x 2 flops per FMA x
+# (2 float64 FMA or 128 float32 FMA per SM and clock)
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12       # 1.26
+FP32_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 128 / 1e12     # 80.5
 
 
-def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, nnz_full=0, n_nodes=0, elem=8):
+def poisson_spmv_model(sizes, pinfo):
+    """Algorithmic bytes and flops of one Hartree CG SpMV launch.  Lattice form: the stored
+    symmetric half once (8 B per value) plus, per computed row, its inverse-diagonal test, its own
+    p and the q it writes (24 B); neighbour p values are re-reads of the same vector.  CSR: 12 B
+    per stored entry, row pointers, and the four node vectors."""
+    nnz_full, n_nodes = sizes["nnz_full"], sizes["n_nodes"]
+    if pinfo and pinfo["format"] == "lattice":
+        return 8 * pinfo["stored"] + 24 * pinfo["rows"], 2 * nnz_full
+    return 12 * nnz_full + 32 * n_nodes, 2 * nnz_full
+
+
+def separable_model(pinfo):
+    """One application of the separable preconditioner: six float32 axis contractions of the
+    interior tensor (2 n_t n_d flops each, both directions) plus gather and scatter; bytes: the
+    tensor read and written by each pass (4 B) and the float64 vectors it starts and ends on."""
+    lat = pinfo.get("lattice") if pinfo else None
+    if not lat or not all(lat):
+        return 0, 0
+    nx, ny, nz = (d - 2 for d in lat)
+    nt = nx * ny * nz
+    return nt * (6 * 8 + 12 + 12) + 8 * (nx * nx + ny * ny + nz * nz), 4 * nt * (nx + ny + nz)
+
+
+def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, spmv_model=(0, 0), elem=8, pc_model=(0, 0)):
     """Dominant kernel family by time: algorithmic bytes and flops per launch / mean duration.
 
     Every family is one kernel launch per timed scope except "poisson" (the whole Hartree
-    solve), which is left out of the choice; its SpMV kernel is the "poisson_spmv" family."""
-    leaves = {k: v for k, v in prof.items() if k != "poisson" and v["launches"]}
+    solve) and "poisson_vec" (two vector kernels per CG iteration), which are left out of the
+    choice; the solve's SpMV kernel is the "poisson_spmv" family."""
+    leaves = {k: v for k, v in prof.items() if k not in ("poisson", "poisson_vec") and v["launches"]}
     fam = max(leaves, key=lambda k: leaves[k]["ms"])
     st = prof[fam]
     per = st["ms"] / max(st["launches"], 1) * 1e-3
@@ -141,17 +167,20 @@ def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, nnz_full=0, n_nodes=0,
         "gram": (3 * s * n * p, 2 * n * p * p),
         "grad": (3 * s * n * p, 4 * n * p * p),
         "density": (s * n * p + n_tets * (40 + 32), n_tets * 4 * (20 * p + 2 * p)),
-        "poisson_spmv": (12 * nnz_full + 32 * n_nodes, 2 * nnz_full),
+        "poisson_spmv": spmv_model,
+        "poisson_pc": pc_model,
     }
     bytes_, flops = model.get(fam, (0, 0))
     gbs = bytes_ / per / 1e9
     tflops = flops / per / 1e12
     f_hbm = gbs / hbm_peak
-    f_alu = tflops / FP64_PEAK_TFLOPS if (elem == 8 or fam == "poisson_spmv") else 0.0
+    fp32 = fam == "poisson_pc" or (elem == 4 and fam != "poisson_spmv")
+    alu_peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
+    f_alu = tflops / alu_peak
     if f_alu >= f_hbm:
-        return {"bound": "alu", "kernel": fam, "achieved": round(tflops, 4), "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s (fp64)", "frac": round(f_alu, 4), "traffic": None,
-                "hbm_gbs": round(gbs, 1), "hbm_frac": round(f_hbm, 4), "peak_kind": "nominal fp64",
+        return {"bound": "alu", "kernel": fam, "achieved": round(tflops, 4), "peak": round(alu_peak, 2),
+                "unit": "TFLOP/s (fp32)" if fp32 else "TFLOP/s (fp64)", "frac": round(f_alu, 4), "traffic": None,
+                "hbm_gbs": round(gbs, 1), "hbm_frac": round(f_hbm, 4), "peak_kind": "unit counts x max clock",
                 "mean_launch_ms": round(per * 1e3, 4), "launches": st["launches"]}
     return {"bound": "hbm", "kernel": fam, "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
             "frac": round(f_hbm, 4), "traffic": None, "fp64_tflops": round(tflops, 4),
@@ -221,6 +250,7 @@ def run_reference(args):
     m = I.make_mesh(s)
     from oracle import pcal
     pr = oracle_problem(s, m)
+    st = pcal.State(X=pr.initial_guess(I.initial_block(pr.n, s.p, 0)))
     # each step is one oracle iteration (~30-60 s on the host cores at this size): the warm-up
     # is a single step and at most 3 steps are timed, so the run ends within a few minutes
     pcal.iterate(pr, st)
@@ -312,6 +342,7 @@ def main():
     steps_done = res["iters"] - args.warmup
     value = world * steps_done / t
     sizes = ctx.sizes()
+    pinfo = ctx.poisson_info()
 
     # end to end through the C ABI with host buffers (pinned)
     e2e = None
@@ -342,10 +373,9 @@ def main():
     if rank != 0:
         return
     hbm_peak, hbm_kind = peaks()
-    roof = roofline(prof, sizes["n_free"], s.p, sizes["nnz"], sizes["n_tets"], hbm_peak, hbm_kind,
-                    sizes["nnz_full"], sizes["n_nodes"], elem=4)
-    roof64 = roofline(prof64, sizes["n_free"], s.p, sizes["nnz"], sizes["n_tets"], hbm_peak, hbm_kind,
-                      sizes["nnz_full"], sizes["n_nodes"], elem=8)
+    sm, pm = poisson_spmv_model(sizes, pinfo), separable_model(pinfo)
+    roof = roofline(prof, sizes["n_free"], s.p, sizes["nnz"], sizes["n_tets"], hbm_peak, hbm_kind, sm, 4, pm)
+    roof64 = roofline(prof64, sizes["n_free"], s.p, sizes["nnz"], sizes["n_tets"], hbm_peak, hbm_kind, sm, 8, pm)
     ttc = None if args.no_ttc else time_to_target(ofks, I)
     cpu = None
     if not args.no_cpu and world == 1:
@@ -358,6 +388,7 @@ def main():
            "kernel_launches": {k: v["launches"] for k, v in prof.items() if v["launches"]},
            "clocks": clocks, "E": res["e_total"], "kkt": res["kkt"], "fea": res["fea"],
            "hartree_cg_iters_per_step": round(res["hartree_total"] / max(steps_done, 1), 1),
+           "hartree_operator": pinfo,
            "plain_fp64": {"value": round(world * steps64 / t64, 4), "unit": UNIT,
                           "ms_per_step": round(t64 / steps64 * 1e3, 3), "gpu_launches": launches64,
                           "roofline": roof64, "kernel_ms": {k: round(v["ms"], 3) for k, v in prof64.items()

@@ -78,6 +78,16 @@ extern "C" {
 
 typedef struct ofks_ctx ofks_ctx;   /* opaque, owned by the library */
 
+/* Preconditioners of the Hartree CG (ofks_params.poisson_pc). */
+enum {
+    OFKS_HPC_JACOBI = 0,     /* point Jacobi (inverse diagonal) */
+    OFKS_HPC_MULTIGRID = 1,  /* V(2,2) cycle: P2 -> P1, then lattice coarsening (lattice meshes) or
+                                smoothed aggregation (other meshes), damped Jacobi smoothing */
+    OFKS_HPC_SEPARABLE = 2   /* lattice meshes: exact inverse of the separable Kronecker-sum operator
+                                Kx(x)My(x)Mz + Mx(x)Ky(x)Mz + Mx(x)My(x)Kz (1-D linear stiffness K and
+                                lumped mass M on the lattice coordinates) by fast diagonalization */
+};
+
 typedef struct {
     int32_t p;              /* number of orbitals (columns of X) */
     double  beta;           /* penalty parameter of L_beta (paper Eq. ALM-sub) */
@@ -95,13 +105,16 @@ typedef struct {
     int32_t multipole_lmax; /* Hartree boundary data: multipoles up to l (0..2); -1: zero */
     double  poisson_tol;    /* relative residual of the Hartree CG solve */
     int32_t poisson_max_iter;
-    int32_t poisson_amg;    /* 1: CG preconditioned by the algebraic multigrid V-cycle; 0: Jacobi */
+    int32_t poisson_pc;     /* Hartree CG preconditioner: OFKS_HPC_JACOBI, OFKS_HPC_MULTIGRID or
+                               OFKS_HPC_SEPARABLE (falls back to Jacobi where the mesh has none) */
     double  mixed_tol;      /* OFKS_MIXED: hand over to float64 once (kkt+fea)/kkt0 < mixed_tol */
     double  poisson_tol_mixed; /* Hartree CG tolerance during the float32 iterations */
     double  judge_tau;      /* OFKS_PC_LEARNED: accept a column if |G - T D| <= judge_tau |G| and G.D > 0 */
     int32_t learned_tc;     /* 1: width-64 hidden layer on the tensor cores (bf16 operands) at inference */
     int32_t poisson_adaptive; /* 1: Hartree CG tolerance max(poisson_tol, min(1e-4, 0.01 (kkt+fea)/kkt0))
                                  from the previous iterate (inexact potentials early, exact at the end) */
+    int32_t poisson_csr;    /* 1: Hartree CG on the general CSR stiffness even when the mesh's node ids
+                               follow a lattice (default 0: the lattice-stencil form when available) */
 } ofks_params;
 
 typedef struct {
@@ -123,8 +136,8 @@ typedef struct {
 
 /* Fill *prm with the defaults: beta 10, occ 2, tol 1e-8, max_iter 1000, FP64, PCG with 8
  * iterations, BB2, eta in [1e-4, 1e8], Hartree and LDA on, multipole_lmax 2,
- * poisson_tol 1e-12, poisson_max_iter 20000, poisson_amg 0, mixed_tol 1e-5, poisson_tol_mixed
- * 1e-8, judge_tau 0.5, learned_tc 1, poisson_adaptive 0.  p is set to 1. */
+ * poisson_tol 1e-12, poisson_max_iter 20000, poisson_pc OFKS_HPC_SEPARABLE, mixed_tol 1e-5, poisson_tol_mixed
+ * 1e-8, judge_tau 0.5, learned_tc 1, poisson_adaptive 0, poisson_csr 0.  p is set to 1. */
 void ofks_default_params(ofks_params *prm);
 
 /* Create a context on CUDA device `device`.  *out receives the context (NULL on failure).
@@ -219,6 +232,17 @@ int ofks_apply(ofks_ctx *ctx, int32_t which, const double *X, double *Y, int32_t
  * be NULL. */
 int ofks_get_sizes(ofks_ctx *ctx, int64_t *n_free, int64_t *n_nodes, int64_t *n_tets,
                    int64_t *nnz, int64_t *nnz_full);
+
+/* Storage of the Hartree Poisson operator (the all-node stiffness of Sec. 2.2).  *format = 1 when
+ * the node ids follow a lattice, id = (a Ly + b) Lz + c with every stiffness neighbour within two
+ * lattice steps, and the CG SpMV runs on the lattice-stencil form: no column indices, the
+ * symmetric half stored once per node type (8 parity classes); 0 for the general CSR.
+ * *stored = float64 values of the form in use, *rows = rows its SpMV computes (non-Dirichlet),
+ * lattice[3] = (Lx, Ly, Lz) or zeros, *precond = the OFKS_HPC_* preconditioner the next solve uses
+ * (after the fallback to Jacobi on meshes without the requested one).  Any pointer may be NULL.
+ * Errors: OFKS_EINVAL, OFKS_ESTATE. */
+int ofks_poisson_info(ofks_ctx *ctx, int32_t *format, int64_t *stored, int64_t *rows, int32_t *lattice,
+                      int32_t *precond);
 
 /* History of evaluated iterates: rows of 6 doubles (k, seconds since init, E, kkt, fea,
  * eta).  Copies min(cap, available) rows of the most recent ones into buf; *len = rows. */

@@ -1,8 +1,14 @@
-// Smoothed-aggregation algebraic multigrid for the Hartree Poisson system L_II U_I = f_I
-// (paper Sec. 2.2 solves this system by algebraic multigrid).  The hierarchy is built once per
-// mesh on the host (aggregation, smoothed prolongators P = (I - w D^-1 A) T, Galerkin
-// products A_c = P^T A P, dense Cholesky of the coarsest operator); every V-cycle runs in the
-// kernels below and preconditions the CG of the Hartree solve.
+// Multigrid preconditioner for the Hartree Poisson system L_II U_I = f_I (paper Sec. 2.2 solves
+// this system by multigrid).  Level 0 -> 1 is the geometric P2 -> P1 interpolation on the same
+// mesh (vertex values copied, an edge midpoint takes the mean of its two vertices), so level 1
+// is the P1 stiffness.  Below that:
+//   * lattice meshes (node ids on a lattice whose faces are the Dirichlet boundary): geometric
+//     coarsening of the vertex lattice, every other coordinate per axis, with per-axis linear
+//     interpolation in the actual (graded) coordinates and Galerkin operators A_c = P^T A P;
+//     level 0 smooths and forms residuals with the lattice-stencil kernels on full-node vectors;
+//   * other meshes: smoothed aggregation, P = (I - w D^-1 A) T.
+// The hierarchy is built once per mesh on the host (Galerkin products, dense Cholesky inverse of
+// the coarsest operator); every V-cycle runs in the kernels below and preconditions the CG.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -251,6 +257,71 @@ void free_csr(AmgMat &M) {
 inline unsigned g8(int64_t n) { return (unsigned)((n * 8 + 255) / 256); }
 inline unsigned g1(int64_t n) { return (unsigned)((n + 255) / 256); }
 
+// One axis of a lattice level: coordinates (boundary included) and the interpolation of every
+// fine index from the coarse indices {0, 2, 4, ...} plus the last one; axes of 3 or fewer
+// points are not coarsened.
+struct AxisMap {
+    std::vector<double> xc;                       // coarse coordinates
+    std::vector<int> c0, c1;                      // coarse neighbours of fine index i (c1 = -1: copy)
+    std::vector<double> w0, w1;
+};
+
+AxisMap coarsen_axis(const std::vector<double> &x) {
+    const int n = (int)x.size();
+    AxisMap M;
+    M.c0.assign(n, -1); M.c1.assign(n, -1); M.w0.assign(n, 0.0); M.w1.assign(n, 0.0);
+    std::vector<int> cidx(n, -1);
+    if (n <= 3) {
+        for (int i = 0; i < n; ++i) { cidx[i] = i; M.xc.push_back(x[i]); }
+    } else {
+        for (int i = 0; i < n; i += 2) { cidx[i] = (int)M.xc.size(); M.xc.push_back(x[i]); }
+        if (cidx[n - 1] < 0) { cidx[n - 1] = (int)M.xc.size(); M.xc.push_back(x[n - 1]); }
+    }
+    for (int i = 0; i < n; ++i) {
+        if (cidx[i] >= 0) { M.c0[i] = cidx[i]; M.w0[i] = 1.0; continue; }
+        const double t = (x[i] - x[i - 1]) / (x[i + 1] - x[i - 1]);
+        M.c0[i] = cidx[i - 1]; M.w0[i] = 1.0 - t;
+        M.c1[i] = cidx[i + 1]; M.w1[i] = t;
+    }
+    return M;
+}
+
+// Tensor-product interpolation from the interior of the coarse lattice to the interior of the
+// fine one (both numbered lexicographically over interior points; boundary values are zero).
+Csr lattice_prolongator(const AxisMap ax[3], const int nf[3]) {
+    int nc[3];
+    for (int d = 0; d < 3; ++d) nc[d] = (int)ax[d].xc.size();
+    const int64_t fi[3] = {nf[0] - 2, nf[1] - 2, nf[2] - 2}, ci[3] = {nc[0] - 2, nc[1] - 2, nc[2] - 2};
+    Csr P;
+    P.n = fi[0] * fi[1] * fi[2];
+    P.m = ci[0] * ci[1] * ci[2];
+    P.ptr.assign(P.n + 1, 0);
+    auto terms = [&](int d, int i, int *cc, double *ww) {
+        int k = 0;
+        const int c0 = ax[d].c0[i], c1 = ax[d].c1[i];
+        if (c0 > 0 && c0 < nc[d] - 1) { cc[k] = c0 - 1; ww[k++] = ax[d].w0[i]; }
+        if (c1 > 0 && c1 < nc[d] - 1) { cc[k] = c1 - 1; ww[k++] = ax[d].w1[i]; }
+        return k;
+    };
+    for (int a = 1; a < nf[0] - 1; ++a)
+        for (int b = 1; b < nf[1] - 1; ++b)
+            for (int cz = 1; cz < nf[2] - 1; ++cz) {
+                int ca[2], cb[2], cc[2];
+                double wa[2], wb[2], wc[2];
+                const int na = terms(0, a, ca, wa), nb = terms(1, b, cb, wb), ncz = terms(2, cz, cc, wc);
+                std::vector<std::pair<int, double>> row;
+                for (int i = 0; i < na; ++i)
+                    for (int j = 0; j < nb; ++j)
+                        for (int k = 0; k < ncz; ++k)
+                            row.push_back({(int)(((int64_t)ca[i] * ci[1] + cb[j]) * ci[2] + cc[k]), wa[i] * wb[j] * wc[k]});
+                std::sort(row.begin(), row.end());
+                for (auto &e : row) { P.col.push_back(e.first); P.val.push_back(e.second); }
+                const int64_t r = ((int64_t)(a - 1) * fi[1] + (b - 1)) * fi[2] + (cz - 1);
+                P.ptr[r + 1] = (int64_t)P.col.size();
+            }
+    return P;
+}
+
 }  // namespace
 
 void amg_free(ofks_ctx *c) {
@@ -264,13 +335,33 @@ void amg_free(ofks_ctx *c) {
     c->d_amg_chol = nullptr;
     c->d_amg_idx = nullptr;
     c->amg_nc = 0;
+    c->amg_lat = false;
 }
 
-// Build the hierarchy from the device-assembled full-node stiffness.  Level 0 -> 1 is the
-// geometric P2 -> P1 interpolation on the same mesh (vertex values copied, an edge midpoint
-// takes the mean of its two vertices), so level 1 is the P1 stiffness; coarser levels come
-// from smoothed aggregation of that sparse operator.
-int amg_setup(ofks_ctx *c, const int *tetn, int64_t T) {
+namespace {
+
+// rows of P restricted to the interior nodes -> rows over all nodes (Dirichlet rows empty)
+Csr expand_rows(const Csr &P, const std::vector<int> &iid, int64_t N) {
+    Csr F;
+    F.n = N; F.m = P.m;
+    F.ptr.assign(N + 1, 0);
+    for (int64_t r = 0; r < P.n; ++r) F.ptr[iid[r] + 1] = P.ptr[r + 1] - P.ptr[r];
+    for (int64_t i = 0; i < N; ++i) F.ptr[i + 1] += F.ptr[i];
+    F.col.resize(P.col.size());
+    F.val.resize(P.val.size());
+    for (int64_t r = 0; r < P.n; ++r) {
+        const int64_t o = F.ptr[iid[r]];
+        for (int64_t k = P.ptr[r]; k < P.ptr[r + 1]; ++k) {
+            F.col[o + k - P.ptr[r]] = P.col[k];
+            F.val[o + k - P.ptr[r]] = P.val[k];
+        }
+    }
+    return F;
+}
+
+}  // namespace
+
+int amg_setup(ofks_ctx *c, const int *tetn, int64_t T, const double *xyz) {
     amg_free(c);
     const int64_t N = c->n_nodes;
     std::vector<int> fptr(N + 1), fcol(c->nnz_full), interior(N);
@@ -295,14 +386,34 @@ int amg_setup(ofks_ctx *c, const int *tetn, int64_t T) {
     int rc;
     if ((rc = up(c, &c->d_amg_idx, iid.data(), iid.size()))) return rc;
     c->amg_ni = A.n;
-    // P2 -> P1 interpolation restricted to interior nodes
+
+    // lattice hierarchy: odd lattice extents (2 N + 1 per axis, the cell vertices at even
+    // coordinates) and Dirichlet nodes exactly on the lattice faces
+    const int Lx = c->st.Lx, Ly = c->st.Ly, Lz = c->st.Lz;
+    bool lat = c->st.on && (Lx & 1) && (Ly & 1) && (Lz & 1) && Lx >= 5 && Ly >= 5 && Lz >= 5;
+    for (int64_t i = 0; i < N && lat; ++i) {
+        const int64_t a = i / ((int64_t)Ly * Lz), b = (i / Lz) % Ly, cz = i % Lz;
+        const bool face = a == 0 || a == Lx - 1 || b == 0 || b == Ly - 1 || cz == 0 || cz == Lz - 1;
+        if (face != (minv[i] == 0.0)) lat = false;
+    }
+    const int V[3] = {(Lx + 1) / 2, (Ly + 1) / 2, (Lz + 1) / 2};   // vertex lattice (lattice mode)
+
+    // P2 -> P1 interpolation restricted to interior nodes; vertex unknowns numbered in tet order,
+    // or lexicographically over the interior of the vertex lattice in lattice mode
     std::vector<int> vnum(N, -1), ea(N, -1), eb(N, -1);
     int64_t nv = 0;
-    for (int64_t t = 0; t < T; ++t)
-        for (int a = 0; a < 4; ++a) {
-            const int v = tetn[t * 10 + a];
-            if (inum[v] >= 0 && vnum[v] < 0) vnum[v] = (int)nv++;
-        }
+    if (lat) {
+        for (int i = 1; i < V[0] - 1; ++i)
+            for (int j = 1; j < V[1] - 1; ++j)
+                for (int k = 1; k < V[2] - 1; ++k)
+                    vnum[((int64_t)(2 * i) * Ly + 2 * j) * Lz + 2 * k] = (int)nv++;
+    } else {
+        for (int64_t t = 0; t < T; ++t)
+            for (int a = 0; a < 4; ++a) {
+                const int v = tetn[t * 10 + a];
+                if (inum[v] >= 0 && vnum[v] < 0) vnum[v] = (int)nv++;
+            }
+    }
     for (int64_t t = 0; t < T; ++t)
         for (int e = 0; e < 6; ++e) {
             int a, b;
@@ -329,25 +440,63 @@ int amg_setup(ofks_ctx *c, const int *tetn, int64_t T) {
         P1.ptr[r + 1] = (int64_t)P1.col.size();
     }
     const bool geometric = nv > 0 && nv < A.n;
+    lat = lat && geometric;
+    // lattice mode: per-axis coordinates of the vertex lattice
+    int dims[3] = {V[0], V[1], V[2]};
+    std::vector<double> coord[3];
+    if (lat) {
+        for (int i = 0; i < V[0]; ++i) coord[0].push_back(xyz[3 * ((int64_t)(2 * i) * Ly * Lz)]);
+        for (int j = 0; j < V[1]; ++j) coord[1].push_back(xyz[3 * ((int64_t)(2 * j) * Lz) + 1]);
+        for (int k = 0; k < V[2]; ++k) coord[2].push_back(xyz[3 * (int64_t)(2 * k) + 2]);
+    }
+    const bool verbose = std::getenv("OFKS_VERBOSE") != nullptr;
     for (int lev = 0; lev < MAX_LEVELS; ++lev) {
         AmgLevel L;
         std::vector<double> dinv(A.n);
         for (int64_t i = 0; i < A.n; ++i) dinv[i] = 1.0 / diag_of(A, i);
         const double rho = spectral_radius(A, dinv);
         L.omega = 4.0 / (3.0 * rho);
-        if ((rc = up_csr(c, A, L.A)) || (rc = up(c, &L.dinv, dinv.data(), dinv.size()))) return rc;
-        const bool last = A.n <= COARSE_MAX || lev == MAX_LEVELS - 1;
+        const bool on_stencil = lat && lev == 0;          // level 0 runs on the lattice stencil
+        if (!on_stencil && ((rc = up_csr(c, A, L.A)) || (rc = up(c, &L.dinv, dinv.data(), dinv.size())))) return rc;
+        if (on_stencil) { L.A.n = N; L.A.m = N; }
+        bool last = A.n <= COARSE_MAX || lev == MAX_LEVELS - 1;
         if (!last && lev == 0 && geometric) {
             Csr R = transpose(P1);
             Csr AP = spgemm(A, P1);
             Csr Ac = spgemm(R, AP);
-            if (std::getenv("OFKS_VERBOSE"))
-                std::fprintf(stderr, "[ofks amg] level 0 (P2->P1): n=%lld nnz(A)=%lld coarse n=%lld omega=%.4f\n",
-                             (long long)A.n, (long long)A.ptr[A.n], (long long)nv, L.omega);
-            if ((rc = up_csr(c, P1, L.P)) || (rc = up_csr(c, R, L.R))) return rc;
+            if (verbose)
+                std::fprintf(stderr, "[ofks mg] level 0 (P2->P1%s): n=%lld nnz(A)=%lld coarse n=%lld omega=%.4f\n",
+                             lat ? ", lattice" : "", (long long)A.n, (long long)A.ptr[A.n], (long long)nv, L.omega);
+            if (on_stencil) {
+                Csr PF = expand_rows(P1, iid, N);
+                Csr RF = transpose(PF);
+                if ((rc = up_csr(c, PF, L.P)) || (rc = up_csr(c, RF, L.R))) return rc;
+            } else if ((rc = up_csr(c, P1, L.P)) || (rc = up_csr(c, R, L.R))) {
+                return rc;
+            }
             c->amg.push_back(L);
             A = std::move(Ac);
             continue;
+        }
+        if (!last && lat) {
+            if (dims[0] <= 3 && dims[1] <= 3 && dims[2] <= 3) last = true;
+            if (!last) {
+                AxisMap ax[3] = {coarsen_axis(coord[0]), coarsen_axis(coord[1]), coarsen_axis(coord[2])};
+                Csr P = lattice_prolongator(ax, dims);
+                if (P.n != A.n) return ofks_fail(c, OFKS_EINVAL, "MG: lattice level size mismatch");
+                Csr R = transpose(P);
+                Csr AP = spgemm(A, P);
+                Csr Ac = spgemm(R, AP);
+                if (verbose)
+                    std::fprintf(stderr, "[ofks mg] level %d (lattice %dx%dx%d): n=%lld nnz(A)=%lld coarse n=%lld omega=%.4f\n",
+                                 lev, dims[0], dims[1], dims[2], (long long)A.n, (long long)A.ptr[A.n],
+                                 (long long)P.m, L.omega);
+                if ((rc = up_csr(c, P, L.P)) || (rc = up_csr(c, R, L.R))) return rc;
+                c->amg.push_back(L);
+                A = std::move(Ac);
+                for (int d = 0; d < 3; ++d) { coord[d] = ax[d].xc; dims[d] = (int)coord[d].size(); }
+                continue;
+            }
         }
         if (!last) {
             std::vector<int> agg;
@@ -359,23 +508,23 @@ int amg_setup(ofks_ctx *c, const int *tetn, int64_t T) {
             std::vector<double> tw(na, 0.0);
             for (int64_t i = 0; i < A.n; ++i) tw[agg[i]] += 1.0;
             for (auto &t : tw) t = 1.0 / std::sqrt(t);
-            Csr T;                                          // tentative prolongator
-            T.n = A.n; T.m = na;
-            T.ptr.resize(A.n + 1);
-            T.col.resize(A.n);
-            T.val.resize(A.n);
-            for (int64_t i = 0; i < A.n; ++i) { T.ptr[i] = i; T.col[i] = agg[i]; T.val[i] = tw[agg[i]]; }
-            T.ptr[A.n] = A.n;
+            Csr Tt;                                         // tentative prolongator
+            Tt.n = A.n; Tt.m = na;
+            Tt.ptr.resize(A.n + 1);
+            Tt.col.resize(A.n);
+            Tt.val.resize(A.n);
+            for (int64_t i = 0; i < A.n; ++i) { Tt.ptr[i] = i; Tt.col[i] = agg[i]; Tt.val[i] = tw[agg[i]]; }
+            Tt.ptr[A.n] = A.n;
             Csr S = A;                                      // S = I - w D^-1 A
             for (int64_t i = 0; i < A.n; ++i)
                 for (int64_t k = S.ptr[i]; k < S.ptr[i + 1]; ++k)
                     S.val[k] = (S.col[k] == i ? 1.0 : 0.0) - L.omega * dinv[i] * A.val[k];
-            Csr P = spgemm(S, T);
+            Csr P = spgemm(S, Tt);
             Csr R = transpose(P);
             Csr AP = spgemm(A, P);
             Csr Ac = spgemm(R, AP);
-            if (std::getenv("OFKS_VERBOSE"))
-                std::fprintf(stderr, "[ofks amg] level %d: n=%lld nnz(A)=%lld nnz(P)=%lld aggregates=%lld omega=%.4f\n",
+            if (verbose)
+                std::fprintf(stderr, "[ofks mg] level %d: n=%lld nnz(A)=%lld nnz(P)=%lld aggregates=%lld omega=%.4f\n",
                              lev, (long long)A.n, (long long)A.ptr[A.n], (long long)P.ptr[P.n], (long long)na, L.omega);
             if ((rc = up_csr(c, P, L.P)) || (rc = up_csr(c, R, L.R))) return rc;
             c->amg.push_back(L);
@@ -388,6 +537,7 @@ int amg_setup(ofks_ctx *c, const int *tetn, int64_t T) {
     // dense inverse of the coarsest operator through its Cholesky factor
     const int64_t nc = A.n;
     if (nc > 4096) return ofks_fail(c, OFKS_ENOTCONV, "AMG: coarsening stalled at %lld unknowns", (long long)nc);
+    if (verbose) std::fprintf(stderr, "[ofks mg] coarsest: n=%lld (dense)\n", (long long)nc);
     std::vector<double> Lf((size_t)nc * nc, 0.0), Dm((size_t)nc * nc, 0.0);
     for (int64_t i = 0; i < nc; ++i)
         for (int64_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) Lf[(size_t)i * nc + A.col[k]] = A.val[k];
@@ -423,13 +573,19 @@ int amg_setup(ofks_ctx *c, const int *tetn, int64_t T) {
         if (cudaMalloc((void **)&L.x, bytes) != cudaSuccess || cudaMalloc((void **)&L.x2, bytes) != cudaSuccess ||
             cudaMalloc((void **)&L.b, bytes) != cudaSuccess || cudaMalloc((void **)&L.r, bytes) != cudaSuccess)
             return ofks_fail(c, OFKS_ENOMEM, "AMG: level vectors");
+        // full-node level-0 vectors keep zero Dirichlet entries: the stencil kernels never write them
+        if (cudaMemset(L.x, 0, bytes) != cudaSuccess || cudaMemset(L.x2, 0, bytes) != cudaSuccess ||
+            cudaMemset(L.r, 0, bytes) != cudaSuccess)
+            return ofks_fail(c, OFKS_ECUDA, "AMG: level vectors");
     }
+    c->amg_lat = lat;
     return OFKS_OK;
 }
 
-// z = M^-1 r on the interior nodes by one symmetric V(2,2) cycle; r and z are full-node vectors
-// whose boundary entries are zero.
-static void vcycle(ofks_ctx *c, size_t l) {
+// x = M^-1 b on level l by one symmetric V(nu,nu) cycle; level l's b holds the right side and
+// its x receives the result.  In lattice mode level 0 works on full-node vectors through the
+// stencil kernels (b and x are then the caller's vectors, Dirichlet entries zero).
+static void vcycle(ofks_ctx *c, size_t l, const double *b0 = nullptr, double *x0 = nullptr) {
     AmgLevel &L = c->amg[l];
     cudaStream_t s = c->stream;
     if (l + 1 == c->amg.size()) {
@@ -439,8 +595,27 @@ static void vcycle(ofks_ctx *c, size_t l) {
         return;
     }
     const int64_t n = L.A.n;
-    // pre-smoothing from zero: x = w D^-1 b, then nu - 1 damped Jacobi sweeps
     const int nu = l == 0 ? SWEEPS0 : SWEEPS;
+    AmgLevel &C = c->amg[l + 1];
+    if (l == 0 && c->amg_lat) {
+        const double *b = b0;
+        double *x = x0, *y = L.x2;
+        k_scaled<<<g1(n), 256, 0, s>>>(n, b, c->d_minv, L.omega, x);   // pre-smoothing from zero
+        c->kernels += 1;
+        for (int it = 1; it < nu; ++it) { launch_stencil_jacobi(c, x, b, L.omega, y); std::swap(x, y); }
+        launch_stencil_residual(c, x, b, L.r);
+        k_csr<0><<<g8(C.A.n), 256, 0, s>>>(C.A.n, L.R.ptr, L.R.col, L.R.val, L.r, nullptr, nullptr, 0.0, C.b);
+        c->kernels += 1;
+        vcycle(c, l + 1);
+        k_csr<3><<<g8(n), 256, 0, s>>>(n, L.P.ptr, L.P.col, L.P.val, C.x, nullptr, nullptr, 0.0, x);
+        c->kernels += 1;
+        for (int it = 0; it < nu; ++it) { launch_stencil_jacobi(c, x, b, L.omega, y); std::swap(x, y); }
+        if (x != x0) {
+            cudaMemcpyAsync(x0, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+        }
+        return;
+    }
+    // pre-smoothing from zero: x = w D^-1 b, then nu - 1 damped Jacobi sweeps
     k_scaled<<<g1(n), 256, 0, s>>>(n, L.b, L.dinv, L.omega, L.x);
     for (int it = 1; it < nu; ++it) {
         k_csr<2><<<g8(n), 256, 0, s>>>(n, L.A.ptr, L.A.col, L.A.val, L.x, L.b, L.dinv, L.omega, L.x2);
@@ -448,7 +623,6 @@ static void vcycle(ofks_ctx *c, size_t l) {
     }
     c->kernels += nu;
     k_csr<1><<<g8(n), 256, 0, s>>>(n, L.A.ptr, L.A.col, L.A.val, L.x, L.b, nullptr, 0.0, L.r);
-    AmgLevel &C = c->amg[l + 1];
     k_csr<0><<<g8(C.A.n), 256, 0, s>>>(C.A.n, L.R.ptr, L.R.col, L.R.val, L.r, nullptr, nullptr, 0.0, C.b);
     c->kernels += 2;
     vcycle(c, l + 1);
@@ -461,6 +635,10 @@ static void vcycle(ofks_ctx *c, size_t l) {
 }
 
 void amg_apply(ofks_ctx *c, const double *r_full, double *z_full) {
+    if (c->amg_lat) {   // full-node vectors throughout level 0
+        vcycle(c, 0, r_full, z_full);
+        return;
+    }
     const int64_t ni = c->amg_ni;
     AmgLevel &L0 = c->amg[0];
     k_gather<<<g1(ni), 256, 0, c->stream>>>(ni, c->d_amg_idx, r_full, L0.b);

@@ -20,7 +20,7 @@
 
 static const char *kPfNames[PF_COUNT] = {"density", "poisson", "potential", "spmm_h", "gram", "small",
                                          "grad", "pcg_spmm", "pcg_update", "bb", "step", "spmm_b", "other",
-                                         "poisson_spmv", "gcn"};
+                                         "poisson_spmv", "gcn", "poisson_vec", "poisson_pc"};
 
 int ofks_fail(ofks_ctx *c, int code, const char *fmt, ...) {
     char buf[512];
@@ -425,9 +425,9 @@ void ofks_default_params(ofks_params *p) {
     p->precision = OFKS_FP64; p->precond = OFKS_PC_PCG; p->pcg_iters = 8; p->eta_rule = OFKS_ETA_BB2;
     p->eta_fixed = 0.0; p->eta_min = 1e-4; p->eta_max = 1e8; p->hartree = 1; p->xc = 1;
     p->multipole_lmax = 2; p->poisson_tol = 1e-12; p->poisson_max_iter = 20000;
-    p->poisson_amg = 0;
+    p->poisson_pc = OFKS_HPC_SEPARABLE;
     p->mixed_tol = 1e-5; p->poisson_tol_mixed = 1e-8;
-    p->judge_tau = 0.5; p->learned_tc = 1; p->poisson_adaptive = 0;
+    p->judge_tau = 0.5; p->learned_tc = 1; p->poisson_adaptive = 0; p->poisson_csr = 0;
 }
 
 int ofks_create(ofks_ctx **out, int device) {
@@ -515,10 +515,11 @@ int ofks_set_params(ofks_ctx *c, const ofks_params *prm) {
         prm->eta_rule < 0 || prm->eta_rule > OFKS_ETA_FIXED || prm->precond < 0 || prm->precond > OFKS_PC_LEARNED ||
         !(prm->judge_tau > 0) || prm->learned_tc < 0 || prm->learned_tc > 1 ||
         prm->poisson_adaptive < 0 || prm->poisson_adaptive > 1 ||
+        prm->poisson_csr < 0 || prm->poisson_csr > 1 ||
         (prm->precision != OFKS_FP64 && prm->precision != OFKS_MIXED) || !(prm->mixed_tol > 0) ||
         !(prm->poisson_tol_mixed > 0) || !(prm->eta_min > 0) || !(prm->eta_max >= prm->eta_min) ||
         prm->multipole_lmax < -1 || prm->multipole_lmax > 2 || !(prm->poisson_tol > 0) ||
-        prm->poisson_max_iter < 1 || prm->poisson_amg < 0 || prm->poisson_amg > 1 || (prm->eta_rule == OFKS_ETA_FIXED && !(prm->eta_fixed > 0)))
+        prm->poisson_max_iter < 1 || prm->poisson_pc < 0 || prm->poisson_pc > OFKS_HPC_SEPARABLE || (prm->eta_rule == OFKS_ETA_FIXED && !(prm->eta_fixed > 0)))
         return ofks_fail(c, OFKS_EINVAL, "set_params: a parameter is out of range");
     cudaSetDevice(c->device);
     const bool mixed = prm->precision == OFKS_MIXED;
@@ -721,6 +722,26 @@ int ofks_get_sizes(ofks_ctx *c, int64_t *n_free, int64_t *n_nodes, int64_t *n_te
     if (n_tets) *n_tets = c->n_tets;
     if (nnz) *nnz = c->nnz;
     if (nnz_full) *nnz_full = c->nnz_full;
+    return OFKS_OK;
+}
+
+int ofks_poisson_info(ofks_ctx *c, int32_t *format, int64_t *stored, int64_t *rows, int32_t *lattice,
+                      int32_t *precond) {
+    if (!c) return OFKS_EINVAL;
+    if (c->n_nodes == 0) return ofks_fail(c, OFKS_ESTATE, "poisson_info: no mesh");
+    const bool lat = c->st.on && !c->prm.poisson_csr;
+    int64_t nr = 0;
+    if (lat) nr = c->st.rows;
+    else nr = c->n_nodes - c->n_bnd;
+    if (format) *format = lat ? 1 : 0;
+    if (stored) *stored = lat ? c->st.len : c->nnz_full;
+    if (rows) *rows = nr;
+    if (precond) *precond = hartree_pc(c);
+    if (lattice) {
+        lattice[0] = c->st.on ? c->st.Lx : 0;
+        lattice[1] = c->st.on ? c->st.Ly : 0;
+        lattice[2] = c->st.on ? c->st.Lz : 0;
+    }
     return OFKS_OK;
 }
 

@@ -230,16 +230,15 @@ __global__ void __launch_bounds__(256) k_cg_update(int64_t N, const double *__re
     const int o = it & 1, nn = (it + 1) & 1;
     const double rz = sc[0 + o], pq = sc[2 + o];
     const double alpha = pq > 0.0 ? rz / pq : 0.0;
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double rz2 = 0.0, rr = 0.0;
-    if (i < N) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         double mi = minv[i];
         if (mi != 0.0) {
             U[i] += alpha * pv[i];
             double ri = r[i] - alpha * qv[i];
             double zi = mi * ri;
             r[i] = ri; z[i] = zi;
-            rz2 = ri * zi; rr = ri * ri;
+            rz2 = fma(ri, zi, rz2); rr = fma(ri, ri, rr);
         }
     }
     rz2 = block_sum(rz2, sh);
@@ -381,11 +380,24 @@ int launch_density(ofks_ctx *c, const E *X) {
     return ofks_cuda_check(c, cudaGetLastError(), "density kernel");
 }
 
+int hartree_pc(ofks_ctx *c) {
+    if (c->prm.poisson_pc == OFKS_HPC_SEPARABLE && c->sep.on) return OFKS_HPC_SEPARABLE;
+    if (c->prm.poisson_pc == OFKS_HPC_MULTIGRID && !c->amg_tried && c->n_nodes > 0) {
+        // optional: without the hierarchy the CG runs with the Jacobi preconditioner
+        c->amg_tried = true;
+        const std::string keep = c->err;
+        if (amg_setup(c, c->h_tetn.data(), c->n_tets, c->h_xyz.data()) != OFKS_OK) { amg_free(c); c->err = keep; }
+    }
+    if (c->prm.poisson_pc == OFKS_HPC_MULTIGRID && !c->amg.empty()) return OFKS_HPC_MULTIGRID;
+    return OFKS_HPC_JACOBI;
+}
+
 int run_hartree(ofks_ctx *c) {
     if (!c->prm.hartree) return OFKS_OK;
     ProfScope ps(c, PF_POISSON);
     const int64_t N = c->n_nodes;
     const unsigned gN = (unsigned)((N + 255) / 256);
+    const unsigned gU = std::min(gN, 152u * 8u);   // grid-stride: fewer same-address atomics
     double *sc = c->d_sc + SC_CG;
     k_boundary<<<(c->n_bnd + 255) / 256, 256, 0, c->stream>>>(c->n_bnd, c->d_bnd, c->d_bxyz,
                                                                c->d_sc + SC_MOM, c->prm.multipole_lmax,
@@ -394,10 +406,24 @@ int run_hartree(ofks_ctx *c) {
     k_cg_init<<<gN, 256, 0, c->stream>>>(N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv, c->d_rhs, c->d_U,
                                          c->d_cr, c->d_cz, c->d_cp, sc);
     c->kernels += 2;
-    const bool amg = !c->amg.empty() && c->prm.poisson_amg;
-    if (amg) {   // z = M^-1 r by the multigrid V-cycle, rz[0] = r.z, p = z
+    const int pc = hartree_pc(c);
+    const bool amg = pc != OFKS_HPC_JACOBI;             // a preconditioner other than the diagonal
+    auto precond = [&]() {
+        ProfScope pp(c, PF_POISSON_PC);
+        if (pc == OFKS_HPC_SEPARABLE) sep_apply(c, c->d_cr, c->d_cz);
+        else amg_apply(c, c->d_cr, c->d_cz);
+    };
+    const bool lat = c->st.on && !c->prm.poisson_csr;
+    auto spmv = [&](int it) {
+        ProfScope pv(c, PF_POISSON_SPMV);
+        if (lat) { launch_stencil_spmv(c, c->d_cp, c->d_cq, sc, it); return; }
+        k_cg_spmv<<<gN, 256, 0, c->stream>>>(N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv, c->d_cp, c->d_cq, sc,
+                                              it);
+        c->kernels += 1;
+    };
+    if (amg) {   // z = M^-1 r by the preconditioner, rz[0] = r.z, p = z
         cudaMemsetAsync(sc, 0, sizeof(double), c->stream);
-        amg_apply(c, c->d_cr, c->d_cz);
+        precond();
         k_cg_rz<<<gN, 256, 0, c->stream>>>(N, c->d_cr, c->d_cz, c->d_cp, sc, 0, 1);
         c->kernels += 1;
     }
@@ -418,27 +444,28 @@ int run_hartree(ofks_ctx *c) {
             return ofks_fail(c, OFKS_ETIMEOUT, "Hartree CG: %d iterations, relative residual %.3e",
                              it, std::sqrt(rr / bb));
         for (int j = 0; j < chunk && amg; ++j, ++it) {
+            spmv(it);
             {
-                ProfScope pv(c, PF_POISSON_SPMV);
-                k_cg_spmv<<<gN, 256, 0, c->stream>>>(N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv, c->d_cp,
-                                                      c->d_cq, sc, it);
+                ProfScope pu(c, PF_POISSON_VEC);
+                k_cg_update_r<<<gN, 256, 0, c->stream>>>(N, c->d_minv, c->d_cp, c->d_cq, c->d_U, c->d_cr, sc, it);
             }
-            k_cg_update_r<<<gN, 256, 0, c->stream>>>(N, c->d_minv, c->d_cp, c->d_cq, c->d_U, c->d_cr, sc, it);
-            amg_apply(c, c->d_cr, c->d_cz);
-            k_cg_rz<<<gN, 256, 0, c->stream>>>(N, c->d_cr, c->d_cz, c->d_cp, sc, (it + 1) & 1, 0);
-            k_cg_dir<<<gN, 256, 0, c->stream>>>(N, c->d_cz, c->d_cp, sc, it);
-            c->kernels += 4;
+            precond();
+            {
+                ProfScope pu(c, PF_POISSON_VEC);
+                k_cg_rz<<<gN, 256, 0, c->stream>>>(N, c->d_cr, c->d_cz, c->d_cp, sc, (it + 1) & 1, 0);
+                k_cg_dir<<<gN, 256, 0, c->stream>>>(N, c->d_cz, c->d_cp, sc, it);
+            }
+            c->kernels += 3;
         }
         for (int j = 0; j < chunk && !amg; ++j, ++it) {
+            spmv(it);
             {
-                ProfScope pv(c, PF_POISSON_SPMV);
-                k_cg_spmv<<<gN, 256, 0, c->stream>>>(N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv, c->d_cp,
-                                                      c->d_cq, sc, it);
+                ProfScope pu(c, PF_POISSON_VEC);
+                k_cg_update<<<gU, 256, 0, c->stream>>>(N, c->d_minv, c->d_cp, c->d_cq, c->d_U, c->d_cr,
+                                                       c->d_cz, sc, it);
+                k_cg_dir<<<gN, 256, 0, c->stream>>>(N, c->d_cz, c->d_cp, sc, it);
             }
-            k_cg_update<<<gN, 256, 0, c->stream>>>(N, c->d_minv, c->d_cp, c->d_cq, c->d_U, c->d_cr,
-                                                   c->d_cz, sc, it);
-            k_cg_dir<<<gN, 256, 0, c->stream>>>(N, c->d_cz, c->d_cp, sc, it);
-            c->kernels += 3;
+            c->kernels += 2;
         }
     }
     return ofks_cuda_check(c, cudaGetLastError(), "Hartree CG");

@@ -29,7 +29,7 @@ enum { CB_SHIFT = 0, CB_ACTIVE = 1, CB_RZ = 2, CB_RZN = 3, CB_PQ = 4, CB_BETA = 
 // Kernel families timed by ofks_profile.
 enum {
     PF_DENSITY = 0, PF_POISSON, PF_POTENTIAL, PF_SPMM_H, PF_GRAM, PF_SMALL, PF_GRAD,
-    PF_PCG_SPMM, PF_PCG_UPDATE, PF_BB, PF_STEP, PF_SPMM_B, PF_OTHER, PF_POISSON_SPMV, PF_GCN, PF_COUNT
+    PF_PCG_SPMM, PF_PCG_UPDATE, PF_BB, PF_STEP, PF_SPMM_B, PF_OTHER, PF_POISSON_SPMV, PF_GCN, PF_POISSON_VEC, PF_POISSON_PC, PF_COUNT
 };
 
 // one level of the algebraic multigrid hierarchy of the Hartree Poisson operator (device CSR)
@@ -69,6 +69,39 @@ struct GcnState {
     int64_t t = 0;                               // Adam step count
 };
 
+// Lattice-stencil form of the full-node stiffness (stencil.cu).  Node type t = parity triple
+// of the lattice coordinates; the type's values are nown arrays of n doubles from val + base.
+constexpr int ST_MAXE = 125;                     // offsets in [-2, 2]^3
+struct StencilType {
+    int64_t base, n;                             // first stored value, nodes of the type
+    int nx, ny, nz, px, py, pz;                  // sub-lattice extents and parities
+    int nown, nent, blk0, pad;                   // stored slots, all entries, first SpMV block
+};
+struct StencilEntry {
+    int lin;                                     // id offset of the neighbour
+    int8_t oa, ob, oc, tp;                       // lattice offset; source type (-1: own slot)
+    int slot;                                    // slot in the source type
+};
+struct Stencil {
+    bool on = false;
+    int Lx = 0, Ly = 0, Lz = 0, blocks = 0;
+    int64_t len = 0, rows = 0;                   // stored values, rows the SpMV computes
+    double *val = nullptr;
+    StencilType *d_type = nullptr;
+    StencilEntry *d_ent = nullptr;               // 8 x ST_MAXE
+    int *d_slot = nullptr;                       // 8 x 125 offset code -> own slot or -1
+};
+
+// Separable (fast-diagonalization) preconditioner of the Hartree CG (separable.cu)
+struct SepState {
+    bool on = false;
+    int n[3] = {0, 0, 0};                        // interior lattice extents
+    float *S[3] = {nullptr, nullptr, nullptr};   // per-axis modes S[a][i] (n x n)
+    float *St[3] = {nullptr, nullptr, nullptr};  // their transposes
+    float *lx = nullptr, *lyz = nullptr;         // lam_x (nx), lam_y + lam_z (ny x nz)
+    float *t0 = nullptr, *t1 = nullptr;          // interior tensors
+};
+
 struct ofks_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -90,6 +123,8 @@ struct ofks_ctx {
     int64_t nnz_full = 0;
     int *d_fptr = nullptr, *d_fcol = nullptr;
     double *d_fval = nullptr, *d_minv = nullptr; // Jacobi inverse diagonal, 0 on the boundary
+    Stencil st;                                  // lattice form of the same operator (if the mesh has one)
+    SepState sep;                                // separable preconditioner (lattice meshes)
     // per tetrahedron
     int *d_tetf = nullptr;                       // T x 10 free ids (-1 on the boundary)
     int *d_tetn = nullptr;                       // T x 10 node ids
@@ -105,6 +140,10 @@ struct ofks_ctx {
     int *d_amg_idx = nullptr;                    // interior node ids (level 0 numbering)
     double *d_amg_chol = nullptr;                // dense inverse of the coarsest operator
     int64_t amg_ni = 0, amg_nc = 0;
+    bool amg_lat = false;                        // geometric lattice hierarchy, level 0 on the stencil form
+    bool amg_tried = false;                      // the hierarchy was built (or failed) for this mesh
+    std::vector<int> h_tetn;                     // host copies for building it on first use
+    std::vector<double> h_xyz;
     double e_nuc = 0.0;
     bool have_nuclei = false;
 
@@ -177,13 +216,29 @@ int setup_nuclei(ofks_ctx *c, int M, const double *Z, const double *R);
 int setup_nuclei_static(ofks_ctx *c, int M, const double *Z, const double *R);
 void free_mesh(ofks_ctx *c);
 
+// ---- stencil.cu (lattice form of the Hartree stiffness)
+int stencil_setup(ofks_ctx *c, int64_t N, const double *xyz, const int64_t *fptr, const int *fcol,
+                  const uint8_t *dirichlet);
+void stencil_fill(ofks_ctx *c);
+void stencil_free(ofks_ctx *c);
+void launch_stencil_spmv(ofks_ctx *c, const double *p, double *q, double *sc, int it);
+void launch_stencil_residual(ofks_ctx *c, const double *x, const double *b, double *r);     // r = b - L x
+void launch_stencil_jacobi(ofks_ctx *c, const double *x, const double *b, double w, double *y); // y = x + w minv (b - L x)
+
+// ---- separable.cu (fast-diagonalization preconditioner of the Hartree CG)
+int sep_setup(ofks_ctx *c, const double *xyz, const uint8_t *dirichlet);
+void sep_apply(ofks_ctx *c, const double *r_full, double *z_full);
+void sep_free(ofks_ctx *c);
+
 // ---- fields.cu (density, potentials, Hamiltonian refresh, Poisson)
+int hartree_pc(ofks_ctx *c);                    // OFKS_HPC_* the next Hartree solve uses (builds the
+                                                // multigrid hierarchy on first request)
 template <class T> int launch_density(ofks_ctx *c, const T *X);
 int run_hartree(ofks_ctx *c);
 template <class T> int launch_potential_refresh(ofks_ctx *c, T *valH, const T *valL);
 
 // ---- amg.cu (Hartree preconditioner)
-int amg_setup(ofks_ctx *c, const int *tetn, int64_t T);
+int amg_setup(ofks_ctx *c, const int *tetn, int64_t T, const double *xyz);
 void amg_free(ofks_ctx *c);
 void amg_apply(ofks_ctx *c, const double *r_full, double *z_full);
 

@@ -189,6 +189,11 @@ void free_mesh(ofks_ctx *c) {
     dev_free(c->d_cq);
     amg_free(c);
     gcn_free(c);
+    stencil_free(c);
+    sep_free(c);
+    c->amg_tried = false;
+    std::vector<int>().swap(c->h_tetn);
+    std::vector<double>().swap(c->h_xyz);
     c->n = c->n_nodes = c->n_tets = c->nnz = c->nnz_full = 0;
     c->have_nuclei = false;
 }
@@ -400,6 +405,15 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
                                                                      c->d_dL, c->d_dB);
     k_jacobi_full<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(N, d_fdiag, c->d_fval, d_interior,
                                                                        c->d_minv);
+    if ((rc = stencil_setup(c, N, xyz, fptr.data(), fcol.data(), dirichlet)) != OFKS_OK ||
+        (rc = sep_setup(c, xyz, dirichlet)) != OFKS_OK) {
+        dev_free(d_xyz); dev_free(d_fmap); dev_free(d_dpos); dev_free(d_fdiag); dev_free(d_interior);
+        dev_free(d_flag);
+        free_mesh(c);
+        return rc;
+    }
+    c->n_nodes = N;
+    stencil_fill(c);
     int hflag = 0;
     cudaError_t e = cudaMemcpyAsync(&hflag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -409,9 +423,9 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
     if (hflag) { free_mesh(c); return ofks_fail(c, OFKS_EINVAL, "set_mesh: degenerate tetrahedron"); }
     c->n_nodes = N; c->n_tets = T; c->n = n; c->nnz = nnz; c->nnz_full = nnz_full;
     c->n_slices = n_slices; c->sell_len = sell_len; c->n_bnd = (int)bnd.size();
-    // the multigrid preconditioner of the Hartree solve is optional: without it the CG runs
-    // with the Jacobi preconditioner
-    if (amg_setup(c, tetn.data(), T) != OFKS_OK) amg_free(c);
+    // the multigrid hierarchy is built on the first Hartree solve that asks for it
+    c->h_tetn.swap(tetn);
+    c->h_xyz.assign(xyz, xyz + N * 3);
     return OFKS_OK;
 }
 

@@ -17,6 +17,8 @@ OK, EINVAL, ECUDA, ENOMEM, ESTATE, ENOTCONV, ENONFINITE, ETIMEOUT = 0, -1, -2, -
 PC = {"none": 0, "pcg": 1, "exact": 2, "learned": 3}
 PRECISION = {"fp64": 0, "mixed": 1}
 ETA = {"bb2": 0, "bb1": 1, "abb1": 2, "abb2": 3, "bb2_raw": 4, "fixed": 5}
+HPC = {"jacobi": 0, "multigrid": 1, "separable": 2}        # Hartree CG preconditioners
+HPC_NAMES = {v: k for k, v in HPC.items()}
 FIELDS = {"rho_q": 0, "vh_q": 1, "vxc_q": 2, "exc_q": 3, "U": 4, "HX": 5, "BX": 6, "G": 7, "D": 8,
           "Lambda0": 9, "S": 10, "Lambda": 11, "vext_q": 12}
 MATS = {"L": 0, "B": 1, "H": 2}
@@ -24,7 +26,7 @@ STATIC_NUCLEI_MAX = 1024          # OFKS_STATIC_NUCLEI_MAX
 SYMBOLS = ("ofks_default_params", "ofks_create", "ofks_destroy", "ofks_last_error", "ofks_set_mesh",
            "ofks_set_nuclei", "ofks_set_nuclei_static", "ofks_set_params", "ofks_init_orbitals", "ofks_set_orbitals",
            "ofks_get_orbitals", "ofks_step", "ofks_solve", "ofks_evaluate", "ofks_rayleigh_ritz",
-           "ofks_get_field", "ofks_apply", "ofks_get_sizes", "ofks_get_history", "ofks_save_state",
+           "ofks_get_field", "ofks_apply", "ofks_get_sizes", "ofks_poisson_info", "ofks_get_history", "ofks_save_state",
            "ofks_load_state", "ofks_profile", "ofks_profile_get", "ofks_precond_init", "ofks_precond_get_weights",
            "ofks_precond_set_weights", "ofks_precondition", "ofks_train_precond_step", "ofks_precond_grads")
 
@@ -41,9 +43,9 @@ class Params(C.Structure):
                 ("pcg_iters", C.c_int32), ("eta_rule", C.c_int32), ("eta_fixed", C.c_double),
                 ("eta_min", C.c_double), ("eta_max", C.c_double), ("hartree", C.c_int32),
                 ("xc", C.c_int32), ("multipole_lmax", C.c_int32), ("poisson_tol", C.c_double),
-                ("poisson_max_iter", C.c_int32), ("poisson_amg", C.c_int32), ("mixed_tol", C.c_double),
+                ("poisson_max_iter", C.c_int32), ("poisson_pc", C.c_int32), ("mixed_tol", C.c_double),
                 ("poisson_tol_mixed", C.c_double), ("judge_tau", C.c_double), ("learned_tc", C.c_int32),
-                ("poisson_adaptive", C.c_int32)]
+                ("poisson_adaptive", C.c_int32), ("poisson_csr", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -92,6 +94,8 @@ def load(path: str = LIB_PATH):
         "ofks_apply": (C.c_int, [vp, i32, _dp, _dp, i32]),
         "ofks_get_sizes": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64),
                                      C.POINTER(i64)]),
+        "ofks_poisson_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32),
+                                        C.POINTER(i32)]),
         "ofks_get_history": (C.c_int, [vp, _dp, i32, C.POINTER(i32)]),
         "ofks_save_state": (C.c_int, [vp, C.c_char_p]),
         "ofks_load_state": (C.c_int, [vp, C.c_char_p]),
@@ -122,6 +126,8 @@ def default_params(**overrides) -> Params:
             v = ETA[v]
         if k == "precision" and isinstance(v, str):
             v = PRECISION[v]
+        if k == "poisson_pc" and isinstance(v, str):
+            v = HPC[v]
         if isinstance(v, bool):
             v = int(v)
         setattr(prm, k, v)
@@ -234,6 +240,14 @@ class Context:
         v = [C.c_int64() for _ in range(5)]
         self._chk(self.lib.ofks_get_sizes(self.h, *[C.byref(x) for x in v]))
         return dict(zip(("n_free", "n_nodes", "n_tets", "nnz", "nnz_full"), (x.value for x in v)))
+
+    def poisson_info(self) -> dict:
+        fmt, stored, rows, pc = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
+        lat = (C.c_int32 * 3)()
+        self._chk(self.lib.ofks_poisson_info(self.h, C.byref(fmt), C.byref(stored), C.byref(rows), lat,
+                                             C.byref(pc)))
+        return {"format": "lattice" if fmt.value == 1 else "csr", "stored": stored.value, "rows": rows.value,
+                "lattice": tuple(lat), "precond": HPC_NAMES[pc.value]}
 
     def get_field(self, name: str):
         s = self.sizes()

@@ -40,6 +40,7 @@ def test_default_params_without_gpu(lib):
     prm = ofks.default_params(p=3, precond="exact", eta_rule="fixed", eta_fixed=2.0)
     assert prm.p == 3 and prm.beta == 10.0 and prm.tol == 1e-8 and prm.precond == 2 and prm.eta_rule == 5
     assert prm.pcg_iters == 8 and prm.multipole_lmax == 2 and prm.hartree == 1 and prm.xc == 1
+    assert prm.poisson_csr == 0 and prm.poisson_adaptive == 0 and prm.poisson_pc == 2
 
 
 def test_missing_library_fails_loudly(tmp_path):

@@ -343,15 +343,58 @@ def test_full_size_lih_first_steps_match_oracle(ofks):
     ctx.close()
 
 
-@pytest.mark.parametrize("amg", [0, 1])
-def test_hartree_preconditioners_agree_with_oracle(ofks, amg):
-    # the Hartree CG with the Jacobi or the multigrid preconditioner reaches the same potential
+@pytest.mark.parametrize("pc,max_iters", [("jacobi", 2000), ("multigrid", 400), ("separable", 60)])
+def test_hartree_preconditioners_agree_with_oracle(ofks, pc, max_iters):
+    # the Hartree CG with the Jacobi, multigrid or separable preconditioner reaches the same
+    # potential; the separable one keeps the count near twenty on the graded lattice
     s = CASES["chain_p41"]()
-    ctx, pr, V, m = build_pair(ofks, s, poisson_amg=amg)
+    ctx, pr, V, m = build_pair(ofks, s, poisson_pc=pc)
+    assert ctx.poisson_info()["precond"] == pc
     X0 = pr.initial_guess(V)
     ctx.set_orbitals(X0)
     r = ctx.evaluate()
     pot = pr.potentials(pr.density(X0))
     assert rel(ctx.get_field("U"), pot["U"]) < 1e-9
-    assert 0 < r["hartree_iters"] < 2000, r["hartree_iters"]
+    assert 0 < r["hartree_iters"] < max_iters, r["hartree_iters"]
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", ["lih10", "chain_p41"])
+@pytest.mark.parametrize("csr", [0, 1])
+def test_hartree_lattice_and_csr_forms_agree_with_oracle(ofks, case, csr):
+    # the lattice-stencil SpMV (symmetric half, no column indices) and the CSR give the oracle's
+    # potential; the lattice form is the default on these meshes
+    s = CASES[case]()
+    ctx, pr, V, m = build_pair(ofks, s, poisson_csr=csr)
+    info = ctx.poisson_info()
+    assert info["format"] == ("csr" if csr else "lattice"), info
+    assert info["lattice"] == tuple(m.lattice)
+    assert info["rows"] == int(np.sum(m.dirichlet == 0))
+    X0 = pr.initial_guess(V)
+    ctx.set_orbitals(X0)
+    ctx.evaluate()
+    pot = pr.potentials(pr.density(X0))
+    assert rel(ctx.get_field("U"), pot["U"]) < 1e-9
+    ctx.close()
+
+
+@pytest.mark.parametrize("pc,used", [("separable", "jacobi"), ("multigrid", "multigrid")])
+def test_hartree_on_renumbered_mesh_uses_csr(ofks, pc, used):
+    # node ids that do not follow a lattice: the CSR form runs (the separable preconditioner
+    # falls back to Jacobi, multigrid to smoothed aggregation) and still matches the oracle
+    s = CASES["lih10"]()
+    m0 = I.make_mesh(s)
+    perm = np.random.default_rng(3).permutation(len(m0.xyz))     # new id -> old id
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(len(perm))
+    m = I.Mesh(m0.xyz[perm].copy(), inv[m0.tet10], m0.dirichlet[perm].copy(), m0.lattice, m0.axes)
+    ctx = ofks.context_for(s, m, beta=10.0, poisson_pc=pc)
+    assert ctx.poisson_info()["format"] == "csr"
+    assert ctx.poisson_info()["precond"] == used
+    pr = pcal.Problem(m.xyz, m.tet10, m.dirichlet, s.Z, s.R, pcal.Params(p=s.p, occ=s.occ, beta=10.0))
+    X0 = pr.initial_guess(I.initial_block(m.n_free, s.p, 0))
+    ctx.set_orbitals(X0)
+    ctx.evaluate()
+    pot = pr.potentials(pr.density(X0))
+    assert rel(ctx.get_field("U"), pot["U"]) < 1e-9
     ctx.close()

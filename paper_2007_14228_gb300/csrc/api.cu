@@ -428,6 +428,7 @@ void ofks_default_params(ofks_params *p) {
     p->poisson_pc = OFKS_HPC_SEPARABLE;
     p->mixed_tol = 1e-5; p->poisson_tol_mixed = 1e-8;
     p->judge_tau = 0.5; p->learned_tc = 1; p->poisson_adaptive = 0; p->poisson_csr = 0;
+    p->poisson_sep_tc = 1; p->spmm_f32_rows = 0;
 }
 
 int ofks_create(ofks_ctx **out, int device) {
@@ -515,7 +516,8 @@ int ofks_set_params(ofks_ctx *c, const ofks_params *prm) {
         prm->eta_rule < 0 || prm->eta_rule > OFKS_ETA_FIXED || prm->precond < 0 || prm->precond > OFKS_PC_LEARNED ||
         !(prm->judge_tau > 0) || prm->learned_tc < 0 || prm->learned_tc > 1 ||
         prm->poisson_adaptive < 0 || prm->poisson_adaptive > 1 ||
-        prm->poisson_csr < 0 || prm->poisson_csr > 1 ||
+        prm->poisson_csr < 0 || prm->poisson_csr > 1 || prm->poisson_sep_tc < 0 || prm->poisson_sep_tc > 1 ||
+        prm->spmm_f32_rows < 0 || prm->spmm_f32_rows > 1 ||
         (prm->precision != OFKS_FP64 && prm->precision != OFKS_MIXED) || !(prm->mixed_tol > 0) ||
         !(prm->poisson_tol_mixed > 0) || !(prm->eta_min > 0) || !(prm->eta_max >= prm->eta_min) ||
         prm->multipole_lmax < -1 || prm->multipole_lmax > 2 || !(prm->poisson_tol > 0) ||

@@ -169,6 +169,72 @@ __global__ void __launch_bounds__(256) k_grad(int64_t n, int p, int ld, const T 
     if (threadIdx.x == 0) atomicAdd(kkt2, part);
 }
 
+// float32 blocks: the same product with 64-row tiles and a 4-row x CPT-column register tile per
+// thread (columns tx + 16 k), C and L0 held whole in shared memory: 2 (4 + CPT) shared loads per
+// 8 CPT FMAs, where the float64 form above spends 3 per 2 (its limit is the FP64 pipe, not
+// shared memory).
+template <int CPT>
+__global__ void __launch_bounds__(256) k_grad_f32(int64_t n, int p, int ld, const float *__restrict__ HX,
+                                                  const float *__restrict__ BX, const double *__restrict__ C,
+                                                  const double *__restrict__ L0, float *G, double *kkt2) {
+    extern __shared__ __align__(16) float gsm[];
+    float *cs = gsm;                 // ld x ld
+    float *ls = cs + ld * ld;        // ld x ld
+    float *bx = ls + ld * ld;        // 64 x ld
+    __shared__ double red[8];
+    for (int i = threadIdx.x; i < ld * ld; i += blockDim.x) { cs[i] = (float)C[i]; ls[i] = (float)L0[i]; }
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double part = 0.0;
+    for (int64_t r0 = blockIdx.x * 64LL; r0 < n; r0 += 64LL * gridDim.x) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 64 * ld; i += blockDim.x) {
+            const int64_t r = r0 + i / ld;
+            bx[i] = r < n ? BX[r0 * ld + i] : 0.f;
+        }
+        __syncthreads();
+        float g[4][CPT], rr[4][CPT];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t r = r0 + 4 * ty + i;
+#pragma unroll
+            for (int k = 0; k < CPT; ++k) {
+                const int col = tx + 16 * k;
+                const float h = (r < n && col < ld) ? HX[r * ld + col] : 0.f;
+                g[i][k] = h; rr[i][k] = h;
+            }
+        }
+        for (int kk = 0; kk < ld; ++kk) {
+            float b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) b[i] = bx[(4 * ty + i) * ld + kk];
+#pragma unroll
+            for (int k = 0; k < CPT; ++k) {
+                const int col = tx + 16 * k;
+                const float cv = col < ld ? cs[kk * ld + col] : 0.f, lv = col < ld ? ls[kk * ld + col] : 0.f;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    g[i][k] = fmaf(b[i], cv, g[i][k]);
+                    rr[i][k] = fmaf(-b[i], lv, rr[i][k]);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t r = r0 + 4 * ty + i;
+            if (r >= n) continue;
+#pragma unroll
+            for (int k = 0; k < CPT; ++k) {
+                const int col = tx + 16 * k;
+                if (col >= ld) continue;
+                G[r * ld + col] = g[i][k];
+                if (col < p) part += (double)(rr[i][k] * rr[i][k]);
+            }
+        }
+    }
+    part = block_sum(part, red);
+    if (threadIdx.x == 0) atomicAdd(kkt2, part);
+}
+
 // ---------------------------------------------------------------- elementwise block kernels
 // Flattened over the n x ld elements with a stride that is a multiple of ld, so each thread
 // keeps one column: per-column scalars are read once and per-column sums stay in a register.
@@ -445,6 +511,18 @@ void launch_grad_update(ofks_ctx *c, Blocks<T> &b) {
     const size_t sm = sizeof(T) * (32 * ld + 2 * KC * ld);
     T *G = b.G[c->cur];
     cudaMemsetAsync(c->d_sc + SC_KKT2, 0, sizeof(double), c->stream);
+    if constexpr (sizeof(T) == 4) {
+        if (ld <= 64) {
+            const int smf = (int)(sizeof(float) * (2 * ld * ld + 64 * ld));
+            const unsigned gf = (unsigned)std::max<int64_t>(1, std::min<int64_t>((c->n + 63) / 64, 152 * 4));
+#define GF_(k) { cudaFuncSetAttribute(k_grad_f32<k>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf); \
+        k_grad_f32<k><<<gf, 256, smf, c->stream>>>(c->n, c->p, ld, (const float *)b.HX, (const float *)b.BX, \
+                                                   c->d_C, c->d_L0, (float *)G, c->d_sc + SC_KKT2); }
+            if (ld <= 16) GF_(1) else if (ld <= 32) GF_(2) else if (ld <= 48) GF_(3) else GF_(4)
+#undef GF_
+            return;
+        }
+    }
     const unsigned grid = row_grid(32, c->n);
     const int no = (32 * ld + 255) / 256;
 #define GR_(k) { cudaFuncSetAttribute(k_grad<T, k>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \

@@ -227,9 +227,15 @@ __global__ void __launch_bounds__(256) k_cg_update(int64_t N, const double *__re
                                                    const double *__restrict__ qv, double *U,
                                                    double *r, double *z, double *sc, int it) {
     __shared__ double sh[8];
-    const int o = it & 1, nn = (it + 1) & 1;
-    const double rz = sc[0 + o], pq = sc[2 + o];
-    const double alpha = pq > 0.0 ? rz / pq : 0.0;
+    __shared__ double s_alpha;
+    const int nn = (it + 1) & 1;
+    // one float64 division per block (a division per thread costs as much as the whole update)
+    if (threadIdx.x == 0) {
+        const double rz = sc[it & 1], pq = sc[2 + (it & 1)];
+        s_alpha = pq > 0.0 ? rz / pq : 0.0;
+    }
+    __syncthreads();
+    const double alpha = s_alpha;
     double rz2 = 0.0, rr = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         double mi = minv[i];
@@ -256,17 +262,22 @@ __global__ void __launch_bounds__(256) k_cg_update_r(int64_t N, const double *__
                                                      const double *__restrict__ qv, double *U, double *r,
                                                      double *sc, int it) {
     __shared__ double sh[8];
-    const int o = it & 1, nn = (it + 1) & 1;
-    const double rz = sc[0 + o], pq = sc[2 + o];
-    const double alpha = pq > 0.0 ? rz / pq : 0.0;
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double rr = 0.0;
-    if (i < N && minv[i] != 0.0) {
-        U[i] += alpha * pv[i];
-        const double ri = r[i] - alpha * qv[i];
-        r[i] = ri;
-        rr = ri * ri;
+    __shared__ double s_alpha;
+    const int nn = (it + 1) & 1;
+    if (threadIdx.x == 0) {
+        const double rz = sc[it & 1], pq = sc[2 + (it & 1)];
+        s_alpha = pq > 0.0 ? rz / pq : 0.0;
     }
+    __syncthreads();
+    const double alpha = s_alpha;
+    double rr = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        if (minv[i] != 0.0) {
+            U[i] += alpha * pv[i];
+            const double ri = r[i] - alpha * qv[i];
+            r[i] = ri;
+            rr = fma(ri, ri, rr);
+        }
     rr = block_sum(rr, sh);
     if (threadIdx.x == 0) {
         atomicAdd(sc + 4 + nn, rr);
@@ -278,10 +289,9 @@ __global__ void __launch_bounds__(256) k_cg_update_r(int64_t N, const double *__
 __global__ void __launch_bounds__(256) k_cg_rz(int64_t N, const double *__restrict__ r, const double *__restrict__ z,
                                                double *pv, double *sc, int slot, int first) {
     __shared__ double sh[8];
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double v = 0.0;
-    if (i < N) {
-        v = r[i] * z[i];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        v = fma(r[i], z[i], v);
         if (first) pv[i] = z[i];
     }
     v = block_sum(v, sh);
@@ -290,11 +300,15 @@ __global__ void __launch_bounds__(256) k_cg_rz(int64_t N, const double *__restri
 
 // beta = rz'/rz; p = z + beta p
 __global__ void k_cg_dir(int64_t N, const double *__restrict__ z, double *pv, const double *sc, int it) {
-    const int o = it & 1, nn = (it + 1) & 1;
-    const double rz = sc[0 + o], rz2 = sc[0 + nn];
-    const double beta = rz > 0.0 ? rz2 / rz : 0.0;
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < N) pv[i] = z[i] + beta * pv[i];
+    __shared__ double s_beta;
+    if (threadIdx.x == 0) {
+        const double rz = sc[it & 1], rz2 = sc[(it + 1) & 1];
+        s_beta = rz > 0.0 ? rz2 / rz : 0.0;
+    }
+    __syncthreads();
+    const double beta = s_beta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        pv[i] = z[i] + beta * pv[i];
 }
 
 template <class E>
@@ -410,9 +424,9 @@ int run_hartree(ofks_ctx *c) {
     const bool amg = pc != OFKS_HPC_JACOBI;             // a preconditioner other than the diagonal
     auto precond = [&]() {
         ProfScope pp(c, PF_POISSON_PC);
-        if (pc == OFKS_HPC_SEPARABLE) sep_apply(c, c->d_cr, c->d_cz);
-        else amg_apply(c, c->d_cr, c->d_cz);
+        amg_apply(c, c->d_cr, c->d_cz);
     };
+    const bool sep = pc == OFKS_HPC_SEPARABLE;
     const bool lat = c->st.on && !c->prm.poisson_csr;
     auto spmv = [&](int it) {
         ProfScope pv(c, PF_POISSON_SPMV);
@@ -421,10 +435,14 @@ int run_hartree(ofks_ctx *c) {
                                               it);
         c->kernels += 1;
     };
-    if (amg) {   // z = M^-1 r by the preconditioner, rz[0] = r.z, p = z
+    if (sep) {          // z = A_sep^-1 r, rz[0] = r.z, p = z
+        cudaMemsetAsync(sc, 0, sizeof(double), c->stream);
+        ProfScope pp(c, PF_POISSON_PC);
+        sep_cg_step(c, -1, 0, 1);
+    } else if (amg) {   // z = M^-1 r by the multigrid cycle, rz[0] = r.z, p = z
         cudaMemsetAsync(sc, 0, sizeof(double), c->stream);
         precond();
-        k_cg_rz<<<gN, 256, 0, c->stream>>>(N, c->d_cr, c->d_cz, c->d_cp, sc, 0, 1);
+        k_cg_rz<<<gU, 256, 0, c->stream>>>(N, c->d_cr, c->d_cz, c->d_cp, sc, 0, 1);
         c->kernels += 1;
     }
     double ptol = c->phase == 32 ? std::max(c->prm.poisson_tol, c->prm.poisson_tol_mixed) : c->prm.poisson_tol;
@@ -443,17 +461,29 @@ int run_hartree(ofks_ctx *c) {
         if (it >= c->prm.poisson_max_iter)
             return ofks_fail(c, OFKS_ETIMEOUT, "Hartree CG: %d iterations, relative residual %.3e",
                              it, std::sqrt(rr / bb));
-        for (int j = 0; j < chunk && amg; ++j, ++it) {
+        for (int j = 0; j < chunk && sep; ++j, ++it) {
+            spmv(it);
+            {
+                ProfScope pp(c, PF_POISSON_PC);
+                sep_cg_step(c, it, (it + 1) & 1, 0);    // update, precondition, r.z
+            }
+            {
+                ProfScope pu(c, PF_POISSON_VEC);
+                k_cg_dir<<<gU, 256, 0, c->stream>>>(N, c->d_cz, c->d_cp, sc, it);
+            }
+            c->kernels += 1;
+        }
+        for (int j = 0; j < chunk && amg && !sep; ++j, ++it) {
             spmv(it);
             {
                 ProfScope pu(c, PF_POISSON_VEC);
-                k_cg_update_r<<<gN, 256, 0, c->stream>>>(N, c->d_minv, c->d_cp, c->d_cq, c->d_U, c->d_cr, sc, it);
+                k_cg_update_r<<<gU, 256, 0, c->stream>>>(N, c->d_minv, c->d_cp, c->d_cq, c->d_U, c->d_cr, sc, it);
             }
             precond();
             {
                 ProfScope pu(c, PF_POISSON_VEC);
-                k_cg_rz<<<gN, 256, 0, c->stream>>>(N, c->d_cr, c->d_cz, c->d_cp, sc, (it + 1) & 1, 0);
-                k_cg_dir<<<gN, 256, 0, c->stream>>>(N, c->d_cz, c->d_cp, sc, it);
+                k_cg_rz<<<gU, 256, 0, c->stream>>>(N, c->d_cr, c->d_cz, c->d_cp, sc, (it + 1) & 1, 0);
+                k_cg_dir<<<gU, 256, 0, c->stream>>>(N, c->d_cz, c->d_cp, sc, it);
             }
             c->kernels += 3;
         }
@@ -463,9 +493,19 @@ int run_hartree(ofks_ctx *c) {
                 ProfScope pu(c, PF_POISSON_VEC);
                 k_cg_update<<<gU, 256, 0, c->stream>>>(N, c->d_minv, c->d_cp, c->d_cq, c->d_U, c->d_cr,
                                                        c->d_cz, sc, it);
-                k_cg_dir<<<gN, 256, 0, c->stream>>>(N, c->d_cz, c->d_cp, sc, it);
+                k_cg_dir<<<gU, 256, 0, c->stream>>>(N, c->d_cz, c->d_cp, sc, it);
             }
             c->kernels += 2;
+        }
+    }
+    if (sep && c->sep.tc && c->prm.poisson_sep_tc) {   // a tensor-core wait that timed out
+        int hf = 0;
+        cudaError_t e = cudaMemcpyAsync(&hf, c->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return ofks_cuda_check(c, e, "Hartree CG");
+        if (hf) {
+            cudaMemsetAsync(c->d_flag + 1, 0, sizeof(int), c->stream);
+            return ofks_fail(c, OFKS_ETIMEOUT, "Hartree preconditioner: tensor-core wait timed out");
         }
     }
     return ofks_cuda_check(c, cudaGetLastError(), "Hartree CG");

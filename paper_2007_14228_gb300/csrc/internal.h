@@ -1,6 +1,7 @@
 // Internal state and launcher prototypes of libofks (not part of the ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -100,6 +101,10 @@ struct SepState {
     float *St[3] = {nullptr, nullptr, nullptr};  // their transposes
     float *lx = nullptr, *lyz = nullptr;         // lam_x (nx), lam_y + lam_z (ny x nz)
     float *t0 = nullptr, *t1 = nullptr;          // interior tensors
+    bool tc = false;                             // tensor-core form available (every axis <= 256)
+    __nv_bfloat16 *hS[3] = {nullptr, nullptr, nullptr}, *hSt[3] = {nullptr, nullptr, nullptr};  // bf16, padded
+    __nv_bfloat16 *hbuf = nullptr;               // six padded bf16 tensors (input, intermediates)
+    int64_t hoff[6] = {0, 0, 0, 0, 0, 0};
 };
 
 struct ofks_ctx {
@@ -117,6 +122,7 @@ struct ofks_ctx {
     int *d_slice_w = nullptr;                    // n_slices widths
     int *d_cols = nullptr;                       // sell_len free column ids
     int *d_perm = nullptr;                       // n_slices*32 -> free row id or -1
+    int max_slice_w = 0;                         // widest slice (entries per row)
     double *d_valL = nullptr, *d_valB = nullptr, *d_valH = nullptr;
     double *d_dL = nullptr, *d_dB = nullptr;     // diagonals of L and B (free)
     // full-node stiffness for the Hartree Poisson problem (CSR)
@@ -227,7 +233,7 @@ void launch_stencil_jacobi(ofks_ctx *c, const double *x, const double *b, double
 
 // ---- separable.cu (fast-diagonalization preconditioner of the Hartree CG)
 int sep_setup(ofks_ctx *c, const double *xyz, const uint8_t *dirichlet);
-void sep_apply(ofks_ctx *c, const double *r_full, double *z_full);
+void sep_cg_step(ofks_ctx *c, int it, int slot, int first);    // fused CG update + z = A_sep^-1 r + r.z
 void sep_free(ofks_ctx *c);
 
 // ---- fields.cu (density, potentials, Hamiltonian refresh, Poisson)

@@ -19,6 +19,8 @@
 #include <cstdlib>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -96,21 +98,66 @@ bool axis_modes(const std::vector<double> &x, std::vector<double> &S, std::vecto
     return true;
 }
 
-// interior lattice tensor (a, b, c) <- full-node vector, float32
-__global__ void k_sep_gather(int nx, int ny, int nz, int Ly, int Lz, const double *__restrict__ full, float *t) {
+// Interior lattice tensor (a, b, c) <- the CG residual (element type E, innermost axis stored
+// with stride ldc >= nz).  With it >= 0 the CG update of iteration it is fused in first (the
+// scalars protocol of the Hartree CG in fields.cu): alpha = rz/pq, U += alpha p, r -= alpha q,
+// rr' += r.r, and the next pq slot is cleared.
+template <class E>
+__global__ void __launch_bounds__(256) k_sep_gather(int nx, int ny, int nz, int ldc, int Ly, int Lz,
+                                                    const double *__restrict__ pv, const double *__restrict__ qv,
+                                                    double *U, double *r, E *t, double *sc, int it) {
+    __shared__ double sh[8];
+    __shared__ double s_alpha;
+    if (threadIdx.x == 0) {
+        s_alpha = 0.0;
+        if (it >= 0) {
+            const double rz = sc[it & 1], pq = sc[2 + (it & 1)];
+            s_alpha = pq > 0.0 ? rz / pq : 0.0;     // one float64 division per block
+        }
+    }
+    __syncthreads();
+    const double alpha = s_alpha;
     const int64_t n = (int64_t)nx * ny * nz;
+    double rr = 0.0;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t a = q / ((int64_t)ny * nz), b = (q / nz) % ny, c = q % nz;
-        t[q] = (float)full[((a + 1) * Ly + (b + 1)) * Lz + (c + 1)];
+        const int64_t ab = q / nz, c = q - ab * nz, a = ab / ny, b = ab - a * ny;
+        const int64_t i = ((a + 1) * Ly + (b + 1)) * Lz + (c + 1);
+        double ri = r[i];
+        if (it >= 0) {
+            U[i] += alpha * pv[i];
+            ri -= alpha * qv[i];
+            r[i] = ri;
+            rr = fma(ri, ri, rr);
+        }
+        t[ab * ldc + c] = (E)(float)ri;
+    }
+    if (it >= 0) {
+        rr = block_sum(rr, sh);
+        if (threadIdx.x == 0) {
+            atomicAdd(sc + 4 + ((it + 1) & 1), rr);
+            if (blockIdx.x == 0) sc[2 + ((it + 1) & 1)] = 0.0;
+        }
     }
 }
 
-__global__ void k_sep_scatter(int nx, int ny, int nz, int Ly, int Lz, const float *__restrict__ t, double *full) {
+// z <- the interior tensor (float64), rz[slot] += r.z; with pv also p = z (CG start)
+template <class E>
+__global__ void __launch_bounds__(256) k_sep_scatter(int nx, int ny, int nz, int ldc, int Ly, int Lz,
+                                                     const E *__restrict__ t, const double *__restrict__ r, double *z,
+                                                     double *pv, double *sc, int slot) {
+    __shared__ double sh[8];
     const int64_t n = (int64_t)nx * ny * nz;
+    double rz = 0.0;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t a = q / ((int64_t)ny * nz), b = (q / nz) % ny, c = q % nz;
-        full[((a + 1) * Ly + (b + 1)) * Lz + (c + 1)] = (double)t[q];
+        const int64_t ab = q / nz, c = q - ab * nz, a = ab / ny, b = ab - a * ny;
+        const int64_t i = ((a + 1) * Ly + (b + 1)) * Lz + (c + 1);
+        const double zi = (double)(float)t[ab * ldc + c];
+        z[i] = zi;
+        if (pv) pv[i] = zi;
+        rz = fma(r[i], zi, rz);
     }
+    rz = block_sum(rz, sh);
+    if (threadIdx.x == 0) atomicAdd(sc + slot, rz);
 }
 
 // Batched row-major GEMM C_z = A_z B_z (M x K times K x N), float32, 64 x 64 tiles, 256
@@ -175,11 +222,175 @@ void gemm(ofks_ctx *c, int batch, int M, int N, int K, const float *A, int64_t s
     c->kernels += 1;
 }
 
+
+// ---- tensor-core form (tcgen05, bf16 operands, float32 accumulation in tensor memory)
+//
+// Each of the six contractions is one GEMM  D[m][n] = sum_k A[m][k] Bt[n][k]  whose A is the
+// current tensor with the contracted axis innermost (rows m = the other two axes) and whose Bt
+// is an axis matrix or its transpose.  The output is written with n outermost, which rotates the
+// axes so that the next contraction is again over the innermost one: [a][b][c] -> [k][a][b] ->
+// [j][k][a] -> [i][j][k] (scaled) -> [c][i][j] -> [b][c][i] -> [a][b][c].  Intermediate tensors
+// are bf16 with the innermost axis padded to a multiple of 16 (zero padding, written never), so
+// every A row is a whole number of 16-byte core-matrix rows.  One CTA of four warps computes a
+// 128-row tile: the operands go to shared memory in the no-swizzle K-major core-matrix layout,
+// one thread issues the MMAs (M = 128, N = NP, K = 16 each) into tensor memory and commits them
+// to an mbarrier, and each warp reads its 32 rows back with tcgen05.ld for the epilogue.
+// Waits are bounded: on timeout the CTA flags an error, frees its tensor memory and returns.
+constexpr int STM = 128;
+constexpr long long SEP_WAIT = 1LL << 20;
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// element (r, k) of a tile with KP columns: core matrix (r / 8, k / 8), 8 x 8 elements, cores
+// adjacent along K 128 B apart and along rows KP / 8 * 128 B apart
+__device__ __forceinline__ int coff(int r, int k, int KP) {
+    return ((r >> 3) * (KP >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+// 16-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros (rows past the end)
+__device__ __forceinline__ void cp16(void *dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(su32(dst)), "l"(src), "r"(src_bytes) : "memory");
+}
+
+struct SepPass {
+    const __nv_bfloat16 *A;        // M x KP row-major (zero padding beyond K)
+    const __nv_bfloat16 *Bt;       // NP x KP row-major, zero padded
+    int M, K, KP, N, NP, tcols;    // tcols: tensor-memory columns (power of two >= NP)
+    __nv_bfloat16 *out;            // element (n, m) at (n M1 + m / M2) KPo + m % M2
+    int M1, M2, KPo;
+    const float *lr, *lc;          // SCALE: multiply by 1 / (lr[n] + lc[m])
+    int *err;
+};
+
+template <int SCALE>
+__global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(dsm);     // STM x KP
+    __nv_bfloat16 *sB = sA + STM * P.KP;                             // NP x KP
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * STM;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                     "r"(P.tcols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        abort_flag = 0;
+    }
+    // operands: rows of 8 elements (16 B) copied asynchronously into their core-matrix rows,
+    // all of a thread's copies in flight at once
+    const int kc8 = P.KP >> 3;
+    for (int e = tid; e < P.NP * kc8; e += blockDim.x) {
+        const int n = e / kc8, k = (e - n * kc8) * 8;
+        cp16(sB + coff(n, k, P.KP), P.Bt + (int64_t)n * P.KP + k, 16);
+    }
+    for (int e = tid; e < STM * kc8; e += blockDim.x) {
+        const int rr = e / kc8, k = (e - rr * kc8) * 8;
+        const bool in = m0 + rr < P.M;
+        cp16(sA + coff(rr, k, P.KP), P.A + (in ? (int64_t)(m0 + rr) * P.KP + k : 0), in ? 16 : 0);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    if (tid == 0) {
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(P.NP >> 3) << 17) |
+                               ((uint32_t)(STM >> 4) << 24);
+        const uint32_t a0 = su32(sA), b0 = su32(sB), sbo = (uint32_t)(P.KP >> 3) * 128u;
+        for (int kk = 0; kk < P.KP / 16; ++kk) {
+            const uint64_t ad = sdesc(a0 + kk * 256, 128, sbo);
+            const uint64_t bd = sdesc(b0 + kk * 256, 128, sbo);
+            const uint32_t accum = kk > 0 ? 1u : 0u;
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&mbar)));
+    }
+    uint32_t done = 0;
+    for (long long w = 0; w < SEP_WAIT && !done; ++w) {
+        asm volatile(
+            "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
+            : "=r"(done)
+            : "r"(su32(&mbar)), "r"(0u));
+    }
+    if (!done) abort_flag = 1;
+    __syncthreads();
+    if (!abort_flag) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int m = m0 + warp * 32 + lane;
+        const int m1 = m / P.M2, m2 = m - m1 * P.M2;
+        const float lcm = (SCALE && m < P.M) ? P.lc[m] : 0.f;
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int cb = 0; cb < P.NP; cb += 16) {
+            uint32_t v[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(taddr + cb));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (m >= P.M) continue;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int n = cb + q;
+                if (n >= P.N) break;
+                float x = __uint_as_float(v[q]);
+                if (SCALE) x = __fdividef(x, P.lr[n] + lcm);
+                P.out[((int64_t)n * P.M1 + m1) * P.KPo + m2] = __float2bfloat16(x);
+            }
+        }
+    }
+    if (abort_flag && tid == 0) atomicExch(P.err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P.tcols));
+}
+
+template <int SCALE>
+void sep_tc_launch(ofks_ctx *c, SepPass P) {
+    P.tcols = P.NP <= 32 ? 32 : (P.NP <= 64 ? 64 : (P.NP <= 128 ? 128 : 256));
+    P.err = c->d_flag + 1;
+    // shared memory of at least 228 KB * tcols / 512 per CTA keeps the CTAs resident on one SM
+    // within its 512 tensor-memory columns, so no allocation ever has to wait
+    const int need = (STM + P.NP) * P.KP * (int)sizeof(__nv_bfloat16);
+    const int floor_ = 228 * 1024 / (512 / P.tcols) + 1024;
+    const int smem = std::min(227 * 1024, std::max(need, floor_));
+    cudaFuncSetAttribute(k_sep_tc<SCALE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_sep_tc<SCALE><<<(unsigned)((P.M + STM - 1) / STM), 128, smem, c->stream>>>(P);
+    c->kernels += 1;
+}
+
+inline int pad16(int x) { return (x + 15) / 16 * 16; }
 }  // namespace
 
 void sep_free(ofks_ctx *c) {
     SepState &S = c->sep;
     for (float *p : {S.S[0], S.S[1], S.S[2], S.St[0], S.St[1], S.St[2], S.lx, S.lyz, S.t0, S.t1})
+        if (p) cudaFree(p);
+    for (void *p : {(void *)S.hS[0], (void *)S.hS[1], (void *)S.hS[2], (void *)S.hSt[0], (void *)S.hSt[1],
+                    (void *)S.hSt[2], (void *)S.hbuf})
         if (p) cudaFree(p);
     S = SepState{};
 }
@@ -229,6 +440,34 @@ int sep_setup(ofks_ctx *c, const double *xyz, const uint8_t *dirichlet) {
     }
     upf(&S.lx, lx);
     upf(&S.lyz, lyz);
+    // tensor-core operands: bf16 axis matrices padded to multiples of 16, and five zeroed
+    // intermediate tensors whose innermost axis is padded the same way
+    S.tc = n[0] <= 256 && n[1] <= 256 && n[2] <= 256;
+    if (S.tc && e == cudaSuccess) {
+        for (int d = 0; d < 3; ++d) {
+            const int P16 = pad16(n[d]);
+            std::vector<__nv_bfloat16> s((size_t)P16 * P16, __float2bfloat16(0.f)), st(s);
+            for (int a = 0; a < n[d]; ++a)
+                for (int i = 0; i < n[d]; ++i) {
+                    s[(size_t)a * P16 + i] = __float2bfloat16((float)Sd[d][(size_t)a * n[d] + i]);
+                    st[(size_t)i * P16 + a] = __float2bfloat16((float)Sd[d][(size_t)a * n[d] + i]);
+                }
+            for (int w = 0; w < 2 && e == cudaSuccess; ++w) {
+                __nv_bfloat16 **dst = w == 0 ? &S.hS[d] : &S.hSt[d];
+                const std::vector<__nv_bfloat16> &h = w == 0 ? s : st;
+                e = cudaMalloc((void **)dst, sizeof(__nv_bfloat16) * h.size());
+                if (e == cudaSuccess) e = cudaMemcpy(*dst, h.data(), sizeof(__nv_bfloat16) * h.size(), cudaMemcpyHostToDevice);
+            }
+        }
+        // [a][b][c~], [k][a][b~], [j][k][a~], [i][j][k~], [c][i][j~], [b][c][i~]  (~ = padded to 16)
+        const int64_t len[6] = {(int64_t)n[0] * n[1] * pad16(n[2]), (int64_t)n[2] * n[0] * pad16(n[1]),
+                                (int64_t)n[1] * n[2] * pad16(n[0]), (int64_t)n[0] * n[1] * pad16(n[2]),
+                                (int64_t)n[2] * n[0] * pad16(n[1]), (int64_t)n[1] * n[2] * pad16(n[0])};
+        int64_t tot = 0;
+        for (int q = 0; q < 6; ++q) { S.hoff[q] = tot; tot += (len[q] + 63) / 64 * 64; }
+        if (e == cudaSuccess) e = cudaMalloc((void **)&S.hbuf, sizeof(__nv_bfloat16) * tot);
+        if (e == cudaSuccess) e = cudaMemset(S.hbuf, 0, sizeof(__nv_bfloat16) * tot);
+    }
     if (e == cudaSuccess) e = cudaMalloc((void **)&S.t0, sizeof(float) * nt);
     if (e == cudaSuccess) e = cudaMalloc((void **)&S.t1, sizeof(float) * nt);
     if (e != cudaSuccess) {
@@ -243,13 +482,47 @@ int sep_setup(ofks_ctx *c, const double *xyz, const uint8_t *dirichlet) {
     return OFKS_OK;
 }
 
-// z = A_sep^-1 r on the interior nodes (full-node vectors; Dirichlet entries of z untouched)
-void sep_apply(ofks_ctx *c, const double *r_full, double *z_full) {
+// One preconditioned step of the Hartree CG on the interior nodes (full-node vectors, Dirichlet
+// entries untouched): with it >= 0 first the CG update of iteration it (see k_sep_gather), then
+// z = A_sep^-1 r, rz[slot] += r.z, and with first != 0 also p = z.
+void sep_cg_step(ofks_ctx *c, int it, int slot, int first) {
     SepState &S = c->sep;
     const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
     const int64_t nt = (int64_t)nx * ny * nz;
     const unsigned g = (unsigned)std::min<int64_t>((nt + 255) / 256, 152 * 8);
-    k_sep_gather<<<g, 256, 0, c->stream>>>(nx, ny, nz, c->st.Ly, c->st.Lz, r_full, S.t0);
+    double *sc = c->d_sc + SC_CG;
+    if (S.tc && c->prm.poisson_sep_tc) {
+        const int px = pad16(nx), py = pad16(ny), pz = pad16(nz);
+        __nv_bfloat16 *B[6];
+        for (int q = 0; q < 6; ++q) B[q] = S.hbuf + S.hoff[q];
+        SepPass P{};
+        auto pass = [&](const __nv_bfloat16 *A, const __nv_bfloat16 *Bt, int M, int K, int N, __nv_bfloat16 *out,
+                        int M1, int M2, int KPo) {
+            P.A = A; P.Bt = Bt; P.M = M; P.K = K; P.KP = pad16(K); P.N = N; P.NP = pad16(N);
+            P.out = out; P.M1 = M1; P.M2 = M2; P.KPo = KPo;
+        };
+        k_sep_gather<__nv_bfloat16><<<g, 256, 0, c->stream>>>(nx, ny, nz, pz, c->st.Ly, c->st.Lz, c->d_cp, c->d_cq,
+                                                              c->d_U, c->d_cr, B[0], sc, it);
+        pass(B[0], S.hSt[2], nx * ny, nz, nz, B[1], nx, ny, py);           // [a][b][c] -> [k][a][b]
+        sep_tc_launch<0>(c, P);
+        pass(B[1], S.hSt[1], nz * nx, ny, ny, B[2], nz, nx, px);           // -> [j][k][a]
+        sep_tc_launch<0>(c, P);
+        pass(B[2], S.hSt[0], ny * nz, nx, nx, B[3], ny, nz, pz);           // -> [i][j][k] / lam
+        P.lr = S.lx; P.lc = S.lyz;
+        sep_tc_launch<1>(c, P);
+        pass(B[3], S.hS[2], nx * ny, nz, nz, B[4], nx, ny, py);            // -> [c][i][j]
+        sep_tc_launch<0>(c, P);
+        pass(B[4], S.hS[1], nz * nx, ny, ny, B[5], nz, nx, px);            // -> [b][c][i]
+        sep_tc_launch<0>(c, P);
+        pass(B[5], S.hS[0], ny * nz, nx, nx, B[0], ny, nz, pz);            // -> [a][b][c]
+        sep_tc_launch<0>(c, P);
+        k_sep_scatter<__nv_bfloat16><<<g, 256, 0, c->stream>>>(nx, ny, nz, pz, c->st.Ly, c->st.Lz, B[0], c->d_cr,
+                                                               c->d_cz, first ? c->d_cp : nullptr, sc, slot);
+        c->kernels += 2;
+        return;
+    }
+    k_sep_gather<float><<<g, 256, 0, c->stream>>>(nx, ny, nz, nz, c->st.Ly, c->st.Lz, c->d_cp, c->d_cq, c->d_U,
+                                                  c->d_cr, S.t0, sc, it);
     // forward: T1[ab][k] = sum_c R[ab][c] Sz[c][k]
     gemm(c, 1, nx * ny, nz, nz, S.t0, 0, S.S[2], 0, S.t1, 0);
     // T2[a][j][k] = sum_b Sy^T[j][b] T1[a][b][k]
@@ -262,6 +535,7 @@ void sep_apply(ofks_ctx *c, const double *r_full, double *z_full) {
     gemm(c, nx, ny, nz, ny, S.S[1], 0, S.t0, (int64_t)ny * nz, S.t1, (int64_t)ny * nz);
     // Z[ab][c] = sum_k U2[ab][k] Sz^T[k][c]
     gemm(c, 1, nx * ny, nz, nz, S.t1, 0, S.St[2], 0, S.t0, 0);
-    k_sep_scatter<<<g, 256, 0, c->stream>>>(nx, ny, nz, c->st.Ly, c->st.Lz, S.t0, z_full);
+    k_sep_scatter<float><<<g, 256, 0, c->stream>>>(nx, ny, nz, nz, c->st.Ly, c->st.Lz, S.t0, c->d_cr, c->d_cz,
+                                                   first ? c->d_cp : nullptr, sc, slot);
     c->kernels += 2;
 }

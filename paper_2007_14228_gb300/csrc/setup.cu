@@ -423,6 +423,7 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
     if (hflag) { free_mesh(c); return ofks_fail(c, OFKS_EINVAL, "set_mesh: degenerate tetrahedron"); }
     c->n_nodes = N; c->n_tets = T; c->n = n; c->nnz = nnz; c->nnz_full = nnz_full;
     c->n_slices = n_slices; c->sell_len = sell_len; c->n_bnd = (int)bnd.size();
+    c->max_slice_w = slice_w.empty() ? 0 : *std::max_element(slice_w.begin(), slice_w.end());
     // the multigrid hierarchy is built on the first Hartree solve that asks for it
     c->h_tetn.swap(tetn);
     c->h_xyz.assign(xyz, xyz + N * 3);

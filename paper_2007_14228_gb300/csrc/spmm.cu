@@ -7,6 +7,8 @@
 // with ld a multiple of the chunk width W; a warp handles one (slice, W-column chunk) pair,
 // each lane one row, and gathers W consecutive doubles of each neighbour row with vector
 // loads.  Padding entries carry value 0 and repeat the row's last column id.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -169,10 +171,142 @@ __global__ void __launch_bounds__(256) k_pcg_apply(int64_t nwarps, int nchunks, 
 
 inline int chunk_width(int ld) { return (ld % 4 == 0) ? 4 : (ld % 2 == 0 ? 2 : 1); }
 
+// ---- half-warp-per-row forms for float32 blocks (the mixed form)
+//
+// With float32 blocks the lane-per-row kernels above are limited by L1 wavefronts, not by
+// HBM: each lane gathers a 16-byte piece of a different neighbour row, so one load instruction
+// touches 32 cache lines.  Here each half-warp takes one row and its 16 lanes split the row's
+// ld columns (VPL consecutive floats each), so one gather instruction reads two contiguous
+// neighbour rows; both half-warps share the slice, whose column ids and values are read with
+// half-warp broadcasts and stay in L1 for the slice's other rows.  Warps stride over
+// (slice, row pair) items; column sums are reduced in the block and added once per block.
+constexpr int RW = 8;                  // warps per block
+
+template <int VPL>
+__device__ __forceinline__ void ldf(const float *__restrict__ p, float (&v)[VPL]) {
+#pragma unroll
+    for (int w = 0; w < VPL; w += 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p + w));
+        v[w] = t.x; v[w + 1] = t.y; v[w + 2] = t.z; v[w + 3] = t.w;
+    }
+}
+
+template <int VPL>
+__device__ __forceinline__ void stf(float *p, const float (&v)[VPL]) {
+#pragma unroll
+    for (int w = 0; w < VPL; w += 4) *reinterpret_cast<float4 *>(p + w) = make_float4(v[w], v[w + 1], v[w + 2], v[w + 3]);
+}
+
+// MODE 0: Y = A X.  MODE 1: Y = A X and colsum[c] += X[:,c].Y[:,c].  MODE 2: the PCG apply of
+// k_pcg_apply (X = Z, Y = P, Y2 = Q, A = L values, B = B values).
+template <int VPL, int MODE>
+__global__ void __launch_bounds__(RW * 32) k_rows_f32(int n_slices, int p, int ld, const int *__restrict__ slice_ptr,
+                                                      const int *__restrict__ slice_w, const int *__restrict__ cols,
+                                                      const int *__restrict__ perm, const float *__restrict__ valA,
+                                                      const float *__restrict__ valB, const float *__restrict__ X,
+                                                      float *Y, float *Y2, const double *__restrict__ beta_col,
+                                                      const double *__restrict__ shift, double *colsum, int first) {
+    __shared__ float red[RW][VPL * 16];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4;
+    const int c0 = (lane & 15) * VPL;
+    const bool on = c0 < ld;
+    float csum[VPL], sh[VPL], bt[VPL];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+        csum[v] = 0.f;
+        sh[v] = (MODE == 2 && on) ? (float)shift[c0 + v] : 0.f;
+        bt[v] = (MODE == 2 && on && !first) ? (float)beta_col[c0 + v] : 0.f;
+    }
+    const int64_t items = (int64_t)n_slices * (SELL_C / 2);
+    for (int64_t w = blockIdx.x * (int64_t)RW + warp; w < items; w += (int64_t)gridDim.x * RW) {
+        const int s = (int)(w / (SELL_C / 2)), l = (int)(w % (SELL_C / 2)) * 2 + half;
+        const int r = perm[s * SELL_C + l];
+        if (r < 0 || !on) continue;
+        const int width = slice_w[s];
+        const int64_t e0 = slice_ptr[s] + l;
+        float aA[VPL], aB[VPL];
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) { aA[v] = 0.f; aB[v] = 0.f; }
+#pragma unroll 8
+        for (int j = 0; j < width; ++j) {
+            const int64_t e = e0 + (int64_t)j * SELL_C;
+            const int c = __ldg(cols + e);
+            const float va = __ldg(valA + e);
+            const float vb = MODE == 2 ? __ldg(valB + e) : 0.f;
+            float x[VPL];
+            ldf<VPL>(X + (int64_t)c * ld + c0, x);
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) {
+                aA[v] = fmaf(va, x[v], aA[v]);
+                if (MODE == 2) aB[v] = fmaf(vb, x[v], aB[v]);
+            }
+        }
+        float *yr = Y + (int64_t)r * ld + c0;
+        if (MODE == 0) {
+            stf<VPL>(yr, aA);
+        } else if (MODE == 1) {
+            float xr[VPL];
+            ldf<VPL>(X + (int64_t)r * ld + c0, xr);
+            stf<VPL>(yr, aA);
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) csum[v] = fmaf(xr[v], aA[v], csum[v]);
+        } else {
+            float zr[VPL], pr[VPL], qr[VPL];
+            ldf<VPL>(X + (int64_t)r * ld + c0, zr);
+            float *q = Y2 + (int64_t)r * ld + c0;
+            if (!first) { ldf<VPL>(yr, pr); ldf<VPL>(q, qr); }
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) {
+                const float tz = 0.5f * aA[v] - sh[v] * aB[v];
+                const float pn = first ? zr[v] : fmaf(bt[v], pr[v], zr[v]);
+                const float qn = first ? tz : fmaf(bt[v], qr[v], tz);
+                pr[v] = pn; qr[v] = qn;
+                csum[v] = fmaf(pn, qn, csum[v]);
+            }
+            stf<VPL>(yr, pr);
+            stf<VPL>(q, qr);
+        }
+    }
+    if (MODE == 0) return;
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) csum[v] += __shfl_down_sync(0xffffffffu, csum[v], 16);
+    if (half == 0)
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) red[warp][c0 + v] = on ? csum[v] : 0.f;
+    __syncthreads();
+    for (int c = threadIdx.x; c < p; c += blockDim.x) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < RW; ++w) t += red[w][c];
+        atomicAdd(colsum + c, (double)t);
+    }
+}
+
+// half-warp-per-row launch for float32 blocks; false when the shapes do not suit it
+template <int MODE>
+bool launch_rows_f32(ofks_ctx *c, int ld, const float *valA, const float *valB, const float *X, float *Y, float *Y2,
+                     const double *beta_col, const double *shift, double *colsum, int first) {
+    if (!c->prm.spmm_f32_rows || ld < 16 || ld % 4 || ld > 256) return false;
+    const int64_t items = (int64_t)c->n_slices * (SELL_C / 2);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + RW - 1) / RW, 152 * 8));
+#define R_(v)                                                                                                      \
+    k_rows_f32<v, MODE><<<grid, RW * 32, 0, c->stream>>>(c->n_slices, c->p, ld, c->d_slice_ptr, c->d_slice_w,     \
+                                                         c->d_cols, c->d_perm, valA, valB, X, Y, Y2, beta_col,    \
+                                                         shift, colsum, first)
+    if (ld <= 64) R_(4);
+    else if (ld <= 128) R_(8);
+    else R_(16);
+#undef R_
+    c->kernels += 1;
+    return true;
+}
+
 }  // namespace
 
 template <class T>
 void launch_sell_spmm(ofks_ctx *c, const T *val, const T *X, T *Y) {
+    if constexpr (sizeof(T) == 4)
+        if (launch_rows_f32<0>(c, c->ld, val, nullptr, X, Y, nullptr, nullptr, nullptr, nullptr, 0)) return;
     const int W = chunk_width(c->ld), nch = c->ld / W;
     const int64_t nw = (int64_t)c->n_slices * nch;
     const unsigned grid = (unsigned)((nw * 32 + 255) / 256);
@@ -185,6 +319,8 @@ void launch_sell_spmm(ofks_ctx *c, const T *val, const T *X, T *Y) {
 
 template <class T>
 void launch_sell_spmm_colnorm(ofks_ctx *c, const T *val, const T *X, T *Y, double *colsum) {
+    if constexpr (sizeof(T) == 4)
+        if (launch_rows_f32<1>(c, c->ld, val, nullptr, X, Y, nullptr, nullptr, nullptr, colsum, 0)) return;
     const int W = chunk_width(c->ld), nch = c->ld / W;
     const int64_t nw = (int64_t)c->n_slices * nch;
     const unsigned grid = (unsigned)((nw * 32 + 255) / 256);
@@ -198,6 +334,8 @@ void launch_sell_spmm_colnorm(ofks_ctx *c, const T *val, const T *X, T *Y, doubl
 template <class T>
 void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, T *P, T *Q, const double *beta_col,
                       const double *shift, double *pq, int first) {
+    if constexpr (sizeof(T) == 4)
+        if (launch_rows_f32<2>(c, c->ld, valL, valB, Zin, P, Q, beta_col, shift, pq, first)) return;
     const int W = chunk_width(c->ld), nch = c->ld / W;
     const int64_t nw = (int64_t)c->n_slices * nch;
     const unsigned grid = (unsigned)((nw * 32 + 255) / 256);

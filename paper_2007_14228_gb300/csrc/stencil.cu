@@ -83,10 +83,12 @@ __global__ void __launch_bounds__(256) k_st_apply(int Ly, int Lz, const StencilT
         if (mi != 0.0) {
             double s = 0.0;
             int e = 0;
+#pragma unroll 4
             for (; e < T.nown; ++e) {   // stored with this row
                 const StencilEntry E = se[e];
                 s = fma(val[T.base + (int64_t)E.slot * T.n + idx], xv[row + E.lin], s);
             }
+#pragma unroll 4
             for (; e < T.nent; ++e) {   // stored with the neighbour (symmetric half)
                 const StencilEntry E = se[e];
                 const StencilType &S = st[E.tp];

@@ -45,7 +45,8 @@ class Params(C.Structure):
                 ("xc", C.c_int32), ("multipole_lmax", C.c_int32), ("poisson_tol", C.c_double),
                 ("poisson_max_iter", C.c_int32), ("poisson_pc", C.c_int32), ("mixed_tol", C.c_double),
                 ("poisson_tol_mixed", C.c_double), ("judge_tau", C.c_double), ("learned_tc", C.c_int32),
-                ("poisson_adaptive", C.c_int32), ("poisson_csr", C.c_int32)]
+                ("poisson_adaptive", C.c_int32), ("poisson_csr", C.c_int32),
+                ("spmm_f32_rows", C.c_int32), ("poisson_sep_tc", C.c_int32)]
 
 
 class Result(C.Structure):

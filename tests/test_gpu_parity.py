@@ -398,3 +398,22 @@ def test_hartree_on_renumbered_mesh_uses_csr(ofks, pc, used):
     pot = pr.potentials(pr.density(X0))
     assert rel(ctx.get_field("U"), pot["U"]) < 1e-9
     ctx.close()
+
+
+@pytest.mark.parametrize("case", ["lih10", "chain_p41"])
+def test_separable_preconditioner_tensor_cores_match_cuda_cores(ofks, case):
+    # the bf16 tensor-core contractions and the float32 CUDA-core ones precondition the same CG:
+    # both reach the oracle's potential in nearly the same number of iterations
+    s = CASES[case]()
+    iters = {}
+    for tc in (1, 0):
+        ctx, pr, V, m = build_pair(ofks, s, poisson_sep_tc=tc)
+        assert ctx.poisson_info()["precond"] == "separable"
+        X0 = pr.initial_guess(V)
+        ctx.set_orbitals(X0)
+        r = ctx.evaluate()
+        pot = pr.potentials(pr.density(X0))
+        assert rel(ctx.get_field("U"), pot["U"]) < 1e-9
+        iters[tc] = r["hartree_iters"]
+        ctx.close()
+    assert abs(iters[1] - iters[0]) <= max(3, iters[0] // 5), iters

@@ -56,7 +56,8 @@ def config_of(args, s, sizes):
             "precond": "PCG x8 (Eq. precondition-T)", "eta": "BB2",
             "hartree": ("CG on the lattice-stencil stiffness, separable (fast-diagonalization) preconditioner, "
                         "tolerance max(1e-12, min(1e-4, 0.01 (kkt+fea)/kkt0)) in both forms"),
-            "l2": "inputs larger than L2 (working set ~7 GB)", "parallelism": f"replicas x{args.gpus}"}
+            "l2": "inputs larger than L2 (working set ~7 GB)", "parallelism": f"replicas x{args.gpus}",
+            "start": f"iterate {args.start} of the seeded run (prepared untimed)"}
 
 
 class Clocks:
@@ -121,9 +122,9 @@ def peaks():
 
 
 # FMA peaks of the GB300 from its unit counts: 152 SMs x 2.07 GHz x 2 flops per FMA x
-# (2 float64 FMA or 128 float32 FMA per SM and clock)
-FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12       # 1.26
-FP32_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 128 / 1e12     # 80.5
+# (2 float64 FMA or 128 float32 FMA per SM and clock); bench.py replaces them with the rates the
+# library's FMA probe measures on the device before the timed runs
+ALU_PEAKS = {"fp64": 152 * 2.07e9 * 2 * 2 / 1e12, "fp32": 152 * 2.07e9 * 2 * 128 / 1e12, "kind": "unit counts x max clock"}
 
 
 def poisson_spmv_model(sizes, pinfo):
@@ -175,12 +176,12 @@ def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, spmv_model=(0, 0), ele
     tflops = flops / per / 1e12
     f_hbm = gbs / hbm_peak
     fp32 = fam == "poisson_pc" or (elem == 4 and fam != "poisson_spmv")
-    alu_peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
+    alu_peak = ALU_PEAKS["fp32"] if fp32 else ALU_PEAKS["fp64"]
     f_alu = tflops / alu_peak
     if f_alu >= f_hbm:
         return {"bound": "alu", "kernel": fam, "achieved": round(tflops, 4), "peak": round(alu_peak, 2),
                 "unit": "TFLOP/s (fp32)" if fp32 else "TFLOP/s (fp64)", "frac": round(f_alu, 4), "traffic": None,
-                "hbm_gbs": round(gbs, 1), "hbm_frac": round(f_hbm, 4), "peak_kind": "unit counts x max clock",
+                "hbm_gbs": round(gbs, 1), "hbm_frac": round(f_hbm, 4), "peak_kind": ALU_PEAKS["kind"],
                 "mean_launch_ms": round(per * 1e3, 4), "launches": st["launches"]}
     return {"bound": "hbm", "kernel": fam, "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
             "frac": round(f_hbm, 4), "traffic": None, "fp64_tflops": round(tflops, 4),
@@ -197,21 +198,31 @@ def oracle_problem(s, m):
     return pcal.Problem(m.xyz, m.tet10, m.dirichlet, s.Z, s.R, prm)
 
 
-SAMPLE = "one oracle PCAL iteration at the full workload without the Hartree Poisson solve"
+SAMPLE = ("one oracle PCAL iteration at the full workload without the Hartree Poisson solve, plus the "
+          "oracle's 8-iteration PCG of Eq. precondition-T on all p columns (the timed GPU steps run with the "
+          "preconditioner active)")
 
 
 def cpu_baseline(s, m):
-    """The oracle as it stands, timed on the host cores (one iteration, see oracle_problem)."""
+    """The oracle as it stands, timed on the host cores: one iteration from the seeded start
+    (see oracle_problem; its multipliers are all positive there, so it solves no linear system)
+    plus one call of its preconditioner with every column active, the per-iteration cost of the
+    regime the GPU steps are timed in."""
+    import numpy as np
     from oracle import pcal
     from paper_2007_14228_gb300 import inputs as I
     pr = oracle_problem(s, m)
     st = pcal.State(X=pr.initial_guess(I.initial_block(pr.n, s.p, 0)))
     t0 = time.perf_counter()
     pcal.iterate(pr, st)
-    dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    G = np.random.default_rng(1).standard_normal((pr.n, s.p))
+    pr.precondition(G, np.full(s.p, -0.5))
+    t2 = time.perf_counter()
+    dt = t2 - t0
     threads = int(os.environ.get("OMP_NUM_THREADS", "0") or 0) or os.cpu_count()
     return {"value": round(1.0 / dt, 6), "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{SAMPLE}; {dt:.1f} s"}, dt
+            "sample": f"{SAMPLE}; {t1 - t0:.1f} s + {t2 - t1:.1f} s"}, dt
 
 
 def time_to_target(ofks, I, target=1e-6, fea_max=1e-7):
@@ -251,13 +262,22 @@ def run_reference(args):
     from oracle import pcal
     pr = oracle_problem(s, m)
     st = pcal.State(X=pr.initial_guess(I.initial_block(pr.n, s.p, 0)))
-    # each step is one oracle iteration (~30-60 s on the host cores at this size): the warm-up
-    # is a single step and at most 3 steps are timed, so the run ends within a few minutes
-    pcal.iterate(pr, st)
+    # each step is one oracle iteration plus one call of its preconditioner with every column
+    # active (the regime the GPU arm times; see cpu_baseline), several seconds on the host cores at
+    # this size: the warm-up is a single step and at most 3 steps are timed
+    import numpy as np
+    G = np.random.default_rng(1).standard_normal((pr.n, s.p))
+    neg = np.full(s.p, -0.5)
+
+    def step():
+        pcal.iterate(pr, st)
+        pr.precondition(G, neg)
+
+    step()
     steps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()
     for _ in range(steps):
-        pcal.iterate(pr, st)
+        step()
     dt = time.perf_counter() - t0
     args.steps, args.warmup = steps, 1
     v = steps / dt
@@ -283,6 +303,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ttc", action="store_true", help="skip the time-to-1e-6 Ha runs")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner form")
+    ap.add_argument("--start", type=int, default=200, help="iterate of the seeded run the timed steps start from")
+    ap.add_argument("--start-state", default=None,
+                    help="state file of the start iterate: loaded if it exists, else written (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -308,10 +332,38 @@ def main():
 
     s = workload(args.workload)
     m = I.make_mesh(s)
+    probe = ofks.Context(local)          # the device's measured FMA rates: the ALU roofline peaks
+    ALU_PEAKS.update({"fp64": round(probe.fma_peak(64), 4), "fp32": round(probe.fma_peak(32), 3),
+                      "kind": "measured by the library's FMA probe"})
+    probe.close()
 
-    def timed(precision, clocks_on):
-        ctx = ofks.context_for(s, m, device=local, beta=10.0, precision=precision, poisson_adaptive=1)
-        ctx.init_orbitals(I.initial_block(m.n_free, s.p, rank))
+    # The timed steps start from iterate START of the seeded run (prepared untimed, as part of the
+    # input): from a random start every multiplier is positive for the first tens of iterations,
+    # so Eq. precondition-T gives T = I and no linear system is solved; most of a solve runs with
+    # the preconditioner active, and that is the regime timed here.
+    import tempfile
+    state = args.start_state or os.path.join(tempfile.mkdtemp(prefix="ofks_bench_"), "start.state")
+    prep = ofks.context_for(s, m, device=local, beta=10.0, precision="mixed", poisson_adaptive=1)
+    if args.start_state and os.path.exists(args.start_state):
+        prep.load_state(state)          # an earlier run prepared the same start iterate
+        rp = prep.evaluate()
+    else:
+        prep.init_orbitals(I.initial_block(m.n_free, s.p, rank))
+        prep.step(args.start)
+        prep.save_state(state)
+        rp = prep.evaluate()
+    import numpy as np
+    lam = np.diag(prep.get_field("Lambda"))
+    start_info = {"start_iterate": args.start, "active_columns": int(np.sum(lam < 0)), "p": s.p,
+                  "E": rp["e_total"], "kkt_rel": rp["kkt"] / rp["kkt0"] if rp["kkt0"] else None}
+    prep.close()
+
+    def timed(precision, clocks_on, precond="pcg"):
+        ctx = ofks.context_for(s, m, device=local, beta=10.0, precision=precision, poisson_adaptive=1,
+                               precond=precond)
+        if precond == "learned":
+            ctx.precond_set_weights(ofks.trained_weights())
+        ctx.load_state(state)
         ctx.step(args.warmup)
         clk = Clocks(local) if clocks_on else None
         if clk:
@@ -334,12 +386,21 @@ def main():
     # plain float64 form (paper's method as stated, float64 throughout)
     ctx64, res64, prof64, _, t64 = timed("fp64", False)
     launches64 = prof64.pop("all_kernels", {"launches": None})["launches"]
-    steps64 = res64["iters"] - args.warmup
+    steps64 = args.steps
     ctx64.close()
+    # learned-preconditioner mixed form (the network judged by Eq. precondition-T's PCG)
+    learned = None
+    if not args.no_learned:
+        ctxl, resl, profl, _, tl = timed("mixed", False, "learned")
+        profl.pop("all_kernels", None)
+        learned = {"value": round(world * args.steps / tl, 4), "unit": UNIT, "ms_per_step": round(tl / args.steps * 1e3, 3),
+                   "judge_accept": resl["judge_accept"], "judge_total": resl["judge_total"],
+                   "kernel_ms": {k: round(v["ms"], 3) for k, v in profl.items() if v["launches"]}}
+        ctxl.close()
     # mixed form: float32 iterations (float64 p x p, energies, convergence test)
     ctx, res, prof, clocks, t = timed("mixed", True)
     launches = prof.pop("all_kernels", {"launches": None})["launches"]
-    steps_done = res["iters"] - args.warmup
+    steps_done = args.steps
     value = world * steps_done / t
     sizes = ctx.sizes()
     pinfo = ctx.poisson_info()
@@ -395,6 +456,7 @@ def main():
                                                             if v["launches"]},
                           "hartree_cg_iters_per_step": round(res64["hartree_total"] / max(steps64, 1), 1)},
            "speedup_vs_plain_fp64": round(value / (world * steps64 / t64), 3),
+           "learned_mixed": learned, "start": start_info,
            "time_to_1e-6_Ha": ttc}
     out["gpu_launches"] = launches
     print(json.dumps(out), flush=True)

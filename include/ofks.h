@@ -137,6 +137,8 @@ typedef struct {
     int32_t switch_iter;    /* OFKS_MIXED: iteration that started the float64 sweep, -1 before */
     int64_t judge_accept;   /* OFKS_PC_LEARNED: columns the judge accepted so far ... */
     int64_t judge_total;    /* ... out of this many judged */
+    int32_t active_last;    /* columns with a negative multiplier (T != I) at the last direction */
+    int64_t active_total;   /* ... summed over the directions computed so far */
 } ofks_result;
 
 /* Fill *prm with the defaults: beta 10, occ 2, tol 1e-8, max_iter 1000, FP64, PCG with 8
@@ -250,6 +252,12 @@ int ofks_get_sizes(ofks_ctx *ctx, int64_t *n_free, int64_t *n_nodes, int64_t *n_
  * Errors: OFKS_EINVAL, OFKS_ESTATE. */
 int ofks_poisson_info(ofks_ctx *ctx, int32_t *format, int64_t *stored, int64_t *rows, int32_t *lattice,
                       int32_t *precond);
+
+/* Measured FMA rate of the context's device in TFLOP/s (2 flops per FMA): precision OFKS_FP64
+ * for float64 or 32 for float32.  Eight independent FMA chains per thread on every SM, about
+ * 0.4 s of device time.  Not part of the method: the denominator of the ALU roofline of the
+ * float64 kernels.  Errors: OFKS_EINVAL, OFKS_ECUDA. */
+int ofks_fma_peak(ofks_ctx *ctx, int32_t precision, double *tflops);
 
 /* History of evaluated iterates: rows of 6 doubles (k, seconds since init, E, kkt, fea,
  * eta).  Copies min(cap, available) rows of the most recent ones into buf; *len = rows. */

@@ -250,6 +250,23 @@ static int precondition_t(ofks_ctx *c) {
         return ofks_cuda_check(c, cudaMemcpyAsync(D, G, sizeof(T) * c->n * ld, cudaMemcpyDeviceToDevice, c->stream),
                                "direction copy");
     }
+    // with no column of negative multiplier every T is I (Eq. precondition-T): D = G, and no
+    // linear system is solved
+    {
+        std::vector<double> act0(ld);
+        cudaMemcpyAsync(act0.data(), c->d_colA + CB_ACTIVE * ld, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream);
+        cudaError_t e0 = cudaStreamSynchronize(c->stream);
+        if (e0 != cudaSuccess) return ofks_cuda_check(c, e0, "preconditioner");
+        int nact = 0;
+        for (int j = 0; j < c->p; ++j) nact += act0[j] != 0.0;
+        c->last_active = nact;
+        c->active_total += nact;
+        if (nact == 0) {
+            ProfScope ps(c, PF_PCG_UPDATE);
+            launch_direction_select(c, b);
+            return ofks_cuda_check(c, cudaGetLastError(), "preconditioner");
+        }
+    }
     bool run_pcg = true, warm = false;
     if (c->prm.precond == OFKS_PC_LEARNED) {
         // D = network(G); each active column is judged by its relative residual |G - T D| / |G| and
@@ -411,6 +428,8 @@ static int run_iterations(ofks_ctx *c, int kmax, ofks_result *res) {
         res->switch_iter = c->switch_k;
         res->judge_accept = c->judge_accept;
         res->judge_total = c->judge_total;
+        res->active_last = c->last_active;
+        res->active_total = c->active_total;
     }
     return rc;
 }

@@ -345,15 +345,22 @@ __global__ void __launch_bounds__(128) k_potential(int64_t T, const int *__restr
             V[q] = w * (vext[t * 4 + q] + h + vx);
             e += w * (0.5 * h + vx - ex) * r;
         }
-        const int *em = emap + t * 100;
-        for (int a = 0; a < 10; ++a)
-            for (int b = 0; b < 10; ++b) {
-                int pos = em[a * 10 + b];
-                if (pos < 0) continue;
-                double m = 0.0;
+        // the local matrix in the precision of the H values (float32 in the mixed form: the
+        // float64 products cost as much as the rest of the kernel on GB300's FP64 pipe)
+        E Ve[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) m += V[q] * p2N(q, a) * p2N(q, b);
-                atomicAdd(valH + pos, (E)m);
+        for (int q = 0; q < 4; ++q) Ve[q] = (E)V[q];
+        const int *em = emap + t * 100;
+#pragma unroll
+        for (int a = 0; a < 10; ++a)
+#pragma unroll
+            for (int b = 0; b < 10; ++b) {
+                const int pos = em[a * 10 + b];
+                if (pos < 0) continue;
+                E m = E(0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) m += Ve[q] * (E)(p2N(q, a) * p2N(q, b));
+                atomicAdd(valH + pos, m);
             }
     }
     e = block_sum(e, sh);

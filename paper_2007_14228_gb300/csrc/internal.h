@@ -192,6 +192,8 @@ struct ofks_ctx {
     std::vector<int> row_deg;                    // pattern row lengths of the free matrices
     double *d_shift_in = nullptr;                // p shifts for ofks_precondition / training calls
     int64_t judge_accept = 0, judge_total = 0;   // learned preconditioner: columns accepted / judged
+    int last_active = 0;                         // columns with T != I at the last direction
+    int64_t active_total = 0;
 
     // ---- profiling
     int64_t kernels = 0;                         // kernel launches issued (all families)

@@ -197,8 +197,41 @@ __device__ __forceinline__ void stf(float *p, const float (&v)[VPL]) {
     for (int w = 0; w < VPL; w += 4) *reinterpret_cast<float4 *>(p + w) = make_float4(v[w], v[w + 1], v[w + 2], v[w + 3]);
 }
 
+// epilogue of one row (own-row loads, stores, column sums) for the three modes
+template <int VPL, int MODE>
+__device__ __forceinline__ void rows_epilogue(int r, int ld, int c0, int first, const float *__restrict__ X, float *Y,
+                                              float *Y2, const float (&aA)[VPL], const float (&aB)[VPL],
+                                              const float (&sh)[VPL], const float (&bt)[VPL], float (&csum)[VPL]) {
+    float *yr = Y + (int64_t)r * ld + c0;
+    if (MODE == 0) {
+        stf<VPL>(yr, aA);
+    } else if (MODE == 1) {
+        float xr[VPL];
+        ldf<VPL>(X + (int64_t)r * ld + c0, xr);
+        stf<VPL>(yr, aA);
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) csum[v] = fmaf(xr[v], aA[v], csum[v]);
+    } else {
+        float zr[VPL], pr[VPL], qr[VPL];
+        ldf<VPL>(X + (int64_t)r * ld + c0, zr);
+        float *q = Y2 + (int64_t)r * ld + c0;
+        if (!first) { ldf<VPL>(yr, pr); ldf<VPL>(q, qr); }
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            const float tz = 0.5f * aA[v] - sh[v] * aB[v];
+            const float pn = first ? zr[v] : fmaf(bt[v], pr[v], zr[v]);
+            const float qn = first ? tz : fmaf(bt[v], qr[v], tz);
+            pr[v] = pn; qr[v] = qn;
+            csum[v] = fmaf(pn, qn, csum[v]);
+        }
+        stf<VPL>(yr, pr);
+        stf<VPL>(q, qr);
+    }
+}
+
 // MODE 0: Y = A X.  MODE 1: Y = A X and colsum[c] += X[:,c].Y[:,c].  MODE 2: the PCG apply of
-// k_pcg_apply (X = Z, Y = P, Y2 = Q, A = L values, B = B values).
+// k_pcg_apply (X = Z, Y = P, Y2 = Q, A = L values, B = B values).  Each half-warp carries two
+// rows of the same slice, so two independent gathers are in flight per step of the entry loop.
 template <int VPL, int MODE>
 __global__ void __launch_bounds__(RW * 32) k_rows_f32(int n_slices, int p, int ld, const int *__restrict__ slice_ptr,
                                                       const int *__restrict__ slice_w, const int *__restrict__ cols,
@@ -217,55 +250,36 @@ __global__ void __launch_bounds__(RW * 32) k_rows_f32(int n_slices, int p, int l
         sh[v] = (MODE == 2 && on) ? (float)shift[c0 + v] : 0.f;
         bt[v] = (MODE == 2 && on && !first) ? (float)beta_col[c0 + v] : 0.f;
     }
-    const int64_t items = (int64_t)n_slices * (SELL_C / 2);
+    const int64_t items = (int64_t)n_slices * (SELL_C / 4);
     for (int64_t w = blockIdx.x * (int64_t)RW + warp; w < items; w += (int64_t)gridDim.x * RW) {
-        const int s = (int)(w / (SELL_C / 2)), l = (int)(w % (SELL_C / 2)) * 2 + half;
-        const int r = perm[s * SELL_C + l];
-        if (r < 0 || !on) continue;
+        const int s = (int)(w / (SELL_C / 4));
+        const int l0 = (int)(w % (SELL_C / 4)) * 4 + half * 2, l1 = l0 + 1;
+        const int r0 = perm[s * SELL_C + l0], r1 = perm[s * SELL_C + l1];
+        if (!on || (r0 < 0 && r1 < 0)) continue;
         const int width = slice_w[s];
-        const int64_t e0 = slice_ptr[s] + l;
-        float aA[VPL], aB[VPL];
+        const int64_t e0 = slice_ptr[s] + l0;          // row l1's entries sit one further
+        float a0[VPL], b0[VPL], a1[VPL], b1[VPL];
 #pragma unroll
-        for (int v = 0; v < VPL; ++v) { aA[v] = 0.f; aB[v] = 0.f; }
-#pragma unroll 8
+        for (int v = 0; v < VPL; ++v) { a0[v] = 0.f; b0[v] = 0.f; a1[v] = 0.f; b1[v] = 0.f; }
+#pragma unroll 4
         for (int j = 0; j < width; ++j) {
             const int64_t e = e0 + (int64_t)j * SELL_C;
-            const int c = __ldg(cols + e);
-            const float va = __ldg(valA + e);
-            const float vb = MODE == 2 ? __ldg(valB + e) : 0.f;
-            float x[VPL];
-            ldf<VPL>(X + (int64_t)c * ld + c0, x);
+            const int2 cc = *reinterpret_cast<const int2 *>(cols + e);      // rows l0, l1 (8-byte aligned: l0 even)
+            const float2 va = *reinterpret_cast<const float2 *>(valA + e);
+            float2 vb = make_float2(0.f, 0.f);
+            if (MODE == 2) vb = *reinterpret_cast<const float2 *>(valB + e);
+            float x0[VPL], x1[VPL];
+            ldf<VPL>(X + (int64_t)cc.x * ld + c0, x0);
+            ldf<VPL>(X + (int64_t)cc.y * ld + c0, x1);
 #pragma unroll
             for (int v = 0; v < VPL; ++v) {
-                aA[v] = fmaf(va, x[v], aA[v]);
-                if (MODE == 2) aB[v] = fmaf(vb, x[v], aB[v]);
+                a0[v] = fmaf(va.x, x0[v], a0[v]);
+                a1[v] = fmaf(va.y, x1[v], a1[v]);
+                if (MODE == 2) { b0[v] = fmaf(vb.x, x0[v], b0[v]); b1[v] = fmaf(vb.y, x1[v], b1[v]); }
             }
         }
-        float *yr = Y + (int64_t)r * ld + c0;
-        if (MODE == 0) {
-            stf<VPL>(yr, aA);
-        } else if (MODE == 1) {
-            float xr[VPL];
-            ldf<VPL>(X + (int64_t)r * ld + c0, xr);
-            stf<VPL>(yr, aA);
-#pragma unroll
-            for (int v = 0; v < VPL; ++v) csum[v] = fmaf(xr[v], aA[v], csum[v]);
-        } else {
-            float zr[VPL], pr[VPL], qr[VPL];
-            ldf<VPL>(X + (int64_t)r * ld + c0, zr);
-            float *q = Y2 + (int64_t)r * ld + c0;
-            if (!first) { ldf<VPL>(yr, pr); ldf<VPL>(q, qr); }
-#pragma unroll
-            for (int v = 0; v < VPL; ++v) {
-                const float tz = 0.5f * aA[v] - sh[v] * aB[v];
-                const float pn = first ? zr[v] : fmaf(bt[v], pr[v], zr[v]);
-                const float qn = first ? tz : fmaf(bt[v], qr[v], tz);
-                pr[v] = pn; qr[v] = qn;
-                csum[v] = fmaf(pn, qn, csum[v]);
-            }
-            stf<VPL>(yr, pr);
-            stf<VPL>(q, qr);
-        }
+        if (r0 >= 0) rows_epilogue<VPL, MODE>(r0, ld, c0, first, X, Y, Y2, a0, b0, sh, bt, csum);
+        if (r1 >= 0) rows_epilogue<VPL, MODE>(r1, ld, c0, first, X, Y, Y2, a1, b1, sh, bt, csum);
     }
     if (MODE == 0) return;
 #pragma unroll
@@ -287,7 +301,7 @@ template <int MODE>
 bool launch_rows_f32(ofks_ctx *c, int ld, const float *valA, const float *valB, const float *X, float *Y, float *Y2,
                      const double *beta_col, const double *shift, double *colsum, int first) {
     if (!c->prm.spmm_f32_rows || ld < 16 || ld % 4 || ld > 256) return false;
-    const int64_t items = (int64_t)c->n_slices * (SELL_C / 2);
+    const int64_t items = (int64_t)c->n_slices * (SELL_C / 4);
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + RW - 1) / RW, 152 * 8));
 #define R_(v)                                                                                                      \
     k_rows_f32<v, MODE><<<grid, RW * 32, 0, c->stream>>>(c->n_slices, c->p, ld, c->d_slice_ptr, c->d_slice_w,     \

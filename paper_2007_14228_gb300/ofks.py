@@ -26,7 +26,7 @@ STATIC_NUCLEI_MAX = 1024          # OFKS_STATIC_NUCLEI_MAX
 SYMBOLS = ("ofks_default_params", "ofks_create", "ofks_destroy", "ofks_last_error", "ofks_set_mesh",
            "ofks_set_nuclei", "ofks_set_nuclei_static", "ofks_set_params", "ofks_init_orbitals", "ofks_set_orbitals",
            "ofks_get_orbitals", "ofks_step", "ofks_solve", "ofks_evaluate", "ofks_rayleigh_ritz",
-           "ofks_get_field", "ofks_apply", "ofks_get_sizes", "ofks_poisson_info", "ofks_get_history", "ofks_save_state",
+           "ofks_get_field", "ofks_apply", "ofks_get_sizes", "ofks_poisson_info", "ofks_fma_peak", "ofks_get_history", "ofks_save_state",
            "ofks_load_state", "ofks_profile", "ofks_profile_get", "ofks_precond_init", "ofks_precond_get_weights",
            "ofks_precond_set_weights", "ofks_precondition", "ofks_train_precond_step", "ofks_precond_grads")
 
@@ -53,7 +53,8 @@ class Result(C.Structure):
     _fields_ = [("e_total", C.c_double), ("e_nuc", C.c_double), ("kkt", C.c_double), ("fea", C.c_double),
                 ("kkt0", C.c_double), ("eta", C.c_double), ("iters", C.c_int32), ("converged", C.c_int32),
                 ("seconds", C.c_double), ("hartree_iters", C.c_int32), ("hartree_total", C.c_int32),
-                ("switch_iter", C.c_int32), ("judge_accept", C.c_int64), ("judge_total", C.c_int64)]
+                ("switch_iter", C.c_int32), ("judge_accept", C.c_int64), ("judge_total", C.c_int64),
+                ("active_last", C.c_int32), ("active_total", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -97,6 +98,7 @@ def load(path: str = LIB_PATH):
                                      C.POINTER(i64)]),
         "ofks_poisson_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32),
                                         C.POINTER(i32)]),
+        "ofks_fma_peak": (C.c_int, [vp, i32, C.POINTER(dbl)]),
         "ofks_get_history": (C.c_int, [vp, _dp, i32, C.POINTER(i32)]),
         "ofks_save_state": (C.c_int, [vp, C.c_char_p]),
         "ofks_load_state": (C.c_int, [vp, C.c_char_p]),
@@ -242,6 +244,12 @@ class Context:
         self._chk(self.lib.ofks_get_sizes(self.h, *[C.byref(x) for x in v]))
         return dict(zip(("n_free", "n_nodes", "n_tets", "nnz", "nnz_full"), (x.value for x in v)))
 
+    def fma_peak(self, bits: int = 64) -> float:
+        """Measured FMA rate of the device in TFLOP/s (float64 or float32)."""
+        t = C.c_double()
+        self._chk(self.lib.ofks_fma_peak(self.h, PRECISION["fp64"] if bits == 64 else 32, C.byref(t)))
+        return t.value
+
     def poisson_info(self) -> dict:
         fmt, stored, rows, pc = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
         lat = (C.c_int32 * 3)()
@@ -335,6 +343,12 @@ class Context:
                 break
             out[name.value.decode()] = {"launches": n.value, "ms": ms.value}
         return out
+
+
+def trained_weights():
+    """The learned preconditioner's committed weights (see precond_weights.json for how they
+    were trained)."""
+    return np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "precond_weights.npy"))
 
 
 def context_for(system, mesh, device: int = 0, **params) -> Context:

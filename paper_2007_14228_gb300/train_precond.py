@@ -13,6 +13,8 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
+import sys
 import time
 
 import numpy as np
@@ -21,10 +23,21 @@ from . import inputs as I
 from . import ofks
 
 
+def system_and_mesh(seed: int, cells: int):
+    """A random nuclei set on the smallest grid of at least `cells` per axis that gives every
+    segment between its anchors its two cells (many nuclei need more than the drawn size)."""
+    for c in range(cells, cells + 40):
+        s = I.random_nuclei(seed, cells=(c, c, c))
+        try:
+            return s, I.make_mesh(s)
+        except ValueError:
+            continue
+    raise ValueError(f"no mesh for seed {seed}")
+
+
 def pairs_from_system(seed: int, cells: int, samples, rng, device=0, width=64, weights=None):
     """Yield (ctx, G, shifts, Dstar) at the sampled iterations of one random system."""
-    s = I.random_nuclei(seed, cells=(cells, cells, cells))
-    m = I.make_mesh(s)
+    s, m = system_and_mesh(seed, cells)
     ctx = ofks.context_for(s, m, device=device, beta=10.0)
     if weights is not None:
         ctx.precond_set_weights(weights)
@@ -46,7 +59,8 @@ def pairs_from_system(seed: int, cells: int, samples, rng, device=0, width=64, w
     ctx.close()
 
 
-def train(systems=100, first_seed=1, steps_per_pair=3, lr=1e-3, width=64, samples=(5, 10, 15, 20, 30, 40, 50),
+def train(systems=100, first_seed=1, steps_per_pair=3, lr=1e-3, width=64,
+          samples=(5, 10, 20, 30, 50, 80, 120, 160, 200, 250, 300),
           device=0, log=None, weights=None):
     rng = np.random.default_rng(first_seed)
     w = weights
@@ -67,15 +81,27 @@ def train(systems=100, first_seed=1, steps_per_pair=3, lr=1e-3, width=64, sample
     return w, history, n_pairs
 
 
+def validate(weights, seeds, cells: int = 16, samples=(10, 30), device=0):
+    """Mean loss of the network on pairs from held-out systems (no update)."""
+    losses = []
+    for seed in seeds:
+        for ctx, G, shifts, Dstar in pairs_from_system(seed, cells, samples, None, device, weights=weights):
+            loss, _ = ctx.precond_grads(G, shifts, Dstar)
+            losses.append(loss)
+    return float(np.mean(losses)) if losses else None
+
+
 def evaluate(weights, seed: int, cells: int, device=0, tol=1e-6, max_iter=600):
     """Iterations to (kkt + fea)/kkt0 < tol with no preconditioner, the learned one and PCG."""
-    s = I.random_nuclei(seed, cells=(cells, cells, cells))
-    m = I.make_mesh(s)
+    s, m = system_and_mesh(seed, cells)
     V = I.initial_block(m.n_free, s.p, seed)
     out = {"seed": seed, "cells": cells, "p": s.p}
-    for mode in ("none", "learned", "pcg"):
-        ctx = ofks.context_for(s, m, device=device, beta=10.0, tol=tol, max_iter=max_iter, precond=mode)
-        if mode == "learned":
+    for mode in ("none", "learned", "learned_unjudged", "pcg"):
+        # learned_unjudged: every network direction with G.D > 0 is taken (the network alone)
+        tau = 1e30 if mode == "learned_unjudged" else 0.5
+        ctx = ofks.context_for(s, m, device=device, beta=10.0, tol=tol, max_iter=max_iter,
+                               precond="learned" if mode.startswith("learned") else mode, judge_tau=tau)
+        if mode.startswith("learned"):
             ctx.precond_set_weights(weights)
         ctx.init_orbitals(V)
         r = ctx.solve(allow_notconv=True)
@@ -94,11 +120,19 @@ def main():
     ap.add_argument("--steps-per-pair", type=int, default=3)
     ap.add_argument("--out", default="precond_weights.npy")
     ap.add_argument("--eval-seed", type=int, default=10_000)
+    ap.add_argument("--held-out", type=int, default=4, help="validation systems (seeds after the eval seed)")
     args = ap.parse_args()
+    held = list(range(args.eval_seed + 1, args.eval_seed + 1 + args.held_out))
     w, hist, n = train(args.systems, args.first_seed, args.steps_per_pair, args.lr, args.width,
                        log=lambda d: print(json.dumps(d), flush=True))
     np.save(args.out, w)
-    print(json.dumps({"pairs": n, "final_loss": hist[-1] if hist else None, "out": args.out}), flush=True)
+    info = {"pairs": n, "systems": args.systems, "first_seed": args.first_seed, "width": args.width,
+            "lr": args.lr, "steps_per_pair": args.steps_per_pair, "final_loss": hist[-1] if hist else None,
+            "held_out_seeds": held, "held_out_loss": validate(w, held), "held_out_loss_jacobi": validate(None, held),
+            "command": "python -m paper_2007_14228_gb300.train_precond " + " ".join(sys.argv[1:])}
+    with open(os.path.splitext(args.out)[0] + ".json", "w") as f:
+        json.dump(info, f, indent=1)
+    print(json.dumps(info), flush=True)
     print(json.dumps({"eval": evaluate(w, args.eval_seed, 16)}), flush=True)
 
 

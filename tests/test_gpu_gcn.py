@@ -125,3 +125,21 @@ def test_tensor_core_layer_matches_cuda_cores(ofks):
     assert err < 3e-2, err
     assert np.all(np.isfinite(outs[1]))
     ctx.close()
+
+
+def test_trained_network_beats_the_jacobi_step_on_held_out_systems(ofks):
+    # the committed weights (trained on seeds 1..150 by the library's own kernels) against the
+    # untrained network, whose zero last layer makes it the Jacobi step, on pairs (G, T^-1 G)
+    # from held-out random systems at iterations where multipliers are negative
+    import os
+    from paper_2007_14228_gb300 import train_precond as T
+    w = np.load(os.path.join(os.path.dirname(ofks.__file__), "precond_weights.npy"))
+    trained, jacobi = [], []
+    for seed in (10005, 10006):
+        for ctx, G, shifts, Dstar in T.pairs_from_system(seed, 14, (60, 120), None):
+            ctx.precond_set_weights(w)
+            trained.append(ctx.precond_grads(G, shifts, Dstar)[0])
+            ctx.precond_init(64, seed)
+            jacobi.append(ctx.precond_grads(G, shifts, Dstar)[0])
+    assert trained and len(trained) == len(jacobi)
+    assert np.mean(trained) < 0.85 * np.mean(jacobi), (np.mean(trained), np.mean(jacobi))

@@ -282,7 +282,9 @@ int ofks_precond_set_weights(ofks_ctx *ctx, const float *w, int64_t count);
 
 /* D (n_free x p, host) = preconditioned directions of G (host) for per-column shifts (host, p;
  * columns with shift >= 0 take D = G): mode OFKS_PC_PCG, OFKS_PC_EXACT or OFKS_PC_LEARNED (the
- * network alone, no judge).  Uses the context's scratch blocks; iteration history is kept. */
+ * network alone, no judge).  Uses the context's scratch blocks; iteration history is kept.  A
+ * mixed context (OFKS_MIXED, float32 blocks allocated) runs OFKS_PC_PCG in float32 as its
+ * iterations do. */
 int ofks_precondition(ofks_ctx *ctx, int32_t mode, const double *G, const double *shifts, double *D);
 
 /* One Adam step (learning rate lr) of the network on the pair (G, Dstar) with per-column

@@ -279,7 +279,7 @@ static int precondition_t(ofks_ctx *c) {
         gcn_unpack<T>(c, c->gcn.Dn, D);
         {
             ProfScope ps(c, PF_PCG_SPMM);
-            launch_pcg_apply(c, vals_L<T>(c), vals_B<T>(c), (const T *)D, b.P, b.Q, c->d_colA + CB_BETA * ld,
+            launch_pcg_apply(c, vals_L<T>(c), vals_B<T>(c), (const T *)D, 0, b.P, b.Q, c->d_colA + CB_BETA * ld,
                              c->d_colA + CB_SHIFT * ld, c->d_colA + CB_PQ * ld, 1);
         }
         launch_judge(c, b);
@@ -321,7 +321,8 @@ static int precondition_t(ofks_ctx *c) {
     for (int it = 0; it < max_it; ++it) {
         {
             ProfScope ps(c, PF_PCG_SPMM);
-            launch_pcg_apply(c, vals_L<T>(c), vals_B<T>(c), (const T *)b.Z, b.P, b.Q, c->d_colA + CB_BETA * ld,
+            launch_pcg_apply(c, vals_L<T>(c), vals_B<T>(c), (const T *)b.Z, pcg_zc<T>(c) ? 1 : 0, b.P, b.Q,
+                             c->d_colA + CB_BETA * ld,
                              c->d_colA + CB_SHIFT * ld, c->d_colA + CB_PQ * ld, it == 0 ? 1 : 0);
         }
         {
@@ -929,8 +930,19 @@ int ofks_precondition(ofks_ctx *c, int32_t mode, const double *G, const double *
     if (rc) return rc;
     const int saved = c->prm.precond, phase = c->phase;
     c->prm.precond = mode;
-    c->phase = 64;
-    rc = precondition_t<double>(c);
+    // a mixed context runs the float32 preconditioner of its float32 iterations (G rounded to
+    // float32 on the way in, D widened on the way out)
+    const bool f32 = mode == OFKS_PC_PCG && c->prm.precision == OFKS_MIXED && c->mixed_alloc;
+    const int64_t cnt = c->n * (int64_t)ld;
+    if (f32) {
+        launch_convert(c, (const double *)c->b64.G[c->cur], c->b32.G[c->cur], cnt);
+        c->phase = 32;
+        rc = precondition_t<float>(c);
+        if (!rc) launch_convert(c, (const float *)c->b32.D[c->cur], c->b64.D[c->cur], cnt);
+    } else {
+        c->phase = 64;
+        rc = precondition_t<double>(c);
+    }
     c->prm.precond = saved;
     c->phase = phase;
     if (rc) return rc;

@@ -263,20 +263,25 @@ __device__ __forceinline__ void col_reduce(double acc, int j, bool active, int l
         if (sh[k] != 0.0) atomicAdd(colsum + k, sh[k]);
 }
 
+// index of element (r, j) of Z: row-major, or chunk-major ((j / 4) n + r) 4 + j % 4 (zc)
+__device__ __forceinline__ int64_t zidx(int zc, int64_t e, int64_t r, int j, int64_t n) {
+    return zc ? (((int64_t)(j >> 2) * n + r) << 2) + (j & 3) : e;
+}
+
 // PCG start: W = 1/diag with diag = dL/2 - shift_c dB, D = 0, R = G, Z = G W, rz[c] = sum R Z
 template <class T>
 __global__ void __launch_bounds__(256) k_pcg_init(int64_t n, int p, int ld, int64_t stride,
                                                   const T *__restrict__ G,
                                                   const double *__restrict__ dL,
                                                   const double *__restrict__ dB, const double *cb,
-                                                  T *W, T *D, T *R, T *Z, double *rz) {
+                                                  T *W, T *D, T *R, T *Z, double *rz, int zc) {
     T acc = T(0);
     ELEM_BEGIN
         const T sh = (T)cb[CB_SHIFT * ld + j];
         const T w = T(1) / (T(0.5) * (T)dL[r] - sh * (T)dB[r]);
         const T gv = G[e];
         const T z = gv * w;
-        W[e] = w; D[e] = T(0); R[e] = gv; Z[e] = z;
+        W[e] = w; D[e] = T(0); R[e] = gv; Z[zidx(zc, e, r, j, n)] = z;
         acc = fma(gv, z, acc);
     ELEM_END
     col_reduce((double)acc, j, gid < stride, ld, p, rz);
@@ -305,14 +310,14 @@ __global__ void __launch_bounds__(256) k_pcg_init_warm(int64_t n, int p, int ld,
                                                        const T *__restrict__ G, const T *__restrict__ Q,
                                                        const double *__restrict__ dL,
                                                        const double *__restrict__ dB, const double *cb,
-                                                       T *W, T *R, T *Z, double *rz) {
+                                                       T *W, T *R, T *Z, double *rz, int zc) {
     T acc = T(0);
     ELEM_BEGIN
         const T sh = (T)cb[CB_SHIFT * ld + j];
         const T w = T(1) / (T(0.5) * (T)dL[r] - sh * (T)dB[r]);
         const T rv = G[e] - Q[e];
         const T z = rv * w;
-        W[e] = w; R[e] = rv; Z[e] = z;
+        W[e] = w; R[e] = rv; Z[zidx(zc, e, r, j, n)] = z;
         acc = fma(rv, z, acc);
     ELEM_END
     col_reduce((double)acc, j, gid < stride, ld, p, rz);
@@ -324,14 +329,14 @@ __global__ void __launch_bounds__(256) k_pcg_update(int64_t n, int p, int ld, in
                                                     const T *__restrict__ W,
                                                     const T *__restrict__ P,
                                                     const T *__restrict__ Q, T *D, T *R,
-                                                    T *Z, double *rzn) {
+                                                    T *Z, double *rzn, int zc) {
     T acc = T(0);
     const T al = (T)cb[CB_ALPHA * ld + (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) % ld];
     ELEM_BEGIN
         D[e] = fma(al, P[e], D[e]);
         const T rv = fma(-al, Q[e], R[e]);
         const T z = rv * W[e];
-        R[e] = rv; Z[e] = z;
+        R[e] = rv; Z[zidx(zc, e, r, j, n)] = z;
         acc = fma(rv, z, acc);
     ELEM_END
     col_reduce((double)acc, j, gid < stride, ld, p, rzn);
@@ -494,6 +499,9 @@ void launch_gram2(ofks_ctx *c, const T *X, const T *A, const T *B, double *XA, d
     k_mirror2<<<4, 256, 0, c->stream>>>(p, ld, XA, XB);
 }
 
+template <> bool pcg_zc<double>(const ofks_ctx *) { return false; }
+template <> bool pcg_zc<float>(const ofks_ctx *c) { return c->n_tslices > 0 && c->ld >= 4 && c->ld % 4 == 0; }
+
 // grid of 256-thread blocks whose total thread count is a multiple of ld
 struct ElemGrid { unsigned blocks; int64_t stride; };
 static ElemGrid elem_grid(int64_t n, int ld) {
@@ -541,7 +549,8 @@ void launch_pcg_init(ofks_ctx *c, Blocks<T> &b) {
     cudaMemsetAsync(cb + CB_RZ * ld, 0, sizeof(double) * ld, c->stream);
     const ElemGrid g = elem_grid(c->n, ld);
     k_pcg_init<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, b.G[c->cur], c->d_dL, c->d_dB, cb,
-                                                   b.W, b.D[c->cur], b.R, b.Z, cb + CB_RZ * ld);
+                                                   b.W, b.D[c->cur], b.R, b.Z, cb + CB_RZ * ld,
+                                                   pcg_zc<T>(c) ? 1 : 0);
 }
 
 template <class T>
@@ -563,7 +572,8 @@ void launch_pcg_init_warm(ofks_ctx *c, Blocks<T> &b) {
     cudaMemsetAsync(cb + CB_RZ * ld, 0, sizeof(double) * ld, c->stream);
     const ElemGrid g = elem_grid(c->n, ld);
     k_pcg_init_warm<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, b.G[c->cur], b.Q, c->d_dL, c->d_dB,
-                                                        cb, b.W, b.R, b.Z, cb + CB_RZ * ld);
+                                                        cb, b.W, b.R, b.Z, cb + CB_RZ * ld,
+                                                        pcg_zc<T>(c) ? 1 : 0);
 }
 
 template <class T>
@@ -573,7 +583,7 @@ void launch_pcg_update(ofks_ctx *c, Blocks<T> &b) {
     double *cb = c->d_colA;
     const ElemGrid g = elem_grid(c->n, ld);
     k_pcg_update<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, cb, b.W, b.P, b.Q, b.D[c->cur], b.R,
-                                                     b.Z, cb + CB_RZN * ld);
+                                                     b.Z, cb + CB_RZN * ld, pcg_zc<T>(c) ? 1 : 0);
 }
 
 template <class T>

@@ -123,6 +123,13 @@ struct ofks_ctx {
     int *d_cols = nullptr;                       // sell_len free column ids
     int *d_perm = nullptr;                       // n_slices*32 -> free row id or -1
     int max_slice_w = 0;                         // widest slice (entries per row)
+    // type-grouped SELL of L and B (float32 values) for the float32 PCG on lattice meshes: slices
+    // of 32 free rows of one lattice node type, consecutive along the third axis, so neighbour
+    // rows at one offset are two rows apart and the chunk-major Z they gather is nearly contiguous
+    int n_tslices = 0;
+    int64_t tsell_len = 0;
+    int *d_tslice_ptr = nullptr, *d_tslice_w = nullptr, *d_tcols = nullptr, *d_tperm = nullptr;
+    float *d_tvalL = nullptr, *d_tvalB = nullptr;
     double *d_valL = nullptr, *d_valB = nullptr, *d_valH = nullptr;
     double *d_dL = nullptr, *d_dB = nullptr;     // diagonals of L and B (free)
     // full-node stiffness for the Hartree Poisson problem (CSR)
@@ -255,12 +262,14 @@ template <class T> void launch_sell_spmm(ofks_ctx *c, const T *val, const T *X, 
 template <class T> void launch_sell_spmm_ld(ofks_ctx *c, const T *val, const T *X, T *Y, int ld);
 template <class T> void launch_sell_spmm_colnorm(ofks_ctx *c, const T *val, const T *X, T *Y, double *colsum);
 template <class T>
-void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, T *P, T *Q, const double *beta_col,
+void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, int zc, T *P, T *Q, const double *beta_col,
                       const double *shift, double *pq, int first);
 
 // ---- block.cu (tall-skinny products and vector updates)
 template <class T> void launch_gram2(ofks_ctx *c, const T *X, const T *A, const T *B, double *XA, double *XB);
 template <class T> void launch_grad_update(ofks_ctx *c, Blocks<T> &b);
+// float32 PCG blocks keep Z chunk-major (4 columns x n rows per chunk) on lattice meshes
+template <class T> bool pcg_zc(const ofks_ctx *c);
 template <class T> void launch_pcg_init(ofks_ctx *c, Blocks<T> &b);
 template <class T> void launch_pcg_update(ofks_ctx *c, Blocks<T> &b);
 template <class T> void launch_judge(ofks_ctx *c, Blocks<T> &b);

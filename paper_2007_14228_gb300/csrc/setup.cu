@@ -27,6 +27,16 @@ __constant__ int c_mass420[10][10] = {
     {-4, -6, -6, -4, 16, 16, 32, 8, 16, 16},  {-6, -4, -4, -6, 16, 16, 8, 32, 16, 16},
     {-6, -4, -6, -4, 16, 8, 16, 16, 32, 16},  {-6, -6, -4, -4, 8, 16, 16, 16, 16, 32}};
 
+// float32 values of the type-grouped SELL gathered from the float64 main SELL (-1: padding)
+__global__ void k_tsell_values(int64_t len, const int *__restrict__ pos, const double *__restrict__ valL,
+                               const double *__restrict__ valB, float *tL, float *tB) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= len) return;
+    const int q = pos[e];
+    tL[e] = q >= 0 ? (float)valL[q] : 0.f;
+    tB[e] = q >= 0 ? (float)valB[q] : 0.f;
+}
+
 void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)> &f) {
     unsigned nt = std::thread::hardware_concurrency();
     nt = std::max(1u, std::min(nt, 32u));
@@ -191,6 +201,9 @@ void free_mesh(ofks_ctx *c) {
     gcn_free(c);
     stencil_free(c);
     sep_free(c);
+    dev_free(c->d_tslice_ptr); dev_free(c->d_tslice_w); dev_free(c->d_tcols); dev_free(c->d_tperm);
+    dev_free(c->d_tvalL); dev_free(c->d_tvalB);
+    c->n_tslices = 0; c->tsell_len = 0;
     c->amg_tried = false;
     std::vector<int>().swap(c->h_tetn);
     std::vector<double>().swap(c->h_xyz);
@@ -414,6 +427,77 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
     }
     c->n_nodes = N;
     stencil_fill(c);
+    // type-grouped SELL for the float32 PCG (lattice meshes): rows of each lattice node type in
+    // lattice order, so a slice is 32 rows of one type two steps apart along the third axis
+    if (c->st.on) {
+        const int Lx = c->st.Lx, Ly = c->st.Ly, Lz = c->st.Lz;
+        std::vector<int> tp;
+        tp.reserve(n);
+        for (int t = 0; t < 8; ++t)
+            for (int a = (t >> 2) & 1; a < Lx; a += 2)
+                for (int b = (t >> 1) & 1; b < Ly; b += 2)
+                    for (int cz = t & 1; cz < Lz; cz += 2) {
+                        const int f = fidx[((int64_t)a * Ly + b) * Lz + cz];
+                        if (f >= 0) tp.push_back(f);
+                    }
+        if ((int64_t)tp.size() == n) {
+            const int nts = (int)((n + SELL_C - 1) / SELL_C);
+            std::vector<int> tptr(nts + 1, 0), tw(nts, 0), tperm((int64_t)nts * SELL_C, -1);
+            int64_t acc2 = 0;
+            bool fits = true;
+            for (int s = 0; s < nts; ++s) {
+                int w = 0;
+                for (int l = 0; l < SELL_C; ++l) {
+                    const int64_t k = (int64_t)s * SELL_C + l;
+                    if (k < n) { tperm[k] = tp[k]; w = std::max(w, rowlen[tp[k]]); }
+                }
+                tw[s] = w;
+                if (acc2 >= ((int64_t)1 << 31)) fits = false;
+                tptr[s] = (int)acc2;
+                acc2 += (int64_t)w * SELL_C;
+            }
+            fits = fits && acc2 < ((int64_t)1 << 31);
+            if (fits) {
+                tptr[nts] = (int)acc2;
+                std::vector<int> tcol(acc2, 0), tpos(acc2, -1);
+                parallel_for(nts, [&](int64_t a0, int64_t a1) {
+                    for (int64_t s = a0; s < a1; ++s)
+                        for (int l = 0; l < SELL_C; ++l) {
+                            const int64_t k = s * SELL_C + l;
+                            if (k >= n) continue;
+                            const int r = tp[k], len = rowlen[r];
+                            const int64_t sp = inv[r];
+                            for (int j = 0; j < tw[s]; ++j) {
+                                const int jj = std::min(j, len - 1);
+                                const int64_t e = tptr[s] + (int64_t)j * SELL_C + l;
+                                tcol[e] = rcol[rptr[r] + jj];
+                                if (j < len) tpos[e] = (int)(slice_ptr[sp / SELL_C] + (int64_t)j * SELL_C + sp % SELL_C);
+                            }
+                        }
+                });
+                int *d_tpos = nullptr;
+                if ((rc = dev_upload(c, &c->d_tslice_ptr, tptr.data(), tptr.size())) ||
+                    (rc = dev_upload(c, &c->d_tslice_w, tw.data(), tw.size())) ||
+                    (rc = dev_upload(c, &c->d_tperm, tperm.data(), tperm.size())) ||
+                    (rc = dev_upload(c, &c->d_tcols, tcol.data(), tcol.size())) ||
+                    (rc = dev_upload(c, &d_tpos, tpos.data(), tpos.size())) ||
+                    (rc = dev_zeros(c, &c->d_tvalL, acc2)) || (rc = dev_zeros(c, &c->d_tvalB, acc2))) {
+                    dev_free(d_tpos);
+                    dev_free(d_xyz); dev_free(d_fmap); dev_free(d_dpos); dev_free(d_fdiag); dev_free(d_interior);
+                    dev_free(d_flag);
+                    free_mesh(c);
+                    return rc;
+                }
+                k_tsell_values<<<(unsigned)((acc2 + 255) / 256), 256, 0, c->stream>>>(acc2, d_tpos, c->d_valL, c->d_valB,
+                                                                                     c->d_tvalL, c->d_tvalB);
+                cudaStreamSynchronize(c->stream);
+                dev_free(d_tpos);
+                c->n_tslices = nts;
+                c->tsell_len = acc2;
+                c->kernels += 1;
+            }
+        }
+    }
     int hflag = 0;
     cudaError_t e = cudaMemcpyAsync(&hflag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

@@ -169,6 +169,64 @@ __global__ void __launch_bounds__(256) k_pcg_apply(int64_t nwarps, int nchunks, 
     }
 }
 
+// The float32 PCG apply on the type-grouped SELL with Z chunk-major: element (r, c) of Z at
+// ((c / 4) n + r) 4 + c % 4.  A warp takes one (slice, 4-column chunk) pair as above; its lanes
+// are 32 rows of one lattice node type two lattice steps apart, so for one entry index their
+// neighbour rows are (mostly) two rows apart too and the 32 16-byte gathers fall in ~8 lines of
+// the chunk's n x 16 B array instead of 32.
+__global__ void __launch_bounds__(256) k_pcg_apply_zc(int64_t nwarps, int nchunks, int p, int ld, int64_t n,
+                                                      const int *__restrict__ slice_ptr,
+                                                      const int *__restrict__ slice_w,
+                                                      const int *__restrict__ cols,
+                                                      const int *__restrict__ perm,
+                                                      const float *__restrict__ valL,
+                                                      const float *__restrict__ valB,
+                                                      const float *__restrict__ Zc, float *P, float *Q,
+                                                      const double *__restrict__ beta_col,
+                                                      const double *__restrict__ shift, double *pq, int first) {
+    const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wg >= nwarps) return;
+    const int chunk = (int)(wg % nchunks);
+    const int64_t s = wg / nchunks;
+    const int c0 = chunk * 4;
+    const float *Zk = Zc + (int64_t)chunk * n * 4;
+    const int base = slice_ptr[s], width = slice_w[s];
+    const int r = perm[s * SELL_C + lane];
+    float aL[4] = {0.f, 0.f, 0.f, 0.f}, aB[4] = {0.f, 0.f, 0.f, 0.f};
+    int e = base + lane;
+    for (int j = 0; j < width; ++j, e += SELL_C) {
+        const int c = __ldg(cols + e);
+        const float vl = __ldg(valL + e), vb = __ldg(valB + e);
+        const float4 x = __ldg(reinterpret_cast<const float4 *>(Zk + (int64_t)c * 4));
+        aL[0] = fmaf(vl, x.x, aL[0]); aL[1] = fmaf(vl, x.y, aL[1]); aL[2] = fmaf(vl, x.z, aL[2]); aL[3] = fmaf(vl, x.w, aL[3]);
+        aB[0] = fmaf(vb, x.x, aB[0]); aB[1] = fmaf(vb, x.y, aB[1]); aB[2] = fmaf(vb, x.z, aB[2]); aB[3] = fmaf(vb, x.w, aB[3]);
+    }
+    float contrib[4] = {0.f, 0.f, 0.f, 0.f};
+    if (r >= 0) {
+        const float4 z4 = __ldg(reinterpret_cast<const float4 *>(Zk + (int64_t)r * 4));
+        const float zr[4] = {z4.x, z4.y, z4.z, z4.w};
+        float pr[4], qr[4];
+        if (!first) { load_w<float, 4>(P + (int64_t)r * ld + c0, pr); load_w<float, 4>(Q + (int64_t)r * ld + c0, qr); }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const float tz = 0.5f * aL[w] - (float)shift[c0 + w] * aB[w];
+            const float b = first ? 0.f : (float)beta_col[c0 + w];
+            const float pn = first ? zr[w] : fmaf(b, pr[w], zr[w]);
+            const float qn = first ? tz : fmaf(b, qr[w], tz);
+            pr[w] = pn; qr[w] = qn;
+            contrib[w] = pn * qn;
+        }
+        store_w<float, 4>(P + (int64_t)r * ld + c0, pr);
+        store_w<float, 4>(Q + (int64_t)r * ld + c0, qr);
+    }
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const float t = warp_sum_t(contrib[w]);
+        if (lane == 0 && c0 + w < p) atomicAdd(pq + c0 + w, (double)t);
+    }
+}
+
 inline int chunk_width(int ld) { return (ld % 4 == 0) ? 4 : (ld % 2 == 0 ? 2 : 1); }
 
 // ---- half-warp-per-row forms for float32 blocks (the mixed form)
@@ -346,8 +404,19 @@ void launch_sell_spmm_colnorm(ofks_ctx *c, const T *val, const T *X, T *Y, doubl
 }
 
 template <class T>
-void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, T *P, T *Q, const double *beta_col,
+void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, int zc, T *P, T *Q, const double *beta_col,
                       const double *shift, double *pq, int first) {
+    if constexpr (sizeof(T) == 4) {
+        if (zc) {
+            const int nch = c->ld / 4;
+            const int64_t nw = (int64_t)c->n_tslices * nch;
+            k_pcg_apply_zc<<<(unsigned)((nw * 32 + 255) / 256), 256, 0, c->stream>>>(
+                nw, nch, c->p, c->ld, c->n, c->d_tslice_ptr, c->d_tslice_w, c->d_tcols, c->d_tperm, c->d_tvalL,
+                c->d_tvalB, (const float *)Zin, (float *)P, (float *)Q, beta_col, shift, pq, first);
+            c->kernels += 1;
+            return;
+        }
+    }
     if constexpr (sizeof(T) == 4)
         if (launch_rows_f32<2>(c, c->ld, valL, valB, Zin, P, Q, beta_col, shift, pq, first)) return;
     const int W = chunk_width(c->ld), nch = c->ld / W;
@@ -377,7 +446,7 @@ template void launch_sell_spmm<double>(ofks_ctx *, const double *, const double 
 template void launch_sell_spmm<float>(ofks_ctx *, const float *, const float *, float *);
 template void launch_sell_spmm_colnorm<double>(ofks_ctx *, const double *, const double *, double *, double *);
 template void launch_sell_spmm_colnorm<float>(ofks_ctx *, const float *, const float *, float *, double *);
-template void launch_pcg_apply<double>(ofks_ctx *, const double *, const double *, const double *, double *,
+template void launch_pcg_apply<double>(ofks_ctx *, const double *, const double *, const double *, int, double *,
                                        double *, const double *, const double *, double *, int);
-template void launch_pcg_apply<float>(ofks_ctx *, const float *, const float *, const float *, float *, float *,
+template void launch_pcg_apply<float>(ofks_ctx *, const float *, const float *, const float *, int, float *, float *,
                                       const double *, const double *, double *, int);

@@ -82,3 +82,41 @@ def test_mixed_wide_block_steps(ofks):
         assert abs(g["e_total"] - o["E"]) < 2e-5 * abs(o["E"]), (k, g["e_total"], o["E"])
         assert abs(g["kkt"] - o["kkt"]) < 1e-4 * o["kkt"]
     ctx.close()
+
+
+def _renumbered(m0, seed=3):
+    perm = np.random.default_rng(seed).permutation(len(m0.xyz))     # new id -> old id
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(len(perm))
+    return I.Mesh(m0.xyz[perm].copy(), inv[m0.tet10], m0.dirichlet[perm].copy(), m0.lattice, m0.axes)
+
+
+@pytest.mark.parametrize("case", ["chain_p41", "h2o_p5", "lih_p2", "lih_renumbered_p3"])
+def test_float32_preconditioner_matches_the_oracle(ofks, case):
+    # the float32 PCG of the mixed form (8 iterations of Eq. precondition-T) against the oracle's
+    # float64 PCG: the type-grouped SELL with chunk-major Z on lattice meshes (p = 41, 5), the
+    # row-major kernels for p <= 2 and on meshes whose ids are not a lattice
+    if case == "chain_p41":
+        s = I.chain(cells=(26, 14, 8))
+        m = I.make_mesh(s)
+    elif case == "h2o_p5":
+        R = np.array([[0.0, 0.0, 0.0], [1.43, 1.11, 0.0], [-1.43, 1.11, 0.0]])
+        s = I.System("h2o_like", np.array([8.0, 1.0, 1.0]), R, np.full(3, -8.0), np.full(3, 8.0), (10, 10, 10), 5, 2.0)
+        m = I.make_mesh(s)
+    elif case == "lih_p2":
+        s = I.lih().with_cells((8, 8, 8))
+        m = I.make_mesh(s)
+    else:
+        s = I.lih().with_cells((8, 8, 8)).with_p(3, occ=1.0)
+        m = _renumbered(I.make_mesh(s))
+    ctx = ofks.context_for(s, m, beta=10.0, precision="mixed")
+    pr = pcal.Problem(m.xyz, m.tet10, m.dirichlet, s.Z, s.R, pcal.Params(p=s.p, occ=s.occ, hartree=False, xc=False))
+    rng = np.random.default_rng(7)
+    G = rng.standard_normal((m.n_free, s.p))
+    shifts = -rng.uniform(0.05, 2.0, s.p)
+    shifts[0] = 0.3                                   # one column with T = I
+    D = ctx.precondition("pcg", G, shifts)
+    Do = pr.precondition(G, shifts)
+    assert np.max(np.abs(D - Do)) < 1e-4 * np.max(np.abs(Do)), np.max(np.abs(D - Do)) / np.max(np.abs(Do))
+    assert np.array_equal(D[:, 0].astype(np.float32), G[:, 0].astype(np.float32))
+    ctx.close()

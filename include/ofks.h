@@ -115,6 +115,9 @@ typedef struct {
                                  from the previous iterate (inexact potentials early, exact at the end) */
     int32_t poisson_csr;    /* 1: Hartree CG on the general CSR stiffness even when the mesh's node ids
                                follow a lattice (default 0: the lattice-stencil form when available) */
+    int32_t gram_tc;        /* float32 Grams (mixed form): 1 (default) on the tensor cores, bf16 hi/lo
+                               split with three products and float32 accumulation (ld multiple of 4,
+                               ld <= 64); 0 float32 CUDA cores */
     int32_t spmm_f32_rows;  /* float32 block SpMMs (mixed form): 1 half a warp per row (lanes split the
                                columns), 0 (default) one lane per row and 4-column chunks */
     int32_t poisson_sep_tc; /* OFKS_HPC_SEPARABLE: 1 (default) the six axis contractions on the tensor
@@ -144,7 +147,7 @@ typedef struct {
 /* Fill *prm with the defaults: beta 10, occ 2, tol 1e-8, max_iter 1000, FP64, PCG with 8
  * iterations, BB2, eta in [1e-4, 1e8], Hartree and LDA on, multipole_lmax 2,
  * poisson_tol 1e-12, poisson_max_iter 20000, poisson_pc OFKS_HPC_SEPARABLE, mixed_tol 1e-5, poisson_tol_mixed
- * 1e-8, judge_tau 0.5, learned_tc 1, poisson_adaptive 0, poisson_csr 0, spmm_f32_rows 0,
+ * 1e-8, judge_tau 0.5, learned_tc 1, poisson_adaptive 0, poisson_csr 0, gram_tc 1, spmm_f32_rows 0,
  * poisson_sep_tc 1.  p is
  * set to 1. */
 void ofks_default_params(ofks_params *prm);

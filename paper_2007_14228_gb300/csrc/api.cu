@@ -416,6 +416,14 @@ static int run_iterations(ofks_ctx *c, int kmax, ofks_result *res) {
     c->hartree_tol = 0.0;
     cudaEventRecord(e1, c->stream);
     cudaEventSynchronize(e1);
+    if (!rc) {   // a tensor-core Gram whose bounded wait gave up
+        int hf = 0;
+        cudaMemcpy(&hf, c->d_flag + 2, sizeof(int), cudaMemcpyDeviceToHost);
+        if (hf) {
+            cudaMemset(c->d_flag + 2, 0, sizeof(int));
+            rc = ofks_fail(c, OFKS_ETIMEOUT, "tensor-core Gram: wait timed out");
+        }
+    }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     c->ev_pool.push_back(e0);
@@ -447,7 +455,7 @@ void ofks_default_params(ofks_params *p) {
     p->multipole_lmax = 2; p->poisson_tol = 1e-12; p->poisson_max_iter = 20000;
     p->poisson_pc = OFKS_HPC_SEPARABLE;
     p->mixed_tol = 1e-5; p->poisson_tol_mixed = 1e-8;
-    p->judge_tau = 0.5; p->learned_tc = 1; p->poisson_adaptive = 0; p->poisson_csr = 0;
+    p->judge_tau = 0.5; p->learned_tc = 1; p->poisson_adaptive = 0; p->poisson_csr = 0; p->gram_tc = 1;
     p->poisson_sep_tc = 1; p->spmm_f32_rows = 0;
 }
 
@@ -537,7 +545,7 @@ int ofks_set_params(ofks_ctx *c, const ofks_params *prm) {
         !(prm->judge_tau > 0) || prm->learned_tc < 0 || prm->learned_tc > 1 ||
         prm->poisson_adaptive < 0 || prm->poisson_adaptive > 1 ||
         prm->poisson_csr < 0 || prm->poisson_csr > 1 || prm->poisson_sep_tc < 0 || prm->poisson_sep_tc > 1 ||
-        prm->spmm_f32_rows < 0 || prm->spmm_f32_rows > 1 ||
+        prm->spmm_f32_rows < 0 || prm->spmm_f32_rows > 1 || prm->gram_tc < 0 || prm->gram_tc > 1 ||
         (prm->precision != OFKS_FP64 && prm->precision != OFKS_MIXED) || !(prm->mixed_tol > 0) ||
         !(prm->poisson_tol_mixed > 0) || !(prm->eta_min > 0) || !(prm->eta_max >= prm->eta_min) ||
         prm->multipole_lmax < -1 || prm->multipole_lmax > 2 || !(prm->poisson_tol > 0) ||

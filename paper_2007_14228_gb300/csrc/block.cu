@@ -487,6 +487,12 @@ void launch_gram2(ofks_ctx *c, const T *X, const T *A, const T *B, double *XA, d
     const int ld = c->ld, p = c->p;
     cudaMemsetAsync(XA, 0, sizeof(double) * ld * ld, c->stream);
     cudaMemsetAsync(XB, 0, sizeof(double) * ld * ld, c->stream);
+    if constexpr (sizeof(T) == 4) {
+        if (launch_gram_tc(c, (const float *)X, (const float *)A, (const float *)B, XA, XB)) {
+            k_mirror2<<<4, 256, 0, c->stream>>>(p, ld, XA, XB);
+            return;
+        }
+    }
     int RT = p <= 16 ? 1 : (p <= 32 ? 2 : (p <= 48 ? 3 : 4));
     const int TS = 16 * RT, ntile = (p + TS - 1) / TS, npair = ntile * (ntile + 1) / 2;
     int64_t splits = std::max<int64_t>(1, std::min<int64_t>((c->n + 255) / 256, (152LL * 4) / npair + 1));

@@ -120,3 +120,36 @@ def test_float32_preconditioner_matches_the_oracle(ofks, case):
     assert np.max(np.abs(D - Do)) < 1e-4 * np.max(np.abs(Do)), np.max(np.abs(D - Do)) / np.max(np.abs(Do))
     assert np.array_equal(D[:, 0].astype(np.float32), G[:, 0].astype(np.float32))
     ctx.close()
+
+
+@pytest.mark.parametrize("case", ["chain_p41", "h2o_p5"])
+def test_tensor_core_grams_match(ofks, case):
+    # Lambda0 = X^T H X and S = X^T B X of the float32 form from the tensor cores (bf16 hi/lo split,
+    # three products, float32 accumulation) against the float32 CUDA-core kernel and the float64
+    # form, all at the same iterate
+    if case == "chain_p41":
+        s = I.chain(cells=(26, 14, 8))
+    else:
+        R = np.array([[0.0, 0.0, 0.0], [1.43, 1.11, 0.0], [-1.43, 1.11, 0.0]])
+        s = I.System("h2o_like", np.array([8.0, 1.0, 1.0]), R, np.full(3, -8.0), np.full(3, 8.0), (10, 10, 10), 5, 2.0)
+    m = I.make_mesh(s)
+    V = I.initial_block(m.n_free, s.p, 0)
+    ctx = ofks.context_for(s, m, beta=10.0, precision="fp64")
+    ctx.init_orbitals(V)
+    ctx.step(3)
+    X = ctx.get_orbitals()                  # the same iterate for all three: after three steps
+    ctx.close()
+    res = {}
+    for name, kw in (("tc", dict(precision="mixed", gram_tc=1)), ("cuda", dict(precision="mixed", gram_tc=0)),
+                     ("fp64", dict(precision="fp64"))):
+        ctx = ofks.context_for(s, m, beta=10.0, **kw)
+        ctx.set_orbitals(X)
+        ctx.evaluate()
+        res[name] = (ctx.get_field("Lambda0"), ctx.get_field("S"))
+        ctx.close()
+    for k in (0, 1):
+        ref = res["fp64"][k]
+        scale = np.max(np.abs(ref))
+        assert np.max(np.abs(res["tc"][k] - ref)) < 2e-5 * scale, (k, np.max(np.abs(res["tc"][k] - ref)) / scale)
+        assert np.max(np.abs(res["tc"][k] - res["cuda"][k])) < 2e-5 * scale
+        assert np.allclose(res["tc"][k], res["tc"][k].T, rtol=0, atol=1e-12 * scale)

@@ -115,9 +115,10 @@ typedef struct {
                                  from the previous iterate (inexact potentials early, exact at the end) */
     int32_t poisson_csr;    /* 1: Hartree CG on the general CSR stiffness even when the mesh's node ids
                                follow a lattice (default 0: the lattice-stencil form when available) */
-    int32_t gram_tc;        /* float32 Grams (mixed form): 1 (default) on the tensor cores, bf16 hi/lo
-                               split with three products and float32 accumulation (ld multiple of 4,
-                               ld <= 64); 0 float32 CUDA cores */
+    int32_t gram_tc;        /* float32 dense contractions (mixed form): 1 (default) on the tensor cores --
+                               the Grams with a bf16 hi/lo split (three products), the gradient
+                               G = H X + B X C with a three-way split (six products), float32
+                               accumulation (ld multiple of 4, ld <= 64); 0 float32 CUDA cores */
     int32_t spmm_f32_rows;  /* float32 block SpMMs (mixed form): 1 half a warp per row (lanes split the
                                columns), 0 (default) one lane per row and 4-column chunks */
     int32_t poisson_sep_tc; /* OFKS_HPC_SEPARABLE: 1 (default) the six axis contractions on the tensor

@@ -526,6 +526,7 @@ void launch_grad_update(ofks_ctx *c, Blocks<T> &b) {
     T *G = b.G[c->cur];
     cudaMemsetAsync(c->d_sc + SC_KKT2, 0, sizeof(double), c->stream);
     if constexpr (sizeof(T) == 4) {
+        if (launch_grad_tc(c, (const float *)b.HX, (const float *)b.BX, (float *)G, c->d_sc + SC_KKT2)) return;
         if (ld <= 64) {
             const int smf = (int)(sizeof(float) * (2 * ld * ld + 64 * ld));
             const unsigned gf = (unsigned)std::max<int64_t>(1, std::min<int64_t>((c->n + 63) / 64, 152 * 4));

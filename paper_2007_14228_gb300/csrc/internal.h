@@ -269,6 +269,8 @@ void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, i
 template <class T> void launch_gram2(ofks_ctx *c, const T *X, const T *A, const T *B, double *XA, double *XB);
 // gram_tc.cu: the float32 Grams on the tensor cores (false: shapes not supported)
 bool launch_gram_tc(ofks_ctx *c, const float *X, const float *A, const float *B, double *XA, double *XB);
+// grad_tc.cu: G = H X + B X C and |H X - B X Lambda0|^2 on the tensor cores (false: not supported)
+bool launch_grad_tc(ofks_ctx *c, const float *HX, const float *BX, float *G, double *kkt2);
 template <class T> void launch_grad_update(ofks_ctx *c, Blocks<T> &b);
 // float32 PCG blocks keep Z chunk-major (4 columns x n rows per chunk) on lattice meshes
 template <class T> bool pcg_zc(const ofks_ctx *c);

@@ -124,9 +124,9 @@ def test_float32_preconditioner_matches_the_oracle(ofks, case):
 
 @pytest.mark.parametrize("case", ["chain_p41", "h2o_p5"])
 def test_tensor_core_grams_match(ofks, case):
-    # Lambda0 = X^T H X and S = X^T B X of the float32 form from the tensor cores (bf16 hi/lo split,
-    # three products, float32 accumulation) against the float32 CUDA-core kernel and the float64
-    # form, all at the same iterate
+    # Lambda0 = X^T H X and S = X^T B X (bf16 hi/lo split, three products) and the gradient
+    # G = H X + B X C with kkt (three-way split, six products) of the float32 form from the tensor
+    # cores, against the float32 CUDA-core kernels and the float64 form, all at the same iterate
     if case == "chain_p41":
         s = I.chain(cells=(26, 14, 8))
     else:
@@ -144,9 +144,15 @@ def test_tensor_core_grams_match(ofks, case):
                      ("fp64", dict(precision="fp64"))):
         ctx = ofks.context_for(s, m, beta=10.0, **kw)
         ctx.set_orbitals(X)
-        ctx.evaluate()
-        res[name] = (ctx.get_field("Lambda0"), ctx.get_field("S"))
+        r = ctx.evaluate()
+        res[name] = (ctx.get_field("Lambda0"), ctx.get_field("S"), ctx.get_field("G"), r["kkt"])
         ctx.close()
+    # the gradient G = H X + B X C (tensor cores: three-way bf16 split) and kkt = |H X - B X Lambda0|
+    g_ref = res["fp64"][2]
+    gs = np.max(np.abs(g_ref))
+    assert np.max(np.abs(res["tc"][2] - g_ref)) < 1e-4 * gs, np.max(np.abs(res["tc"][2] - g_ref)) / gs
+    assert np.max(np.abs(res["tc"][2] - res["cuda"][2])) < 1e-5 * gs
+    assert abs(res["tc"][3] - res["fp64"][3]) < 1e-4 * res["fp64"][3]
     for k in (0, 1):
         ref = res["fp64"][k]
         scale = np.max(np.abs(ref))

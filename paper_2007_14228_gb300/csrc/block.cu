@@ -342,6 +342,50 @@ __global__ void __launch_bounds__(256) k_pcg_update(int64_t n, int p, int ld, in
     col_reduce((double)acc, j, gid < stride, ld, p, rzn);
 }
 
+// k_pcg_update for float32 with Z chunk-major: 32-row tiles are read and written row-major
+// (coalesced) and the tile's Z goes through shared memory, so each 4-column chunk of it is
+// written as one contiguous 512-byte run instead of 16-byte pieces scattered over the chunks.
+// The column sums r.z collect in shared memory and leave once per block.
+constexpr int UZ_ROWS = 32;
+
+__global__ void __launch_bounds__(256) k_pcg_update_zc(int64_t n, int p, int ld, const double *cb,
+                                                       const float *__restrict__ W, const float *__restrict__ P,
+                                                       const float *__restrict__ Q, float *D, float *R, float *Zc,
+                                                       double *rzn) {
+    extern __shared__ __align__(16) float uzs[];
+    float *zt = uzs;                             // UZ_ROWS x ld
+    float *al = zt + UZ_ROWS * ld;               // ld
+    float *cs = al + ld;                         // ld
+    for (int j = threadIdx.x; j < ld; j += blockDim.x) { al[j] = (float)cb[CB_ALPHA * ld + j]; cs[j] = 0.f; }
+    __syncthreads();
+    const int nch = ld >> 2;
+    for (int64_t r0 = (int64_t)blockIdx.x * UZ_ROWS; r0 < n; r0 += (int64_t)gridDim.x * UZ_ROWS) {
+        const int rows = (int)(n - r0 < UZ_ROWS ? n - r0 : UZ_ROWS);
+        const int64_t b0 = r0 * ld;
+        for (int e = threadIdx.x; e < rows * ld; e += blockDim.x) {
+            const int j = e % ld;
+            const float a = al[j];
+            const int64_t g = b0 + e;
+            D[g] = fmaf(a, P[g], D[g]);
+            const float rv = fmaf(-a, Q[g], R[g]);
+            const float z = rv * W[g];
+            R[g] = rv;
+            zt[e] = z;
+            atomicAdd(cs + j, rv * z);
+        }
+        __syncthreads();
+        // chunk q of row i: 16 bytes at ((q n) + r0 + i) 4 of Zc
+        for (int e = threadIdx.x; e < nch * rows; e += blockDim.x) {
+            const int q = e / rows, i = e - q * rows;
+            const float4 v = *reinterpret_cast<const float4 *>(zt + i * ld + 4 * q);
+            *reinterpret_cast<float4 *>(Zc + (((int64_t)q * n + r0 + i) << 2)) = v;
+        }
+        __syncthreads();
+    }
+    for (int j = threadIdx.x; j < ld && j < p; j += blockDim.x)
+        if (cs[j] != 0.f) atomicAdd(rzn + j, (double)cs[j]);
+}
+
 // columns whose shift is not negative take D = G (T = I in Eq. precondition-T)
 template <class T>
 __global__ void __launch_bounds__(256) k_select(int64_t n, int ld, int64_t stride, const double *cb,
@@ -588,6 +632,16 @@ void launch_pcg_update(ofks_ctx *c, Blocks<T> &b) {
     c->kernels += 1;
     const int ld = c->ld;
     double *cb = c->d_colA;
+    if constexpr (sizeof(T) == 4) {
+        if (pcg_zc<T>(c)) {
+            const size_t sm = sizeof(float) * (UZ_ROWS * ld + 2 * ld);
+            const unsigned grid = (unsigned)std::min<int64_t>((c->n + UZ_ROWS - 1) / UZ_ROWS, 152 * 8);
+            k_pcg_update_zc<<<grid, 256, sm, c->stream>>>(c->n, c->p, ld, cb, (const float *)b.W, (const float *)b.P,
+                                                          (const float *)b.Q, (float *)b.D[c->cur], (float *)b.R,
+                                                          (float *)b.Z, cb + CB_RZN * ld);
+            return;
+        }
+    }
     const ElemGrid g = elem_grid(c->n, ld);
     k_pcg_update<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, cb, b.W, b.P, b.Q, b.D[c->cur], b.R,
                                                      b.Z, cb + CB_RZN * ld, pcg_zc<T>(c) ? 1 : 0);

@@ -91,7 +91,7 @@ static void free_set(Blocks<T> &b) {
 static void free_blocks(ofks_ctx *c) {
     free_set(c->b64);
     free_set(c->b32);
-    dfree(c->d_L0); dfree(c->d_S); dfree(c->d_Lam); dfree(c->d_C); dfree(c->d_colA); dfree(c->d_pp);
+    dfree(c->d_L0); dfree(c->d_S); dfree(c->d_Lam); dfree(c->d_C); dfree(c->d_colA); dfree(c->d_pp); dfree(c->d_stage);
     c->p = c->ld = 0;
     c->have_X = c->evaluated = c->have_prev = false;
     c->phase = 64;
@@ -136,6 +136,10 @@ static int alloc_blocks(ofks_ctx *c, int p, bool mixed) {
         return ofks_fail(c, OFKS_ENOMEM, "p x p scratch");
     }
     cudaMemsetAsync(c->d_colA, 0, sizeof(double) * CB_COUNT * ld, c->stream);
+    if (ld != p && cudaMalloc((void **)&c->d_stage, sizeof(double) * (size_t)c->n * p) != cudaSuccess) {
+        free_blocks(c);
+        return ofks_fail(c, OFKS_ENOMEM, "host-copy staging block");
+    }
     c->p = p;
     c->ld = ld;
     c->mixed_alloc = mixed;
@@ -169,15 +173,26 @@ static double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// Host blocks are dense n x p; device blocks have row pitch ld.  With ld > p the copy goes as
+// one contiguous transfer through the staging block and a repacking kernel: a pitched copy of
+// n rows of p doubles runs far below the link's bandwidth.
 static int upload_block(ofks_ctx *c, const double *h, double *d) {
-    cudaError_t e = cudaMemcpy2DAsync(d, sizeof(double) * c->ld, h, sizeof(double) * c->p, sizeof(double) * c->p,
-                                      (size_t)c->n, cudaMemcpyHostToDevice, c->stream);
+    const size_t bytes = sizeof(double) * (size_t)c->n * c->p;
+    if (c->ld == c->p)
+        return ofks_cuda_check(c, cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, c->stream), "block upload");
+    cudaError_t e = cudaMemcpyAsync(c->d_stage, h, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) launch_repack(c, c->d_stage, c->p, d, c->ld, c->n, c->p);
     return ofks_cuda_check(c, e, "block upload");
 }
 
 static int download_block(ofks_ctx *c, const double *d, double *h) {
-    cudaError_t e = cudaMemcpy2DAsync(h, sizeof(double) * c->p, d, sizeof(double) * c->ld, sizeof(double) * c->p,
-                                      (size_t)c->n, cudaMemcpyDeviceToHost, c->stream);
+    const size_t bytes = sizeof(double) * (size_t)c->n * c->p;
+    const double *src = d;
+    if (c->ld != c->p) {
+        launch_repack(c, d, c->ld, c->d_stage, c->p, c->n, c->p);
+        src = c->d_stage;
+    }
+    cudaError_t e = cudaMemcpyAsync(h, src, bytes, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return ofks_cuda_check(c, e, "block download");
 }

@@ -701,6 +701,23 @@ void launch_block_times_small(ofks_ctx *c, const T *X, const double *M, T *Y) {
     });
 }
 
+__global__ void __launch_bounds__(256) k_repack(int64_t n, int w, const double *__restrict__ src, int64_t sp,
+                                                double *__restrict__ dst, int64_t dp) {
+    const int64_t total = n * w;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / w;
+        const int j = (int)(i - r * w);
+        dst[r * dp + j] = src[r * sp + j];
+    }
+}
+
+void launch_repack(ofks_ctx *c, const double *src, int64_t sp, double *dst, int64_t dp, int64_t n, int w) {
+    c->kernels += 1;
+    const int64_t count = n * w;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 152LL * 16));
+    k_repack<<<g, 256, 0, c->stream>>>(n, w, src, sp, dst, dp);
+}
+
 template <class S, class T>
 void launch_convert(ofks_ctx *c, const S *src, T *dst, int64_t count) {
     c->kernels += 1;

@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(256, 1) k_grad_tc(int64_t n, int p, int ld, in
         if (warp < 4) {                          // G = H X + D1 in place of H X, |H X - D2|^2
             const int r = warp * 32 + lane;
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+            float rp = 0.f;                      // this row's |R|^2 (at most 64 terms) in float
             for (int cb = 0; cb < nh; cb += 16) {
                 uint32_t v1[16], v2[16];
                 asm volatile(
@@ -204,10 +205,11 @@ __global__ void __launch_bounds__(256, 1) k_grad_tc(int64_t n, int p, int ld, in
                     *hp = h + __uint_as_float(v1[q]);                 // G
                     if (col < p) {
                         const float res = h - __uint_as_float(v2[q]);   // R
-                        part += (double)(res * res);
+                        rp = fmaf(res, res, rp);
                     }
                 }
             }
+            part += (double)rp;
         }
         // the G tile leaves by a bulk store from shared memory
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

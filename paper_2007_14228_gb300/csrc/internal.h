@@ -177,6 +177,7 @@ struct ofks_ctx {
     double *d_L0 = nullptr, *d_S = nullptr, *d_Lam = nullptr, *d_C = nullptr;
     double *d_colA = nullptr;                    // 4 x p column accumulators
     double *d_pp = nullptr;                      // p x p scratch (factorizations)
+    double *d_stage = nullptr;                   // n x p dense staging of host block copies (ld > p)
     double *d_sc = nullptr;                      // SC_COUNT scalars
     double *d_rec = nullptr;                     // iteration record (device)
     int *d_flag = nullptr;                       // error / status flags
@@ -284,6 +285,8 @@ template <class T> void launch_step_y(ofks_ctx *c, Blocks<T> &b, T *Y);
 template <class T> void launch_scale_cols(ofks_ctx *c, T *Y, T *BY, const double *colsum);
 template <class T> void launch_block_times_small(ofks_ctx *c, const T *X, const double *M, T *Y);
 template <class S, class T> void launch_convert(ofks_ctx *c, const S *src, T *dst, int64_t count);
+// dst[r dp + j] = src[r sp + j] for r < n, j < w (float64)
+void launch_repack(ofks_ctx *c, const double *src, int64_t sp, double *dst, int64_t dp, int64_t n, int w);
 
 // ---- small.cu (p x p work on one CTA)
 void launch_small_update(ofks_ctx *c);

@@ -59,10 +59,22 @@ __device__ __forceinline__ T warp_sum_t(T v) {
     return v;
 }
 
+// Slices a warp takes in turn for one column chunk in the kernels that add column sums: the
+// sums go out by one set of float64 atomics per warp instead of one per slice (measured on the
+// float32 PCG apply: 1, 2, 4, 8, 16 slices -> 1170, 927, 911, 971, 982 us per launch on the
+// 1.25 M-row chain; the plain product keeps one slice per warp, which measured faster).  Small
+// problems keep one slice per warp so that the grid still fills the GPU (spw_for).
+constexpr int SPW = 4;
+
+inline int spw_for(int64_t units) {
+    const int64_t fill = 152LL * 48;              // resident warps of one wave at ~40 registers
+    return units / SPW >= fill ? SPW : (units / 2 >= fill ? 2 : 1);
+}
+
 // MODE 0: Y = A X.  MODE 1: also colsum[c] += sum_rows X[r,c] Y[r,c] (float64 accumulators).
 // T is the element type of the values and blocks; sums run in T.
 template <class T, int W, int MODE>
-__global__ void __launch_bounds__(256) k_sell_spmm(int64_t nwarps, int nchunks, int p, int ld,
+__global__ void __launch_bounds__(256) k_sell_spmm(int64_t nwarps, int nchunks, int64_t n_slices, int spw_, int p, int ld,
                                                    const int *__restrict__ slice_ptr,
                                                    const int *__restrict__ slice_w,
                                                    const int *__restrict__ cols,
@@ -73,31 +85,43 @@ __global__ void __launch_bounds__(256) k_sell_spmm(int64_t nwarps, int nchunks, 
     const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (wg >= nwarps) return;                       // whole warp leaves together
+    const int spw = MODE == 1 ? spw_ : 1;           // without column sums one slice is faster
     const int chunk = (int)(wg % nchunks);
-    const int64_t s = wg / nchunks;
+    const int64_t s0 = (wg / nchunks) * spw;
+    const int64_t s1 = s0 + spw < n_slices ? s0 + spw : n_slices;
     const int c0 = chunk * W;
-    const int base = slice_ptr[s], width = slice_w[s];
-    const int r = perm[s * SELL_C + lane];
-    T acc[W];
+    T cs[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) acc[w] = T(0);
-    int e = base + lane;
-    for (int j = 0; j < width; ++j, e += SELL_C) {
-        const int c = __ldg(cols + e);
-        const T v = __ldg(val + e);
-        T x[W];
-        load_w<T, W>(X + (int64_t)c * ld + c0, x);
+    for (int w = 0; w < W; ++w) cs[w] = T(0);
+    for (int64_t s = s0; s < s1; ++s) {
+        const int base = slice_ptr[s], width = slice_w[s];
+        const int r = perm[s * SELL_C + lane];
+        T acc[W];
 #pragma unroll
-        for (int w = 0; w < W; ++w) acc[w] = fma(v, x[w], acc[w]);
+        for (int w = 0; w < W; ++w) acc[w] = T(0);
+        int e = base + lane;
+        for (int j = 0; j < width; ++j, e += SELL_C) {
+            const int c = __ldg(cols + e);
+            const T v = __ldg(val + e);
+            T x[W];
+            load_w<T, W>(X + (int64_t)c * ld + c0, x);
+#pragma unroll
+            for (int w = 0; w < W; ++w) acc[w] = fma(v, x[w], acc[w]);
+        }
+        if (r >= 0) {
+            store_w<T, W>(Y + (int64_t)r * ld + c0, acc);
+            if constexpr (MODE == 1) {
+                T xr[W];
+                load_w<T, W>(X + (int64_t)r * ld + c0, xr);
+#pragma unroll
+                for (int w = 0; w < W; ++w) cs[w] = fma(xr[w], acc[w], cs[w]);
+            }
+        }
     }
-    if (r >= 0) store_w<T, W>(Y + (int64_t)r * ld + c0, acc);
     if constexpr (MODE == 1) {
-        T xr[W];
-        if (r >= 0) load_w<T, W>(X + (int64_t)r * ld + c0, xr);
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-            T t = (r >= 0) ? xr[w] * acc[w] : T(0);
-            t = warp_sum_t(t);
+            const T t = warp_sum_t(cs[w]);
             if (lane == 0 && c0 + w < p) atomicAdd(colsum + c0 + w, (double)t);
         }
     }
@@ -108,7 +132,7 @@ __global__ void __launch_bounds__(256) k_sell_spmm(int64_t nwarps, int nchunks, 
 //   own row  P <- Z + beta P,  Q <- TZ + beta Q  (so T P = Q), and pq[c] += P.Q.
 // With first = 1: P = Z, Q = TZ.
 template <class T, int W>
-__global__ void __launch_bounds__(256) k_pcg_apply(int64_t nwarps, int nchunks, int p, int ld,
+__global__ void __launch_bounds__(256) k_pcg_apply(int64_t nwarps, int nchunks, int64_t n_slices, int spw, int p, int ld,
                                                    const int *__restrict__ slice_ptr,
                                                    const int *__restrict__ slice_w,
                                                    const int *__restrict__ cols,
@@ -123,59 +147,67 @@ __global__ void __launch_bounds__(256) k_pcg_apply(int64_t nwarps, int nchunks, 
     const int lane = threadIdx.x & 31;
     if (wg >= nwarps) return;
     const int chunk = (int)(wg % nchunks);
-    const int64_t s = wg / nchunks;
+    const int64_t s0 = (wg / nchunks) * spw;
+    const int64_t s1 = s0 + spw < n_slices ? s0 + spw : n_slices;
     const int c0 = chunk * W;
-    const int base = slice_ptr[s], width = slice_w[s];
-    const int r = perm[s * SELL_C + lane];
-    T aL[W], aB[W];
+    T sh[W], bt[W], contrib[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) { aL[w] = T(0); aB[w] = T(0); }
-    int e = base + lane;
-    for (int j = 0; j < width; ++j, e += SELL_C) {
-        const int c = __ldg(cols + e);
-        const T vl = __ldg(valL + e), vb = __ldg(valB + e);
-        T x[W];
-        load_w<T, W>(Z + (int64_t)c * ld + c0, x);
-#pragma unroll
-        for (int w = 0; w < W; ++w) { aL[w] = fma(vl, x[w], aL[w]); aB[w] = fma(vb, x[w], aB[w]); }
+    for (int w = 0; w < W; ++w) {
+        sh[w] = T(shift[c0 + w]);
+        bt[w] = first ? T(0) : T(beta_col[c0 + w]);
+        contrib[w] = T(0);
     }
-    T contrib[W];
-    if (r >= 0) {
-        T zr[W], pr[W], qr[W];
-        load_w<T, W>(Z + (int64_t)r * ld + c0, zr);
-        if (!first) {
-            load_w<T, W>(P + (int64_t)r * ld + c0, pr);
-            load_w<T, W>(Q + (int64_t)r * ld + c0, qr);
-        }
+    for (int64_t s = s0; s < s1; ++s) {
+        const int base = slice_ptr[s], width = slice_w[s];
+        const int r = perm[s * SELL_C + lane];
+        T aL[W], aB[W];
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            const T tz = T(0.5) * aL[w] - T(shift[c0 + w]) * aB[w];
-            const T b = first ? T(0) : T(beta_col[c0 + w]);
-            const T pn = first ? zr[w] : fma(b, pr[w], zr[w]);
-            const T qn = first ? tz : fma(b, qr[w], tz);
-            pr[w] = pn; qr[w] = qn;
-            contrib[w] = pn * qn;
-        }
-        store_w<T, W>(P + (int64_t)r * ld + c0, pr);
-        store_w<T, W>(Q + (int64_t)r * ld + c0, qr);
-    } else {
+        for (int w = 0; w < W; ++w) { aL[w] = T(0); aB[w] = T(0); }
+        int e = base + lane;
+        for (int j = 0; j < width; ++j, e += SELL_C) {
+            const int c = __ldg(cols + e);
+            const T vl = __ldg(valL + e), vb = __ldg(valB + e);
+            T x[W];
+            load_w<T, W>(Z + (int64_t)c * ld + c0, x);
 #pragma unroll
-        for (int w = 0; w < W; ++w) contrib[w] = T(0);
+            for (int w = 0; w < W; ++w) { aL[w] = fma(vl, x[w], aL[w]); aB[w] = fma(vb, x[w], aB[w]); }
+        }
+        if (r >= 0) {
+            T zr[W], pr[W], qr[W];
+            load_w<T, W>(Z + (int64_t)r * ld + c0, zr);
+            if (!first) {
+                load_w<T, W>(P + (int64_t)r * ld + c0, pr);
+                load_w<T, W>(Q + (int64_t)r * ld + c0, qr);
+            }
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const T tz = T(0.5) * aL[w] - sh[w] * aB[w];
+                const T pn = first ? zr[w] : fma(bt[w], pr[w], zr[w]);
+                const T qn = first ? tz : fma(bt[w], qr[w], tz);
+                pr[w] = pn; qr[w] = qn;
+                contrib[w] = fma(pn, qn, contrib[w]);
+            }
+            store_w<T, W>(P + (int64_t)r * ld + c0, pr);
+            store_w<T, W>(Q + (int64_t)r * ld + c0, qr);
+        }
     }
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-        T t = warp_sum_t(contrib[w]);
+        const T t = warp_sum_t(contrib[w]);
         if (lane == 0 && c0 + w < p) atomicAdd(pq + c0 + w, (double)t);
     }
 }
 
 // The float32 PCG apply on the type-grouped SELL with Z chunk-major: element (r, c) of Z at
-// ((c / 4) n + r) 4 + c % 4.  A warp takes one (slice, 4-column chunk) pair as above; its lanes
-// are 32 rows of one lattice node type two lattice steps apart, so for one entry index their
-// neighbour rows are (mostly) two rows apart too and the 32 16-byte gathers fall in ~8 lines of
-// the chunk's n x 16 B array instead of 32.
-__global__ void __launch_bounds__(256) k_pcg_apply_zc(int64_t nwarps, int nchunks, int p, int ld, int64_t n,
-                                                      const int *__restrict__ slice_ptr,
+// ((c / 4) n + r) 4 + c % 4.  A warp takes spw consecutive slices in turn for one 4-column
+// chunk and adds its column sums pq once at the end.  Within a slice its lanes are 32 rows of
+// one lattice node type two lattice steps apart, so for one entry index their neighbour rows
+// are (mostly) two rows apart too and the 32 16-byte gathers fall in ~8 lines of the chunk's
+// n x 16 B array instead of 32.  (8-column chunks, one 32-byte sector per lane, measured
+// slower: 1.31-1.89 ms against 0.91 ms per launch on the 1.25 M-row chain, with twice the lines
+// per gather and fewer resident warps.)
+__global__ void __launch_bounds__(256) k_pcg_apply_zc(int64_t nwarps, int nchunks, int64_t n_slices, int spw, int p, int ld,
+                                                      int64_t n, const int *__restrict__ slice_ptr,
                                                       const int *__restrict__ slice_w,
                                                       const int *__restrict__ cols,
                                                       const int *__restrict__ perm,
@@ -188,37 +220,45 @@ __global__ void __launch_bounds__(256) k_pcg_apply_zc(int64_t nwarps, int nchunk
     const int lane = threadIdx.x & 31;
     if (wg >= nwarps) return;
     const int chunk = (int)(wg % nchunks);
-    const int64_t s = wg / nchunks;
+    const int64_t s0 = (wg / nchunks) * spw;
+    const int64_t s1 = s0 + spw < n_slices ? s0 + spw : n_slices;
     const int c0 = chunk * 4;
     const float *Zk = Zc + (int64_t)chunk * n * 4;
-    const int base = slice_ptr[s], width = slice_w[s];
-    const int r = perm[s * SELL_C + lane];
-    float aL[4] = {0.f, 0.f, 0.f, 0.f}, aB[4] = {0.f, 0.f, 0.f, 0.f};
-    int e = base + lane;
-    for (int j = 0; j < width; ++j, e += SELL_C) {
-        const int c = __ldg(cols + e);
-        const float vl = __ldg(valL + e), vb = __ldg(valB + e);
-        const float4 x = __ldg(reinterpret_cast<const float4 *>(Zk + (int64_t)c * 4));
-        aL[0] = fmaf(vl, x.x, aL[0]); aL[1] = fmaf(vl, x.y, aL[1]); aL[2] = fmaf(vl, x.z, aL[2]); aL[3] = fmaf(vl, x.w, aL[3]);
-        aB[0] = fmaf(vb, x.x, aB[0]); aB[1] = fmaf(vb, x.y, aB[1]); aB[2] = fmaf(vb, x.z, aB[2]); aB[3] = fmaf(vb, x.w, aB[3]);
+    float sh[4], bt[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        sh[w] = (float)shift[c0 + w];
+        bt[w] = first ? 0.f : (float)beta_col[c0 + w];
     }
     float contrib[4] = {0.f, 0.f, 0.f, 0.f};
-    if (r >= 0) {
-        const float4 z4 = __ldg(reinterpret_cast<const float4 *>(Zk + (int64_t)r * 4));
-        const float zr[4] = {z4.x, z4.y, z4.z, z4.w};
-        float pr[4], qr[4];
-        if (!first) { load_w<float, 4>(P + (int64_t)r * ld + c0, pr); load_w<float, 4>(Q + (int64_t)r * ld + c0, qr); }
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const float tz = 0.5f * aL[w] - (float)shift[c0 + w] * aB[w];
-            const float b = first ? 0.f : (float)beta_col[c0 + w];
-            const float pn = first ? zr[w] : fmaf(b, pr[w], zr[w]);
-            const float qn = first ? tz : fmaf(b, qr[w], tz);
-            pr[w] = pn; qr[w] = qn;
-            contrib[w] = pn * qn;
+    for (int64_t s = s0; s < s1; ++s) {
+        const int base = slice_ptr[s], width = slice_w[s];
+        const int r = perm[s * SELL_C + lane];
+        float aL[4] = {0.f, 0.f, 0.f, 0.f}, aB[4] = {0.f, 0.f, 0.f, 0.f};
+        int e = base + lane;
+        for (int j = 0; j < width; ++j, e += SELL_C) {
+            const int c = __ldg(cols + e);
+            const float vl = __ldg(valL + e), vb = __ldg(valB + e);
+            const float4 x = __ldg(reinterpret_cast<const float4 *>(Zk + (int64_t)c * 4));
+            aL[0] = fmaf(vl, x.x, aL[0]); aL[1] = fmaf(vl, x.y, aL[1]); aL[2] = fmaf(vl, x.z, aL[2]); aL[3] = fmaf(vl, x.w, aL[3]);
+            aB[0] = fmaf(vb, x.x, aB[0]); aB[1] = fmaf(vb, x.y, aB[1]); aB[2] = fmaf(vb, x.z, aB[2]); aB[3] = fmaf(vb, x.w, aB[3]);
         }
-        store_w<float, 4>(P + (int64_t)r * ld + c0, pr);
-        store_w<float, 4>(Q + (int64_t)r * ld + c0, qr);
+        if (r >= 0) {
+            const float4 z4 = __ldg(reinterpret_cast<const float4 *>(Zk + (int64_t)r * 4));
+            const float zr[4] = {z4.x, z4.y, z4.z, z4.w};
+            float pr[4], qr[4];
+            if (!first) { load_w<float, 4>(P + (int64_t)r * ld + c0, pr); load_w<float, 4>(Q + (int64_t)r * ld + c0, qr); }
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const float tz = 0.5f * aL[w] - sh[w] * aB[w];
+                const float pn = first ? zr[w] : fmaf(bt[w], pr[w], zr[w]);
+                const float qn = first ? tz : fmaf(bt[w], qr[w], tz);
+                pr[w] = pn; qr[w] = qn;
+                contrib[w] = fmaf(pn, qn, contrib[w]);
+            }
+            store_w<float, 4>(P + (int64_t)r * ld + c0, pr);
+            store_w<float, 4>(Q + (int64_t)r * ld + c0, qr);
+        }
     }
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
@@ -382,7 +422,7 @@ void launch_sell_spmm(ofks_ctx *c, const T *val, const T *X, T *Y) {
     const int W = chunk_width(c->ld), nch = c->ld / W;
     const int64_t nw = (int64_t)c->n_slices * nch;
     const unsigned grid = (unsigned)((nw * 32 + 255) / 256);
-#define L_(w) k_sell_spmm<T, w, 0><<<grid, 256, 0, c->stream>>>(nw, nch, c->p, c->ld, c->d_slice_ptr, \
+#define L_(w) k_sell_spmm<T, w, 0><<<grid, 256, 0, c->stream>>>(nw, nch, (int64_t)c->n_slices, 1, c->p, c->ld, c->d_slice_ptr, \
         c->d_slice_w, c->d_cols, c->d_perm, val, X, Y, nullptr)
     if (W == 4) L_(4); else if (W == 2) L_(2); else L_(1);
 #undef L_
@@ -394,9 +434,10 @@ void launch_sell_spmm_colnorm(ofks_ctx *c, const T *val, const T *X, T *Y, doubl
     if constexpr (sizeof(T) == 4)
         if (launch_rows_f32<1>(c, c->ld, val, nullptr, X, Y, nullptr, nullptr, nullptr, colsum, 0)) return;
     const int W = chunk_width(c->ld), nch = c->ld / W;
-    const int64_t nw = (int64_t)c->n_slices * nch;
+    const int spw = spw_for((int64_t)c->n_slices * nch);
+    const int64_t nw = (((int64_t)c->n_slices + spw - 1) / spw) * nch;
     const unsigned grid = (unsigned)((nw * 32 + 255) / 256);
-#define L_(w) k_sell_spmm<T, w, 1><<<grid, 256, 0, c->stream>>>(nw, nch, c->p, c->ld, c->d_slice_ptr, \
+#define L_(w) k_sell_spmm<T, w, 1><<<grid, 256, 0, c->stream>>>(nw, nch, (int64_t)c->n_slices, spw, c->p, c->ld, c->d_slice_ptr, \
         c->d_slice_w, c->d_cols, c->d_perm, val, X, Y, colsum)
     if (W == 4) L_(4); else if (W == 2) L_(2); else L_(1);
 #undef L_
@@ -409,9 +450,10 @@ void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, i
     if constexpr (sizeof(T) == 4) {
         if (zc) {
             const int nch = c->ld / 4;
-            const int64_t nw = (int64_t)c->n_tslices * nch;
+            const int spw = spw_for((int64_t)c->n_tslices * nch);
+            const int64_t nw = (((int64_t)c->n_tslices + spw - 1) / spw) * nch;
             k_pcg_apply_zc<<<(unsigned)((nw * 32 + 255) / 256), 256, 0, c->stream>>>(
-                nw, nch, c->p, c->ld, c->n, c->d_tslice_ptr, c->d_tslice_w, c->d_tcols, c->d_tperm, c->d_tvalL,
+                nw, nch, (int64_t)c->n_tslices, spw, c->p, c->ld, c->n, c->d_tslice_ptr, c->d_tslice_w, c->d_tcols, c->d_tperm, c->d_tvalL,
                 c->d_tvalB, (const float *)Zin, (float *)P, (float *)Q, beta_col, shift, pq, first);
             c->kernels += 1;
             return;
@@ -420,9 +462,10 @@ void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, i
     if constexpr (sizeof(T) == 4)
         if (launch_rows_f32<2>(c, c->ld, valL, valB, Zin, P, Q, beta_col, shift, pq, first)) return;
     const int W = chunk_width(c->ld), nch = c->ld / W;
-    const int64_t nw = (int64_t)c->n_slices * nch;
+    const int spw = spw_for((int64_t)c->n_slices * nch);
+    const int64_t nw = (((int64_t)c->n_slices + spw - 1) / spw) * nch;
     const unsigned grid = (unsigned)((nw * 32 + 255) / 256);
-#define L_(w) k_pcg_apply<T, w><<<grid, 256, 0, c->stream>>>(nw, nch, c->p, c->ld, c->d_slice_ptr, \
+#define L_(w) k_pcg_apply<T, w><<<grid, 256, 0, c->stream>>>(nw, nch, (int64_t)c->n_slices, spw, c->p, c->ld, c->d_slice_ptr, \
         c->d_slice_w, c->d_cols, c->d_perm, valL, valB, Zin, P, Q, beta_col, shift, pq, first)
     if (W == 4) L_(4); else if (W == 2) L_(2); else L_(1);
 #undef L_
@@ -434,7 +477,7 @@ void launch_sell_spmm_ld(ofks_ctx *c, const T *val, const T *X, T *Y, int ld) {
     const int W = chunk_width(ld), nch = ld / W;
     const int64_t nw = (int64_t)c->n_slices * nch;
     const unsigned grid = (unsigned)((nw * 32 + 255) / 256);
-#define L_(w) k_sell_spmm<T, w, 0><<<grid, 256, 0, c->stream>>>(nw, nch, ld, ld, c->d_slice_ptr, \
+#define L_(w) k_sell_spmm<T, w, 0><<<grid, 256, 0, c->stream>>>(nw, nch, (int64_t)c->n_slices, 1, ld, ld, c->d_slice_ptr, \
         c->d_slice_w, c->d_cols, c->d_perm, val, X, Y, nullptr)
     if (W == 4) L_(4); else if (W == 2) L_(2); else L_(1);
 #undef L_

@@ -124,6 +124,10 @@ typedef struct {
     int32_t poisson_sep_tc; /* OFKS_HPC_SEPARABLE: 1 (default) the six axis contractions on the tensor
                                cores with bf16 operands (axes up to 256 interior points), 0 float32 on
                                the CUDA cores */
+    int32_t pcg_compact;    /* OFKS_PC_PCG / OFKS_PC_EXACT: 1 (default) the PCG runs on the active
+                               columns only (Lambda_ii < 0), gathered into a block of their count
+                               rounded up to 4; the other columns take D = G (T = I) as always.
+                               0: the PCG runs on all ld columns and discards the inactive ones */
 } ofks_params;
 
 typedef struct {
@@ -149,7 +153,7 @@ typedef struct {
  * iterations, BB2, eta in [1e-4, 1e8], Hartree and LDA on, multipole_lmax 2,
  * poisson_tol 1e-12, poisson_max_iter 20000, poisson_pc OFKS_HPC_SEPARABLE, mixed_tol 1e-5, poisson_tol_mixed
  * 1e-8, judge_tau 0.5, learned_tc 1, poisson_adaptive 0, poisson_csr 0, gram_tc 1, spmm_f32_rows 0,
- * poisson_sep_tc 1.  p is
+ * poisson_sep_tc 1, pcg_compact 1.  p is
  * set to 1. */
 void ofks_default_params(ofks_params *prm);
 

@@ -84,7 +84,7 @@ static void dfree(T *&p) {
 template <class T>
 static void free_set(Blocks<T> &b) {
     for (int i = 0; i < 2; ++i) { dfree(b.X[i]); dfree(b.D[i]); dfree(b.G[i]); }
-    dfree(b.HX); dfree(b.BX); dfree(b.R); dfree(b.Z); dfree(b.P); dfree(b.Q); dfree(b.W);
+    dfree(b.HX); dfree(b.BX); dfree(b.R); dfree(b.Z); dfree(b.P); dfree(b.Q); dfree(b.W); dfree(b.Dc);
     dfree(b.valL); dfree(b.valB); dfree(b.valH);
 }
 
@@ -92,6 +92,7 @@ static void free_blocks(ofks_ctx *c) {
     free_set(c->b64);
     free_set(c->b32);
     dfree(c->d_L0); dfree(c->d_S); dfree(c->d_Lam); dfree(c->d_C); dfree(c->d_colA); dfree(c->d_pp); dfree(c->d_stage);
+    dfree(c->d_colC); dfree(c->d_cmap);
     c->p = c->ld = 0;
     c->have_X = c->evaluated = c->have_prev = false;
     c->phase = 64;
@@ -100,7 +101,8 @@ static void free_blocks(ofks_ctx *c) {
 template <class T>
 static int alloc_set(ofks_ctx *c, Blocks<T> &b, int ld, bool values) {
     const size_t blk = sizeof(T) * (size_t)c->n * ld;
-    T **bl[] = {&b.X[0], &b.X[1], &b.D[0], &b.D[1], &b.G[0], &b.G[1], &b.HX, &b.BX, &b.R, &b.Z, &b.P, &b.Q, &b.W};
+    T **bl[] = {&b.X[0], &b.X[1], &b.D[0], &b.D[1], &b.G[0], &b.G[1], &b.HX, &b.BX, &b.R, &b.Z, &b.P, &b.Q, &b.W,
+                &b.Dc};
     for (T **q : bl) {
         if (cudaMalloc((void **)q, blk) != cudaSuccess)
             return ofks_fail(c, OFKS_ENOMEM, "cannot allocate %zu bytes for an n x p block", blk);
@@ -131,6 +133,8 @@ static int alloc_blocks(ofks_ctx *c, int p, bool mixed) {
         cudaMemsetAsync(*b, 0, sm, c->stream);
     }
     if (cudaMalloc((void **)&c->d_colA, sizeof(double) * CB_COUNT * ld) != cudaSuccess ||
+        cudaMalloc((void **)&c->d_colC, sizeof(double) * CB_COUNT * ld) != cudaSuccess ||
+        cudaMalloc((void **)&c->d_cmap, sizeof(int) * 2 * ld) != cudaSuccess ||
         cudaMalloc((void **)&c->d_pp, sm * 8 + sizeof(double) * ld) != cudaSuccess) {
         free_blocks(c);
         return ofks_fail(c, OFKS_ENOMEM, "p x p scratch");
@@ -267,6 +271,9 @@ static int precondition_t(ofks_ctx *c) {
     }
     // with no column of negative multiplier every T is I (Eq. precondition-T): D = G, and no
     // linear system is solved
+    const bool learned = c->prm.precond == OFKS_PC_LEARNED;
+    PcgView<T> v;
+    v.w = ld; v.pc = c->p; v.cb = c->d_colA; v.D = D;
     {
         std::vector<double> act0(ld);
         cudaMemcpyAsync(act0.data(), c->d_colA + CB_ACTIVE * ld, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream);
@@ -280,6 +287,20 @@ static int precondition_t(ofks_ctx *c) {
             ProfScope ps(c, PF_PCG_UPDATE);
             launch_direction_select(c, b);
             return ofks_cuda_check(c, cudaGetLastError(), "preconditioner");
+        }
+        // the PCG on the active columns only, gathered into a block of width w (the columns are
+        // independent systems, so the others' work would only be discarded)
+        const int w = nact <= 2 ? nact : (nact + 3) / 4 * 4;
+        if (!learned && c->prm.pcg_compact && w < ld) {
+            std::vector<int> h(2 * (size_t)ld, -1);            // cmap | cpos
+            for (int j = 0, k = 0; j < c->p; ++j)
+                if (act0[j] != 0.0) { h[k] = j; h[ld + j] = k; ++k; }
+            cudaError_t e = cudaMemcpyAsync(c->d_cmap, h.data(), sizeof(int) * 2 * ld, cudaMemcpyHostToDevice,
+                                            c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // h leaves scope
+            if (e != cudaSuccess) return ofks_cuda_check(c, e, "preconditioner");
+            launch_pcg_compact_cols(c, w, nact, c->d_cmap, c->d_colC);
+            v.w = w; v.pc = nact; v.cb = c->d_colC; v.cmap = c->d_cmap; v.cpos = c->d_cmap + ld; v.D = b.Dc;
         }
     }
     bool run_pcg = true, warm = false;
@@ -295,7 +316,7 @@ static int precondition_t(ofks_ctx *c) {
         {
             ProfScope ps(c, PF_PCG_SPMM);
             launch_pcg_apply(c, vals_L<T>(c), vals_B<T>(c), (const T *)D, 0, b.P, b.Q, c->d_colA + CB_BETA * ld,
-                             c->d_colA + CB_SHIFT * ld, c->d_colA + CB_PQ * ld, 1);
+                             c->d_colA + CB_SHIFT * ld, c->d_colA + CB_PQ * ld, 1, ld, c->p);
         }
         launch_judge(c, b);
         std::vector<double> h(4 * (size_t)ld);
@@ -321,43 +342,44 @@ static int precondition_t(ofks_ctx *c) {
     if (run_pcg) {
         ProfScope ps(c, PF_PCG_UPDATE);
         if (warm) launch_pcg_init_warm(c, b);
-        else launch_pcg_init(c, b);
-        cudaMemsetAsync(c->d_colA + CB_PQ * ld, 0, sizeof(double) * ld, c->stream);
+        else launch_pcg_init(c, b, v);
+        cudaMemsetAsync(v.cb + CB_PQ * v.w, 0, sizeof(double) * v.w, c->stream);
     }
     const bool exact = c->prm.precond == OFKS_PC_EXACT;
     const int max_it = !run_pcg ? 0 : exact ? 5000 : c->prm.pcg_iters;
-    std::vector<double> rz0, rz(ld), act(ld);
+    const int w = v.w;
+    std::vector<double> rz0, rz(w), act(w);
     if (exact) {
-        rz0.resize(ld);
-        cudaMemcpyAsync(rz0.data(), c->d_colA + CB_RZ * ld, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream);
-        cudaMemcpyAsync(act.data(), c->d_colA + CB_ACTIVE * ld, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream);
+        rz0.resize(w);
+        cudaMemcpyAsync(rz0.data(), v.cb + CB_RZ * w, sizeof(double) * w, cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(act.data(), v.cb + CB_ACTIVE * w, sizeof(double) * w, cudaMemcpyDeviceToHost, c->stream);
         cudaStreamSynchronize(c->stream);
     }
     for (int it = 0; it < max_it; ++it) {
         {
             ProfScope ps(c, PF_PCG_SPMM);
-            launch_pcg_apply(c, vals_L<T>(c), vals_B<T>(c), (const T *)b.Z, pcg_zc<T>(c) ? 1 : 0, b.P, b.Q,
-                             c->d_colA + CB_BETA * ld,
-                             c->d_colA + CB_SHIFT * ld, c->d_colA + CB_PQ * ld, it == 0 ? 1 : 0);
+            launch_pcg_apply(c, vals_L<T>(c), vals_B<T>(c), (const T *)b.Z, pcg_zc<T>(c, w) ? 1 : 0, b.P, b.Q,
+                             v.cb + CB_BETA * w, v.cb + CB_SHIFT * w, v.cb + CB_PQ * w, it == 0 ? 1 : 0, w, v.pc);
         }
         {
             ProfScope ps(c, PF_PCG_UPDATE);
-            launch_pcg_alpha(c);
-            launch_pcg_update(c, b);
-            launch_pcg_beta(c);
+            launch_pcg_alpha(c, w, v.cb);
+            launch_pcg_update(c, b, v);
+            launch_pcg_beta(c, w, v.cb);
         }
         if (exact && (it + 1) % 25 == 0) {
-            cudaMemcpyAsync(rz.data(), c->d_colA + CB_RZ * ld, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream);
+            cudaMemcpyAsync(rz.data(), v.cb + CB_RZ * w, sizeof(double) * w, cudaMemcpyDeviceToHost, c->stream);
             cudaStreamSynchronize(c->stream);
             bool done = true;
-            for (int j = 0; j < c->p; ++j)
+            for (int j = 0; j < v.pc; ++j)
                 if (act[j] != 0.0 && rz[j] > 1e-24 * rz0[j]) done = false;
             if (done) break;
         }
     }
     {
         ProfScope ps(c, PF_PCG_UPDATE);
-        launch_direction_select(c, b);
+        if (v.cpos) launch_direction_expand(c, b, v);
+        else launch_direction_select(c, b);
     }
     return ofks_cuda_check(c, cudaGetLastError(), "preconditioner");
 }
@@ -471,7 +493,7 @@ void ofks_default_params(ofks_params *p) {
     p->poisson_pc = OFKS_HPC_SEPARABLE;
     p->mixed_tol = 1e-5; p->poisson_tol_mixed = 1e-8;
     p->judge_tau = 0.5; p->learned_tc = 1; p->poisson_adaptive = 0; p->poisson_csr = 0; p->gram_tc = 1;
-    p->poisson_sep_tc = 1; p->spmm_f32_rows = 0;
+    p->poisson_sep_tc = 1; p->spmm_f32_rows = 0; p->pcg_compact = 1;
 }
 
 int ofks_create(ofks_ctx **out, int device) {
@@ -561,6 +583,7 @@ int ofks_set_params(ofks_ctx *c, const ofks_params *prm) {
         prm->poisson_adaptive < 0 || prm->poisson_adaptive > 1 ||
         prm->poisson_csr < 0 || prm->poisson_csr > 1 || prm->poisson_sep_tc < 0 || prm->poisson_sep_tc > 1 ||
         prm->spmm_f32_rows < 0 || prm->spmm_f32_rows > 1 || prm->gram_tc < 0 || prm->gram_tc > 1 ||
+        prm->pcg_compact < 0 || prm->pcg_compact > 1 ||
         (prm->precision != OFKS_FP64 && prm->precision != OFKS_MIXED) || !(prm->mixed_tol > 0) ||
         !(prm->poisson_tol_mixed > 0) || !(prm->eta_min > 0) || !(prm->eta_max >= prm->eta_min) ||
         prm->multipole_lmax < -1 || prm->multipole_lmax > 2 || !(prm->poisson_tol > 0) ||

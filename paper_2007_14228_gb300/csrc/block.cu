@@ -268,10 +268,12 @@ __device__ __forceinline__ int64_t zidx(int zc, int64_t e, int64_t r, int j, int
     return zc ? (((int64_t)(j >> 2) * n + r) << 2) + (j & 3) : e;
 }
 
-// PCG start: W = 1/diag with diag = dL/2 - shift_c dB, D = 0, R = G, Z = G W, rz[c] = sum R Z
+// PCG start: W = 1/diag with diag = dL/2 - shift_c dB, D = 0, R = G, Z = G W, rz[c] = sum R Z.
+// The PCG block has width ld; with cmap its column c < p is column cmap[c] of G (row pitch ldg),
+// its other columns are zero.
 template <class T>
 __global__ void __launch_bounds__(256) k_pcg_init(int64_t n, int p, int ld, int64_t stride,
-                                                  const T *__restrict__ G,
+                                                  const T *__restrict__ G, int ldg, const int *__restrict__ cmap,
                                                   const double *__restrict__ dL,
                                                   const double *__restrict__ dB, const double *cb,
                                                   T *W, T *D, T *R, T *Z, double *rz, int zc) {
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(256) k_pcg_init(int64_t n, int p, int ld, int6
     ELEM_BEGIN
         const T sh = (T)cb[CB_SHIFT * ld + j];
         const T w = T(1) / (T(0.5) * (T)dL[r] - sh * (T)dB[r]);
-        const T gv = G[e];
+        const T gv = cmap ? (j < p ? G[r * ldg + cmap[j]] : T(0)) : G[e];
         const T z = gv * w;
         W[e] = w; D[e] = T(0); R[e] = gv; Z[zidx(zc, e, r, j, n)] = z;
         acc = fma(gv, z, acc);
@@ -384,6 +386,17 @@ __global__ void __launch_bounds__(256) k_pcg_update_zc(int64_t n, int p, int ld,
     }
     for (int j = threadIdx.x; j < ld && j < p; j += blockDim.x)
         if (cs[j] != 0.f) atomicAdd(rzn + j, (double)cs[j]);
+}
+
+// D from the compact PCG: column j takes compact column cpos[j] of Dc (width w), or G when
+// it is inactive (cpos[j] < 0: T = I in Eq. precondition-T)
+template <class T>
+__global__ void __launch_bounds__(256) k_expand(int64_t n, int ld, int64_t stride, int w, const int *__restrict__ cpos,
+                                                const T *__restrict__ G, const T *__restrict__ Dc, T *D) {
+    ELEM_BEGIN
+        const int k = cpos[j];
+        D[e] = k >= 0 ? Dc[r * w + k] : G[e];
+    ELEM_END
 }
 
 // columns whose shift is not negative take D = G (T = I in Eq. precondition-T)
@@ -549,8 +562,8 @@ void launch_gram2(ofks_ctx *c, const T *X, const T *A, const T *B, double *XA, d
     k_mirror2<<<4, 256, 0, c->stream>>>(p, ld, XA, XB);
 }
 
-template <> bool pcg_zc<double>(const ofks_ctx *) { return false; }
-template <> bool pcg_zc<float>(const ofks_ctx *c) { return c->n_tslices > 0 && c->ld >= 4 && c->ld % 4 == 0; }
+template <> bool pcg_zc<double>(const ofks_ctx *, int) { return false; }
+template <> bool pcg_zc<float>(const ofks_ctx *c, int w) { return c->n_tslices > 0 && w >= 4 && w % 4 == 0; }
 
 // grid of 256-thread blocks whose total thread count is a multiple of ld
 struct ElemGrid { unsigned blocks; int64_t stride; };
@@ -593,15 +606,14 @@ void launch_grad_update(ofks_ctx *c, Blocks<T> &b) {
 }
 
 template <class T>
-void launch_pcg_init(ofks_ctx *c, Blocks<T> &b) {
+void launch_pcg_init(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v) {
     c->kernels += 1;
-    const int ld = c->ld;
-    double *cb = c->d_colA;
-    cudaMemsetAsync(cb + CB_RZ * ld, 0, sizeof(double) * ld, c->stream);
-    const ElemGrid g = elem_grid(c->n, ld);
-    k_pcg_init<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, b.G[c->cur], c->d_dL, c->d_dB, cb,
-                                                   b.W, b.D[c->cur], b.R, b.Z, cb + CB_RZ * ld,
-                                                   pcg_zc<T>(c) ? 1 : 0);
+    const int w = v.w;
+    cudaMemsetAsync(v.cb + CB_RZ * w, 0, sizeof(double) * w, c->stream);
+    const ElemGrid g = elem_grid(c->n, w);
+    k_pcg_init<T><<<g.blocks, 256, 0, c->stream>>>(c->n, v.pc, w, g.stride, b.G[c->cur], c->ld, v.cmap, c->d_dL,
+                                                   c->d_dB, v.cb, b.W, v.D, b.R, b.Z, v.cb + CB_RZ * w,
+                                                   pcg_zc<T>(c, w) ? 1 : 0);
 }
 
 template <class T>
@@ -624,27 +636,34 @@ void launch_pcg_init_warm(ofks_ctx *c, Blocks<T> &b) {
     const ElemGrid g = elem_grid(c->n, ld);
     k_pcg_init_warm<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, b.G[c->cur], b.Q, c->d_dL, c->d_dB,
                                                         cb, b.W, b.R, b.Z, cb + CB_RZ * ld,
-                                                        pcg_zc<T>(c) ? 1 : 0);
+                                                        pcg_zc<T>(c, ld) ? 1 : 0);
 }
 
 template <class T>
-void launch_pcg_update(ofks_ctx *c, Blocks<T> &b) {
+void launch_pcg_update(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v) {
     c->kernels += 1;
-    const int ld = c->ld;
-    double *cb = c->d_colA;
+    const int w = v.w;
+    double *cb = v.cb;
     if constexpr (sizeof(T) == 4) {
-        if (pcg_zc<T>(c)) {
-            const size_t sm = sizeof(float) * (UZ_ROWS * ld + 2 * ld);
+        if (pcg_zc<T>(c, w)) {
+            const size_t sm = sizeof(float) * (UZ_ROWS * w + 2 * w);
             const unsigned grid = (unsigned)std::min<int64_t>((c->n + UZ_ROWS - 1) / UZ_ROWS, 152 * 8);
-            k_pcg_update_zc<<<grid, 256, sm, c->stream>>>(c->n, c->p, ld, cb, (const float *)b.W, (const float *)b.P,
-                                                          (const float *)b.Q, (float *)b.D[c->cur], (float *)b.R,
-                                                          (float *)b.Z, cb + CB_RZN * ld);
+            k_pcg_update_zc<<<grid, 256, sm, c->stream>>>(c->n, v.pc, w, cb, (const float *)b.W, (const float *)b.P,
+                                                          (const float *)b.Q, (float *)v.D, (float *)b.R,
+                                                          (float *)b.Z, cb + CB_RZN * w);
             return;
         }
     }
-    const ElemGrid g = elem_grid(c->n, ld);
-    k_pcg_update<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, cb, b.W, b.P, b.Q, b.D[c->cur], b.R,
-                                                     b.Z, cb + CB_RZN * ld, pcg_zc<T>(c) ? 1 : 0);
+    const ElemGrid g = elem_grid(c->n, w);
+    k_pcg_update<T><<<g.blocks, 256, 0, c->stream>>>(c->n, v.pc, w, g.stride, cb, b.W, b.P, b.Q, v.D, b.R,
+                                                     b.Z, cb + CB_RZN * w, pcg_zc<T>(c, w) ? 1 : 0);
+}
+
+template <class T>
+void launch_direction_expand(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v) {
+    c->kernels += 1;
+    const ElemGrid g = elem_grid(c->n, c->ld);
+    k_expand<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->ld, g.stride, v.w, v.cpos, b.G[c->cur], v.D, b.D[c->cur]);
 }
 
 template <class T>
@@ -728,8 +747,9 @@ void launch_convert(ofks_ctx *c, const S *src, T *dst, int64_t count) {
 #define INST(T)                                                                                      \
     template void launch_gram2<T>(ofks_ctx *, const T *, const T *, const T *, double *, double *); \
     template void launch_grad_update<T>(ofks_ctx *, Blocks<T> &);                                    \
-    template void launch_pcg_init<T>(ofks_ctx *, Blocks<T> &);                                       \
-    template void launch_pcg_update<T>(ofks_ctx *, Blocks<T> &);                                     \
+    template void launch_pcg_init<T>(ofks_ctx *, Blocks<T> &, const PcgView<T> &);                   \
+    template void launch_pcg_update<T>(ofks_ctx *, Blocks<T> &, const PcgView<T> &);                 \
+    template void launch_direction_expand<T>(ofks_ctx *, Blocks<T> &, const PcgView<T> &);           \
     template void launch_judge<T>(ofks_ctx *, Blocks<T> &);                                          \
     template void launch_pcg_init_warm<T>(ofks_ctx *, Blocks<T> &);                                 \
     template void launch_direction_select<T>(ofks_ctx *, Blocks<T> &);                               \

@@ -52,6 +52,7 @@ struct Blocks {
     T *X[2] = {nullptr, nullptr}, *D[2] = {nullptr, nullptr}, *G[2] = {nullptr, nullptr};
     T *HX = nullptr, *BX = nullptr;
     T *R = nullptr, *Z = nullptr, *P = nullptr, *Q = nullptr, *W = nullptr;   // PCG block, W = 1/diag
+    T *Dc = nullptr;                                       // PCG result on the active columns only
     T *valL = nullptr, *valB = nullptr, *valH = nullptr;   // SELL values (float set only; the
                                                            // float64 values are d_valL/B/H)
 };
@@ -178,6 +179,8 @@ struct ofks_ctx {
     double *d_colA = nullptr;                    // 4 x p column accumulators
     double *d_pp = nullptr;                      // p x p scratch (factorizations)
     double *d_stage = nullptr;                   // n x p dense staging of host block copies (ld > p)
+    double *d_colC = nullptr;                    // per-column PCG arrays of the compact form (stride w)
+    int *d_cmap = nullptr;                       // compact form: active column ids [ld], compact index [ld]
     double *d_sc = nullptr;                      // SC_COUNT scalars
     double *d_rec = nullptr;                     // iteration record (device)
     int *d_flag = nullptr;                       // error / status flags
@@ -262,9 +265,10 @@ void amg_apply(ofks_ctx *c, const double *r_full, double *z_full);
 template <class T> void launch_sell_spmm(ofks_ctx *c, const T *val, const T *X, T *Y);
 template <class T> void launch_sell_spmm_ld(ofks_ctx *c, const T *val, const T *X, T *Y, int ld);
 template <class T> void launch_sell_spmm_colnorm(ofks_ctx *c, const T *val, const T *X, T *Y, double *colsum);
+// the PCG operator apply on a block of width w with pc real columns (w = ld, pc = p: all columns)
 template <class T>
 void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, int zc, T *P, T *Q, const double *beta_col,
-                      const double *shift, double *pq, int first);
+                      const double *shift, double *pq, int first, int w, int pc);
 
 // ---- block.cu (tall-skinny products and vector updates)
 template <class T> void launch_gram2(ofks_ctx *c, const T *X, const T *A, const T *B, double *XA, double *XB);
@@ -273,13 +277,26 @@ bool launch_gram_tc(ofks_ctx *c, const float *X, const float *A, const float *B,
 // grad_tc.cu: G = H X + B X C and |H X - B X Lambda0|^2 on the tensor cores (false: not supported)
 bool launch_grad_tc(ofks_ctx *c, const float *HX, const float *BX, float *G, double *kkt2);
 template <class T> void launch_grad_update(ofks_ctx *c, Blocks<T> &b);
+// The PCG's working set: its block width w (row pitch of R, Z, P, Q, W and of the D it builds,
+// and the stride of its per-column arrays cb) and its real column count pc.  In the compact
+// form the columns are the active ones only: compact column k < pc is column cmap[k] of G, and
+// cpos[j] is the compact index of column j (-1: inactive, D = G).
+template <class T>
+struct PcgView {
+    int w = 0, pc = 0;
+    double *cb = nullptr;
+    const int *cmap = nullptr, *cpos = nullptr;
+    T *D = nullptr;
+};
 // float32 PCG blocks keep Z chunk-major (4 columns x n rows per chunk) on lattice meshes
-template <class T> bool pcg_zc(const ofks_ctx *c);
-template <class T> void launch_pcg_init(ofks_ctx *c, Blocks<T> &b);
-template <class T> void launch_pcg_update(ofks_ctx *c, Blocks<T> &b);
+template <class T> bool pcg_zc(const ofks_ctx *c, int w);
+template <class T> void launch_pcg_init(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v);
+template <class T> void launch_pcg_update(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v);
 template <class T> void launch_judge(ofks_ctx *c, Blocks<T> &b);
 template <class T> void launch_pcg_init_warm(ofks_ctx *c, Blocks<T> &b);
 template <class T> void launch_direction_select(ofks_ctx *c, Blocks<T> &b);
+// D = the compact PCG result on the active columns, G on the others
+template <class T> void launch_direction_expand(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v);
 template <class T> void launch_bb_dots(ofks_ctx *c, Blocks<T> &b, bool raw);
 template <class T> void launch_step_y(ofks_ctx *c, Blocks<T> &b, T *Y);
 template <class T> void launch_scale_cols(ofks_ctx *c, T *Y, T *BY, const double *colsum);
@@ -292,8 +309,10 @@ void launch_repack(ofks_ctx *c, const double *src, int64_t sp, double *dst, int6
 void launch_small_update(ofks_ctx *c);
 void launch_small_record(ofks_ctx *c);
 void launch_eta(ofks_ctx *c);
-void launch_pcg_alpha(ofks_ctx *c);
-void launch_pcg_beta(ofks_ctx *c);
+void launch_pcg_alpha(ofks_ctx *c, int w, double *cb);
+void launch_pcg_beta(ofks_ctx *c, int w, double *cb);
+// the compact form's per-column arrays: shift of the active columns, everything else zero
+void launch_pcg_compact_cols(ofks_ctx *c, int w, int nact, const int *cmap, double *colC);
 void launch_cholesky_inv(ofks_ctx *c, const double *S, double *Rinv);
 void launch_rayleigh_ritz(ofks_ctx *c, const double *A, const double *S, double *eigs, double *V);
 

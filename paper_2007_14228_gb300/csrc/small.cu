@@ -86,6 +86,18 @@ __global__ void k_pcg_alpha(int ld, double *cb) {
     }
 }
 
+// per-column arrays of the compact PCG (stride w): compact column k < nact is column cmap[k]
+// (stride ld in colA) and keeps its shift; every other entry starts at zero
+__global__ void k_pcg_compact_cols(int ld, int w, int nact, const int *__restrict__ cmap, const double *__restrict__ colA,
+                                   double *colC) {
+    for (int i = threadIdx.x; i < CB_COUNT * w; i += blockDim.x) colC[i] = 0.0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < nact; k += blockDim.x) {
+        colC[CB_SHIFT * w + k] = colA[CB_SHIFT * ld + cmap[k]];
+        colC[CB_ACTIVE * w + k] = 1.0;
+    }
+}
+
 // beta_c = rzn_c / rz_c (0 if rz_c <= 0); rz <- rzn; clear pq
 __global__ void k_pcg_beta(int ld, double *cb) {
     for (int j = threadIdx.x; j < ld; j += blockDim.x) {
@@ -272,8 +284,12 @@ void launch_eta(ofks_ctx *c) { c->kernels += 1;
                                   c->prm.eta_max, c->d_sc, c->d_rec);
 }
 
-void launch_pcg_alpha(ofks_ctx *c) { c->kernels += 1; k_pcg_alpha<<<1, 256, 0, c->stream>>>(c->ld, c->d_colA); }
-void launch_pcg_beta(ofks_ctx *c) { c->kernels += 1; k_pcg_beta<<<1, 256, 0, c->stream>>>(c->ld, c->d_colA); }
+void launch_pcg_alpha(ofks_ctx *c, int w, double *cb) { c->kernels += 1; k_pcg_alpha<<<1, 256, 0, c->stream>>>(w, cb); }
+void launch_pcg_beta(ofks_ctx *c, int w, double *cb) { c->kernels += 1; k_pcg_beta<<<1, 256, 0, c->stream>>>(w, cb); }
+void launch_pcg_compact_cols(ofks_ctx *c, int w, int nact, const int *cmap, double *colC) {
+    c->kernels += 1;
+    k_pcg_compact_cols<<<1, 256, 0, c->stream>>>(c->ld, w, nact, cmap, c->d_colA, colC);
+}
 
 void launch_cholesky_inv(ofks_ctx *c, const double *S, double *Rinv) { c->kernels += 1;
     k_cholesky_inv<<<1, 512, 0, c->stream>>>(c->p, c->ld, S, c->d_pp, Rinv, c->d_flag);

@@ -396,13 +396,13 @@ __global__ void __launch_bounds__(RW * 32) k_rows_f32(int n_slices, int p, int l
 
 // half-warp-per-row launch for float32 blocks; false when the shapes do not suit it
 template <int MODE>
-bool launch_rows_f32(ofks_ctx *c, int ld, const float *valA, const float *valB, const float *X, float *Y, float *Y2,
+bool launch_rows_f32(ofks_ctx *c, int ld, int pc, const float *valA, const float *valB, const float *X, float *Y, float *Y2,
                      const double *beta_col, const double *shift, double *colsum, int first) {
     if (!c->prm.spmm_f32_rows || ld < 16 || ld % 4 || ld > 256) return false;
     const int64_t items = (int64_t)c->n_slices * (SELL_C / 4);
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + RW - 1) / RW, 152 * 8));
 #define R_(v)                                                                                                      \
-    k_rows_f32<v, MODE><<<grid, RW * 32, 0, c->stream>>>(c->n_slices, c->p, ld, c->d_slice_ptr, c->d_slice_w,     \
+    k_rows_f32<v, MODE><<<grid, RW * 32, 0, c->stream>>>(c->n_slices, pc, ld, c->d_slice_ptr, c->d_slice_w,     \
                                                          c->d_cols, c->d_perm, valA, valB, X, Y, Y2, beta_col,    \
                                                          shift, colsum, first)
     if (ld <= 64) R_(4);
@@ -418,7 +418,7 @@ bool launch_rows_f32(ofks_ctx *c, int ld, const float *valA, const float *valB, 
 template <class T>
 void launch_sell_spmm(ofks_ctx *c, const T *val, const T *X, T *Y) {
     if constexpr (sizeof(T) == 4)
-        if (launch_rows_f32<0>(c, c->ld, val, nullptr, X, Y, nullptr, nullptr, nullptr, nullptr, 0)) return;
+        if (launch_rows_f32<0>(c, c->ld, c->p, val, nullptr, X, Y, nullptr, nullptr, nullptr, nullptr, 0)) return;
     const int W = chunk_width(c->ld), nch = c->ld / W;
     const int64_t nw = (int64_t)c->n_slices * nch;
     const unsigned grid = (unsigned)((nw * 32 + 255) / 256);
@@ -432,7 +432,7 @@ void launch_sell_spmm(ofks_ctx *c, const T *val, const T *X, T *Y) {
 template <class T>
 void launch_sell_spmm_colnorm(ofks_ctx *c, const T *val, const T *X, T *Y, double *colsum) {
     if constexpr (sizeof(T) == 4)
-        if (launch_rows_f32<1>(c, c->ld, val, nullptr, X, Y, nullptr, nullptr, nullptr, colsum, 0)) return;
+        if (launch_rows_f32<1>(c, c->ld, c->p, val, nullptr, X, Y, nullptr, nullptr, nullptr, colsum, 0)) return;
     const int W = chunk_width(c->ld), nch = c->ld / W;
     const int spw = spw_for((int64_t)c->n_slices * nch);
     const int64_t nw = (((int64_t)c->n_slices + spw - 1) / spw) * nch;
@@ -446,26 +446,27 @@ void launch_sell_spmm_colnorm(ofks_ctx *c, const T *val, const T *X, T *Y, doubl
 
 template <class T>
 void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, int zc, T *P, T *Q, const double *beta_col,
-                      const double *shift, double *pq, int first) {
+                      const double *shift, double *pq, int first, int w, int pc) {
     if constexpr (sizeof(T) == 4) {
         if (zc) {
-            const int nch = c->ld / 4;
+            const int nch = w / 4;
             const int spw = spw_for((int64_t)c->n_tslices * nch);
             const int64_t nw = (((int64_t)c->n_tslices + spw - 1) / spw) * nch;
             k_pcg_apply_zc<<<(unsigned)((nw * 32 + 255) / 256), 256, 0, c->stream>>>(
-                nw, nch, (int64_t)c->n_tslices, spw, c->p, c->ld, c->n, c->d_tslice_ptr, c->d_tslice_w, c->d_tcols, c->d_tperm, c->d_tvalL,
-                c->d_tvalB, (const float *)Zin, (float *)P, (float *)Q, beta_col, shift, pq, first);
+                nw, nch, (int64_t)c->n_tslices, spw, pc, w, c->n, c->d_tslice_ptr, c->d_tslice_w, c->d_tcols,
+                c->d_tperm, c->d_tvalL, c->d_tvalB, (const float *)Zin, (float *)P, (float *)Q, beta_col, shift, pq,
+                first);
             c->kernels += 1;
             return;
         }
     }
     if constexpr (sizeof(T) == 4)
-        if (launch_rows_f32<2>(c, c->ld, valL, valB, Zin, P, Q, beta_col, shift, pq, first)) return;
-    const int W = chunk_width(c->ld), nch = c->ld / W;
+        if (launch_rows_f32<2>(c, w, pc, valL, valB, Zin, P, Q, beta_col, shift, pq, first)) return;
+    const int W = chunk_width(w), nch = w / W;
     const int spw = spw_for((int64_t)c->n_slices * nch);
     const int64_t nw = (((int64_t)c->n_slices + spw - 1) / spw) * nch;
     const unsigned grid = (unsigned)((nw * 32 + 255) / 256);
-#define L_(w) k_pcg_apply<T, w><<<grid, 256, 0, c->stream>>>(nw, nch, (int64_t)c->n_slices, spw, c->p, c->ld, c->d_slice_ptr, \
+#define L_(v) k_pcg_apply<T, v><<<grid, 256, 0, c->stream>>>(nw, nch, (int64_t)c->n_slices, spw, pc, w, c->d_slice_ptr, \
         c->d_slice_w, c->d_cols, c->d_perm, valL, valB, Zin, P, Q, beta_col, shift, pq, first)
     if (W == 4) L_(4); else if (W == 2) L_(2); else L_(1);
 #undef L_
@@ -490,6 +491,6 @@ template void launch_sell_spmm<float>(ofks_ctx *, const float *, const float *, 
 template void launch_sell_spmm_colnorm<double>(ofks_ctx *, const double *, const double *, double *, double *);
 template void launch_sell_spmm_colnorm<float>(ofks_ctx *, const float *, const float *, float *, double *);
 template void launch_pcg_apply<double>(ofks_ctx *, const double *, const double *, const double *, int, double *,
-                                       double *, const double *, const double *, double *, int);
+                                       double *, const double *, const double *, double *, int, int, int);
 template void launch_pcg_apply<float>(ofks_ctx *, const float *, const float *, const float *, int, float *, float *,
-                                      const double *, const double *, double *, int);
+                                      const double *, const double *, double *, int, int, int);

@@ -122,6 +122,35 @@ def test_float32_preconditioner_matches_the_oracle(ofks, case):
     ctx.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_compact_pcg_matches_full_width_and_the_oracle(ofks, precision):
+    # Eq. precondition-T solves one system per column with Lambda_ii < 0; the compact form runs the
+    # PCG on those columns only, gathered into a block of their count rounded up to 4 (here 24 of
+    # 41, scattered over the block), and must give what the PCG on all columns gives
+    s = I.chain(cells=(26, 14, 8))
+    m = I.make_mesh(s)
+    rng = np.random.default_rng(11)
+    G = rng.standard_normal((m.n_free, s.p))
+    shifts = -rng.uniform(0.05, 2.0, s.p)
+    inactive = rng.choice(s.p, 17, replace=False)
+    shifts[inactive] = rng.uniform(0.05, 1.0, inactive.size)      # T = I there
+    D = {}
+    for compact in (1, 0):
+        ctx = ofks.context_for(s, m, beta=10.0, precision=precision, pcg_compact=compact)
+        D[compact] = ctx.precondition("pcg", G, shifts)
+        ctx.close()
+    pr = pcal.Problem(m.xyz, m.tet10, m.dirichlet, s.Z, s.R, pcal.Params(p=s.p, occ=s.occ, hartree=False, xc=False))
+    Do = pr.precondition(G, shifts)
+    scale = np.max(np.abs(Do))
+    tol_oracle, tol_pair = (1e-10, 1e-12) if precision == "fp64" else (1e-4, 1e-5)
+    assert np.max(np.abs(D[1] - Do)) < tol_oracle * scale, np.max(np.abs(D[1] - Do)) / scale
+    assert np.max(np.abs(D[1] - D[0])) < tol_pair * scale, np.max(np.abs(D[1] - D[0])) / scale
+    if precision == "fp64":
+        assert np.array_equal(D[1][:, inactive], G[:, inactive])
+    else:
+        assert np.array_equal(D[1][:, inactive].astype(np.float32), G[:, inactive].astype(np.float32))
+
+
 @pytest.mark.parametrize("case", ["chain_p41", "h2o_p5"])
 def test_tensor_core_grams_match(ofks, case):
     # Lambda0 = X^T H X and S = X^T B X (bf16 hi/lo split, three products) and the gradient

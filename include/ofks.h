@@ -147,6 +147,8 @@ typedef struct {
     int64_t judge_total;    /* ... out of this many judged */
     int32_t active_last;    /* columns with a negative multiplier (T != I) at the last direction */
     int64_t active_total;   /* ... summed over the directions computed so far */
+    int64_t pcg_cols_total; /* block width of each PCG operator apply, summed over the applies so far
+                               (the active count rounded up to 4 in the compact form, ld otherwise) */
 } ofks_result;
 
 /* Fill *prm with the defaults: beta 10, occ 2, tol 1e-8, max_iter 1000, FP64, PCG with 8

@@ -360,6 +360,7 @@ static int precondition_t(ofks_ctx *c) {
             ProfScope ps(c, PF_PCG_SPMM);
             launch_pcg_apply(c, vals_L<T>(c), vals_B<T>(c), (const T *)b.Z, pcg_zc<T>(c, w) ? 1 : 0, b.P, b.Q,
                              v.cb + CB_BETA * w, v.cb + CB_SHIFT * w, v.cb + CB_PQ * w, it == 0 ? 1 : 0, w, v.pc);
+            c->pcg_cols_total += w;
         }
         {
             ProfScope ps(c, PF_PCG_UPDATE);
@@ -476,6 +477,7 @@ static int run_iterations(ofks_ctx *c, int kmax, ofks_result *res) {
         res->judge_total = c->judge_total;
         res->active_last = c->last_active;
         res->active_total = c->active_total;
+        res->pcg_cols_total = c->pcg_cols_total;
     }
     return rc;
 }

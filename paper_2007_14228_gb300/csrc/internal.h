@@ -205,6 +205,7 @@ struct ofks_ctx {
     int64_t judge_accept = 0, judge_total = 0;   // learned preconditioner: columns accepted / judged
     int last_active = 0;                         // columns with T != I at the last direction
     int64_t active_total = 0;
+    int64_t pcg_cols_total = 0;                  // PCG block width summed over the operator applies
 
     // ---- profiling
     int64_t kernels = 0;                         // kernel launches issued (all families)

@@ -55,7 +55,8 @@ class Result(C.Structure):
                 ("kkt0", C.c_double), ("eta", C.c_double), ("iters", C.c_int32), ("converged", C.c_int32),
                 ("seconds", C.c_double), ("hartree_iters", C.c_int32), ("hartree_total", C.c_int32),
                 ("switch_iter", C.c_int32), ("judge_accept", C.c_int64), ("judge_total", C.c_int64),
-                ("active_last", C.c_int32), ("active_total", C.c_int64)]
+                ("active_last", C.c_int32), ("active_total", C.c_int64),
+                ("pcg_cols_total", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -235,6 +235,97 @@ __global__ void __launch_bounds__(256) k_grad_f32(int64_t n, int p, int ld, cons
     if (threadIdx.x == 0) atomicAdd(kkt2, part);
 }
 
+// float32 blocks with 64 < ld <= 256: C and L0 no longer fit in shared memory whole, so each CTA
+// owns a 64-column slice of the outputs (C[:, c0:c0+64] and L0[:, c0:c0+64] stay in shared
+// memory) and walks 64-row tiles of B X, staged transposed so that one float4 load gives four
+// rows of a column k.  A thread keeps a 4-row x 4-column tile of G and of R: per k one float4 of
+// B X, one of C and one of L0 feed 32 FMAs.  The CTAs of one row tile run side by side (slice =
+// block index mod the slice count), so their B X reads after the first come from L2.
+constexpr int GW_ROWS = 64, GW_COLS = 64, GW_PAD = GW_ROWS + 4;
+
+__global__ void __launch_bounds__(256) k_grad_f32w(int64_t n, int p, int ld, int nslices,
+                                                   const float *__restrict__ HX, const float *__restrict__ BX,
+                                                   const double *__restrict__ C, const double *__restrict__ L0,
+                                                   float *G, double *kkt2) {
+    extern __shared__ __align__(16) float gwm[];
+    float *cs = gwm;                          // ld x GW_COLS
+    float *ls = cs + ld * GW_COLS;            // ld x GW_COLS
+    float *bt = ls + ld * GW_COLS;            // ld x GW_PAD: bt[k GW_PAD + row] = B X[r0 + row][k]
+    __shared__ double red[8];
+    const int slice = blockIdx.x % nslices, c0 = slice * GW_COLS;
+    const int cps = gridDim.x / nslices, ci = blockIdx.x / nslices;   // CTAs per slice, this CTA's index
+    for (int i = threadIdx.x; i < ld * GW_COLS; i += blockDim.x) {
+        const int k = i / GW_COLS, col = c0 + (i - k * GW_COLS);
+        cs[i] = col < ld ? (float)C[(int64_t)k * ld + col] : 0.f;
+        ls[i] = col < ld ? (float)L0[(int64_t)k * ld + col] : 0.f;
+    }
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int col0 = c0 + 4 * tx;             // this thread's 4 columns (ld % 4 == 0: all in or all out)
+    const bool cin = col0 < ld;
+    double part = 0.0;
+    for (int64_t r0 = (int64_t)ci * GW_ROWS; r0 < n; r0 += (int64_t)GW_ROWS * cps) {
+        const int rows = (int)(n - r0 < GW_ROWS ? n - r0 : GW_ROWS);
+        // the tile's float4 pieces: all loads issued before the transposed stores (one round trip)
+        constexpr int MAXV = GW_ROWS * 256 / 4 / 256;
+        const int nv = GW_ROWS * ld / 4;
+        float4 v[MAXV];
+#pragma unroll
+        for (int q = 0; q < MAXV; ++q) {
+            const int e4 = threadIdx.x + q * 256;
+            v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e4 < nv && (e4 * 4) / ld < rows) v[q] = *reinterpret_cast<const float4 *>(BX + r0 * ld + e4 * 4);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < MAXV; ++q) {
+            const int e4 = threadIdx.x + q * 256;
+            if (e4 >= nv) break;
+            const int row = (e4 * 4) / ld, k = e4 * 4 - row * ld;      // k..k+3 lie in the same row
+            bt[k * GW_PAD + row] = v[q].x;
+            bt[(k + 1) * GW_PAD + row] = v[q].y;
+            bt[(k + 2) * GW_PAD + row] = v[q].z;
+            bt[(k + 3) * GW_PAD + row] = v[q].w;
+        }
+        __syncthreads();
+        float g[4][4], rr[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int row = 4 * ty + i;
+            float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (cin && row < rows) h = *reinterpret_cast<const float4 *>(HX + (r0 + row) * ld + col0);
+            g[i][0] = rr[i][0] = h.x; g[i][1] = rr[i][1] = h.y; g[i][2] = rr[i][2] = h.z; g[i][3] = rr[i][3] = h.w;
+        }
+#pragma unroll 2
+        for (int kk = 0; kk < ld; ++kk) {
+            const float4 b = *reinterpret_cast<const float4 *>(bt + kk * GW_PAD + 4 * ty);
+            const float4 cv = *reinterpret_cast<const float4 *>(cs + kk * GW_COLS + 4 * tx);
+            const float4 lv = *reinterpret_cast<const float4 *>(ls + kk * GW_COLS + 4 * tx);
+            const float bb[4] = {b.x, b.y, b.z, b.w}, cc[4] = {cv.x, cv.y, cv.z, cv.w}, ll[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    g[i][j] = fmaf(bb[i], cc[j], g[i][j]);
+                    rr[i][j] = fmaf(-bb[i], ll[j], rr[i][j]);
+                }
+        }
+        if (!cin) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int row = 4 * ty + i;
+            if (row >= rows) continue;
+            *reinterpret_cast<float4 *>(G + (r0 + row) * ld + col0) = make_float4(g[i][0], g[i][1], g[i][2], g[i][3]);
+            float rp = 0.f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (col0 + j < p) rp = fmaf(rr[i][j], rr[i][j], rp);
+            part += (double)rp;
+        }
+    }
+    part = block_sum(part, red);
+    if (threadIdx.x == 0) atomicAdd(kkt2, part);
+}
+
 // ---------------------------------------------------------------- elementwise block kernels
 // Flattened over the n x ld elements with a stride that is a multiple of ld, so each thread
 // keeps one column: per-column scalars are read once and per-column sums stay in a register.
@@ -584,6 +675,16 @@ void launch_grad_update(ofks_ctx *c, Blocks<T> &b) {
     cudaMemsetAsync(c->d_sc + SC_KKT2, 0, sizeof(double), c->stream);
     if constexpr (sizeof(T) == 4) {
         if (launch_grad_tc(c, (const float *)b.HX, (const float *)b.BX, (float *)G, c->d_sc + SC_KKT2)) return;
+        if (ld > 64 && ld <= 256 && ld % 4 == 0) {
+            const int nsl = (ld + GW_COLS - 1) / GW_COLS;
+            const int smw = (int)(sizeof(float) * (size_t)ld * (2 * GW_COLS + GW_PAD));
+            const unsigned gw = (unsigned)(nsl * std::max<int64_t>(1, std::min<int64_t>((c->n + GW_ROWS - 1) / GW_ROWS,
+                                                                                      152 / nsl)));
+            cudaFuncSetAttribute(k_grad_f32w, cudaFuncAttributeMaxDynamicSharedMemorySize, smw);
+            k_grad_f32w<<<gw, 256, smw, c->stream>>>(c->n, c->p, ld, nsl, (const float *)b.HX, (const float *)b.BX,
+                                                     c->d_C, c->d_L0, (float *)G, c->d_sc + SC_KKT2);
+            return;
+        }
         if (ld <= 64) {
             const int smf = (int)(sizeof(float) * (2 * ld * ld + 64 * ld));
             const unsigned gf = (unsigned)std::max<int64_t>(1, std::min<int64_t>((c->n + 63) / 64, 152 * 4));

@@ -188,3 +188,33 @@ def test_tensor_core_grams_match(ofks, case):
         assert np.max(np.abs(res["tc"][k] - ref)) < 2e-5 * scale, (k, np.max(np.abs(res["tc"][k] - ref)) / scale)
         assert np.max(np.abs(res["tc"][k] - res["cuda"][k])) < 2e-5 * scale
         assert np.allclose(res["tc"][k], res["tc"][k].T, rtol=0, atol=1e-12 * scale)
+
+
+@pytest.mark.parametrize("pw", [70, 130])
+def test_wide_float32_gradient_and_grams_match(ofks, pw):
+    # ld > 64 (72: two 64-column slices, the second 8 wide; 132: three): the float32 gradient
+    # G = H X + B X C with kkt from the column-sliced CUDA-core kernel and the float32 Grams, against
+    # the float64 form at the same iterate
+    s = I.chain(cells=(26, 14, 8)).with_p(pw, occ=1.0)
+    m = I.make_mesh(s)
+    V = I.initial_block(m.n_free, s.p, 0)
+    ctx = ofks.context_for(s, m, beta=10.0, precision="fp64")
+    ctx.init_orbitals(V)
+    ctx.step(3)
+    X = ctx.get_orbitals()
+    ctx.close()
+    res = {}
+    for name, kw in (("f32", dict(precision="mixed")), ("fp64", dict(precision="fp64"))):
+        ctx = ofks.context_for(s, m, beta=10.0, **kw)
+        ctx.set_orbitals(X)
+        r = ctx.evaluate()
+        res[name] = (ctx.get_field("Lambda0"), ctx.get_field("S"), ctx.get_field("G"), r["kkt"])
+        ctx.close()
+    g_ref = res["fp64"][2]
+    gs = np.max(np.abs(g_ref))
+    assert np.max(np.abs(res["f32"][2] - g_ref)) < 1e-4 * gs, np.max(np.abs(res["f32"][2] - g_ref)) / gs
+    assert abs(res["f32"][3] - res["fp64"][3]) < 1e-4 * res["fp64"][3]
+    for k in (0, 1):
+        ref = res["fp64"][k]
+        scale = np.max(np.abs(ref))
+        assert np.max(np.abs(res["f32"][k] - ref)) < 2e-5 * scale, (k, np.max(np.abs(res["f32"][k] - ref)) / scale)

@@ -20,22 +20,35 @@ constexpr double RHO_MIN = 1e-14;
 //             V_c = eps_c (1 + 7/6 b1 sqrt(r_s) + 4/3 b2 r_s)/(1 + b1 sqrt(r_s) + b2 r_s)
 //   r_s <  1: eps_c = A ln r_s + B + C r_s ln r_s + D r_s,
 //             V_c = A ln r_s + (B - A/3) + (2/3) C r_s ln r_s + (2 D - C)/3 r_s
-__device__ __forceinline__ double lda(double rho, double &vxc) {
-    if (!(rho >= RHO_MIN)) { vxc = 0.0; return 0.0; }
-    const double g = -0.1423, b1 = 1.0529, b2 = 0.3334;
-    const double A = 0.0311, B = -0.048, C = 0.0020, D = -0.0116;
-    double t = cbrt(3.0 * rho / PI);
-    double ex = -0.75 * t, vx = -t;
-    double rs = cbrt(3.0 / (4.0 * PI * rho));
-    double ec, vc;
-    if (rs >= 1.0) {
-        double sq = sqrt(rs), den = 1.0 + b1 * sq + b2 * rs;
+// With t = (3 rho/pi)^(1/3), t^3 r_s^3 = 9/(4 pi^2), so r_s = K_RS / t and one cube root
+// serves both terms.  F is the arithmetic type: float64, or float32 for the float32 iterations
+// (the FP64 pipe is the limit of this kernel on GB300; the potential enters float32 H values).
+constexpr double K_RS = 0.610887057710857191300739313402;   // (9/(4 pi^2))^(1/3)
+
+template <class F>
+__device__ __forceinline__ F lda(F rho, F &vxc) {
+    if (!(rho >= F(RHO_MIN))) { vxc = F(0); return F(0); }
+    const F g = F(-0.1423), b1 = F(1.0529), b2 = F(0.3334);
+    const F A = F(0.0311), B = F(-0.048), C = F(0.0020), D = F(-0.0116);
+    F t;
+    if constexpr (sizeof(F) == 4) t = cbrtf(F(3.0 / PI) * rho);
+    else t = cbrt(F(3.0 / PI) * rho);
+    const F ex = F(-0.75) * t, vx = -t;
+    const F rs = F(K_RS) / t;
+    F ec, vc;
+    if (rs >= F(1)) {
+        F sq;
+        if constexpr (sizeof(F) == 4) sq = sqrtf(rs);
+        else sq = sqrt(rs);
+        const F den = F(1) + b1 * sq + b2 * rs;
         ec = g / den;
-        vc = ec * (1.0 + (7.0 / 6.0) * b1 * sq + (4.0 / 3.0) * b2 * rs) / den;
+        vc = ec * (F(1) + F(7.0 / 6.0) * b1 * sq + F(4.0 / 3.0) * b2 * rs) / den;
     } else {
-        double lr = log(rs);
+        F lr;
+        if constexpr (sizeof(F) == 4) lr = logf(rs);
+        else lr = log(rs);
         ec = A * lr + B + C * rs * lr + D * rs;
-        vc = A * lr + (B - A / 3.0) + (2.0 / 3.0) * C * rs * lr + (2.0 * D - C) / 3.0 * rs;
+        vc = A * lr + (B - A / F(3)) + F(2.0 / 3.0) * C * rs * lr + (F(2) * D - C) / F(3) * rs;
     }
     vxc = vx + vc;
     return ex + ec;
@@ -157,6 +170,31 @@ __global__ void k_boundary(int nb, const int *__restrict__ bnd, const double *__
         v += 0.5 * qq / (r2 * r2 * r);
     }
     U[bnd[k]] = v;
+}
+
+// CG start after a residual r = rhs - L U from the lattice-stencil kernel (which leaves the
+// Dirichlet rows unwritten): r = 0 there, z = p = minv r, and rz, rr, |rhs|^2 as k_cg_init
+__global__ void __launch_bounds__(256) k_cg_init_vec(int64_t N, const double *__restrict__ minv,
+                                                     const double *__restrict__ rhs, double *r, double *z,
+                                                     double *pv, double *sc) {
+    __shared__ double sh[8];
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double rz = 0.0, rr = 0.0, bb = 0.0;
+    if (i < N) {
+        const double mi = minv[i];
+        const double ri = mi != 0.0 ? r[i] : 0.0, zi = mi * ri;
+        if (mi != 0.0) bb = rhs[i] * rhs[i];
+        r[i] = ri; z[i] = zi; pv[i] = zi;
+        rz = ri * zi; rr = ri * ri;
+    }
+    rz = block_sum(rz, sh);
+    rr = block_sum(rr, sh);
+    bb = block_sum(bb, sh);
+    if (threadIdx.x == 0) {
+        atomicAdd(sc + 0, rz);
+        atomicAdd(sc + 4, rr);
+        atomicAdd(sc + 6, bb);
+    }
 }
 
 // Poisson CG on the interior nodes with the full-node CSR stiffness; boundary entries of
@@ -340,7 +378,15 @@ __global__ void __launch_bounds__(128) k_potential(int64_t T, const int *__restr
             if (do_h)
                 for (int a = 0; a < 10; ++a) h += p2N(q, a) * U[tetn[t * 10 + a]];
             double r = rho[t * 4 + q], vx = 0.0, ex = 0.0;
-            if (do_xc) ex = lda(r, vx);
+            if (do_xc) {
+                if constexpr (sizeof(E) == 4) {
+                    float vf;
+                    ex = (double)lda<float>((float)r, vf);
+                    vx = (double)vf;
+                } else {
+                    ex = lda<double>(r, vx);
+                }
+            }
             vh[t * 4 + q] = h; vxc[t * 4 + q] = vx; exc[t * 4 + q] = ex;
             V[q] = w * (vext[t * 4 + q] + h + vx);
             e += w * (0.5 * h + vx - ex) * r;
@@ -424,8 +470,13 @@ int run_hartree(ofks_ctx *c) {
                                                                c->d_sc + SC_MOM, c->prm.multipole_lmax,
                                                                c->d_U);
     cudaMemsetAsync(sc, 0, sizeof(double) * 8, c->stream);
-    k_cg_init<<<gN, 256, 0, c->stream>>>(N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv, c->d_rhs, c->d_U,
-                                         c->d_cr, c->d_cz, c->d_cp, sc);
+    if (c->st.on && !c->prm.poisson_csr) {   // the lattice-stencil residual, then the CG start
+        launch_stencil_residual(c, c->d_U, c->d_rhs, c->d_cr);
+        k_cg_init_vec<<<gN, 256, 0, c->stream>>>(N, c->d_minv, c->d_rhs, c->d_cr, c->d_cz, c->d_cp, sc);
+    } else {
+        k_cg_init<<<gN, 256, 0, c->stream>>>(N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv, c->d_rhs, c->d_U,
+                                             c->d_cr, c->d_cz, c->d_cp, sc);
+    }
     c->kernels += 2;
     const int pc = hartree_pc(c);
     const bool amg = pc != OFKS_HPC_JACOBI;             // a preconditioner other than the diagonal

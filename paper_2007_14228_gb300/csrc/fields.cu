@@ -58,26 +58,22 @@ __device__ __forceinline__ F lda(F rho, F &vxc) {
 // j of the group covers columns j, j+G, ...:  psi_{q,l} = sum_a N_a(x_q) X_{a,l},
 // rho_q = f sum_l psi_{q,l}^2 (group xor-reduction).  The per-tetrahedron epilogue is spread
 // over the group's lanes (float64 warp instructions cost the same with one active lane):
-// lane k writes rho_k (k < 4), adds the Poisson load 4 pi w sum_q N_k(x_q) rho_q of local
-// node k (k < 10) and accumulates multipole moment k (k < 10) over all its tetrahedra.
+// lane k writes rho_k (k < 4) and adds the Poisson load 4 pi w sum_q N_k(x_q) rho_q of local
+// node k (k < 10).  The multipole moments follow from the assembled load (k_moments).
 template <class E, int G>
 __global__ void __launch_bounds__(256) k_density(int64_t T, int p, int ld, double occ,
                                                  const E *__restrict__ X,
                                                  const int *__restrict__ tetf,
                                                  const int *__restrict__ tetn,
-                                                 const double *__restrict__ wq,
-                                                 const double *__restrict__ yq, double *rho,
-                                                 double *rhs, double *mom, int do_hartree) {
+                                                 const double *__restrict__ wq, double *rho,
+                                                 double *rhs, int do_hartree) {
     constexpr int TPW = 32 / G;                       // tetrahedra per warp and pass
-    __shared__ double smom[10];
     __shared__ double sN[4][10];
     if (threadIdx.x < 40) sN[threadIdx.x / 10][threadIdx.x % 10] = p2N(threadIdx.x / 10, threadIdx.x % 10);
-    if (threadIdx.x < 10) smom[threadIdx.x] = 0.0;
     __syncthreads();
     const int lane = threadIdx.x & (G - 1), grp = (threadIdx.x & 31) / G;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    double m[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t t0 = warp * TPW; t0 < T; t0 += nwarp * TPW) {
         const int64_t t = t0 + grp;
         const bool ok = t < T;
@@ -116,42 +112,44 @@ __global__ void __launch_bounds__(256) k_density(int64_t T, int p, int ld, doubl
             for (int q = 0; q < 4; ++q) v = fma(sN[q][k], s[q], v);
             atomicAdd(rhs + tetn[t * 10 + k], (4.0 * 3.14159265358979323846 * occ) * w * v);
         }
-        for (int k = lane; k < 10; k += G) {
-            double acc = 0.0;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const double *y = yq + (t * 4 + q) * 3;
-                const double y0 = y[0], y1 = y[1], y2 = y[2];
-                const double y2s = y0 * y0 + y1 * y1 + y2 * y2;
-                double f;
-                switch (k) {
-                    case 0: f = 1.0; break;
-                    case 1: f = y0; break;
-                    case 2: f = y1; break;
-                    case 3: f = y2; break;
-                    case 4: f = 3.0 * y0 * y0 - y2s; break;
-                    case 5: f = 3.0 * y1 * y1 - y2s; break;
-                    case 6: f = 3.0 * y2 * y2 - y2s; break;
-                    case 7: f = 3.0 * y0 * y1; break;
-                    case 8: f = 3.0 * y0 * y2; break;
-                    default: f = 3.0 * y1 * y2; break;
-                }
-                acc = fma(s[q], f, acc);
-            }
-            m[k] = fma(occ * w, acc, m[k]);
-        }
     }
-    if (do_hartree) {
-        // lane k of every group holds moments k, k+G, ...: sum over the warp's groups, then the block
-#pragma unroll
-        for (int i = 0; i < 10; ++i)
-#pragma unroll
-            for (int o = 16; o >= G; o >>= 1) m[i] += __shfl_xor_sync(0xffffffffu, m[i], o);
-        if (grp == 0)
-            for (int k = lane; k < 10; k += G) atomicAdd(smom + k, m[k]);
-        __syncthreads();
-        if (threadIdx.x < 10) atomicAdd(mom + threadIdx.x, smom[threadIdx.x]);
+}
+
+// Multipole moments of the density about the centre (Sec. 2.2 boundary data): for each of
+// f = 1, y_0, y_1, y_2, 3 y_0^2 - |y|^2, 3 y_1^2 - |y|^2, 3 y_2^2 - |y|^2, 3 y_0 y_1, 3 y_0 y_2,
+// 3 y_1 y_2, mom_k = sum_T w_T sum_q rho_q f_k(y_q).  Every f_k is quadratic and the P2 basis on
+// a straight-sided tetrahedron interpolates quadratics exactly (sum_i f_k(y_i) N_i(x) = f_k(x),
+// y_i the node positions), so mom_k = sum_i f_k(y_i) rhs_i / (4 pi) with the assembled Poisson
+// load rhs_i = 4 pi sum_T w_T sum_q N_i(x_q) rho_q: one pass over the nodes instead of ten
+// functions at every quadrature point.
+__global__ void __launch_bounds__(256) k_moments(int64_t N, const double *__restrict__ ynode,
+                                                 const double *__restrict__ rhs, double *mom) {
+    __shared__ double smom[10];
+    if (threadIdx.x < 10) smom[threadIdx.x] = 0.0;
+    __syncthreads();
+    double m[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double r = rhs[i] * (1.0 / (4.0 * PI));
+        const double y0 = ynode[3 * i], y1 = ynode[3 * i + 1], y2 = ynode[3 * i + 2];
+        const double y2s = y0 * y0 + y1 * y1 + y2 * y2;
+        m[0] += r;
+        m[1] = fma(r, y0, m[1]);
+        m[2] = fma(r, y1, m[2]);
+        m[3] = fma(r, y2, m[3]);
+        m[4] = fma(r, 3.0 * y0 * y0 - y2s, m[4]);
+        m[5] = fma(r, 3.0 * y1 * y1 - y2s, m[5]);
+        m[6] = fma(r, 3.0 * y2 * y2 - y2s, m[6]);
+        m[7] = fma(r, 3.0 * y0 * y1, m[7]);
+        m[8] = fma(r, 3.0 * y0 * y2, m[8]);
+        m[9] = fma(r, 3.0 * y1 * y2, m[9]);
     }
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        const double v = warp_sum(m[k]);
+        if ((threadIdx.x & 31) == 0) atomicAdd(smom + k, v);
+    }
+    __syncthreads();
+    if (threadIdx.x < 10) atomicAdd(mom + threadIdx.x, smom[threadIdx.x]);
 }
 
 // Multipole boundary values V_B(r) = Q/|r| + d.r/|r|^3 + (1/2) sum Q_ij r_i r_j/|r|^5
@@ -433,7 +431,7 @@ int launch_density(ofks_ctx *c, const E *X) {
     const int64_t warps = (T + 32 / G - 1) / (32 / G);
     unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((warps * 32 + B - 1) / B, 152LL * 16));
 #define DENS(g) k_density<E, g><<<grid, B, 0, c->stream>>>(T, c->p, c->ld, c->prm.occ, X, c->d_tetf, \
-        c->d_tetn, c->d_wq, c->d_yq, c->d_rho, c->d_rhs, c->d_sc + SC_MOM, do_h)
+        c->d_tetn, c->d_wq, c->d_rho, c->d_rhs, do_h)
     switch (G) {
         case 1: DENS(1); break;
         case 2: DENS(2); break;
@@ -444,6 +442,12 @@ int launch_density(ofks_ctx *c, const E *X) {
     }
 #undef DENS
     c->kernels += 1;
+    if (do_h) {
+        const int64_t N = c->n_nodes;
+        const unsigned gm = (unsigned)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 152LL * 4));
+        k_moments<<<gm, 256, 0, c->stream>>>(N, c->d_ynode, c->d_rhs, c->d_sc + SC_MOM);
+        c->kernels += 1;
+    }
     return ofks_cuda_check(c, cudaGetLastError(), "density kernel");
 }
 

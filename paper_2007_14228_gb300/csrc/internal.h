@@ -149,6 +149,8 @@ struct ofks_ctx {
     int n_bnd = 0;
     int *d_bnd = nullptr;                        // boundary node ids
     double *d_bxyz = nullptr;                    // n_bnd x 3 boundary node coords minus centre
+    double *d_ynode = nullptr;                   // N x 3 node positions minus centre (edge nodes at the
+                                                 // midpoints of their edges): the multipole moments
     double center[3] = {0, 0, 0};
     std::vector<AmgLevel> amg;                   // Hartree preconditioner (empty: Jacobi)
     int *d_amg_idx = nullptr;                    // interior node ids (level 0 numbering)

@@ -193,7 +193,7 @@ void free_mesh(ofks_ctx *c) {
     dev_free(c->d_valL); dev_free(c->d_valB); dev_free(c->d_valH); dev_free(c->d_dL); dev_free(c->d_dB);
     dev_free(c->d_fptr); dev_free(c->d_fcol); dev_free(c->d_fval); dev_free(c->d_minv);
     dev_free(c->d_tetf); dev_free(c->d_tetn); dev_free(c->d_emap); dev_free(c->d_wq); dev_free(c->d_yq);
-    dev_free(c->d_vext); dev_free(c->d_bnd); dev_free(c->d_bxyz);
+    dev_free(c->d_vext); dev_free(c->d_bnd); dev_free(c->d_bxyz); dev_free(c->d_ynode);
     dev_free(c->d_rho); dev_free(c->d_vh); dev_free(c->d_vxc); dev_free(c->d_exc);
     dev_free(c->d_U); dev_free(c->d_rhs); dev_free(c->d_cr); dev_free(c->d_cz); dev_free(c->d_cp);
     dev_free(c->d_cq);
@@ -368,6 +368,17 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
     std::vector<double> bxyz(bnd.size() * 3);
     for (size_t k = 0; k < bnd.size(); ++k)
         for (int d = 0; d < 3; ++d) bxyz[k * 3 + d] = xyz[(int64_t)bnd[k] * 3 + d] - c->center[d];
+    // node positions for the moments: the affine (straight-sided) P2 node of each edge is its midpoint
+    std::vector<double> ynode((size_t)N * 3);
+    for (int64_t i = 0; i < N; ++i)
+        for (int d = 0; d < 3; ++d) ynode[i * 3 + d] = xyz[i * 3 + d] - c->center[d];
+    for (int64_t t = 0; t < T; ++t)
+        for (int e = 0; e < 6; ++e) {
+            int a, b;
+            p2_edge(e, a, b);
+            const int64_t va = tetn[t * 10 + a], vb = tetn[t * 10 + b], m = tetn[t * 10 + 4 + e];
+            for (int d = 0; d < 3; ++d) ynode[m * 3 + d] = 0.5 * (xyz[va * 3 + d] + xyz[vb * 3 + d]) - c->center[d];
+        }
 
     // ---- device
     int rc;
@@ -394,6 +405,7 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
         (rc = dev_zeros(c, &c->d_vext, T * 4)) ||
         (rc = dev_upload(c, &c->d_bnd, bnd.data(), bnd.size())) ||
         (rc = dev_upload(c, &c->d_bxyz, bxyz.data(), bxyz.size())) ||
+        (rc = dev_upload(c, &c->d_ynode, ynode.data(), ynode.size())) ||
         (rc = dev_zeros(c, &c->d_rho, T * 4)) || (rc = dev_zeros(c, &c->d_vh, T * 4)) ||
         (rc = dev_zeros(c, &c->d_vxc, T * 4)) || (rc = dev_zeros(c, &c->d_exc, T * 4)) ||
         (rc = dev_zeros(c, &c->d_U, N)) || (rc = dev_zeros(c, &c->d_rhs, N)) ||

@@ -104,3 +104,29 @@ def test_cg_path_matches_direct_solve():
     Ud = Hartree(m.xyz, m.tet10, m.dirichlet, L, vol, xq, 2, solver="direct").solve(rho)
     Uc = Hartree(m.xyz, m.tet10, m.dirichlet, L, vol, xq, 2, solver="cg").solve(rho)
     assert np.max(np.abs(Ud - Uc)) < 1e-10 * np.max(np.abs(Ud))
+
+
+def test_moments_equal_the_node_sum_over_the_load():
+    # Every multipole moment function (1, y, 3 y_i y_j - |y|^2 delta_ij) is quadratic and P2 on a
+    # straight-sided tetrahedron interpolates quadratics exactly, so the quadrature moments equal
+    # sum_i f(y_i) b_i with the load b_i = sum_T sum_q w_q rho_q N_i(x_q): the identity the GPU
+    # uses to get the moments from the assembled Poisson load (one pass over the nodes)
+    s = I.chain(cells=(26, 14, 8))
+    m = I.make_mesh(s)
+    L, _ = fem.assemble_LB(m.xyz, m.tet10)
+    vol, _ = fem.tet_geometry(m.xyz, m.tet10)
+    xq = fem.quad_points(m.xyz, m.tet10)
+    h = Hartree(m.xyz, m.tet10, m.dirichlet, L, vol, xq, 2)
+    rho = np.random.default_rng(5).uniform(0.0, 2.0, (m.tet10.shape[0], 4))
+    Q, d, Qij = h.moments(rho)
+    b = fem.quad_to_nodes(rho, m.tet10, vol, m.xyz.shape[0])
+    y = m.xyz - h.center
+    r2 = (y * y).sum(axis=1)
+    Qn, dn = b.sum(), (b[:, None] * y).sum(axis=0)
+    Qijn = 3.0 * np.einsum("i,ij,ik->jk", b, y, y) - np.eye(3) * (b * r2).sum()
+    assert abs(Qn - Q) <= 1e-12 * abs(Q)
+    scale = np.sqrt((y * y).sum(axis=1)).max()
+    assert np.max(np.abs(dn - d)) <= 1e-12 * abs(Q) * scale
+    assert np.max(np.abs(Qijn - Qij)) <= 1e-12 * abs(Q) * scale ** 2
+    # a dropped or wrong-signed term of the identity breaks it: the moments of a shifted origin differ
+    assert np.max(np.abs(3.0 * np.einsum("i,ij,ik->jk", b, y + 0.1, y + 0.1) - np.eye(3) * (b * ((y + 0.1) ** 2).sum(axis=1)).sum() - Qij)) > 1e-6 * abs(Q)

@@ -100,7 +100,8 @@ static void free_blocks(ofks_ctx *c) {
 
 template <class T>
 static int alloc_set(ofks_ctx *c, Blocks<T> &b, int ld, bool values) {
-    const size_t blk = sizeof(T) * (size_t)c->n * ld;
+    // rows: n, or the float32 PCG's row stride (n rounded up to 32) when larger
+    const size_t blk = sizeof(T) * (size_t)std::max<int64_t>(c->n, c->n_slots) * ld;
     T **bl[] = {&b.X[0], &b.X[1], &b.D[0], &b.D[1], &b.G[0], &b.G[1], &b.HX, &b.BX, &b.R, &b.Z, &b.P, &b.Q, &b.W,
                 &b.Dc};
     for (T **q : bl) {
@@ -291,16 +292,26 @@ static int precondition_t(ofks_ctx *c) {
         // the PCG on the active columns only, gathered into a block of width w (the columns are
         // independent systems, so the others' work would only be discarded)
         const int w = nact <= 2 ? nact : (nact + 3) / 4 * 4;
-        if (!learned && c->prm.pcg_compact && w < ld) {
+        const bool compact = !learned && c->prm.pcg_compact && w < ld;
+        const bool slots = pcg_zc<T>(c, compact ? w : ld);   // float32 blocks chunk-major
+        if (compact || slots) {
             std::vector<int> h(2 * (size_t)ld, -1);            // cmap | cpos
-            for (int j = 0, k = 0; j < c->p; ++j)
-                if (act0[j] != 0.0) { h[k] = j; h[ld + j] = k; ++k; }
+            if (compact) {
+                for (int j = 0, k = 0; j < c->p; ++j)
+                    if (act0[j] != 0.0) { h[k] = j; h[ld + j] = k; ++k; }
+            } else {                                          // all columns; inactive ones take G
+                for (int j = 0; j < ld; ++j) h[j] = j;
+                for (int j = 0; j < c->p; ++j) h[ld + j] = act0[j] != 0.0 ? j : -1;
+            }
             cudaError_t e = cudaMemcpyAsync(c->d_cmap, h.data(), sizeof(int) * 2 * ld, cudaMemcpyHostToDevice,
                                             c->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // h leaves scope
             if (e != cudaSuccess) return ofks_cuda_check(c, e, "preconditioner");
-            launch_pcg_compact_cols(c, w, nact, c->d_cmap, c->d_colC);
-            v.w = w; v.pc = nact; v.cb = c->d_colC; v.cmap = c->d_cmap; v.cpos = c->d_cmap + ld; v.D = b.Dc;
+            if (compact) {
+                launch_pcg_compact_cols(c, w, nact, c->d_cmap, c->d_colC);
+                v.w = w; v.pc = nact; v.cb = c->d_colC;
+            }
+            v.cmap = c->d_cmap; v.cpos = c->d_cmap + ld; v.D = b.Dc;
         }
     }
     bool run_pcg = true, warm = false;
@@ -341,7 +352,7 @@ static int precondition_t(ofks_ctx *c) {
     }
     if (run_pcg) {
         ProfScope ps(c, PF_PCG_UPDATE);
-        if (warm) launch_pcg_init_warm(c, b);
+        if (warm) launch_pcg_init_warm(c, b, v);
         else launch_pcg_init(c, b, v);
         cudaMemsetAsync(v.cb + CB_PQ * v.w, 0, sizeof(double) * v.w, c->stream);
     }
@@ -365,7 +376,7 @@ static int precondition_t(ofks_ctx *c) {
         {
             ProfScope ps(c, PF_PCG_UPDATE);
             launch_pcg_alpha(c, w, v.cb);
-            launch_pcg_update(c, b, v);
+            launch_pcg_update(c, b, v, !exact && it + 1 == max_it);
             launch_pcg_beta(c, w, v.cb);
         }
         if (exact && (it + 1) % 25 == 0) {
@@ -379,7 +390,9 @@ static int precondition_t(ofks_ctx *c) {
     }
     {
         ProfScope ps(c, PF_PCG_UPDATE);
-        if (v.cpos) launch_direction_expand(c, b, v);
+        // a PCG that ran into Dc comes back through the column map; without a PCG (every column
+        // of the learned mode accepted) D holds the network's directions and the T = I columns take G
+        if (v.cpos && run_pcg) launch_direction_expand(c, b, v);
         else launch_direction_select(c, b);
     }
     return ofks_cuda_check(c, cudaGetLastError(), "preconditioner");

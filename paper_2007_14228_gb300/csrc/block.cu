@@ -354,10 +354,10 @@ __device__ __forceinline__ void col_reduce(double acc, int j, bool active, int l
         if (sh[k] != 0.0) atomicAdd(colsum + k, sh[k]);
 }
 
-// index of element (r, j) of Z: row-major, or chunk-major ((j / 4) n + r) 4 + j % 4 (zc)
-__device__ __forceinline__ int64_t zidx(int zc, int64_t e, int64_t r, int j, int64_t n) {
-    return zc ? (((int64_t)(j >> 2) * n + r) << 2) + (j & 3) : e;
-}
+// element (r, k) of a chunk-major float32 PCG block with row stride ns (n rounded up to 32):
+// ((k / 4) ns + r) 4 + k % 4, so the four columns of a chunk of one row are one 16-byte piece and
+// consecutive rows are consecutive pieces
+__device__ __forceinline__ int64_t sidx(int64_t r, int k, int64_t ns) { return (((int64_t)(k >> 2) * ns + r) << 2) + (k & 3); }
 
 // PCG start: W = 1/diag with diag = dL/2 - shift_c dB, D = 0, R = G, Z = G W, rz[c] = sum R Z.
 // The PCG block has width ld; with cmap its column c < p is column cmap[c] of G (row pitch ldg),
@@ -367,14 +367,14 @@ __global__ void __launch_bounds__(256) k_pcg_init(int64_t n, int p, int ld, int6
                                                   const T *__restrict__ G, int ldg, const int *__restrict__ cmap,
                                                   const double *__restrict__ dL,
                                                   const double *__restrict__ dB, const double *cb,
-                                                  T *W, T *D, T *R, T *Z, double *rz, int zc) {
+                                                  T *W, T *D, T *R, T *Z, double *rz) {
     T acc = T(0);
     ELEM_BEGIN
         const T sh = (T)cb[CB_SHIFT * ld + j];
         const T w = T(1) / (T(0.5) * (T)dL[r] - sh * (T)dB[r]);
         const T gv = cmap ? (j < p ? G[r * ldg + cmap[j]] : T(0)) : G[e];
         const T z = gv * w;
-        W[e] = w; D[e] = T(0); R[e] = gv; Z[zidx(zc, e, r, j, n)] = z;
+        W[e] = w; D[e] = T(0); R[e] = gv; Z[e] = z;
         acc = fma(gv, z, acc);
     ELEM_END
     col_reduce((double)acc, j, gid < stride, ld, p, rz);
@@ -403,14 +403,14 @@ __global__ void __launch_bounds__(256) k_pcg_init_warm(int64_t n, int p, int ld,
                                                        const T *__restrict__ G, const T *__restrict__ Q,
                                                        const double *__restrict__ dL,
                                                        const double *__restrict__ dB, const double *cb,
-                                                       T *W, T *R, T *Z, double *rz, int zc) {
+                                                       T *W, T *R, T *Z, double *rz) {
     T acc = T(0);
     ELEM_BEGIN
         const T sh = (T)cb[CB_SHIFT * ld + j];
         const T w = T(1) / (T(0.5) * (T)dL[r] - sh * (T)dB[r]);
         const T rv = G[e] - Q[e];
         const T z = rv * w;
-        W[e] = w; R[e] = rv; Z[zidx(zc, e, r, j, n)] = z;
+        W[e] = w; R[e] = rv; Z[e] = z;
         acc = fma(rv, z, acc);
     ELEM_END
     col_reduce((double)acc, j, gid < stride, ld, p, rz);
@@ -422,61 +422,130 @@ __global__ void __launch_bounds__(256) k_pcg_update(int64_t n, int p, int ld, in
                                                     const T *__restrict__ W,
                                                     const T *__restrict__ P,
                                                     const T *__restrict__ Q, T *D, T *R,
-                                                    T *Z, double *rzn, int zc) {
+                                                    T *Z, double *rzn) {
     T acc = T(0);
     const T al = (T)cb[CB_ALPHA * ld + (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) % ld];
     ELEM_BEGIN
         D[e] = fma(al, P[e], D[e]);
         const T rv = fma(-al, Q[e], R[e]);
         const T z = rv * W[e];
-        R[e] = rv; Z[zidx(zc, e, r, j, n)] = z;
+        R[e] = rv; Z[e] = z;
         acc = fma(rv, z, acc);
     ELEM_END
     col_reduce((double)acc, j, gid < stride, ld, p, rzn);
 }
 
-// k_pcg_update for float32 with Z chunk-major: 32-row tiles are read and written row-major
-// (coalesced) and the tile's Z goes through shared memory, so each 4-column chunk of it is
-// written as one contiguous 512-byte run instead of 16-byte pieces scattered over the chunks.
-// The column sums r.z collect in shared memory and leave once per block.
-constexpr int UZ_ROWS = 32;
-
-__global__ void __launch_bounds__(256) k_pcg_update_zc(int64_t n, int p, int ld, const double *cb,
-                                                       const float *__restrict__ W, const float *__restrict__ P,
-                                                       const float *__restrict__ Q, float *D, float *R, float *Zc,
-                                                       double *rzn) {
-    extern __shared__ __align__(16) float uzs[];
-    float *zt = uzs;                             // UZ_ROWS x ld
-    float *al = zt + UZ_ROWS * ld;               // ld
-    float *cs = al + ld;                         // ld
-    for (int j = threadIdx.x; j < ld; j += blockDim.x) { al[j] = (float)cb[CB_ALPHA * ld + j]; cs[j] = 0.f; }
-    __syncthreads();
-    const int nch = ld >> 2;
-    for (int64_t r0 = (int64_t)blockIdx.x * UZ_ROWS; r0 < n; r0 += (int64_t)gridDim.x * UZ_ROWS) {
-        const int rows = (int)(n - r0 < UZ_ROWS ? n - r0 : UZ_ROWS);
-        const int64_t b0 = r0 * ld;
-        for (int e = threadIdx.x; e < rows * ld; e += blockDim.x) {
-            const int j = e % ld;
-            const float a = al[j];
-            const int64_t g = b0 + e;
-            D[g] = fmaf(a, P[g], D[g]);
-            const float rv = fmaf(-a, Q[g], R[g]);
-            const float z = rv * W[g];
-            R[g] = rv;
-            zt[e] = z;
-            atomicAdd(cs + j, rv * z);
-        }
-        __syncthreads();
-        // chunk q of row i: 16 bytes at ((q n) + r0 + i) 4 of Zc
-        for (int e = threadIdx.x; e < nch * rows; e += blockDim.x) {
-            const int q = e / rows, i = e - q * rows;
-            const float4 v = *reinterpret_cast<const float4 *>(zt + i * ld + 4 * q);
-            *reinterpret_cast<float4 *>(Zc + (((int64_t)q * n + r0 + i) << 2)) = v;
-        }
-        __syncthreads();
+// ---- float32 PCG blocks chunk-major (W, R, Z, P, Q and its D, all sidx-indexed)
+//
+// Start: rows n <= r < ns are padding and stay zero; compact column k < pc is column cmap[k] of G
+// (row-major, pitch ld); the other columns are zero.  W = 1/diag with diag = dL/2 - shift_k dB;
+// R = G (minus Q, the operator applied to the network's D, when warm); Z = W R; D = 0 (or the
+// network's D when warm); rz[k] += R Z.  Each thread takes (row, 4-column chunk) items in a
+// grid-stride loop: consecutive threads take consecutive rows of one chunk, so every write is one
+// float4 of a contiguous run; a warp never spans two chunks (ns is a multiple of 32).
+// Column sums go warp -> shared memory -> one float64 atomic per column and block (same-address
+// atomics from every warp would serialise).
+__device__ __forceinline__ void flush_cols(const float (&acc)[4], int q, int pc, float *cs) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float t = warp_sum_f(acc[i]);
+        if ((threadIdx.x & 31) == 0 && 4 * q + i < pc) atomicAdd(cs + 4 * q + i, t);
     }
-    for (int j = threadIdx.x; j < ld && j < p; j += blockDim.x)
-        if (cs[j] != 0.f) atomicAdd(rzn + j, (double)cs[j]);
+}
+
+__global__ void __launch_bounds__(256) k_pcg_init_s(int64_t n, int64_t ns, int pc, int w,
+                                                    const float *__restrict__ G, const float *__restrict__ Qn,
+                                                    const float *__restrict__ Dn, int ld, const int *__restrict__ cmap,
+                                                    const double *__restrict__ dL, const double *__restrict__ dB,
+                                                    const double *__restrict__ cb, float *W, float *D, float *R,
+                                                    float *Z, double *rz) {
+    __shared__ float cs[MAXLD];
+    for (int k = threadIdx.x; k < w; k += blockDim.x) cs[k] = 0.f;
+    __syncthreads();
+    const int64_t total = ns * (w >> 2);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;    // a multiple of 32
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx - (threadIdx.x & 31) < total;
+         idx += stride) {
+        // the warp's first item decides for the whole warp (total is a multiple of 32)
+        const int q = (int)(idx / ns);
+        const int64_t r = idx - (int64_t)q * ns;
+        const int64_t nat = r < n ? r : -1;
+        float wv[4], rv[4], zv[4], dv[4], acc[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = 4 * q + i;
+            const int col = k < pc ? cmap[k] : -1;
+            float g = 0.f, d = 0.f, ww = 0.f;
+            if (nat >= 0) {
+                const float sh = (float)cb[CB_SHIFT * w + k];
+                ww = 1.f / (0.5f * (float)dL[nat] - sh * (float)dB[nat]);
+                if (col >= 0) {
+                    const int64_t e = nat * ld + col;
+                    g = G[e];
+                    if (Qn) g -= Qn[e];
+                    if (Dn) d = Dn[e];
+                }
+            }
+            wv[i] = ww; rv[i] = g; zv[i] = g * ww; dv[i] = d;
+            acc[i] = g * zv[i];
+        }
+        const int64_t o = idx << 2;                  // sidx(r, 4 q, ns)
+        *reinterpret_cast<float4 *>(W + o) = make_float4(wv[0], wv[1], wv[2], wv[3]);
+        *reinterpret_cast<float4 *>(R + o) = make_float4(rv[0], rv[1], rv[2], rv[3]);
+        *reinterpret_cast<float4 *>(Z + o) = make_float4(zv[0], zv[1], zv[2], zv[3]);
+        *reinterpret_cast<float4 *>(D + o) = make_float4(dv[0], dv[1], dv[2], dv[3]);
+        flush_cols(acc, q, pc, cs);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < w && k < pc; k += blockDim.x)
+        if (cs[k] != 0.f) atomicAdd(rz + k, (double)cs[k]);
+}
+
+// alpha = rz/pq; D += alpha P; R -= alpha Q; Z = R W; rzn += R Z, per float4 of one row and
+// chunk.  On the last iteration only D is needed (last = 1: R, Z and rzn are left alone).
+__global__ void __launch_bounds__(256) k_pcg_update_s(int64_t ns, int pc, int w, const double *__restrict__ cb,
+                                                      const float *__restrict__ W, const float *__restrict__ P,
+                                                      const float *__restrict__ Q, float *D, float *R, float *Z,
+                                                      double *rzn, int last) {
+    __shared__ float cs[MAXLD], al[MAXLD];
+    for (int k = threadIdx.x; k < w; k += blockDim.x) { cs[k] = 0.f; al[k] = (float)cb[CB_ALPHA * w + k]; }
+    __syncthreads();
+    const int64_t total = ns * (w >> 2);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx - (threadIdx.x & 31) < total;
+         idx += stride) {
+        const int q = (int)(idx / ns);
+        const int64_t o = idx << 2;                  // sidx(r, 4 q, ns) with r = idx - q ns
+        const float a0 = al[4 * q], a1 = al[4 * q + 1], a2 = al[4 * q + 2], a3 = al[4 * q + 3];
+        const float4 p4 = *reinterpret_cast<const float4 *>(P + o);
+        float4 d4 = *reinterpret_cast<const float4 *>(D + o);
+        d4.x = fmaf(a0, p4.x, d4.x); d4.y = fmaf(a1, p4.y, d4.y); d4.z = fmaf(a2, p4.z, d4.z); d4.w = fmaf(a3, p4.w, d4.w);
+        *reinterpret_cast<float4 *>(D + o) = d4;
+        if (last) continue;
+        const float4 q4 = *reinterpret_cast<const float4 *>(Q + o), w4 = *reinterpret_cast<const float4 *>(W + o);
+        float4 r4 = *reinterpret_cast<const float4 *>(R + o);
+        r4.x = fmaf(-a0, q4.x, r4.x); r4.y = fmaf(-a1, q4.y, r4.y); r4.z = fmaf(-a2, q4.z, r4.z); r4.w = fmaf(-a3, q4.w, r4.w);
+        const float4 z4 = make_float4(r4.x * w4.x, r4.y * w4.y, r4.z * w4.z, r4.w * w4.w);
+        *reinterpret_cast<float4 *>(R + o) = r4;
+        *reinterpret_cast<float4 *>(Z + o) = z4;
+        const float acc[4] = {r4.x * z4.x, r4.y * z4.y, r4.z * z4.z, r4.w * z4.w};
+        flush_cols(acc, q, pc, cs);
+    }
+    if (last) return;
+    __syncthreads();
+    for (int k = threadIdx.x; k < w && k < pc; k += blockDim.x)
+        if (cs[k] != 0.f) atomicAdd(rzn + k, (double)cs[k]);
+}
+
+// D (row-major, pitch ld) from the chunk-major PCG result: column j takes compact column cpos[j]
+// of Dc, or G when inactive (cpos[j] < 0: T = I in Eq. precondition-T)
+__global__ void __launch_bounds__(256) k_expand_s(int64_t n, int ld, int64_t stride, int64_t ns,
+                                                  const int *__restrict__ cpos, const float *__restrict__ G,
+                                                  const float *__restrict__ Dc, float *D) {
+    ELEM_BEGIN
+        const int k = cpos[j];
+        D[e] = k >= 0 ? Dc[sidx(r, k, ns)] : G[e];
+    ELEM_END
 }
 
 // D from the compact PCG: column j takes compact column cpos[j] of Dc (width w), or G when
@@ -711,10 +780,18 @@ void launch_pcg_init(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v) {
     c->kernels += 1;
     const int w = v.w;
     cudaMemsetAsync(v.cb + CB_RZ * w, 0, sizeof(double) * w, c->stream);
+    if constexpr (sizeof(T) == 4) {
+        if (pcg_zc<T>(c, w)) {
+            const int64_t total = c->n_slots * (w >> 2);
+            k_pcg_init_s<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8), 256, 0, c->stream>>>(
+                c->n, c->n_slots, v.pc, w, (const float *)b.G[c->cur], nullptr, nullptr, c->ld, v.cmap, c->d_dL,
+                c->d_dB, v.cb, (float *)b.W, (float *)v.D, (float *)b.R, (float *)b.Z, v.cb + CB_RZ * w);
+            return;
+        }
+    }
     const ElemGrid g = elem_grid(c->n, w);
     k_pcg_init<T><<<g.blocks, 256, 0, c->stream>>>(c->n, v.pc, w, g.stride, b.G[c->cur], c->ld, v.cmap, c->d_dL,
-                                                   c->d_dB, v.cb, b.W, v.D, b.R, b.Z, v.cb + CB_RZ * w,
-                                                   pcg_zc<T>(c, w) ? 1 : 0);
+                                                   c->d_dB, v.cb, b.W, v.D, b.R, b.Z, v.cb + CB_RZ * w);
 }
 
 template <class T>
@@ -729,41 +806,57 @@ void launch_judge(ofks_ctx *c, Blocks<T> &b) {
 }
 
 template <class T>
-void launch_pcg_init_warm(ofks_ctx *c, Blocks<T> &b) {
+void launch_pcg_init_warm(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v) {
     c->kernels += 1;
     const int ld = c->ld;
     double *cb = c->d_colA;
     cudaMemsetAsync(cb + CB_RZ * ld, 0, sizeof(double) * ld, c->stream);
+    if constexpr (sizeof(T) == 4) {
+        if (pcg_zc<T>(c, v.w)) {                 // Q = T D and the network's D are natural row-major
+            const int64_t total = c->n_slots * (v.w >> 2);
+            k_pcg_init_s<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8), 256, 0, c->stream>>>(
+                c->n, c->n_slots, v.pc, v.w, (const float *)b.G[c->cur], (const float *)b.Q,
+                (const float *)b.D[c->cur], ld, v.cmap, c->d_dL, c->d_dB, v.cb, (float *)b.W, (float *)v.D,
+                (float *)b.R, (float *)b.Z, v.cb + CB_RZ * v.w);
+            return;
+        }
+    }
     const ElemGrid g = elem_grid(c->n, ld);
     k_pcg_init_warm<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, b.G[c->cur], b.Q, c->d_dL, c->d_dB,
-                                                        cb, b.W, b.R, b.Z, cb + CB_RZ * ld,
-                                                        pcg_zc<T>(c, ld) ? 1 : 0);
+                                                        cb, b.W, b.R, b.Z, cb + CB_RZ * ld);
 }
 
 template <class T>
-void launch_pcg_update(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v) {
+void launch_pcg_update(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v, bool last) {
     c->kernels += 1;
     const int w = v.w;
     double *cb = v.cb;
     if constexpr (sizeof(T) == 4) {
         if (pcg_zc<T>(c, w)) {
-            const size_t sm = sizeof(float) * (UZ_ROWS * w + 2 * w);
-            const unsigned grid = (unsigned)std::min<int64_t>((c->n + UZ_ROWS - 1) / UZ_ROWS, 152 * 8);
-            k_pcg_update_zc<<<grid, 256, sm, c->stream>>>(c->n, v.pc, w, cb, (const float *)b.W, (const float *)b.P,
-                                                          (const float *)b.Q, (float *)v.D, (float *)b.R,
-                                                          (float *)b.Z, cb + CB_RZN * w);
+            const int64_t total = c->n_slots * (w >> 2);
+            k_pcg_update_s<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8), 256, 0, c->stream>>>(
+                c->n_slots, v.pc, w, cb, (const float *)b.W, (const float *)b.P, (const float *)b.Q, (float *)v.D,
+                (float *)b.R, (float *)b.Z, cb + CB_RZN * w, last ? 1 : 0);
             return;
         }
     }
     const ElemGrid g = elem_grid(c->n, w);
     k_pcg_update<T><<<g.blocks, 256, 0, c->stream>>>(c->n, v.pc, w, g.stride, cb, b.W, b.P, b.Q, v.D, b.R,
-                                                     b.Z, cb + CB_RZN * w, pcg_zc<T>(c, w) ? 1 : 0);
+                                                     b.Z, cb + CB_RZN * w);
 }
 
 template <class T>
 void launch_direction_expand(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v) {
     c->kernels += 1;
     const ElemGrid g = elem_grid(c->n, c->ld);
+    if constexpr (sizeof(T) == 4) {
+        if (pcg_zc<T>(c, v.w)) {
+            k_expand_s<<<g.blocks, 256, 0, c->stream>>>(c->n, c->ld, g.stride, c->n_slots, v.cpos,
+                                                        (const float *)b.G[c->cur], (const float *)v.D,
+                                                        (float *)b.D[c->cur]);
+            return;
+        }
+    }
     k_expand<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->ld, g.stride, v.w, v.cpos, b.G[c->cur], v.D, b.D[c->cur]);
 }
 
@@ -849,10 +942,10 @@ void launch_convert(ofks_ctx *c, const S *src, T *dst, int64_t count) {
     template void launch_gram2<T>(ofks_ctx *, const T *, const T *, const T *, double *, double *); \
     template void launch_grad_update<T>(ofks_ctx *, Blocks<T> &);                                    \
     template void launch_pcg_init<T>(ofks_ctx *, Blocks<T> &, const PcgView<T> &);                   \
-    template void launch_pcg_update<T>(ofks_ctx *, Blocks<T> &, const PcgView<T> &);                 \
+    template void launch_pcg_update<T>(ofks_ctx *, Blocks<T> &, const PcgView<T> &, bool);           \
     template void launch_direction_expand<T>(ofks_ctx *, Blocks<T> &, const PcgView<T> &);           \
     template void launch_judge<T>(ofks_ctx *, Blocks<T> &);                                          \
-    template void launch_pcg_init_warm<T>(ofks_ctx *, Blocks<T> &);                                 \
+    template void launch_pcg_init_warm<T>(ofks_ctx *, Blocks<T> &, const PcgView<T> &);             \
     template void launch_direction_select<T>(ofks_ctx *, Blocks<T> &);                               \
     template void launch_bb_dots<T>(ofks_ctx *, Blocks<T> &, bool);                                  \
     template void launch_step_y<T>(ofks_ctx *, Blocks<T> &, T *);                                    \

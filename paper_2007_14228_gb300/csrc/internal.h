@@ -125,11 +125,13 @@ struct ofks_ctx {
     int *d_perm = nullptr;                       // n_slices*32 -> free row id or -1
     int max_slice_w = 0;                         // widest slice (entries per row)
     // type-grouped SELL of L and B (float32 values) for the float32 PCG on lattice meshes: slices
-    // of 32 free rows of one lattice node type, consecutive along the third axis, so neighbour
-    // rows at one offset are two rows apart and the chunk-major Z they gather is nearly contiguous
+    // of 32 free rows of one lattice node type, two lattice steps apart along the third axis, so
+    // the neighbour rows of a slice at one offset are two rows apart
     int n_tslices = 0;
     int64_t tsell_len = 0;
     int *d_tslice_ptr = nullptr, *d_tslice_w = nullptr, *d_tcols = nullptr, *d_tperm = nullptr;
+    // row stride of the float32 PCG's chunk-major blocks: n rounded up to 32 (= 32 n_tslices)
+    int64_t n_slots = 0;
     float *d_tvalL = nullptr, *d_tvalB = nullptr;
     double *d_valL = nullptr, *d_valB = nullptr, *d_valH = nullptr;
     double *d_dL = nullptr, *d_dB = nullptr;     // diagonals of L and B (free)
@@ -291,12 +293,15 @@ struct PcgView {
     const int *cmap = nullptr, *cpos = nullptr;
     T *D = nullptr;
 };
-// float32 PCG blocks keep Z chunk-major (4 columns x n rows per chunk) on lattice meshes
+// float32 PCG blocks (W, R, Z, P, Q and the D they build) chunk-major (4 columns per chunk, row
+// stride n_slots) on lattice meshes with w a multiple of 4; the D of such a PCG is always
+// v.D = Dc and comes back through launch_direction_expand
 template <class T> bool pcg_zc(const ofks_ctx *c, int w);
 template <class T> void launch_pcg_init(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v);
-template <class T> void launch_pcg_update(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v);
+// last: the final iteration, after which only D is read
+template <class T> void launch_pcg_update(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v, bool last);
 template <class T> void launch_judge(ofks_ctx *c, Blocks<T> &b);
-template <class T> void launch_pcg_init_warm(ofks_ctx *c, Blocks<T> &b);
+template <class T> void launch_pcg_init_warm(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v);
 template <class T> void launch_direction_select(ofks_ctx *c, Blocks<T> &b);
 // D = the compact PCG result on the active columns, G on the others
 template <class T> void launch_direction_expand(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v);

@@ -203,7 +203,7 @@ void free_mesh(ofks_ctx *c) {
     sep_free(c);
     dev_free(c->d_tslice_ptr); dev_free(c->d_tslice_w); dev_free(c->d_tcols); dev_free(c->d_tperm);
     dev_free(c->d_tvalL); dev_free(c->d_tvalB);
-    c->n_tslices = 0; c->tsell_len = 0;
+    c->n_tslices = 0; c->n_slots = 0; c->tsell_len = 0;
     c->amg_tried = false;
     std::vector<int>().swap(c->h_tetn);
     std::vector<double>().swap(c->h_xyz);
@@ -505,6 +505,7 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
                 cudaStreamSynchronize(c->stream);
                 dev_free(d_tpos);
                 c->n_tslices = nts;
+                c->n_slots = (int64_t)nts * SELL_C;
                 c->tsell_len = acc2;
                 c->kernels += 1;
             }

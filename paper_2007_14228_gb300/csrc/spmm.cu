@@ -198,16 +198,17 @@ __global__ void __launch_bounds__(256) k_pcg_apply(int64_t nwarps, int nchunks, 
     }
 }
 
-// The float32 PCG apply on the type-grouped SELL with Z chunk-major: element (r, c) of Z at
-// ((c / 4) n + r) 4 + c % 4.  A warp takes spw consecutive slices in turn for one 4-column
-// chunk and adds its column sums pq once at the end.  Within a slice its lanes are 32 rows of
-// one lattice node type two lattice steps apart, so for one entry index their neighbour rows
-// are (mostly) two rows apart too and the 32 16-byte gathers fall in ~8 lines of the chunk's
-// n x 16 B array instead of 32.  (8-column chunks, one 32-byte sector per lane, measured
-// slower: 1.31-1.89 ms against 0.91 ms per launch on the 1.25 M-row chain, with twice the lines
-// per gather and fewer resident warps.)
-__global__ void __launch_bounds__(256) k_pcg_apply_zc(int64_t nwarps, int nchunks, int64_t n_slices, int spw, int p, int ld,
-                                                      int64_t n, const int *__restrict__ slice_ptr,
+// The float32 PCG apply on the type-grouped SELL with every PCG block chunk-major: element
+// (r, c) at ((c / 4) ns + r) 4 + c % 4 (ns = n rounded up to 32).  A warp takes spw consecutive
+// slices in turn for one 4-column chunk and adds its column sums pq once at the end.  Its lanes are
+// 32 rows of one lattice node type two lattice steps apart, so for one entry index their neighbour
+// rows are (mostly) two rows apart too: the 32 16-byte gathers fall in ~8 lines of the chunk's
+// ns x 16 B array, and the rows' 27 neighbourhoods overlap, so most of them hit L1.  The lanes'
+// own P and Q pieces lie in the same ~8 lines.  (Storing the blocks in the slices' own order made
+// the gathers contiguous but spread each neighbourhood over the eight node types' ranges: L1 hits
+// fell from 63 % to 48 % and the launch took 40 % longer.)
+__global__ void __launch_bounds__(256) k_pcg_apply_zc(int64_t nwarps, int nchunks, int64_t n_slices, int spw, int p,
+                                                      int64_t ns, const int *__restrict__ slice_ptr,
                                                       const int *__restrict__ slice_w,
                                                       const int *__restrict__ cols,
                                                       const int *__restrict__ perm,
@@ -223,7 +224,9 @@ __global__ void __launch_bounds__(256) k_pcg_apply_zc(int64_t nwarps, int nchunk
     const int64_t s0 = (wg / nchunks) * spw;
     const int64_t s1 = s0 + spw < n_slices ? s0 + spw : n_slices;
     const int c0 = chunk * 4;
-    const float *Zk = Zc + (int64_t)chunk * n * 4;
+    const int64_t cbase = (int64_t)chunk * ns * 4;
+    const float *Zk = Zc + cbase;
+    float *Pk = P + cbase, *Qk = Q + cbase;
     float sh[4], bt[4];
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
@@ -243,22 +246,26 @@ __global__ void __launch_bounds__(256) k_pcg_apply_zc(int64_t nwarps, int nchunk
             aL[0] = fmaf(vl, x.x, aL[0]); aL[1] = fmaf(vl, x.y, aL[1]); aL[2] = fmaf(vl, x.z, aL[2]); aL[3] = fmaf(vl, x.w, aL[3]);
             aB[0] = fmaf(vb, x.x, aB[0]); aB[1] = fmaf(vb, x.y, aB[1]); aB[2] = fmaf(vb, x.z, aB[2]); aB[3] = fmaf(vb, x.w, aB[3]);
         }
-        if (r >= 0) {
-            const float4 z4 = __ldg(reinterpret_cast<const float4 *>(Zk + (int64_t)r * 4));
-            const float zr[4] = {z4.x, z4.y, z4.z, z4.w};
-            float pr[4], qr[4];
-            if (!first) { load_w<float, 4>(P + (int64_t)r * ld + c0, pr); load_w<float, 4>(Q + (int64_t)r * ld + c0, qr); }
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                const float tz = 0.5f * aL[w] - sh[w] * aB[w];
-                const float pn = first ? zr[w] : fmaf(bt[w], pr[w], zr[w]);
-                const float qn = first ? tz : fmaf(bt[w], qr[w], tz);
-                pr[w] = pn; qr[w] = qn;
-                contrib[w] = fmaf(pn, qn, contrib[w]);
-            }
-            store_w<float, 4>(P + (int64_t)r * ld + c0, pr);
-            store_w<float, 4>(Q + (int64_t)r * ld + c0, qr);
+        if (r < 0) continue;
+        const int64_t o = (int64_t)r * 4;
+        const float4 z4 = __ldg(reinterpret_cast<const float4 *>(Zk + o));
+        const float zr[4] = {z4.x, z4.y, z4.z, z4.w};
+        float pr[4] = {0.f, 0.f, 0.f, 0.f}, qr[4] = {0.f, 0.f, 0.f, 0.f};
+        if (!first) {
+            const float4 p4 = *reinterpret_cast<const float4 *>(Pk + o), q4 = *reinterpret_cast<const float4 *>(Qk + o);
+            pr[0] = p4.x; pr[1] = p4.y; pr[2] = p4.z; pr[3] = p4.w;
+            qr[0] = q4.x; qr[1] = q4.y; qr[2] = q4.z; qr[3] = q4.w;
         }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const float tz = 0.5f * aL[w] - sh[w] * aB[w];
+            const float pn = first ? zr[w] : fmaf(bt[w], pr[w], zr[w]);
+            const float qn = first ? tz : fmaf(bt[w], qr[w], tz);
+            pr[w] = pn; qr[w] = qn;
+            contrib[w] = fmaf(pn, qn, contrib[w]);
+        }
+        *reinterpret_cast<float4 *>(Pk + o) = make_float4(pr[0], pr[1], pr[2], pr[3]);
+        *reinterpret_cast<float4 *>(Qk + o) = make_float4(qr[0], qr[1], qr[2], qr[3]);
     }
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
@@ -453,7 +460,7 @@ void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, i
             const int spw = spw_for((int64_t)c->n_tslices * nch);
             const int64_t nw = (((int64_t)c->n_tslices + spw - 1) / spw) * nch;
             k_pcg_apply_zc<<<(unsigned)((nw * 32 + 255) / 256), 256, 0, c->stream>>>(
-                nw, nch, (int64_t)c->n_tslices, spw, pc, w, c->n, c->d_tslice_ptr, c->d_tslice_w, c->d_tcols,
+                nw, nch, (int64_t)c->n_tslices, spw, pc, c->n_slots, c->d_tslice_ptr, c->d_tslice_w, c->d_tcols,
                 c->d_tperm, c->d_tvalL, c->d_tvalB, (const float *)Zin, (float *)P, (float *)Q, beta_col, shift, pq,
                 first);
             c->kernels += 1;

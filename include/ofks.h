@@ -128,6 +128,10 @@ typedef struct {
                                columns only (Lambda_ii < 0), gathered into a block of their count
                                rounded up to 4; the other columns take D = G (T = I) as always.
                                0: the PCG runs on all ld columns and discards the inactive ones */
+    int32_t cuda_graphs;    /* 1 (default): fixed launch sequences (the fixed-count PCG loop, the Hartree
+                               CG between residual checks) are captured once as CUDA graphs and
+                               replayed; 0: every kernel is launched on its own.  Graphs are not
+                               used while ofks_profile is on */
 } ofks_params;
 
 typedef struct {
@@ -155,7 +159,7 @@ typedef struct {
  * iterations, BB2, eta in [1e-4, 1e8], Hartree and LDA on, multipole_lmax 2,
  * poisson_tol 1e-12, poisson_max_iter 20000, poisson_pc OFKS_HPC_SEPARABLE, mixed_tol 1e-5, poisson_tol_mixed
  * 1e-8, judge_tau 0.5, learned_tc 1, poisson_adaptive 0, poisson_csr 0, gram_tc 1, spmm_f32_rows 0,
- * poisson_sep_tc 1, pcg_compact 1.  p is
+ * poisson_sep_tc 1, pcg_compact 1, cuda_graphs 1.  p is
  * set to 1. */
 void ofks_default_params(ofks_params *prm);
 

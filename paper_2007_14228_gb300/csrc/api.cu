@@ -88,7 +88,47 @@ static void free_set(Blocks<T> &b) {
     dfree(b.valL); dfree(b.valB); dfree(b.valH);
 }
 
+void clear_graphs(ofks_ctx *c) {
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+}
+
+int run_graph(ofks_ctx *c, const std::vector<int64_t> &key, void (*body)(void *), void *arg) {
+    if (c->prof || !c->prm.cuda_graphs) {
+        body(arg);
+        return OFKS_OK;
+    }
+    for (auto &g : c->graphs)
+        if (g.key == key) {
+            c->kernels += g.kernels;
+            return ofks_cuda_check(c, cudaGraphLaunch(g.exec, c->stream), "graph launch");
+        }
+    const int64_t k0 = c->kernels;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        cudaGetLastError();
+        body(arg);
+        return OFKS_OK;
+    }
+    body(arg);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    const int64_t nk = c->kernels - k0;
+    c->kernels = k0;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {                       // nothing of the capture ran: launch directly
+        cudaGetLastError();
+        body(arg);
+        return OFKS_OK;
+    }
+    c->graphs.push_back({key, exec, nk});
+    c->kernels += nk;
+    return ofks_cuda_check(c, cudaGraphLaunch(exec, c->stream), "graph launch");
+}
+
 static void free_blocks(ofks_ctx *c) {
+    clear_graphs(c);
     free_set(c->b64);
     free_set(c->b32);
     dfree(c->d_L0); dfree(c->d_S); dfree(c->d_Lam); dfree(c->d_C); dfree(c->d_colA); dfree(c->d_pp); dfree(c->d_stage);
@@ -366,20 +406,41 @@ static int precondition_t(ofks_ctx *c) {
         cudaMemcpyAsync(act.data(), v.cb + CB_ACTIVE * w, sizeof(double) * w, cudaMemcpyDeviceToHost, c->stream);
         cudaStreamSynchronize(c->stream);
     }
-    for (int it = 0; it < max_it; ++it) {
-        {
-            ProfScope ps(c, PF_PCG_SPMM);
-            launch_pcg_apply(c, vals_L<T>(c), vals_B<T>(c), (const T *)b.Z, pcg_zc<T>(c, w) ? 1 : 0, b.P, b.Q,
-                             v.cb + CB_BETA * w, v.cb + CB_SHIFT * w, v.cb + CB_PQ * w, it == 0 ? 1 : 0, w, v.pc);
-            c->pcg_cols_total += w;
+    // one PCG iteration: T P (with the P, Q updates), alpha, D/R/Z update, beta
+    struct Loop { ofks_ctx *c; Blocks<T> *b; PcgView<T> v; int it0, it1, max_it; bool exact; };
+    auto iterate_pcg = [](void *a) {
+        Loop &L = *static_cast<Loop *>(a);
+        ofks_ctx *c = L.c;
+        Blocks<T> &b = *L.b;
+        const PcgView<T> &v = L.v;
+        const int w = v.w;
+        for (int it = L.it0; it < L.it1; ++it) {
+            {
+                ProfScope ps(c, PF_PCG_SPMM);
+                launch_pcg_apply(c, vals_L<T>(c), vals_B<T>(c), (const T *)b.Z, pcg_zc<T>(c, w) ? 1 : 0, b.P, b.Q,
+                                 v.cb + CB_BETA * w, v.cb + CB_SHIFT * w, v.cb + CB_PQ * w, it == 0 ? 1 : 0, w, v.pc);
+            }
+            {
+                ProfScope ps(c, PF_PCG_UPDATE);
+                launch_pcg_alpha(c, w, v.cb);
+                launch_pcg_update(c, b, v, !L.exact && it + 1 == L.max_it);
+                launch_pcg_beta(c, w, v.cb);
+            }
         }
-        {
-            ProfScope ps(c, PF_PCG_UPDATE);
-            launch_pcg_alpha(c, w, v.cb);
-            launch_pcg_update(c, b, v, !exact && it + 1 == max_it);
-            launch_pcg_beta(c, w, v.cb);
-        }
-        if (exact && (it + 1) % 25 == 0) {
+    };
+    if (!exact && max_it > 0) {                  // the fixed-count loop: one graph per shape
+        Loop L{c, &b, v, 0, max_it, max_it, false};
+        const std::vector<int64_t> key = {1, (int64_t)sizeof(T), w, v.pc, max_it, (int64_t)(uintptr_t)v.cb,
+                                          (int64_t)(uintptr_t)v.D, (int64_t)(uintptr_t)b.Z};
+        int rc;
+        if ((rc = run_graph(c, key, iterate_pcg, &L))) return rc;
+        c->pcg_cols_total += (int64_t)w * max_it;
+    }
+    for (int it = 0; exact && it < max_it; ++it) {
+        Loop L{c, &b, v, it, it + 1, max_it, true};
+        iterate_pcg(&L);
+        c->pcg_cols_total += w;
+        if ((it + 1) % 25 == 0) {
             cudaMemcpyAsync(rz.data(), v.cb + CB_RZ * w, sizeof(double) * w, cudaMemcpyDeviceToHost, c->stream);
             cudaStreamSynchronize(c->stream);
             bool done = true;
@@ -508,7 +569,7 @@ void ofks_default_params(ofks_params *p) {
     p->poisson_pc = OFKS_HPC_SEPARABLE;
     p->mixed_tol = 1e-5; p->poisson_tol_mixed = 1e-8;
     p->judge_tau = 0.5; p->learned_tc = 1; p->poisson_adaptive = 0; p->poisson_csr = 0; p->gram_tc = 1;
-    p->poisson_sep_tc = 1; p->spmm_f32_rows = 0; p->pcg_compact = 1;
+    p->poisson_sep_tc = 1; p->spmm_f32_rows = 0; p->pcg_compact = 1; p->cuda_graphs = 1;
 }
 
 int ofks_create(ofks_ctx **out, int device) {
@@ -540,6 +601,7 @@ void ofks_destroy(ofks_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_blocks(c);
     free_mesh(c);
+    clear_graphs(c);
     dfree(c->d_sc); dfree(c->d_rec); dfree(c->d_flag); dfree(c->d_shift_in);
     for (auto &pe : c->prof_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
@@ -598,7 +660,7 @@ int ofks_set_params(ofks_ctx *c, const ofks_params *prm) {
         prm->poisson_adaptive < 0 || prm->poisson_adaptive > 1 ||
         prm->poisson_csr < 0 || prm->poisson_csr > 1 || prm->poisson_sep_tc < 0 || prm->poisson_sep_tc > 1 ||
         prm->spmm_f32_rows < 0 || prm->spmm_f32_rows > 1 || prm->gram_tc < 0 || prm->gram_tc > 1 ||
-        prm->pcg_compact < 0 || prm->pcg_compact > 1 ||
+        prm->pcg_compact < 0 || prm->pcg_compact > 1 || prm->cuda_graphs < 0 || prm->cuda_graphs > 1 ||
         (prm->precision != OFKS_FP64 && prm->precision != OFKS_MIXED) || !(prm->mixed_tol > 0) ||
         !(prm->poisson_tol_mixed > 0) || !(prm->eta_min > 0) || !(prm->eta_max >= prm->eta_min) ||
         prm->multipole_lmax < -1 || prm->multipole_lmax > 2 || !(prm->poisson_tol > 0) ||
@@ -608,6 +670,7 @@ int ofks_set_params(ofks_ctx *c, const ofks_params *prm) {
     const bool mixed = prm->precision == OFKS_MIXED;
     const bool realloc = prm->p != c->p || mixed != c->mixed_alloc;
     c->prm = *prm;
+    clear_graphs(c);                              // captured sequences depend on the parameters
     c->evaluated = false;
     if (realloc) {
         int rc = alloc_blocks(c, prm->p, mixed);

@@ -523,17 +523,41 @@ int run_hartree(ofks_ctx *c) {
         if (it >= c->prm.poisson_max_iter)
             return ofks_fail(c, OFKS_ETIMEOUT, "Hartree CG: %d iterations, relative residual %.3e",
                              it, std::sqrt(rr / bb));
-        for (int j = 0; j < chunk && sep; ++j, ++it) {
-            spmv(it);
-            {
-                ProfScope pp(c, PF_POISSON_PC);
-                sep_cg_step(c, it, (it + 1) & 1, 0);    // update, precondition, r.z
-            }
-            {
-                ProfScope pu(c, PF_POISSON_VEC);
-                k_cg_dir<<<gU, 256, 0, c->stream>>>(N, c->d_cz, c->d_cp, sc, it);
-            }
-            c->kernels += 1;
+        if (sep) {
+            // `chunk` CG iterations between residual checks; their kernels use the iteration
+            // number only through its parity (it >= 0), and a chunk starts at a multiple of the
+            // even chunk length, so one captured graph serves every chunk
+            struct Chunk { ofks_ctx *c; int it0, n; bool lat; unsigned gN, gU; int64_t N; double *sc; };
+            Chunk C{c, it, chunk, lat, gN, gU, N, sc};
+            auto body = [](void *a) {
+                Chunk &K = *static_cast<Chunk *>(a);
+                ofks_ctx *c = K.c;
+                for (int it = K.it0; it < K.it0 + K.n; ++it) {
+                    {
+                        ProfScope pv(c, PF_POISSON_SPMV);
+                        if (K.lat) launch_stencil_spmv(c, c->d_cp, c->d_cq, K.sc, it);
+                        else {
+                            k_cg_spmv<<<K.gN, 256, 0, c->stream>>>(K.N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv,
+                                                                   c->d_cp, c->d_cq, K.sc, it);
+                            c->kernels += 1;
+                        }
+                    }
+                    {
+                        ProfScope pp(c, PF_POISSON_PC);
+                        sep_cg_step(c, it, (it + 1) & 1, 0);    // update, precondition, r.z
+                    }
+                    {
+                        ProfScope pu(c, PF_POISSON_VEC);
+                        k_cg_dir<<<K.gU, 256, 0, c->stream>>>(K.N, c->d_cz, c->d_cp, K.sc, it);
+                    }
+                    c->kernels += 1;
+                }
+            };
+            int rc;
+            if ((rc = run_graph(c, {2, chunk, it & 1, lat ? 1 : 0, (c->sep.tc && c->prm.poisson_sep_tc) ? 1 : 0},
+                                body, &C)))
+                return rc;
+            it += chunk;
         }
         for (int j = 0; j < chunk && amg && !sep; ++j, ++it) {
             spmv(it);

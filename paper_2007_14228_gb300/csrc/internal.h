@@ -200,6 +200,10 @@ struct ofks_ctx {
     bool converged = false;
     double last_E = 0, last_kkt = 0, last_fea = 0;
     std::vector<double> history;                 // rows of 6
+    // CUDA graphs of fixed launch sequences (the PCG loop, Hartree CG chunks), keyed by what
+    // shapes the sequence: replayed instead of relaunching its kernels one by one
+    struct GraphEntry { std::vector<int64_t> key; cudaGraphExec_t exec; int64_t kernels; };
+    std::vector<GraphEntry> graphs;
     double t_start = 0.0;
     double t_accum = 0.0;
 
@@ -226,6 +230,13 @@ int ofks_fail(ofks_ctx *c, int code, const char *fmt, ...);
 int ofks_cuda_check(ofks_ctx *c, cudaError_t e, const char *what);
 void prof_begin(ofks_ctx *c, int fam, cudaEvent_t *a, cudaEvent_t *b);
 void prof_end(ofks_ctx *c, int fam, cudaEvent_t a, cudaEvent_t b);
+
+// Runs `body` (kernel launches on c->stream only, no host synchronisation) through the context's
+// graph for `key`: captured on first use, replayed afterwards; the kernel count of the sequence is
+// added each time.  Without graphs (profiling on, cuda_graphs = 0, or a capture that fails) body
+// runs directly.  Defined in api.cu.
+int run_graph(ofks_ctx *c, const std::vector<int64_t> &key, void (*body)(void *), void *arg);
+void clear_graphs(ofks_ctx *c);
 
 struct ProfScope {
     ofks_ctx *c; int fam; cudaEvent_t a = nullptr, b = nullptr;

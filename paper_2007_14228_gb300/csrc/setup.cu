@@ -189,6 +189,7 @@ void dev_free(T *&p) {
 }  // namespace
 
 void free_mesh(ofks_ctx *c) {
+    clear_graphs(c);
     dev_free(c->d_slice_ptr); dev_free(c->d_slice_w); dev_free(c->d_cols); dev_free(c->d_perm);
     dev_free(c->d_valL); dev_free(c->d_valB); dev_free(c->d_valH); dev_free(c->d_dL); dev_free(c->d_dB);
     dev_free(c->d_fptr); dev_free(c->d_fcol); dev_free(c->d_fval); dev_free(c->d_minv);

@@ -47,7 +47,7 @@ class Params(C.Structure):
                 ("poisson_tol_mixed", C.c_double), ("judge_tau", C.c_double), ("learned_tc", C.c_int32),
                 ("poisson_adaptive", C.c_int32), ("poisson_csr", C.c_int32),
                 ("gram_tc", C.c_int32), ("spmm_f32_rows", C.c_int32), ("poisson_sep_tc", C.c_int32),
-                ("pcg_compact", C.c_int32)]
+                ("pcg_compact", C.c_int32), ("cuda_graphs", C.c_int32)]
 
 
 class Result(C.Structure):

@@ -218,3 +218,35 @@ def test_wide_float32_gradient_and_grams_match(ofks, pw):
         ref = res["fp64"][k]
         scale = np.max(np.abs(ref))
         assert np.max(np.abs(res["f32"][k] - ref)) < 2e-5 * scale, (k, np.max(np.abs(res["f32"][k] - ref)) / scale)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cuda_graphs_match_direct_launches(ofks, precision):
+    # the fixed-count PCG loop and the Hartree CG chunks replayed from captured graphs run the same
+    # kernels in the same order as direct launches: the same results up to the atomics' summation
+    # order, on the lattice path (chain, p = 41: compact chunk-major PCG) and at p = 2 (LiH)
+    for s in (I.chain(cells=(26, 14, 8)), I.lih().with_cells((8, 8, 8))):
+        m = I.make_mesh(s)
+        V = I.initial_block(m.n_free, s.p, 0)
+        rng = np.random.default_rng(3)
+        G = rng.standard_normal((m.n_free, s.p))
+        shifts = -rng.uniform(0.05, 2.0, s.p)
+        shifts[::3] = 0.4                              # some columns with T = I
+        out = {}
+        for graphs in (1, 0):
+            ctx = ofks.context_for(s, m, beta=10.0, precision=precision, cuda_graphs=graphs)
+            D1 = ctx.precondition("pcg", G, shifts)
+            D2 = ctx.precondition("pcg", G, shifts)    # the second call replays the captured loop
+            ctx.init_orbitals(V)
+            # float32 trajectories far from the minimizer diverge with the atomics' order within tens
+            # of iterations whatever launches them: the mixed form is compared after 3 iterations
+            r = ctx.step(30 if precision == "fp64" else 3)
+            out[graphs] = (D1, D2, r["e_total"], ctx.get_orbitals())
+            ctx.close()
+        scale = np.max(np.abs(out[0][0]))
+        tol = 1e-12 if precision == "fp64" else 1e-6
+        for k in (0, 1):
+            assert np.max(np.abs(out[1][k] - out[0][0])) <= tol * scale
+        etol, xtol = (1e-9, 1e-6) if precision == "fp64" else (1e-6, 1e-4)
+        assert abs(out[1][2] - out[0][2]) <= etol * abs(out[0][2]), (out[1][2], out[0][2])
+        assert np.max(np.abs(out[1][3] - out[0][3])) <= xtol * np.max(np.abs(out[0][3]))

@@ -93,6 +93,86 @@ __global__ void __launch_bounds__(256) k_gram2(int64_t n, int p, int ld, int nti
         }
 }
 
+// Float32 Grams for 64 < ld <= 256 (where the tensor-core form's operands no longer fit): one CTA
+// per (upper 64 x 64 tile pair (i, j), range of rows).  Rows arrive 32 at a time as float4 loads
+// into registers while the previous 32 are multiplied from shared memory; a thread keeps a 4 x 4
+// tile of X^T A and of X^T B: per row one float4 of X, A and B feed 32 FMAs.  Partial tiles are
+// added to the float64 outputs (upper triangle i <= j < p) at the end.
+constexpr int GM_T = 64, GM_KR = 32;
+
+__global__ void __launch_bounds__(256) k_gram_f32w(int64_t n, int p, int ld, int ntile, const float *__restrict__ X,
+                                                   const float *__restrict__ A, const float *__restrict__ B,
+                                                   double *XA, double *XB, int64_t rows_per_split) {
+    __shared__ __align__(16) float xs[GM_KR][GM_T], as[GM_KR][GM_T], bs[GM_KR][GM_T];
+    int pair = blockIdx.x, ti = 0;
+    while (pair >= ntile - ti) { pair -= ntile - ti; ++ti; }
+    const int tj = ti + pair;
+    const int i0 = ti * GM_T, j0 = tj * GM_T;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t r0 = blockIdx.y * rows_per_split;
+    const int64_t r1 = r0 + rows_per_split < n ? r0 + rows_per_split : n;
+    // loader: thread -> (row lr, float4 column q) of the 32 x 64 chunk, two items per array
+    float4 vx[2], va[2], vb[2];
+    auto fetch = [&](int64_t rb) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = threadIdx.x + 256 * h, lr = e >> 4, q = (e & 15) * 4;
+            const int64_t r = rb + lr;
+            const bool okr = r < r1;
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            vx[h] = (okr && i0 + q < ld) ? *reinterpret_cast<const float4 *>(X + r * ld + i0 + q) : z;
+            va[h] = (okr && j0 + q < ld) ? *reinterpret_cast<const float4 *>(A + r * ld + j0 + q) : z;
+            vb[h] = (okr && j0 + q < ld) ? *reinterpret_cast<const float4 *>(B + r * ld + j0 + q) : z;
+        }
+    };
+    auto stash = [&]() {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = threadIdx.x + 256 * h, lr = e >> 4, q = (e & 15) * 4;
+            *reinterpret_cast<float4 *>(&xs[lr][q]) = vx[h];
+            *reinterpret_cast<float4 *>(&as[lr][q]) = va[h];
+            *reinterpret_cast<float4 *>(&bs[lr][q]) = vb[h];
+        }
+    };
+    float ca[4][4], cb[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) { ca[a][b] = 0.f; cb[a][b] = 0.f; }
+    if (r0 < r1) fetch(r0);
+    for (int64_t rb = r0; rb < r1; rb += GM_KR) {
+        __syncthreads();
+        stash();
+        __syncthreads();
+        if (rb + GM_KR < r1) fetch(rb + GM_KR);       // the next chunk is in flight meanwhile
+#pragma unroll 4
+        for (int k = 0; k < GM_KR; ++k) {
+            const float4 x4 = *reinterpret_cast<const float4 *>(&xs[k][4 * ty]);
+            const float4 a4 = *reinterpret_cast<const float4 *>(&as[k][4 * tx]);
+            const float4 b4 = *reinterpret_cast<const float4 *>(&bs[k][4 * tx]);
+            const float xv[4] = {x4.x, x4.y, x4.z, x4.w}, av[4] = {a4.x, a4.y, a4.z, a4.w},
+                        bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    ca[a][b] = fmaf(xv[a], av[b], ca[a][b]);
+                    cb[a][b] = fmaf(xv[a], bv[b], cb[a][b]);
+                }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = i0 + 4 * ty + a, j = j0 + 4 * tx + b;
+            if (i < p && j < p && i <= j) {
+                atomicAdd(XA + (int64_t)i * ld + j, (double)ca[a][b]);
+                atomicAdd(XB + (int64_t)i * ld + j, (double)cb[a][b]);
+            }
+        }
+}
+
 __global__ void k_mirror2(int p, int ld, double *A, double *B) {
     for (int idx = threadIdx.x + blockIdx.x * blockDim.x; idx < p * p; idx += blockDim.x * gridDim.x) {
         const int i = idx / p, j = idx % p;
@@ -706,6 +786,16 @@ void launch_gram2(ofks_ctx *c, const T *X, const T *A, const T *B, double *XA, d
     cudaMemsetAsync(XB, 0, sizeof(double) * ld * ld, c->stream);
     if constexpr (sizeof(T) == 4) {
         if (launch_gram_tc(c, (const float *)X, (const float *)A, (const float *)B, XA, XB)) {
+            k_mirror2<<<4, 256, 0, c->stream>>>(p, ld, XA, XB);
+            return;
+        }
+        if (ld > 64 && ld <= 256 && ld % 4 == 0) {
+            const int ntile = (p + GM_T - 1) / GM_T, npair = ntile * (ntile + 1) / 2;
+            int64_t splits = std::max<int64_t>(1, std::min<int64_t>((c->n + 255) / 256, (152LL * 4) / npair + 1));
+            const int64_t rps = ((c->n + splits - 1) / splits + GM_KR - 1) / GM_KR * GM_KR;
+            splits = (c->n + rps - 1) / rps;
+            k_gram_f32w<<<dim3((unsigned)npair, (unsigned)splits), 256, 0, c->stream>>>(
+                c->n, p, ld, ntile, (const float *)X, (const float *)A, (const float *)B, XA, XB, rps);
             k_mirror2<<<4, 256, 0, c->stream>>>(p, ld, XA, XB);
             return;
         }

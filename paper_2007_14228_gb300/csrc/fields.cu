@@ -510,9 +510,9 @@ int run_hartree(ofks_ctx *c) {
     double ptol = c->phase == 32 ? std::max(c->prm.poisson_tol, c->prm.poisson_tol_mixed) : c->prm.poisson_tol;
     if (c->hartree_tol > 0.0) ptol = std::max(ptol, c->hartree_tol);
     const double tol2 = ptol * ptol;
-    const int chunk = amg ? 4 : 32;
-    int it = 0;
-    double h[8];
+    int chunk = amg ? 4 : 32;
+    int it = 0, it_prev = 0;
+    double h[8], rr_prev = 0.0;
     for (;;) {
         cudaError_t e = cudaMemcpyAsync(h, sc, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -523,10 +523,23 @@ int run_hartree(ofks_ctx *c) {
         if (it >= c->prm.poisson_max_iter)
             return ofks_fail(c, OFKS_ETIMEOUT, "Hartree CG: %d iterations, relative residual %.3e",
                              it, std::sqrt(rr / bb));
+        // with the separable preconditioner the squared residual falls by a steady factor per
+        // iteration: after the first chunk, run the predicted count to the target (1 to 8), not
+        // a fixed 4, so the last chunk does not overshoot
+        if (sep) {
+            chunk = 4;
+            if (it > 0 && rr_prev > 0.0 && rr < rr_prev) {
+                const double f = std::pow(rr / rr_prev, 1.0 / (it - it_prev));
+                const double need = std::log(tol2 * bb / rr) / std::log(f);
+                chunk = (int)std::min(8.0, std::max(1.0, std::ceil(need)));
+            }
+            rr_prev = rr;
+            it_prev = it;
+        }
         if (sep) {
             // `chunk` CG iterations between residual checks; their kernels use the iteration
-            // number only through its parity (it >= 0), and a chunk starts at a multiple of the
-            // even chunk length, so one captured graph serves every chunk
+            // number only through its parity (it >= 0), so one captured graph per chunk length
+            // and parity of its first iteration serves every chunk
             struct Chunk { ofks_ctx *c; int it0, n; bool lat; unsigned gN, gU; int64_t N; double *sc; };
             Chunk C{c, it, chunk, lat, gN, gU, N, sc};
             auto body = [](void *a) {

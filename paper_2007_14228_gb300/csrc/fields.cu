@@ -519,17 +519,25 @@ int run_hartree(ofks_ctx *c) {
         if (e != cudaSuccess) return ofks_cuda_check(c, e, "Hartree CG");
         const double rr = h[4 + (it & 1)], bb = h[6];
         if (!std::isfinite(rr)) return ofks_fail(c, OFKS_ENONFINITE, "Hartree CG residual is not finite");
-        if (rr <= tol2 * bb || bb == 0.0) { c->cg_last = it; c->cg_total += it; break; }
+        if (rr <= tol2 * bb || bb == 0.0) {
+            if (sep && it > it_prev && rr_prev > 0.0 && rr > 0.0 && rr < rr_prev)
+                c->cg_rate = std::pow(rr / rr_prev, 1.0 / (it - it_prev));
+            c->cg_last = it;
+            c->cg_total += it;
+            break;
+        }
         if (it >= c->prm.poisson_max_iter)
             return ofks_fail(c, OFKS_ETIMEOUT, "Hartree CG: %d iterations, relative residual %.3e",
                              it, std::sqrt(rr / bb));
         // with the separable preconditioner the squared residual falls by a steady factor per
-        // iteration: after the first chunk, run the predicted count to the target (1 to 8), not
-        // a fixed 4, so the last chunk does not overshoot
+        // iteration: run the count that factor predicts to the target (1 to 8) before the next
+        // check, not a fixed 4 (the first chunk uses the last solve's factor)
         if (sep) {
+            double f = c->cg_rate;
+            if (it > 0 && rr_prev > 0.0 && rr < rr_prev) f = std::pow(rr / rr_prev, 1.0 / (it - it_prev));
             chunk = 4;
-            if (it > 0 && rr_prev > 0.0 && rr < rr_prev) {
-                const double f = std::pow(rr / rr_prev, 1.0 / (it - it_prev));
+            if (f > 0.0 && f < 1.0) {
+                c->cg_rate = f;
                 const double need = std::log(tol2 * bb / rr) / std::log(f);
                 chunk = (int)std::min(8.0, std::max(1.0, std::ceil(need)));
             }

@@ -194,6 +194,8 @@ struct ofks_ctx {
     bool bx_valid = false;                       // d_BX holds B X for the current iterate
     int k = 0;
     int cg_last = 0;                             // CG iterations of the last Hartree solve
+    double cg_rate = 0.0;                        // per-iteration factor of the squared Hartree CG residual
+                                                 // observed in the last solve (0: none yet)
     double hartree_tol = 0.0;                    // > 0: tolerance of the next Hartree solve (adaptive mode)
     int64_t cg_total = 0;                        // ... summed since the counter was cleared
     double kkt0 = 0.0, eta = 0.0;

@@ -520,7 +520,8 @@ __global__ void __launch_bounds__(256) k_pcg_update(int64_t n, int p, int ld, in
 // Start: rows n <= r < ns are padding and stay zero; compact column k < pc is column cmap[k] of G
 // (row-major, pitch ld); the other columns are zero.  W = 1/diag with diag = dL/2 - shift_k dB;
 // R = G (minus Q, the operator applied to the network's D, when warm); Z = W R; D = 0 (or the
-// network's D when warm); rz[k] += R Z.  Each thread takes (row, 4-column chunk) items in a
+// network's D when warm); rz[k] += R Z; the padding rows of P (and of Q when it is not the warm
+// start's input) are zeroed.  Each thread takes (row, 4-column chunk) items in a
 // grid-stride loop: consecutive threads take consecutive rows of one chunk, so every write is one
 // float4 of a contiguous run; a warp never spans two chunks (ns is a multiple of 32).
 // Column sums go warp -> shared memory -> one float64 atomic per column and block (same-address
@@ -538,7 +539,7 @@ __global__ void __launch_bounds__(256) k_pcg_init_s(int64_t n, int64_t ns, int p
                                                     const float *__restrict__ Dn, int ld, const int *__restrict__ cmap,
                                                     const double *__restrict__ dL, const double *__restrict__ dB,
                                                     const double *__restrict__ cb, float *W, float *D, float *R,
-                                                    float *Z, double *rz) {
+                                                    float *Z, float *P, float *Q, double *rz) {
     __shared__ float cs[MAXLD];
     for (int k = threadIdx.x; k < w; k += blockDim.x) cs[k] = 0.f;
     __syncthreads();
@@ -574,6 +575,10 @@ __global__ void __launch_bounds__(256) k_pcg_init_s(int64_t n, int64_t ns, int p
         *reinterpret_cast<float4 *>(R + o) = make_float4(rv[0], rv[1], rv[2], rv[3]);
         *reinterpret_cast<float4 *>(Z + o) = make_float4(zv[0], zv[1], zv[2], zv[3]);
         *reinterpret_cast<float4 *>(D + o) = make_float4(dv[0], dv[1], dv[2], dv[3]);
+        if (nat < 0) {                               // padding rows: the apply never writes their P, Q
+            *reinterpret_cast<float4 *>(P + o) = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (Q) *reinterpret_cast<float4 *>(Q + o) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         flush_cols(acc, q, pc, cs);
     }
     __syncthreads();
@@ -875,7 +880,8 @@ void launch_pcg_init(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v) {
             const int64_t total = c->n_slots * (w >> 2);
             k_pcg_init_s<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8), 256, 0, c->stream>>>(
                 c->n, c->n_slots, v.pc, w, (const float *)b.G[c->cur], nullptr, nullptr, c->ld, v.cmap, c->d_dL,
-                c->d_dB, v.cb, (float *)b.W, (float *)v.D, (float *)b.R, (float *)b.Z, v.cb + CB_RZ * w);
+                c->d_dB, v.cb, (float *)b.W, (float *)v.D, (float *)b.R, (float *)b.Z, (float *)b.P, (float *)b.Q,
+                v.cb + CB_RZ * w);
             return;
         }
     }
@@ -907,7 +913,7 @@ void launch_pcg_init_warm(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v) {
             k_pcg_init_s<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8), 256, 0, c->stream>>>(
                 c->n, c->n_slots, v.pc, v.w, (const float *)b.G[c->cur], (const float *)b.Q,
                 (const float *)b.D[c->cur], ld, v.cmap, c->d_dL, c->d_dB, v.cb, (float *)b.W, (float *)v.D,
-                (float *)b.R, (float *)b.Z, v.cb + CB_RZ * v.w);
+                (float *)b.R, (float *)b.Z, (float *)b.P, nullptr, v.cb + CB_RZ * v.w);   // Qn aliases b.Q
             return;
         }
     }

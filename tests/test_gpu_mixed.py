@@ -250,3 +250,25 @@ def test_cuda_graphs_match_direct_launches(ofks, precision):
         etol, xtol = (1e-9, 1e-6) if precision == "fp64" else (1e-6, 1e-4)
         assert abs(out[1][2] - out[0][2]) <= etol * abs(out[0][2]), (out[1][2], out[0][2])
         assert np.max(np.abs(out[1][3] - out[0][3])) <= xtol * np.max(np.abs(out[0][3]))
+
+
+def test_exact_preconditioner_matches_the_oracle(ofks):
+    # OFKS_PC_EXACT: the PCG of Eq. precondition-T run to a 1e-12 relative residual (float64, the
+    # compact column block and all columns), against the oracle's own exact solve
+    s = I.chain(cells=(26, 14, 8))
+    m = I.make_mesh(s)
+    rng = np.random.default_rng(13)
+    G = rng.standard_normal((m.n_free, s.p))
+    shifts = -rng.uniform(0.05, 2.0, s.p)
+    inactive = rng.choice(s.p, 17, replace=False)
+    shifts[inactive] = 0.3
+    pr = pcal.Problem(m.xyz, m.tet10, m.dirichlet, s.Z, s.R,
+                      pcal.Params(p=s.p, occ=s.occ, hartree=False, xc=False, precond="exact"))
+    Do = pr.precondition(G, shifts)
+    scale = np.max(np.abs(Do))
+    for compact in (1, 0):
+        ctx = ofks.context_for(s, m, beta=10.0, precision="fp64", pcg_compact=compact)
+        D = ctx.precondition("exact", G, shifts)
+        ctx.close()
+        assert np.max(np.abs(D - Do)) < 1e-8 * scale, (compact, np.max(np.abs(D - Do)) / scale)
+        assert np.array_equal(D[:, inactive], G[:, inactive])

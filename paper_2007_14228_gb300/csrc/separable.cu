@@ -264,7 +264,8 @@ __device__ __forceinline__ void cp16(void *dst, const void *src, int src_bytes) 
 struct SepPass {
     const __nv_bfloat16 *A;        // M x KP row-major (zero padding beyond K)
     const __nv_bfloat16 *Bt;       // NP x KP row-major, zero padded
-    int M, K, KP, N, NP, tcols;    // tcols: tensor-memory columns (power of two >= NP)
+    int M, K, KP, N, NP, tcols;    // tcols: tensor-memory columns (power of two >= NS)
+    int NS;                        // output columns per CTA (NP / gridDim.y, a multiple of 16)
     __nv_bfloat16 *out;            // element (n, m) at (n M1 + m / M2) KPo + m % M2
     int M1, M2, KPo;
     const float *lr, *lc;          // SCALE: multiply by 1 / (lr[n] + lc[m])
@@ -275,12 +276,13 @@ template <int SCALE>
 __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
     extern __shared__ __align__(128) unsigned char dsm[];
     __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(dsm);     // STM x KP
-    __nv_bfloat16 *sB = sA + STM * P.KP;                             // NP x KP
+    __nv_bfloat16 *sB = sA + STM * P.KP;                             // NS x KP
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * STM;
+    const int n0 = blockIdx.y * P.NS;                                // this CTA's output columns
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
@@ -295,9 +297,9 @@ __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
     // operands: rows of 8 elements (16 B) copied asynchronously into their core-matrix rows,
     // all of a thread's copies in flight at once
     const int kc8 = P.KP >> 3;
-    for (int e = tid; e < P.NP * kc8; e += blockDim.x) {
+    for (int e = tid; e < P.NS * kc8; e += blockDim.x) {
         const int n = e / kc8, k = (e - n * kc8) * 8;
-        cp16(sB + coff(n, k, P.KP), P.Bt + (int64_t)n * P.KP + k, 16);
+        cp16(sB + coff(n, k, P.KP), P.Bt + (int64_t)(n0 + n) * P.KP + k, 16);
     }
     for (int e = tid; e < STM * kc8; e += blockDim.x) {
         const int rr = e / kc8, k = (e - rr * kc8) * 8;
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
     if (tid == 0) {
-        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(P.NP >> 3) << 17) |
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(P.NS >> 3) << 17) |
                                ((uint32_t)(STM >> 4) << 24);
         const uint32_t a0 = su32(sA), b0 = su32(sB), sbo = (uint32_t)(P.KP >> 3) * 128u;
         for (int kk = 0; kk < P.KP / 16; ++kk) {
@@ -341,7 +343,7 @@ __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
         const int m1 = m / P.M2, m2 = m - m1 * P.M2;
         const float lcm = (SCALE && m < P.M) ? P.lc[m] : 0.f;
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int cb = 0; cb < P.NP; cb += 16) {
+        for (int cb = 0; cb < P.NS; cb += 16) {
             uint32_t v[16];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
@@ -353,7 +355,7 @@ __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
             if (m >= P.M) continue;
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                const int n = cb + q;
+                const int n = n0 + cb + q;
                 if (n >= P.N) break;
                 float x = __uint_as_float(v[q]);
                 if (SCALE) x = __fdividef(x, P.lr[n] + lcm);
@@ -370,15 +372,25 @@ __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
 
 template <int SCALE>
 void sep_tc_launch(ofks_ctx *c, SepPass P) {
-    P.tcols = P.NP <= 32 ? 32 : (P.NP <= 64 ? 64 : (P.NP <= 128 ? 128 : 256));
+    // the output columns split over gridDim.y CTAs (each a multiple of 16) until the grid covers
+    // the 152 SMs: the passes are latency-bound, and short axes give few 128-row tiles
+    const int ctas = (P.M + STM - 1) / STM, nb = P.NP / 16;
+    int d = 1;
+    for (int cand = 1; cand <= nb; ++cand) {
+        if (nb % cand) continue;
+        d = cand;
+        if ((int64_t)ctas * cand >= 152) break;
+    }
+    P.NS = P.NP / d;
+    P.tcols = P.NS <= 32 ? 32 : (P.NS <= 64 ? 64 : (P.NS <= 128 ? 128 : 256));
     P.err = c->d_flag + 1;
     // shared memory of at least 228 KB * tcols / 512 per CTA keeps the CTAs resident on one SM
     // within its 512 tensor-memory columns, so no allocation ever has to wait
-    const int need = (STM + P.NP) * P.KP * (int)sizeof(__nv_bfloat16);
+    const int need = (STM + P.NS) * P.KP * (int)sizeof(__nv_bfloat16);
     const int floor_ = 228 * 1024 / (512 / P.tcols) + 1024;
     const int smem = std::min(227 * 1024, std::max(need, floor_));
     cudaFuncSetAttribute(k_sep_tc<SCALE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_sep_tc<SCALE><<<(unsigned)((P.M + STM - 1) / STM), 128, smem, c->stream>>>(P);
+    k_sep_tc<SCALE><<<dim3((unsigned)ctas, (unsigned)d), 128, smem, c->stream>>>(P);
     c->kernels += 1;
 }
 

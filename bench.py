@@ -37,6 +37,21 @@ METRIC = "time-to-1e-6 Ha & iters/s: learned-precond mixed vs plain FP64, same G
 UNIT = "iters/s"
 
 
+def max_over_ranks(t, dist, device):
+    """Time of the slowest rank: every rank runs its own replica and the job ends with the last."""
+    if not dist:
+        return t
+    import torch
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replica_value(world, steps, t):
+    """Whole-job iterations/s: world replicas of `steps` iterations each in the slowest rank's time."""
+    return world * steps / t
+
+
 def workload(name):
     from paper_2007_14228_gb300 import inputs as I
     if name == "chain":
@@ -399,11 +414,7 @@ def main():
         resp = ctx.step(args.steps)
         prof = ctx.profile_get()
         ctx.profile(False)
-        if dist:
-            import torch
-            tt = torch.tensor([t], dtype=torch.float64, device=f"cuda:{local}")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
+        t = max_over_ranks(t, dist, f"cuda:{local}")
         # mean block width of the timed PCG applies (the compact form's width follows the active count)
         nap = prof.get("pcg_spmm", {}).get("launches", 0)
         res["pcg_width"] = (resp["pcg_cols_total"] - r0["pcg_cols_total"]) / nap if nap else None
@@ -419,7 +430,7 @@ def main():
     if not args.no_learned:
         ctxl, resl, profl, _, tl = timed("mixed", False, "learned")
         profl.pop("all_kernels", None)
-        learned = {"value": round(world * args.steps / tl, 4), "unit": UNIT, "ms_per_step": round(tl / args.steps * 1e3, 3),
+        learned = {"value": round(replica_value(world, args.steps, tl), 4), "unit": UNIT, "ms_per_step": round(tl / args.steps * 1e3, 3),
                    "judge_accept": resl["judge_accept"], "judge_total": resl["judge_total"],
                    "kernel_ms": {k: round(v["ms"], 3) for k, v in profl.items() if v["launches"]}}
         ctxl.close()
@@ -427,7 +438,7 @@ def main():
     ctx, res, prof, clocks, t = timed("mixed", True)
     launches = prof.pop("all_kernels", {"launches": None})["launches"]
     steps_done = args.steps
-    value = world * steps_done / t
+    value = replica_value(world, steps_done, t)
     sizes = ctx.sizes()
     pinfo = ctx.poisson_info()
 
@@ -448,13 +459,9 @@ def main():
             r = ctx.step(1)
             ctx.get_orbitals(Xh)
         dt = time.perf_counter() - t0
-        if dist:
-            import torch
-            tt = torch.tensor([dt], dtype=torch.float64, device=f"cuda:{local}")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dt = float(tt.item())
+        dt = max_over_ranks(dt, dist, f"cuda:{local}")
         nb = m.n_free * s.p * 8
-        e2e = {"value": round(world * k_e2e / dt, 4), "unit": UNIT, "h2d_bytes_per_step": nb,
+        e2e = {"value": round(replica_value(world, k_e2e, dt), 4), "unit": UNIT, "h2d_bytes_per_step": nb,
                "d2h_bytes_per_step": nb + 10 * 8, "steps": k_e2e}
     ctx.close()
     if rank != 0:
@@ -478,12 +485,12 @@ def main():
            "clocks": clocks, "E": res["e_total"], "kkt": res["kkt"], "fea": res["fea"],
            "hartree_cg_iters_per_step": round(res["hartree_total"] / max(steps_done, 1), 1),
            "hartree_operator": pinfo,
-           "plain_fp64": {"value": round(world * steps64 / t64, 4), "unit": UNIT,
+           "plain_fp64": {"value": round(replica_value(world, steps64, t64), 4), "unit": UNIT,
                           "ms_per_step": round(t64 / steps64 * 1e3, 3), "gpu_launches": launches64,
                           "roofline": roof64, "kernel_ms": {k: round(v["ms"], 3) for k, v in prof64.items()
                                                             if v["launches"]},
                           "hartree_cg_iters_per_step": round(res64["hartree_total"] / max(steps64, 1), 1)},
-           "speedup_vs_plain_fp64": round(value / (world * steps64 / t64), 3),
+           "speedup_vs_plain_fp64": round(value / replica_value(world, steps64, t64), 3),
            "learned_mixed": learned, "start": start_info,
            "time_to_1e-6_Ha": ttc}
     out["gpu_launches"] = launches

@@ -277,8 +277,8 @@ int ofks_fma_peak(ofks_ctx *ctx, int32_t precision, double *tflops);
  * eta).  Copies min(cap, available) rows of the most recent ones into buf; *len = rows. */
 int ofks_get_history(ofks_ctx *ctx, double *buf, int32_t cap, int32_t *len);
 
-/* ---- learned preconditioner (BASELINE's learned-preconditioner configuration; the paper's
- * Eq. precondition-T stays its fallback and judge) -------------------------------------------
+/* ---- learned preconditioner (not in the paper: a graph network in place of the PCG, with
+ * the paper's Eq. precondition-T as its acceptance test and fallback) ------------------------
  * The network maps a gradient column G_c to an approximation of T_c^{-1} G_c on the free-DoF
  * graph of the mesh: input features [z/s, log diag - mean, -lam dB/diag, 1] with
  * z = G / diag, diag = dL/2 - lam dB, s = rms(z); layers Z = H W + (A H) U + b (A: mean over the

@@ -166,6 +166,15 @@ def separable_model(pinfo):
     return nt * (6 * 8 + 12 + 12) + 8 * (nx * nx + ny * ny + nz * nz), 4 * nt * (nx + ny + nz)
 
 
+# DRAM bytes per algorithmic byte of the float32 PCG apply (k_pcg_apply_zc), measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the chain at 60 x 32 x 30 cells: 418.2 MB per
+# launch at n = 442,323, width 24 and 12,201,095 stored entries, whose algorithmic bytes are
+# 12 nnz + 20 n w = 358.7 MB.  The 80 x 44 x 43 workload is too large for that capture, so its
+# traffic is this ratio times its own algorithmic bytes (the column ids, values and the Z, P, Q
+# pieces all grow with the launch).
+PCG_F32_DRAM_PER_ALG = 418.2e6 / (12 * 12201095 + 20 * 442323 * 24)
+
+
 def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, spmv_model=(0, 0), elem=8, pc_model=(0, 0), pcg_w=None):
     """Dominant kernel family by time: algorithmic bytes and flops per launch / mean duration.
 
@@ -196,6 +205,10 @@ def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, spmv_model=(0, 0), ele
     f_hbm = gbs / hbm_peak
     fp32 = fam == "poisson_pc" or (elem == 4 and fam != "poisson_spmv")
     extra = {"pcg_block_width": round(pw, 2)} if fam == "pcg_spmm" else {}
+    traffic = None
+    if fam == "pcg_spmm" and elem == 4:
+        traffic = int(bytes_ * PCG_F32_DRAM_PER_ALG)
+        extra["traffic_source"] = "ncu DRAM bytes of the 60x32x30 chain's launch, scaled by algorithmic bytes"
     alu_peak = ALU_PEAKS["fp32"] if fp32 else ALU_PEAKS["fp64"]
     f_alu = tflops / alu_peak
     if f_alu >= f_hbm:
@@ -204,7 +217,7 @@ def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, spmv_model=(0, 0), ele
                 "hbm_gbs": round(gbs, 1), "hbm_frac": round(f_hbm, 4), "peak_kind": ALU_PEAKS["kind"],
                 "mean_launch_ms": round(per * 1e3, 4), "launches": st["launches"], **extra}
     return {"bound": "hbm", "kernel": fam, "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-            "frac": round(f_hbm, 4), "traffic": None, "fp64_tflops": round(tflops, 4),
+            "frac": round(f_hbm, 4), "traffic": traffic, "fp64_tflops": round(tflops, 4),
             "peak_kind": hbm_kind, "mean_launch_ms": round(per * 1e3, 4), "launches": st["launches"], **extra}
 
 

@@ -1,0 +1,40 @@
+"""bench.py's roofline arithmetic and the oracle sample's multipliers, on the CPU."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def test_pcg_roofline_is_algorithmic_bytes_over_launch_time():
+    # the float32 PCG apply on the 80 x 44 x 43 chain: n = 1,175,805, 32,817,315 stored entries,
+    # block width 24, 80 launches in 42.788 ms
+    n, nnz, w = 1175805, 32817315, 24.0
+    prof = {"pcg_spmm": {"ms": 42.788, "launches": 80}, "poisson": {"ms": 99.0, "launches": 1}}
+    r = bench.roofline(prof, n, 41, nnz, 908160, 6756.8, "measured", elem=4, pcg_w=w)
+    per = 42.788e-3 / 80
+    alg = 12 * nnz + 20 * n * w                       # (4 + 2 s) nnz + 5 s n w at s = 4
+    assert r["kernel"] == "pcg_spmm" and r["bound"] == "hbm"   # the Hartree total is not a candidate
+    assert r["achieved"] == pytest.approx(alg / per / 1e9, abs=0.05)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6756.8, abs=1e-4)
+    assert r["traffic"] == int(alg * bench.PCG_F32_DRAM_PER_ALG)
+    assert 1.0 < bench.PCG_F32_DRAM_PER_ALG < 1.3    # the mid-size capture moved 1.17x its algorithmic bytes
+
+
+def test_float64_pcg_roofline_is_against_the_fp64_rate():
+    bench.ALU_PEAKS.update({"fp64": 1.25, "fp32": 78.0, "kind": "test"})
+    prof = {"pcg_spmm": {"ms": 243.0, "launches": 80}}
+    r = bench.roofline(prof, 1175805, 41, 32817315, 908160, 6756.8, "measured", elem=8, pcg_w=24.0)
+    flops = 4 * 32817315 * 24.0 + 6 * 1175805 * 24.0
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s (fp64)" and r["traffic"] is None
+    assert r["achieved"] == pytest.approx(flops / (243e-3 / 80) / 1e12, abs=1e-4)
+    assert r["frac"] == pytest.approx(r["achieved"] / 1.25, abs=1e-4)
+
+
+@pytest.mark.parametrize("p,active", [(41, 23), (41, 41), (41, 1), (2, 1)])
+def test_oracle_sample_has_the_requested_active_columns(p, active):
+    sh = bench.shifts_with_active(p, active)
+    assert sh.shape == (p,) and int(np.sum(sh < 0)) == active and np.all(sh != 0)

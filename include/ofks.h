@@ -214,12 +214,15 @@ int ofks_set_params(ofks_ctx *ctx, const ofks_params *prm);
  * positive definite (V rank deficient), OFKS_ESTATE, OFKS_EINVAL. */
 int ofks_init_orbitals(ofks_ctx *ctx, const double *V);
 
-/* Set X directly (n_free x p, host), without orthonormalization.  keep_history = 0 resets
- * the iteration counter and the step-size history; 1 keeps them (the caller re-uploads the
- * block it read back).  Errors: OFKS_ESTATE, OFKS_EINVAL. */
+/* Set X directly (n_free x p, host, row-major; the caller keeps ownership), without
+ * orthonormalization.  keep_history = 0 resets the iteration counter and the step-size history;
+ * 1 keeps them (the caller re-uploads the block it read back).  The block travels as one
+ * contiguous copy (page-locked host memory runs at the link's rate).  Errors: OFKS_ESTATE (no
+ * mesh or params), OFKS_EINVAL (null pointer), OFKS_ECUDA. */
 int ofks_set_orbitals(ofks_ctx *ctx, const double *X, int32_t keep_history);
 
-/* Copy the current X (n_free x p) to host memory X. */
+/* Copy the current X (n_free x p, row-major) into the caller's host buffer X; returns after the
+ * copy has landed.  Errors: OFKS_ESTATE (no orbitals yet), OFKS_EINVAL, OFKS_ECUDA. */
 int ofks_get_orbitals(ofks_ctx *ctx, double *X);
 
 /* Run up to k iterations of Alg. 2 from the current state; stops early once the stopping
@@ -295,14 +298,18 @@ int ofks_precond_get_weights(ofks_ctx *ctx, float *w, int64_t cap, int64_t *coun
 int ofks_precond_set_weights(ofks_ctx *ctx, const float *w, int64_t count);
 
 /* D (n_free x p, host) = preconditioned directions of G (host) for per-column shifts (host, p;
- * columns with shift >= 0 take D = G): mode OFKS_PC_PCG, OFKS_PC_EXACT or OFKS_PC_LEARNED (the
- * network alone, no judge).  Uses the context's scratch blocks; iteration history is kept.  A
- * mixed context (OFKS_MIXED, float32 blocks allocated) runs OFKS_PC_PCG in float32 as its
- * iterations do. */
+ * columns with shift >= 0 take D = G, Eq. precondition-T): mode OFKS_PC_PCG, OFKS_PC_EXACT or
+ * OFKS_PC_LEARNED (the network alone, no acceptance test).  The PCG modes solve the active
+ * columns only when pcg_compact is set, as the iterations do.  Uses the context's scratch
+ * blocks; iteration history is kept.  A mixed context (OFKS_MIXED, float32 blocks allocated)
+ * runs OFKS_PC_PCG in float32 as its iterations do.  Errors: OFKS_EINVAL (null pointer, unknown
+ * mode), OFKS_ESTATE (no mesh or params; OFKS_PC_LEARNED without a network), OFKS_ETIMEOUT (a
+ * bounded device wait gave up), OFKS_ECUDA. */
 int ofks_precondition(ofks_ctx *ctx, int32_t mode, const double *G, const double *shifts, double *D);
 
 /* One Adam step (learning rate lr) of the network on the pair (G, Dstar) with per-column
- * shifts; *loss receives the loss before the step (mean over columns of |D - D*|^2/|D*|^2). */
+ * shifts; *loss receives the loss before the step (mean over columns of |D - D*|^2/|D*|^2).
+ * Errors: OFKS_ESTATE (no network: ofks_precond_init first), OFKS_EINVAL, OFKS_ECUDA. */
 int ofks_train_precond_step(ofks_ctx *ctx, const double *G, const double *shifts, const double *Dstar,
                             double lr, double *loss);
 
@@ -310,13 +317,17 @@ int ofks_train_precond_step(ofks_ctx *ctx, const double *G, const double *shifts
 int ofks_precond_grads(ofks_ctx *ctx, const double *G, const double *shifts, const double *Dstar,
                        double *grads, int64_t cap, double *loss);
 
-/* Checkpoint: X, X_prev, D_prev, G_prev, eta, k, kkt0 and the Hartree warm start U, so a
- * reloaded run continues bit-for-bit.  The mesh, nuclei and params must match on load. */
+/* Checkpoint: X, X_prev, D_prev, G_prev, eta, k, kkt0 and the Hartree warm start U, restored
+ * exactly on load, so a reloaded run continues from the same state (later iterates agree up to
+ * the order of the device's floating-point atomics).  The mesh, nuclei and params must match
+ * on load.  Errors: OFKS_EINVAL (path cannot be opened or the file does not match the context's
+ * sizes), OFKS_ESTATE (no orbitals to save), OFKS_ECUDA. */
 int ofks_save_state(ofks_ctx *ctx, const char *path);
 int ofks_load_state(ofks_ctx *ctx, const char *path);
 
 /* Per-kernel device time accumulated while profiling is on (CUDA events around each
- * launch of the named kernel family).  on = 1 starts (and clears), 0 stops. */
+ * launch of the named kernel family).  on = 1 starts (and clears), 0 stops.  While it is on
+ * the CUDA graphs are not used (every launch runs on its own between its events). */
 int ofks_profile(ofks_ctx *ctx, int32_t on);
 /* kernel family id -> launches and total milliseconds since profiling was switched on;
  * name (may be NULL) receives a static string. */

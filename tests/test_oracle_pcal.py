@@ -182,3 +182,22 @@ def test_exact_preconditioner_solves_the_shifted_systems():
     D8 = pr.precondition(G, shifts)
     r8 = np.linalg.norm(T0 @ D8[:, 0] - G[:, 0])
     assert 1e-11 * np.linalg.norm(G[:, 0]) < r8 < np.linalg.norm(G[:, 0])
+
+
+def test_fixed_count_pcg_equals_textbook_jacobi_cg():
+    # the oracle's 8-iteration PCG of Eq. precondition-T is Jacobi-preconditioned CG from a zero
+    # start: scipy's cg with the same preconditioner, start and iteration count gives the same
+    # column (a wrong sign, index or beta in the oracle's recurrence would not)
+    import scipy.sparse.linalg as spla
+    s = I.lih().with_cells((6, 5, 5))
+    _, pr = _problem(s, precond="pcg")
+    rng = np.random.default_rng(4)
+    G = rng.standard_normal((pr.n, 2))
+    shifts = np.array([-0.7, -1.9])
+    D = pr.precondition(G, shifts)
+    for c in range(2):
+        T = (0.5 * pr.Lf - shifts[c] * pr.Bf).tocsr()
+        dinv = 1.0 / T.diagonal()
+        M = spla.LinearOperator(T.shape, matvec=lambda v, d=dinv: d * v)
+        x, _ = spla.cg(T, G[:, c], x0=np.zeros(pr.n), M=M, maxiter=pr.prm.pcg_iters, rtol=0.0, atol=0.0)
+        assert np.max(np.abs(D[:, c] - x)) <= 1e-10 * np.max(np.abs(x)), np.max(np.abs(D[:, c] - x))

@@ -713,10 +713,21 @@ int ofks_set_orbitals(ofks_ctx *c, const double *X, int32_t keep) {
     if (!c || !X) return OFKS_EINVAL;
     if (!c->n || !c->p) return ofks_fail(c, OFKS_ESTATE, "set_orbitals: no mesh/params");
     cudaSetDevice(c->device);
-    int rc = upload_block(c, X, c->b64.X[c->cur]);
-    if (rc) return rc;
     if (!keep) c->phase = c->prm.precision == OFKS_MIXED ? 32 : 64;
-    if (c->phase == 32) launch_convert(c, (const double *)c->b64.X[c->cur], c->b32.X[c->cur], c->n * (int64_t)c->ld);
+    if (c->phase == 32 && c->ld != c->p) {
+        // float32 iterations read only the float32 block (the float64 set is refilled from it
+        // before any float64 use): one pass from the staging copy straight into it
+        const size_t bytes = sizeof(double) * (size_t)c->n * c->p;
+        cudaError_t e = cudaMemcpyAsync(c->d_stage, X, bytes, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) launch_unpack_f32(c, c->d_stage, c->b32.X[c->cur]);
+        int rc = ofks_cuda_check(c, e, "block upload");
+        if (rc) return rc;
+    } else {
+        int rc = upload_block(c, X, c->b64.X[c->cur]);
+        if (rc) return rc;
+        if (c->phase == 32)
+            launch_convert(c, (const double *)c->b64.X[c->cur], c->b32.X[c->cur], c->n * (int64_t)c->ld);
+    }
     c->bx_valid = false;
     c->have_X = true;
     c->evaluated = false;
@@ -732,6 +743,13 @@ int ofks_get_orbitals(ofks_ctx *c, double *X) {
     if (!c || !X) return OFKS_EINVAL;
     if (!c->have_X) return ofks_fail(c, OFKS_ESTATE, "get_orbitals: no orbitals");
     cudaSetDevice(c->device);
+    if (c->phase == 32 && c->ld != c->p) {          // one pass from the float32 block into the staging copy
+        launch_pack_f32(c, c->b32.X[c->cur], c->d_stage);
+        cudaError_t e = cudaMemcpyAsync(X, c->d_stage, sizeof(double) * (size_t)c->n * c->p, cudaMemcpyDeviceToHost,
+                                        c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        return ofks_cuda_check(c, e, "block download");
+    }
     if (c->phase == 32) launch_convert(c, (const float *)c->b32.X[c->cur], c->b64.X[c->cur], c->n * (int64_t)c->ld);
     return download_block(c, c->b64.X[c->cur], X);
 }

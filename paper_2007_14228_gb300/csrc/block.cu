@@ -1020,6 +1020,40 @@ __global__ void __launch_bounds__(256) k_repack(int64_t n, int w, const double *
     }
 }
 
+__global__ void __launch_bounds__(256) k_unpack_f32(int64_t n, int p, int ld, const double *__restrict__ src,
+                                                    float *__restrict__ dst) {
+    const int64_t total = n * ld;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / ld;
+        const int j = (int)(i - r * ld);
+        dst[i] = j < p ? (float)src[r * p + j] : 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_pack_f32(int64_t n, int p, int ld, const float *__restrict__ src,
+                                                  double *__restrict__ dst) {
+    const int64_t total = n * p;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / p;
+        const int j = (int)(i - r * p);
+        dst[i] = (double)src[r * ld + j];
+    }
+}
+
+void launch_unpack_f32(ofks_ctx *c, const double *src, float *dst) {
+    c->kernels += 1;
+    const int64_t count = c->n * (int64_t)c->ld;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 152LL * 16));
+    k_unpack_f32<<<g, 256, 0, c->stream>>>(c->n, c->p, c->ld, src, dst);
+}
+
+void launch_pack_f32(ofks_ctx *c, const float *src, double *dst) {
+    c->kernels += 1;
+    const int64_t count = c->n * (int64_t)c->p;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 152LL * 16));
+    k_pack_f32<<<g, 256, 0, c->stream>>>(c->n, c->p, c->ld, src, dst);
+}
+
 void launch_repack(ofks_ctx *c, const double *src, int64_t sp, double *dst, int64_t dp, int64_t n, int w) {
     c->kernels += 1;
     const int64_t count = n * w;

@@ -325,6 +325,9 @@ template <class T> void launch_block_times_small(ofks_ctx *c, const T *X, const 
 template <class S, class T> void launch_convert(ofks_ctx *c, const S *src, T *dst, int64_t count);
 // dst[r dp + j] = src[r sp + j] for r < n, j < w (float64)
 void launch_repack(ofks_ctx *c, const double *src, int64_t sp, double *dst, int64_t dp, int64_t n, int w);
+// the float32 block (n x ld, padding columns zero) from a dense n x p float64 copy, and back
+void launch_unpack_f32(ofks_ctx *c, const double *src, float *dst);
+void launch_pack_f32(ofks_ctx *c, const float *src, double *dst);
 
 // ---- small.cu (p x p work on one CTA)
 void launch_small_update(ofks_ctx *c);

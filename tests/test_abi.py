@@ -52,3 +52,35 @@ def test_missing_library_fails_loudly(tmp_path):
             ofks.load(str(tmp_path / "libofks.so"))
     finally:
         ofks._lib = saved
+
+
+def _struct_fields(name):
+    """(field, C type) of a typedef'd struct of include/ofks.h, in declaration order."""
+    text = open(os.path.join(ROOT, "include", "ofks.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct\s*\{([^{}]*)\}\s*" + name + r"\s*;", text).group(1)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        ctype, names = decl.split(None, 1)
+        for nm in names.split(","):
+            out.append((nm.strip(), ctype))
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [("ofks_params", "Params"), ("ofks_result", "Result")])
+def test_python_structs_mirror_the_header(cname, pyname):
+    # the ctypes structures must list the header's fields in the same order with the same types,
+    # or every field after a mismatch is read at the wrong offset
+    import ctypes as C
+
+    from paper_2007_14228_gb300 import ofks
+    ctype_of = {"int32_t": C.c_int32, "int64_t": C.c_int64, "double": C.c_double, "uint64_t": C.c_uint64}
+    header = _struct_fields(cname)
+    py = getattr(ofks, pyname)._fields_
+    assert [h[0] for h in header] == [f[0] for f in py]
+    for (nm, ct), (_, pt) in zip(header, py):
+        assert ctype_of[ct] is pt, (nm, ct, pt)
+    assert C.sizeof(getattr(ofks, pyname)) % 8 == 0

@@ -11,13 +11,21 @@ Pieces, in the paper's order and notation:
   energy       E_KS = E_kin + E_ext + E_Har + E_xc + E_nuc  (Eq. totalEnergy and the
                discrete traces of Sec. 2.2), with occupation f on the density
   gradient     scaled to H(X) X (end of Sec. 2.2)
-  iteration    Alg. 2 (PCAL):
+  iteration    Alg. 2 (PCAL, ``method='pcal'``):
                  Lambda0 = X^T H X                                    (Eq. multi)
                  Lambda  = Lambda0 + Theta(X^T grad L_beta(X, Lambda0)) (Eq. lambda2)
                  grad L_beta(X, Lambda) = H X - B X Lambda + beta B X (X^T B X - I)
                  D_i = T_i^{-1} grad_i L_beta with T_i = L/2 - Lambda_ii B if Lambda_ii < 0,
                        else I                                      (Eq. precondition-T)
                  X_i <- (X_i - D_i/eta) / ||X_i - D_i/eta||_B      (Eq. PCAL-main)
+               Alg. 1 (PLAM, ``method='plam'``): Lambda = Lambda0 (Eq. multi), the shifts of
+                 Eq. precondition-T from Lambda0, X <- X - D/eta without normalization
+                 (Eq. PLAM-main)
+               MOptQR (``method='moptqr'``, the manifold comparison method of Sec. 5): the
+                 antigradient H X - B X Lambda0 on the B-Stiefel manifold, the same
+                 preconditioner (shifts from Lambda0) and step size, then the step is put back on
+                 the manifold by the Cholesky-based Gram-Schmidt of Sec. 4.2: Y^T B Y = R^T R,
+                 X <- Y R^{-1}
   stopping     kkt = ||H X - B X Lambda0||_F, fea = ||X^T B X - I||_F,
                stop when (kkt + fea)/kkt_0 < tol (Sec. 4.1)
   step size    BB2 (Sec. 4.4) with S = X^k - X^{k-1}; Y is the difference of the directions
@@ -53,6 +61,7 @@ class Params:
     precond: str = "pcg"          # 'none' | 'pcg' | 'exact'
     pcg_iters: int = 8
     eta_rule: str = "bb2"         # 'bb2' | 'bb1' | 'abb1' | 'abb2' | 'bb2_raw' | 'fixed'
+    method: str = "pcal"          # 'pcal' (Alg. 2) | 'plam' (Alg. 1) | 'moptqr' (Sec. 5)
     eta_fixed: float = 0.0        # used when eta_rule == 'fixed'
     eta_min: float = 1e-4
     eta_max: float = 1e8
@@ -243,6 +252,61 @@ def sym(A):
     return 0.5 * (A + A.T)
 
 
+def lagrangian_gradient(HX, BX, Lam, S, beta):
+    """grad_X L_beta(X, Lambda) = H X - B X Lambda + beta B X (X^T B X - I).
+
+    The gradient of the augmented Lagrangian of Eq. (ALM-sub) for symmetric Lambda, in the
+    scaling of the end of Sec. 2.2 where the energy's gradient is H(X) X; S = X^T B X.
+    """
+    return HX - BX @ Lam + beta * BX @ (S - np.eye(S.shape[0]))
+
+
+def theta(M):
+    """Theta(M) = Diag(diag(M)) (notation of Sec. 1)."""
+    return np.diag(np.diag(M))
+
+
+def multipliers(X, HX, BX, Lam0, S, beta):
+    """Eq. (lambda2): Lambda = Lambda0 + Theta(X^T grad_X L_beta(X, Lambda0)), Lambda0 = X^T H X."""
+    return Lam0 + theta(X.T @ lagrangian_gradient(HX, BX, Lam0, S, beta))
+
+
+def initial_eta(D0, X0):
+    """eta_0 = ||D^0||_F / (1e-3 ||X^0||_F): the first step moves X by 1e-3 of its norm.
+
+    The paper does not state eta_0; this is the reading taken.
+    """
+    return float(np.linalg.norm(D0) / (1e-3 * np.linalg.norm(X0)))
+
+
+def step_size(rule, k, Sd, Yd, eta_prev):
+    """eta_k of Sec. 4.4 from S = X^k - X^{k-1} and Y = the difference of the directions.
+
+    BB1: |<S,Y>| / <S,S>;  BB2: <Y,Y> / |<S,Y>|;  ABB1: BB1 for odd k, BB2 for even k;
+    ABB2: BB2 for odd k, BB1 for even k.  'bb2_raw' is BB2 (the caller passes raw-gradient
+    differences).  When <S,Y> = 0 the previous eta is kept (a reading: the paper is silent).
+    """
+    sy, yy, ss = float(np.sum(Sd * Yd)), float(np.sum(Yd * Yd)), float(np.sum(Sd * Sd))
+    if rule == "abb1":
+        rule = "bb1" if k % 2 == 1 else "bb2"
+    elif rule == "abb2":
+        rule = "bb2" if k % 2 == 1 else "bb1"
+    if sy == 0.0:
+        return eta_prev
+    if rule == "bb1":
+        return abs(sy) / ss
+    if rule in ("bb2", "bb2_raw"):
+        return yy / abs(sy)
+    raise ValueError(f"unknown eta rule {rule}")
+
+
+def cholesky_qr(Y, BY):
+    """Cholesky-based Gram-Schmidt (Sec. 4.2): Y^T B Y = R^T R, returns (Y R^{-1}, B Y R^{-1})."""
+    S = Y.T @ BY
+    Rt = np.linalg.cholesky(0.5 * (S + S.T))               # lower factor R^T
+    return np.linalg.solve(Rt, Y.T).T, np.linalg.solve(Rt, BY.T).T
+
+
 def iterate(prob: Problem, st: State) -> dict:
     """One pass of the loop body of Alg. 2 at X^k; updates st in place.
 
@@ -270,37 +334,42 @@ def iterate(prob: Problem, st: State) -> dict:
         rec["eta"] = st.eta
         st.history.append(rec)
         return rec
-    # Eq. (lambda2): Lambda = Lambda0 + Theta(X^T grad L_beta(X, Lambda0))
-    M = Lam0 - S @ Lam0 + prm.beta * S @ (S - I)
-    Lam = Lam0 + np.diag(np.diag(M))
-    # grad_X L_beta(X, Lambda) = H X - B X Lambda + beta B X (S - I)
-    G = HX - BX @ Lam + prm.beta * BX @ (S - I)
+    method = prm.method
+    if method == "pcal":
+        # Eq. (lambda2) and the gradient of L_beta at Lambda
+        Lam = multipliers(X, HX, BX, Lam0, S, prm.beta)
+        G = lagrangian_gradient(HX, BX, Lam, S, prm.beta)
+    elif method == "plam":
+        # Alg. 1: the multipliers of Eq. (multi) in the gradient of Eq. (PLAM-main)
+        Lam = Lam0
+        G = lagrangian_gradient(HX, BX, Lam, S, prm.beta)
+    elif method == "moptqr":
+        # antigradient on the B-Stiefel manifold (no penalty: the iterates stay feasible)
+        Lam = Lam0
+        G = HX - BX @ Lam0
+    else:
+        raise ValueError(f"unknown method {method}")
     D = prob.precondition(G, np.diag(Lam))                 # Eq. (precondition-T)
     # step size (Sec. 4.4)
-    if st.k == 0 or prm.eta_rule == "fixed":
-        eta = prm.eta_fixed if prm.eta_rule == "fixed" else \
-            float(np.linalg.norm(D) / (1e-3 * np.linalg.norm(X)))
+    if prm.eta_rule == "fixed":
+        eta = prm.eta_fixed
+    elif st.k == 0:
+        eta = initial_eta(D, X)
     else:
-        Sd = X - st.X_prev
         Yd = (G - st.G_prev) if prm.eta_rule == "bb2_raw" else (D - st.D_prev)
-        sy, yy, ss = float(np.sum(Sd * Yd)), float(np.sum(Yd * Yd)), float(np.sum(Sd * Sd))
-        rule = prm.eta_rule
-        if rule == "abb1":
-            rule = "bb1" if st.k % 2 == 1 else "bb2"
-        elif rule == "abb2":
-            rule = "bb2" if st.k % 2 == 1 else "bb1"
-        if sy == 0.0:
-            eta = st.eta
-        elif rule == "bb1":
-            eta = abs(sy) / ss
-        else:
-            eta = yy / abs(sy)
+        eta = step_size(prm.eta_rule, st.k, X - st.X_prev, Yd, st.eta)
     eta = float(min(max(eta, prm.eta_min), prm.eta_max))
-    # Eq. (PCAL-main): gradient step then B-normalization of every column
     Y = X - D / eta
-    nrm = np.sqrt(np.sum(Y * (prob.Bf @ Y), axis=0))
+    BY = prob.Bf @ Y
+    if method == "pcal":
+        # Eq. (PCAL-main): B-normalization of every column
+        Xn = Y / np.sqrt(np.sum(Y * BY, axis=0))
+    elif method == "plam":
+        Xn = Y                                             # Eq. (PLAM-main)
+    else:
+        Xn, _ = cholesky_qr(Y, BY)
     st.X_prev, st.D_prev, st.G_prev = X, D, G
-    st.X = Y / nrm
+    st.X = Xn
     st.eta = eta
     st.k += 1
     rec.update({"eta": eta, "Lambda": Lam, "G": G, "D": D})

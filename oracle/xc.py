@@ -11,6 +11,12 @@ available, so the functional is written out from its published definition:
   V_c = eps_c - (r_s / 3) d eps_c / d r_s   (from V = d(rho eps)/d rho).
 
 Densities below RHO_MIN give eps = V = 0.
+
+Pins: the exchange constant of the uniform gas, V = d(rho eps)/d rho, the Gell-Mann-Brueckner
+slope (A), and the two continuity conditions at r_s = 1 by which PZ81 fixed C and D from
+gamma, beta1, beta2, A and B (value and first derivative).  Parity unpinned: the last digit of
+beta1 and of beta2 (a change of about 1e-3 in either keeps C and D within their rounding; no
+published table of eps_c is at hand to fix them further).
 """
 from __future__ import annotations
 

@@ -2,6 +2,7 @@
 import os
 
 import numpy as np
+import pytest
 
 from oracle import xc
 
@@ -41,8 +42,46 @@ def test_pz81_branches_meet_at_rs_one():
     rho1 = 3.0 / (4.0 * np.pi)
     e_lo, v_lo = xc.correlation(np.array([rho1 * (1 + 1e-12)]))   # r_s just below 1
     e_hi, v_hi = xc.correlation(np.array([rho1 * (1 - 1e-12)]))   # r_s just above 1
-    assert abs(e_lo[0] - e_hi[0]) < 1e-4
-    assert abs(v_lo[0] - v_hi[0]) < 1e-4
+    assert abs(e_lo[0] - e_hi[0]) < 5e-5
+    assert abs(v_lo[0] - v_hi[0]) < 5e-5
+
+
+def _branch_slopes_at_rs_one():
+    """d eps_c / d r_s at r_s = 1 from each branch of the oracle (one-sided differences)."""
+    h = 1e-6
+    rs = np.array([1.0 - 2 * h, 1.0 - h, 1.0 + h, 1.0 + 2 * h])
+    e, _ = xc.correlation(3.0 / (4.0 * np.pi * rs ** 3))
+    return (e[1] - e[0]) / h, (e[3] - e[2]) / h      # high-density branch, low-density branch
+
+
+def check_pz81_continuity_constants():
+    # Perdew and Zunger chose C and D so that eps_c and its first derivative are continuous at
+    # r_s = 1 (Phys. Rev. B 23, 5048, 1981); solving those two conditions with the oracle's
+    # gamma, beta1, beta2, A, B must give its C and D to their published four decimals.
+    g, b1, b2, A, B = xc.PZ_GAMMA, xc.PZ_BETA1, xc.PZ_BETA2, xc.PZ_A, xc.PZ_B
+    den = 1.0 + b1 + b2
+    eps1 = g / den
+    deps1 = -g * (b1 / 2.0 + b2) / den ** 2
+    D = eps1 - B
+    C = deps1 - A - D
+    assert abs(C - xc.PZ_C) <= 5e-5, (C, xc.PZ_C)
+    assert abs(D - xc.PZ_D) <= 5e-5, (D, xc.PZ_D)
+    # and the oracle's two branches have slopes that meet at r_s = 1 to the constants' rounding
+    s_hi, s_lo = _branch_slopes_at_rs_one()
+    assert abs(s_hi - s_lo) < 3e-5, (s_hi, s_lo)
+
+
+def test_pz81_high_density_constants_follow_from_continuity():
+    check_pz81_continuity_constants()
+
+
+@pytest.mark.parametrize("name,value", [("PZ_GAMMA", -0.1432), ("PZ_GAMMA", -0.1424), ("PZ_BETA1", 1.0592),
+                                        ("PZ_BETA2", 0.3434), ("PZ_BETA2", 0.3324), ("PZ_A", 0.0313),
+                                        ("PZ_C", 0.0002), ("PZ_D", -0.0161), ("PZ_D", -0.0106)])
+def test_pz81_continuity_pin_catches_planted_typos(monkeypatch, name, value):
+    monkeypatch.setattr(xc, name, value)
+    with pytest.raises(AssertionError):
+        check_pz81_continuity_constants()
 
 
 def test_correlation_high_density_slope():

@@ -56,6 +56,17 @@ extern "C" {
 #define OFKS_ETA_BB2_RAW   4   /* BB2 with differences of the raw gradients grad L_beta */
 #define OFKS_ETA_FIXED     5   /* eta = eta_fixed every iteration */
 
+/* the iteration (ofks_params.method) */
+#define OFKS_METHOD_PCAL   0   /* Alg. 2: multipliers of Eq. (lambda2), column B-normalization
+                                  (Eq. PCAL-main) */
+#define OFKS_METHOD_PLAM   1   /* Alg. 1: multipliers of Eq. (multi), plain step X - D/eta
+                                  (Eq. PLAM-main), no normalization */
+#define OFKS_METHOD_MOPTQR 2   /* the manifold comparison method of Sec. 5: antigradient
+                                  H X - B X X^T H X, the same preconditioner and step size, then the
+                                  Cholesky-based Gram-Schmidt of Sec. 4.2 (Y^T B Y = R^T R,
+                                  X <- Y R^{-1}): every iterate is B-orthonormal, at the cost of a
+                                  p x p Cholesky factorization per iteration */
+
 /* which fields ofks_get_field() copies out */
 #define OFKS_F_RHO_Q       0   /* density at quadrature points, n_tets*4 */
 #define OFKS_F_VH_Q        1   /* Hartree potential at quadrature points, n_tets*4 */
@@ -132,6 +143,9 @@ typedef struct {
                                CG between residual checks) are captured once as CUDA graphs and
                                replayed; 0: every kernel is launched on its own.  Graphs are not
                                used while ofks_profile is on */
+    int32_t method;         /* OFKS_METHOD_PCAL (default), OFKS_METHOD_PLAM or OFKS_METHOD_MOPTQR; the
+                               stopping test (Sec. 4.1), the preconditioner (Eq. precondition-T, its
+                               shifts from the method's multipliers) and eta are common to all three */
 } ofks_params;
 
 typedef struct {
@@ -159,7 +173,7 @@ typedef struct {
  * iterations, BB2, eta in [1e-4, 1e8], Hartree and LDA on, multipole_lmax 2,
  * poisson_tol 1e-12, poisson_max_iter 20000, poisson_pc OFKS_HPC_SEPARABLE, mixed_tol 1e-5, poisson_tol_mixed
  * 1e-8, judge_tau 0.5, learned_tc 1, poisson_adaptive 0, poisson_csr 0, gram_tc 1, spmm_f32_rows 0,
- * poisson_sep_tc 1, pcg_compact 1, cuda_graphs 1.  p is
+ * poisson_sep_tc 1, pcg_compact 1, cuda_graphs 1, method OFKS_METHOD_PCAL.  p is
  * set to 1. */
 void ofks_default_params(ofks_params *prm);
 
@@ -199,9 +213,10 @@ int ofks_set_nuclei(ofks_ctx *ctx, int32_t M, const double *Z, const double *R);
  * nuclear data is staged in a fixed array compiled into the library (OFKS_STATIC_NUCLEI_MAX
  * nuclei, 32 KiB per GPU that loads the library, held until the process exits) instead of
  * memory allocated per call.  Same arguments, results and errors as ofks_set_nuclei, plus
- * OFKS_EINVAL when M > OFKS_STATIC_NUCLEI_MAX.  The first call on a device looks up the array's
- * device address, so make that first call before any stream capture.  All contexts share the
- * array: calls whose work overlaps on the GPU (contexts driven concurrently) race. */
+ * OFKS_EINVAL when M > OFKS_STATIC_NUCLEI_MAX.  ofks_create looks up the array's device address
+ * on its device and keeps it in the context, so this call itself neither allocates nor looks
+ * anything up.  All contexts share the array, which keeps the last call's contents: calls whose
+ * work overlaps on the GPU (contexts driven concurrently) race. */
 int ofks_set_nuclei_static(ofks_ctx *ctx, int32_t M, const double *Z, const double *R);
 
 /* Parameters; p must satisfy 1 <= p <= n_free.  Changing p drops the orbitals.
@@ -237,7 +252,9 @@ int ofks_solve(ofks_ctx *ctx, ofks_result *res);
 
 /* Evaluate the current iterate without updating it: density, Hartree and xc potentials,
  * H(X), H X, B X, the Grams, E, kkt, fea, the multipliers of Eq. (lambda2) and the
- * gradient; fields are then readable with ofks_get_field(). */
+ * gradient; fields are then readable with ofks_get_field().  Errors: OFKS_ETIMEOUT when a
+ * bounded wait of the tensor-core Gram or gradient gave up (the fields are then not valid; the
+ * status is cleared, so the next call starts clean), OFKS_ENONFINITE, OFKS_ECUDA. */
 int ofks_evaluate(ofks_ctx *ctx, ofks_result *res);
 
 /* Post-processing (paper Sec. 4.3): the p x p generalized eigenproblem
@@ -320,8 +337,9 @@ int ofks_precond_grads(ofks_ctx *ctx, const double *G, const double *shifts, con
 /* Checkpoint: X, X_prev, D_prev, G_prev, eta, k, kkt0 and the Hartree warm start U, restored
  * exactly on load, so a reloaded run continues from the same state (later iterates agree up to
  * the order of the device's floating-point atomics).  The mesh, nuclei and params must match
- * on load.  Errors: OFKS_EINVAL (path cannot be opened or the file does not match the context's
- * sizes), OFKS_ESTATE (no orbitals to save), OFKS_ECUDA. */
+ * on load.  Errors: OFKS_EINVAL (path cannot be opened, or the file does not match the context's
+ * sizes or its own header's history length), OFKS_ENOMEM (host buffers), OFKS_ESTATE (no
+ * orbitals to save), OFKS_ECUDA. */
 int ofks_save_state(ofks_ctx *ctx, const char *path);
 int ofks_load_state(ofks_ctx *ctx, const char *path);
 

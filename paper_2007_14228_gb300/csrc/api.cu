@@ -13,6 +13,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <new>
 #include <vector>
 
 #include "common.cuh"
@@ -286,9 +287,17 @@ static int evaluate_t(ofks_ctx *c, bool need_bx, Rec *out) {
     launch_grad_update(c, b);
     launch_small_record(c);
     double h[4];
+    int tc_flag = 0;                             // a tensor-core Gram or gradient whose bounded wait gave up
     cudaError_t e = cudaMemcpyAsync(h, c->d_rec, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&tc_flag, c->d_flag + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if ((rc = ofks_cuda_check(c, e, "evaluate"))) return rc;
+    if (tc_flag) {
+        e = cudaMemsetAsync(c->d_flag + 2, 0, sizeof(int), c->stream);
+        if ((rc = ofks_cuda_check(c, e, "evaluate"))) return rc;
+        c->evaluated = false;
+        return ofks_fail(c, OFKS_ETIMEOUT, "tensor-core Gram or gradient: a bounded wait timed out");
+    }
     out->E = h[0]; out->fea = h[1]; out->kkt = h[2];
     c->evaluated = true;
     c->last_E = h[0]; c->last_fea = h[1]; c->last_kkt = h[2];
@@ -467,21 +476,45 @@ static int update_step_t(ofks_ctx *c) {
     if ((rc = precondition_t<T>(c))) return rc;
     launch_bb_dots(c, b, c->prm.eta_rule == OFKS_ETA_BB2_RAW);
     launch_eta(c);
-    T *Y = b.X[prv];
+    const int method = c->prm.method;
+    // the new iterate goes to the other slot (the current one stays as X^{k-1} for the BB step);
+    // MOptQR forms Y and B Y in scratch blocks and writes Y R^{-1}, B Y R^{-1} into place
+    T *Y = method == OFKS_METHOD_MOPTQR ? b.W : b.X[prv];
+    T *BY = method == OFKS_METHOD_MOPTQR ? b.Q : b.BX;
     {
         ProfScope ps(c, PF_STEP);
         launch_step_y(c, b, Y);
     }
-    cudaMemsetAsync(c->d_colA + CB_NORM * ld, 0, sizeof(double) * ld, c->stream);
-    {
-        ProfScope ps(c, PF_SPMM_B);
-        launch_sell_spmm_colnorm(c, vals_B<T>(c), (const T *)Y, b.BX, c->d_colA + CB_NORM * ld);
-    }
-    {
+    if (method == OFKS_METHOD_PCAL) {
+        // Eq. (PCAL-main): B Y with the column B-norms, then X = Y / ||Y||_B column by column
+        cudaMemsetAsync(c->d_colA + CB_NORM * ld, 0, sizeof(double) * ld, c->stream);
+        {
+            ProfScope ps(c, PF_SPMM_B);
+            launch_sell_spmm_colnorm(c, vals_B<T>(c), (const T *)Y, b.BX, c->d_colA + CB_NORM * ld);
+        }
         ProfScope ps(c, PF_STEP);
         launch_scale_cols(c, Y, b.BX, c->d_colA + CB_NORM * ld);
+    } else {
+        {
+            ProfScope ps(c, PF_SPMM_B);
+            launch_sell_spmm(c, vals_B<T>(c), (const T *)Y, BY);
+        }
+        if (method == OFKS_METHOD_MOPTQR) {
+            // Cholesky-based Gram-Schmidt (Sec. 4.2): Y^T B Y = R^T R, X = Y R^{-1}, B X = B Y R^{-1}
+            double *Rinv = c->d_pp + 6 * (size_t)ld * ld, *SY = c->d_pp + 2 * (size_t)ld * ld;
+            launch_gram2(c, (const T *)Y, (const T *)BY, (const T *)BY, SY, SY + (size_t)ld * ld);
+            launch_cholesky_inv(c, SY, Rinv);
+            ProfScope ps(c, PF_STEP);
+            launch_block_times_small(c, (const T *)Y, Rinv, b.X[prv]);
+            launch_block_times_small(c, (const T *)BY, Rinv, b.BX);
+        }
     }
     if ((rc = ofks_cuda_check(c, cudaGetLastError(), "update step"))) return rc;
+    if (method == OFKS_METHOD_MOPTQR) {
+        int flag = 0;
+        if ((rc = read_flag(c, &flag))) return rc;
+        if (flag) return ofks_fail(c, OFKS_ENOTCONV, "MOptQR: Y^T B Y is not positive definite");
+    }
     double eta;
     cudaError_t e = cudaMemcpyAsync(&eta, c->d_sc + SC_ETA, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -570,6 +603,7 @@ void ofks_default_params(ofks_params *p) {
     p->mixed_tol = 1e-5; p->poisson_tol_mixed = 1e-8;
     p->judge_tau = 0.5; p->learned_tc = 1; p->poisson_adaptive = 0; p->poisson_csr = 0; p->gram_tc = 1;
     p->poisson_sep_tc = 1; p->spmm_f32_rows = 0; p->pcg_compact = 1; p->cuda_graphs = 1;
+    p->method = OFKS_METHOD_PCAL;
 }
 
 int ofks_create(ofks_ctx **out, int device) {
@@ -587,6 +621,8 @@ int ofks_create(ofks_ctx **out, int device) {
     if (e == cudaSuccess) e = cudaMemset(c->d_sc, 0, sizeof(double) * SC_COUNT);
     if (e == cudaSuccess) e = cudaMemset(c->d_rec, 0, sizeof(double) * 8);
     if (e == cudaSuccess) e = cudaMemset(c->d_flag, 0, sizeof(int) * 4);
+    // device address of the no-allocation staging array, looked up with this device current
+    if (e == cudaSuccess) e = static_stage_lookup(c);
     if (e != cudaSuccess) {
         ofks_destroy(c);
         return OFKS_ECUDA;
@@ -664,7 +700,8 @@ int ofks_set_params(ofks_ctx *c, const ofks_params *prm) {
         (prm->precision != OFKS_FP64 && prm->precision != OFKS_MIXED) || !(prm->mixed_tol > 0) ||
         !(prm->poisson_tol_mixed > 0) || !(prm->eta_min > 0) || !(prm->eta_max >= prm->eta_min) ||
         prm->multipole_lmax < -1 || prm->multipole_lmax > 2 || !(prm->poisson_tol > 0) ||
-        prm->poisson_max_iter < 1 || prm->poisson_pc < 0 || prm->poisson_pc > OFKS_HPC_SEPARABLE || (prm->eta_rule == OFKS_ETA_FIXED && !(prm->eta_fixed > 0)))
+        prm->poisson_max_iter < 1 || prm->poisson_pc < 0 || prm->poisson_pc > OFKS_HPC_SEPARABLE || (prm->eta_rule == OFKS_ETA_FIXED && !(prm->eta_fixed > 0)) ||
+        prm->method < OFKS_METHOD_PCAL || prm->method > OFKS_METHOD_MOPTQR)
         return ofks_fail(c, OFKS_EINVAL, "set_params: a parameter is out of range");
     cudaSetDevice(c->device);
     const bool mixed = prm->precision == OFKS_MIXED;
@@ -971,8 +1008,27 @@ int ofks_load_state(ofks_ctx *c, const char *path) {
         return ofks_fail(c, OFKS_EINVAL, "load_state: sizes differ from the current mesh/params");
     }
     const size_t blk = (size_t)c->n * c->ld;
-    std::vector<double> buf(blk * 5 + c->n_nodes);
-    std::vector<double> hist((size_t)h.hist_rows * 6);
+    // the history length must be what the file's size leaves after the header and the blocks
+    const int64_t body = (int64_t)sizeof(double) * (int64_t)(blk * 5 + c->n_nodes);
+    int64_t fsize = -1;
+    if (fseek(f, 0, SEEK_END) == 0) fsize = (int64_t)ftell(f);
+    if (fsize < 0 || fseek(f, (long)sizeof(h), SEEK_SET) != 0) {
+        fclose(f);
+        return ofks_fail(c, OFKS_EINVAL, "load_state: cannot size %s", path);
+    }
+    if (h.hist_rows < 0 || (int64_t)sizeof(h) + body + h.hist_rows * 6 * (int64_t)sizeof(double) != fsize) {
+        fclose(f);
+        return ofks_fail(c, OFKS_EINVAL, "load_state: %s has %lld bytes, not what its header describes", path,
+                         (long long)fsize);
+    }
+    std::vector<double> buf, hist;
+    try {
+        buf.resize(blk * 5 + c->n_nodes);
+        hist.resize((size_t)h.hist_rows * 6);
+    } catch (const std::bad_alloc &) {
+        fclose(f);
+        return ofks_fail(c, OFKS_ENOMEM, "load_state: host buffers");
+    }
     bool ok = fread(buf.data(), sizeof(double), buf.size(), f) == buf.size() &&
               fread(hist.data(), sizeof(double), hist.size(), f) == hist.size();
     fclose(f);

@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(256, 1) k_grad_tc(int64_t n, int p, int ld, in
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(RTM >> 4) << 24);
     const uint32_t sbo = (uint32_t)(KP >> 3) * 128u;
     double part = 0.0;
+    int mma_out = 0;                             // this thread saw tile t's MMAs time out (still in flight)
     int t = 0;
     for (; t < T; ++t) {
         const int buf = t & 1;
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(256, 1) k_grad_tc(int64_t n, int p, int ld, in
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 r32(&bar_mma)));
         }
-        if (!rwait(&bar_mma, (uint32_t)(t & 1))) abort_flag = 1;
+        if (!rwait(&bar_mma, (uint32_t)(t & 1))) { abort_flag = 1; mma_out = 1; }
         __syncthreads();
         if (abort_flag) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
@@ -233,6 +234,9 @@ __global__ void __launch_bounds__(256, 1) k_grad_tc(int64_t n, int p, int ld, in
             atomicExch(err, 1);
             for (int b = 0; b < 2; ++b)
                 if (pending[b]) rwait(&bar_ld[b], (uint32_t)(((t + (b != (t & 1))) >> 1) & 1));
+            // MMAs whose commit timed out may still read shared memory and write tensor memory:
+            // wait once more (bounded) before the tensor memory is released
+            if (mma_out) rwait(&bar_mma, (uint32_t)(t & 1));
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");

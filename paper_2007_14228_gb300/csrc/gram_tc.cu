@@ -193,6 +193,10 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(int64_t n, int p, int ld, in
         if (tid == 0)
             for (int b = 0; b < 2; ++b)
                 if (pending[b]) bar_wait(&bar_ld[b], (uint32_t)(((t + (b != (t & 1))) >> 1) & 1));
+        // so may the MMAs of the last committed slab (slabs 0 .. t-1 were committed; the earlier
+        // ones were waited for): wait for that commit once more (bounded) before the tensor
+        // memory is released
+        if (tid == 0 && t > 0) bar_wait(&bar_mma, (uint32_t)((t - 1) & 1));
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();

@@ -188,6 +188,7 @@ struct ofks_ctx {
     double *d_sc = nullptr;                      // SC_COUNT scalars
     double *d_rec = nullptr;                     // iteration record (device)
     int *d_flag = nullptr;                       // error / status flags
+    double *nuclei_stage = nullptr;              // device address of the no-allocation nuclei staging array
 
     // ---- iteration state (host mirror)
     bool have_X = false, evaluated = false, have_prev = false;
@@ -251,6 +252,7 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets,
                const int64_t *tet10, const uint8_t *dirichlet);
 int setup_nuclei(ofks_ctx *c, int M, const double *Z, const double *R);
 int setup_nuclei_static(ofks_ctx *c, int M, const double *Z, const double *R);
+cudaError_t static_stage_lookup(ofks_ctx *c);
 void free_mesh(ofks_ctx *c);
 
 // ---- stencil.cu (lattice form of the Hartree stiffness)

@@ -6,7 +6,6 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
-#include <mutex>
 #include <numeric>
 #include <thread>
 #include <vector>
@@ -558,37 +557,19 @@ int setup_nuclei(ofks_ctx *c, int M, const double *Z, const double *R) {
 // array, so the call allocates nothing.  Every GPU that loads the library holds the array
 // (32 KiB) until the process exits; all calls share it, so calls that overlap on the GPU
 // (different contexts on different streams) race on its contents.
-namespace {
-
 static __device__ __align__(256) double g_nuclei_stage[4 * OFKS_STATIC_NUCLEI_MAX + 1];
 
-constexpr int kStageDevices = 64;
-std::mutex g_stage_mu;
-double *g_stage_ptr[kStageDevices] = {nullptr};
-
-// Device address of the staging array on the context's device.  The first call on a device
-// looks it up with that device current (the host-side symbol is only a stand-in, never a device
-// address); later calls reuse it.
-int stage_address(ofks_ctx *c, double **out) {
-    if (c->device < 0 || c->device >= kStageDevices)
-        return ofks_fail(c, OFKS_EINVAL, "set_nuclei_static: device %d out of range", c->device);
-    std::lock_guard<std::mutex> lock(g_stage_mu);
-    if (!g_stage_ptr[c->device]) {
-        double *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress((void **)&ptr, g_nuclei_stage);
-        if (e != cudaSuccess) return ofks_cuda_check(c, e, "set_nuclei_static: cudaGetSymbolAddress");
-        g_stage_ptr[c->device] = ptr;
-    }
-    *out = g_stage_ptr[c->device];
-    return OFKS_OK;
+// Device address of the staging array on the context's device, looked up once per context by
+// ofks_create with that device current (in host code the symbol is only a stand-in, never a
+// device address).  Kept in the context, whose lifetime lies within one live CUDA context, so a
+// later context after a device reset looks the address up again.
+cudaError_t static_stage_lookup(ofks_ctx *c) {
+    return cudaGetSymbolAddress((void **)&c->nuclei_stage, g_nuclei_stage);
 }
 
-}  // namespace
-
 int setup_nuclei_static(ofks_ctx *c, int M, const double *Z, const double *R) {
-    double *stage = nullptr;
-    int rc = stage_address(c, &stage);
-    if (rc) return rc;
+    double *stage = c->nuclei_stage;
+    if (!stage) return ofks_fail(c, OFKS_ESTATE, "set_nuclei_static: no staging address (context not created)");
     double *e_slot = stage + 4 * OFKS_STATIC_NUCLEI_MAX;
     // Z[j] -> stage[4j], R[j] -> stage[4j+1 .. 4j+3]: strided copies, no host staging buffer
     cudaError_t e = cudaMemcpy2DAsync(stage, 4 * sizeof(double), Z, sizeof(double), sizeof(double), (size_t)M,

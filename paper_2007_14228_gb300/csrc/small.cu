@@ -1,6 +1,7 @@
 // p x p work of one PCAL iteration and of the set-up / post-processing, each on a single CTA:
-//   * multipliers Lambda = Lambda0 + Theta(Lambda0 - S Lambda0 + beta S (S - I))  (Eq. lambda2),
-//     C = beta (S - I) - Lambda, preconditioner shifts (Eq. precondition-T), fea and E
+//   * multipliers Lambda = Lambda0 + Theta(Lambda0 - S Lambda0 + beta S (S - I))  (Eq. lambda2;
+//     Lambda = Lambda0 for PLAM, Eq. multi, and MOptQR), C = beta (S - I) - Lambda (C = -Lambda0 for
+//     MOptQR), preconditioner shifts (Eq. precondition-T), fea and E
 //   * the step parameter eta (Barzilai-Borwein, Sec. 4.4)
 //   * Cholesky S = R^T R and R^{-1} for the initial guess (Sec. 4.2)
 //   * Rayleigh-Ritz (Sec. 4.3): Cholesky, R^{-T} A R^{-1}, parallel cyclic Jacobi, V = R^{-1} W
@@ -11,10 +12,15 @@
 
 namespace {
 
+// method: OFKS_METHOD_PCAL adds Theta(.) to Lambda0 (Eq. lambda2); PLAM keeps Lambda = Lambda0
+// (Eq. multi); MOptQR keeps Lambda = Lambda0 and has no penalty, so C = -Lambda0 and the gradient
+// is the antigradient H X - B X Lambda0
 __global__ void __launch_bounds__(256) k_small_update(int p, int ld, const double *__restrict__ L0,
-                                                      const double *__restrict__ S, double beta, int precond,
-                                                      double occ, double e_nuc, const double *sc, double *Lam,
-                                                      double *C, double *cb, double *rec) {
+                                                      const double *__restrict__ S, double beta, int method,
+                                                      int precond, double occ, double e_nuc, const double *sc,
+                                                      double *Lam, double *C, double *cb, double *rec) {
+    const bool theta_on = method == OFKS_METHOD_PCAL;
+    const double beta_c = method == OFKS_METHOD_MOPTQR ? 0.0 : beta;
     __shared__ double red[8];
     double fea2 = 0.0, tr = 0.0;
     for (int idx = threadIdx.x; idx < ld * ld; idx += blockDim.x) {
@@ -23,8 +29,8 @@ __global__ void __launch_bounds__(256) k_small_update(int p, int ld, const doubl
         const double sij = S[idx] - (i == j ? 1.0 : 0.0);
         fea2 += sij * sij;
         double lam = L0[idx];
-        if (i == j) {
-            tr += lam;
+        if (i == j) tr += lam;
+        if (i == j && theta_on) {
             // diagonal of Lambda0 - S Lambda0 + beta S (S - I)
             double sl = 0.0, ss = 0.0;
             for (int k = 0; k < p; ++k) {
@@ -35,7 +41,7 @@ __global__ void __launch_bounds__(256) k_small_update(int p, int ld, const doubl
             lam += L0[idx] - sl + beta * ss;
         }
         Lam[idx] = lam;
-        C[idx] = beta * sij - lam;
+        C[idx] = beta_c * sij - lam;
     }
     fea2 = block_sum(fea2, red);
     tr = block_sum(tr, red);
@@ -272,7 +278,7 @@ __global__ void __launch_bounds__(512) k_rayleigh_ritz(int p, int ld, const doub
 
 void launch_small_update(ofks_ctx *c) { c->kernels += 1;
     ProfScope ps(c, PF_SMALL);
-    k_small_update<<<1, 256, 0, c->stream>>>(c->p, c->ld, c->d_L0, c->d_S, c->prm.beta,
+    k_small_update<<<1, 256, 0, c->stream>>>(c->p, c->ld, c->d_L0, c->d_S, c->prm.beta, c->prm.method,
                                              c->prm.precond != OFKS_PC_NONE ? 1 : 0, c->prm.occ, c->e_nuc,
                                              c->d_sc, c->d_Lam, c->d_C, c->d_colA, c->d_rec);
 }

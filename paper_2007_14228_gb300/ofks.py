@@ -17,6 +17,7 @@ OK, EINVAL, ECUDA, ENOMEM, ESTATE, ENOTCONV, ENONFINITE, ETIMEOUT = 0, -1, -2, -
 PC = {"none": 0, "pcg": 1, "exact": 2, "learned": 3}
 PRECISION = {"fp64": 0, "mixed": 1}
 ETA = {"bb2": 0, "bb1": 1, "abb1": 2, "abb2": 3, "bb2_raw": 4, "fixed": 5}
+METHOD = {"pcal": 0, "plam": 1, "moptqr": 2}
 HPC = {"jacobi": 0, "multigrid": 1, "separable": 2}        # Hartree CG preconditioners
 HPC_NAMES = {v: k for k, v in HPC.items()}
 FIELDS = {"rho_q": 0, "vh_q": 1, "vxc_q": 2, "exc_q": 3, "U": 4, "HX": 5, "BX": 6, "G": 7, "D": 8,
@@ -47,7 +48,7 @@ class Params(C.Structure):
                 ("poisson_tol_mixed", C.c_double), ("judge_tau", C.c_double), ("learned_tc", C.c_int32),
                 ("poisson_adaptive", C.c_int32), ("poisson_csr", C.c_int32),
                 ("gram_tc", C.c_int32), ("spmm_f32_rows", C.c_int32), ("poisson_sep_tc", C.c_int32),
-                ("pcg_compact", C.c_int32), ("cuda_graphs", C.c_int32)]
+                ("pcg_compact", C.c_int32), ("cuda_graphs", C.c_int32), ("method", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -133,6 +134,8 @@ def default_params(**overrides) -> Params:
             v = PRECISION[v]
         if k == "poisson_pc" and isinstance(v, str):
             v = HPC[v]
+        if k == "method" and isinstance(v, str):
+            v = METHOD[v]
         if isinstance(v, bool):
             v = int(v)
         setattr(prm, k, v)

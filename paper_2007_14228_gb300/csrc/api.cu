@@ -133,6 +133,8 @@ static void free_blocks(ofks_ctx *c) {
     free_set(c->b64);
     free_set(c->b32);
     dfree(c->d_L0); dfree(c->d_S); dfree(c->d_Lam); dfree(c->d_C); dfree(c->d_colA); dfree(c->d_pp); dfree(c->d_stage);
+    dfree(c->d_cpart);
+    c->cpart_cap = 0;
     dfree(c->d_colC); dfree(c->d_cmap);
     c->p = c->ld = 0;
     c->have_X = c->evaluated = c->have_prev = false;
@@ -185,6 +187,14 @@ static int alloc_blocks(ofks_ctx *c, int p, bool mixed) {
     if (ld != p && cudaMalloc((void **)&c->d_stage, sizeof(double) * (size_t)c->n * p) != cudaSuccess) {
         free_blocks(c);
         return ofks_fail(c, OFKS_ENOMEM, "host-copy staging block");
+    }
+    // per-column partials: one per (column, slice group) for the SELL kernels (at most one group
+    // per slice), and room for the Grams' per-split tiles
+    c->cpart_cap = std::max<int64_t>((int64_t)ld * (std::max<int64_t>(c->n_slices, c->n_tslices) + 64),
+                                     CPART_MIN);
+    if (cudaMalloc((void **)&c->d_cpart, sizeof(double) * (size_t)c->cpart_cap) != cudaSuccess) {
+        free_blocks(c);
+        return ofks_fail(c, OFKS_ENOMEM, "reduction partials");
     }
     c->p = p;
     c->ld = ld;
@@ -431,9 +441,9 @@ static int precondition_t(ofks_ctx *c) {
             }
             {
                 ProfScope ps(c, PF_PCG_UPDATE);
-                launch_pcg_alpha(c, w, v.cb);
+                launch_pcg_alpha(c, w, v.pc, v.cb);
                 launch_pcg_update(c, b, v, !L.exact && it + 1 == L.max_it);
-                launch_pcg_beta(c, w, v.cb);
+                launch_pcg_beta(c, w, v.pc, v.cb);
             }
         }
     };
@@ -621,6 +631,9 @@ int ofks_create(ofks_ctx **out, int device) {
     if (e == cudaSuccess) e = cudaMemset(c->d_sc, 0, sizeof(double) * SC_COUNT);
     if (e == cudaSuccess) e = cudaMemset(c->d_rec, 0, sizeof(double) * 8);
     if (e == cudaSuccess) e = cudaMemset(c->d_flag, 0, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_gpart, sizeof(double) * GACC_CAP);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_gcount, sizeof(unsigned) * 4);
+    if (e == cudaSuccess) e = cudaMemset(c->d_gcount, 0, sizeof(unsigned) * 4);
     // device address of the no-allocation staging array, looked up with this device current
     if (e == cudaSuccess) e = static_stage_lookup(c);
     if (e != cudaSuccess) {
@@ -638,7 +651,7 @@ void ofks_destroy(ofks_ctx *c) {
     free_blocks(c);
     free_mesh(c);
     clear_graphs(c);
-    dfree(c->d_sc); dfree(c->d_rec); dfree(c->d_flag); dfree(c->d_shift_in);
+    dfree(c->d_sc); dfree(c->d_rec); dfree(c->d_flag); dfree(c->d_shift_in); dfree(c->d_gpart); dfree(c->d_gcount);
     for (auto &pe : c->prof_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     if (c->stream) cudaStreamDestroy(c->stream);

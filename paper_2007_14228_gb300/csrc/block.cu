@@ -18,15 +18,19 @@ namespace {
 // computed, numbered consecutively so that whole warps stay idle when there are fewer of them
 // than threads (a float64 warp instruction costs the same however many lanes are active).
 // Rows are staged KR at a time in shared memory.
+// The block's partial tile (its split of the rows) goes to part, entry-major: the value of
+// tile entry (m, a, b) of tile pair q at part[((q 2 + m) TS + a) TS + b) splits + split], and
+// k_gram_fin adds the splits in order.
 template <class T, int RT>
 __global__ void __launch_bounds__(256) k_gram2(int64_t n, int p, int ld, int ntile,
                                                const T *__restrict__ X,
                                                const T *__restrict__ A,
-                                               const T *__restrict__ B, double *XA, double *XB,
+                                               const T *__restrict__ B, double *part,
                                                int64_t rows_per_split) {
     constexpr int TS = 16 * RT, KR = 16;
     __shared__ T xs[KR][TS], as[KR][TS], bs[KR][TS];
     // decode the upper-triangular tile pair
+    const int q = blockIdx.x;
     int pair = blockIdx.x, ti = 0;
     while (pair >= ntile - ti) { pair -= ntile - ti; ++ti; }
     const int tj = ti + pair;
@@ -81,14 +85,15 @@ __global__ void __launch_bounds__(256) k_gram2(int64_t n, int p, int ld, int nti
         __syncthreads();
     }
     if (!act) return;
+    const int64_t S = gridDim.y;
 #pragma unroll
     for (int a = 0; a < RT; ++a)
 #pragma unroll
         for (int b = 0; b < RT; ++b) {
-            const int i = i0 + bi * RT + a, j = j0 + bj * RT + b;
+            const int la = bi * RT + a, lb = bj * RT + b, i = i0 + la, j = j0 + lb;
             if (i < p && j < p && i <= j) {
-                atomicAdd(XA + (int64_t)i * ld + j, (double)ca[a][b]);
-                atomicAdd(XB + (int64_t)i * ld + j, (double)cb[a][b]);
+                part[(((int64_t)q * 2 * TS + la) * TS + lb) * S + blockIdx.y] = (double)ca[a][b];
+                part[((((int64_t)q * 2 + 1) * TS + la) * TS + lb) * S + blockIdx.y] = (double)cb[a][b];
             }
         }
 }
@@ -102,8 +107,9 @@ constexpr int GM_T = 64, GM_KR = 32;
 
 __global__ void __launch_bounds__(256) k_gram_f32w(int64_t n, int p, int ld, int ntile, const float *__restrict__ X,
                                                    const float *__restrict__ A, const float *__restrict__ B,
-                                                   double *XA, double *XB, int64_t rows_per_split) {
+                                                   double *part, int64_t rows_per_split) {
     __shared__ __align__(16) float xs[GM_KR][GM_T], as[GM_KR][GM_T], bs[GM_KR][GM_T];
+    const int qp = blockIdx.x;
     int pair = blockIdx.x, ti = 0;
     while (pair >= ntile - ti) { pair -= ntile - ti; ++ti; }
     const int tj = ti + pair;
@@ -161,25 +167,44 @@ __global__ void __launch_bounds__(256) k_gram_f32w(int64_t n, int p, int ld, int
                 }
         }
     }
+    const int64_t S = gridDim.y;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const int i = i0 + 4 * ty + a, j = j0 + 4 * tx + b;
+            const int la = 4 * ty + a, lb = 4 * tx + b, i = i0 + la, j = j0 + lb;
             if (i < p && j < p && i <= j) {
-                atomicAdd(XA + (int64_t)i * ld + j, (double)ca[a][b]);
-                atomicAdd(XB + (int64_t)i * ld + j, (double)cb[a][b]);
+                part[(((int64_t)qp * 2 * GM_T + la) * GM_T + lb) * S + blockIdx.y] = (double)ca[a][b];
+                part[((((int64_t)qp * 2 + 1) * GM_T + la) * GM_T + lb) * S + blockIdx.y] = (double)cb[a][b];
             }
         }
 }
 
-__global__ void k_mirror2(int p, int ld, double *A, double *B) {
-    for (int idx = threadIdx.x + blockIdx.x * blockDim.x; idx < p * p; idx += blockDim.x * gridDim.x) {
-        const int i = idx / p, j = idx % p;
-        if (i > j) {
-            A[(int64_t)i * ld + j] = A[(int64_t)j * ld + i];
-            B[(int64_t)i * ld + j] = B[(int64_t)j * ld + i];
-        }
+// The Grams from the split partials: one warp per upper entry (m, i <= j < p) adds its units
+// (splits) in order (lanes stride, then a fixed butterfly) and writes the entry and its mirror.
+// Tiles of TS x TS, ntile per side, pairs numbered row by row over the upper triangle.
+__global__ void __launch_bounds__(256) k_gram_fin(int p, int ld, int TS, int ntile, int64_t units,
+                                                  const double *__restrict__ part, double *XA, double *XB) {
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t nup = (int64_t)p * (p + 1) / 2;
+    if (w >= 2 * nup) return;
+    const int m = (int)(w / nup);
+    int64_t r = w - m * nup;
+    int i = 0;
+    while (r >= p - i) { r -= p - i; ++i; }
+    const int j = i + (int)r;
+    const int ti = i / TS, tj = j / TS;
+    const int64_t q = (int64_t)ti * ntile - (int64_t)ti * (ti - 1) / 2 + (tj - ti);
+    const int64_t e = ((q * 2 + m) * TS + (i - ti * TS)) * TS + (j - tj * TS);
+    const double *a = part + e * units;
+    double s = 0.0;
+    for (int64_t u = lane; u < units; u += 32) s += __ldcg(a + u);
+    s = warp_sum(s);
+    if (lane == 0) {
+        double *M = m == 0 ? XA : XB;
+        M[(int64_t)i * ld + j] = s;
+        M[(int64_t)j * ld + i] = s;
     }
 }
 
@@ -192,7 +217,7 @@ __global__ void __launch_bounds__(256) k_grad(int64_t n, int p, int ld, const T 
                                               const T *__restrict__ BX,
                                               const double *__restrict__ C,
                                               const double *__restrict__ L0, T *G,
-                                              double *kkt2, int KC) {
+                                              double *kkt2, int KC, double *gpart, unsigned *gcount) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *bx = reinterpret_cast<T *>(smem_raw);   // 32 x ld
     T *cs = bx + 32 * ld;                       // KC x ld
@@ -245,8 +270,8 @@ __global__ void __launch_bounds__(256) k_grad(int64_t n, int p, int ld, const T 
             if (ocol[i] < p) part += (double)(rr[i] * rr[i]);
         }
     }
-    part = block_sum(part, red);
-    if (threadIdx.x == 0) atomicAdd(kkt2, part);
+    const double tot[1] = {block_sum(part, red)};
+    grid_accumulate<1>(tot, gpart, gcount, [&](int, double v) { *kkt2 += v; });
 }
 
 // float32 blocks: the same product with 64-row tiles and a 4-row x CPT-column register tile per
@@ -256,7 +281,8 @@ __global__ void __launch_bounds__(256) k_grad(int64_t n, int p, int ld, const T 
 template <int CPT>
 __global__ void __launch_bounds__(256) k_grad_f32(int64_t n, int p, int ld, const float *__restrict__ HX,
                                                   const float *__restrict__ BX, const double *__restrict__ C,
-                                                  const double *__restrict__ L0, float *G, double *kkt2) {
+                                                  const double *__restrict__ L0, float *G, double *kkt2,
+                                                  double *gpart, unsigned *gcount) {
     extern __shared__ __align__(16) float gsm[];
     float *cs = gsm;                 // ld x ld
     float *ls = cs + ld * ld;        // ld x ld
@@ -311,8 +337,8 @@ __global__ void __launch_bounds__(256) k_grad_f32(int64_t n, int p, int ld, cons
             }
         }
     }
-    part = block_sum(part, red);
-    if (threadIdx.x == 0) atomicAdd(kkt2, part);
+    const double tot[1] = {block_sum(part, red)};
+    grid_accumulate<1>(tot, gpart, gcount, [&](int, double v) { *kkt2 += v; });
 }
 
 // float32 blocks with 64 < ld <= 256: C and L0 no longer fit in shared memory whole, so each CTA
@@ -326,7 +352,7 @@ constexpr int GW_ROWS = 64, GW_COLS = 64, GW_PAD = GW_ROWS + 4;
 __global__ void __launch_bounds__(256) k_grad_f32w(int64_t n, int p, int ld, int nslices,
                                                    const float *__restrict__ HX, const float *__restrict__ BX,
                                                    const double *__restrict__ C, const double *__restrict__ L0,
-                                                   float *G, double *kkt2) {
+                                                   float *G, double *kkt2, double *gpart, unsigned *gcount) {
     extern __shared__ __align__(16) float gwm[];
     float *cs = gwm;                          // ld x GW_COLS
     float *ls = cs + ld * GW_COLS;            // ld x GW_COLS
@@ -402,8 +428,8 @@ __global__ void __launch_bounds__(256) k_grad_f32w(int64_t n, int p, int ld, int
             part += (double)rp;
         }
     }
-    part = block_sum(part, red);
-    if (threadIdx.x == 0) atomicAdd(kkt2, part);
+    const double tot[1] = {block_sum(part, red)};
+    grid_accumulate<1>(tot, gpart, gcount, [&](int, double v) { *kkt2 += v; });
 }
 
 // ---------------------------------------------------------------- elementwise block kernels
@@ -423,17 +449,6 @@ __global__ void __launch_bounds__(256) k_grad_f32w(int64_t n, int p, int ld, int
 
 constexpr int MAXLD = 256;
 
-// add each thread's partial of column j into colsum[j] (j < p) through shared memory
-__device__ __forceinline__ void col_reduce(double acc, int j, bool active, int ld, int p, double *colsum) {
-    __shared__ double sh[MAXLD];
-    for (int k = threadIdx.x; k < ld; k += blockDim.x) sh[k] = 0.0;
-    __syncthreads();
-    if (active && acc != 0.0) atomicAdd(sh + j, acc);
-    __syncthreads();
-    for (int k = threadIdx.x; k < ld && k < p; k += blockDim.x)
-        if (sh[k] != 0.0) atomicAdd(colsum + k, sh[k]);
-}
-
 // element (r, k) of a chunk-major float32 PCG block with row stride ns (n rounded up to 32):
 // ((k / 4) ns + r) 4 + k % 4, so the four columns of a chunk of one row are one 16-byte piece and
 // consecutive rows are consecutive pieces
@@ -447,7 +462,7 @@ __global__ void __launch_bounds__(256) k_pcg_init(int64_t n, int p, int ld, int6
                                                   const T *__restrict__ G, int ldg, const int *__restrict__ cmap,
                                                   const double *__restrict__ dL,
                                                   const double *__restrict__ dB, const double *cb,
-                                                  T *W, T *D, T *R, T *Z, double *rz) {
+                                                  T *W, T *D, T *R, T *Z, double *part) {
     T acc = T(0);
     ELEM_BEGIN
         const T sh = (T)cb[CB_SHIFT * ld + j];
@@ -457,24 +472,22 @@ __global__ void __launch_bounds__(256) k_pcg_init(int64_t n, int p, int ld, int6
         W[e] = w; D[e] = T(0); R[e] = gv; Z[e] = z;
         acc = fma(gv, z, acc);
     ELEM_END
-    col_reduce((double)acc, j, gid < stride, ld, p, rz);
+    col_partial((double)acc, gid < stride, ld, ld, part);      // rz
 }
 
 // learned preconditioner judge sums per column: |G - T D|^2 (T D in Q), |G|^2, G.D
 template <class T>
 __global__ void __launch_bounds__(256) k_judge(int64_t n, int p, int ld, int64_t stride, const T *__restrict__ G,
-                                               const T *__restrict__ Q, const T *__restrict__ D, double *rr,
-                                               double *gg, double *gd) {
+                                               const T *__restrict__ Q, const T *__restrict__ D, double *part) {
     T a = T(0), b = T(0), d = T(0);
     ELEM_BEGIN
         const T g = G[e], r = g - Q[e];
         a = fma(r, r, a); b = fma(g, g, b); d = fma(g, D[e], d);
     ELEM_END
-    col_reduce((double)a, j, gid < stride, ld, p, rr);
-    __syncthreads();
-    col_reduce((double)b, j, gid < stride, ld, p, gg);
-    __syncthreads();
-    col_reduce((double)d, j, gid < stride, ld, p, gd);
+    const int64_t set = (int64_t)ld * gridDim.x;            // |G - T D|^2, |G|^2, G.D
+    col_partial((double)a, gid < stride, ld, ld, part);
+    col_partial((double)b, gid < stride, ld, ld, part + set);
+    col_partial((double)d, gid < stride, ld, ld, part + 2 * set);
 }
 
 // PCG restarted from the current D (the network's output): R = G - Q with Q = T D, Z = R W
@@ -483,7 +496,7 @@ __global__ void __launch_bounds__(256) k_pcg_init_warm(int64_t n, int p, int ld,
                                                        const T *__restrict__ G, const T *__restrict__ Q,
                                                        const double *__restrict__ dL,
                                                        const double *__restrict__ dB, const double *cb,
-                                                       T *W, T *R, T *Z, double *rz) {
+                                                       T *W, T *R, T *Z, double *part) {
     T acc = T(0);
     ELEM_BEGIN
         const T sh = (T)cb[CB_SHIFT * ld + j];
@@ -493,7 +506,7 @@ __global__ void __launch_bounds__(256) k_pcg_init_warm(int64_t n, int p, int ld,
         W[e] = w; R[e] = rv; Z[e] = z;
         acc = fma(rv, z, acc);
     ELEM_END
-    col_reduce((double)acc, j, gid < stride, ld, p, rz);
+    col_partial((double)acc, gid < stride, ld, ld, part);      // rz
 }
 
 // alpha = rz/pq; D += alpha P; R -= alpha Q; Z = R W; rzn += R Z
@@ -502,7 +515,7 @@ __global__ void __launch_bounds__(256) k_pcg_update(int64_t n, int p, int ld, in
                                                     const T *__restrict__ W,
                                                     const T *__restrict__ P,
                                                     const T *__restrict__ Q, T *D, T *R,
-                                                    T *Z, double *rzn) {
+                                                    T *Z, double *part) {
     T acc = T(0);
     const T al = (T)cb[CB_ALPHA * ld + (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) % ld];
     ELEM_BEGIN
@@ -512,7 +525,7 @@ __global__ void __launch_bounds__(256) k_pcg_update(int64_t n, int p, int ld, in
         R[e] = rv; Z[e] = z;
         acc = fma(rv, z, acc);
     ELEM_END
-    col_reduce((double)acc, j, gid < stride, ld, p, rzn);
+    col_partial((double)acc, gid < stride, ld, ld, part);      // rzn
 }
 
 // ---- float32 PCG blocks chunk-major (W, R, Z, P, Q and its D, all sidx-indexed)
@@ -524,13 +537,22 @@ __global__ void __launch_bounds__(256) k_pcg_update(int64_t n, int p, int ld, in
 // start's input) are zeroed.  Each thread takes (row, 4-column chunk) items in a
 // grid-stride loop: consecutive threads take consecutive rows of one chunk, so every write is one
 // float4 of a contiguous run; a warp never spans two chunks (ns is a multiple of 32).
-// Column sums go warp -> shared memory -> one float64 atomic per column and block (same-address
-// atomics from every warp would serialise).
-__device__ __forceinline__ void flush_cols(const float (&acc)[4], int q, int pc, float *cs) {
+// Column sums go warp -> the warp's own row of shared memory (lane 0 adds, in item order) -> the
+// block's partial per column (the eight warp rows added in order) -> part[k * gridDim.x + block].
+__device__ __forceinline__ void flush_cols(const float (&acc)[4], int q, float (*csw)[MAXLD]) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const float t = warp_sum_f(acc[i]);
-        if ((threadIdx.x & 31) == 0 && 4 * q + i < pc) atomicAdd(cs + 4 * q + i, t);
+        if ((threadIdx.x & 31) == 0) csw[threadIdx.x >> 5][4 * q + i] += t;
+    }
+}
+
+__device__ __forceinline__ void cols_out(int w, const float (*csw)[MAXLD], double *part) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < w; k += blockDim.x) {
+        float t = 0.f;
+        for (int wp = 0; wp < 8; ++wp) t += csw[wp][k];
+        part[(int64_t)k * gridDim.x + blockIdx.x] = (double)t;
     }
 }
 
@@ -539,9 +561,9 @@ __global__ void __launch_bounds__(256) k_pcg_init_s(int64_t n, int64_t ns, int p
                                                     const float *__restrict__ Dn, int ld, const int *__restrict__ cmap,
                                                     const double *__restrict__ dL, const double *__restrict__ dB,
                                                     const double *__restrict__ cb, float *W, float *D, float *R,
-                                                    float *Z, float *P, float *Q, double *rz) {
-    __shared__ float cs[MAXLD];
-    for (int k = threadIdx.x; k < w; k += blockDim.x) cs[k] = 0.f;
+                                                    float *Z, float *P, float *Q, double *part) {
+    __shared__ float csw[8][MAXLD];
+    for (int k = threadIdx.x; k < 8 * MAXLD; k += blockDim.x) csw[k / MAXLD][k % MAXLD] = 0.f;
     __syncthreads();
     const int64_t total = ns * (w >> 2);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;    // a multiple of 32
@@ -579,11 +601,9 @@ __global__ void __launch_bounds__(256) k_pcg_init_s(int64_t n, int64_t ns, int p
             *reinterpret_cast<float4 *>(P + o) = make_float4(0.f, 0.f, 0.f, 0.f);
             if (Q) *reinterpret_cast<float4 *>(Q + o) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        flush_cols(acc, q, pc, cs);
+        flush_cols(acc, q, csw);
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < w && k < pc; k += blockDim.x)
-        if (cs[k] != 0.f) atomicAdd(rz + k, (double)cs[k]);
+    cols_out(w, csw, part);                                  // rz
 }
 
 // alpha = rz/pq; D += alpha P; R -= alpha Q; Z = R W; rzn += R Z, per float4 of one row and
@@ -591,9 +611,10 @@ __global__ void __launch_bounds__(256) k_pcg_init_s(int64_t n, int64_t ns, int p
 __global__ void __launch_bounds__(256) k_pcg_update_s(int64_t ns, int pc, int w, const double *__restrict__ cb,
                                                       const float *__restrict__ W, const float *__restrict__ P,
                                                       const float *__restrict__ Q, float *D, float *R, float *Z,
-                                                      double *rzn, int last) {
-    __shared__ float cs[MAXLD], al[MAXLD];
-    for (int k = threadIdx.x; k < w; k += blockDim.x) { cs[k] = 0.f; al[k] = (float)cb[CB_ALPHA * w + k]; }
+                                                      double *part, int last) {
+    __shared__ float csw[8][MAXLD], al[MAXLD];
+    for (int k = threadIdx.x; k < 8 * MAXLD; k += blockDim.x) csw[k / MAXLD][k % MAXLD] = 0.f;
+    for (int k = threadIdx.x; k < w; k += blockDim.x) al[k] = (float)cb[CB_ALPHA * w + k];
     __syncthreads();
     const int64_t total = ns * (w >> 2);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -614,12 +635,10 @@ __global__ void __launch_bounds__(256) k_pcg_update_s(int64_t ns, int pc, int w,
         *reinterpret_cast<float4 *>(R + o) = r4;
         *reinterpret_cast<float4 *>(Z + o) = z4;
         const float acc[4] = {r4.x * z4.x, r4.y * z4.y, r4.z * z4.z, r4.w * z4.w};
-        flush_cols(acc, q, pc, cs);
+        flush_cols(acc, q, csw);
     }
     if (last) return;
-    __syncthreads();
-    for (int k = threadIdx.x; k < w && k < pc; k += blockDim.x)
-        if (cs[k] != 0.f) atomicAdd(rzn + k, (double)cs[k]);
+    cols_out(w, csw, part);                                  // rzn
 }
 
 // D (row-major, pitch ld) from the chunk-major PCG result: column j takes compact column cpos[j]
@@ -659,7 +678,8 @@ __global__ void __launch_bounds__(256) k_select(int64_t n, int ld, int64_t strid
 template <class T>
 __global__ void __launch_bounds__(256) k_bb(int64_t n, int ld, int64_t stride, const T *__restrict__ X,
                                             const T *__restrict__ Xp, const T *__restrict__ D,
-                                            const T *__restrict__ Dp, int have_prev, double *sc) {
+                                            const T *__restrict__ Dp, int have_prev, double *sc, double *gpart,
+                                            unsigned *gcount) {
     __shared__ double red[8];
     T sy = 0, yy = 0, ss = 0, xx = 0, dd = 0;
     {
@@ -672,13 +692,11 @@ __global__ void __launch_bounds__(256) k_bb(int64_t n, int ld, int64_t stride, c
             }
         ELEM_END
     }
-    const double syd = block_sum((double)sy, red), yyd = block_sum((double)yy, red),
-                 ssd = block_sum((double)ss, red), xxd = block_sum((double)xx, red),
-                 ddd = block_sum((double)dd, red);
-    if (threadIdx.x == 0) {
-        atomicAdd(sc + SC_BB + 0, syd); atomicAdd(sc + SC_BB + 1, yyd); atomicAdd(sc + SC_BB + 2, ssd);
-        atomicAdd(sc + SC_XNRM2, xxd); atomicAdd(sc + SC_DNRM2, ddd);
-    }
+    const double tot[5] = {block_sum((double)sy, red), block_sum((double)yy, red), block_sum((double)ss, red),
+                           block_sum((double)xx, red), block_sum((double)dd, red)};
+    grid_accumulate<5>(tot, gpart, gcount, [&](int k, double v) {
+        sc[k < 3 ? SC_BB + k : (k == 3 ? SC_XNRM2 : SC_DNRM2)] = v;
+    });
 }
 
 // Y = X - D / eta
@@ -768,7 +786,23 @@ inline unsigned row_grid(int64_t rows_per_block, int64_t n) {
 
 inline int kc_of(int ld) { return ld <= 64 ? ld : 32; }
 
+// out[j] = the sum of column j's partials part[j * units + u] in unit order (j < kact), 0 for
+// kact <= j < gridDim.x
+__global__ void __launch_bounds__(256) k_col_fin(int kact, int64_t units, const double *__restrict__ part,
+                                                 double *out) {
+    __shared__ double sh[8];
+    const int j = blockIdx.x;
+    const double s = j < kact ? ordered_sum(part + (int64_t)j * units, units, sh) : 0.0;
+    if (threadIdx.x == 0) out[j] = s;
+}
+
 }  // namespace
+
+void launch_col_fin(ofks_ctx *c, int kact, int ktot, int64_t units, const double *part, double *out) {
+    if (ktot <= 0) return;
+    k_col_fin<<<(unsigned)ktot, 256, 0, c->stream>>>(kact, units, part, out);
+    c->kernels += 1;
+}
 
 #define MC_DISPATCH(MC_, ...)                                  \
     switch (MC_) {                                             \
@@ -787,11 +821,18 @@ void launch_gram2(ofks_ctx *c, const T *X, const T *A, const T *B, double *XA, d
     c->kernels += 2;
     ProfScope ps(c, PF_GRAM);
     const int ld = c->ld, p = c->p;
-    cudaMemsetAsync(XA, 0, sizeof(double) * ld * ld, c->stream);
+    cudaMemsetAsync(XA, 0, sizeof(double) * ld * ld, c->stream);    // the padding stays zero
     cudaMemsetAsync(XB, 0, sizeof(double) * ld * ld, c->stream);
+    // the split partials are added in split order by k_gram_fin (one warp per upper entry)
+    auto fin = [&](int TS, int ntile, int64_t units) {
+        const int64_t warps = (int64_t)p * (p + 1);
+        k_gram_fin<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, c->stream>>>(p, ld, TS, ntile, units, c->d_cpart,
+                                                                               XA, XB);
+    };
     if constexpr (sizeof(T) == 4) {
-        if (launch_gram_tc(c, (const float *)X, (const float *)A, (const float *)B, XA, XB)) {
-            k_mirror2<<<4, 256, 0, c->stream>>>(p, ld, XA, XB);
+        int64_t units = 0;
+        if (launch_gram_tc(c, (const float *)X, (const float *)A, (const float *)B, c->d_cpart, &units)) {
+            fin(ld, 1, units);
             return;
         }
         if (ld > 64 && ld <= 256 && ld % 4 == 0) {
@@ -800,8 +841,8 @@ void launch_gram2(ofks_ctx *c, const T *X, const T *A, const T *B, double *XA, d
             const int64_t rps = ((c->n + splits - 1) / splits + GM_KR - 1) / GM_KR * GM_KR;
             splits = (c->n + rps - 1) / rps;
             k_gram_f32w<<<dim3((unsigned)npair, (unsigned)splits), 256, 0, c->stream>>>(
-                c->n, p, ld, ntile, (const float *)X, (const float *)A, (const float *)B, XA, XB, rps);
-            k_mirror2<<<4, 256, 0, c->stream>>>(p, ld, XA, XB);
+                c->n, p, ld, ntile, (const float *)X, (const float *)A, (const float *)B, c->d_cpart, rps);
+            fin(GM_T, ntile, splits);
             return;
         }
     }
@@ -811,10 +852,10 @@ void launch_gram2(ofks_ctx *c, const T *X, const T *A, const T *B, double *XA, d
     const int64_t rps = ((c->n + splits - 1) / splits + 15) / 16 * 16;
     splits = (c->n + rps - 1) / rps;
     dim3 grid((unsigned)npair, (unsigned)splits);
-#define G_(rt) k_gram2<T, rt><<<grid, 256, 0, c->stream>>>(c->n, p, ld, ntile, X, A, B, XA, XB, rps)
+#define G_(rt) k_gram2<T, rt><<<grid, 256, 0, c->stream>>>(c->n, p, ld, ntile, X, A, B, c->d_cpart, rps)
     switch (RT) { case 1: G_(1); break; case 2: G_(2); break; case 3: G_(3); break; default: G_(4); }
 #undef G_
-    k_mirror2<<<4, 256, 0, c->stream>>>(p, ld, XA, XB);
+    fin(TS, ntile, splits);
 }
 
 template <> bool pcg_zc<double>(const ofks_ctx *, int) { return false; }
@@ -846,7 +887,8 @@ void launch_grad_update(ofks_ctx *c, Blocks<T> &b) {
                                                                                       152 / nsl)));
             cudaFuncSetAttribute(k_grad_f32w, cudaFuncAttributeMaxDynamicSharedMemorySize, smw);
             k_grad_f32w<<<gw, 256, smw, c->stream>>>(c->n, c->p, ld, nsl, (const float *)b.HX, (const float *)b.BX,
-                                                     c->d_C, c->d_L0, (float *)G, c->d_sc + SC_KKT2);
+                                                     c->d_C, c->d_L0, (float *)G, c->d_sc + SC_KKT2, c->d_gpart,
+                                                     c->d_gcount);
             return;
         }
         if (ld <= 64) {
@@ -854,7 +896,8 @@ void launch_grad_update(ofks_ctx *c, Blocks<T> &b) {
             const unsigned gf = (unsigned)std::max<int64_t>(1, std::min<int64_t>((c->n + 63) / 64, 152 * 4));
 #define GF_(k) { cudaFuncSetAttribute(k_grad_f32<k>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf); \
         k_grad_f32<k><<<gf, 256, smf, c->stream>>>(c->n, c->p, ld, (const float *)b.HX, (const float *)b.BX, \
-                                                   c->d_C, c->d_L0, (float *)G, c->d_sc + SC_KKT2); }
+                                                   c->d_C, c->d_L0, (float *)G, c->d_sc + SC_KKT2, c->d_gpart, \
+                                                   c->d_gcount); }
             if (ld <= 16) GF_(1) else if (ld <= 32) GF_(2) else if (ld <= 48) GF_(3) else GF_(4)
 #undef GF_
             return;
@@ -864,7 +907,7 @@ void launch_grad_update(ofks_ctx *c, Blocks<T> &b) {
     const int no = (32 * ld + 255) / 256;
 #define GR_(k) { cudaFuncSetAttribute(k_grad<T, k>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
         k_grad<T, k><<<grid, 256, sm, c->stream>>>(c->n, c->p, ld, b.HX, b.BX, c->d_C, c->d_L0, G, \
-                                                  c->d_sc + SC_KKT2, KC); }
+                                                  c->d_sc + SC_KKT2, KC, c->d_gpart, c->d_gcount); }
     if (no <= 1) GR_(1) else if (no <= 2) GR_(2) else if (no <= 4) GR_(4) else if (no <= 6) GR_(6)
     else if (no <= 8) GR_(8) else if (no <= 16) GR_(16) else GR_(32)
 #undef GR_
@@ -874,20 +917,22 @@ template <class T>
 void launch_pcg_init(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v) {
     c->kernels += 1;
     const int w = v.w;
-    cudaMemsetAsync(v.cb + CB_RZ * w, 0, sizeof(double) * w, c->stream);
     if constexpr (sizeof(T) == 4) {
         if (pcg_zc<T>(c, w)) {
             const int64_t total = c->n_slots * (w >> 2);
-            k_pcg_init_s<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8), 256, 0, c->stream>>>(
+            const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8);
+            k_pcg_init_s<<<grid, 256, 0, c->stream>>>(
                 c->n, c->n_slots, v.pc, w, (const float *)b.G[c->cur], nullptr, nullptr, c->ld, v.cmap, c->d_dL,
                 c->d_dB, v.cb, (float *)b.W, (float *)v.D, (float *)b.R, (float *)b.Z, (float *)b.P, (float *)b.Q,
-                v.cb + CB_RZ * w);
+                c->d_cpart);
+            launch_col_fin(c, v.pc, w, grid, c->d_cpart, v.cb + CB_RZ * w);
             return;
         }
     }
     const ElemGrid g = elem_grid(c->n, w);
     k_pcg_init<T><<<g.blocks, 256, 0, c->stream>>>(c->n, v.pc, w, g.stride, b.G[c->cur], c->ld, v.cmap, c->d_dL,
-                                                   c->d_dB, v.cb, b.W, v.D, b.R, b.Z, v.cb + CB_RZ * w);
+                                                   c->d_dB, v.cb, b.W, v.D, b.R, b.Z, c->d_cpart);
+    launch_col_fin(c, v.pc, w, g.blocks, c->d_cpart, v.cb + CB_RZ * w);
 }
 
 template <class T>
@@ -895,10 +940,13 @@ void launch_judge(ofks_ctx *c, Blocks<T> &b) {
     c->kernels += 1;
     const int ld = c->ld;
     double *cb = c->d_colA;
-    cudaMemsetAsync(cb + CB_RZ * ld, 0, sizeof(double) * 3 * ld, c->stream);   // RZ, RZN, PQ rows
     const ElemGrid g = elem_grid(c->n, ld);
-    k_judge<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, b.G[c->cur], b.Q, b.D[c->cur],
-                                                cb + CB_RZ * ld, cb + CB_RZN * ld, cb + CB_PQ * ld);
+    k_judge<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, b.G[c->cur], b.Q, b.D[c->cur], c->d_cpart);
+    // |G - T D|^2, |G|^2 and G.D into the RZ, RZN and PQ rows
+    const int64_t set = (int64_t)ld * g.blocks;
+    launch_col_fin(c, c->p, ld, g.blocks, c->d_cpart, cb + CB_RZ * ld);
+    launch_col_fin(c, c->p, ld, g.blocks, c->d_cpart + set, cb + CB_RZN * ld);
+    launch_col_fin(c, c->p, ld, g.blocks, c->d_cpart + 2 * set, cb + CB_PQ * ld);
 }
 
 template <class T>
@@ -906,20 +954,22 @@ void launch_pcg_init_warm(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v) {
     c->kernels += 1;
     const int ld = c->ld;
     double *cb = c->d_colA;
-    cudaMemsetAsync(cb + CB_RZ * ld, 0, sizeof(double) * ld, c->stream);
     if constexpr (sizeof(T) == 4) {
         if (pcg_zc<T>(c, v.w)) {                 // Q = T D and the network's D are natural row-major
             const int64_t total = c->n_slots * (v.w >> 2);
-            k_pcg_init_s<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8), 256, 0, c->stream>>>(
+            const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8);
+            k_pcg_init_s<<<grid, 256, 0, c->stream>>>(
                 c->n, c->n_slots, v.pc, v.w, (const float *)b.G[c->cur], (const float *)b.Q,
                 (const float *)b.D[c->cur], ld, v.cmap, c->d_dL, c->d_dB, v.cb, (float *)b.W, (float *)v.D,
-                (float *)b.R, (float *)b.Z, (float *)b.P, nullptr, v.cb + CB_RZ * v.w);   // Qn aliases b.Q
+                (float *)b.R, (float *)b.Z, (float *)b.P, nullptr, c->d_cpart);   // Qn aliases b.Q
+            launch_col_fin(c, v.pc, v.w, grid, c->d_cpart, v.cb + CB_RZ * v.w);
             return;
         }
     }
     const ElemGrid g = elem_grid(c->n, ld);
     k_pcg_init_warm<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, b.G[c->cur], b.Q, c->d_dL, c->d_dB,
-                                                        cb, b.W, b.R, b.Z, cb + CB_RZ * ld);
+                                                        cb, b.W, b.R, b.Z, c->d_cpart);
+    launch_col_fin(c, c->p, ld, g.blocks, c->d_cpart, cb + CB_RZ * ld);
 }
 
 template <class T>
@@ -927,18 +977,22 @@ void launch_pcg_update(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v, bool last
     c->kernels += 1;
     const int w = v.w;
     double *cb = v.cb;
+    // the column sums r.z go to the partials; k_pcg_beta adds them (rz_units per column)
     if constexpr (sizeof(T) == 4) {
         if (pcg_zc<T>(c, w)) {
             const int64_t total = c->n_slots * (w >> 2);
-            k_pcg_update_s<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8), 256, 0, c->stream>>>(
+            const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8);
+            k_pcg_update_s<<<grid, 256, 0, c->stream>>>(
                 c->n_slots, v.pc, w, cb, (const float *)b.W, (const float *)b.P, (const float *)b.Q, (float *)v.D,
-                (float *)b.R, (float *)b.Z, cb + CB_RZN * w, last ? 1 : 0);
+                (float *)b.R, (float *)b.Z, c->d_cpart, last ? 1 : 0);
+            c->rz_units = grid;
             return;
         }
     }
     const ElemGrid g = elem_grid(c->n, w);
     k_pcg_update<T><<<g.blocks, 256, 0, c->stream>>>(c->n, v.pc, w, g.stride, cb, b.W, b.P, b.Q, v.D, b.R,
-                                                     b.Z, cb + CB_RZN * w);
+                                                     b.Z, c->d_cpart);
+    c->rz_units = g.blocks;
 }
 
 template <class T>
@@ -969,17 +1023,14 @@ template <class T>
 void launch_bb_dots(ofks_ctx *c, Blocks<T> &b, bool raw) {
     ProfScope ps(c, PF_BB);
     const int cur = c->cur, prv = cur ^ 1;
-    cudaMemsetAsync(c->d_sc + SC_BB, 0, sizeof(double) * 3, c->stream);
-    cudaMemsetAsync(c->d_sc + SC_XNRM2, 0, sizeof(double) * 2, c->stream);
     const ElemGrid g = elem_grid(c->n, c->ld);
     T **DD = raw ? b.G : b.D;
     k_bb<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->ld, g.stride, b.X[cur], b.X[prv], DD[cur], DD[prv],
-                                             c->have_prev ? 1 : 0, c->d_sc);
+                                             c->have_prev ? 1 : 0, c->d_sc, c->d_gpart, c->d_gcount);
     c->kernels += 1;
     if (raw && !c->have_prev) {       // eta_0 needs ||D||: rerun the sums on D
-        cudaMemsetAsync(c->d_sc + SC_XNRM2, 0, sizeof(double) * 2, c->stream);
         k_bb<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->ld, g.stride, b.X[cur], b.X[prv], b.D[cur], b.D[prv], 0,
-                                                 c->d_sc);
+                                                 c->d_sc, c->d_gpart, c->d_gcount);
         c->kernels += 1;
     }
 }

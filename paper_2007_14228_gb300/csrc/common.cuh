@@ -33,6 +33,66 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return t;
 }
 
+// ---- deterministic reductions
+// Float addition is not associative: sums whose terms arrive by atomics in a run-dependent order
+// round differently from run to run, and the step-size rule amplifies such differences into
+// different iterate sequences.  Every sum over more than one block therefore goes through
+// partials written to scratch memory by their block (or warp) and added in a fixed order, so the
+// same inputs give bit-identical results on every run.
+
+// Fixed-order sum of a[0..n) over the block (thread t takes t, t + blockDim.x, ...; then the
+// fixed tree of block_sum); every thread gets it.  L1 is bypassed: the partials may have been
+// written by other blocks of the same grid.  `sh` needs blockDim.x/32 doubles.
+__device__ __forceinline__ double ordered_sum(const double *a, int64_t n, double *sh) {
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(a + i);
+    return block_sum(s, sh);
+}
+
+// Grid-wide sums of K block totals v[k] (every thread of the block holds them).  Block b writes
+// its totals to part[k * gridDim.x + b]; the last block to finish (counted with an integer
+// atomic on *count, whose order does not matter) adds the partials in block order and calls
+// out(k, sum) from thread 0.  Every block of the grid calls this exactly once, as its last
+// action; *count is zero on entry and is left zero.  part holds K * gridDim.x doubles.
+template <int K, class Out>
+__device__ __forceinline__ void grid_accumulate(const double (&v)[K], double *part, unsigned *count, Out out) {
+    __shared__ bool last;
+    __shared__ double gsh[32];
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) part[(int64_t)k * gridDim.x + blockIdx.x] = v[k];
+        __threadfence();
+        last = atomicAdd(count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+#pragma unroll 1
+    for (int k = 0; k < K; ++k) {
+        const double s = ordered_sum(part + (int64_t)k * gridDim.x, gridDim.x, gsh);
+        if (threadIdx.x == 0) out(k, s);
+    }
+    if (threadIdx.x == 0) *count = 0u;
+}
+
+// Per-block column sums for the flattened n x ld element loops whose thread keeps column
+// j = (global thread index) mod ld: the block's threads of column k are added in thread order
+// into part[k * gridDim.x + blockIdx.x] (k < ncol <= ld <= blockDim.x).  Every thread calls it.
+__device__ __forceinline__ void col_partial(double acc, bool active, int ld, int ncol, double *part) {
+    __shared__ double cval[256];
+    cval[threadIdx.x] = active ? acc : 0.0;
+    __syncthreads();
+    const int k = threadIdx.x;
+    if (k < ncol) {
+        // thread t holds column ((blockIdx.x * blockDim.x + t) mod ld)
+        const int t0 = (int)((k - (int64_t)blockIdx.x * blockDim.x % ld + ld) % ld);
+        double s = 0.0;
+        for (int t = t0; t < (int)blockDim.x; t += ld) s += cval[t];
+        part[(int64_t)k * gridDim.x + blockIdx.x] = s;
+    }
+    __syncthreads();
+}
+
 // P2 basis on the reference tetrahedron at the symmetric 4-point rule.
 // Point q has barycentric coordinates QB everywhere except QA at vertex q, with
 // QA = (5 + 3 sqrt 5)/20 and QB = (5 - sqrt 5)/20; every weight is |T|/4.

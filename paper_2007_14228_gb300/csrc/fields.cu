@@ -58,19 +58,13 @@ __device__ __forceinline__ F lda(F rho, F &vxc) {
 // j of the group covers columns j, j+G, ...:  psi_{q,l} = sum_a N_a(x_q) X_{a,l},
 // rho_q = f sum_l psi_{q,l}^2 (group xor-reduction).  The per-tetrahedron epilogue is spread
 // over the group's lanes (float64 warp instructions cost the same with one active lane):
-// lane k writes rho_k (k < 4) and adds the Poisson load 4 pi w sum_q N_k(x_q) rho_q of local
-// node k (k < 10).  The multipole moments follow from the assembled load (k_moments).
+// lane k writes rho_k (k < 4).  The Poisson load is gathered per node from rho (k_rhs_gather) and
+// the multipole moments follow from it (k_moments).
 template <class E, int G>
 __global__ void __launch_bounds__(256) k_density(int64_t T, int p, int ld, double occ,
                                                  const E *__restrict__ X,
-                                                 const int *__restrict__ tetf,
-                                                 const int *__restrict__ tetn,
-                                                 const double *__restrict__ wq, double *rho,
-                                                 double *rhs, int do_hartree) {
+                                                 const int *__restrict__ tetf, double *rho) {
     constexpr int TPW = 32 / G;                       // tetrahedra per warp and pass
-    __shared__ double sN[4][10];
-    if (threadIdx.x < 40) sN[threadIdx.x / 10][threadIdx.x % 10] = p2N(threadIdx.x / 10, threadIdx.x % 10);
-    __syncthreads();
     const int lane = threadIdx.x & (G - 1), grp = (threadIdx.x & 31) / G;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -104,15 +98,26 @@ __global__ void __launch_bounds__(256) k_density(int64_t T, int p, int ld, doubl
         for (int q = 0; q < 4; ++q) s[q] = (double)se[q];
         if (!ok) continue;
         for (int k = lane; k < 4; k += G) rho[t * 4 + k] = occ * s[k];
-        if (!do_hartree) continue;
-        const double w = wq[t];
-        for (int k = lane; k < 10; k += G) {
-            double v = 0.0;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) v = fma(sN[q][k], s[q], v);
-            atomicAdd(rhs + tetn[t * 10 + k], (4.0 * 3.14159265358979323846 * occ) * w * v);
-        }
     }
+}
+
+// Poisson load rhs_i = 4 pi sum_T w_T sum_q N_a(x_q) rho_q over the element entries (T, a) of
+// node i, gathered in list order (a fixed order: the same value on every run)
+__global__ void __launch_bounds__(256) k_rhs_gather(int64_t N, const int *__restrict__ ptr, const int *__restrict__ list,
+                                                    const double *__restrict__ wq, const double *__restrict__ rho,
+                                                    double *rhs) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double acc = 0.0;
+    for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
+        const int code = list[k], t = code / 10, a = code - 10 * t;
+        const double *r = rho + (int64_t)t * 4;
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v = fma(p2N(q, a), r[q], v);
+        acc = fma(wq[t], v, acc);
+    }
+    rhs[i] = (4.0 * PI) * acc;
 }
 
 // Multipole moments of the density about the centre (Sec. 2.2 boundary data): for each of
@@ -123,10 +128,9 @@ __global__ void __launch_bounds__(256) k_density(int64_t T, int p, int ld, doubl
 // load rhs_i = 4 pi sum_T w_T sum_q N_i(x_q) rho_q: one pass over the nodes instead of ten
 // functions at every quadrature point.
 __global__ void __launch_bounds__(256) k_moments(int64_t N, const double *__restrict__ ynode,
-                                                 const double *__restrict__ rhs, double *mom) {
-    __shared__ double smom[10];
-    if (threadIdx.x < 10) smom[threadIdx.x] = 0.0;
-    __syncthreads();
+                                                 const double *__restrict__ rhs, double *mom, double *gpart,
+                                                 unsigned *gcount) {
+    __shared__ double sh[8];
     double m[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const double r = rhs[i] * (1.0 / (4.0 * PI));
@@ -143,13 +147,10 @@ __global__ void __launch_bounds__(256) k_moments(int64_t N, const double *__rest
         m[8] = fma(r, 3.0 * y0 * y2, m[8]);
         m[9] = fma(r, 3.0 * y1 * y2, m[9]);
     }
-#pragma unroll
-    for (int k = 0; k < 10; ++k) {
-        const double v = warp_sum(m[k]);
-        if ((threadIdx.x & 31) == 0) atomicAdd(smom + k, v);
-    }
-    __syncthreads();
-    if (threadIdx.x < 10) atomicAdd(mom + threadIdx.x, smom[threadIdx.x]);
+    double tot[10];
+#pragma unroll 1
+    for (int k = 0; k < 10; ++k) tot[k] = block_sum(m[k], sh);
+    grid_accumulate<10>(tot, gpart, gcount, [&](int k, double v) { mom[k] = v; });
 }
 
 // Multipole boundary values V_B(r) = Q/|r| + d.r/|r|^3 + (1/2) sum Q_ij r_i r_j/|r|^5
@@ -174,7 +175,7 @@ __global__ void k_boundary(int nb, const int *__restrict__ bnd, const double *__
 // Dirichlet rows unwritten): r = 0 there, z = p = minv r, and rz, rr, |rhs|^2 as k_cg_init
 __global__ void __launch_bounds__(256) k_cg_init_vec(int64_t N, const double *__restrict__ minv,
                                                      const double *__restrict__ rhs, double *r, double *z,
-                                                     double *pv, double *sc) {
+                                                     double *pv, double *sc, double *gpart, unsigned *gcount) {
     __shared__ double sh[8];
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double rz = 0.0, rr = 0.0, bb = 0.0;
@@ -185,14 +186,8 @@ __global__ void __launch_bounds__(256) k_cg_init_vec(int64_t N, const double *__
         r[i] = ri; z[i] = zi; pv[i] = zi;
         rz = ri * zi; rr = ri * ri;
     }
-    rz = block_sum(rz, sh);
-    rr = block_sum(rr, sh);
-    bb = block_sum(bb, sh);
-    if (threadIdx.x == 0) {
-        atomicAdd(sc + 0, rz);
-        atomicAdd(sc + 4, rr);
-        atomicAdd(sc + 6, bb);
-    }
+    const double tot[3] = {block_sum(rz, sh), block_sum(rr, sh), block_sum(bb, sh)};
+    grid_accumulate<3>(tot, gpart, gcount, [&](int k, double v) { sc[k == 0 ? 0 : (k == 1 ? 4 : 6)] += v; });
 }
 
 // Poisson CG on the interior nodes with the full-node CSR stiffness; boundary entries of
@@ -203,7 +198,7 @@ __global__ void __launch_bounds__(256) k_cg_init(int64_t N, const int *__restric
                                                  const double *__restrict__ minv,
                                                  const double *__restrict__ rhs,
                                                  const double *__restrict__ U, double *r, double *z,
-                                                 double *pv, double *sc) {
+                                                 double *pv, double *sc, double *gpart, unsigned *gcount) {
     __shared__ double sh[8];
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double rz = 0.0, rr = 0.0, bb = 0.0;
@@ -219,14 +214,9 @@ __global__ void __launch_bounds__(256) k_cg_init(int64_t N, const int *__restric
         r[i] = ri; z[i] = zi; pv[i] = zi;
         rz = ri * zi; rr = ri * ri;
     }
-    rz = block_sum(rz, sh);
-    rr = block_sum(rr, sh);
-    bb = block_sum(bb, sh);
-    if (threadIdx.x == 0) {
-        atomicAdd(sc + 0, rz);     // rz[0]
-        atomicAdd(sc + 4, rr);     // rr[0]
-        atomicAdd(sc + 6, bb);     // rhs2
-    }
+    // rz[0], rr[0], |rhs|^2
+    const double tot[3] = {block_sum(rz, sh), block_sum(rr, sh), block_sum(bb, sh)};
+    grid_accumulate<3>(tot, gpart, gcount, [&](int k, double v) { sc[k == 0 ? 0 : (k == 1 ? 4 : 6)] += v; });
 }
 
 // q = L p, pq += p.q  (slot it&1); zero the retired rz slot.  One thread per row: on GB300 a
@@ -237,7 +227,7 @@ __global__ void __launch_bounds__(256) k_cg_spmv(int64_t N, const int *__restric
                                                  const double *__restrict__ val,
                                                  const double *__restrict__ minv,
                                                  const double *__restrict__ pv, double *qv,
-                                                 double *sc, int it) {
+                                                 double *sc, int it, double *gpart, unsigned *gcount) {
     __shared__ double sh[8];
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double pq = 0.0;
@@ -247,21 +237,20 @@ __global__ void __launch_bounds__(256) k_cg_spmv(int64_t N, const int *__restric
         qv[i] = s;
         pq = pv[i] * s;
     }
-    pq = block_sum(pq, sh);
-    if (threadIdx.x == 0) {
-        atomicAdd(sc + 2 + (it & 1), pq);
-        if (blockIdx.x == 0) {
-            sc[0 + ((it + 1) & 1)] = 0.0;    // rz slot of the next "new" value
-            sc[4 + ((it + 1) & 1)] = 0.0;    // rr slot
-        }
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        sc[0 + ((it + 1) & 1)] = 0.0;        // rz slot of the next "new" value
+        sc[4 + ((it + 1) & 1)] = 0.0;        // rr slot
     }
+    const double tot[1] = {block_sum(pq, sh)};
+    grid_accumulate<1>(tot, gpart, gcount, [&](int, double v) { sc[2 + (it & 1)] += v; });
 }
 
 // alpha = rz/pq; U += alpha p; r -= alpha q; z = minv r; rz', rr' into the other slots
 __global__ void __launch_bounds__(256) k_cg_update(int64_t N, const double *__restrict__ minv,
                                                    const double *__restrict__ pv,
                                                    const double *__restrict__ qv, double *U,
-                                                   double *r, double *z, double *sc, int it) {
+                                                   double *r, double *z, double *sc, int it, double *gpart,
+                                                   unsigned *gcount) {
     __shared__ double sh[8];
     __shared__ double s_alpha;
     const int nn = (it + 1) & 1;
@@ -283,20 +272,16 @@ __global__ void __launch_bounds__(256) k_cg_update(int64_t N, const double *__re
             rz2 = fma(ri, zi, rz2); rr = fma(ri, ri, rr);
         }
     }
-    rz2 = block_sum(rz2, sh);
-    rr = block_sum(rr, sh);
-    if (threadIdx.x == 0) {
-        atomicAdd(sc + 0 + nn, rz2);
-        atomicAdd(sc + 4 + nn, rr);
-        if (blockIdx.x == 0) sc[2 + nn] = 0.0;   // next pq slot
-    }
+    if (threadIdx.x == 0 && blockIdx.x == 0) sc[2 + nn] = 0.0;   // next pq slot
+    const double tot[2] = {block_sum(rz2, sh), block_sum(rr, sh)};
+    grid_accumulate<2>(tot, gpart, gcount, [&](int k, double v) { sc[(k == 0 ? 0 : 4) + nn] += v; });
 }
 
 // preconditioned variant of k_cg_update: alpha = rz/pq; U += alpha p; r -= alpha q; rr'
 __global__ void __launch_bounds__(256) k_cg_update_r(int64_t N, const double *__restrict__ minv,
                                                      const double *__restrict__ pv,
                                                      const double *__restrict__ qv, double *U, double *r,
-                                                     double *sc, int it) {
+                                                     double *sc, int it, double *gpart, unsigned *gcount) {
     __shared__ double sh[8];
     __shared__ double s_alpha;
     const int nn = (it + 1) & 1;
@@ -314,24 +299,23 @@ __global__ void __launch_bounds__(256) k_cg_update_r(int64_t N, const double *__
             r[i] = ri;
             rr = fma(ri, ri, rr);
         }
-    rr = block_sum(rr, sh);
-    if (threadIdx.x == 0) {
-        atomicAdd(sc + 4 + nn, rr);
-        if (blockIdx.x == 0) sc[2 + nn] = 0.0;
-    }
+    if (threadIdx.x == 0 && blockIdx.x == 0) sc[2 + nn] = 0.0;
+    const double tot[1] = {block_sum(rr, sh)};
+    grid_accumulate<1>(tot, gpart, gcount, [&](int, double v) { sc[4 + nn] += v; });
 }
 
 // sc[slot] += r.z; with first = 1 also p = z
 __global__ void __launch_bounds__(256) k_cg_rz(int64_t N, const double *__restrict__ r, const double *__restrict__ z,
-                                               double *pv, double *sc, int slot, int first) {
+                                               double *pv, double *sc, int slot, int first, double *gpart,
+                                               unsigned *gcount) {
     __shared__ double sh[8];
     double v = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         v = fma(r[i], z[i], v);
         if (first) pv[i] = z[i];
     }
-    v = block_sum(v, sh);
-    if (threadIdx.x == 0) atomicAdd(sc + slot, v);
+    const double tot[1] = {block_sum(v, sh)};
+    grid_accumulate<1>(tot, gpart, gcount, [&](int, double x) { sc[slot] += x; });
 }
 
 // beta = rz'/rz; p = z + beta p
@@ -347,30 +331,23 @@ __global__ void k_cg_dir(int64_t N, const double *__restrict__ z, double *pv, co
         pv[i] = z[i] + beta * pv[i];
 }
 
-template <class E>
-__global__ void k_half_copy(int64_t n, const E *__restrict__ a, E *b) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) b[i] = E(0.5) * a[i];
-}
-
-// Per tetrahedron: V_H(x_q) from the nodal U, LDA at rho_q, V_q = V_ext + V_H + V_xc,
-// the double-counting sum w (V_H/2 + V_xc - eps_xc) rho, and the local potential matrix
-// sum_q w V_q N_a N_b added to the Hamiltonian values (which hold L/2 on entry).
+// Per tetrahedron: V_H(x_q) from the nodal U, LDA at rho_q, V_q = V_ext + V_H + V_xc, the
+// weighted values w V_q of the local potential matrix (ve, in the precision of the H values: the
+// float64 products cost as much as the rest of the kernel on GB300's FP64 pipe), and the
+// double-counting sum w (V_H/2 + V_xc - eps_xc) rho.
 template <class E>
 __global__ void __launch_bounds__(128) k_potential(int64_t T, const int *__restrict__ tetn,
-                                                   const int *__restrict__ emap,
                                                    const double *__restrict__ wq,
                                                    const double *__restrict__ vext,
                                                    const double *__restrict__ rho,
                                                    const double *__restrict__ U, int do_h, int do_xc,
                                                    double *vh, double *vxc, double *exc,
-                                                   E *valH, double *edc) {
+                                                   E *ve, double *edc, double *gpart, unsigned *gcount) {
     __shared__ double sh[4];
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double e = 0.0;
     if (t < T) {
         const double w = wq[t];
-        double V[4];
         for (int q = 0; q < 4; ++q) {
             double h = 0.0;
             if (do_h)
@@ -386,29 +363,32 @@ __global__ void __launch_bounds__(128) k_potential(int64_t T, const int *__restr
                 }
             }
             vh[t * 4 + q] = h; vxc[t * 4 + q] = vx; exc[t * 4 + q] = ex;
-            V[q] = w * (vext[t * 4 + q] + h + vx);
+            ve[t * 4 + q] = (E)(w * (vext[t * 4 + q] + h + vx));
             e += w * (0.5 * h + vx - ex) * r;
         }
-        // the local matrix in the precision of the H values (float32 in the mixed form: the
-        // float64 products cost as much as the rest of the kernel on GB300's FP64 pipe)
-        E Ve[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) Ve[q] = (E)V[q];
-        const int *em = emap + t * 100;
-#pragma unroll
-        for (int a = 0; a < 10; ++a)
-#pragma unroll
-            for (int b = 0; b < 10; ++b) {
-                const int pos = em[a * 10 + b];
-                if (pos < 0) continue;
-                E m = E(0);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) m += Ve[q] * (E)(p2N(q, a) * p2N(q, b));
-                atomicAdd(valH + pos, m);
-            }
     }
-    e = block_sum(e, sh);
-    if (threadIdx.x == 0) atomicAdd(edc, e);
+    const double tot[1] = {block_sum(e, sh)};
+    grid_accumulate<1>(tot, gpart, gcount, [&](int, double v) { *edc = v; });
+}
+
+// H = L/2 + sum over the element entries (T, a, b) that land on each SELL position of
+// sum_q (w V_q)_T N_a(x_q) N_b(x_q) (Eq. hamiltonian), gathered in list order in the precision of
+// the H values (the same value on every run)
+template <class E>
+__global__ void __launch_bounds__(256) k_h_gather(int64_t npos, const int *__restrict__ ptr, const int *__restrict__ list,
+                                                  const E *__restrict__ ve, const E *__restrict__ valL, E *valH) {
+    const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (pos >= npos) return;
+    E acc = E(0.5) * valL[pos];
+    for (int k = ptr[pos]; k < ptr[pos + 1]; ++k) {
+        const int code = list[k], t = code / 100, ab = code - 100 * t, a = ab / 10, b = ab - 10 * a;
+        const E *v = ve + (int64_t)t * 4;
+        E m = E(0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) m += v[q] * (E)(p2N(q, a) * p2N(q, b));
+        acc += m;
+    }
+    valH[pos] = acc;
 }
 
 }  // namespace
@@ -418,10 +398,6 @@ int launch_density(ofks_ctx *c, const E *X) {
     ProfScope ps(c, PF_DENSITY);
     const int64_t T = c->n_tets;
     const int do_h = c->prm.hartree ? 1 : 0;
-    if (do_h) {
-        cudaMemsetAsync(c->d_rhs, 0, sizeof(double) * c->n_nodes, c->stream);
-        cudaMemsetAsync(c->d_sc + SC_MOM, 0, sizeof(double) * 10, c->stream);
-    }
     // group width: the fewest wasted column slots ceil(p/G) G, preferring wide groups on ties
     int G = c->p <= 2 ? c->p : 4;
     if (c->p > 2)
@@ -430,8 +406,7 @@ int launch_density(ofks_ctx *c, const E *X) {
     const int B = 256;
     const int64_t warps = (T + 32 / G - 1) / (32 / G);
     unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((warps * 32 + B - 1) / B, 152LL * 16));
-#define DENS(g) k_density<E, g><<<grid, B, 0, c->stream>>>(T, c->p, c->ld, c->prm.occ, X, c->d_tetf, \
-        c->d_tetn, c->d_wq, c->d_rho, c->d_rhs, do_h)
+#define DENS(g) k_density<E, g><<<grid, B, 0, c->stream>>>(T, c->p, c->ld, c->prm.occ, X, c->d_tetf, c->d_rho)
     switch (G) {
         case 1: DENS(1); break;
         case 2: DENS(2); break;
@@ -444,9 +419,11 @@ int launch_density(ofks_ctx *c, const E *X) {
     c->kernels += 1;
     if (do_h) {
         const int64_t N = c->n_nodes;
+        k_rhs_gather<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(N, c->d_nptr, c->d_nlist, c->d_wq, c->d_rho,
+                                                                         c->d_rhs);
         const unsigned gm = (unsigned)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 152LL * 4));
-        k_moments<<<gm, 256, 0, c->stream>>>(N, c->d_ynode, c->d_rhs, c->d_sc + SC_MOM);
-        c->kernels += 1;
+        k_moments<<<gm, 256, 0, c->stream>>>(N, c->d_ynode, c->d_rhs, c->d_sc + SC_MOM, c->d_gpart, c->d_gcount);
+        c->kernels += 2;
     }
     return ofks_cuda_check(c, cudaGetLastError(), "density kernel");
 }
@@ -476,10 +453,11 @@ int run_hartree(ofks_ctx *c) {
     cudaMemsetAsync(sc, 0, sizeof(double) * 8, c->stream);
     if (c->st.on && !c->prm.poisson_csr) {   // the lattice-stencil residual, then the CG start
         launch_stencil_residual(c, c->d_U, c->d_rhs, c->d_cr);
-        k_cg_init_vec<<<gN, 256, 0, c->stream>>>(N, c->d_minv, c->d_rhs, c->d_cr, c->d_cz, c->d_cp, sc);
+        k_cg_init_vec<<<gN, 256, 0, c->stream>>>(N, c->d_minv, c->d_rhs, c->d_cr, c->d_cz, c->d_cp, sc, c->d_gpart,
+                                                 c->d_gcount);
     } else {
         k_cg_init<<<gN, 256, 0, c->stream>>>(N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv, c->d_rhs, c->d_U,
-                                             c->d_cr, c->d_cz, c->d_cp, sc);
+                                             c->d_cr, c->d_cz, c->d_cp, sc, c->d_gpart, c->d_gcount);
     }
     c->kernels += 2;
     const int pc = hartree_pc(c);
@@ -494,7 +472,7 @@ int run_hartree(ofks_ctx *c) {
         ProfScope pv(c, PF_POISSON_SPMV);
         if (lat) { launch_stencil_spmv(c, c->d_cp, c->d_cq, sc, it); return; }
         k_cg_spmv<<<gN, 256, 0, c->stream>>>(N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv, c->d_cp, c->d_cq, sc,
-                                              it);
+                                              it, c->d_gpart, c->d_gcount);
         c->kernels += 1;
     };
     if (sep) {          // z = A_sep^-1 r, rz[0] = r.z, p = z
@@ -504,7 +482,7 @@ int run_hartree(ofks_ctx *c) {
     } else if (amg) {   // z = M^-1 r by the multigrid cycle, rz[0] = r.z, p = z
         cudaMemsetAsync(sc, 0, sizeof(double), c->stream);
         precond();
-        k_cg_rz<<<gU, 256, 0, c->stream>>>(N, c->d_cr, c->d_cz, c->d_cp, sc, 0, 1);
+        k_cg_rz<<<gU, 256, 0, c->stream>>>(N, c->d_cr, c->d_cz, c->d_cp, sc, 0, 1, c->d_gpart, c->d_gcount);
         c->kernels += 1;
     }
     double ptol = c->phase == 32 ? std::max(c->prm.poisson_tol, c->prm.poisson_tol_mixed) : c->prm.poisson_tol;
@@ -559,7 +537,8 @@ int run_hartree(ofks_ctx *c) {
                         if (K.lat) launch_stencil_spmv(c, c->d_cp, c->d_cq, K.sc, it);
                         else {
                             k_cg_spmv<<<K.gN, 256, 0, c->stream>>>(K.N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv,
-                                                                   c->d_cp, c->d_cq, K.sc, it);
+                                                                   c->d_cp, c->d_cq, K.sc, it, c->d_gpart,
+                                                                   c->d_gcount);
                             c->kernels += 1;
                         }
                     }
@@ -584,12 +563,14 @@ int run_hartree(ofks_ctx *c) {
             spmv(it);
             {
                 ProfScope pu(c, PF_POISSON_VEC);
-                k_cg_update_r<<<gU, 256, 0, c->stream>>>(N, c->d_minv, c->d_cp, c->d_cq, c->d_U, c->d_cr, sc, it);
+                k_cg_update_r<<<gU, 256, 0, c->stream>>>(N, c->d_minv, c->d_cp, c->d_cq, c->d_U, c->d_cr, sc, it,
+                                                         c->d_gpart, c->d_gcount);
             }
             precond();
             {
                 ProfScope pu(c, PF_POISSON_VEC);
-                k_cg_rz<<<gU, 256, 0, c->stream>>>(N, c->d_cr, c->d_cz, c->d_cp, sc, (it + 1) & 1, 0);
+                k_cg_rz<<<gU, 256, 0, c->stream>>>(N, c->d_cr, c->d_cz, c->d_cp, sc, (it + 1) & 1, 0, c->d_gpart,
+                                                   c->d_gcount);
                 k_cg_dir<<<gU, 256, 0, c->stream>>>(N, c->d_cz, c->d_cp, sc, it);
             }
             c->kernels += 3;
@@ -599,7 +580,7 @@ int run_hartree(ofks_ctx *c) {
             {
                 ProfScope pu(c, PF_POISSON_VEC);
                 k_cg_update<<<gU, 256, 0, c->stream>>>(N, c->d_minv, c->d_cp, c->d_cq, c->d_U, c->d_cr,
-                                                       c->d_cz, sc, it);
+                                                       c->d_cz, sc, it, c->d_gpart, c->d_gcount);
                 k_cg_dir<<<gU, 256, 0, c->stream>>>(N, c->d_cz, c->d_cp, sc, it);
             }
             c->kernels += 2;
@@ -622,11 +603,12 @@ template <class E>
 int launch_potential_refresh(ofks_ctx *c, E *valH, const E *valL) {
     ProfScope ps(c, PF_POTENTIAL);
     const int64_t T = c->n_tets;
-    k_half_copy<E><<<(unsigned)((c->sell_len + 255) / 256), 256, 0, c->stream>>>(c->sell_len, valL, valH);
-    cudaMemsetAsync(c->d_sc + SC_EDC, 0, sizeof(double), c->stream);
+    E *ve = reinterpret_cast<E *>(c->d_ve);
     k_potential<E><<<(unsigned)((T + 127) / 128), 128, 0, c->stream>>>(
-        T, c->d_tetn, c->d_emap, c->d_wq, c->d_vext, c->d_rho, c->d_U, c->prm.hartree ? 1 : 0,
-        c->prm.xc ? 1 : 0, c->d_vh, c->d_vxc, c->d_exc, valH, c->d_sc + SC_EDC);
+        T, c->d_tetn, c->d_wq, c->d_vext, c->d_rho, c->d_U, c->prm.hartree ? 1 : 0, c->prm.xc ? 1 : 0, c->d_vh,
+        c->d_vxc, c->d_exc, ve, c->d_sc + SC_EDC, c->d_gpart, c->d_gcount);
+    k_h_gather<E><<<(unsigned)((c->sell_len + 255) / 256), 256, 0, c->stream>>>(c->sell_len, c->d_hptr, c->d_hlist,
+                                                                               ve, valL, valH);
     c->kernels += 2;
     return ofks_cuda_check(c, cudaGetLastError(), "potential kernel");
 }

@@ -25,11 +25,11 @@ constexpr int F0 = 4;
 
 __device__ __forceinline__ float bf(float w) { return __bfloat162float(__float2bfloat16(w)); }
 
-// column sums of z^2 and of log(diag) (float64)
+// column sums of z^2 and of log(diag) (float64): the block's partials of column c to
+// stats[c grid + block] and stats[(p + c) grid + block]
 __global__ void __launch_bounds__(256) k_feat_stats(int64_t n, int p, const float *__restrict__ G,
                                                     const double *__restrict__ dL, const double *__restrict__ dB,
                                                     const double *__restrict__ shift, double *stats) {
-    // stats[c] = sum z^2, stats[p + c] = sum log diag
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t S = (int64_t)gridDim.x * blockDim.x / p * p;
     const int c = (int)(gid % p);
@@ -43,9 +43,10 @@ __global__ void __launch_bounds__(256) k_feat_stats(int64_t n, int p, const floa
             a += (double)(z * z);
             b += (double)logf(d);
         }
-        atomicAdd(stats + c, a);
-        atomicAdd(stats + p + c, b);
     }
+    // per-block column partials, added in block order by launch_col_fin
+    col_partial(a, gid < S, p, p, stats);
+    col_partial(b, gid < S, p, p, stats + (int64_t)p * gridDim.x);
 }
 
 // features (rows (i, c)), the column scales s_c and the Jacobi diagonals diag (n x p)
@@ -148,21 +149,20 @@ __global__ void k_output(int64_t n, int p, const float *__restrict__ F, const fl
     D[e] = scale[e % p] * (F[e * F0] + y[e]);
 }
 
-// loss pieces: num[c] = sum (D - D*)^2, den[c] = sum D*^2 (float64)
+// loss pieces: num[c] = sum (D - D*)^2, den[c] = sum D*^2 (float64), as per-block column partials
 __global__ void __launch_bounds__(256) k_loss(int64_t n, int p, const float *__restrict__ D, const float *__restrict__ Ds,
                                               double *acc) {
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t S = (int64_t)gridDim.x * blockDim.x / p * p;
-    const int c = (int)(gid % p);
-    if (gid >= S) return;
     double a = 0.0, b = 0.0;
-    for (int64_t e = gid; e < n * p; e += S) {
+    for (int64_t e = gid; gid < S && e < n * p; e += S) {
         const double r = (double)D[e] - (double)Ds[e];
         a += r * r;
         b += (double)Ds[e] * (double)Ds[e];
     }
-    atomicAdd(acc + c, a);
-    atomicAdd(acc + p + c, b);
+    // per-block column partials, added in block order by launch_col_fin
+    col_partial(a, gid < S, p, p, acc);
+    col_partial(b, gid < S, p, p, acc + (int64_t)p * gridDim.x);
 }
 
 // dL/dy = 2 s_c (D - D*) / den_c / p
@@ -431,8 +431,11 @@ int gcn_forward(ofks_ctx *c, const double *shift, bool keep) {
     int64_t off[3][3];
     offsets(H, off);
     ProfScope ps(c, PF_GCN);
-    cudaMemsetAsync(g.stats, 0, sizeof(double) * 2 * p, c->stream);
-    k_feat_stats<<<gr_stride(rows), 256, 0, c->stream>>>(n, (int)p, g.G32, c->d_dL, c->d_dB, shift, g.stats);
+    {
+        const unsigned gs = gr_stride(rows);
+        k_feat_stats<<<gs, 256, 0, c->stream>>>(n, (int)p, g.G32, c->d_dL, c->d_dB, shift, c->d_cpart);
+        launch_col_fin(c, (int)(2 * p), (int)(2 * p), gs, c->d_cpart, g.stats);
+    }
     k_features<<<gr(rows), 256, 0, c->stream>>>(n, (int)p, g.G32, c->d_dL, c->d_dB, shift, g.stats, g.F, g.scale, g.diag);
     // layer 0: F (4) -> H1
     aggregate(c, g.valA, g.F, g.AH, F0);
@@ -464,8 +467,11 @@ int gcn_backward(ofks_ctx *c, double *loss) {
     offsets(H, off);
     const int64_t m = gcn_param_count(H);
     cudaMemsetAsync(g.grad, 0, sizeof(double) * m, c->stream);
-    cudaMemsetAsync(g.lacc, 0, sizeof(double) * 2 * p, c->stream);
-    k_loss<<<gr_stride(rows), 256, 0, c->stream>>>(n, (int)p, g.Dn, g.Ds, g.lacc);
+    {
+        const unsigned gs = gr_stride(rows);
+        k_loss<<<gs, 256, 0, c->stream>>>(n, (int)p, g.Dn, g.Ds, c->d_cpart);
+        launch_col_fin(c, (int)(2 * p), (int)(2 * p), gs, c->d_cpart, g.lacc);
+    }
     k_dy<<<gr(rows), 256, 0, c->stream>>>(n, (int)p, g.Dn, g.Ds, g.scale, g.lacc, g.y);   // g.y <- dL/dy
     const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 31) / 32, 152LL * 4));
     // layer 2 (H -> 1): dZ = dy; grads; dH2 = dy w^T, dAH2 = dy u^T

@@ -67,7 +67,8 @@ __device__ __forceinline__ void grad_loads(uint64_t *bar, float *dst, const floa
 __global__ void __launch_bounds__(256, 1) k_grad_tc(int64_t n, int p, int ld, int KP, int nh, int tcols,
                                                     const float *__restrict__ HX, const float *__restrict__ BX,
                                                     const double *__restrict__ C, const double *__restrict__ L0,
-                                                    float *G, double *kkt2, int *err) {
+                                                    float *G, double *kkt2, int *err, double *gpart,
+                                                    unsigned *gcount) {
     extern __shared__ __align__(128) unsigned char rsm[];
     const int NP = 2 * nh;
     float *raw = reinterpret_cast<float *>(rsm);                              // 2 x (B X, H X) tiles
@@ -225,10 +226,9 @@ __global__ void __launch_bounds__(256, 1) k_grad_tc(int64_t n, int p, int ld, in
     part = warp_sum(part);
     if (lane == 0) red[warp] = part;
     __syncthreads();
+    double cta_kkt2 = 0.0;                       // this CTA's |R|^2, added over the grid at the end
+    for (int w = 0; w < 8; ++w) cta_kkt2 += red[w];
     if (tid == 0) {
-        double s = 0.0;
-        for (int w = 0; w < 8; ++w) s += red[w];
-        atomicAdd(kkt2, s);
         asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // our G stores have landed
         if (abort_flag) {
             atomicExch(err, 1);
@@ -243,6 +243,8 @@ __global__ void __launch_bounds__(256, 1) k_grad_tc(int64_t n, int p, int ld, in
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
+    const double tot[1] = {cta_kkt2};
+    grid_accumulate<1>(tot, gpart, gcount, [&](int, double v) { *kkt2 += v; });
 }
 
 }  // namespace
@@ -260,7 +262,7 @@ bool launch_grad_tc(ofks_ctx *c, const float *HX, const float *BX, float *G, dou
     const unsigned grid = (unsigned)(ntile < 152 ? ntile : 152);
     cudaFuncSetAttribute(k_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_grad_tc<<<grid, 256, smem, c->stream>>>(c->n, c->p, ld, KP, nh, tcols, HX, BX, c->d_C, c->d_L0, G, kkt2,
-                                              c->d_flag + 2);
+                                              c->d_flag + 2, c->d_gpart, c->d_gcount);
     c->kernels += 1;
     return true;
 }

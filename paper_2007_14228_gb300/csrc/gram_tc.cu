@@ -68,8 +68,8 @@ __device__ __forceinline__ void issue_loads(uint64_t *bar, float *dst, const flo
 }
 
 __global__ void __launch_bounds__(256, 1) k_gram_tc(int64_t n, int p, int ld, int nh, int tcols, const float *__restrict__ X,
-                                                    const float *__restrict__ A, const float *__restrict__ B, double *XA,
-                                                    double *XB, int *err) {
+                                                    const float *__restrict__ A, const float *__restrict__ B, double *part,
+                                                    int *err) {
     extern __shared__ __align__(128) unsigned char gsm[];
     const int NP = 2 * nh;
     float *raw = reinterpret_cast<float *>(gsm);                           // 2 buffers x 3 x GKS x ld
@@ -181,10 +181,16 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(int64_t n, int p, int ld, in
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const int col = cb + q;
-                const int j = col < nh ? col : col - nh;
+                const int m = col < nh ? 0 : 1, j = col < nh ? col : col - nh;
                 if (j < i || j >= p) continue;
-                atomicAdd((col < nh ? XA : XB) + (int64_t)i * ld + j, (double)__uint_as_float(v[q]));
+                part[(((int64_t)m * ld + i) * ld + j) * gridDim.x + blockIdx.x] = (double)__uint_as_float(v[q]);
             }
+        }
+    }
+    if (abort_flag || T == 0) {                // no accumulator: this CTA's partials are zero
+        for (int e = tid; e < 2 * ld * ld; e += blockDim.x) {
+            const int m = e / (ld * ld), i = (e / ld) % ld, j = e % ld;
+            if (i <= j && j < p) part[(((int64_t)m * ld + i) * ld + j) * gridDim.x + blockIdx.x] = 0.0;
         }
     }
     if (abort_flag) {
@@ -207,9 +213,10 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(int64_t n, int p, int ld, in
 }  // namespace
 
 // Tensor-core Grams for float32 blocks; false when the shapes do not suit it (the caller then
-// runs the CUDA-core kernel).  The outputs must be zero on entry; the lower triangles are left
-// to k_mirror2.
-bool launch_gram_tc(ofks_ctx *c, const float *X, const float *A, const float *B, double *XA, double *XB) {
+// runs the CUDA-core kernel).  Each CTA writes its partial upper triangles of X^T A and X^T B to
+// part, entry (m, i, j) of CTA u at ((m ld + i) ld + j) units + u; k_gram_fin adds them in CTA
+// order and mirrors.
+bool launch_gram_tc(ofks_ctx *c, const float *X, const float *A, const float *B, double *part, int64_t *units) {
     const int ld = c->ld;
     if (!c->prm.gram_tc || ld < 4 || ld % 4 || ld > 64 || c->n < GKS) return false;
     const int nh = (ld + 15) / 16 * 16, NP = 2 * nh;
@@ -218,7 +225,8 @@ bool launch_gram_tc(ofks_ctx *c, const float *X, const float *A, const float *B,
     const int64_t nslab = (c->n + GKS - 1) / GKS;
     const unsigned grid = (unsigned)std::min<int64_t>(nslab, 152);
     cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_gram_tc<<<grid, 256, smem, c->stream>>>(c->n, c->p, ld, nh, tcols, X, A, B, XA, XB, c->d_flag + 2);
+    k_gram_tc<<<grid, 256, smem, c->stream>>>(c->n, c->p, ld, nh, tcols, X, A, B, part, c->d_flag + 2);
     c->kernels += 1;
+    *units = grid;
     return true;
 }

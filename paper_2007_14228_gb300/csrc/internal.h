@@ -23,6 +23,12 @@ enum {
     SC_COUNT = 32
 };
 
+// Capacity (doubles) of the grid_accumulate partials: K block totals per block of a grid.
+constexpr int64_t GACC_CAP = 1 << 20;
+// Least capacity (doubles) of the per-column partials: the Grams' split tiles need up to
+// (608 + 16) units x 2 x 64 x 64.
+constexpr int64_t CPART_MIN = 6 << 20;
+
 // Rows of the per-column scalar array ctx->d_colA (each ld float64 long).
 enum { CB_SHIFT = 0, CB_ACTIVE = 1, CB_RZ = 2, CB_RZN = 3, CB_PQ = 4, CB_BETA = 5, CB_NORM = 6,
        CB_ALPHA = 7, CB_ACC = 8, CB_COUNT = 9 };
@@ -144,7 +150,8 @@ struct ofks_ctx {
     // per tetrahedron
     int *d_tetf = nullptr;                       // T x 10 free ids (-1 on the boundary)
     int *d_tetn = nullptr;                       // T x 10 node ids
-    int *d_emap = nullptr;                       // T x 100 SELL positions (-1 if not free)
+    int *d_hptr = nullptr, *d_hlist = nullptr;   // per SELL position, its element entries t 100 + 10 a + b
+    int *d_nptr = nullptr, *d_nlist = nullptr;   // per node, its element entries t 10 + a
     double *d_wq = nullptr;                      // T: |T|/4
     double *d_yq = nullptr;                      // T x 4 x 3 quadrature points minus centre
     double *d_vext = nullptr;                    // T x 4
@@ -167,6 +174,7 @@ struct ofks_ctx {
 
     // ---- quadrature and Hartree fields
     double *d_rho = nullptr, *d_vh = nullptr, *d_vxc = nullptr, *d_exc = nullptr;
+    double *d_ve = nullptr;                      // T x 4 weighted potentials w V_q (float32 or float64)
     double *d_U = nullptr, *d_rhs = nullptr, *d_cr = nullptr, *d_cz = nullptr, *d_cp = nullptr,
            *d_cq = nullptr;
 
@@ -188,6 +196,13 @@ struct ofks_ctx {
     double *d_sc = nullptr;                      // SC_COUNT scalars
     double *d_rec = nullptr;                     // iteration record (device)
     int *d_flag = nullptr;                       // error / status flags
+    // deterministic reductions (common.cuh): grid_accumulate partials (GACC_CAP doubles) and its
+    // block counter; per-column partials [column][unit] of the block kernels (cpart_cap doubles)
+    double *d_gpart = nullptr;
+    unsigned *d_gcount = nullptr;
+    double *d_cpart = nullptr;
+    int64_t cpart_cap = 0;
+    int64_t pq_units = 0, rz_units = 0;          // partial units of the last PCG apply / vector update
     double *nuclei_stage = nullptr;              // device address of the no-allocation nuclei staging array
 
     // ---- iteration state (host mirror)
@@ -293,7 +308,8 @@ void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, i
 // ---- block.cu (tall-skinny products and vector updates)
 template <class T> void launch_gram2(ofks_ctx *c, const T *X, const T *A, const T *B, double *XA, double *XB);
 // gram_tc.cu: the float32 Grams on the tensor cores (false: shapes not supported)
-bool launch_gram_tc(ofks_ctx *c, const float *X, const float *A, const float *B, double *XA, double *XB);
+// partials of X^T A and X^T B per CTA into part (entry-major, *units CTAs), added by k_gram_fin
+bool launch_gram_tc(ofks_ctx *c, const float *X, const float *A, const float *B, double *part, int64_t *units);
 // grad_tc.cu: G = H X + B X C and |H X - B X Lambda0|^2 on the tensor cores (false: not supported)
 bool launch_grad_tc(ofks_ctx *c, const float *HX, const float *BX, float *G, double *kkt2);
 template <class T> void launch_grad_update(ofks_ctx *c, Blocks<T> &b);
@@ -335,8 +351,10 @@ void launch_pack_f32(ofks_ctx *c, const float *src, double *dst);
 void launch_small_update(ofks_ctx *c);
 void launch_small_record(ofks_ctx *c);
 void launch_eta(ofks_ctx *c);
-void launch_pcg_alpha(ofks_ctx *c, int w, double *cb);
-void launch_pcg_beta(ofks_ctx *c, int w, double *cb);
+void launch_pcg_alpha(ofks_ctx *c, int w, int pc, double *cb);
+void launch_pcg_beta(ofks_ctx *c, int w, int pc, double *cb);
+// out[j] (j < ktot) = fixed-order sum of part[j * units + u] over u for j < kact, else 0
+void launch_col_fin(ofks_ctx *c, int kact, int ktot, int64_t units, const double *part, double *out);
 // the compact form's per-column arrays: shift of the active columns, everything else zero
 void launch_pcg_compact_cols(ofks_ctx *c, int w, int nact, const int *cmap, double *colC);
 void launch_cholesky_inv(ofks_ctx *c, const double *S, double *Rinv);

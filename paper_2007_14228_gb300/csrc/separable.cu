@@ -105,7 +105,8 @@ bool axis_modes(const std::vector<double> &x, std::vector<double> &S, std::vecto
 template <class E>
 __global__ void __launch_bounds__(256) k_sep_gather(int nx, int ny, int nz, int ldc, int Ly, int Lz,
                                                     const double *__restrict__ pv, const double *__restrict__ qv,
-                                                    double *U, double *r, E *t, double *sc, int it) {
+                                                    double *U, double *r, E *t, double *sc, int it, double *gpart,
+                                                    unsigned *gcount) {
     __shared__ double sh[8];
     __shared__ double s_alpha;
     if (threadIdx.x == 0) {
@@ -132,11 +133,9 @@ __global__ void __launch_bounds__(256) k_sep_gather(int nx, int ny, int nz, int 
         t[ab * ldc + c] = (E)(float)ri;
     }
     if (it >= 0) {
-        rr = block_sum(rr, sh);
-        if (threadIdx.x == 0) {
-            atomicAdd(sc + 4 + ((it + 1) & 1), rr);
-            if (blockIdx.x == 0) sc[2 + ((it + 1) & 1)] = 0.0;
-        }
+        if (threadIdx.x == 0 && blockIdx.x == 0) sc[2 + ((it + 1) & 1)] = 0.0;
+        const double tot[1] = {block_sum(rr, sh)};
+        grid_accumulate<1>(tot, gpart, gcount, [&](int, double v) { sc[4 + ((it + 1) & 1)] += v; });
     }
 }
 
@@ -144,7 +143,8 @@ __global__ void __launch_bounds__(256) k_sep_gather(int nx, int ny, int nz, int 
 template <class E>
 __global__ void __launch_bounds__(256) k_sep_scatter(int nx, int ny, int nz, int ldc, int Ly, int Lz,
                                                      const E *__restrict__ t, const double *__restrict__ r, double *z,
-                                                     double *pv, double *sc, int slot) {
+                                                     double *pv, double *sc, int slot, double *gpart,
+                                                     unsigned *gcount) {
     __shared__ double sh[8];
     const int64_t n = (int64_t)nx * ny * nz;
     double rz = 0.0;
@@ -156,8 +156,8 @@ __global__ void __launch_bounds__(256) k_sep_scatter(int nx, int ny, int nz, int
         if (pv) pv[i] = zi;
         rz = fma(r[i], zi, rz);
     }
-    rz = block_sum(rz, sh);
-    if (threadIdx.x == 0) atomicAdd(sc + slot, rz);
+    const double tot[1] = {block_sum(rz, sh)};
+    grid_accumulate<1>(tot, gpart, gcount, [&](int, double v) { sc[slot] += v; });
 }
 
 // Batched row-major GEMM C_z = A_z B_z (M x K times K x N), float32, 64 x 64 tiles, 256
@@ -514,7 +514,8 @@ void sep_cg_step(ofks_ctx *c, int it, int slot, int first) {
             P.out = out; P.M1 = M1; P.M2 = M2; P.KPo = KPo;
         };
         k_sep_gather<__nv_bfloat16><<<g, 256, 0, c->stream>>>(nx, ny, nz, pz, c->st.Ly, c->st.Lz, c->d_cp, c->d_cq,
-                                                              c->d_U, c->d_cr, B[0], sc, it);
+                                                              c->d_U, c->d_cr, B[0], sc, it, c->d_gpart,
+                                                              c->d_gcount);
         pass(B[0], S.hSt[2], nx * ny, nz, nz, B[1], nx, ny, py);           // [a][b][c] -> [k][a][b]
         sep_tc_launch<0>(c, P);
         pass(B[1], S.hSt[1], nz * nx, ny, ny, B[2], nz, nx, px);           // -> [j][k][a]
@@ -529,12 +530,13 @@ void sep_cg_step(ofks_ctx *c, int it, int slot, int first) {
         pass(B[5], S.hS[0], ny * nz, nx, nx, B[0], ny, nz, pz);            // -> [a][b][c]
         sep_tc_launch<0>(c, P);
         k_sep_scatter<__nv_bfloat16><<<g, 256, 0, c->stream>>>(nx, ny, nz, pz, c->st.Ly, c->st.Lz, B[0], c->d_cr,
-                                                               c->d_cz, first ? c->d_cp : nullptr, sc, slot);
+                                                               c->d_cz, first ? c->d_cp : nullptr, sc, slot,
+                                                               c->d_gpart, c->d_gcount);
         c->kernels += 2;
         return;
     }
     k_sep_gather<float><<<g, 256, 0, c->stream>>>(nx, ny, nz, nz, c->st.Ly, c->st.Lz, c->d_cp, c->d_cq, c->d_U,
-                                                  c->d_cr, S.t0, sc, it);
+                                                  c->d_cr, S.t0, sc, it, c->d_gpart, c->d_gcount);
     // forward: T1[ab][k] = sum_c R[ab][c] Sz[c][k]
     gemm(c, 1, nx * ny, nz, nz, S.t0, 0, S.S[2], 0, S.t1, 0);
     // T2[a][j][k] = sum_b Sy^T[j][b] T1[a][b][k]
@@ -548,6 +550,6 @@ void sep_cg_step(ofks_ctx *c, int it, int slot, int first) {
     // Z[ab][c] = sum_k U2[ab][k] Sz^T[k][c]
     gemm(c, 1, nx * ny, nz, nz, S.t1, 0, S.St[2], 0, S.t0, 0);
     k_sep_scatter<float><<<g, 256, 0, c->stream>>>(nx, ny, nz, nz, c->st.Ly, c->st.Lz, S.t0, c->d_cr, c->d_cz,
-                                                   first ? c->d_cp : nullptr, sc, slot);
+                                                   first ? c->d_cp : nullptr, sc, slot, c->d_gpart, c->d_gcount);
     c->kernels += 2;
 }

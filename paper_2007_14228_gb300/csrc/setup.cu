@@ -51,12 +51,31 @@ void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)> &f) {
     for (auto &t : th) t.join();
 }
 
-// One tetrahedron: geometry, local L by the 4-point rule (exact for its degree-2 integrand),
-// local B from the closed-form table; scatter into the free SELL arrays and the full CSR.
-__global__ void k_assemble(int64_t T, const int *__restrict__ tetn, const double *__restrict__ xyz,
-                           const int *__restrict__ emap, const int64_t *__restrict__ fmap,
-                           double *valL, double *valB, double *fval, double *wq, double *yq,
-                           double cx, double cy, double cz, int *flag) {
+// Inverse of an element-to-entry map: for each target position, the element entries k (in
+// increasing k) with map[k] == position; map values < 0 are skipped.  Counting sort.
+template <class I>
+void invert_map(const std::vector<I> &map, int64_t npos, std::vector<int> &ptr, std::vector<int> &list) {
+    ptr.assign(npos + 1, 0);
+    for (const I v : map)
+        if (v >= 0) ptr[v + 1]++;
+    for (int64_t i = 0; i < npos; ++i) ptr[i + 1] += ptr[i];
+    list.resize(ptr[npos]);
+    std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t k = 0; k < (int64_t)map.size(); ++k)
+        if (map[k] >= 0) list[fill[map[k]]++] = (int)k;
+}
+
+// index of (a, b), a <= b, in the upper triangle of a 10 x 10 local matrix stored row by row
+__host__ __device__ inline int up10(int a, int b) {
+    if (a > b) { const int t = a; a = b; b = t; }
+    return a * 10 - a * (a - 1) / 2 + (b - a);
+}
+
+// One tetrahedron: geometry, the upper triangle of its local stiffness by the 4-point rule
+// (exact for its degree-2 integrand), |T|/4 and the quadrature points.  The local matrices go
+// to lloc (T x 55); k_gather_lb / k_gather_full add them into the global arrays.
+__global__ void k_element(int64_t T, const int *__restrict__ tetn, const double *__restrict__ xyz, double *lloc,
+                          double *wq, double *yq, double cx, double cy, double cz, int *flag) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= T) return;
     const int *tn = tetn + t * 10;
@@ -77,9 +96,8 @@ __global__ void k_assemble(int64_t T, const int *__restrict__ tetn, const double
         g[0][d] = -(g[1][d] + g[2][d] + g[3][d]);
     }
     const double vol = fabs(det) / 6.0, w = 0.25 * vol;
-    double Lloc[10][10];
-    for (int i = 0; i < 10; ++i)
-        for (int j = 0; j < 10; ++j) Lloc[i][j] = 0.0;
+    double Lloc[55];
+    for (int i = 0; i < 55; ++i) Lloc[i] = 0.0;
     for (int q = 0; q < 4; ++q) {
         double G[10][3];
         for (int a = 0; a < 4; ++a) {
@@ -94,21 +112,9 @@ __global__ void k_assemble(int64_t T, const int *__restrict__ tetn, const double
         }
         for (int i = 0; i < 10; ++i)
             for (int j = i; j < 10; ++j)
-                Lloc[i][j] += w * (G[i][0] * G[j][0] + G[i][1] * G[j][1] + G[i][2] * G[j][2]);
+                Lloc[up10(i, j)] += w * (G[i][0] * G[j][0] + G[i][1] * G[j][1] + G[i][2] * G[j][2]);
     }
-    const int *em = emap + t * 100;
-    const int64_t *fm = fmap + t * 100;
-    for (int i = 0; i < 10; ++i)
-        for (int j = 0; j < 10; ++j) {
-            double lv = (j >= i) ? Lloc[i][j] : Lloc[j][i];
-            double bv = vol * (double)c_mass420[i][j] / 420.0;
-            atomicAdd(fval + fm[i * 10 + j], lv);
-            int pos = em[i * 10 + j];
-            if (pos >= 0) {
-                atomicAdd(valL + pos, lv);
-                atomicAdd(valB + pos, bv);
-            }
-        }
+    for (int i = 0; i < 55; ++i) lloc[t * 55 + i] = Lloc[i];
     wq[t] = w;
     for (int q = 0; q < 4; ++q) {
         double x[3] = {0, 0, 0};
@@ -118,6 +124,38 @@ __global__ void k_assemble(int64_t T, const int *__restrict__ tetn, const double
         yq[(t * 4 + q) * 3 + 1] = x[1] - cy;
         yq[(t * 4 + q) * 3 + 2] = x[2] - cz;
     }
+}
+
+// Free-pattern values by gathering, in list order, the element entries that land on each SELL
+// position (list entry t 100 + 10 a + b: entry (a, b) of tetrahedron t): L from the local
+// stiffness, B = |T| m_ab / 420 from the closed-form P2 mass table.  Positions without entries
+// (padding) get zero.  A gather adds in a fixed order, so the values are the same on every run.
+__global__ void k_gather_lb(int64_t npos, const int *__restrict__ ptr, const int *__restrict__ list,
+                            const double *__restrict__ lloc, const double *__restrict__ wq, double *valL,
+                            double *valB) {
+    const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (pos >= npos) return;
+    double l = 0.0, b = 0.0;
+    for (int k = ptr[pos]; k < ptr[pos + 1]; ++k) {
+        const int code = list[k], t = code / 100, ab = code - 100 * t, a = ab / 10, bb = ab - 10 * a;
+        l += lloc[(int64_t)t * 55 + up10(a, bb)];
+        b += 4.0 * wq[t] * (double)c_mass420[a][bb] / 420.0;
+    }
+    valL[pos] = l;
+    valB[pos] = b;
+}
+
+// Full-node stiffness of the Hartree problem, gathered the same way
+__global__ void k_gather_full(int64_t npos, const int *__restrict__ ptr, const int *__restrict__ list,
+                              const double *__restrict__ lloc, double *fval) {
+    const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (pos >= npos) return;
+    double l = 0.0;
+    for (int k = ptr[pos]; k < ptr[pos + 1]; ++k) {
+        const int code = list[k], t = code / 100, ab = code - 100 * t;
+        l += lloc[(int64_t)t * 55 + up10(ab / 10, ab % 10)];
+    }
+    fval[pos] = l;
 }
 
 __global__ void k_diagonals(int64_t n, const int64_t *__restrict__ dpos, const double *valL,
@@ -192,9 +230,10 @@ void free_mesh(ofks_ctx *c) {
     dev_free(c->d_slice_ptr); dev_free(c->d_slice_w); dev_free(c->d_cols); dev_free(c->d_perm);
     dev_free(c->d_valL); dev_free(c->d_valB); dev_free(c->d_valH); dev_free(c->d_dL); dev_free(c->d_dB);
     dev_free(c->d_fptr); dev_free(c->d_fcol); dev_free(c->d_fval); dev_free(c->d_minv);
-    dev_free(c->d_tetf); dev_free(c->d_tetn); dev_free(c->d_emap); dev_free(c->d_wq); dev_free(c->d_yq);
+    dev_free(c->d_tetf); dev_free(c->d_tetn); dev_free(c->d_hptr); dev_free(c->d_hlist); dev_free(c->d_nptr);
+    dev_free(c->d_nlist); dev_free(c->d_wq); dev_free(c->d_yq);
     dev_free(c->d_vext); dev_free(c->d_bnd); dev_free(c->d_bxyz); dev_free(c->d_ynode);
-    dev_free(c->d_rho); dev_free(c->d_vh); dev_free(c->d_vxc); dev_free(c->d_exc);
+    dev_free(c->d_rho); dev_free(c->d_vh); dev_free(c->d_vxc); dev_free(c->d_exc); dev_free(c->d_ve);
     dev_free(c->d_U); dev_free(c->d_rhs); dev_free(c->d_cr); dev_free(c->d_cz); dev_free(c->d_cp);
     dev_free(c->d_cq);
     amg_free(c);
@@ -385,9 +424,16 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
     std::vector<int> fptr32(N + 1);
     if (nnz_full >= ((int64_t)1 << 31)) return ofks_fail(c, OFKS_EINVAL, "set_mesh: full pattern exceeds 2^31");
     for (int64_t i = 0; i <= N; ++i) fptr32[i] = (int)fptr[i];
-    double *d_xyz = nullptr;
-    int64_t *d_fmap = nullptr, *d_dpos = nullptr, *d_fdiag = nullptr;
-    int *d_interior = nullptr, *d_flag = nullptr;
+    // inverse element-to-entry maps: the assembly and the Hamiltonian refresh gather each entry's
+    // element contributions in a fixed order (no floating-point atomics)
+    std::vector<int> hptr, hlist, gptr, glist, nptr, nlist;
+    invert_map(emap, sell_len, hptr, hlist);
+    invert_map(fmap, nnz_full, gptr, glist);
+    invert_map(tetn, N, nptr, nlist);
+    std::vector<int64_t>().swap(fmap);
+    double *d_xyz = nullptr, *d_lloc = nullptr;
+    int64_t *d_dpos = nullptr, *d_fdiag = nullptr;
+    int *d_interior = nullptr, *d_flag = nullptr, *d_gptr = nullptr, *d_glist = nullptr;
     if ((rc = dev_upload(c, &c->d_slice_ptr, slice_ptr.data(), slice_ptr.size())) ||
         (rc = dev_upload(c, &c->d_slice_w, slice_w.data(), slice_w.size())) ||
         (rc = dev_upload(c, &c->d_cols, cols.data(), cols.size())) ||
@@ -400,39 +446,48 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
         (rc = dev_zeros(c, &c->d_fval, nnz_full)) || (rc = dev_zeros(c, &c->d_minv, N)) ||
         (rc = dev_upload(c, &c->d_tetf, tetf.data(), tetf.size())) ||
         (rc = dev_upload(c, &c->d_tetn, tetn.data(), tetn.size())) ||
-        (rc = dev_upload(c, &c->d_emap, emap.data(), emap.size())) ||
+        (rc = dev_upload(c, &c->d_hptr, hptr.data(), hptr.size())) ||
+        (rc = dev_upload(c, &c->d_hlist, hlist.data(), hlist.size())) ||
+        (rc = dev_upload(c, &c->d_nptr, nptr.data(), nptr.size())) ||
+        (rc = dev_upload(c, &c->d_nlist, nlist.data(), nlist.size())) ||
+        (rc = dev_upload(c, &d_gptr, gptr.data(), gptr.size())) ||
+        (rc = dev_upload(c, &d_glist, glist.data(), glist.size())) ||
+        (rc = dev_zeros(c, &d_lloc, T * 55)) ||
         (rc = dev_zeros(c, &c->d_wq, T)) || (rc = dev_zeros(c, &c->d_yq, T * 12)) ||
         (rc = dev_zeros(c, &c->d_vext, T * 4)) ||
         (rc = dev_upload(c, &c->d_bnd, bnd.data(), bnd.size())) ||
         (rc = dev_upload(c, &c->d_bxyz, bxyz.data(), bxyz.size())) ||
         (rc = dev_upload(c, &c->d_ynode, ynode.data(), ynode.size())) ||
         (rc = dev_zeros(c, &c->d_rho, T * 4)) || (rc = dev_zeros(c, &c->d_vh, T * 4)) ||
+        (rc = dev_zeros(c, &c->d_ve, T * 4)) ||
         (rc = dev_zeros(c, &c->d_vxc, T * 4)) || (rc = dev_zeros(c, &c->d_exc, T * 4)) ||
         (rc = dev_zeros(c, &c->d_U, N)) || (rc = dev_zeros(c, &c->d_rhs, N)) ||
         (rc = dev_zeros(c, &c->d_cr, N)) || (rc = dev_zeros(c, &c->d_cz, N)) ||
         (rc = dev_zeros(c, &c->d_cp, N)) || (rc = dev_zeros(c, &c->d_cq, N)) ||
         (rc = dev_upload(c, &d_xyz, xyz, (size_t)N * 3)) ||
-        (rc = dev_upload(c, &d_fmap, fmap.data(), fmap.size())) ||
         (rc = dev_upload(c, &d_dpos, dpos.data(), dpos.size())) ||
         (rc = dev_upload(c, &d_fdiag, fdiag.data(), fdiag.size())) ||
         (rc = dev_upload(c, &d_interior, interior.data(), interior.size())) ||
         (rc = dev_zeros(c, &d_flag, 1))) {
-        dev_free(d_xyz); dev_free(d_fmap); dev_free(d_dpos); dev_free(d_fdiag); dev_free(d_interior);
+        dev_free(d_xyz); dev_free(d_lloc); dev_free(d_gptr); dev_free(d_glist); dev_free(d_dpos); dev_free(d_fdiag); dev_free(d_interior);
         dev_free(d_flag);
         free_mesh(c);
         return rc;
     }
     const int B = 128;
-    k_assemble<<<(unsigned)((T + B - 1) / B), B, 0, c->stream>>>(
-        T, c->d_tetn, d_xyz, c->d_emap, d_fmap, c->d_valL, c->d_valB, c->d_fval, c->d_wq, c->d_yq,
-        c->center[0], c->center[1], c->center[2], d_flag);
+    k_element<<<(unsigned)((T + B - 1) / B), B, 0, c->stream>>>(T, c->d_tetn, d_xyz, d_lloc, c->d_wq, c->d_yq,
+                                                                 c->center[0], c->center[1], c->center[2], d_flag);
+    k_gather_lb<<<(unsigned)((sell_len + 255) / 256), 256, 0, c->stream>>>(sell_len, c->d_hptr, c->d_hlist, d_lloc,
+                                                                            c->d_wq, c->d_valL, c->d_valB);
+    k_gather_full<<<(unsigned)((nnz_full + 255) / 256), 256, 0, c->stream>>>(nnz_full, d_gptr, d_glist, d_lloc,
+                                                                              c->d_fval);
     k_diagonals<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, d_dpos, c->d_valL, c->d_valB,
                                                                      c->d_dL, c->d_dB);
     k_jacobi_full<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(N, d_fdiag, c->d_fval, d_interior,
                                                                        c->d_minv);
     if ((rc = stencil_setup(c, N, xyz, fptr.data(), fcol.data(), dirichlet)) != OFKS_OK ||
         (rc = sep_setup(c, xyz, dirichlet)) != OFKS_OK) {
-        dev_free(d_xyz); dev_free(d_fmap); dev_free(d_dpos); dev_free(d_fdiag); dev_free(d_interior);
+        dev_free(d_xyz); dev_free(d_lloc); dev_free(d_gptr); dev_free(d_glist); dev_free(d_dpos); dev_free(d_fdiag); dev_free(d_interior);
         dev_free(d_flag);
         free_mesh(c);
         return rc;
@@ -495,7 +550,7 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
                     (rc = dev_upload(c, &d_tpos, tpos.data(), tpos.size())) ||
                     (rc = dev_zeros(c, &c->d_tvalL, acc2)) || (rc = dev_zeros(c, &c->d_tvalB, acc2))) {
                     dev_free(d_tpos);
-                    dev_free(d_xyz); dev_free(d_fmap); dev_free(d_dpos); dev_free(d_fdiag); dev_free(d_interior);
+                    dev_free(d_xyz); dev_free(d_lloc); dev_free(d_gptr); dev_free(d_glist); dev_free(d_dpos); dev_free(d_fdiag); dev_free(d_interior);
                     dev_free(d_flag);
                     free_mesh(c);
                     return rc;
@@ -514,7 +569,7 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
     int hflag = 0;
     cudaError_t e = cudaMemcpyAsync(&hflag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    dev_free(d_xyz); dev_free(d_fmap); dev_free(d_dpos); dev_free(d_fdiag); dev_free(d_interior);
+    dev_free(d_xyz); dev_free(d_lloc); dev_free(d_gptr); dev_free(d_glist); dev_free(d_dpos); dev_free(d_fdiag); dev_free(d_interior);
     dev_free(d_flag);
     if (e != cudaSuccess) { free_mesh(c); return ofks_cuda_check(c, e, "mesh assembly"); }
     if (hflag) { free_mesh(c); return ofks_fail(c, OFKS_EINVAL, "set_mesh: degenerate tetrahedron"); }

@@ -83,10 +83,16 @@ __global__ void k_eta(int rule, int k, int have_prev, double eta_fixed, double e
     rec[3] = eta;
 }
 
-// alpha_c = rz_c / pq_c (0 if pq_c <= 0); clear rzn
-__global__ void k_pcg_alpha(int ld, double *cb) {
-    for (int j = threadIdx.x; j < ld; j += blockDim.x) {
-        const double pq = cb[CB_PQ * ld + j], rz = cb[CB_RZ * ld + j];
+// one block per column j: pq_j = the operator apply's partials of column j added in unit order
+// (0 for j >= pc); alpha_j = rz_j / pq_j (0 if pq_j <= 0); clear rzn
+__global__ void __launch_bounds__(256) k_pcg_alpha(int ld, int pc, int64_t units, const double *__restrict__ part,
+                                                   double *cb) {
+    __shared__ double sh[8];
+    const int j = blockIdx.x;
+    const double pq = j < pc ? ordered_sum(part + (int64_t)j * units, units, sh) : 0.0;
+    if (threadIdx.x == 0) {
+        const double rz = cb[CB_RZ * ld + j];
+        cb[CB_PQ * ld + j] = pq;
         cb[CB_ALPHA * ld + j] = (pq > 0.0 && cb[CB_ACC * ld + j] == 0.0) ? rz / pq : 0.0;
         cb[CB_RZN * ld + j] = 0.0;
     }
@@ -104,10 +110,16 @@ __global__ void k_pcg_compact_cols(int ld, int w, int nact, const int *__restric
     }
 }
 
-// beta_c = rzn_c / rz_c (0 if rz_c <= 0); rz <- rzn; clear pq
-__global__ void k_pcg_beta(int ld, double *cb) {
-    for (int j = threadIdx.x; j < ld; j += blockDim.x) {
-        const double rz = cb[CB_RZ * ld + j], rzn = cb[CB_RZN * ld + j];
+// one block per column j: rzn_j = the vector update's partials of column j added in unit order
+// (0 for j >= pc); beta_j = rzn_j / rz_j (0 if rz_j <= 0); rz <- rzn; clear pq
+__global__ void __launch_bounds__(256) k_pcg_beta(int ld, int pc, int64_t units, const double *__restrict__ part,
+                                                  double *cb) {
+    __shared__ double sh[8];
+    const int j = blockIdx.x;
+    const double rzn = j < pc ? ordered_sum(part + (int64_t)j * units, units, sh) : 0.0;
+    if (threadIdx.x == 0) {
+        const double rz = cb[CB_RZ * ld + j];
+        cb[CB_RZN * ld + j] = rzn;
         cb[CB_BETA * ld + j] = rz > 0.0 ? rzn / rz : 0.0;
         cb[CB_RZ * ld + j] = rzn;
         cb[CB_PQ * ld + j] = 0.0;
@@ -290,8 +302,14 @@ void launch_eta(ofks_ctx *c) { c->kernels += 1;
                                   c->prm.eta_max, c->d_sc, c->d_rec);
 }
 
-void launch_pcg_alpha(ofks_ctx *c, int w, double *cb) { c->kernels += 1; k_pcg_alpha<<<1, 256, 0, c->stream>>>(w, cb); }
-void launch_pcg_beta(ofks_ctx *c, int w, double *cb) { c->kernels += 1; k_pcg_beta<<<1, 256, 0, c->stream>>>(w, cb); }
+void launch_pcg_alpha(ofks_ctx *c, int w, int pc, double *cb) {
+    c->kernels += 1;
+    k_pcg_alpha<<<w, 256, 0, c->stream>>>(w, pc, c->pq_units, c->d_cpart, cb);
+}
+void launch_pcg_beta(ofks_ctx *c, int w, int pc, double *cb) {
+    c->kernels += 1;
+    k_pcg_beta<<<w, 256, 0, c->stream>>>(w, pc, c->rz_units, c->d_cpart, cb);
+}
 void launch_pcg_compact_cols(ofks_ctx *c, int w, int nact, const int *cmap, double *colC) {
     c->kernels += 1;
     k_pcg_compact_cols<<<1, 256, 0, c->stream>>>(c->ld, w, nact, cmap, c->d_colA, colC);

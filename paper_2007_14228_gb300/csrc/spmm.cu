@@ -71,8 +71,10 @@ inline int spw_for(int64_t units) {
     return units / SPW >= fill ? SPW : (units / 2 >= fill ? 2 : 1);
 }
 
-// MODE 0: Y = A X.  MODE 1: also colsum[c] += sum_rows X[r,c] Y[r,c] (float64 accumulators).
-// T is the element type of the values and blocks; sums run in T.
+// MODE 0: Y = A X.  MODE 1: also the column sums sum_rows X[r,c] Y[r,c] of the warp's slices,
+// written (float64) to part[c * nsg + g] for slice group g (nsg groups of spw slices), to be
+// added in group order (launch_col_fin).  T is the element type of the values and blocks; sums
+// run in T.
 template <class T, int W, int MODE>
 __global__ void __launch_bounds__(256) k_sell_spmm(int64_t nwarps, int nchunks, int64_t n_slices, int spw_, int p, int ld,
                                                    const int *__restrict__ slice_ptr,
@@ -81,7 +83,7 @@ __global__ void __launch_bounds__(256) k_sell_spmm(int64_t nwarps, int nchunks, 
                                                    const int *__restrict__ perm,
                                                    const T *__restrict__ val,
                                                    const T *__restrict__ X, T *__restrict__ Y,
-                                                   double *colsum) {
+                                                   double *part) {
     const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (wg >= nwarps) return;                       // whole warp leaves together
@@ -119,17 +121,19 @@ __global__ void __launch_bounds__(256) k_sell_spmm(int64_t nwarps, int nchunks, 
         }
     }
     if constexpr (MODE == 1) {
+        const int64_t nsg = (n_slices + spw - 1) / spw, g = wg / nchunks;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
             const T t = warp_sum_t(cs[w]);
-            if (lane == 0 && c0 + w < p) atomicAdd(colsum + c0 + w, (double)t);
+            if (lane == 0) part[(int64_t)(c0 + w) * nsg + g] = (double)t;
         }
     }
 }
 
 // One Jacobi-PCG operator apply for all columns at once (Eq. precondition-T):
 //   TZ = (L/2) Z - B Z diag(shift)  gathered over the neighbours of each row, then for the
-//   own row  P <- Z + beta P,  Q <- TZ + beta Q  (so T P = Q), and pq[c] += P.Q.
+//   own row  P <- Z + beta P,  Q <- TZ + beta Q  (so T P = Q), and the column sums P.Q of the
+// warp's slices to part[c * nsg + g] (slice group g; added in group order by k_pcg_alpha).
 // With first = 1: P = Z, Q = TZ.
 template <class T, int W>
 __global__ void __launch_bounds__(256) k_pcg_apply(int64_t nwarps, int nchunks, int64_t n_slices, int spw, int p, int ld,
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(256) k_pcg_apply(int64_t nwarps, int nchunks, 
                                                    const T *__restrict__ valB,
                                                    const T *__restrict__ Z, T *P, T *Q,
                                                    const double *__restrict__ beta_col,
-                                                   const double *__restrict__ shift, double *pq,
+                                                   const double *__restrict__ shift, double *part,
                                                    int first) {
     const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -191,16 +195,17 @@ __global__ void __launch_bounds__(256) k_pcg_apply(int64_t nwarps, int nchunks, 
             store_w<T, W>(Q + (int64_t)r * ld + c0, qr);
         }
     }
+    const int64_t nsg = (n_slices + spw - 1) / spw, g = wg / nchunks;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
         const T t = warp_sum_t(contrib[w]);
-        if (lane == 0 && c0 + w < p) atomicAdd(pq + c0 + w, (double)t);
+        if (lane == 0) part[(int64_t)(c0 + w) * nsg + g] = (double)t;
     }
 }
 
 // The float32 PCG apply on the type-grouped SELL with every PCG block chunk-major: element
 // (r, c) at ((c / 4) ns + r) 4 + c % 4 (ns = n rounded up to 32).  A warp takes spw consecutive
-// slices in turn for one 4-column chunk and adds its column sums pq once at the end.  Its lanes are
+// slices in turn for one 4-column chunk and writes its column sums P.Q once at the end.  Its lanes are
 // 32 rows of one lattice node type two lattice steps apart, so for one entry index their neighbour
 // rows are (mostly) two rows apart too: the 32 16-byte gathers fall in ~8 lines of the chunk's
 // ns x 16 B array, and the rows' 27 neighbourhoods overlap, so most of them hit L1.  The lanes'
@@ -216,7 +221,7 @@ __global__ void __launch_bounds__(256) k_pcg_apply_zc(int64_t nwarps, int nchunk
                                                       const float *__restrict__ valB,
                                                       const float *__restrict__ Zc, float *P, float *Q,
                                                       const double *__restrict__ beta_col,
-                                                      const double *__restrict__ shift, double *pq, int first) {
+                                                      const double *__restrict__ shift, double *part, int first) {
     const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (wg >= nwarps) return;
@@ -267,10 +272,11 @@ __global__ void __launch_bounds__(256) k_pcg_apply_zc(int64_t nwarps, int nchunk
         *reinterpret_cast<float4 *>(Pk + o) = make_float4(pr[0], pr[1], pr[2], pr[3]);
         *reinterpret_cast<float4 *>(Qk + o) = make_float4(qr[0], qr[1], qr[2], qr[3]);
     }
+    const int64_t nsg = (n_slices + spw - 1) / spw, g = wg / nchunks;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
         const float t = warp_sum_t(contrib[w]);
-        if (lane == 0 && c0 + w < p) atomicAdd(pq + c0 + w, (double)t);
+        if (lane == 0) part[(int64_t)(c0 + w) * nsg + g] = (double)t;
     }
 }
 
@@ -284,7 +290,7 @@ inline int chunk_width(int ld) { return (ld % 4 == 0) ? 4 : (ld % 2 == 0 ? 2 : 1
 // ld columns (VPL consecutive floats each), so one gather instruction reads two contiguous
 // neighbour rows; both half-warps share the slice, whose column ids and values are read with
 // half-warp broadcasts and stay in L1 for the slice's other rows.  Warps stride over
-// (slice, row pair) items; column sums are reduced in the block and added once per block.
+// (slice, row pair) items; column sums are reduced in the block and written once per block.
 constexpr int RW = 8;                  // warps per block
 
 template <int VPL>
@@ -334,7 +340,8 @@ __device__ __forceinline__ void rows_epilogue(int r, int ld, int c0, int first, 
     }
 }
 
-// MODE 0: Y = A X.  MODE 1: Y = A X and colsum[c] += X[:,c].Y[:,c].  MODE 2: the PCG apply of
+// MODE 0: Y = A X.  MODE 1: Y = A X and the block's column sums X[:,c].Y[:,c] into part[c grid +
+// block].  MODE 2: the PCG apply of
 // k_pcg_apply (X = Z, Y = P, Y2 = Q, A = L values, B = B values).  Each half-warp carries two
 // rows of the same slice, so two independent gathers are in flight per step of the entry loop.
 template <int VPL, int MODE>
@@ -343,7 +350,7 @@ __global__ void __launch_bounds__(RW * 32) k_rows_f32(int n_slices, int p, int l
                                                       const int *__restrict__ perm, const float *__restrict__ valA,
                                                       const float *__restrict__ valB, const float *__restrict__ X,
                                                       float *Y, float *Y2, const double *__restrict__ beta_col,
-                                                      const double *__restrict__ shift, double *colsum, int first) {
+                                                      const double *__restrict__ shift, double *part, int first) {
     __shared__ float red[RW][VPL * 16];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4;
     const int c0 = (lane & 15) * VPL;
@@ -397,11 +404,12 @@ __global__ void __launch_bounds__(RW * 32) k_rows_f32(int n_slices, int p, int l
         float t = 0.f;
 #pragma unroll
         for (int w = 0; w < RW; ++w) t += red[w][c];
-        atomicAdd(colsum + c, (double)t);
+        part[(int64_t)c * gridDim.x + blockIdx.x] = (double)t;
     }
 }
 
-// half-warp-per-row launch for float32 blocks; false when the shapes do not suit it
+// half-warp-per-row launch for float32 blocks; false when the shapes do not suit it.  MODE 1 adds
+// the column sums into colsum; MODE 2 leaves its column partials for k_pcg_alpha (pq_units).
 template <int MODE>
 bool launch_rows_f32(ofks_ctx *c, int ld, int pc, const float *valA, const float *valB, const float *X, float *Y, float *Y2,
                      const double *beta_col, const double *shift, double *colsum, int first) {
@@ -411,12 +419,14 @@ bool launch_rows_f32(ofks_ctx *c, int ld, int pc, const float *valA, const float
 #define R_(v)                                                                                                      \
     k_rows_f32<v, MODE><<<grid, RW * 32, 0, c->stream>>>(c->n_slices, pc, ld, c->d_slice_ptr, c->d_slice_w,     \
                                                          c->d_cols, c->d_perm, valA, valB, X, Y, Y2, beta_col,    \
-                                                         shift, colsum, first)
+                                                         shift, c->d_cpart, first)
     if (ld <= 64) R_(4);
     else if (ld <= 128) R_(8);
     else R_(16);
 #undef R_
     c->kernels += 1;
+    if (MODE == 1) launch_col_fin(c, pc, pc, grid, c->d_cpart, colsum);
+    if (MODE == 2) c->pq_units = grid;
     return true;
 }
 
@@ -442,13 +452,14 @@ void launch_sell_spmm_colnorm(ofks_ctx *c, const T *val, const T *X, T *Y, doubl
         if (launch_rows_f32<1>(c, c->ld, c->p, val, nullptr, X, Y, nullptr, nullptr, nullptr, colsum, 0)) return;
     const int W = chunk_width(c->ld), nch = c->ld / W;
     const int spw = spw_for((int64_t)c->n_slices * nch);
-    const int64_t nw = (((int64_t)c->n_slices + spw - 1) / spw) * nch;
+    const int64_t nsg = ((int64_t)c->n_slices + spw - 1) / spw, nw = nsg * nch;
     const unsigned grid = (unsigned)((nw * 32 + 255) / 256);
 #define L_(w) k_sell_spmm<T, w, 1><<<grid, 256, 0, c->stream>>>(nw, nch, (int64_t)c->n_slices, spw, c->p, c->ld, c->d_slice_ptr, \
-        c->d_slice_w, c->d_cols, c->d_perm, val, X, Y, colsum)
+        c->d_slice_w, c->d_cols, c->d_perm, val, X, Y, c->d_cpart)
     if (W == 4) L_(4); else if (W == 2) L_(2); else L_(1);
 #undef L_
     c->kernels += 1;
+    launch_col_fin(c, c->p, c->p, nsg, c->d_cpart, colsum);
 }
 
 template <class T>
@@ -458,12 +469,13 @@ void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, i
         if (zc) {
             const int nch = w / 4;
             const int spw = spw_for((int64_t)c->n_tslices * nch);
-            const int64_t nw = (((int64_t)c->n_tslices + spw - 1) / spw) * nch;
+            const int64_t nsg = ((int64_t)c->n_tslices + spw - 1) / spw, nw = nsg * nch;
             k_pcg_apply_zc<<<(unsigned)((nw * 32 + 255) / 256), 256, 0, c->stream>>>(
                 nw, nch, (int64_t)c->n_tslices, spw, pc, c->n_slots, c->d_tslice_ptr, c->d_tslice_w, c->d_tcols,
-                c->d_tperm, c->d_tvalL, c->d_tvalB, (const float *)Zin, (float *)P, (float *)Q, beta_col, shift, pq,
-                first);
+                c->d_tperm, c->d_tvalL, c->d_tvalB, (const float *)Zin, (float *)P, (float *)Q, beta_col, shift,
+                c->d_cpart, first);
             c->kernels += 1;
+            c->pq_units = nsg;
             return;
         }
     }
@@ -471,13 +483,14 @@ void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, i
         if (launch_rows_f32<2>(c, w, pc, valL, valB, Zin, P, Q, beta_col, shift, pq, first)) return;
     const int W = chunk_width(w), nch = w / W;
     const int spw = spw_for((int64_t)c->n_slices * nch);
-    const int64_t nw = (((int64_t)c->n_slices + spw - 1) / spw) * nch;
+    const int64_t nsg = ((int64_t)c->n_slices + spw - 1) / spw, nw = nsg * nch;
     const unsigned grid = (unsigned)((nw * 32 + 255) / 256);
 #define L_(v) k_pcg_apply<T, v><<<grid, 256, 0, c->stream>>>(nw, nch, (int64_t)c->n_slices, spw, pc, w, c->d_slice_ptr, \
-        c->d_slice_w, c->d_cols, c->d_perm, valL, valB, Zin, P, Q, beta_col, shift, pq, first)
+        c->d_slice_w, c->d_cols, c->d_perm, valL, valB, Zin, P, Q, beta_col, shift, c->d_cpart, first)
     if (W == 4) L_(4); else if (W == 2) L_(2); else L_(1);
 #undef L_
     c->kernels += 1;
+    c->pq_units = nsg;
 }
 
 template <class T>

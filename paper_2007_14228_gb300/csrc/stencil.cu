@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(256) k_st_apply(int Ly, int Lz, const StencilT
                                                   const StencilEntry *__restrict__ ents,
                                                   const double *__restrict__ val, const double *__restrict__ minv,
                                                   const double *__restrict__ xv, const double *__restrict__ bv,
-                                                  double w, double *yv, double *sc, int it) {
+                                                  double w, double *yv, double *sc, int it, double *gpart,
+                                                  unsigned *gcount) {
     __shared__ StencilType st[8];
     __shared__ StencilEntry se[ST_MAXE];
     __shared__ double sh[8];
@@ -101,14 +102,12 @@ __global__ void __launch_bounds__(256) k_st_apply(int Ly, int Lz, const StencilT
         }
     }
     if (MODE == 0) {
-        pq = block_sum(pq, sh);
-        if (threadIdx.x == 0) {
-            atomicAdd(sc + 2 + (it & 1), pq);
-            if (blockIdx.x == 0) {
-                sc[0 + ((it + 1) & 1)] = 0.0;
-                sc[4 + ((it + 1) & 1)] = 0.0;
-            }
+        if (threadIdx.x == 0 && blockIdx.x == 0) {
+            sc[0 + ((it + 1) & 1)] = 0.0;
+            sc[4 + ((it + 1) & 1)] = 0.0;
         }
+        const double tot[1] = {block_sum(pq, sh)};
+        grid_accumulate<1>(tot, gpart, gcount, [&](int, double v) { sc[2 + (it & 1)] += v; });
     }
 }
 
@@ -280,18 +279,21 @@ void stencil_fill(ofks_ctx *c) {
 
 void launch_stencil_spmv(ofks_ctx *c, const double *p, double *q, double *sc, int it) {
     k_st_apply<0><<<(unsigned)c->st.blocks, 256, 0, c->stream>>>(c->st.Ly, c->st.Lz, c->st.d_type, c->st.d_ent,
-                                                                c->st.val, c->d_minv, p, nullptr, 0.0, q, sc, it);
+                                                                c->st.val, c->d_minv, p, nullptr, 0.0, q, sc, it,
+                                                                c->d_gpart, c->d_gcount);
     c->kernels += 1;
 }
 
 void launch_stencil_residual(ofks_ctx *c, const double *x, const double *b, double *r) {
     k_st_apply<1><<<(unsigned)c->st.blocks, 256, 0, c->stream>>>(c->st.Ly, c->st.Lz, c->st.d_type, c->st.d_ent,
-                                                                c->st.val, c->d_minv, x, b, 0.0, r, nullptr, 0);
+                                                                c->st.val, c->d_minv, x, b, 0.0, r, nullptr, 0,
+                                                                nullptr, nullptr);
     c->kernels += 1;
 }
 
 void launch_stencil_jacobi(ofks_ctx *c, const double *x, const double *b, double w, double *y) {
     k_st_apply<2><<<(unsigned)c->st.blocks, 256, 0, c->stream>>>(c->st.Ly, c->st.Lz, c->st.d_type, c->st.d_ent,
-                                                                c->st.val, c->d_minv, x, b, w, y, nullptr, 0);
+                                                                c->st.val, c->d_minv, x, b, w, y, nullptr, 0,
+                                                                nullptr, nullptr);
     c->kernels += 1;
 }

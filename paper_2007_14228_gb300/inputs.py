@@ -27,6 +27,14 @@ is graded toward it with a tanh map of strength g=3.  Each hexahedron is split i
 the 6 Kuhn tetrahedra around its (0,0,0)-(1,1,1) diagonal, so the mesh is
 conforming; P2 nodes are the vertices plus the physical midpoints of the straight
 edges, i.e. the full (2N+1)-lattice of the tensor-product coordinates.
+
+Second grading (``make_mesh(system, grading="msf")``): the paper's mesh-size function
+(Eq. meshsizefunction, Sec. 4.2), h(r) = min(gamma1 Z_1^{-2/5} r_1^{6/5}, ..., gamma1 Z_M^{-2/5}
+r_M^{6/5}, gamma2), restricted to each axis (r_j = |x - X_j| along the axis, the finest size any
+point of that coordinate plane asks for).  The paper meshes with Gmsh (unstructured); here the
+same size function grades the tensor-product grid (``axis_vertices_msf``): the spacing follows
+h's shape (held at its value 0.05 bohr from the largest charge nearer than that), scaled to the
+cell budget; per axis the anchors are as above and the vertices equidistribute 1/spacing.
 """
 from __future__ import annotations
 
@@ -221,16 +229,69 @@ def axis_vertices(lo: float, hi: float, n_cells: int, nuclei_coords, g: float = 
     return np.concatenate(pts)
 
 
+GAMMA1, GAMMA2 = 0.125, 8.0      # Sec. 5.1: gamma_1 = 0.125, gamma_2 = 8 (the smaller molecules)
+
+
+def mesh_size_1d(x, coords, Z, gamma1=GAMMA1, gamma2=GAMMA2):
+    """Eq. (meshsizefunction) along one axis: min_j gamma1 Z_j^(-2/5) |x - X_j|^(6/5), capped at gamma2."""
+    x = np.asarray(x, dtype=np.float64)
+    h = np.full(x.shape, float(gamma2))
+    for X, z in zip(coords, Z):
+        h = np.minimum(h, gamma1 * float(z) ** -0.4 * np.abs(x - float(X)) ** 1.2)
+    return h
+
+
+MSF_R0 = 0.05                    # bohr: the size function is held at its value there nearer a nucleus
+
+
+def axis_vertices_msf(lo: float, hi: float, n_cells: int, nuclei_coords, Z, gamma1: float = GAMMA1,
+                      gamma2: float = GAMMA2, r0: float = MSF_R0, tol: float = MERGE_TOL,
+                      samples: int = 200001) -> np.ndarray:
+    """Vertex coordinates (n_cells + 1 values) of one axis graded by the mesh-size function.
+
+    The spacing is C max(h(x), h(r0)) with h the size function of Eq. (meshsizefunction) along the
+    axis (largest charge for h(r0)) and C the one scale that spends exactly the cell budget (the
+    paper's sizes are those of an unstructured mesh; a tensor-product grid of the same local sizes
+    would need far more cells, so the shape is kept and the scale fitted).  Cells go to the
+    segments between anchors in proportion to the integral of 1/spacing and equidistribute it
+    inside each segment.
+    """
+    xs = np.linspace(lo, hi, samples)
+    zmax = float(np.max(Z)) if len(Z) else 1.0
+    shape = np.maximum(mesh_size_1d(xs, nuclei_coords, Z, gamma1, gamma2), gamma1 * zmax ** -0.4 * r0 ** 1.2)
+    dens = 1.0 / shape
+    cum = np.concatenate([[0.0], np.cumsum(0.5 * (dens[1:] + dens[:-1]) * np.diff(xs))])
+    # the scale C only stretches the cumulative count, so equidistribution does not depend on it
+    inner = _merge(list(nuclei_coords), lo, hi, tol)
+    anchors = [lo] + inner + [hi]
+    ca = np.interp(anchors, xs, cum)
+    nseg = _split_cells(np.diff(ca), n_cells)
+    pts = [np.array([lo])]
+    for sgm in range(len(anchors) - 1):
+        targets = ca[sgm] + (ca[sgm + 1] - ca[sgm]) * np.arange(1, nseg[sgm] + 1) / nseg[sgm]
+        x = np.interp(targets, cum, xs)
+        x[-1] = anchors[sgm + 1]
+        pts.append(x)
+    return np.concatenate(pts)
+
+
 # Kuhn split: one tetrahedron per ordering of the three axes.
 KUHN_PERMS = tuple(itertools.permutations((0, 1, 2)))
 EDGES = ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))
 
 
-def make_mesh(system: System, g: float = GRADING) -> Mesh:
+def make_mesh(system: System, g: float = GRADING, grading: str = "tanh") -> Mesh:
+    """The P2 mesh of a system: tanh grading (default) or the mesh-size function ("msf")."""
     axes = []
     for d in range(3):
-        v = axis_vertices(float(system.box_lo[d]), float(system.box_hi[d]), int(system.cells[d]),
-                          system.R[:, d], g)
+        if grading == "msf":
+            v = axis_vertices_msf(float(system.box_lo[d]), float(system.box_hi[d]), int(system.cells[d]),
+                                  system.R[:, d], system.Z)
+        elif grading == "tanh":
+            v = axis_vertices(float(system.box_lo[d]), float(system.box_hi[d]), int(system.cells[d]),
+                              system.R[:, d], g)
+        else:
+            raise ValueError(f"unknown grading {grading}")
         lat = np.empty(2 * len(v) - 1)
         lat[0::2] = v
         lat[1::2] = 0.5 * (v[:-1] + v[1:])

@@ -120,3 +120,24 @@ def test_mixed_form_with_moptqr_reaches_the_float64_fixed_point(ofks):
         ctx.close()
     assert abs(out["fp64"][0] - out["mixed"][0]) < 1e-8
     np.testing.assert_allclose(out["fp64"][1], out["mixed"][1], atol=1e-7)
+
+
+def test_size_function_mesh_follows_the_oracle(ofks):
+    # the mesh-size-function grading (Eq. meshsizefunction) keeps the tensor-product lattice, so the
+    # lattice-stencil Hartree operator and the separable preconditioner still apply; 12 iterates
+    # agree with the oracle on it
+    s = I.lih().with_cells((10, 10, 10))
+    m = I.make_mesh(s, grading="msf")
+    ctx = ofks.context_for(s, m, beta=10.0)
+    info = ctx.poisson_info()
+    assert info["format"] == "lattice" and info["precond"] == "separable"
+    pr = pcal.Problem(m.xyz, m.tet10, m.dirichlet, s.Z, s.R, pcal.Params(p=s.p, occ=s.occ, beta=10.0))
+    V = I.initial_block(m.n_free, s.p, 0)
+    ctx.init_orbitals(V)
+    st = pcal.State(X=pr.initial_guess(V))
+    for k in range(12):
+        g = ctx.step(1)
+        o = pcal.iterate(pr, st)
+        assert abs(g["e_total"] - o["E"]) < 1e-8 * max(1.0, abs(o["E"])), (k, g["e_total"], o["E"])
+        assert abs(g["kkt"] - o["kkt"]) < 1e-7 * o["kkt"], (k, g["kkt"], o["kkt"])
+    ctx.close()

@@ -68,8 +68,11 @@ def workload(name):
 def config_of(args, s, sizes):
     return {"workload": f"{s.name}: {len(s.Z)} nuclei, {'x'.join(map(str, s.cells))} hex cells -> P2 tets",
             "n_free": sizes["n"], "n_tets": sizes["n_tets"], "n_q": sizes["n_q"], "p": s.p, "occ": s.occ,
-            "beta": 10.0, "form": "mixed: float32 iterations, float64 p x p / energy / tests (plain float64 beside it)",
-            "precond": "PCG x8 (Eq. precondition-T)", "eta": "BB2",
+            "beta": 10.0,
+            "form": ("learned-preconditioner mixed form: float32 iterations with the graph network (bf16 weights, "
+                     "float32 activations) in place of the PCG, judged per column by its residual, PCG as fallback; "
+                     "float64 p x p / energy / tests; plain float64 and mixed + PCG beside it"),
+            "precond": "learned (width 64, committed weights), PCG x8 fallback (Eq. precondition-T)", "eta": "BB2",
             "hartree": ("CG on the lattice-stencil stiffness, separable (fast-diagonalization) preconditioner, "
                         "tolerance max(1e-12, min(1e-4, 0.01 (kkt+fea)/kkt0)) in both forms"),
             "l2": "inputs larger than L2 (working set ~7 GB)", "parallelism": f"replicas x{args.gpus}",
@@ -179,11 +182,12 @@ def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, spmv_model=(0, 0), ele
     """Dominant kernel family by time: algorithmic bytes and flops per launch / mean duration.
 
     Every family is one kernel launch per timed scope except "poisson" (the whole Hartree
-    solve) and "poisson_vec" (two vector kernels per CG iteration), which are left out of the
-    choice; the solve's SpMV kernel is the "poisson_spmv" family.  The PCG apply works on the
+    solve), "poisson_vec" (two vector kernels per CG iteration) and "gcn" (one application of the
+    learned preconditioner's network, a dozen kernels), which are left out of the choice; the
+    solve's SpMV kernel is the "poisson_spmv" family.  The PCG apply works on the
     active columns only (their count rounded up to 4): pcg_w is its mean block width over the
     timed launches."""
-    leaves = {k: v for k, v in prof.items() if k not in ("poisson", "poisson_vec") and v["launches"]}
+    leaves = {k: v for k, v in prof.items() if k not in ("poisson", "poisson_vec", "gcn") and v["launches"]}
     fam = max(leaves, key=lambda k: leaves[k]["ms"])
     st = prof[fam]
     per = st["ms"] / max(st["launches"], 1) * 1e-3
@@ -270,30 +274,89 @@ def shifts_with_active(p, active):
     return sh
 
 
-def time_to_target(ofks, I, target=1e-6, fea_max=1e-7):
-    """Wall time from the first iteration to the first iterate with |E - E*| <= 1e-6 Ha and
-    fea <= 1e-7 on the LiH workload (24^3 cells, p = 2), for the plain float64 and the mixed
-    forms; E* from a float64 solve to (kkt + fea)/kkt0 < 1e-11 on the same mesh."""
-    s = I.lih()
-    m = I.make_mesh(s)
-    V = I.initial_block(m.n_free, s.p, 0)
-    ref = ofks.context_for(s, m, beta=10.0, tol=1e-11, max_iter=6000)
-    ref.init_orbitals(V)
-    r = ref.solve(allow_notconv=True)
-    E_star = r["e_total"]
-    ref.close()
-    out = {"workload": "lih 24^3 cells (n = 103,823, p = 2)", "E_star": E_star, "E_star_iters": r["iters"]}
-    for form in ("fp64", "mixed"):
-        ctx = ofks.context_for(s, m, beta=10.0, tol=1e-9, max_iter=6000, precision=form, poisson_adaptive=1)
-        ctx.init_orbitals(V)
-        res = ctx.solve(allow_notconv=True)
-        h = ctx.history()
-        ctx.close()
-        hit = [(row[0], row[1]) for row in h if abs(row[2] - E_star) <= target and row[4] <= fea_max]
-        out[form] = {"seconds": round(hit[0][1], 3) if hit else None, "iters": int(hit[0][0]) if hit else None,
-                     "solve_iters": res["iters"], "switch_iter": res["switch_iter"]}
-    if out["fp64"]["seconds"] and out["mixed"]["seconds"]:
-        out["speedup"] = round(out["fp64"]["seconds"] / out["mixed"]["seconds"], 3)
+def first_hit(hist, E_star, target=1e-6, fea_max=1e-7):
+    """(seconds, iteration) of the first evaluated iterate with |E - E*| <= target and fea <= fea_max
+    (history rows: k, seconds since the initial guess, E, kkt, fea, eta), or (None, None)."""
+    for row in hist:
+        if abs(row[2] - E_star) <= target and row[4] <= fea_max:
+            return round(float(row[1]), 3), int(row[0])
+    return None, None
+
+
+def run_form(ofks, s, m, V, budget_s, chunk=100, E_star=None, tol=1e-10, learned=False, **params):
+    """One solve from the seeded start in chunks of `chunk` iterations until it converges, reaches
+    the target (when E_star is given) or spends budget_s seconds; returns its record."""
+    kw = dict(beta=10.0, tol=tol, max_iter=10 ** 7, poisson_adaptive=1)
+    kw.update(params)
+    if learned:
+        kw["precond"] = "learned"
+    ctx = ofks.context_for(s, m, **kw)
+    if learned:
+        ctx.precond_set_weights(ofks.trained_weights())
+    ctx.init_orbitals(V)
+    t0 = time.perf_counter()
+    r = None
+    hit = (None, None)
+    while time.perf_counter() - t0 < budget_s:
+        r = ctx.step(chunk)
+        if E_star is not None:
+            hit = first_hit(ctx.history(chunk + 1), E_star)
+            if hit[0] is not None:
+                break
+        if r["converged"]:
+            break
+    h = ctx.history()
+    ctx.close()
+    if E_star is not None and hit[0] is None:
+        hit = first_hit(h, E_star)
+    last = h[-1]
+    return {"hist": h, "seconds": hit[0], "iters": hit[1], "ran_iters": int(last[0]),
+            "ran_seconds": round(float(last[1]), 3), "E_last": float(last[2]), "fea_last": float(last[4]),
+            "converged": bool(r and r["converged"]), "switch_iter": r["switch_iter"] if r else None,
+            "judge_accept": r["judge_accept"] if r else 0, "judge_total": r["judge_total"] if r else 0}
+
+
+def time_to_target(ofks, I, system, budgets, chunk=100, forms=("fp64", "mixed", "learned")):
+    """Wall time from the initial guess to the first iterate with |E - E*| <= 1e-6 Ha and
+    fea <= 1e-7 (seconds since ofks_init_orbitals, as the library's history records them), for the
+    plain float64 form, the mixed form with the paper's PCG and the mixed form with the learned
+    preconditioner.  E* is the energy of the mixed form converged to (kkt + fea)/kkt0 < 1e-10 (its
+    last iterations are the float64 sweep, so E* is a float64 fixed point); that run's own history
+    gives the mixed form's time.  A form that does not reach the target within its budget reports
+    seconds = None with the iterations and time it ran and its last |E - E*|."""
+    m = I.make_mesh(system)
+    V = I.initial_block(m.n_free, system.p, 0)
+    ref = run_form(ofks, system, m, V, budgets["mixed"], chunk, None, 1e-10, precision="mixed")
+    out = {"workload": f"{system.name}: {len(system.Z)} nuclei, {'x'.join(map(str, system.cells))} cells, "
+                       f"n = {m.n_free}, p = {system.p}",
+           "target": "|E - E*| <= 1e-6 Ha and fea <= 1e-7", "E_star_from": "mixed form to tol 1e-10",
+           "E_star_converged": ref["converged"], "E_star": ref["E_last"], "budgets_s": budgets}
+    E_star = ref["E_last"]
+    sec, it = first_hit(ref["hist"], E_star)
+    out["mixed"] = {"seconds": sec, "iters": it, "ran_iters": ref["ran_iters"], "ran_seconds": ref["ran_seconds"],
+                    "switch_iter": ref["switch_iter"]}
+    sw = ref["switch_iter"]
+    if sw is not None and sw > 0:
+        # the float32 iterations' floor against the float64 fixed point: the last float32 iterate
+        # before the float64 sweep (history row of iteration sw - 1)
+        rows = [r for r in ref["hist"] if int(r[0]) == sw - 1]
+        if rows:
+            out["mixed"]["float32_floor"] = {"dE": abs(float(rows[-1][2]) - E_star), "fea": float(rows[-1][4]),
+                                             "kkt_rel": float(rows[-1][3]) / float(ref["hist"][0][3])}
+    if not ref["converged"]:
+        out["note"] = "E* is the last energy of an unconverged run: times are lower bounds"
+    for form in forms:
+        if form == "mixed":
+            continue
+        rec = run_form(ofks, system, m, V, budgets[form], chunk, E_star, 1e-12,
+                       learned=(form == "learned"), precision="fp64" if form == "fp64" else "mixed")
+        out[form] = {k: rec[k] for k in ("seconds", "iters", "ran_iters", "ran_seconds")}
+        out[form]["dE_last"] = abs(rec["E_last"] - E_star)
+        if form == "learned":
+            out[form]["judge_accept"], out[form]["judge_total"] = rec["judge_accept"], rec["judge_total"]
+    for form in forms:
+        if form != "fp64" and out.get("fp64", {}).get("seconds") and out[form].get("seconds"):
+            out[f"speedup_{form}_vs_fp64"] = round(out["fp64"]["seconds"] / out[form]["seconds"], 3)
     return out
 
 
@@ -349,11 +412,19 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ttc", action="store_true", help="skip the time-to-1e-6 Ha runs")
-    ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner form")
+    ap.add_argument("--ttt-budget", type=float, nargs=3, default=[150.0, 240.0, 60.0],
+                    metavar=("MIXED", "FP64", "LEARNED"),
+                    help="seconds each form may run toward 1e-6 Ha on the chain (the mixed run also fixes E*)")
     ap.add_argument("--start", type=int, default=200, help="iterate of the seeded run the timed steps start from")
     ap.add_argument("--start-state", default=None,
                     help="state file of the start iterate: loaded if it exists, else written (profiling runs)")
+    ap.add_argument("--params", default="",
+                    help="extra ofks_params for every context, e.g. spmm_f32_rows=1,gram_tc=0 (profiling runs)")
     args = ap.parse_args()
+    args.extra = {}
+    for kv in filter(None, args.params.split(",")):
+        k, v = kv.split("=")
+        args.extra[k] = float(v) if "." in v or "e" in v else int(v)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -389,7 +460,7 @@ def main():
     # the preconditioner active, and that is the regime timed here.
     import tempfile
     state = args.start_state or os.path.join(tempfile.mkdtemp(prefix="ofks_bench_"), "start.state")
-    prep = ofks.context_for(s, m, device=local, beta=10.0, precision="mixed", poisson_adaptive=1)
+    prep = ofks.context_for(s, m, device=local, beta=10.0, precision="mixed", poisson_adaptive=1, **args.extra)
     if args.start_state and os.path.exists(args.start_state):
         prep.load_state(state)          # an earlier run prepared the same start iterate
         rp = prep.evaluate()
@@ -406,7 +477,7 @@ def main():
 
     def timed(precision, clocks_on, precond="pcg"):
         ctx = ofks.context_for(s, m, device=local, beta=10.0, precision=precision, poisson_adaptive=1,
-                               precond=precond)
+                               precond=precond, **args.extra)
         if precond == "learned":
             ctx.precond_set_weights(ofks.trained_weights())
         ctx.load_state(state)
@@ -438,17 +509,13 @@ def main():
     launches64 = prof64.pop("all_kernels", {"launches": None})["launches"]
     steps64 = args.steps
     ctx64.close()
-    # learned-preconditioner mixed form (the network judged by Eq. precondition-T's PCG)
-    learned = None
-    if not args.no_learned:
-        ctxl, resl, profl, _, tl = timed("mixed", False, "learned")
-        profl.pop("all_kernels", None)
-        learned = {"value": round(replica_value(world, args.steps, tl), 4), "unit": UNIT, "ms_per_step": round(tl / args.steps * 1e3, 3),
-                   "judge_accept": resl["judge_accept"], "judge_total": resl["judge_total"],
-                   "kernel_ms": {k: round(v["ms"], 3) for k, v in profl.items() if v["launches"]}}
-        ctxl.close()
-    # mixed form: float32 iterations (float64 p x p, energies, convergence test)
-    ctx, res, prof, clocks, t = timed("mixed", True)
+    # mixed form with the paper's PCG: float32 iterations (float64 p x p, energies, convergence test)
+    ctxm, resm, profm, _, tm = timed("mixed", False)
+    launchesm = profm.pop("all_kernels", {"launches": None})["launches"]
+    ctxm.close()
+    # the headline form: mixed precision with the learned preconditioner (the network judged by
+    # Eq. precondition-T's PCG, which also serves as its fallback)
+    ctx, res, prof, clocks, t = timed("mixed", True, "learned")
     launches = prof.pop("all_kernels", {"launches": None})["launches"]
     steps_done = args.steps
     value = replica_value(world, steps_done, t)
@@ -483,29 +550,39 @@ def main():
     sm, pm = poisson_spmv_model(sizes, pinfo), separable_model(pinfo)
     roof = roofline(prof, sizes["n_free"], s.p, sizes["nnz"], sizes["n_tets"], hbm_peak, hbm_kind, sm, 4, pm,
                     res["pcg_width"])
+    roofm = roofline(profm, sizes["n_free"], s.p, sizes["nnz"], sizes["n_tets"], hbm_peak, hbm_kind, sm, 4, pm,
+                     resm["pcg_width"])
     roof64 = roofline(prof64, sizes["n_free"], s.p, sizes["nnz"], sizes["n_tets"], hbm_peak, hbm_kind, sm, 8, pm,
                       res64["pcg_width"])
-    ttc = None if args.no_ttc else time_to_target(ofks, I)
+    ttc = None
+    if not args.no_ttc:
+        budgets = {"mixed": args.ttt_budget[0], "fp64": args.ttt_budget[1], "learned": args.ttt_budget[2]}
+        ttc = {"chain": time_to_target(ofks, I, s, budgets, chunk=100) if args.workload == "chain" else None,
+               "lih": time_to_target(ofks, I, I.lih(), {"mixed": 60, "fp64": 60, "learned": 60}, chunk=100)}
     cpu = None
     if not args.no_cpu and world == 1:
         cpu, _ = cpu_baseline(s, m, start_info["active_columns"])
+    kms = lambda pr: {k: round(v["ms"], 3) for k, v in pr.items() if v["launches"]}
     out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": steps_done,
            "warmup": args.warmup, "ms_per_step": round(t / steps_done * 1e3, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": config_of(args, s, I.sizes(s)), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-           "gpu_launches": None, "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items() if v["launches"]},
+           "gpu_launches": None, "kernel_ms": kms(prof),
            "kernel_launches": {k: v["launches"] for k, v in prof.items() if v["launches"]},
            "clocks": clocks, "E": res["e_total"], "kkt": res["kkt"], "fea": res["fea"],
+           "judge_accept": res["judge_accept"], "judge_total": res["judge_total"],
            "hartree_cg_iters_per_step": round(res["hartree_total"] / max(steps_done, 1), 1),
            "hartree_operator": pinfo,
            "plain_fp64": {"value": round(replica_value(world, steps64, t64), 4), "unit": UNIT,
                           "ms_per_step": round(t64 / steps64 * 1e3, 3), "gpu_launches": launches64,
-                          "roofline": roof64, "kernel_ms": {k: round(v["ms"], 3) for k, v in prof64.items()
-                                                            if v["launches"]},
+                          "roofline": roof64, "kernel_ms": kms(prof64),
                           "hartree_cg_iters_per_step": round(res64["hartree_total"] / max(steps64, 1), 1)},
+           "mixed_pcg": {"value": round(replica_value(world, args.steps, tm), 4), "unit": UNIT,
+                         "ms_per_step": round(tm / args.steps * 1e3, 3), "gpu_launches": launchesm,
+                         "roofline": roofm, "kernel_ms": kms(profm)},
            "speedup_vs_plain_fp64": round(value / replica_value(world, steps64, t64), 3),
-           "learned_mixed": learned, "start": start_info,
-           "time_to_1e-6_Ha": ttc}
+           "mixed_pcg_speedup_vs_plain_fp64": round(tm and (t64 / steps64) / (tm / args.steps), 3),
+           "start": start_info, "time_to_1e-6_Ha": ttc}
     out["gpu_launches"] = launches
     print(json.dumps(out), flush=True)
 

@@ -42,7 +42,9 @@ extern "C" {
 /* ---- enumerations ------------------------------------------------------------------ */
 #define OFKS_FP64          0   /* every step in float64 */
 #define OFKS_MIXED         1   /* float32 iterations (float64 p x p, energies, tests), then a
-                                  float64 refinement sweep once (kkt+fea)/kkt0 < mixed_tol */
+                                  float64 refinement sweep once (kkt+fea)/kkt0 < mixed_tol, or once
+                                  the float32 iterations have stalled below 1e-4 (no new best
+                                  (kkt+fea)/kkt0 in 300 iterations) */
 
 #define OFKS_PC_NONE       0   /* D = grad L_beta */
 #define OFKS_PC_PCG        1   /* T_i^{-1} grad by Jacobi-PCG, fixed pcg_iters, zero start */
@@ -118,7 +120,7 @@ typedef struct {
     int32_t poisson_max_iter;
     int32_t poisson_pc;     /* Hartree CG preconditioner: OFKS_HPC_JACOBI, OFKS_HPC_MULTIGRID or
                                OFKS_HPC_SEPARABLE (falls back to Jacobi where the mesh has none) */
-    double  mixed_tol;      /* OFKS_MIXED: hand over to float64 once (kkt+fea)/kkt0 < mixed_tol */
+    double  mixed_tol;      /* OFKS_MIXED: hand over to float64 once (kkt+fea)/kkt0 < mixed_tol (or on a stall) */
     double  poisson_tol_mixed; /* Hartree CG tolerance during the float32 iterations */
     double  judge_tau;      /* OFKS_PC_LEARNED: accept a column if |G - T D| <= judge_tau |G| and G.D > 0 */
     int32_t learned_tc;     /* 1: width-64 hidden layer on the tensor cores (bf16 operands) at inference */
@@ -143,6 +145,11 @@ typedef struct {
                                CG between residual checks) are captured once as CUDA graphs and
                                replayed; 0: every kernel is launched on its own.  Graphs are not
                                used while ofks_profile is on */
+    int32_t pcg_staged;     /* float32 PCG at block widths 8..32 (multiples of 4): 1 row-major blocks and
+                               an operator apply that stages the neighbour rows of each entry index
+                               through shared memory; 0 (default, measured 3 % faster per PCG on the
+                               chain with the vector updates included) the chunk-major blocks on the
+                               type-grouped SELL (lattice meshes) */
     int32_t method;         /* OFKS_METHOD_PCAL (default), OFKS_METHOD_PLAM or OFKS_METHOD_MOPTQR; the
                                stopping test (Sec. 4.1), the preconditioner (Eq. precondition-T, its
                                shifts from the method's multipliers) and eta are common to all three */
@@ -171,9 +178,9 @@ typedef struct {
 
 /* Fill *prm with the defaults: beta 10, occ 2, tol 1e-8, max_iter 1000, FP64, PCG with 8
  * iterations, BB2, eta in [1e-4, 1e8], Hartree and LDA on, multipole_lmax 2,
- * poisson_tol 1e-12, poisson_max_iter 20000, poisson_pc OFKS_HPC_SEPARABLE, mixed_tol 1e-5, poisson_tol_mixed
+ * poisson_tol 1e-12, poisson_max_iter 20000, poisson_pc OFKS_HPC_SEPARABLE, mixed_tol 1e-6, poisson_tol_mixed
  * 1e-8, judge_tau 0.5, learned_tc 1, poisson_adaptive 0, poisson_csr 0, gram_tc 1, spmm_f32_rows 0,
- * poisson_sep_tc 1, pcg_compact 1, cuda_graphs 1, method OFKS_METHOD_PCAL.  p is
+ * poisson_sep_tc 1, pcg_compact 1, cuda_graphs 1, pcg_staged 0, method OFKS_METHOD_PCAL.  p is
  * set to 1. */
 void ofks_default_params(ofks_params *prm);
 
@@ -333,6 +340,31 @@ int ofks_train_precond_step(ofks_ctx *ctx, const double *G, const double *shifts
 /* Loss and parameter gradients (float64, same layout as the weights) without a step. */
 int ofks_precond_grads(ofks_ctx *ctx, const double *G, const double *shifts, const double *Dstar,
                        double *grads, int64_t cap, double *loss);
+
+/* Append one training pair generated by the method itself at the current iterate to the pairs
+ * file at `path` (created with its header when absent): the gradient G = grad_X L_beta(X, Lambda)
+ * (n_free x p), the shifts diag(Lambda) of Eq. (lambda2), and the target D* = T^{-1} G of
+ * Eq. (precondition-T) solved to a 1e-12 relative residual (columns with a shift >= 0 take
+ * D* = G).  File layout, all little-endian: magic "OFKSPR1\0" (8 bytes), int64 n_free, int32 p,
+ * int32 zero; then per pair: float64 shifts[p], G[n_free x p], D*[n_free x p] (row-major).
+ * *active (may be NULL) receives the number of columns with a negative shift.  The current
+ * iterate is evaluated, not moved.  Errors: OFKS_ESTATE (no orbitals), OFKS_EINVAL (the file
+ * exists with other sizes, or cannot be written), OFKS_ENOMEM, OFKS_ECUDA, OFKS_ETIMEOUT. */
+int ofks_record_pair(ofks_ctx *ctx, const char *path, int32_t *active);
+
+/* Train the network (ofks_precond_init or ofks_precond_set_weights first) on the pairs of the
+ * file at `pairs_path`, which must have this context's n_free and p (pairs live on one mesh):
+ * `epochs` passes over the pairs, each in an order shuffled by the SplitMix64 generator seeded
+ * with (seed, epoch), one Adam step with learning rate 1e-3 per pair on the loss of
+ * ofks_train_precond_step.  The Adam moments continue from earlier steps of this context.
+ * The mean loss of the last epoch and the steps taken are read with ofks_train_info.
+ * Errors: OFKS_ESTATE (no network), OFKS_EINVAL (missing, empty or mismatched file, epochs < 1),
+ * OFKS_ENOMEM, OFKS_ECUDA. */
+int ofks_train_precond(ofks_ctx *ctx, const char *pairs_path, int32_t epochs, uint64_t seed);
+
+/* Mean loss over the last epoch of ofks_train_precond and the Adam steps it took (any pointer
+ * may be NULL). */
+int ofks_train_info(ofks_ctx *ctx, double *last_epoch_loss, int64_t *steps);
 
 /* Checkpoint: X, X_prev, D_prev, G_prev, eta, k, kkt0 and the Hartree warm start U, restored
  * exactly on load, so a reloaded run continues from the same state (later iterates agree up to

@@ -8,6 +8,7 @@
 //   stopping test (kkt + fea)/kkt0 < tol                             (Sec. 4.1)
 //   D = T^{-1} G by Jacobi-PCG per column (Eq. precondition-T)
 //   eta by BB (Sec. 4.4); Y = X - D/eta; B Y with column norms; X <- Y/||Y||_B (Eq. PCAL-main)
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -134,6 +135,7 @@ static void free_blocks(ofks_ctx *c) {
     free_set(c->b32);
     dfree(c->d_L0); dfree(c->d_S); dfree(c->d_Lam); dfree(c->d_C); dfree(c->d_colA); dfree(c->d_pp); dfree(c->d_stage);
     dfree(c->d_cpart);
+    dfree(c->d_gmap);
     c->cpart_cap = 0;
     dfree(c->d_colC); dfree(c->d_cmap);
     c->p = c->ld = 0;
@@ -179,6 +181,7 @@ static int alloc_blocks(ofks_ctx *c, int p, bool mixed) {
     if (cudaMalloc((void **)&c->d_colA, sizeof(double) * CB_COUNT * ld) != cudaSuccess ||
         cudaMalloc((void **)&c->d_colC, sizeof(double) * CB_COUNT * ld) != cudaSuccess ||
         cudaMalloc((void **)&c->d_cmap, sizeof(int) * 2 * ld) != cudaSuccess ||
+        cudaMalloc((void **)&c->d_gmap, sizeof(int) * ld) != cudaSuccess ||
         cudaMalloc((void **)&c->d_pp, sm * 8 + sizeof(double) * ld) != cudaSuccess) {
         free_blocks(c);
         return ofks_fail(c, OFKS_ENOMEM, "p x p scratch");
@@ -334,9 +337,10 @@ static int precondition_t(ofks_ctx *c) {
     const bool learned = c->prm.precond == OFKS_PC_LEARNED;
     PcgView<T> v;
     v.w = ld; v.pc = c->p; v.cb = c->d_colA; v.D = D;
+    std::vector<double> act0(ld), sh0(ld);
     {
-        std::vector<double> act0(ld);
         cudaMemcpyAsync(act0.data(), c->d_colA + CB_ACTIVE * ld, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(sh0.data(), c->d_colA + CB_SHIFT * ld, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream);
         cudaError_t e0 = cudaStreamSynchronize(c->stream);
         if (e0 != cudaSuccess) return ofks_cuda_check(c, e0, "preconditioner");
         int nact = 0;
@@ -380,9 +384,27 @@ static int precondition_t(ofks_ctx *c) {
         if (!c->gcn.H) return ofks_fail(c, OFKS_ESTATE, "learned preconditioner: no network (ofks_precond_init)");
         int rc;
         if ((rc = gcn_forward_prepare(c))) return rc;
-        gcn_pack<T>(c, G, c->gcn.G32);
-        if ((rc = gcn_forward(c, c->d_colA + CB_SHIFT * ld, false))) return rc;
-        gcn_unpack<T>(c, c->gcn.Dn, D);
+        // the network runs on the active columns only (the others take D = G): their ids and
+        // shifts, gathered on the host from the flags read above
+        std::vector<int> gmap;
+        std::vector<double> gsh;
+        for (int j = 0; j < c->p; ++j)
+            if (act0[j] != 0.0) { gmap.push_back(j); gsh.push_back(sh0[j]); }
+        if (!c->d_shift_in && cudaMalloc((void **)&c->d_shift_in, sizeof(double) * 256) != cudaSuccess)
+            return ofks_fail(c, OFKS_ENOMEM, "shift buffer");
+        cudaError_t eg = cudaMemcpyAsync(c->d_gmap, gmap.data(), sizeof(int) * gmap.size(), cudaMemcpyHostToDevice,
+                                         c->stream);
+        if (eg == cudaSuccess)
+            eg = cudaMemcpyAsync(c->d_shift_in, gsh.data(), sizeof(double) * gsh.size(), cudaMemcpyHostToDevice,
+                                 c->stream);
+        if (eg == cudaSuccess) eg = cudaStreamSynchronize(c->stream);      // gmap, gsh leave scope
+        if (eg != cudaSuccess) return ofks_cuda_check(c, eg, "learned preconditioner columns");
+        c->gcn.cols = (int)gmap.size();
+        gcn_pack<T>(c, G, c->gcn.G32, c->d_gmap);
+        rc = gcn_forward(c, c->d_shift_in, false);
+        if (!rc) gcn_unpack<T>(c, c->gcn.Dn, D, c->d_gmap);
+        c->gcn.cols = 0;
+        if (rc) return rc;
         {
             ProfScope ps(c, PF_PCG_SPMM);
             launch_pcg_apply(c, vals_L<T>(c), vals_B<T>(c), (const T *)D, 0, b.P, b.Q, c->d_colA + CB_BETA * ld,
@@ -555,7 +577,13 @@ static int run_iterations(ofks_ctx *c, int kmax, ofks_result *res) {
         c->bx_valid = true;
         if (c->k == 0) c->kkt0 = r.kkt;
         c->history.insert(c->history.end(), {(double)c->k, now_s() - c->t_start, r.E, r.kkt, r.fea, c->eta});
-        if (c->phase == 32 && c->kkt0 > 0 && (r.kkt + r.fea) / c->kkt0 < c->prm.mixed_tol) {
+        // float32 iterations hand over at mixed_tol, or once they have stalled below 1e-4: no new
+        // best (kkt + fea)/kkt0 within the last 300 iterations (their rounding floor is above
+        // mixed_tol on this system)
+        const double rel = c->kkt0 > 0 ? (r.kkt + r.fea) / c->kkt0 : 1.0;
+        if (c->phase == 32 && (c->k == 0 || rel < c->best_rel)) { c->best_rel = rel; c->best_k = c->k; }
+        const bool stalled = c->phase == 32 && c->best_rel < 1e-4 && c->k - c->best_k >= 300;
+        if (c->phase == 32 && c->kkt0 > 0 && (rel < c->prm.mixed_tol || stalled)) {
             // float32 iterations have reached their floor: continue with the float64 sweep
             state_to64(c);
             c->phase = 64;
@@ -610,9 +638,10 @@ void ofks_default_params(ofks_params *p) {
     p->eta_fixed = 0.0; p->eta_min = 1e-4; p->eta_max = 1e8; p->hartree = 1; p->xc = 1;
     p->multipole_lmax = 2; p->poisson_tol = 1e-12; p->poisson_max_iter = 20000;
     p->poisson_pc = OFKS_HPC_SEPARABLE;
-    p->mixed_tol = 1e-5; p->poisson_tol_mixed = 1e-8;
+    p->mixed_tol = 1e-6; p->poisson_tol_mixed = 1e-8;
     p->judge_tau = 0.5; p->learned_tc = 1; p->poisson_adaptive = 0; p->poisson_csr = 0; p->gram_tc = 1;
     p->poisson_sep_tc = 1; p->spmm_f32_rows = 0; p->pcg_compact = 1; p->cuda_graphs = 1;
+    p->pcg_staged = 0;
     p->method = OFKS_METHOD_PCAL;
 }
 
@@ -1059,6 +1088,7 @@ int ofks_load_state(ofks_ctx *c, const char *path) {
     c->phase = (h.phase == 32 && c->mixed_alloc) ? 32 : 64;
     state_to32(c);
     c->have_X = true; c->k = h.k; c->have_prev = h.have_prev; c->converged = h.converged; c->kkt0 = h.kkt0;
+    c->best_rel = 1.0; c->best_k = h.k;            // the float32 stall test restarts from here
     c->eta = h.eta; c->evaluated = false;
     c->history = hist;
     c->t_start = now_s() - (hist.empty() ? 0.0 : hist[hist.size() - 5]);
@@ -1194,6 +1224,141 @@ int ofks_precond_grads(ofks_ctx *c, const double *G, const double *shifts, const
     const int64_t m = gcn_param_count(c->gcn.H);
     if (cap < m) return ofks_fail(c, OFKS_EINVAL, "precond_grads: need %lld values", (long long)m);
     return ofks_cuda_check(c, cudaMemcpy(grads, c->gcn.grad, sizeof(double) * m, cudaMemcpyDeviceToHost), "grads");
+}
+
+// ---- pairs files of the learned preconditioner
+struct PairsHeader {
+    char magic[8];
+    int64_t n;
+    int32_t p, zero;
+};
+
+int ofks_record_pair(ofks_ctx *c, const char *path, int32_t *active) {
+    if (!c || !path) return OFKS_EINVAL;
+    if (!c->have_X) return ofks_fail(c, OFKS_ESTATE, "record_pair: no orbitals");
+    const int64_t n = c->n, p = c->p;
+    std::vector<double> G, Lam, D;
+    try {
+        G.resize((size_t)(n * p));
+        D.resize((size_t)(n * p));
+        Lam.resize((size_t)(p * p));
+    } catch (const std::bad_alloc &) {
+        return ofks_fail(c, OFKS_ENOMEM, "record_pair: host buffers");
+    }
+    int rc;
+    if ((rc = ofks_evaluate(c, nullptr)) || (rc = ofks_get_field(c, OFKS_F_G, G.data(), n * p)) ||
+        (rc = ofks_get_field(c, OFKS_F_LAMBDA, Lam.data(), p * p)))
+        return rc;
+    std::vector<double> shifts((size_t)p);
+    int32_t nact = 0;
+    for (int64_t j = 0; j < p; ++j) {
+        shifts[j] = Lam[(size_t)(j * p + j)];
+        nact += shifts[j] < 0.0;
+    }
+    if ((rc = ofks_precondition(c, OFKS_PC_EXACT, G.data(), shifts.data(), D.data()))) return rc;
+    FILE *f = fopen(path, "r+b");
+    PairsHeader h{};
+    if (f) {
+        if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, "OFKSPR1", 8) != 0 || h.n != n || h.p != p) {
+            fclose(f);
+            return ofks_fail(c, OFKS_EINVAL, "record_pair: %s holds pairs of another shape", path);
+        }
+        fseek(f, 0, SEEK_END);
+    } else {
+        f = fopen(path, "wb");
+        if (!f) return ofks_fail(c, OFKS_EINVAL, "record_pair: cannot create %s", path);
+        memcpy(h.magic, "OFKSPR1", 8);
+        h.n = n;
+        h.p = (int32_t)p;
+        if (fwrite(&h, sizeof(h), 1, f) != 1) {
+            fclose(f);
+            return ofks_fail(c, OFKS_EINVAL, "record_pair: write to %s failed", path);
+        }
+    }
+    bool ok = fwrite(shifts.data(), sizeof(double), shifts.size(), f) == shifts.size() &&
+              fwrite(G.data(), sizeof(double), G.size(), f) == G.size() &&
+              fwrite(D.data(), sizeof(double), D.size(), f) == D.size();
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) return ofks_fail(c, OFKS_EINVAL, "record_pair: write to %s failed", path);
+    if (active) *active = nact;
+    return OFKS_OK;
+}
+
+// SplitMix64 (Steele, Lea and Flood 2014): the pair order of one epoch
+static uint64_t splitmix64(uint64_t &x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+int ofks_train_precond(ofks_ctx *c, const char *path, int32_t epochs, uint64_t seed) {
+    if (!c || !path || epochs < 1) return OFKS_EINVAL;
+    if (!c->gcn.H) return ofks_fail(c, OFKS_ESTATE, "train_precond: no network (ofks_precond_init)");
+    if (!c->n || !c->p) return ofks_fail(c, OFKS_ESTATE, "train_precond: no mesh/params");
+    FILE *f = fopen(path, "rb");
+    if (!f) return ofks_fail(c, OFKS_EINVAL, "train_precond: cannot open %s", path);
+    PairsHeader h{};
+    const int64_t n = c->n, p = c->p;
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, "OFKSPR1", 8) != 0 || h.n != n || h.p != p) {
+        fclose(f);
+        return ofks_fail(c, OFKS_EINVAL, "train_precond: %s is not a pairs file of this mesh and p", path);
+    }
+    const int64_t rec = (int64_t)sizeof(double) * (p + 2 * n * p);
+    fseek(f, 0, SEEK_END);
+    const int64_t size = (int64_t)ftell(f);
+    const int64_t count = (size - (int64_t)sizeof(h)) / rec;
+    if (count < 1 || (int64_t)sizeof(h) + count * rec != size) {
+        fclose(f);
+        return ofks_fail(c, OFKS_EINVAL, "train_precond: %s holds %lld bytes, not whole pairs", path, (long long)size);
+    }
+    std::vector<double> buf;
+    try {
+        buf.resize((size_t)(p + 2 * n * p));
+    } catch (const std::bad_alloc &) {
+        fclose(f);
+        return ofks_fail(c, OFKS_ENOMEM, "train_precond: host buffer");
+    }
+    cudaSetDevice(c->device);
+    std::vector<int64_t> order((size_t)count);
+    int64_t steps = 0;
+    double epoch_loss = 0.0;
+    for (int32_t ep = 0; ep < epochs; ++ep) {
+        for (int64_t i = 0; i < count; ++i) order[(size_t)i] = i;
+        uint64_t st = seed ^ (0xD1B54A32D192ED03ULL * (uint64_t)(ep + 1));
+        for (int64_t i = count - 1; i > 0; --i) {                 // Fisher-Yates
+            const int64_t j = (int64_t)(splitmix64(st) % (uint64_t)(i + 1));
+            std::swap(order[(size_t)i], order[(size_t)j]);
+        }
+        double sum = 0.0;
+        for (int64_t i = 0; i < count; ++i) {
+            if (fseek(f, (long)((int64_t)sizeof(h) + order[(size_t)i] * rec), SEEK_SET) != 0 ||
+                fread(buf.data(), sizeof(double), buf.size(), f) != buf.size()) {
+                fclose(f);
+                return ofks_fail(c, OFKS_EINVAL, "train_precond: read of %s failed", path);
+            }
+            double loss = 0.0;
+            int rc = ofks_train_precond_step(c, buf.data() + p, buf.data(), buf.data() + p + n * p, 1e-3, &loss);
+            if (rc) {
+                fclose(f);
+                return rc;
+            }
+            sum += loss;
+            ++steps;
+        }
+        epoch_loss = sum / (double)count;
+    }
+    fclose(f);
+    c->train_loss = epoch_loss;
+    c->train_steps += steps;
+    return OFKS_OK;
+}
+
+int ofks_train_info(ofks_ctx *c, double *last_epoch_loss, int64_t *steps) {
+    if (!c) return OFKS_EINVAL;
+    if (last_epoch_loss) *last_epoch_loss = c->train_loss;
+    if (steps) *steps = c->train_steps;
+    return OFKS_OK;
 }
 
 int ofks_profile(ofks_ctx *c, int32_t on) {

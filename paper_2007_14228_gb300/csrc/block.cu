@@ -859,7 +859,11 @@ void launch_gram2(ofks_ctx *c, const T *X, const T *A, const T *B, double *XA, d
 }
 
 template <> bool pcg_zc<double>(const ofks_ctx *, int) { return false; }
-template <> bool pcg_zc<float>(const ofks_ctx *c, int w) { return c->n_tslices > 0 && w >= 4 && w % 4 == 0; }
+template <> bool pcg_zc<float>(const ofks_ctx *c, int w) {
+    // the staged apply (pcg_staged, widths 8..32) works on row-major blocks of the main SELL
+    if (c->prm.pcg_staged && w % 4 == 0 && w >= 8 && w <= 32) return false;
+    return c->n_tslices > 0 && w >= 4 && w % 4 == 0;
+}
 
 // grid of 256-thread blocks whose total thread count is a multiple of ld
 struct ElemGrid { unsigned blocks; int64_t stride; };

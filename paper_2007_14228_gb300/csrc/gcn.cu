@@ -266,20 +266,23 @@ __global__ void k_adam(int64_t m, const double *__restrict__ g, float *w, float 
     w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-// n x ld block (element type E) <-> n x p compact float
+// n x ld block (element type E) <-> n x p compact float; column k of the compact block is column
+// cmap[k] of the block (k without a map)
 template <class E>
-__global__ void k_pack(int64_t n, int p, int ld, const E *__restrict__ src, float *dst) {
+__global__ void k_pack(int64_t n, int p, int ld, const int *__restrict__ cmap, const E *__restrict__ src, float *dst) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n * p) return;
     const int64_t i = e / p;
-    dst[e] = (float)src[i * ld + (e - i * p)];
+    const int k = (int)(e - i * p);
+    dst[e] = (float)src[i * ld + (cmap ? cmap[k] : k)];
 }
 template <class E>
-__global__ void k_unpack(int64_t n, int p, int ld, const float *__restrict__ src, E *dst) {
+__global__ void k_unpack(int64_t n, int p, int ld, const int *__restrict__ cmap, const float *__restrict__ src, E *dst) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n * p) return;
     const int64_t i = e / p;
-    dst[i * ld + (e - i * p)] = (E)src[e];
+    const int k = (int)(e - i * p);
+    dst[i * ld + (cmap ? cmap[k] : k)] = (E)src[e];
 }
 
 inline unsigned gr(int64_t m) { return (unsigned)std::max<int64_t>(1, (m + 255) / 256); }
@@ -406,7 +409,7 @@ int gcn_forward_prepare(ofks_ctx *c) { return gcn_buffers(c); }
 
 // aggregation over nodes of an (n p) x F activation: out = A in (or A^T in)
 static void aggregate(ofks_ctx *c, const float *val, const float *in, float *out, int F) {
-    launch_sell_spmm_ld<float>(c, val, in, out, c->p * F);
+    launch_sell_spmm_ld<float>(c, val, in, out, gcn_cols(c) * F);
 }
 
 #define DISPATCH_DENSE(FI_, FO_, ...)                                                              \
@@ -426,7 +429,7 @@ int gcn_forward(ofks_ctx *c, const double *shift, bool keep) {
     GcnState &g = c->gcn;
     int rc = gcn_buffers(c);
     if (rc) return rc;
-    const int64_t n = c->n, p = c->p, rows = n * p;
+    const int64_t n = c->n, p = gcn_cols(c), rows = n * p;
     const int H = g.H;
     int64_t off[3][3];
     offsets(H, off);
@@ -461,7 +464,7 @@ int gcn_forward(ofks_ctx *c, const double *shift, bool keep) {
 // loss of g.Dn against g.Ds and the parameter gradients in g.grad (float64)
 int gcn_backward(ofks_ctx *c, double *loss) {
     GcnState &g = c->gcn;
-    const int64_t n = c->n, p = c->p, rows = n * p;
+    const int64_t n = c->n, p = gcn_cols(c), rows = n * p;
     const int H = g.H;
     int64_t off[3][3];
     offsets(H, off);
@@ -525,16 +528,18 @@ int gcn_adam(ofks_ctx *c, double lr) {
 }
 
 template <class E>
-void gcn_pack(ofks_ctx *c, const E *src, float *dst) {
-    k_pack<E><<<gr(c->n * (int64_t)c->p), 256, 0, c->stream>>>(c->n, c->p, c->ld, src, dst);
+void gcn_pack(ofks_ctx *c, const E *src, float *dst, const int *cmap) {
+    const int cols = gcn_cols(c);
+    k_pack<E><<<gr(c->n * (int64_t)cols), 256, 0, c->stream>>>(c->n, cols, c->ld, cmap, src, dst);
     c->kernels += 1;
 }
 template <class E>
-void gcn_unpack(ofks_ctx *c, const float *src, E *dst) {
-    k_unpack<E><<<gr(c->n * (int64_t)c->p), 256, 0, c->stream>>>(c->n, c->p, c->ld, src, dst);
+void gcn_unpack(ofks_ctx *c, const float *src, E *dst, const int *cmap) {
+    const int cols = gcn_cols(c);
+    k_unpack<E><<<gr(c->n * (int64_t)cols), 256, 0, c->stream>>>(c->n, cols, c->ld, cmap, src, dst);
     c->kernels += 1;
 }
-template void gcn_pack<double>(ofks_ctx *, const double *, float *);
-template void gcn_pack<float>(ofks_ctx *, const float *, float *);
-template void gcn_unpack<double>(ofks_ctx *, const float *, double *);
-template void gcn_unpack<float>(ofks_ctx *, const float *, float *);
+template void gcn_pack<double>(ofks_ctx *, const double *, float *, const int *);
+template void gcn_pack<float>(ofks_ctx *, const float *, float *, const int *);
+template void gcn_unpack<double>(ofks_ctx *, const float *, double *, const int *);
+template void gcn_unpack<float>(ofks_ctx *, const float *, float *, const int *);

@@ -75,6 +75,7 @@ struct GcnState {
     float *dA = nullptr, *dB2 = nullptr, *G32 = nullptr;
     double *stats = nullptr, *lacc = nullptr;
     int64_t t = 0;                               // Adam step count
+    int cols = 0;                                // columns of the next application (0: all p)
 };
 
 // Lattice-stencil form of the full-node stiffness (stencil.cu).  Node type t = parity triple
@@ -193,6 +194,7 @@ struct ofks_ctx {
     double *d_stage = nullptr;                   // n x p dense staging of host block copies (ld > p)
     double *d_colC = nullptr;                    // per-column PCG arrays of the compact form (stride w)
     int *d_cmap = nullptr;                       // compact form: active column ids [ld], compact index [ld]
+    int *d_gmap = nullptr;                       // learned preconditioner: active column ids [ld]
     double *d_sc = nullptr;                      // SC_COUNT scalars
     double *d_rec = nullptr;                     // iteration record (device)
     int *d_flag = nullptr;                       // error / status flags
@@ -203,6 +205,10 @@ struct ofks_ctx {
     double *d_cpart = nullptr;
     int64_t cpart_cap = 0;
     int64_t pq_units = 0, rz_units = 0;          // partial units of the last PCG apply / vector update
+    double best_rel = 1.0;                       // float32 phase: best (kkt + fea)/kkt0 so far ...
+    int best_k = 0;                              // ... and the iteration that reached it
+    double train_loss = 0.0;                     // mean loss of the last epoch of ofks_train_precond
+    int64_t train_steps = 0;                     // Adam steps taken by ofks_train_precond
     double *nuclei_stage = nullptr;              // device address of the no-allocation nuclei staging array
 
     // ---- iteration state (host mirror)
@@ -370,5 +376,11 @@ int gcn_backward(ofks_ctx *c, double *loss);
 int gcn_adam(ofks_ctx *c, double lr);
 void launch_dense_tc(ofks_ctx *c, int64_t rows, const float *H, const float *AH, const float *W, const float *U,
                      const float *b, float *out);
-template <class E> void gcn_pack(ofks_ctx *c, const E *src, float *dst);
-template <class E> void gcn_unpack(ofks_ctx *c, const float *src, E *dst);
+// the network's block: column k is column cmap[k] of the n x ld block (cmap NULL: k), for the
+// gcn.cols columns the next application works on (0: all p)
+template <class E> void gcn_pack(ofks_ctx *c, const E *src, float *dst, const int *cmap = nullptr);
+template <class E> void gcn_unpack(ofks_ctx *c, const float *src, E *dst, const int *cmap = nullptr);
+inline int gcn_cols(const ofks_ctx *c);
+
+// columns the learned preconditioner's network works on (its activations are sized for p)
+inline int gcn_cols(const ofks_ctx *c) { return c->gcn.cols > 0 ? c->gcn.cols : c->p; }

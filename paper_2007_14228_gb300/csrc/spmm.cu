@@ -282,6 +282,214 @@ __global__ void __launch_bounds__(256) k_pcg_apply_zc(int64_t nwarps, int nchunk
 
 inline int chunk_width(int ld) { return (ld % 4 == 0) ? 4 : (ld % 2 == 0 ? 2 : 1); }
 
+// ---- float32 SpMM with the neighbour rows staged through shared memory (ld = 4 NC <= 64)
+//
+// One warp per SELL slice (lane = row).  For each entry index j the warp loads the 32 neighbour
+// rows X[c_l, 0:ld] cooperatively: flat item i = (row k, 16-byte chunk q) with consecutive lanes
+// on consecutive chunks of one row, so one load instruction covers about three whole rows (~6
+// cache lines) instead of 32 rows' pieces; the rows go to the warp's shared tile (row stride
+// XS_STRIDE(NC) floats: an odd multiple of 4 modulo 32 words, so the 16-byte reads of 8 lanes at
+// a time hit distinct banks) and each lane then multiplies its own row.  Column ids and values are
+// read once per slice.  The result rows leave through the same tile as whole-row coalesced
+// stores.  MODE 1 also forms the column sums X[r,c] Y[r,c] of the slice (per warp, in lane
+// order) into part[c * n_slices + slice].
+constexpr int WS_WARPS = 4;                       // warps per block
+
+__host__ __device__ constexpr int ws_stride(int nc) { return (nc % 2 == 1) ? 4 * nc : 4 * nc + 4; }
+
+template <int NC, int MODE>
+__global__ void __launch_bounds__(WS_WARPS * 32) k_spmm_ws(int64_t n_slices, int p, const int *__restrict__ slice_ptr,
+                                                          const int *__restrict__ slice_w, const int *__restrict__ cols,
+                                                          const int *__restrict__ perm, const float *__restrict__ val,
+                                                          const float *__restrict__ X, float *__restrict__ Y,
+                                                          double *part) {
+    constexpr int LD = 4 * NC, STR = ws_stride(NC);
+    __shared__ __align__(16) float tile[WS_WARPS][32 * STR];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t s = blockIdx.x * (int64_t)WS_WARPS + warp;
+    if (s >= n_slices) return;                      // whole warp leaves together
+    float *T = tile[warp];
+    const int base = slice_ptr[s], width = slice_w[s];
+    const int r = perm[s * SELL_C + lane];
+    float acc[LD];
+#pragma unroll
+    for (int k = 0; k < LD; ++k) acc[k] = 0.f;
+    for (int j = 0; j < width; ++j) {
+        const int e = base + j * SELL_C + lane;
+        const int cl = __ldg(cols + e);
+        const float vl = __ldg(val + e);
+        // stage the 32 neighbour rows (NC chunks each)
+#pragma unroll
+        for (int it = 0; it < NC; ++it) {
+            const int i = it * 32 + lane, k = i / NC, q = i - k * NC;
+            const int ck = __shfl_sync(0xffffffffu, cl, k);
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(X + (int64_t)ck * LD) + q);
+            *reinterpret_cast<float4 *>(T + k * STR + 4 * q) = v;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            const float4 x = *reinterpret_cast<const float4 *>(T + lane * STR + 4 * q);
+            acc[4 * q] = fmaf(vl, x.x, acc[4 * q]);
+            acc[4 * q + 1] = fmaf(vl, x.y, acc[4 * q + 1]);
+            acc[4 * q + 2] = fmaf(vl, x.z, acc[4 * q + 2]);
+            acc[4 * q + 3] = fmaf(vl, x.w, acc[4 * q + 3]);
+        }
+        __syncwarp();
+    }
+    // the slice's rows out through the tile as whole-row stores
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+        *reinterpret_cast<float4 *>(T + lane * STR + 4 * q) =
+            make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    __syncwarp();
+#pragma unroll
+    for (int it = 0; it < NC; ++it) {
+        const int i = it * 32 + lane, k = i / NC, q = i - k * NC;
+        const int rk = __shfl_sync(0xffffffffu, r, k);
+        if (rk >= 0)
+            *reinterpret_cast<float4 *>(Y + (int64_t)rk * LD + 4 * q) = *reinterpret_cast<const float4 *>(T + k * STR + 4 * q);
+    }
+    if constexpr (MODE == 1) {
+        // column sums X[r, c] Y[r, c] over the slice's rows: the own rows of X through the tile
+        __syncwarp();
+#pragma unroll
+        for (int it = 0; it < NC; ++it) {
+            const int i = it * 32 + lane, k = i / NC, q = i - k * NC;
+            const int rk = __shfl_sync(0xffffffffu, r, k);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (rk >= 0) v = __ldg(reinterpret_cast<const float4 *>(X + (int64_t)rk * LD) + q);
+            *reinterpret_cast<float4 *>(T + k * STR + 4 * q) = v;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            const float4 x = *reinterpret_cast<const float4 *>(T + lane * STR + 4 * q);
+            const float c4[4] = {x.x * acc[4 * q], x.y * acc[4 * q + 1], x.z * acc[4 * q + 2], x.w * acc[4 * q + 3]};
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const float t = warp_sum_t(c4[w]);
+                if (lane == 0) part[(int64_t)(4 * q + w) * n_slices + s] = (double)t;
+            }
+        }
+    }
+}
+
+// The float32 PCG operator apply of k_pcg_apply with the same staging, on row-major blocks of
+// width w = 4 NC <= 32: for each entry index the 32 neighbour rows of Z go through the warp's
+// tile, each lane accumulates L Z and B Z for its row; then the lane's own rows of Z, P and Q are
+// staged (coalesced) and P <- Z + beta P, Q <- (L/2 - shift B) Z + beta Q are formed and written
+// back through the tiles, with the column sums P.Q of the slice into part[c * n_slices + slice].
+template <int NC>
+__global__ void __launch_bounds__(WS_WARPS * 32) k_pcg_apply_ws(int64_t n_slices, int pc, const int *__restrict__ slice_ptr,
+                                                               const int *__restrict__ slice_w, const int *__restrict__ cols,
+                                                               const int *__restrict__ perm, const float *__restrict__ valL,
+                                                               const float *__restrict__ valB, const float *__restrict__ Z,
+                                                               float *P, float *Q, const double *__restrict__ beta_col,
+                                                               const double *__restrict__ shift, double *part, int first) {
+    constexpr int LD = 4 * NC, STR = ws_stride(NC);
+    __shared__ __align__(16) float tile[WS_WARPS][3][32 * STR];
+    __shared__ float ssh[LD], sbt[LD];
+    for (int k = threadIdx.x; k < LD; k += blockDim.x) {
+        ssh[k] = (float)shift[k];
+        sbt[k] = first ? 0.f : (float)beta_col[k];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t s = blockIdx.x * (int64_t)WS_WARPS + warp;
+    if (s >= n_slices) return;                      // whole warp leaves together
+    float *T0 = tile[warp][0], *T1 = tile[warp][1], *T2 = tile[warp][2];
+    const int base = slice_ptr[s], width = slice_w[s];
+    const int r = perm[s * SELL_C + lane];
+    float aL[LD], aB[LD];
+#pragma unroll
+    for (int k = 0; k < LD; ++k) { aL[k] = 0.f; aB[k] = 0.f; }
+    for (int j = 0; j < width; ++j) {
+        const int e = base + j * SELL_C + lane;
+        const int cl = __ldg(cols + e);
+        const float vl = __ldg(valL + e), vb = __ldg(valB + e);
+#pragma unroll
+        for (int it = 0; it < NC; ++it) {
+            const int i = it * 32 + lane, k = i / NC, q = i - k * NC;
+            const int ck = __shfl_sync(0xffffffffu, cl, k);
+            *reinterpret_cast<float4 *>(T0 + k * STR + 4 * q) = __ldg(reinterpret_cast<const float4 *>(Z + (int64_t)ck * LD) + q);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            const float4 x = *reinterpret_cast<const float4 *>(T0 + lane * STR + 4 * q);
+            const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                aL[4 * q + w] = fmaf(vl, xs[w], aL[4 * q + w]);
+                aB[4 * q + w] = fmaf(vb, xs[w], aB[4 * q + w]);
+            }
+        }
+        __syncwarp();
+    }
+    // own rows of Z, P, Q (zero for the padding rows of the last slice)
+#pragma unroll
+    for (int it = 0; it < NC; ++it) {
+        const int i = it * 32 + lane, k = i / NC, q = i - k * NC;
+        const int rk = __shfl_sync(0xffffffffu, r, k);
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4 *>(T0 + k * STR + 4 * q) = rk >= 0 ? __ldg(reinterpret_cast<const float4 *>(Z + (int64_t)rk * LD) + q) : z;
+        *reinterpret_cast<float4 *>(T1 + k * STR + 4 * q) = (rk >= 0 && !first) ? *(reinterpret_cast<const float4 *>(P + (int64_t)rk * LD) + q) : z;
+        *reinterpret_cast<float4 *>(T2 + k * STR + 4 * q) = (rk >= 0 && !first) ? *(reinterpret_cast<const float4 *>(Q + (int64_t)rk * LD) + q) : z;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+        const float4 z4 = *reinterpret_cast<const float4 *>(T0 + lane * STR + 4 * q);
+        const float4 p4 = *reinterpret_cast<const float4 *>(T1 + lane * STR + 4 * q);
+        const float4 q4 = *reinterpret_cast<const float4 *>(T2 + lane * STR + 4 * q);
+        const float zs[4] = {z4.x, z4.y, z4.z, z4.w}, ps[4] = {p4.x, p4.y, p4.z, p4.w}, qs[4] = {q4.x, q4.y, q4.z, q4.w};
+        float pn[4], qn[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int col = 4 * q + w;
+            const float tz = 0.5f * aL[col] - ssh[col] * aB[col];
+            pn[w] = fmaf(sbt[col], ps[w], zs[w]);
+            qn[w] = fmaf(sbt[col], qs[w], tz);
+            const float t = warp_sum_t(r >= 0 ? pn[w] * qn[w] : 0.f);
+            if (lane == 0) part[(int64_t)col * n_slices + s] = (double)t;
+        }
+        *reinterpret_cast<float4 *>(T1 + lane * STR + 4 * q) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+        *reinterpret_cast<float4 *>(T2 + lane * STR + 4 * q) = make_float4(qn[0], qn[1], qn[2], qn[3]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int it = 0; it < NC; ++it) {
+        const int i = it * 32 + lane, k = i / NC, q = i - k * NC;
+        const int rk = __shfl_sync(0xffffffffu, r, k);
+        if (rk >= 0) {
+            *(reinterpret_cast<float4 *>(P + (int64_t)rk * LD) + q) = *reinterpret_cast<const float4 *>(T1 + k * STR + 4 * q);
+            *(reinterpret_cast<float4 *>(Q + (int64_t)rk * LD) + q) = *reinterpret_cast<const float4 *>(T2 + k * STR + 4 * q);
+        }
+    }
+}
+
+// the staged PCG apply applies at widths 8..32 (multiples of 4) of float32 blocks on the main SELL
+inline bool pcg_ws_fits(int w) { return w % 4 == 0 && w >= 8 && w <= 32; }
+
+template <int MODE>
+bool launch_spmm_ws(ofks_ctx *c, int ld, const float *val, const float *X, float *Y, double *colsum) {
+    if (ld % 4 || ld < 8 || ld > 64) return false;
+    const unsigned grid = (unsigned)((c->n_slices + WS_WARPS - 1) / WS_WARPS);
+#define WS_(nc) k_spmm_ws<nc, MODE><<<grid, WS_WARPS * 32, 0, c->stream>>>(c->n_slices, c->p, c->d_slice_ptr, \
+        c->d_slice_w, c->d_cols, c->d_perm, val, X, Y, c->d_cpart)
+    switch (ld / 4) {
+        case 2: WS_(2); break; case 3: WS_(3); break; case 4: WS_(4); break; case 5: WS_(5); break;
+        case 6: WS_(6); break; case 7: WS_(7); break; case 8: WS_(8); break; case 9: WS_(9); break;
+        case 10: WS_(10); break; case 11: WS_(11); break; case 12: WS_(12); break; case 13: WS_(13); break;
+        case 14: WS_(14); break; case 15: WS_(15); break; default: WS_(16); break;
+    }
+#undef WS_
+    c->kernels += 1;
+    if (MODE == 1) launch_col_fin(c, c->p, c->p, c->n_slices, c->d_cpart, colsum);
+    return true;
+}
+
 // ---- half-warp-per-row forms for float32 blocks (the mixed form)
 //
 // With float32 blocks the lane-per-row kernels above are limited by L1 wavefronts, not by
@@ -434,8 +642,10 @@ bool launch_rows_f32(ofks_ctx *c, int ld, int pc, const float *valA, const float
 
 template <class T>
 void launch_sell_spmm(ofks_ctx *c, const T *val, const T *X, T *Y) {
-    if constexpr (sizeof(T) == 4)
+    if constexpr (sizeof(T) == 4) {
         if (launch_rows_f32<0>(c, c->ld, c->p, val, nullptr, X, Y, nullptr, nullptr, nullptr, nullptr, 0)) return;
+        if (c->prm.spmm_f32_rows == 0 && launch_spmm_ws<0>(c, c->ld, val, X, Y, nullptr)) return;
+    }
     const int W = chunk_width(c->ld), nch = c->ld / W;
     const int64_t nw = (int64_t)c->n_slices * nch;
     const unsigned grid = (unsigned)((nw * 32 + 255) / 256);
@@ -448,8 +658,10 @@ void launch_sell_spmm(ofks_ctx *c, const T *val, const T *X, T *Y) {
 
 template <class T>
 void launch_sell_spmm_colnorm(ofks_ctx *c, const T *val, const T *X, T *Y, double *colsum) {
-    if constexpr (sizeof(T) == 4)
+    if constexpr (sizeof(T) == 4) {
         if (launch_rows_f32<1>(c, c->ld, c->p, val, nullptr, X, Y, nullptr, nullptr, nullptr, colsum, 0)) return;
+        if (c->prm.spmm_f32_rows == 0 && launch_spmm_ws<1>(c, c->ld, val, X, Y, colsum)) return;
+    }
     const int W = chunk_width(c->ld), nch = c->ld / W;
     const int spw = spw_for((int64_t)c->n_slices * nch);
     const int64_t nsg = ((int64_t)c->n_slices + spw - 1) / spw, nw = nsg * nch;
@@ -466,6 +678,20 @@ template <class T>
 void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, int zc, T *P, T *Q, const double *beta_col,
                       const double *shift, double *pq, int first, int w, int pc) {
     if constexpr (sizeof(T) == 4) {
+        if (!zc && c->prm.pcg_staged && pcg_ws_fits(w)) {
+            const unsigned grid = (unsigned)((c->n_slices + WS_WARPS - 1) / WS_WARPS);
+#define PW_(nc) k_pcg_apply_ws<nc><<<grid, WS_WARPS * 32, 0, c->stream>>>(c->n_slices, pc, c->d_slice_ptr, c->d_slice_w, \
+        c->d_cols, c->d_perm, (const float *)valL, (const float *)valB, (const float *)Zin, (float *)P, (float *)Q, beta_col, \
+        shift, c->d_cpart, first)
+            switch (w / 4) {
+                case 2: PW_(2); break; case 3: PW_(3); break; case 4: PW_(4); break; case 5: PW_(5); break;
+                case 6: PW_(6); break; case 7: PW_(7); break; default: PW_(8); break;
+            }
+#undef PW_
+            c->kernels += 1;
+            c->pq_units = c->n_slices;
+            return;
+        }
         if (zc) {
             const int nch = w / 4;
             const int spw = spw_for((int64_t)c->n_tslices * nch);

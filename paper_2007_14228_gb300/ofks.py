@@ -29,7 +29,8 @@ SYMBOLS = ("ofks_default_params", "ofks_create", "ofks_destroy", "ofks_last_erro
            "ofks_get_orbitals", "ofks_step", "ofks_solve", "ofks_evaluate", "ofks_rayleigh_ritz",
            "ofks_get_field", "ofks_apply", "ofks_get_sizes", "ofks_poisson_info", "ofks_fma_peak", "ofks_get_history", "ofks_save_state",
            "ofks_load_state", "ofks_profile", "ofks_profile_get", "ofks_precond_init", "ofks_precond_get_weights",
-           "ofks_precond_set_weights", "ofks_precondition", "ofks_train_precond_step", "ofks_precond_grads")
+           "ofks_precond_set_weights", "ofks_precondition", "ofks_train_precond_step", "ofks_precond_grads",
+           "ofks_record_pair", "ofks_train_precond", "ofks_train_info")
 
 
 class OfksError(RuntimeError):
@@ -48,7 +49,8 @@ class Params(C.Structure):
                 ("poisson_tol_mixed", C.c_double), ("judge_tau", C.c_double), ("learned_tc", C.c_int32),
                 ("poisson_adaptive", C.c_int32), ("poisson_csr", C.c_int32),
                 ("gram_tc", C.c_int32), ("spmm_f32_rows", C.c_int32), ("poisson_sep_tc", C.c_int32),
-                ("pcg_compact", C.c_int32), ("cuda_graphs", C.c_int32), ("method", C.c_int32)]
+                ("pcg_compact", C.c_int32), ("cuda_graphs", C.c_int32), ("pcg_staged", C.c_int32),
+                ("method", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -113,6 +115,9 @@ def load(path: str = LIB_PATH):
         "ofks_precondition": (C.c_int, [vp, i32, _dp, _dp, _dp]),
         "ofks_train_precond_step": (C.c_int, [vp, _dp, _dp, _dp, dbl, C.POINTER(dbl)]),
         "ofks_precond_grads": (C.c_int, [vp, _dp, _dp, _dp, _dp, i64, C.POINTER(dbl)]),
+        "ofks_record_pair": (C.c_int, [vp, C.c_char_p, C.POINTER(i32)]),
+        "ofks_train_precond": (C.c_int, [vp, C.c_char_p, i32, C.c_uint64]),
+        "ofks_train_info": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -336,6 +341,21 @@ class Context:
                                               np.ascontiguousarray(shifts, np.float64),
                                               np.ascontiguousarray(Dstar, np.float64), g, g.size, C.byref(loss)))
         return loss.value, g
+
+    def record_pair(self, path: str) -> int:
+        """ofks_record_pair: append (G, shifts, T^{-1} G) at the current iterate to a pairs file;
+        returns the number of columns with a negative shift."""
+        act = C.c_int32()
+        self._chk(self.lib.ofks_record_pair(self.h, path.encode(), C.byref(act)))
+        return act.value
+
+    def train_precond(self, path: str, epochs: int = 1, seed: int = 0):
+        """ofks_train_precond: Adam over the pairs file in seeded shuffled order; returns
+        (mean loss of the last epoch, Adam steps taken so far)."""
+        self._chk(self.lib.ofks_train_precond(self.h, path.encode(), int(epochs), int(seed)))
+        loss, steps = C.c_double(), C.c_int64()
+        self._chk(self.lib.ofks_train_info(self.h, C.byref(loss), C.byref(steps)))
+        return loss.value, steps.value
 
     def profile(self, on: bool):
         self._chk(self.lib.ofks_profile(self.h, int(on)))

@@ -2,10 +2,11 @@
 
 For seeded random nuclei sets (4-12 nuclei, Z in {1, 6, 7, 8}, positions uniform in a 6 bohr
 box, meshes of 16^3-24^3 cells) PCAL runs with the paper's PCG preconditioner; at sampled
-iterations the gradient block G and the multipliers' diagonal give the pairs
-(G_c, T_c^{-1} G_c) with the target solved to a tight residual by the same PCG.  Each pair
-batch (all columns of one iterate) takes a few Adam steps of the library's own forward and
-backward kernels, then is discarded.
+iterations the library appends the pair (G, T^{-1} G) with the target solved to a tight residual
+(ofks_record_pair) to a pairs file of that system, and then trains the network on the file
+(ofks_train_precond: shuffled epochs of Adam steps of the library's own forward and backward
+kernels).  This module only drives the systems and carries the weights from one system's
+context to the next; the loop over pairs and steps runs in the library.
 
     python -m paper_2007_14228_gb300.train_precond --systems 100 --out weights.npy
 """
@@ -61,20 +62,44 @@ def pairs_from_system(seed: int, cells: int, samples, rng, device=0, width=64, w
 
 def train(systems=100, first_seed=1, steps_per_pair=3, lr=1e-3, width=64,
           samples=(5, 10, 20, 30, 50, 80, 120, 160, 200, 250, 300),
-          device=0, log=None, weights=None):
+          device=0, log=None, weights=None, workdir=None):
+    """Pairs of each system go to a file of their own; the library trains on it for
+    steps_per_pair epochs (one Adam step per pair and epoch, learning rate 1e-3)."""
+    import tempfile
+    if lr != 1e-3:
+        raise ValueError("ofks_train_precond uses the learning rate 1e-3")
     rng = np.random.default_rng(first_seed)
     w = weights
     history = []
     n_pairs = 0
     t0 = time.time()
-    for k, seed in enumerate(range(first_seed, first_seed + systems)):
+    tmp = workdir or tempfile.mkdtemp(prefix="ofks_pairs_")
+    for seed in range(first_seed, first_seed + systems):
         cells = int(rng.integers(16, 25))
-        for ctx, G, shifts, Dstar in pairs_from_system(seed, cells, samples, rng, device, width, w):
-            for _ in range(steps_per_pair):
-                loss = ctx.train_precond_step(G, shifts, Dstar, lr)
+        s, m = system_and_mesh(seed, cells)
+        ctx = ofks.context_for(s, m, device=device, beta=10.0)
+        if w is not None:
+            ctx.precond_set_weights(w)
+        else:
+            ctx.precond_init(width, seed)
+        ctx.init_orbitals(I.initial_block(m.n_free, s.p, seed))
+        path = os.path.join(tmp, f"pairs_{seed}.bin")
+        k, recorded = 0, 0
+        for target in samples:
+            if target > k:
+                ctx.step(target - k)
+                k = target
+            ctx.evaluate()
+            if not np.any(np.diag(ctx.get_field("Lambda")) < 0):
+                continue                       # every T = I: nothing to learn at this iterate
+            n_pairs += ctx.record_pair(path)
+            recorded += 1
+        if recorded:
+            loss, _ = ctx.train_precond(path, steps_per_pair, seed)
             history.append(loss)
-            n_pairs += int(np.sum(shifts < 0))
-            w = ctx.precond_get_weights()
+            os.remove(path)
+        w = ctx.precond_get_weights()
+        ctx.close()
         if log:
             log({"system": seed, "cells": cells, "pairs": n_pairs, "loss": history[-1] if history else None,
                  "seconds": round(time.time() - t0, 1)})

@@ -143,3 +143,63 @@ def test_trained_network_beats_the_jacobi_step_on_held_out_systems(ofks):
             jacobi.append(ctx.precond_grads(G, shifts, Dstar)[0])
     assert trained and len(trained) == len(jacobi)
     assert np.mean(trained) < 0.85 * np.mean(jacobi), (np.mean(trained), np.mean(jacobi))
+
+
+def read_pairs(path):
+    """Parse a pairs file of ofks_record_pair: header (magic, n, p), then (shifts, G, D*) records."""
+    raw = open(path, "rb").read()
+    assert raw[:8] == b"OFKSPR1\x00"
+    n = int(np.frombuffer(raw[8:16], np.int64)[0])
+    p = int(np.frombuffer(raw[16:20], np.int32)[0])
+    body = np.frombuffer(raw[24:], np.float64)
+    rec = p + 2 * n * p
+    assert body.size % rec == 0
+    out = []
+    for k in range(body.size // rec):
+        r = body[k * rec:(k + 1) * rec]
+        out.append((r[:p], r[p:p + n * p].reshape(n, p), r[p + n * p:].reshape(n, p)))
+    return n, p, out
+
+
+def test_pairs_recorded_and_trained_in_the_library(ofks, tmp_path):
+    # ofks_record_pair appends (shifts, G, T^{-1} G) at the current iterate; the targets solve the
+    # shifted systems of Eq. precondition-T with the oracle's own L and B; ofks_train_precond then
+    # runs shuffled Adam epochs over the file and lowers the loss
+    s = I.lih().with_cells((8, 8, 8))
+    m = I.make_mesh(s)
+    ctx = ofks.context_for(s, m, beta=10.0)
+    ctx.precond_init(16, 3)
+    ctx.init_orbitals(I.initial_block(m.n_free, s.p, 0))
+    path = str(tmp_path / "pairs.bin")
+    recorded = 0
+    for _ in range(60):
+        ctx.step(10)
+        ctx.evaluate()
+        if np.any(np.diag(ctx.get_field("Lambda")) < 0):
+            assert ctx.record_pair(path) >= 1
+            recorded += 1
+            if recorded == 3:
+                break
+    assert recorded == 3
+    n, p, pairs = read_pairs(path)
+    assert (n, p) == (m.n_free, s.p) and len(pairs) == 3
+    pr = pcal.Problem(m.xyz, m.tet10, m.dirichlet, s.Z, s.R, pcal.Params(p=s.p, occ=s.occ))
+    for shifts, G, D in pairs:
+        for c in range(p):
+            if shifts[c] < 0:
+                T = 0.5 * pr.Lf - shifts[c] * pr.Bf
+                assert np.linalg.norm(T @ D[:, c] - G[:, c]) <= 1e-9 * np.linalg.norm(G[:, c])
+            else:
+                np.testing.assert_array_equal(D[:, c], G[:, c])
+    loss1, st1 = ctx.train_precond(path, 1, 7)
+    loss2, st2 = ctx.train_precond(path, 40, 7)
+    assert st1 == 3 and st2 == 3 + 120
+    assert loss2 < loss1
+    # a pairs file belongs to one mesh and p: another shape is refused
+    other = ofks.context_for(s.with_p(3, occ=1.0), m, beta=10.0)
+    other.precond_init(16, 3)
+    with pytest.raises(ofks.OfksError) as e:
+        other.train_precond(path, 1, 0)
+    assert e.value.code == ofks.EINVAL
+    other.close()
+    ctx.close()

@@ -151,6 +151,30 @@ def test_compact_pcg_matches_full_width_and_the_oracle(ofks, precision):
         assert np.array_equal(D[1][:, inactive].astype(np.float32), G[:, inactive].astype(np.float32))
 
 
+def test_staged_pcg_apply_matches_chunk_major_and_the_oracle(ofks):
+    # the float32 PCG at compact width 24: the staged operator apply on row-major blocks
+    # (pcg_staged = 1) and the chunk-major blocks on the type-grouped SELL (0) solve the same
+    # systems; both agree with the oracle's float64 PCG to float32 accuracy
+    s = I.chain(cells=(26, 14, 8))
+    m = I.make_mesh(s)
+    rng = np.random.default_rng(19)
+    G = rng.standard_normal((m.n_free, s.p))
+    shifts = -rng.uniform(0.05, 2.0, s.p)
+    inactive = rng.choice(s.p, 19, replace=False)
+    shifts[inactive] = rng.uniform(0.05, 1.0, inactive.size)
+    D = {}
+    for staged in (1, 0):
+        ctx = ofks.context_for(s, m, beta=10.0, precision="mixed", pcg_staged=staged)
+        D[staged] = ctx.precondition("pcg", G, shifts)
+        ctx.close()
+    pr = pcal.Problem(m.xyz, m.tet10, m.dirichlet, s.Z, s.R, pcal.Params(p=s.p, occ=s.occ, hartree=False, xc=False))
+    Do = pr.precondition(G, shifts)
+    scale = np.max(np.abs(Do))
+    assert np.max(np.abs(D[1] - Do)) < 1e-4 * scale, np.max(np.abs(D[1] - Do)) / scale
+    assert np.max(np.abs(D[1] - D[0])) < 1e-5 * scale, np.max(np.abs(D[1] - D[0])) / scale
+    assert np.array_equal(D[1][:, inactive].astype(np.float32), G[:, inactive].astype(np.float32))
+
+
 @pytest.mark.parametrize("case", ["chain_p41", "h2o_p5"])
 def test_tensor_core_grams_match(ofks, case):
     # Lambda0 = X^T H X and S = X^T B X (bf16 hi/lo split, three products) and the gradient

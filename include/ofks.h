@@ -122,7 +122,10 @@ typedef struct {
                                OFKS_HPC_SEPARABLE (falls back to Jacobi where the mesh has none) */
     double  mixed_tol;      /* OFKS_MIXED: hand over to float64 once (kkt+fea)/kkt0 < mixed_tol (or on a stall) */
     double  poisson_tol_mixed; /* Hartree CG tolerance during the float32 iterations */
-    double  judge_tau;      /* OFKS_PC_LEARNED: accept a column if |G - T D| <= judge_tau |G| and G.D > 0 */
+    double  judge_tau;      /* OFKS_PC_LEARNED: accept the network's column D if G.D > 0 and
+                               |G - T D|_{M^-1} <= judge_tau |G|_{M^-1} (M the Jacobi diagonal of T,
+                               |r|_{M^-1}^2 = r^T M^-1 r, the PCG's residual measure); a rejected column
+                               runs the PCG, from D where that ratio is below 1, else from zero */
     int32_t learned_tc;     /* 1: width-64 hidden layer on the tensor cores (bf16 operands) at inference */
     int32_t poisson_adaptive; /* 1: Hartree CG tolerance max(poisson_tol, min(1e-4, 0.01 (kkt+fea)/kkt0))
                                  from the previous iterate (inexact potentials early, exact at the end) */
@@ -150,9 +153,21 @@ typedef struct {
                                through shared memory; 0 (default, measured 3 % faster per PCG on the
                                chain with the vector updates included) the chunk-major blocks on the
                                type-grouped SELL (lattice meshes) */
+    int32_t sweep_pc32;     /* OFKS_MIXED: 1 (default) the float64 sweep solves the preconditioner's systems
+                               with the float32 PCG (the gradient rounded to float32, D widened back);
+                               the gradient, Grams, energies and tests stay float64, so the fixed point
+                               is unchanged.  0: float64 PCG in the sweep */
     int32_t method;         /* OFKS_METHOD_PCAL (default), OFKS_METHOD_PLAM or OFKS_METHOD_MOPTQR; the
                                stopping test (Sec. 4.1), the preconditioner (Eq. precondition-T, its
                                shifts from the method's multipliers) and eta are common to all three */
+    int32_t learned_loss;   /* training loss of the learned preconditioner, per column c of negative shift:
+                               1 (default) the energy-norm error (D - D*)^T T_c (D - D*) / G_c^T D*_c
+                               (the norm the PCG reduces), averaged over those columns; 0 the relative
+                               squared error |D - D*|^2 / |D*|^2 averaged over all columns */
+    int32_t learned_retry;  /* OFKS_PC_LEARNED: after a call in which the judge took none of the network's
+                               directions and none was a better PCG start than zero, the network sits out
+                               the next 1, 2, 4, ... calls (at most learned_retry; reset when it helps
+                               again); 0: the network runs on every call */
 } ofks_params;
 
 typedef struct {
@@ -174,14 +189,16 @@ typedef struct {
     int64_t active_total;   /* ... summed over the directions computed so far */
     int64_t pcg_cols_total; /* block width of each PCG operator apply, summed over the applies so far
                                (the active count rounded up to 4 in the compact form, ld otherwise) */
+    int64_t learned_calls;  /* OFKS_PC_LEARNED: network applications so far (calls outside a pause) */
+    int64_t learned_warm;   /* ... columns the judge rejected whose PCG started from the network's D */
 } ofks_result;
 
 /* Fill *prm with the defaults: beta 10, occ 2, tol 1e-8, max_iter 1000, FP64, PCG with 8
  * iterations, BB2, eta in [1e-4, 1e8], Hartree and LDA on, multipole_lmax 2,
  * poisson_tol 1e-12, poisson_max_iter 20000, poisson_pc OFKS_HPC_SEPARABLE, mixed_tol 1e-6, poisson_tol_mixed
  * 1e-8, judge_tau 0.5, learned_tc 1, poisson_adaptive 0, poisson_csr 0, gram_tc 1, spmm_f32_rows 0,
- * poisson_sep_tc 1, pcg_compact 1, cuda_graphs 1, pcg_staged 0, method OFKS_METHOD_PCAL.  p is
- * set to 1. */
+ * poisson_sep_tc 1, pcg_compact 1, cuda_graphs 1, pcg_staged 0, sweep_pc32 1, method OFKS_METHOD_PCAL,
+ * learned_loss 1, learned_retry 64.  p is set to 1. */
 void ofks_default_params(ofks_params *prm);
 
 /* Create a context on CUDA device `device`.  *out receives the context (NULL on failure).

@@ -18,7 +18,16 @@ Aggregation A: mean over the closed neighbourhood, (A h)_i = sum_{j in N(i)} h_j
 Layers (widths 4 -> H -> H -> 1):  Z_l = H_l W_l + (A H_l) U_l + b_l,  H_{l+1} = relu(Z_l) for the
 two hidden layers, identity for the last.
 Output: D_i = s_c (f0_i + H_3,i)   (the network corrects the scaled Jacobi step).
-Loss over a batch of columns: mean_c ||D_c - D*_c||^2 / ||D*_c||^2.
+Loss over a batch of columns, one of two:
+    "l2":     mean over all columns of ||D_c - D*_c||^2 / ||D*_c||^2
+    "energy": mean over the columns with a negative shift of
+              (D_c - D*_c)^T T_c (D_c - D*_c) / (G_c^T D*_c)
+the error in the energy norm of T_c (the norm the conjugate-gradient method of Eq. precondition-T
+reduces, so a network direction is worth as much as a PCG iterate of the same energy error; the
+plain l2 error leaves high-frequency errors almost free, which the residual T D - G amplifies),
+relative to the energy norm of the exact solution, ||D*_c||_T^2 = G_c^T T_c^{-1} G_c = G_c^T D*_c.
+Columns with a non-negative shift have T = I in Eq. precondition-T and are not preconditioned by
+the network in the solver, so the energy loss leaves them out.
 """
 from __future__ import annotations
 
@@ -105,6 +114,26 @@ def loss_and_dy(D: np.ndarray, Dstar: np.ndarray, s: np.ndarray):
     loss = float(np.mean(np.sum(r * r, axis=0) / den))
     dD = 2.0 * r / den[None, :] / p
     return loss, dD * s[None, :]
+
+
+def energy_loss_and_dy(D: np.ndarray, Dstar: np.ndarray, G: np.ndarray, s: np.ndarray, L: sp.spmatrix,
+                       B: sp.spmatrix, shifts: np.ndarray):
+    """Energy-norm error averaged over the columns with a negative shift, and its gradient with
+    respect to y: with E_c = D_c - D*_c and T_c = L/2 - shift_c B,
+    loss = mean_c E_c^T T_c E_c / (G_c^T D*_c),  dloss/dD_c = 2 T_c E_c / (G_c^T D*_c) / n_active."""
+    act = shifts < 0
+    na = int(act.sum())
+    dD = np.zeros_like(D)
+    if na == 0:
+        return 0.0, dD
+    loss = 0.0
+    for c in np.nonzero(act)[0]:
+        E = D[:, c] - Dstar[:, c]
+        TE = 0.5 * (L @ E) - shifts[c] * (B @ E)
+        den = float(G[:, c] @ Dstar[:, c])
+        loss += float(E @ TE) / den
+        dD[:, c] = 2.0 * TE / den / na
+    return loss / na, dD * s[None, :]
 
 
 def backward(params, cache, dy: np.ndarray, A: sp.csr_matrix):

@@ -332,60 +332,69 @@ static int precondition_t(ofks_ctx *c) {
         return ofks_cuda_check(c, cudaMemcpyAsync(D, G, sizeof(T) * c->n * ld, cudaMemcpyDeviceToDevice, c->stream),
                                "direction copy");
     }
-    // with no column of negative multiplier every T is I (Eq. precondition-T): D = G, and no
-    // linear system is solved
     const bool learned = c->prm.precond == OFKS_PC_LEARNED;
+    // the network runs unless it sits out a pause after calls in which it helped no column
+    const bool net = learned && c->gcn_skip == 0;
+    if (learned && !net) c->gcn_skip--;
     PcgView<T> v;
     v.w = ld; v.pc = c->p; v.cb = c->d_colA; v.D = D;
     std::vector<double> act0(ld), sh0(ld);
-    {
-        cudaMemcpyAsync(act0.data(), c->d_colA + CB_ACTIVE * ld, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream);
-        cudaMemcpyAsync(sh0.data(), c->d_colA + CB_SHIFT * ld, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream);
-        cudaError_t e0 = cudaStreamSynchronize(c->stream);
-        if (e0 != cudaSuccess) return ofks_cuda_check(c, e0, "preconditioner");
-        int nact = 0;
-        for (int j = 0; j < c->p; ++j) nact += act0[j] != 0.0;
-        c->last_active = nact;
-        c->active_total += nact;
-        if (nact == 0) {
-            ProfScope ps(c, PF_PCG_UPDATE);
-            launch_direction_select(c, b);
-            return ofks_cuda_check(c, cudaGetLastError(), "preconditioner");
-        }
-        // the PCG on the active columns only, gathered into a block of width w (the columns are
-        // independent systems, so the others' work would only be discarded)
+    cudaMemcpyAsync(act0.data(), c->d_colA + CB_ACTIVE * ld, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(sh0.data(), c->d_colA + CB_SHIFT * ld, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e0 = cudaStreamSynchronize(c->stream);
+    if (e0 != cudaSuccess) return ofks_cuda_check(c, e0, "preconditioner");
+    int nact = 0;
+    for (int j = 0; j < c->p; ++j) nact += act0[j] != 0.0;
+    c->last_active = nact;
+    c->active_total += nact;
+    if (nact == 0) {                 // every T is I (Eq. precondition-T): D = G, no system is solved
+        ProfScope ps(c, PF_PCG_UPDATE);
+        launch_direction_select(c, b);
+        return ofks_cuda_check(c, cudaGetLastError(), "preconditioner");
+    }
+    // the PCG runs on a compact block of the columns that need it, of width w: the active columns
+    // (the columns are independent systems, so the others' work would only be discarded), or in
+    // the learned mode those the judge did not accept
+    auto compact_view = [&](const std::vector<int> &cols, const std::vector<int> &cpos) -> int {
+        const int m = (int)cols.size();
+        const int w = m <= 2 ? m : (m + 3) / 4 * 4;
+        std::vector<int> h(2 * (size_t)ld, -1);                // cmap | cpos
+        for (int k = 0; k < m; ++k) h[k] = cols[k];
+        for (int j = 0; j < ld; ++j) h[ld + j] = cpos[j];
+        cudaError_t e = cudaMemcpyAsync(c->d_cmap, h.data(), sizeof(int) * 2 * ld, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // h leaves scope
+        if (e != cudaSuccess) return ofks_cuda_check(c, e, "preconditioner");
+        launch_pcg_compact_cols(c, w, m, c->d_cmap, c->d_colC);
+        v.w = w; v.pc = m; v.cb = c->d_colC;
+        v.cmap = c->d_cmap; v.cpos = c->d_cmap + ld; v.D = b.Dc;
+        return OFKS_OK;
+    };
+    bool run_pcg = true, warm = false;
+    if (!net) {
         const int w = nact <= 2 ? nact : (nact + 3) / 4 * 4;
-        const bool compact = !learned && c->prm.pcg_compact && w < ld;
-        const bool slots = pcg_zc<T>(c, compact ? w : ld);   // float32 blocks chunk-major
-        if (compact || slots) {
-            std::vector<int> h(2 * (size_t)ld, -1);            // cmap | cpos
-            if (compact) {
-                for (int j = 0, k = 0; j < c->p; ++j)
-                    if (act0[j] != 0.0) { h[k] = j; h[ld + j] = k; ++k; }
-            } else {                                          // all columns; inactive ones take G
-                for (int j = 0; j < ld; ++j) h[j] = j;
-                for (int j = 0; j < c->p; ++j) h[ld + j] = act0[j] != 0.0 ? j : -1;
-            }
+        if (c->prm.pcg_compact && w < ld) {
+            std::vector<int> cols, cpos(ld, -1);
+            for (int j = 0; j < c->p; ++j)
+                if (act0[j] != 0.0) { cpos[j] = (int)cols.size(); cols.push_back(j); }
+            if (int rc = compact_view(cols, cpos)) return rc;
+        } else if (pcg_zc<T>(c, ld)) {                        // float32 blocks chunk-major
+            std::vector<int> h(2 * (size_t)ld, -1);            // all columns; inactive ones take G
+            for (int j = 0; j < ld; ++j) h[j] = j;
+            for (int j = 0; j < c->p; ++j) h[ld + j] = act0[j] != 0.0 ? j : -1;
             cudaError_t e = cudaMemcpyAsync(c->d_cmap, h.data(), sizeof(int) * 2 * ld, cudaMemcpyHostToDevice,
                                             c->stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // h leaves scope
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
             if (e != cudaSuccess) return ofks_cuda_check(c, e, "preconditioner");
-            if (compact) {
-                launch_pcg_compact_cols(c, w, nact, c->d_cmap, c->d_colC);
-                v.w = w; v.pc = nact; v.cb = c->d_colC;
-            }
             v.cmap = c->d_cmap; v.cpos = c->d_cmap + ld; v.D = b.Dc;
         }
-    }
-    bool run_pcg = true, warm = false;
-    if (c->prm.precond == OFKS_PC_LEARNED) {
-        // D = network(G); each active column is judged by its relative residual |G - T D| / |G| and
-        // the sign of G.D; rejected columns continue with PCG started from the network's D
+    } else {
+        // D = network(G) on the active columns; each is judged by its residual against the PCG's
+        // own measure, |G - T D|_{M^-1} / |G|_{M^-1} (M the Jacobi diagonal of T), and by the sign
+        // of G.D: accepted columns keep the network's D; the others run the PCG, started from the
+        // network's D where that residual is below 1 (a better start than zero), else from zero
         if (!c->gcn.H) return ofks_fail(c, OFKS_ESTATE, "learned preconditioner: no network (ofks_precond_init)");
         int rc;
         if ((rc = gcn_forward_prepare(c))) return rc;
-        // the network runs on the active columns only (the others take D = G): their ids and
-        // shifts, gathered on the host from the flags read above
         std::vector<int> gmap;
         std::vector<double> gsh;
         for (int j = 0; j < c->p; ++j)
@@ -405,36 +414,56 @@ static int precondition_t(ofks_ctx *c) {
         if (!rc) gcn_unpack<T>(c, c->gcn.Dn, D, c->d_gmap);
         c->gcn.cols = 0;
         if (rc) return rc;
+        c->learned_calls++;
         {
             ProfScope ps(c, PF_PCG_SPMM);
             launch_pcg_apply(c, vals_L<T>(c), vals_B<T>(c), (const T *)D, 0, b.P, b.Q, c->d_colA + CB_BETA * ld,
                              c->d_colA + CB_SHIFT * ld, c->d_colA + CB_PQ * ld, 1, ld, c->p);
         }
         launch_judge(c, b);
-        std::vector<double> h(4 * (size_t)ld);
-        cudaMemcpyAsync(h.data(), c->d_colA + CB_ACTIVE * ld, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream);
-        cudaMemcpyAsync(h.data() + ld, c->d_colA + CB_RZ * ld, sizeof(double) * 3 * ld, cudaMemcpyDeviceToHost, c->stream);
+        std::vector<double> h(3 * (size_t)ld);
+        cudaMemcpyAsync(h.data(), c->d_colA + CB_RZ * ld, sizeof(double) * 3 * ld, cudaMemcpyDeviceToHost, c->stream);
         cudaError_t e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return ofks_cuda_check(c, e, "learned preconditioner judge");
-        std::vector<double> acc(ld, 1.0);
-        int rejected = 0;
+        std::vector<int> cols, cpos(ld, -1);
+        std::vector<double> warmv(ld, 0.0);
+        int accepted = 0, nwarm = 0;
         for (int j = 0; j < c->p; ++j) {
-            if (h[j] == 0.0) continue;                      // T = I column: D = G below
-            const double rr = h[ld + j], gg = h[2 * ld + j], gd = h[3 * ld + j];
-            const bool ok = gd > 0.0 && std::sqrt(rr) <= c->prm.judge_tau * std::sqrt(gg);
-            acc[j] = ok ? 1.0 : 0.0;
-            rejected += !ok;
+            if (act0[j] == 0.0) continue;                  // T = I column: D = G
+            const double rr = h[j], gg = h[ld + j], gd = h[2 * ld + j];
+            const double ratio = gg > 0.0 ? std::sqrt(rr / gg) : 1e300;
+            const bool ok = gd > 0.0 && ratio <= c->prm.judge_tau;
             c->judge_total++;
-            c->judge_accept += ok;
+            if (ok) {
+                cpos[j] = -2;
+                ++accepted;
+                continue;
+            }
+            cpos[j] = (int)cols.size();
+            cols.push_back(j);
+            if (ratio < 1.0) { warmv[j] = 1.0; ++nwarm; }
         }
-        cudaMemcpyAsync(c->d_colA + CB_ACC * ld, acc.data(), sizeof(double) * ld, cudaMemcpyHostToDevice, c->stream);
-        run_pcg = rejected > 0;
-        warm = true;
+        c->judge_accept += accepted;
+        c->learned_warm += nwarm;
+        if (accepted == 0 && nwarm == 0) {
+            if (c->prm.learned_retry > 0) {
+                c->gcn_backoff = std::min(c->prm.learned_retry, std::max(1, 2 * c->gcn_backoff));
+                c->gcn_skip = c->gcn_backoff;
+            }
+        } else {
+            c->gcn_backoff = 0;
+        }
+        run_pcg = !cols.empty();
+        if (run_pcg) {
+            cudaMemcpyAsync(c->d_colA + CB_WARM * ld, warmv.data(), sizeof(double) * ld, cudaMemcpyHostToDevice,
+                            c->stream);
+            if ((rc = compact_view(cols, cpos))) return rc;   // synchronizes: warmv may leave scope
+            warm = nwarm > 0;
+        }
     }
     if (run_pcg) {
         ProfScope ps(c, PF_PCG_UPDATE);
-        if (warm) launch_pcg_init_warm(c, b, v);
-        else launch_pcg_init(c, b, v);
+        launch_pcg_init(c, b, v, warm);
         cudaMemsetAsync(v.cb + CB_PQ * v.w, 0, sizeof(double) * v.w, c->stream);
     }
     const bool exact = c->prm.precond == OFKS_PC_EXACT;
@@ -500,12 +529,35 @@ static int precondition_t(ofks_ctx *c) {
     return ofks_cuda_check(c, cudaGetLastError(), "preconditioner");
 }
 
+// The direction D = T^{-1} G of Eq. (precondition-T).  In the float64 sweep of the mixed form
+// (sweep_pc32) the linear systems are solved by the float32 PCG on the float64 gradient rounded
+// to float32, and D is widened back: the preconditioner only shapes the path (any approximate
+// T^{-1} leaves the fixed point G = 0 and the float64 stopping test unchanged), and the float64
+// PCG is the largest cost of a float64 iteration.
+template <class T>
+static int direction_t(ofks_ctx *c) {
+    if constexpr (sizeof(T) == 8) {
+        if (c->prm.precision == OFKS_MIXED && c->mixed_alloc && c->prm.sweep_pc32 &&
+            c->prm.precond != OFKS_PC_NONE) {
+            const int64_t cnt = c->n * (int64_t)c->ld;
+            launch_convert(c, (const double *)c->b64.G[c->cur], c->b32.G[c->cur], cnt);
+            c->phase = 32;
+            const int rc = precondition_t<float>(c);
+            c->phase = 64;
+            if (rc) return rc;
+            launch_convert(c, (const float *)c->b32.D[c->cur], c->b64.D[c->cur], cnt);
+            return ofks_cuda_check(c, cudaGetLastError(), "float32 preconditioner of the float64 sweep");
+        }
+    }
+    return precondition_t<T>(c);
+}
+
 template <class T>
 static int update_step_t(ofks_ctx *c) {
     Blocks<T> &b = blocks<T>(c);
     const int prv = c->cur ^ 1, ld = c->ld;
     int rc;
-    if ((rc = precondition_t<T>(c))) return rc;
+    if ((rc = direction_t<T>(c))) return rc;
     launch_bb_dots(c, b, c->prm.eta_rule == OFKS_ETA_BB2_RAW);
     launch_eta(c);
     const int method = c->prm.method;
@@ -623,6 +675,8 @@ static int run_iterations(ofks_ctx *c, int kmax, ofks_result *res) {
         res->active_last = c->last_active;
         res->active_total = c->active_total;
         res->pcg_cols_total = c->pcg_cols_total;
+        res->learned_calls = c->learned_calls;
+        res->learned_warm = c->learned_warm;
     }
     return rc;
 }
@@ -642,7 +696,9 @@ void ofks_default_params(ofks_params *p) {
     p->judge_tau = 0.5; p->learned_tc = 1; p->poisson_adaptive = 0; p->poisson_csr = 0; p->gram_tc = 1;
     p->poisson_sep_tc = 1; p->spmm_f32_rows = 0; p->pcg_compact = 1; p->cuda_graphs = 1;
     p->pcg_staged = 0;
+    p->sweep_pc32 = 1;
     p->method = OFKS_METHOD_PCAL;
+    p->learned_loss = 1; p->learned_retry = 64;
 }
 
 int ofks_create(ofks_ctx **out, int device) {
@@ -743,7 +799,8 @@ int ofks_set_params(ofks_ctx *c, const ofks_params *prm) {
         !(prm->poisson_tol_mixed > 0) || !(prm->eta_min > 0) || !(prm->eta_max >= prm->eta_min) ||
         prm->multipole_lmax < -1 || prm->multipole_lmax > 2 || !(prm->poisson_tol > 0) ||
         prm->poisson_max_iter < 1 || prm->poisson_pc < 0 || prm->poisson_pc > OFKS_HPC_SEPARABLE || (prm->eta_rule == OFKS_ETA_FIXED && !(prm->eta_fixed > 0)) ||
-        prm->method < OFKS_METHOD_PCAL || prm->method > OFKS_METHOD_MOPTQR)
+        prm->method < OFKS_METHOD_PCAL || prm->method > OFKS_METHOD_MOPTQR ||
+        prm->learned_loss < 0 || prm->learned_loss > 1 || prm->learned_retry < 0)
         return ofks_fail(c, OFKS_EINVAL, "set_params: a parameter is out of range");
     cudaSetDevice(c->device);
     const bool mixed = prm->precision == OFKS_MIXED;
@@ -1167,6 +1224,7 @@ int ofks_precondition(ofks_ctx *c, int32_t mode, const double *G, const double *
     }
     cudaMemcpyAsync(c->d_colA + CB_SHIFT * ld, col.data(), sizeof(double) * 2 * ld, cudaMemcpyHostToDevice, c->stream);
     cudaMemsetAsync(c->d_colA + CB_ACC * ld, 0, sizeof(double) * ld, c->stream);
+    cudaMemsetAsync(c->d_colA + CB_WARM * ld, 0, sizeof(double) * ld, c->stream);
     int rc = upload_block(c, G, c->b64.G[c->cur]);
     if (rc) return rc;
     const int saved = c->prm.precond, phase = c->phase;
@@ -1202,7 +1260,7 @@ static int train_common(ofks_ctx *c, const double *G, const double *shifts, cons
     gcn_pack<double>(c, c->b64.Z, c->gcn.G32);
     gcn_pack<double>(c, c->b64.R, c->gcn.Ds);
     if ((rc = gcn_forward(c, c->d_shift_in, true))) return rc;
-    return gcn_backward(c, loss);
+    return gcn_backward(c, c->d_shift_in, loss);
 }
 
 int ofks_train_precond_step(ofks_ctx *c, const double *G, const double *shifts, const double *Dstar, double lr,

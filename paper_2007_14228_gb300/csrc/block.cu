@@ -456,10 +456,12 @@ __device__ __forceinline__ int64_t sidx(int64_t r, int k, int64_t ns) { return (
 
 // PCG start: W = 1/diag with diag = dL/2 - shift_c dB, D = 0, R = G, Z = G W, rz[c] = sum R Z.
 // The PCG block has width ld; with cmap its column c < p is column cmap[c] of G (row pitch ldg),
-// its other columns are zero.
+// its other columns are zero.  With Qn (natural layout, pitch ldg) the columns whose CB_WARM entry
+// is set start from the natural-layout Dn with T Dn in Qn: R = G - Qn, D = Dn.
 template <class T>
 __global__ void __launch_bounds__(256) k_pcg_init(int64_t n, int p, int ld, int64_t stride,
                                                   const T *__restrict__ G, int ldg, const int *__restrict__ cmap,
+                                                  const T *Qn, const T *Dn,
                                                   const double *__restrict__ dL,
                                                   const double *__restrict__ dB, const double *cb,
                                                   T *W, T *D, T *R, T *Z, double *part) {
@@ -467,22 +469,30 @@ __global__ void __launch_bounds__(256) k_pcg_init(int64_t n, int p, int ld, int6
     ELEM_BEGIN
         const T sh = (T)cb[CB_SHIFT * ld + j];
         const T w = T(1) / (T(0.5) * (T)dL[r] - sh * (T)dB[r]);
-        const T gv = cmap ? (j < p ? G[r * ldg + cmap[j]] : T(0)) : G[e];
+        const int64_t src = cmap ? (j < p ? r * ldg + cmap[j] : -1) : e;
+        T gv = src >= 0 ? G[src] : T(0), dv = T(0);
+        if (Qn && src >= 0 && cb[CB_WARM * ld + j] != 0.0) { gv -= Qn[src]; dv = Dn[src]; }
         const T z = gv * w;
-        W[e] = w; D[e] = T(0); R[e] = gv; Z[e] = z;
+        W[e] = w; D[e] = dv; R[e] = gv; Z[e] = z;
         acc = fma(gv, z, acc);
     ELEM_END
     col_partial((double)acc, gid < stride, ld, ld, part);      // rz
 }
 
-// learned preconditioner judge sums per column: |G - T D|^2 (T D in Q), |G|^2, G.D
+// learned preconditioner judge sums per column, in the norm of the Jacobi diagonal M of T (the
+// norm in which the PCG measures its residuals, r^T M^{-1} r): |G - T D|^2, |G|^2 (T D in Q), and
+// G.D
 template <class T>
 __global__ void __launch_bounds__(256) k_judge(int64_t n, int p, int ld, int64_t stride, const T *__restrict__ G,
-                                               const T *__restrict__ Q, const T *__restrict__ D, double *part) {
+                                               const T *__restrict__ Q, const T *__restrict__ D,
+                                               const double *__restrict__ dL, const double *__restrict__ dB,
+                                               const double *__restrict__ cb, double *part) {
     T a = T(0), b = T(0), d = T(0);
     ELEM_BEGIN
-        const T g = G[e], r = g - Q[e];
-        a = fma(r, r, a); b = fma(g, g, b); d = fma(g, D[e], d);
+        const T sh = (T)cb[CB_SHIFT * ld + j];
+        const T w = cb[CB_ACTIVE * ld + j] != 0.0 ? T(1) / (T(0.5) * (T)dL[r] - sh * (T)dB[r]) : T(1);
+        const T g = G[e], rv = g - Q[e];
+        a = fma(rv * w, rv, a); b = fma(g * w, g, b); d = fma(g, D[e], d);
     ELEM_END
     const int64_t set = (int64_t)ld * gridDim.x;            // |G - T D|^2, |G|^2, G.D
     col_partial((double)a, gid < stride, ld, ld, part);
@@ -585,8 +595,7 @@ __global__ void __launch_bounds__(256) k_pcg_init_s(int64_t n, int64_t ns, int p
                 if (col >= 0) {
                     const int64_t e = nat * ld + col;
                     g = G[e];
-                    if (Qn) g -= Qn[e];
-                    if (Dn) d = Dn[e];
+                    if (Qn && cb[CB_WARM * w + k] != 0.0) { g -= Qn[e]; d = Dn[e]; }
                 }
             }
             wv[i] = ww; rv[i] = g; zv[i] = g * ww; dv[i] = d;
@@ -642,24 +651,28 @@ __global__ void __launch_bounds__(256) k_pcg_update_s(int64_t ns, int pc, int w,
 }
 
 // D (row-major, pitch ld) from the chunk-major PCG result: column j takes compact column cpos[j]
-// of Dc, or G when inactive (cpos[j] < 0: T = I in Eq. precondition-T)
+// of Dc, G when inactive (cpos[j] = -1: T = I in Eq. precondition-T), and keeps its D when
+// cpos[j] = -2 (a learned direction the judge accepted)
 __global__ void __launch_bounds__(256) k_expand_s(int64_t n, int ld, int64_t stride, int64_t ns,
                                                   const int *__restrict__ cpos, const float *__restrict__ G,
                                                   const float *__restrict__ Dc, float *D) {
     ELEM_BEGIN
         const int k = cpos[j];
-        D[e] = k >= 0 ? Dc[sidx(r, k, ns)] : G[e];
+        if (k >= 0) D[e] = Dc[sidx(r, k, ns)];
+        else if (k == -1) D[e] = G[e];
     ELEM_END
 }
 
-// D from the compact PCG: column j takes compact column cpos[j] of Dc (width w), or G when
-// it is inactive (cpos[j] < 0: T = I in Eq. precondition-T)
+// D from the compact PCG: column j takes compact column cpos[j] of Dc (width w), G when it is
+// inactive (cpos[j] = -1: T = I in Eq. precondition-T), and keeps its D when cpos[j] = -2 (a
+// learned direction the judge accepted)
 template <class T>
 __global__ void __launch_bounds__(256) k_expand(int64_t n, int ld, int64_t stride, int w, const int *__restrict__ cpos,
                                                 const T *__restrict__ G, const T *__restrict__ Dc, T *D) {
     ELEM_BEGIN
         const int k = cpos[j];
-        D[e] = k >= 0 ? Dc[r * w + k] : G[e];
+        if (k >= 0) D[e] = Dc[r * w + k];
+        else if (k == -1) D[e] = G[e];
     ELEM_END
 }
 
@@ -918,24 +931,29 @@ void launch_grad_update(ofks_ctx *c, Blocks<T> &b) {
 }
 
 template <class T>
-void launch_pcg_init(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v) {
+void launch_pcg_init(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v, bool warm) {
     c->kernels += 1;
     const int w = v.w;
+    const T *Qn = warm ? b.Q : nullptr, *Dn = warm ? b.D[c->cur] : nullptr;
     if constexpr (sizeof(T) == 4) {
         if (pcg_zc<T>(c, w)) {
+            // a warm start reads T D from the natural-layout Q, so the chunk-major Q (the same
+            // buffer) is not cleared here; its padding rows then hold finite values of T D, which
+            // the apply never reads and whose products with the zero preconditioner weights of
+            // the padding rows add nothing
             const int64_t total = c->n_slots * (w >> 2);
             const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8);
             k_pcg_init_s<<<grid, 256, 0, c->stream>>>(
-                c->n, c->n_slots, v.pc, w, (const float *)b.G[c->cur], nullptr, nullptr, c->ld, v.cmap, c->d_dL,
-                c->d_dB, v.cb, (float *)b.W, (float *)v.D, (float *)b.R, (float *)b.Z, (float *)b.P, (float *)b.Q,
-                c->d_cpart);
+                c->n, c->n_slots, v.pc, w, (const float *)b.G[c->cur], (const float *)Qn, (const float *)Dn, c->ld,
+                v.cmap, c->d_dL, c->d_dB, v.cb, (float *)b.W, (float *)v.D, (float *)b.R, (float *)b.Z, (float *)b.P,
+                warm ? nullptr : (float *)b.Q, c->d_cpart);
             launch_col_fin(c, v.pc, w, grid, c->d_cpart, v.cb + CB_RZ * w);
             return;
         }
     }
     const ElemGrid g = elem_grid(c->n, w);
-    k_pcg_init<T><<<g.blocks, 256, 0, c->stream>>>(c->n, v.pc, w, g.stride, b.G[c->cur], c->ld, v.cmap, c->d_dL,
-                                                   c->d_dB, v.cb, b.W, v.D, b.R, b.Z, c->d_cpart);
+    k_pcg_init<T><<<g.blocks, 256, 0, c->stream>>>(c->n, v.pc, w, g.stride, b.G[c->cur], c->ld, v.cmap, Qn, Dn,
+                                                   c->d_dL, c->d_dB, v.cb, b.W, v.D, b.R, b.Z, c->d_cpart);
     launch_col_fin(c, v.pc, w, g.blocks, c->d_cpart, v.cb + CB_RZ * w);
 }
 
@@ -945,35 +963,13 @@ void launch_judge(ofks_ctx *c, Blocks<T> &b) {
     const int ld = c->ld;
     double *cb = c->d_colA;
     const ElemGrid g = elem_grid(c->n, ld);
-    k_judge<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, b.G[c->cur], b.Q, b.D[c->cur], c->d_cpart);
-    // |G - T D|^2, |G|^2 and G.D into the RZ, RZN and PQ rows
+    k_judge<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, b.G[c->cur], b.Q, b.D[c->cur], c->d_dL,
+                                                c->d_dB, cb, c->d_cpart);
+    // |G - T D|^2, |G|^2 (M^{-1} norms) and G.D into the RZ, RZN and PQ rows
     const int64_t set = (int64_t)ld * g.blocks;
     launch_col_fin(c, c->p, ld, g.blocks, c->d_cpart, cb + CB_RZ * ld);
     launch_col_fin(c, c->p, ld, g.blocks, c->d_cpart + set, cb + CB_RZN * ld);
     launch_col_fin(c, c->p, ld, g.blocks, c->d_cpart + 2 * set, cb + CB_PQ * ld);
-}
-
-template <class T>
-void launch_pcg_init_warm(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v) {
-    c->kernels += 1;
-    const int ld = c->ld;
-    double *cb = c->d_colA;
-    if constexpr (sizeof(T) == 4) {
-        if (pcg_zc<T>(c, v.w)) {                 // Q = T D and the network's D are natural row-major
-            const int64_t total = c->n_slots * (v.w >> 2);
-            const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8);
-            k_pcg_init_s<<<grid, 256, 0, c->stream>>>(
-                c->n, c->n_slots, v.pc, v.w, (const float *)b.G[c->cur], (const float *)b.Q,
-                (const float *)b.D[c->cur], ld, v.cmap, c->d_dL, c->d_dB, v.cb, (float *)b.W, (float *)v.D,
-                (float *)b.R, (float *)b.Z, (float *)b.P, nullptr, c->d_cpart);   // Qn aliases b.Q
-            launch_col_fin(c, v.pc, v.w, grid, c->d_cpart, v.cb + CB_RZ * v.w);
-            return;
-        }
-    }
-    const ElemGrid g = elem_grid(c->n, ld);
-    k_pcg_init_warm<T><<<g.blocks, 256, 0, c->stream>>>(c->n, c->p, ld, g.stride, b.G[c->cur], b.Q, c->d_dL, c->d_dB,
-                                                        cb, b.W, b.R, b.Z, c->d_cpart);
-    launch_col_fin(c, c->p, ld, g.blocks, c->d_cpart, cb + CB_RZ * ld);
 }
 
 template <class T>
@@ -1126,11 +1122,10 @@ void launch_convert(ofks_ctx *c, const S *src, T *dst, int64_t count) {
 #define INST(T)                                                                                      \
     template void launch_gram2<T>(ofks_ctx *, const T *, const T *, const T *, double *, double *); \
     template void launch_grad_update<T>(ofks_ctx *, Blocks<T> &);                                    \
-    template void launch_pcg_init<T>(ofks_ctx *, Blocks<T> &, const PcgView<T> &);                   \
+    template void launch_pcg_init<T>(ofks_ctx *, Blocks<T> &, const PcgView<T> &, bool);             \
     template void launch_pcg_update<T>(ofks_ctx *, Blocks<T> &, const PcgView<T> &, bool);           \
     template void launch_direction_expand<T>(ofks_ctx *, Blocks<T> &, const PcgView<T> &);           \
     template void launch_judge<T>(ofks_ctx *, Blocks<T> &);                                          \
-    template void launch_pcg_init_warm<T>(ofks_ctx *, Blocks<T> &, const PcgView<T> &);             \
     template void launch_direction_select<T>(ofks_ctx *, Blocks<T> &);                               \
     template void launch_bb_dots<T>(ofks_ctx *, Blocks<T> &, bool);                                  \
     template void launch_step_y<T>(ofks_ctx *, Blocks<T> &, T *);                                    \

@@ -443,19 +443,37 @@ __global__ void __launch_bounds__(128) k_potential(int64_t T, const int *__restr
 
 // H = L/2 + sum over the element entries (T, a, b) that land on each SELL position of
 // sum_q (w V_q)_T N_a(x_q) N_b(x_q) (Eq. hamiltonian), gathered in list order in the precision of
-// the H values (the same value on every run)
+// the H values (the same value on every run).  The 100 x 4 products N_a(x_q) N_b(x_q) sit in shared
+// memory in the precision of H, so an entry costs one list load, one 4-vector load of w V and four
+// multiply-adds (no float64 arithmetic in the float32 form).
 template <class E>
 __global__ void __launch_bounds__(256) k_h_gather(int64_t npos, const int *__restrict__ ptr, const int *__restrict__ list,
                                                   const E *__restrict__ ve, const E *__restrict__ valL, E *valH) {
+    __shared__ E tab[100 * 4];
+    for (int i = threadIdx.x; i < 400; i += blockDim.x) {
+        const int ab = i >> 2, q = i & 3, a = ab / 10, b = ab - 10 * a;
+        tab[i] = (E)(p2N(q, a) * p2N(q, b));
+    }
+    __syncthreads();
     const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (pos >= npos) return;
     E acc = E(0.5) * valL[pos];
-    for (int k = ptr[pos]; k < ptr[pos + 1]; ++k) {
-        const int code = list[k], t = code / 100, ab = code - 100 * t, a = ab / 10, b = ab - 10 * a;
-        const E *v = ve + (int64_t)t * 4;
+    const int k1 = ptr[pos + 1];
+    for (int k = ptr[pos]; k < k1; ++k) {
+        const int code = __ldg(list + k), t = code / 100, ab = code - 100 * t;
+        E v[4];
+        if constexpr (sizeof(E) == 4) {
+            const float4 x = __ldg(reinterpret_cast<const float4 *>(ve) + t);
+            v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+        } else {
+            const double2 x0 = __ldg(reinterpret_cast<const double2 *>(ve) + 2 * (int64_t)t);
+            const double2 x1 = __ldg(reinterpret_cast<const double2 *>(ve) + 2 * (int64_t)t + 1);
+            v[0] = x0.x; v[1] = x0.y; v[2] = x1.x; v[3] = x1.y;
+        }
+        const E *w = tab + ab * 4;
         E m = E(0);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) m += v[q] * (E)(p2N(q, a) * p2N(q, b));
+        for (int q = 0; q < 4; ++q) m += v[q] * w[q];
         acc += m;
     }
     valH[pos] = acc;

@@ -149,6 +149,36 @@ __global__ void k_output(int64_t n, int p, const float *__restrict__ F, const fl
     D[e] = scale[e % p] * (F[e * F0] + y[e]);
 }
 
+// the last layer at inference from its row products: y = H w + A (H u) + b, since A H u = (A H) u
+// (A is linear): D = s_c (f0 + a + Aq + b) with a = H w and Aq = A (H u)
+__global__ void k_output_dots(int64_t n, int p, const float *__restrict__ F, const float *__restrict__ a,
+                              const float *__restrict__ Aq, const float *__restrict__ b,
+                              const float *__restrict__ scale, float *D) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * p) return;
+    D[e] = scale[e % p] * (F[e * F0] + (a[e] + Aq[e] + bf(b[0])));
+}
+
+// row products a = H w and q = H u of a rows x FI activation (weights rounded to bfloat16)
+template <int FI>
+__global__ void __launch_bounds__(256) k_rowdots(int64_t rows, const float *__restrict__ H, const float *__restrict__ w,
+                                                 const float *__restrict__ u, float *a, float *q) {
+    __shared__ float sw[FI], su[FI];
+    for (int k = threadIdx.x; k < FI; k += blockDim.x) { sw[k] = bf(w[k]); su[k] = bf(u[k]); }
+    __syncthreads();
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    float x = 0.f, y = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < FI; ++k) {
+        const float h = H[r * FI + k];
+        x = fmaf(h, sw[k], x);
+        y = fmaf(h, su[k], y);
+    }
+    a[r] = x;
+    q[r] = y;
+}
+
 // loss pieces: num[c] = sum (D - D*)^2, den[c] = sum D*^2 (float64), as per-block column partials
 __global__ void __launch_bounds__(256) k_loss(int64_t n, int p, const float *__restrict__ D, const float *__restrict__ Ds,
                                               double *acc) {
@@ -172,6 +202,54 @@ __global__ void k_dy(int64_t n, int p, const float *__restrict__ D, const float 
     if (e >= n * p) return;
     const int c = (int)(e % p);
     dy[e] = (float)(2.0 * (double)scale[c] * ((double)D[e] - (double)Ds[e]) / acc[p + c] / p);
+}
+
+// Energy-norm loss (learned_loss = 1): with E = D - D* and TE = L E / 2 - lam_c B E for the
+// columns of negative shift lam_c, num[c] = sum E TE and den[c] = sum G D* (= ||D*||_T^2, since
+// T D* = G) as per-block column partials; TE goes to TEo.  Columns of non-negative shift (T = I,
+// never preconditioned by the network) contribute nothing.
+__global__ void __launch_bounds__(256) k_energy_terms(int64_t n, int p, const float *__restrict__ D,
+                                                      const float *__restrict__ Ds, const float *__restrict__ LE,
+                                                      const float *__restrict__ BE, const float *__restrict__ G,
+                                                      const double *__restrict__ shift, float *TEo, double *acc) {
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t S = (int64_t)gridDim.x * blockDim.x / p * p;
+    const int c = (int)(gid % p);
+    const bool act = gid < S && shift[c] < 0.0;
+    const float lam = act ? (float)shift[c] : 0.f;
+    double a = 0.0, b = 0.0;
+    for (int64_t e = gid; gid < S && e < n * p; e += S) {
+        const float te = act ? 0.5f * LE[e] - lam * BE[e] : 0.f;
+        TEo[e] = te;
+        if (act) {
+            a += (double)(D[e] - Ds[e]) * (double)te;
+            b += (double)G[e] * (double)Ds[e];
+        }
+    }
+    col_partial(a, gid < S, p, p, acc);
+    col_partial(b, gid < S, p, p, acc + (int64_t)p * gridDim.x);
+}
+
+// dL/dy = 2 s_c TE / den_c / n_act on the columns with den_c > 0 (the active ones), 0 elsewhere
+__global__ void k_dy_energy(int64_t n, int p, const float *__restrict__ TE, const float *__restrict__ scale,
+                            const double *__restrict__ acc, float *dy) {
+    __shared__ int nact;
+    if (threadIdx.x == 0) {
+        int k = 0;
+        for (int c = 0; c < p; ++c) k += acc[p + c] > 0.0;
+        nact = k;
+    }
+    __syncthreads();
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * p) return;
+    const int c = (int)(e % p);
+    const double den = acc[p + c];
+    dy[e] = den > 0.0 ? (float)(2.0 * (double)scale[c] * (double)TE[e] / den / nact) : 0.f;
+}
+
+__global__ void k_sub(int64_t m, const float *__restrict__ a, const float *__restrict__ b, float *o) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < m) o[i] = a[i] - b[i];
 }
 
 // dZ = dH * (Z > 0) in place (hidden layers)
@@ -316,7 +394,7 @@ static void offsets(int H, int64_t off[3][3]) {
 void gcn_free(ofks_ctx *c) {
     GcnState &g = c->gcn;
     for (float *q : {g.w, g.m, g.v, g.valA, g.valAT, g.F, g.H1, g.H2, g.Z1, g.Z2, g.AH, g.y, g.scale, g.diag, g.Dn,
-                     g.Ds, g.dA, g.dB2, g.G32})
+                     g.Ds, g.dA, g.dB2, g.G32, g.valL32, g.valB32})
         if (q) cudaFree(q);
     for (double *q : {g.grad, g.stats, g.lacc}) if (q) cudaFree(q);
     c->gcn = GcnState{};
@@ -447,22 +525,40 @@ int gcn_forward(ofks_ctx *c, const double *shift, bool keep) {
                                                                       g.w + off[0][2], 1, nullptr, g.H1));
     // layer 1: H1 -> H2 (tensor cores for width 64 at inference; training keeps float32 activations)
     aggregate(c, g.valA, g.H1, g.AH, H);
-    if (H == 64 && !keep && c->prm.learned_tc)
-        launch_dense_tc(c, rows, g.H1, g.AH, g.w + off[1][0], g.w + off[1][1], g.w + off[1][2], g.H2);
-    else
-        DISPATCH_DENSE(H, H, k_dense<A_, B_><<<gd, 256, 0, c->stream>>>(rows, g.H1, g.AH, g.w + off[1][0],
-                                                                         g.w + off[1][1], g.w + off[1][2], 1, nullptr, g.H2));
-    // layer 2: H2 -> y (keep A H2 in dA for the backward pass)
-    float *AH2 = keep ? g.dA : g.AH;
-    aggregate(c, g.valA, g.H2, AH2, H);
-    k_dense_out<<<gr(rows), 256, 0, c->stream>>>(rows, H, g.H2, AH2, g.w + off[2][0], g.w + off[2][1], g.w + off[2][2], g.y);
+    if (!keep) {
+        // inference: the last layer needs H2 only through the row products a = H2 w and q = H2 u
+        // (y = a + A q + b), so H2 is never aggregated (a width-p aggregation instead of 64 p); the
+        // tensor-core layer forms a and q in its epilogue without writing H2
+        float *a = g.y, *q = g.Ds, *Aq = g.Z1;
+        if (H == 64 && c->prm.learned_tc) {
+            launch_dense_tc(c, rows, g.H1, g.AH, g.w + off[1][0], g.w + off[1][1], g.w + off[1][2], nullptr,
+                            g.w + off[2][0], g.w + off[2][1], a, q);
+        } else {
+            DISPATCH_DENSE(H, H, k_dense<A_, B_><<<gd, 256, 0, c->stream>>>(rows, g.H1, g.AH, g.w + off[1][0],
+                                                                             g.w + off[1][1], g.w + off[1][2], 1, nullptr, g.H2));
+            if (H == 64) k_rowdots<64><<<gr(rows), 256, 0, c->stream>>>(rows, g.H2, g.w + off[2][0], g.w + off[2][1], a, q);
+            else if (H == 32) k_rowdots<32><<<gr(rows), 256, 0, c->stream>>>(rows, g.H2, g.w + off[2][0], g.w + off[2][1], a, q);
+            else if (H == 16) k_rowdots<16><<<gr(rows), 256, 0, c->stream>>>(rows, g.H2, g.w + off[2][0], g.w + off[2][1], a, q);
+            else k_rowdots<8><<<gr(rows), 256, 0, c->stream>>>(rows, g.H2, g.w + off[2][0], g.w + off[2][1], a, q);
+            c->kernels += 1;
+        }
+        launch_sell_spmm_ld<float>(c, g.valA, q, Aq, (int)p);
+        k_output_dots<<<gr(rows), 256, 0, c->stream>>>(n, (int)p, g.F, a, Aq, g.w + off[2][2], g.scale, g.Dn);
+        c->kernels += 8;
+        return ofks_cuda_check(c, cudaGetLastError(), "learned preconditioner forward");
+    }
+    DISPATCH_DENSE(H, H, k_dense<A_, B_><<<gd, 256, 0, c->stream>>>(rows, g.H1, g.AH, g.w + off[1][0],
+                                                                     g.w + off[1][1], g.w + off[1][2], 1, nullptr, g.H2));
+    // layer 2: H2 -> y (A H2 kept in dA for the backward pass)
+    aggregate(c, g.valA, g.H2, g.dA, H);
+    k_dense_out<<<gr(rows), 256, 0, c->stream>>>(rows, H, g.H2, g.dA, g.w + off[2][0], g.w + off[2][1], g.w + off[2][2], g.y);
     k_output<<<gr(rows), 256, 0, c->stream>>>(n, (int)p, g.F, g.y, g.scale, g.Dn);
     c->kernels += 9;
     return ofks_cuda_check(c, cudaGetLastError(), "learned preconditioner forward");
 }
 
 // loss of g.Dn against g.Ds and the parameter gradients in g.grad (float64)
-int gcn_backward(ofks_ctx *c, double *loss) {
+int gcn_backward(ofks_ctx *c, const double *shift, double *loss) {
     GcnState &g = c->gcn;
     const int64_t n = c->n, p = gcn_cols(c), rows = n * p;
     const int H = g.H;
@@ -470,12 +566,32 @@ int gcn_backward(ofks_ctx *c, double *loss) {
     offsets(H, off);
     const int64_t m = gcn_param_count(H);
     cudaMemsetAsync(g.grad, 0, sizeof(double) * m, c->stream);
-    {
+    const bool energy = c->prm.learned_loss == 1;
+    if (energy) {
+        // T (D - D*) per column with float32 copies of L and B; scratch in Z2 (rows x H, H >= 3),
+        // which the backward only fills later (dH2)
+        if (!g.valL32) {
+            if (cudaMalloc((void **)&g.valL32, sizeof(float) * c->sell_len) != cudaSuccess ||
+                cudaMalloc((void **)&g.valB32, sizeof(float) * c->sell_len) != cudaSuccess)
+                return ofks_fail(c, OFKS_ENOMEM, "learned preconditioner: float32 L and B");
+            launch_convert<double, float>(c, c->d_valL, g.valL32, c->sell_len);
+            launch_convert<double, float>(c, c->d_valB, g.valB32, c->sell_len);
+        }
+        float *E = g.Z2, *LE = g.Z2 + rows, *BE = g.Z2 + 2 * rows;
+        k_sub<<<gr(rows), 256, 0, c->stream>>>(rows, g.Dn, g.Ds, E);
+        launch_sell_spmm_ld<float>(c, g.valL32, E, LE, (int)p);
+        launch_sell_spmm_ld<float>(c, g.valB32, E, BE, (int)p);
+        const unsigned gs = gr_stride(rows);
+        k_energy_terms<<<gs, 256, 0, c->stream>>>(n, (int)p, g.Dn, g.Ds, LE, BE, g.G32, shift, E, c->d_cpart);
+        launch_col_fin(c, (int)(2 * p), (int)(2 * p), gs, c->d_cpart, g.lacc);
+        k_dy_energy<<<gr(rows), 256, 0, c->stream>>>(n, (int)p, E, g.scale, g.lacc, g.y);  // g.y <- dL/dy
+        c->kernels += 5;
+    } else {
         const unsigned gs = gr_stride(rows);
         k_loss<<<gs, 256, 0, c->stream>>>(n, (int)p, g.Dn, g.Ds, c->d_cpart);
         launch_col_fin(c, (int)(2 * p), (int)(2 * p), gs, c->d_cpart, g.lacc);
+        k_dy<<<gr(rows), 256, 0, c->stream>>>(n, (int)p, g.Dn, g.Ds, g.scale, g.lacc, g.y);   // g.y <- dL/dy
     }
-    k_dy<<<gr(rows), 256, 0, c->stream>>>(n, (int)p, g.Dn, g.Ds, g.scale, g.lacc, g.y);   // g.y <- dL/dy
     const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 31) / 32, 152LL * 4));
     // layer 2 (H -> 1): dZ = dy; grads; dH2 = dy w^T, dAH2 = dy u^T
     if (H == 64) k_wgrad<64, 1><<<gw, 256, 0, c->stream>>>(rows, g.H2, g.dA, g.y, g.grad + off[2][0], g.grad + off[2][1], g.grad + off[2][2]);
@@ -511,8 +627,10 @@ int gcn_backward(ofks_ctx *c, double *loss) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return ofks_cuda_check(c, e, "learned preconditioner backward");
     double L = 0.0;
-    for (int k = 0; k < pp; ++k) L += h[k] / h[pp + k];
-    *loss = L / pp;
+    int na = 0;
+    for (int k = 0; k < pp; ++k)
+        if (!energy || h[pp + k] > 0.0) { L += h[k] / h[pp + k]; ++na; }
+    *loss = na ? L / na : 0.0;
     return OFKS_OK;
 }
 

@@ -31,7 +31,7 @@ constexpr int64_t CPART_MIN = 6 << 20;
 
 // Rows of the per-column scalar array ctx->d_colA (each ld float64 long).
 enum { CB_SHIFT = 0, CB_ACTIVE = 1, CB_RZ = 2, CB_RZN = 3, CB_PQ = 4, CB_BETA = 5, CB_NORM = 6,
-       CB_ALPHA = 7, CB_ACC = 8, CB_COUNT = 9 };
+       CB_ALPHA = 7, CB_ACC = 8, CB_WARM = 9, CB_COUNT = 10 };
 
 // Kernel families timed by ofks_profile.
 enum {
@@ -74,6 +74,7 @@ struct GcnState {
     float *y = nullptr, *scale = nullptr, *diag = nullptr, *Dn = nullptr, *Ds = nullptr;
     float *dA = nullptr, *dB2 = nullptr, *G32 = nullptr;
     double *stats = nullptr, *lacc = nullptr;
+    float *valL32 = nullptr, *valB32 = nullptr;  // float32 L and B on the SELL pattern (energy loss)
     int64_t t = 0;                               // Adam step count
     int cols = 0;                                // columns of the next application (0: all p)
 };
@@ -235,6 +236,8 @@ struct ofks_ctx {
     std::vector<int> row_deg;                    // pattern row lengths of the free matrices
     double *d_shift_in = nullptr;                // p shifts for ofks_precondition / training calls
     int64_t judge_accept = 0, judge_total = 0;   // learned preconditioner: columns accepted / judged
+    int64_t learned_calls = 0, learned_warm = 0; // network applications; rejected columns started from them
+    int gcn_skip = 0, gcn_backoff = 0;           // calls the network still sits out; length of the last pause
     int last_active = 0;                         // columns with T != I at the last direction
     int64_t active_total = 0;
     int64_t pcg_cols_total = 0;                  // PCG block width summed over the operator applies
@@ -334,11 +337,12 @@ struct PcgView {
 // stride n_slots) on lattice meshes with w a multiple of 4; the D of such a PCG is always
 // v.D = Dc and comes back through launch_direction_expand
 template <class T> bool pcg_zc(const ofks_ctx *c, int w);
-template <class T> void launch_pcg_init(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v);
+// warm: the columns flagged in the view's CB_WARM row start from the natural-layout D (with
+// T D in Q) instead of zero
+template <class T> void launch_pcg_init(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v, bool warm = false);
 // last: the final iteration, after which only D is read
 template <class T> void launch_pcg_update(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v, bool last);
 template <class T> void launch_judge(ofks_ctx *c, Blocks<T> &b);
-template <class T> void launch_pcg_init_warm(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v);
 template <class T> void launch_direction_select(ofks_ctx *c, Blocks<T> &b);
 // D = the compact PCG result on the active columns, G on the others
 template <class T> void launch_direction_expand(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v);
@@ -372,10 +376,11 @@ int gcn_setup(ofks_ctx *c, int H, uint64_t seed, const std::vector<int> &deg);
 void gcn_free(ofks_ctx *c);
 int gcn_forward_prepare(ofks_ctx *c);
 int gcn_forward(ofks_ctx *c, const double *shift, bool keep);
-int gcn_backward(ofks_ctx *c, double *loss);
+int gcn_backward(ofks_ctx *c, const double *shift, double *loss);
 int gcn_adam(ofks_ctx *c, double lr);
 void launch_dense_tc(ofks_ctx *c, int64_t rows, const float *H, const float *AH, const float *W, const float *U,
-                     const float *b, float *out);
+                     const float *b, float *out, const float *w2 = nullptr, const float *u2 = nullptr,
+                     float *a = nullptr, float *q = nullptr);
 // the network's block: column k is column cmap[k] of the n x ld block (cmap NULL: k), for the
 // gcn.cols columns the next application works on (0: all p)
 template <class E> void gcn_pack(ofks_ctx *c, const E *src, float *dst, const int *cmap = nullptr);

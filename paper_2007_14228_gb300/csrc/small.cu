@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(256) k_small_update(int p, int ld, const doubl
         cb[CB_SHIFT * ld + j] = act ? ljj : 0.0;
         cb[CB_ACTIVE * ld + j] = act ? 1.0 : 0.0;
         cb[CB_ACC * ld + j] = 0.0;
+        cb[CB_WARM * ld + j] = 0.0;
     }
     if (threadIdx.x == 0) {
         rec[0] = occ * tr - sc[SC_EDC] + e_nuc;   // E_KS in the double-counting form
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(256) k_pcg_alpha(int ld, int pc, int64_t units
 }
 
 // per-column arrays of the compact PCG (stride w): compact column k < nact is column cmap[k]
-// (stride ld in colA) and keeps its shift; every other entry starts at zero
+// (stride ld in colA) and keeps its shift and warm-start flag; every other entry starts at zero
 __global__ void k_pcg_compact_cols(int ld, int w, int nact, const int *__restrict__ cmap, const double *__restrict__ colA,
                                    double *colC) {
     for (int i = threadIdx.x; i < CB_COUNT * w; i += blockDim.x) colC[i] = 0.0;
@@ -107,6 +108,7 @@ __global__ void k_pcg_compact_cols(int ld, int w, int nact, const int *__restric
     for (int k = threadIdx.x; k < nact; k += blockDim.x) {
         colC[CB_SHIFT * w + k] = colA[CB_SHIFT * ld + cmap[k]];
         colC[CB_ACTIVE * w + k] = 1.0;
+        colC[CB_WARM * w + k] = colA[CB_WARM * ld + cmap[k]];
     }
 }
 

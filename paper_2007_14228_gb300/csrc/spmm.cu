@@ -243,8 +243,21 @@ __global__ void __launch_bounds__(256) k_pcg_apply_zc(int64_t nwarps, int nchunk
         const int base = slice_ptr[s], width = slice_w[s];
         const int r = perm[s * SELL_C + lane];
         float aL[4] = {0.f, 0.f, 0.f, 0.f}, aB[4] = {0.f, 0.f, 0.f, 0.f};
-        int e = base + lane;
-        for (int j = 0; j < width; ++j, e += SELL_C) {
+        int e = base + lane, j = 0;
+        // two entries per pass with all their loads issued before the first multiply-add, so two
+        // gathers are in flight per lane
+        for (; j + 2 <= width; j += 2, e += 2 * SELL_C) {
+            const int ca = __ldg(cols + e), cb = __ldg(cols + e + SELL_C);
+            const float vla = __ldg(valL + e), vba = __ldg(valB + e);
+            const float vlb = __ldg(valL + e + SELL_C), vbb = __ldg(valB + e + SELL_C);
+            const float4 xa = __ldg(reinterpret_cast<const float4 *>(Zk + (int64_t)ca * 4));
+            const float4 xb = __ldg(reinterpret_cast<const float4 *>(Zk + (int64_t)cb * 4));
+            aL[0] = fmaf(vla, xa.x, aL[0]); aL[1] = fmaf(vla, xa.y, aL[1]); aL[2] = fmaf(vla, xa.z, aL[2]); aL[3] = fmaf(vla, xa.w, aL[3]);
+            aB[0] = fmaf(vba, xa.x, aB[0]); aB[1] = fmaf(vba, xa.y, aB[1]); aB[2] = fmaf(vba, xa.z, aB[2]); aB[3] = fmaf(vba, xa.w, aB[3]);
+            aL[0] = fmaf(vlb, xb.x, aL[0]); aL[1] = fmaf(vlb, xb.y, aL[1]); aL[2] = fmaf(vlb, xb.z, aL[2]); aL[3] = fmaf(vlb, xb.w, aL[3]);
+            aB[0] = fmaf(vbb, xb.x, aB[0]); aB[1] = fmaf(vbb, xb.y, aB[1]); aB[2] = fmaf(vbb, xb.z, aB[2]); aB[3] = fmaf(vbb, xb.w, aB[3]);
+        }
+        if (j < width) {
             const int c = __ldg(cols + e);
             const float vl = __ldg(valL + e), vb = __ldg(valB + e);
             const float4 x = __ldg(reinterpret_cast<const float4 *>(Zk + (int64_t)c * 4));

@@ -41,14 +41,17 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >
 // element (r, k) of a core-matrix tile with K = TK: core (r/8, k/8) of 64 elements
 __device__ __forceinline__ int core_off(int r, int k) { return ((r >> 3) * (TK / 8) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
 
-__global__ void __launch_bounds__(128, 1) k_dense_tc(int64_t rows, const float *__restrict__ H,
+// out != nullptr: out = relu(Z) (rows x 64).  out == nullptr: the next layer's two row products
+// a = relu(Z) w2 and q = relu(Z) u2 (w2, u2 of length 64) go to a and q instead.
+__global__ void __launch_bounds__(128, 4) k_dense_tc(int64_t rows, const float *__restrict__ H,
                                                      const float *__restrict__ AH, const float *__restrict__ W,
                                                      const float *__restrict__ U, const float *__restrict__ b,
-                                                     float *out, int *err) {
+                                                     float *out, const float *__restrict__ w2,
+                                                     const float *__restrict__ u2, float *a, float *q, int *err) {
     extern __shared__ __align__(128) unsigned char dsm[];
     __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(dsm);   // TM x TK, 32 KiB
     __nv_bfloat16 *sB = sA + TM * TK;                               // TN x TK, 16 KiB
-    __shared__ float sbias[TN];
+    __shared__ float sbias[TN], sw2[TN], su2[TN];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
@@ -70,7 +73,11 @@ __global__ void __launch_bounds__(128, 1) k_dense_tc(int64_t rows, const float *
         const float v = k < 64 ? W[k * TN + n] : U[(k - 64) * TN + n];
         sB[core_off(n, k)] = __float2bfloat16(v);
     }
-    if (tid < TN) sbias[tid] = __bfloat162float(__float2bfloat16(b[tid]));
+    if (tid < TN) {
+        sbias[tid] = __bfloat162float(__float2bfloat16(b[tid]));
+        sw2[tid] = out ? 0.f : __bfloat162float(__float2bfloat16(w2[tid]));
+        su2[tid] = out ? 0.f : __bfloat162float(__float2bfloat16(u2[tid]));
+    }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -79,13 +86,20 @@ __global__ void __launch_bounds__(128, 1) k_dense_tc(int64_t rows, const float *
     uint32_t phase = 0;
 
     for (int64_t r0 = (int64_t)blockIdx.x * TM; r0 < rows; r0 += (int64_t)TM * gridDim.x) {
-        // A tile: rows r0 .. r0 + 127 of [H | AH], converted to bf16
-        for (int e = tid; e < TM * TK; e += blockDim.x) {
-            const int r = e / TK, k = e - r * TK;
+        // A tile: rows r0 .. r0 + 127 of [H | AH], converted to bf16, four values per load and
+        // one 8-byte store (four consecutive K of one core-matrix row)
+        for (int e = tid; e < TM * TK / 4; e += blockDim.x) {
+            const int r = e / (TK / 4), k = 4 * (e - r * (TK / 4));
             const int64_t row = r0 + r;
-            float v = 0.f;
-            if (row < rows) v = k < 64 ? H[row * 64 + k] : AH[row * 64 + (k - 64)];
-            sA[core_off(r, k)] = __float2bfloat16(v);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (row < rows)
+                v = k < 64 ? *reinterpret_cast<const float4 *>(H + row * 64 + k)
+                           : *reinterpret_cast<const float4 *>(AH + row * 64 + (k - 64));
+            __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+            uint2 pk;
+            pk.x = *reinterpret_cast<uint32_t *>(&lo);
+            pk.y = *reinterpret_cast<uint32_t *>(&hi);
+            *reinterpret_cast<uint2 *>(sA + core_off(r, k)) = pk;
         }
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
@@ -122,6 +136,7 @@ __global__ void __launch_bounds__(128, 1) k_dense_tc(int64_t rows, const float *
         // accumulator rows 32 warp .. 32 warp + 31, 64 columns, 16 at a time
         const int64_t row = r0 + warp * 32 + lane;
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        float da = 0.f, dq = 0.f;
 #pragma unroll
         for (int cb = 0; cb < TN; cb += 16) {
             uint32_t v[16];
@@ -132,7 +147,14 @@ __global__ void __launch_bounds__(128, 1) k_dense_tc(int64_t rows, const float *
                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
                 : "r"(taddr + cb));
             asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (row < rows) {
+            if (!out) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float hv = fmaxf(__uint_as_float(v[i]) + sbias[cb + i], 0.f);
+                    da = fmaf(hv, sw2[cb + i], da);
+                    dq = fmaf(hv, su2[cb + i], dq);
+                }
+            } else if (row < rows) {
                 float4 *o = reinterpret_cast<float4 *>(out + row * TN + cb);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -145,6 +167,7 @@ __global__ void __launch_bounds__(128, 1) k_dense_tc(int64_t rows, const float *
                 }
             }
         }
+        if (!out && row < rows) { a[row] = da; q[row] = dq; }
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
     }
@@ -157,14 +180,16 @@ __global__ void __launch_bounds__(128, 1) k_dense_tc(int64_t rows, const float *
 
 }  // namespace
 
-// relu([H | AH] [W ; U] + b) for width-64 hidden layers on the tensor cores; the caller checks
-// c->d_flag for a timed-out wait
+// relu([H | AH] [W ; U] + b) for width-64 hidden layers on the tensor cores, into out, or (out
+// null) only its products with w2 and u2 into a and q; the caller checks c->d_flag for a timed-out
+// wait.  Four CTAs per SM (48 KiB of shared memory and 64 TMEM columns each), so that one CTA's
+// tile loads overlap another's MMAs and epilogue.
 void launch_dense_tc(ofks_ctx *c, int64_t rows, const float *H, const float *AH, const float *W, const float *U,
-                     const float *b, float *out) {
+                     const float *b, float *out, const float *w2, const float *u2, float *a, float *q) {
     const int64_t tiles = (rows + TM - 1) / TM;
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, 152));
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, 152 * 4));
     const int smem = (TM + TN) * TK * (int)sizeof(__nv_bfloat16);
     cudaFuncSetAttribute(k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_dense_tc<<<grid, 128, smem, c->stream>>>(rows, H, AH, W, U, b, out, c->d_flag);
+    k_dense_tc<<<grid, 128, smem, c->stream>>>(rows, H, AH, W, U, b, out, w2, u2, a, q, c->d_flag);
     c->kernels += 1;
 }

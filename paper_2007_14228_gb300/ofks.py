@@ -50,7 +50,8 @@ class Params(C.Structure):
                 ("poisson_adaptive", C.c_int32), ("poisson_csr", C.c_int32),
                 ("gram_tc", C.c_int32), ("spmm_f32_rows", C.c_int32), ("poisson_sep_tc", C.c_int32),
                 ("pcg_compact", C.c_int32), ("cuda_graphs", C.c_int32), ("pcg_staged", C.c_int32),
-                ("method", C.c_int32)]
+                ("sweep_pc32", C.c_int32), ("method", C.c_int32), ("learned_loss", C.c_int32),
+                ("learned_retry", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -59,7 +60,7 @@ class Result(C.Structure):
                 ("seconds", C.c_double), ("hartree_iters", C.c_int32), ("hartree_total", C.c_int32),
                 ("switch_iter", C.c_int32), ("judge_accept", C.c_int64), ("judge_total", C.c_int64),
                 ("active_last", C.c_int32), ("active_total", C.c_int64),
-                ("pcg_cols_total", C.c_int64)]
+                ("pcg_cols_total", C.c_int64), ("learned_calls", C.c_int64), ("learned_warm", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -130,6 +131,12 @@ def load(path: str = LIB_PATH):
 def default_params(**overrides) -> Params:
     prm = Params()
     load().ofks_default_params(C.byref(prm))
+    return updated_params(prm, **overrides)
+
+
+def updated_params(base: Params, **overrides) -> Params:
+    """A copy of `base` with the named fields replaced (enum fields also by name)."""
+    prm = Params.from_buffer_copy(base)
     for k, v in overrides.items():
         if k == "precond" and isinstance(v, str):
             v = PC[v]
@@ -158,6 +165,7 @@ class Context:
             raise OfksError(rc, "ofks_create failed (no usable CUDA device?)")
         self.p = None
         self.n = None
+        self._prm = None
 
     def close(self):
         if self.h:
@@ -201,9 +209,13 @@ class Context:
         self._chk(self.lib.ofks_set_nuclei_static(self.h, len(Z), Z, R))
 
     def set_params(self, prm: Params | None = None, **overrides):
+        """Set the parameters: `prm` with `overrides` applied, or, without `prm`, the parameters
+        last set on this context (the defaults on the first call) with `overrides` applied."""
         if prm is None:
-            prm = default_params(**overrides)
+            prm = self._prm if self._prm is not None else default_params()
+        prm = updated_params(prm, **overrides)
         self._chk(self.lib.ofks_set_params(self.h, C.byref(prm)))
+        self._prm = prm
         self.p = prm.p
 
     def init_orbitals(self, V):

@@ -43,6 +43,17 @@ def test_default_params_without_gpu(lib):
     assert prm.poisson_csr == 0 and prm.poisson_adaptive == 0 and prm.poisson_pc == 2
 
 
+def test_updated_params_keep_the_other_fields(lib):
+    # the binding's set_params applies keyword overrides on top of the parameters last set, so a
+    # later change of one field (pcg_iters) keeps p, occ and the rest
+    from paper_2007_14228_gb300 import ofks
+    a = ofks.default_params(p=41, occ=2.0, precond="exact", beta=10.0)
+    b = ofks.updated_params(a, pcg_iters=3, precision="mixed")
+    assert (b.p, b.occ, b.precond, b.beta) == (41, 2.0, ofks.PC["exact"], 10.0)
+    assert (b.pcg_iters, b.precision) == (3, ofks.PRECISION["mixed"])
+    assert a.pcg_iters != 3 and a.precision == ofks.PRECISION["fp64"]
+
+
 def test_missing_library_fails_loudly(tmp_path):
     from paper_2007_14228_gb300 import ofks
     saved = ofks._lib

@@ -69,14 +69,19 @@ def test_network_output_matches_oracle(ofks, width):
 
 
 @pytest.mark.parametrize("width", [8, 64])
-def test_network_gradients_match_oracle(ofks, width):
+@pytest.mark.parametrize("kind", ["l2", "energy"])
+def test_network_gradients_match_oracle(ofks, width, kind):
     ctx, pr, G, shifts, w, A = setup(ofks, width, seed=1)
+    ctx.set_params(learned_loss=1 if kind == "energy" else 0)
     Dstar = pr.precondition(G, shifts)
     loss, g = ctx.precond_grads(G, shifts, Dstar)
     f, s, _ = gcn.features(G, pr.Lf.diagonal(), pr.Bf.diagonal(), shifts)
     params = flat_to_params(w, width)
     D, y, cache = gcn.predict(params, f, s, A)
-    lo, dy = gcn.loss_and_dy(D, Dstar, s)
+    if kind == "energy":
+        lo, dy = gcn.energy_loss_and_dy(D, Dstar, G, s, pr.Lf, pr.Bf, shifts)
+    else:
+        lo, dy = gcn.loss_and_dy(D, Dstar, s)
     grads = gcn.backward(params, cache, dy, A)
     go = np.concatenate([np.concatenate([gr["W"].ravel(), gr["U"].ravel(), gr["b"].ravel()]) for gr in grads])
     assert abs(loss - lo) < 1e-4 * lo
@@ -84,12 +89,16 @@ def test_network_gradients_match_oracle(ofks, width):
     ctx.close()
 
 
-def test_training_steps_reduce_the_loss(ofks):
+@pytest.mark.parametrize("kind,factor", [("l2", 0.75), ("energy", 0.92)])
+def test_training_steps_reduce_the_loss(ofks, kind, factor):
+    # 100 Adam steps on one pair from the Jacobi start (the energy-norm loss falls more slowly: it
+    # weighs the smooth error the 3-hop network cannot reach; measured 0.549 -> 0.484)
     ctx, pr, G, shifts, w, A = setup(ofks, 16, seed=2)
+    ctx.set_params(learned_loss=1 if kind == "energy" else 0)
     ctx.precond_init(16, 3)                 # last layer zero: starts as the Jacobi step
     Dstar = pr.precondition(G, shifts)
     losses = [ctx.train_precond_step(G, shifts, Dstar, lr=3e-3) for _ in range(100)]
-    assert losses[-1] < 0.75 * losses[0], (losses[0], losses[-1])
+    assert losses[-1] < factor * losses[0], (losses[0], losses[-1])
     ctx.close()
 
 
@@ -202,4 +211,107 @@ def test_pairs_recorded_and_trained_in_the_library(ofks, tmp_path):
         other.train_precond(path, 1, 0)
     assert e.value.code == ofks.EINVAL
     other.close()
+    ctx.close()
+
+
+def test_trained_network_keeps_the_fixed_point(ofks):
+    # the learned form with the committed weights: the judge and the PCG fallback change the path
+    # only; the converged energy and eigenvalues are those of the PCG form (LiH, 6^3 cells)
+    s = I.lih().with_cells((6, 6, 6))
+    m = I.make_mesh(s)
+    V = I.initial_block(m.n_free, s.p, 0)
+    out = {}
+    for mode in ("pcg", "learned"):
+        ctx = ofks.context_for(s, m, beta=10.0, tol=1e-11, max_iter=6000, precond=mode)
+        if mode == "learned":
+            ctx.precond_set_weights(ofks.trained_weights())
+        ctx.init_orbitals(V)
+        r = ctx.solve()
+        assert r["converged"] == 1, mode
+        out[mode] = (r["e_total"], ctx.rayleigh_ritz(), r["judge_total"])
+        ctx.close()
+    assert abs(out["pcg"][0] - out["learned"][0]) < 1e-8
+    np.testing.assert_allclose(out["pcg"][1], out["learned"][1], atol=1e-7)
+    assert out["learned"][2] > 0                  # the network was judged on every active column
+
+
+def near_converged_lih(ofks):
+    """LiH 6^3 solved to 1e-6 with the PCG: both multipliers are negative from here on, so every
+    later direction preconditions two columns"""
+    s = I.lih().with_cells((6, 6, 6))
+    m = I.make_mesh(s)
+    ctx = ofks.context_for(s, m, beta=10.0, tol=1e-6, max_iter=3000)
+    ctx.init_orbitals(I.initial_block(m.n_free, s.p, 0))
+    assert ctx.solve()["converged"] == 1
+    assert np.all(np.diag(ctx.get_field("Lambda")) < 0)
+    return ctx
+
+
+def test_judge_accepts_takes_warm_starts_and_pauses_the_network(ofks):
+    ctx = near_converged_lih(ofks)
+    ctx.precond_init(16, 5)                  # zero last layer: the network is the Jacobi step M^-1 G
+    w_jacobi = ctx.precond_get_weights()
+    # (1) a judge that accepts every direction with G.D > 0 (M^-1 G always has it): the network runs
+    # on every call and its directions are taken
+    ctx.set_params(precond="learned", judge_tau=1e30, tol=1e-14)
+    r = ctx.step(11)
+    assert r["learned_calls"] == 11 and r["judge_total"] == 22 and r["judge_accept"] == 22
+    # (2) a network far off (a large constant output): every column is rejected and started from zero
+    # (its residual exceeds that of D = 0), so the network pauses 1, 2, 4, ... calls: it runs on calls
+    # 1, 3, 6 and 11 of the next 11
+    w_bad = w_jacobi.copy()
+    w_bad[-1] = 1e3                          # the output layer's bias
+    ctx.precond_set_weights(w_bad)
+    ctx.set_params(judge_tau=1e-30)
+    r2 = ctx.step(11)
+    assert r2["learned_calls"] - r["learned_calls"] == 4
+    assert r2["judge_accept"] == r["judge_accept"] and r2["learned_warm"] == r["learned_warm"]
+    # (3) learned_retry = 0: no pause
+    ctx.set_params(learned_retry=0)
+    r3 = ctx.step(5)
+    assert r3["learned_calls"] - r2["learned_calls"] == 5
+    assert np.isfinite(r3["e_total"])
+    ctx.close()
+
+
+def test_warm_started_pcg_matches_the_oracle_pcg_from_the_same_start(ofks):
+    # a rejected column whose network residual is below that of zero runs the PCG from the network's
+    # direction: D equals the oracle's Jacobi-PCG of Eq. precondition-T started from that direction
+    ctx = near_converged_lih(ofks)
+    ctx.precond_init(16, 5)                  # zero last layer: the network is the Jacobi step M^-1 G
+    ctx.set_params(precond="learned", judge_tau=1e-30, tol=1e-14, pcg_iters=5)
+    ctx.evaluate()
+    G = ctx.get_field("G")
+    lam = np.diag(ctx.get_field("Lambda")).copy()
+    r0 = ctx.step(1)
+    D = ctx.get_field("D")
+    s = I.lih().with_cells((6, 6, 6))
+    m = I.make_mesh(s)
+    pr = pcal.Problem(m.xyz, m.tet10, m.dirichlet, s.Z, s.R, pcal.Params(p=s.p, occ=s.occ, pcg_iters=5))
+    warm = 0
+    for c in range(2):
+        T = (0.5 * pr.Lf - lam[c] * pr.Bf).tocsr()
+        Minv = 1.0 / T.diagonal()
+        x = Minv * G[:, c]                   # the network's direction (the Jacobi step)
+        r = G[:, c] - T @ x
+        ratio = np.sqrt((r * Minv) @ r / ((G[:, c] * Minv) @ G[:, c]))
+        if ratio >= 1.0:                     # not a better start than zero: the PCG starts from zero
+            x = np.zeros_like(x)
+            r = G[:, c].copy()
+        else:
+            warm += 1
+        z = Minv * r
+        pdir = z.copy()
+        rz = r @ z
+        for _ in range(5):
+            q = T @ pdir
+            a = rz / (pdir @ q)
+            x += a * pdir
+            r -= a * q
+            z = Minv * r
+            rzn = r @ z
+            pdir = z + (rzn / rz) * pdir
+            rz = rzn
+        np.testing.assert_allclose(D[:, c], x, rtol=0, atol=1e-9 * np.max(np.abs(x)))
+    assert r0["learned_warm"] == warm and warm >= 1, (r0, warm)
     ctx.close()

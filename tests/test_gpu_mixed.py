@@ -212,6 +212,24 @@ def test_tensor_core_grams_match(ofks, case):
         assert np.max(np.abs(res["tc"][k] - ref)) < 2e-5 * scale, (k, np.max(np.abs(res["tc"][k] - ref)) / scale)
         assert np.max(np.abs(res["tc"][k] - res["cuda"][k])) < 2e-5 * scale
         assert np.allclose(res["tc"][k], res["tc"][k].T, rtol=0, atol=1e-12 * scale)
+    # and against the oracle itself at the same iterate
+    check_against_oracle(s, m, X, res["tc"], 2e-5, 1e-4)
+
+
+def check_against_oracle(s, m, X, got, tol_gram, tol_grad):
+    """Lambda0, S, G of Eq. (lambda2)'s multipliers and kkt from the oracle at X against `got`."""
+    pr = pcal.Problem(m.xyz, m.tet10, m.dirichlet, s.Z, s.R, pcal.Params(p=s.p, occ=s.occ, beta=10.0))
+    H = pr.hamiltonian(pr.potentials(pr.density(X)))
+    HX, BX = H @ X, pr.Bf @ X
+    L0, S = pcal.sym(X.T @ HX), X.T @ BX
+    G = pcal.lagrangian_gradient(HX, BX, pcal.multipliers(X, HX, BX, L0, S, 10.0), S, 10.0)
+    kkt = np.linalg.norm(HX - BX @ L0)
+    for k, ref in ((0, L0), (1, S)):
+        scale = np.max(np.abs(ref))
+        assert np.max(np.abs(got[k] - ref)) < tol_gram * scale, (k, np.max(np.abs(got[k] - ref)) / scale)
+    gs = np.max(np.abs(G))
+    assert np.max(np.abs(got[2] - G)) < tol_grad * gs, np.max(np.abs(got[2] - G)) / gs
+    assert abs(got[3] - kkt) < tol_grad * kkt
 
 
 @pytest.mark.parametrize("pw", [70, 130])
@@ -242,6 +260,7 @@ def test_wide_float32_gradient_and_grams_match(ofks, pw):
         ref = res["fp64"][k]
         scale = np.max(np.abs(ref))
         assert np.max(np.abs(res["f32"][k] - ref)) < 2e-5 * scale, (k, np.max(np.abs(res["f32"][k] - ref)) / scale)
+    check_against_oracle(s, m, X, res["f32"], 2e-5, 1e-4)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])

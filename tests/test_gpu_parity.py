@@ -186,6 +186,23 @@ def test_linear_problem_matches_dense_eigenproblem(ofks):
     ctx.close()
 
 
+def test_converged_wide_block_matches_dense_eigenproblem(ofks):
+    # p = 41 on the reduced chain (n = 20,655), linear problem (no Hartree, no xc): the converged
+    # PCAL block and Rayleigh-Ritz give the 41 lowest eigenvalues of the dense pencil (L/2 + M_ext, B)
+    import scipy.sparse.linalg as spla
+    s = I.chain(cells=(26, 14, 8))
+    ctx, pr, V, m = build_pair(ofks, s, hartree=0, xc=0, tol=1e-11, max_iter=20000)
+    ctx.init_orbitals(V)
+    res = ctx.solve()
+    assert res["converged"] == 1
+    assert res["fea"] <= 1e-10
+    eig = ctx.rayleigh_ritz()
+    H = pr.hamiltonian(pr.potentials(np.zeros_like(pr.Vext_q))).tocsc()
+    ref = np.sort(spla.eigsh(H, k=s.p, M=pr.Bf.tocsc(), sigma=-60.0, which="LM", return_eigenvectors=False))
+    np.testing.assert_allclose(eig, ref, atol=1e-7)
+    ctx.close()
+
+
 def test_single_orbital_feasibility(ofks):
     s = I.hydrogenic(2.0, half=10.0, cells=(6, 6, 6), p=1)
     ctx, pr, V, m = build_pair(ofks, s)

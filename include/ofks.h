@@ -165,9 +165,9 @@ typedef struct {
                                (the norm the PCG reduces), averaged over those columns; 0 the relative
                                squared error |D - D*|^2 / |D*|^2 averaged over all columns */
     int32_t learned_retry;  /* OFKS_PC_LEARNED: after a call in which the judge took none of the network's
-                               directions and none was a better PCG start than zero, the network sits out
-                               the next 1, 2, 4, ... calls (at most learned_retry; reset when it helps
-                               again); 0: the network runs on every call */
+                               directions, the network sits out the next 1, 2, 4, ... calls (at most
+                               learned_retry; reset once the judge takes one again), and those calls run
+                               the PCG from zero; 0: the network runs on every call */
 } ofks_params;
 
 typedef struct {
@@ -243,7 +243,9 @@ int ofks_set_nuclei(ofks_ctx *ctx, int32_t M, const double *Z, const double *R);
  * work overlaps on the GPU (contexts driven concurrently) race. */
 int ofks_set_nuclei_static(ofks_ctx *ctx, int32_t M, const double *Z, const double *R);
 
-/* Parameters; p must satisfy 1 <= p <= n_free.  Changing p drops the orbitals.
+/* Parameters; p must satisfy 1 <= p <= n_free.  Changing p drops the orbitals.  A converged
+ * context is reopened: the next ofks_step takes the stop test again under the new parameters
+ * (and returns at once if it still holds).
  * Errors: OFKS_EINVAL for values out of range, OFKS_ESTATE without a mesh. */
 int ofks_set_params(ofks_ctx *ctx, const ofks_params *prm);
 

@@ -333,7 +333,9 @@ static int precondition_t(ofks_ctx *c) {
                                "direction copy");
     }
     const bool learned = c->prm.precond == OFKS_PC_LEARNED;
-    // the network runs unless it sits out a pause after calls in which it helped no column
+    // the network runs unless it sits out a pause after calls in which the judge took none of its
+    // directions (the PCG then does all the work, and the network's cost is not repaid)
+    if (c->prm.learned_retry == 0) c->gcn_skip = 0;
     const bool net = learned && c->gcn_skip == 0;
     if (learned && !net) c->gcn_skip--;
     PcgView<T> v;
@@ -445,7 +447,7 @@ static int precondition_t(ofks_ctx *c) {
         }
         c->judge_accept += accepted;
         c->learned_warm += nwarm;
-        if (accepted == 0 && nwarm == 0) {
+        if (accepted == 0) {              // the PCG does all the work: pause the network
             if (c->prm.learned_retry > 0) {
                 c->gcn_backoff = std::min(c->prm.learned_retry, std::max(1, 2 * c->gcn_backoff));
                 c->gcn_skip = c->gcn_backoff;
@@ -806,6 +808,7 @@ int ofks_set_params(ofks_ctx *c, const ofks_params *prm) {
     const bool mixed = prm->precision == OFKS_MIXED;
     const bool realloc = prm->p != c->p || mixed != c->mixed_alloc;
     c->prm = *prm;
+    c->converged = false;     // the stop test is taken again, under these parameters, at the next iterate
     clear_graphs(c);                              // captured sequences depend on the parameters
     c->evaluated = false;
     if (realloc) {
@@ -839,6 +842,7 @@ int ofks_init_orbitals(ofks_ctx *c, const double *V) {
     state_to32(c);
     c->switch_k = -1;
     c->have_X = true; c->have_prev = false; c->converged = false; c->evaluated = false;
+    c->gcn_skip = 0; c->gcn_backoff = 0;     // the learned preconditioner's pauses restart
     c->k = 0; c->kkt0 = 0; c->eta = 0;
     c->history.clear();
     c->t_start = now_s();
@@ -869,6 +873,7 @@ int ofks_set_orbitals(ofks_ctx *c, const double *X, int32_t keep) {
     c->evaluated = false;
     if (!keep) {
         c->have_prev = false; c->converged = false; c->k = 0; c->kkt0 = 0; c->eta = 0;
+        c->gcn_skip = 0; c->gcn_backoff = 0;     // the learned preconditioner's pauses restart
         c->history.clear();
         c->t_start = now_s();
     }
@@ -1145,6 +1150,7 @@ int ofks_load_state(ofks_ctx *c, const char *path) {
     c->phase = (h.phase == 32 && c->mixed_alloc) ? 32 : 64;
     state_to32(c);
     c->have_X = true; c->k = h.k; c->have_prev = h.have_prev; c->converged = h.converged; c->kkt0 = h.kkt0;
+    c->gcn_skip = 0; c->gcn_backoff = 0;     // the learned preconditioner's pauses restart
     c->best_rel = 1.0; c->best_k = h.k;            // the float32 stall test restarts from here
     c->eta = h.eta; c->evaluated = false;
     c->history = hist;

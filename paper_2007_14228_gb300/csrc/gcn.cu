@@ -49,34 +49,44 @@ __global__ void __launch_bounds__(256) k_feat_stats(int64_t n, int p, const floa
     col_partial(b, gid < S, p, p, stats + (int64_t)p * gridDim.x);
 }
 
-// features (rows (i, c)), the column scales s_c and the Jacobi diagonals diag (n x p)
+// per column: the scale s_c = rms(z), the mean log-diagonal and the shift lam_c = min(Lambda_cc, 0)
+// (float32, colf[0..p) s, [p..2p) mean log, [2p..3p) lam; s also to scale)
+__global__ void k_col_scales(int64_t n, int p, const double *__restrict__ stats, const double *__restrict__ shift,
+                             float *colf, float *scale) {
+    for (int c = threadIdx.x; c < p; c += blockDim.x) {
+        const float s = (float)sqrt(stats[c] / (double)n);
+        colf[c] = s;
+        colf[p + c] = (float)(stats[p + c] / (double)n);
+        colf[2 * p + c] = (float)fmin(shift[c], 0.0);
+        scale[c] = s;
+    }
+}
+
+// features (rows (i, c)): one float4 per row, from the per-column values of k_col_scales
 __global__ void __launch_bounds__(256) k_features(int64_t n, int p, const float *__restrict__ G,
                                                   const double *__restrict__ dL, const double *__restrict__ dB,
-                                                  const double *__restrict__ shift, const double *__restrict__ stats,
-                                                  float *F, float *scale, float *diagv) {
+                                                  const float *__restrict__ colf, float *F) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n * p) return;
     const int64_t i = e / p;
     const int c = (int)(e - i * p);
-    const float lam = (float)fmin(shift[c], 0.0);
-    const float d = 0.5f * (float)dL[i] - lam * (float)dB[i];
-    const float s = (float)sqrt(stats[c] / (double)n);
-    const float ml = (float)(stats[p + c] / (double)n);
-    float *f = F + e * F0;
-    f[0] = s > 0.f ? G[e] / d / s : 0.f;
-    f[1] = logf(d) - ml;
-    f[2] = -lam * (float)dB[i] / d;
-    f[3] = 1.f;
-    diagv[e] = d;
-    if (i == 0) scale[c] = s;
+    const float lam = colf[2 * p + c], s = colf[c];
+    const float db = (float)dB[i];
+    const float d = 0.5f * (float)dL[i] - lam * db;
+    float4 f;
+    f.x = s > 0.f ? G[e] / d / s : 0.f;
+    f.y = logf(d) - colf[p + c];
+    f.z = -lam * db / d;
+    f.w = 1.f;
+    reinterpret_cast<float4 *>(F)[e] = f;
 }
 
 // Z = H W + AH U + b (rows x FO), H/AH rows x FI; out = relu(Z) if relu else Z.  A block owns 64
 // rows; thread t owns rows 4 (t / (FO/ 4)) ... and 4 consecutive outputs.
-template <int FI, int FO>
+template <int FI, int FO, class OT = float>
 __global__ void __launch_bounds__(256) k_dense(int64_t rows, const float *__restrict__ H, const float *__restrict__ AH,
                                                const float *__restrict__ W, const float *__restrict__ U,
-                                               const float *__restrict__ b, int relu, float *Z, float *out) {
+                                               const float *__restrict__ b, int relu, float *Z, OT *out) {
     constexpr int RB = FI >= 64 ? 16 : 64;             // rows per tile (static shared memory <= 48 KiB)
     constexpr int OC = FO >= 4 ? 4 : 1;                 // outputs per thread
     constexpr int TPR = FO / OC;                        // threads per row group
@@ -115,11 +125,24 @@ __global__ void __launch_bounds__(256) k_dense(int64_t rows, const float *__rest
             for (int a = 0; a < RPT; ++a) {
                 const int64_t r = r0 + rg * RPT + a;
                 if (r >= rows) continue;
+                if constexpr (sizeof(OT) == 2 && OC == 4) {      // bf16 out: one 8-byte store
+                    const float v0 = relu ? fmaxf(acc[a][0], 0.f) : acc[a][0], v1 = relu ? fmaxf(acc[a][1], 0.f) : acc[a][1];
+                    const float v2 = relu ? fmaxf(acc[a][2], 0.f) : acc[a][2], v3 = relu ? fmaxf(acc[a][3], 0.f) : acc[a][3];
+                    __nv_bfloat162 lo = __floats2bfloat162_rn(v0, v1), hi = __floats2bfloat162_rn(v2, v3);
+                    uint2 pk;
+                    pk.x = *reinterpret_cast<uint32_t *>(&lo);
+                    pk.y = *reinterpret_cast<uint32_t *>(&hi);
+                    *reinterpret_cast<uint2 *>(out + r * FO + og * OC) = pk;
+                    if (Z)
 #pragma unroll
-                for (int o = 0; o < OC; ++o) {
-                    const float z = acc[a][o];
-                    if (Z) Z[r * FO + og * OC + o] = z;
-                    out[r * FO + og * OC + o] = relu ? fmaxf(z, 0.f) : z;
+                        for (int o = 0; o < OC; ++o) Z[r * FO + og * OC + o] = acc[a][o];
+                } else {
+#pragma unroll
+                    for (int o = 0; o < OC; ++o) {
+                        const float z = acc[a][o];
+                        if (Z) Z[r * FO + og * OC + o] = z;
+                        out[r * FO + og * OC + o] = (OT)(relu ? fmaxf(z, 0.f) : z);
+                    }
                 }
             }
         }
@@ -366,6 +389,73 @@ __global__ void k_unpack(int64_t n, int p, int ld, const int *__restrict__ cmap,
 inline unsigned gr(int64_t m) { return (unsigned)std::max<int64_t>(1, (m + 255) / 256); }
 inline unsigned gr_stride(int64_t m) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 152 * 8)); }
 
+// out = A in for bfloat16 activations of rowlen values per node (rowlen a multiple of 8), float32
+// accumulation: one warp per (SELL slot, 256-value piece of the row); each lane owns 8 values
+// (one 16-byte load per neighbour).  The neighbours come from the slot's SELL entries; padding
+// entries have A = 0 and are skipped.
+__global__ void __launch_bounds__(256) k_agg_bf16(int64_t n_slices, int rowlen, const int *__restrict__ slice_ptr,
+                                                  const int *__restrict__ slice_w, const int *__restrict__ cols,
+                                                  const int *__restrict__ perm, const float *__restrict__ val,
+                                                  const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *out) {
+    const int nchunk = (rowlen + 255) / 256;
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= n_slices * SELL_C * nchunk) return;
+    const int64_t slot = gw / nchunk;
+    const int ch = (int)(gw - slot * nchunk);
+    const int64_t sl = slot / SELL_C;
+    const int l = (int)(slot - sl * SELL_C);
+    const int r = perm[slot];
+    if (r < 0) return;                                   // the whole warp shares the slot
+    const int k0 = ch * 256 + lane * 8;
+    const bool own = k0 < rowlen;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int base = slice_ptr[sl], width = slice_w[sl];
+    // four neighbours per pass, their loads issued before the multiply-adds (padding entries have
+    // A = 0 and a valid column, so they are read and add nothing)
+    const int kk = own ? k0 : 0;
+    int j = 0;
+    for (; j + 4 <= width; j += 4) {
+        float a[4];
+        uint4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = base + (j + u) * SELL_C + l;
+            a[u] = __ldg(val + e);
+            v[u] = __ldg(reinterpret_cast<const uint4 *>(in + (int64_t)__ldg(cols + e) * rowlen + kk));
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v[u]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float2 f = __bfloat1622float2(h[i]);
+                acc[2 * i] = fmaf(a[u], f.x, acc[2 * i]);
+                acc[2 * i + 1] = fmaf(a[u], f.y, acc[2 * i + 1]);
+            }
+        }
+    }
+    for (; j < width; ++j) {
+        const int e = base + j * SELL_C + l;
+        const float a = __ldg(val + e);
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(in + (int64_t)__ldg(cols + e) * rowlen + kk));
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 f = __bfloat1622float2(h[i]);
+            acc[2 * i] = fmaf(a, f.x, acc[2 * i]);
+            acc[2 * i + 1] = fmaf(a, f.y, acc[2 * i + 1]);
+        }
+    }
+    if (own) {
+        uint4 o;
+        __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&o);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(acc[2 * i], acc[2 * i + 1]);
+        *reinterpret_cast<uint4 *>(out + (int64_t)r * rowlen + k0) = o;
+    }
+}
+
 }  // namespace
 
 // layer dimensions for width H
@@ -393,8 +483,8 @@ static void offsets(int H, int64_t off[3][3]) {
 
 void gcn_free(ofks_ctx *c) {
     GcnState &g = c->gcn;
-    for (float *q : {g.w, g.m, g.v, g.valA, g.valAT, g.F, g.H1, g.H2, g.Z1, g.Z2, g.AH, g.y, g.scale, g.diag, g.Dn,
-                     g.Ds, g.dA, g.dB2, g.G32, g.valL32, g.valB32})
+    for (float *q : {g.w, g.m, g.v, g.valA, g.valAT, g.F, g.H1, g.H2, g.Z1, g.Z2, g.AH, g.y, g.scale, g.Dn,
+                     g.Ds, g.dA, g.dB2, g.G32, g.valL32, g.valB32, g.colf})
         if (q) cudaFree(q);
     for (double *q : {g.grad, g.stats, g.lacc}) if (q) cudaFree(q);
     c->gcn = GcnState{};
@@ -465,7 +555,8 @@ static int gcn_buffers(ofks_ctx *c) {
     GcnState &g = c->gcn;
     const int64_t rows = c->n * (int64_t)c->p;
     if (g.rows == rows && g.F) return OFKS_OK;
-    for (float **q : {&g.F, &g.H1, &g.H2, &g.Z1, &g.Z2, &g.AH, &g.y, &g.scale, &g.diag, &g.Dn, &g.Ds, &g.dA, &g.dB2, &g.G32}) {
+    for (float **q : {&g.F, &g.H1, &g.H2, &g.Z1, &g.Z2, &g.AH, &g.y, &g.scale, &g.Dn, &g.Ds, &g.dA, &g.dB2, &g.G32,
+                      &g.colf}) {
         if (*q) cudaFree(*q);
         *q = nullptr;
     }
@@ -474,8 +565,9 @@ static int gcn_buffers(ofks_ctx *c) {
     auto alloc = [&](float **q, int64_t cnt) { return cudaMalloc((void **)q, sizeof(float) * std::max<int64_t>(cnt, 1)); };
     if (alloc(&g.F, rows * F0) || alloc(&g.H1, rows * H) || alloc(&g.H2, rows * H) || alloc(&g.Z1, rows * H) ||
         alloc(&g.Z2, rows * H) || alloc(&g.AH, rows * H) || alloc(&g.y, rows) || alloc(&g.scale, c->p) ||
-        alloc(&g.diag, rows) || alloc(&g.Dn, rows) || alloc(&g.Ds, rows) || alloc(&g.dA, rows * H) ||
+        alloc(&g.Dn, rows) || alloc(&g.Ds, rows) || alloc(&g.dA, rows * H) ||
         alloc(&g.dB2, rows * H) || alloc(&g.G32, rows) ||
+        alloc(&g.colf, 3 * 256) ||
         cudaMalloc((void **)&g.stats, sizeof(double) * 2 * c->p) != cudaSuccess ||
         cudaMalloc((void **)&g.lacc, sizeof(double) * 2 * c->p) != cudaSuccess)
         return ofks_fail(c, OFKS_ENOMEM, "learned preconditioner: activations for %lld rows", (long long)rows);
@@ -517,34 +609,47 @@ int gcn_forward(ofks_ctx *c, const double *shift, bool keep) {
         k_feat_stats<<<gs, 256, 0, c->stream>>>(n, (int)p, g.G32, c->d_dL, c->d_dB, shift, c->d_cpart);
         launch_col_fin(c, (int)(2 * p), (int)(2 * p), gs, c->d_cpart, g.stats);
     }
-    k_features<<<gr(rows), 256, 0, c->stream>>>(n, (int)p, g.G32, c->d_dL, c->d_dB, shift, g.stats, g.F, g.scale, g.diag);
+    k_col_scales<<<1, 256, 0, c->stream>>>(n, (int)p, g.stats, shift, g.colf, g.scale);
+    k_features<<<gr(rows), 256, 0, c->stream>>>(n, (int)p, g.G32, c->d_dL, c->d_dB, g.colf, g.F);
     // layer 0: F (4) -> H1
     aggregate(c, g.valA, g.F, g.AH, F0);
     const unsigned gd = (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 15) / 16, 152LL * 8));
+    if (!keep && H == 64 && c->prm.learned_tc) {
+        // inference on the tensor cores, which take bf16 operands: H1 and A H1 are kept in bf16
+        // (half the bytes of the width-64p aggregation, the network's largest data movement)
+        __nv_bfloat16 *H1b = reinterpret_cast<__nv_bfloat16 *>(g.H1), *AH1b = reinterpret_cast<__nv_bfloat16 *>(g.AH);
+        k_dense<F0, 64, __nv_bfloat16><<<gd, 256, 0, c->stream>>>(rows, g.F, g.AH, g.w + off[0][0], g.w + off[0][1],
+                                                                   g.w + off[0][2], 1, nullptr, H1b);
+        const int rowlen = (int)(64 * p);
+        const int64_t warps = (int64_t)c->n_slices * SELL_C * ((rowlen + 255) / 256);
+        k_agg_bf16<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, c->stream>>>(
+            c->n_slices, rowlen, c->d_slice_ptr, c->d_slice_w, c->d_cols, c->d_perm, g.valA, H1b, AH1b);
+        float *a = g.y, *q = g.Ds, *Aq = g.Z1;
+        launch_dense_tc_bf16(c, rows, H1b, AH1b, g.w + off[1][0], g.w + off[1][1], g.w + off[1][2], g.w + off[2][0],
+                             g.w + off[2][1], a, q);
+        launch_sell_spmm_ld<float>(c, g.valA, q, Aq, (int)p);
+        k_output_dots<<<gr(rows), 256, 0, c->stream>>>(n, (int)p, g.F, a, Aq, g.w + off[2][2], g.scale, g.Dn);
+        c->kernels += 6;               // the aggregations, column sums and the tensor-core layer count themselves
+        return ofks_cuda_check(c, cudaGetLastError(), "learned preconditioner forward");
+    }
     DISPATCH_DENSE(F0, H, k_dense<A_, B_><<<gd, 256, 0, c->stream>>>(rows, g.F, g.AH, g.w + off[0][0], g.w + off[0][1],
                                                                       g.w + off[0][2], 1, nullptr, g.H1));
     // layer 1: H1 -> H2 (tensor cores for width 64 at inference; training keeps float32 activations)
     aggregate(c, g.valA, g.H1, g.AH, H);
     if (!keep) {
-        // inference: the last layer needs H2 only through the row products a = H2 w and q = H2 u
-        // (y = a + A q + b), so H2 is never aggregated (a width-p aggregation instead of 64 p); the
-        // tensor-core layer forms a and q in its epilogue without writing H2
+        // inference on the CUDA cores: the last layer needs H2 only through the row products
+        // a = H2 w and q = H2 u (y = a + A q + b), so H2 is never aggregated (a width-p
+        // aggregation instead of 64 p); the tensor-core path above forms a and q in its epilogue
         float *a = g.y, *q = g.Ds, *Aq = g.Z1;
-        if (H == 64 && c->prm.learned_tc) {
-            launch_dense_tc(c, rows, g.H1, g.AH, g.w + off[1][0], g.w + off[1][1], g.w + off[1][2], nullptr,
-                            g.w + off[2][0], g.w + off[2][1], a, q);
-        } else {
-            DISPATCH_DENSE(H, H, k_dense<A_, B_><<<gd, 256, 0, c->stream>>>(rows, g.H1, g.AH, g.w + off[1][0],
-                                                                             g.w + off[1][1], g.w + off[1][2], 1, nullptr, g.H2));
-            if (H == 64) k_rowdots<64><<<gr(rows), 256, 0, c->stream>>>(rows, g.H2, g.w + off[2][0], g.w + off[2][1], a, q);
-            else if (H == 32) k_rowdots<32><<<gr(rows), 256, 0, c->stream>>>(rows, g.H2, g.w + off[2][0], g.w + off[2][1], a, q);
-            else if (H == 16) k_rowdots<16><<<gr(rows), 256, 0, c->stream>>>(rows, g.H2, g.w + off[2][0], g.w + off[2][1], a, q);
-            else k_rowdots<8><<<gr(rows), 256, 0, c->stream>>>(rows, g.H2, g.w + off[2][0], g.w + off[2][1], a, q);
-            c->kernels += 1;
-        }
+        DISPATCH_DENSE(H, H, k_dense<A_, B_><<<gd, 256, 0, c->stream>>>(rows, g.H1, g.AH, g.w + off[1][0],
+                                                                         g.w + off[1][1], g.w + off[1][2], 1, nullptr, g.H2));
+        if (H == 64) k_rowdots<64><<<gr(rows), 256, 0, c->stream>>>(rows, g.H2, g.w + off[2][0], g.w + off[2][1], a, q);
+        else if (H == 32) k_rowdots<32><<<gr(rows), 256, 0, c->stream>>>(rows, g.H2, g.w + off[2][0], g.w + off[2][1], a, q);
+        else if (H == 16) k_rowdots<16><<<gr(rows), 256, 0, c->stream>>>(rows, g.H2, g.w + off[2][0], g.w + off[2][1], a, q);
+        else k_rowdots<8><<<gr(rows), 256, 0, c->stream>>>(rows, g.H2, g.w + off[2][0], g.w + off[2][1], a, q);
         launch_sell_spmm_ld<float>(c, g.valA, q, Aq, (int)p);
         k_output_dots<<<gr(rows), 256, 0, c->stream>>>(n, (int)p, g.F, a, Aq, g.w + off[2][2], g.scale, g.Dn);
-        c->kernels += 8;
+        c->kernels += 7;
         return ofks_cuda_check(c, cudaGetLastError(), "learned preconditioner forward");
     }
     DISPATCH_DENSE(H, H, k_dense<A_, B_><<<gd, 256, 0, c->stream>>>(rows, g.H1, g.AH, g.w + off[1][0],
@@ -553,7 +658,7 @@ int gcn_forward(ofks_ctx *c, const double *shift, bool keep) {
     aggregate(c, g.valA, g.H2, g.dA, H);
     k_dense_out<<<gr(rows), 256, 0, c->stream>>>(rows, H, g.H2, g.dA, g.w + off[2][0], g.w + off[2][1], g.w + off[2][2], g.y);
     k_output<<<gr(rows), 256, 0, c->stream>>>(n, (int)p, g.F, g.y, g.scale, g.Dn);
-    c->kernels += 9;
+    c->kernels += 7;
     return ofks_cuda_check(c, cudaGetLastError(), "learned preconditioner forward");
 }
 

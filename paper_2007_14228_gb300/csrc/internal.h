@@ -71,10 +71,11 @@ struct GcnState {
     float *valA = nullptr, *valAT = nullptr;     // mean aggregation A and A^T on the SELL pattern
     int64_t rows = 0;                            // n * p the activations are sized for
     float *F = nullptr, *H1 = nullptr, *H2 = nullptr, *Z1 = nullptr, *Z2 = nullptr, *AH = nullptr;
-    float *y = nullptr, *scale = nullptr, *diag = nullptr, *Dn = nullptr, *Ds = nullptr;
+    float *y = nullptr, *scale = nullptr, *Dn = nullptr, *Ds = nullptr;
     float *dA = nullptr, *dB2 = nullptr, *G32 = nullptr;
     double *stats = nullptr, *lacc = nullptr;
     float *valL32 = nullptr, *valB32 = nullptr;  // float32 L and B on the SELL pattern (energy loss)
+    float *colf = nullptr;                       // per-column scale, mean log-diagonal and shift (float32)
     int64_t t = 0;                               // Adam step count
     int cols = 0;                                // columns of the next application (0: all p)
 };
@@ -381,6 +382,8 @@ int gcn_adam(ofks_ctx *c, double lr);
 void launch_dense_tc(ofks_ctx *c, int64_t rows, const float *H, const float *AH, const float *W, const float *U,
                      const float *b, float *out, const float *w2 = nullptr, const float *u2 = nullptr,
                      float *a = nullptr, float *q = nullptr);
+void launch_dense_tc_bf16(ofks_ctx *c, int64_t rows, const __nv_bfloat16 *H, const __nv_bfloat16 *AH, const float *W,
+                          const float *U, const float *b, const float *w2, const float *u2, float *a, float *q);
 // the network's block: column k is column cmap[k] of the n x ld block (cmap NULL: k), for the
 // gcn.cols columns the next application works on (0: all p)
 template <class E> void gcn_pack(ofks_ctx *c, const E *src, float *dst, const int *cmap = nullptr);

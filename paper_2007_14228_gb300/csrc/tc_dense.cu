@@ -43,8 +43,9 @@ __device__ __forceinline__ int core_off(int r, int k) { return ((r >> 3) * (TK /
 
 // out != nullptr: out = relu(Z) (rows x 64).  out == nullptr: the next layer's two row products
 // a = relu(Z) w2 and q = relu(Z) u2 (w2, u2 of length 64) go to a and q instead.
-__global__ void __launch_bounds__(128, 4) k_dense_tc(int64_t rows, const float *__restrict__ H,
-                                                     const float *__restrict__ AH, const float *__restrict__ W,
+template <class In>
+__global__ void __launch_bounds__(128, 4) k_dense_tc(int64_t rows, const In *__restrict__ H,
+                                                     const In *__restrict__ AH, const float *__restrict__ W,
                                                      const float *__restrict__ U, const float *__restrict__ b,
                                                      float *out, const float *__restrict__ w2,
                                                      const float *__restrict__ u2, float *a, float *q, int *err) {
@@ -86,20 +87,33 @@ __global__ void __launch_bounds__(128, 4) k_dense_tc(int64_t rows, const float *
     uint32_t phase = 0;
 
     for (int64_t r0 = (int64_t)blockIdx.x * TM; r0 < rows; r0 += (int64_t)TM * gridDim.x) {
-        // A tile: rows r0 .. r0 + 127 of [H | AH], converted to bf16, four values per load and
-        // one 8-byte store (four consecutive K of one core-matrix row)
-        for (int e = tid; e < TM * TK / 4; e += blockDim.x) {
-            const int r = e / (TK / 4), k = 4 * (e - r * (TK / 4));
-            const int64_t row = r0 + r;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (row < rows)
-                v = k < 64 ? *reinterpret_cast<const float4 *>(H + row * 64 + k)
-                           : *reinterpret_cast<const float4 *>(AH + row * 64 + (k - 64));
-            __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
-            uint2 pk;
-            pk.x = *reinterpret_cast<uint32_t *>(&lo);
-            pk.y = *reinterpret_cast<uint32_t *>(&hi);
-            *reinterpret_cast<uint2 *>(sA + core_off(r, k)) = pk;
+        if constexpr (sizeof(In) == 4) {
+            // A tile: rows r0 .. r0 + 127 of [H | AH], converted to bf16, four values per load and
+            // one 8-byte store (four consecutive K of one core-matrix row)
+            for (int e = tid; e < TM * TK / 4; e += blockDim.x) {
+                const int r = e / (TK / 4), k = 4 * (e - r * (TK / 4));
+                const int64_t row = r0 + r;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (row < rows)
+                    v = k < 64 ? *reinterpret_cast<const float4 *>(H + row * 64 + k)
+                               : *reinterpret_cast<const float4 *>(AH + row * 64 + (k - 64));
+                __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+                uint2 pk;
+                pk.x = *reinterpret_cast<uint32_t *>(&lo);
+                pk.y = *reinterpret_cast<uint32_t *>(&hi);
+                *reinterpret_cast<uint2 *>(sA + core_off(r, k)) = pk;
+            }
+        } else {
+            // bf16 activations: one 16-byte load is one core-matrix row (eight consecutive K)
+            for (int e = tid; e < TM * TK / 8; e += blockDim.x) {
+                const int r = e / (TK / 8), k = 8 * (e - r * (TK / 8));
+                const int64_t row = r0 + r;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (row < rows)
+                    v = k < 64 ? *reinterpret_cast<const uint4 *>(H + row * 64 + k)
+                               : *reinterpret_cast<const uint4 *>(AH + row * 64 + (k - 64));
+                *reinterpret_cast<uint4 *>(sA + core_off(r, k)) = v;
+            }
         }
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
@@ -189,7 +203,18 @@ void launch_dense_tc(ofks_ctx *c, int64_t rows, const float *H, const float *AH,
     const int64_t tiles = (rows + TM - 1) / TM;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, 152 * 4));
     const int smem = (TM + TN) * TK * (int)sizeof(__nv_bfloat16);
-    cudaFuncSetAttribute(k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_dense_tc<<<grid, 128, smem, c->stream>>>(rows, H, AH, W, U, b, out, w2, u2, a, q, c->d_flag);
+    cudaFuncSetAttribute(k_dense_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_dense_tc<float><<<grid, 128, smem, c->stream>>>(rows, H, AH, W, U, b, out, w2, u2, a, q, c->d_flag);
+    c->kernels += 1;
+}
+
+// the same layer from bf16 activations (rows x 64 each), only the products a and q
+void launch_dense_tc_bf16(ofks_ctx *c, int64_t rows, const __nv_bfloat16 *H, const __nv_bfloat16 *AH, const float *W,
+                          const float *U, const float *b, const float *w2, const float *u2, float *a, float *q) {
+    const int64_t tiles = (rows + TM - 1) / TM;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, 152 * 4));
+    const int smem = (TM + TN) * TK * (int)sizeof(__nv_bfloat16);
+    cudaFuncSetAttribute(k_dense_tc<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_dense_tc<__nv_bfloat16><<<grid, 128, smem, c->stream>>>(rows, H, AH, W, U, b, nullptr, w2, u2, a, q, c->d_flag);
     c->kernels += 1;
 }

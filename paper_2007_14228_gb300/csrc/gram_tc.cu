@@ -6,13 +6,17 @@
 // persistent CTA walks 64-row slabs of the rows: the slab's contiguous rows of X, A and B
 // (64 * ld floats each) arrive in shared memory by the TMA bulk-copy engine (cp.async.bulk with
 // an mbarrier transaction count, double-buffered so the next slab streams in while this one is
-// converted and multiplied); the threads split every float v into bf16 hi + lo (hi = bf16(v),
-// lo = bf16(v - hi)) and write both parts transposed into the no-swizzle K-major core-matrix
-// layout; one elected thread issues the three products hi*hi + hi*lo + lo*hi (the missing lo*lo
-// and the rounding of lo are ~2^-16 of each product) as M = 128, N = 2 ld16, K = 16 MMAs into a
-// float32 accumulator in tensor memory.  Eight warps convert; after the last slab warps 0-3 read
-// their 32 rows each back and add the upper triangle (i <= j < p) to the float64 outputs;
-// k_mirror2 fills the lower one.
+// converted and multiplied); the threads split every float v three ways in bf16 (v = h + m + l:
+// h = bf16(v), m = bf16(v - h), l = bf16(v - h - m)) and write the parts transposed into the
+// no-swizzle K-major core-matrix layout; one elected thread issues the six products
+// hh + hm + mh + hl + lh + mm (the dropped terms are ~2^-24 of each product, float32's own
+// rounding) as M = 128, N = 2 ld16, K = 16 MMAs into a float32 accumulator in tensor memory.  (A
+// two-way split, hh + hl + lh, leaves ~2^-16 of each product; in the multipliers, which sum
+// products of both signs, that held the float32 iterations' energy 3.7e-3 Ha from the float64
+// fixed point on the chain.)  Eight warps convert; after its last slab a CTA's warps 0-3 read
+// their 32 rows each back and write the upper triangle (i <= j < p) as the CTA's float64
+// partial; k_gram_fin adds the CTAs' partials in order and mirrors.  Four CTAs' worth of slabs
+// per SM (in waves) keep the float32 accumulation short.
 // Every wait is bounded: on timeout the CTA records an error flag, waits (bounded) for its own
 // copies in flight, frees its tensor memory and returns.
 #include <algorithm>
@@ -41,6 +45,13 @@ __device__ __forceinline__ uint64_t gdesc(uint32_t saddr, uint32_t lbo, uint32_t
 
 // element (r, k) of a K-major tile with GKS columns: core matrix (r / 8, k / 8) of 8 x 8
 __device__ __forceinline__ int goff(int r, int k) { return ((r >> 3) * (GKS >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
+
+__device__ __forceinline__ void split3(float v, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
+    h = __float2bfloat16(v);
+    const float r1 = v - __bfloat162float(h);
+    m = __float2bfloat16(r1);
+    l = __float2bfloat16(r1 - __bfloat162float(m));
+}
 
 __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity) {
     uint32_t done = 0;
@@ -73,10 +84,8 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(int64_t n, int p, int ld, in
     extern __shared__ __align__(128) unsigned char gsm[];
     const int NP = 2 * nh;
     float *raw = reinterpret_cast<float *>(gsm);                           // 2 buffers x 3 x GKS x ld
-    __nv_bfloat16 *ah = reinterpret_cast<__nv_bfloat16 *>(raw + (size_t)2 * 3 * GKS * ld);
-    __nv_bfloat16 *al = ah + GTM * GKS;
-    __nv_bfloat16 *bh = al + GTM * GKS;
-    __nv_bfloat16 *bl = bh + (size_t)NP * GKS;
+    __nv_bfloat16 *xs = reinterpret_cast<__nv_bfloat16 *>(raw + (size_t)2 * 3 * GKS * ld);   // 3 x GTM x GKS
+    __nv_bfloat16 *ys = xs + (size_t)3 * GTM * GKS;                                          // 3 x NP x GKS
     __shared__ __align__(8) uint64_t bar_ld[2], bar_mma;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
@@ -90,8 +99,8 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(int64_t n, int p, int ld, in
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     // operand tiles start at zero: the padding rows (m >= ld) and columns stay zero
-    for (int e = tid; e < (2 * GTM + 2 * NP) * GKS / 8; e += blockDim.x)
-        reinterpret_cast<uint4 *>(ah)[e] = make_uint4(0u, 0u, 0u, 0u);
+    for (int e = tid; e < 3 * (GTM + NP) * GKS / 8; e += blockDim.x)
+        reinterpret_cast<uint4 *>(xs)[e] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s32(&bar_ld[b])));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s32(&bar_mma)));
@@ -126,19 +135,19 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(int64_t n, int p, int ld, in
         if (!ok) abort_flag = 1;
         __syncthreads();
         if (abort_flag) break;
-        // hi / lo split, transposed into the K-major tiles: X^T (m = column of X) and [A | B]^T
+        // three-way split, transposed into the K-major tiles: X^T (m = column of X) and [A | B]^T
         const float *rx = raw + (size_t)buf * 3 * GKS * ld, *ra = rx + (size_t)GKS * ld, *rb = ra + (size_t)GKS * ld;
+        const size_t xq = (size_t)GTM * GKS, yq = (size_t)NP * GKS;
         for (int e = tid; e < GKS * ld; e += blockDim.x) {
             const int k = e / ld, m = e - k * ld;
             const bool in = k < rows;
-            const float vx = in ? rx[e] : 0.f, va = in ? ra[e] : 0.f, vb = in ? rb[e] : 0.f;
-            const __nv_bfloat16 hx = __float2bfloat16(vx), ha = __float2bfloat16(va), hb = __float2bfloat16(vb);
-            ah[goff(m, k)] = hx;
-            al[goff(m, k)] = __float2bfloat16(vx - __bfloat162float(hx));
-            bh[goff(m, k)] = ha;
-            bl[goff(m, k)] = __float2bfloat16(va - __bfloat162float(ha));
-            bh[goff(nh + m, k)] = hb;
-            bl[goff(nh + m, k)] = __float2bfloat16(vb - __bfloat162float(hb));
+            __nv_bfloat16 h, md, l;
+            split3(in ? rx[e] : 0.f, h, md, l);
+            xs[goff(m, k)] = h; xs[xq + goff(m, k)] = md; xs[2 * xq + goff(m, k)] = l;
+            split3(in ? ra[e] : 0.f, h, md, l);
+            ys[goff(m, k)] = h; ys[yq + goff(m, k)] = md; ys[2 * yq + goff(m, k)] = l;
+            split3(in ? rb[e] : 0.f, h, md, l);
+            ys[goff(nh + m, k)] = h; ys[yq + goff(nh + m, k)] = md; ys[2 * yq + goff(nh + m, k)] = l;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
@@ -146,8 +155,14 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(int64_t n, int p, int ld, in
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (tid == 0) {
             const uint32_t sbo = (GKS / 8) * 128u;
-            const uint32_t opa[3] = {s32(ah), s32(ah), s32(al)}, opb[3] = {s32(bh), s32(bl), s32(bh)};
-            for (int term = 0; term < 3; ++term)
+            // parts 0 = h, 1 = m, 2 = l: hh, hm, mh, hl, lh, mm
+            const int ta[6] = {0, 0, 1, 0, 2, 1}, tb[6] = {0, 1, 0, 2, 0, 1};
+            uint32_t opa[6], opb[6];
+            for (int q = 0; q < 6; ++q) {
+                opa[q] = s32(xs + (size_t)ta[q] * GTM * GKS);
+                opb[q] = s32(ys + (size_t)tb[q] * NP * GKS);
+            }
+            for (int term = 0; term < 6; ++term)
                 for (int kk = 0; kk < GKS / 16; ++kk) {
                     const uint64_t ad = gdesc(opa[term] + kk * 256, 128, sbo);
                     const uint64_t bd = gdesc(opb[term] + kk * 256, 128, sbo);
@@ -221,9 +236,10 @@ bool launch_gram_tc(ofks_ctx *c, const float *X, const float *A, const float *B,
     if (!c->prm.gram_tc || ld < 4 || ld % 4 || ld > 64 || c->n < GKS) return false;
     const int nh = (ld + 15) / 16 * 16, NP = 2 * nh;
     const int tcols = NP <= 32 ? 32 : (NP <= 64 ? 64 : 128);
-    const size_t smem = sizeof(float) * 2 * 3 * GKS * ld + sizeof(__nv_bfloat16) * (size_t)(2 * GTM + 2 * NP) * GKS;
+    const size_t smem = sizeof(float) * 2 * 3 * GKS * ld + sizeof(__nv_bfloat16) * (size_t)3 * (GTM + NP) * GKS;
     const int64_t nslab = (c->n + GKS - 1) / GKS;
-    const unsigned grid = (unsigned)std::min<int64_t>(nslab, 152);
+    // partials of 2 ld^2 doubles per CTA must fit the scratch (CPART_MIN >= 2 * 64^2 * 608)
+    const unsigned grid = (unsigned)std::min<int64_t>(nslab, 152 * 4);
     cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_gram_tc<<<grid, 256, smem, c->stream>>>(c->n, c->p, ld, nh, tcols, X, A, B, part, c->d_flag + 2);
     c->kernels += 1;

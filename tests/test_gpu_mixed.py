@@ -177,9 +177,9 @@ def test_staged_pcg_apply_matches_chunk_major_and_the_oracle(ofks):
 
 @pytest.mark.parametrize("case", ["chain_p41", "h2o_p5"])
 def test_tensor_core_grams_match(ofks, case):
-    # Lambda0 = X^T H X and S = X^T B X (bf16 hi/lo split, three products) and the gradient
-    # G = H X + B X C with kkt (three-way split, six products) of the float32 form from the tensor
-    # cores, against the float32 CUDA-core kernels and the float64 form, all at the same iterate
+    # Lambda0 = X^T H X and S = X^T B X and the gradient G = H X + B X C with kkt (both with a
+    # three-way bf16 split, six products) of the float32 form from the tensor cores, against the
+    # float32 CUDA-core kernels and the float64 form, all at the same iterate
     if case == "chain_p41":
         s = I.chain(cells=(26, 14, 8))
     else:
@@ -209,7 +209,9 @@ def test_tensor_core_grams_match(ofks, case):
     for k in (0, 1):
         ref = res["fp64"][k]
         scale = np.max(np.abs(ref))
-        assert np.max(np.abs(res["tc"][k] - ref)) < 2e-5 * scale, (k, np.max(np.abs(res["tc"][k] - ref)) / scale)
+        # (a two-way split, three products, was 2e-5 off)
+        assert np.max(np.abs(res["tc"][k] - ref)) < 5e-6 * scale, (k, np.max(np.abs(res["tc"][k] - ref)) / scale)
+        assert np.max(np.abs(res["tc"][k] - res["cuda"][k])) < 5e-6 * scale
         assert np.max(np.abs(res["tc"][k] - res["cuda"][k])) < 2e-5 * scale
         assert np.allclose(res["tc"][k], res["tc"][k].T, rtol=0, atol=1e-12 * scale)
     # and against the oracle itself at the same iterate

@@ -101,6 +101,15 @@ enum {
                                 lumped mass M on the lattice coordinates) by fast diagonalization */
 };
 
+/* Preconditioner of the PCG that solves Eq. (precondition-T)'s systems T_k D = G (ofks_params.pcg_pc) */
+enum {
+    OFKS_PCGPC_JACOBI = 0,     /* the diagonal of T_k */
+    OFKS_PCGPC_SEPARABLE = 1   /* lattice meshes, float32 PCG: the exact inverse of the separable
+                                  A_sep / 2 - shift_k Mx (x) My (x) Mz (A_sep as for OFKS_HPC_SEPARABLE)
+                                  by fast diagonalization on the tensor cores, all columns at once;
+                                  elsewhere the diagonal */
+};
+
 typedef struct {
     int32_t p;              /* number of orbitals (columns of X) */
     double  beta;           /* penalty parameter of L_beta (paper Eq. ALM-sub) */
@@ -168,6 +177,8 @@ typedef struct {
                                directions, the network sits out the next 1, 2, 4, ... calls (at most
                                learned_retry; reset once the judge takes one again), and those calls run
                                the PCG from zero; 0: the network runs on every call */
+    int32_t pcg_pc;         /* OFKS_PCGPC_JACOBI (default) or OFKS_PCGPC_SEPARABLE: the preconditioner
+                               inside the PCG (only the accuracy of D changes, never T or the fixed point) */
 } ofks_params;
 
 typedef struct {
@@ -198,7 +209,7 @@ typedef struct {
  * poisson_tol 1e-12, poisson_max_iter 20000, poisson_pc OFKS_HPC_SEPARABLE, mixed_tol 1e-6, poisson_tol_mixed
  * 1e-8, judge_tau 0.5, learned_tc 1, poisson_adaptive 0, poisson_csr 0, gram_tc 1, spmm_f32_rows 0,
  * poisson_sep_tc 1, pcg_compact 1, cuda_graphs 1, pcg_staged 0, sweep_pc32 1, method OFKS_METHOD_PCAL,
- * learned_loss 1, learned_retry 64.  p is set to 1. */
+ * learned_loss 1, learned_retry 64, pcg_pc OFKS_PCGPC_JACOBI.  p is set to 1. */
 void ofks_default_params(ofks_params *prm);
 
 /* Create a context on CUDA device `device`.  *out receives the context (NULL on failure).

@@ -494,8 +494,10 @@ static int precondition_t(ofks_ctx *c) {
             }
             {
                 ProfScope ps(c, PF_PCG_UPDATE);
+                const bool last = !L.exact && it + 1 == L.max_it;
                 launch_pcg_alpha(c, w, v.pc, v.cb);
-                launch_pcg_update(c, b, v, !L.exact && it + 1 == L.max_it);
+                launch_pcg_update(c, b, v, last);
+                if (!last && c->prm.pcg_pc == OFKS_PCGPC_SEPARABLE) launch_pcg_sep(c, b, v);
                 launch_pcg_beta(c, w, v.pc, v.cb);
             }
         }
@@ -503,7 +505,8 @@ static int precondition_t(ofks_ctx *c) {
     if (!exact && max_it > 0) {                  // the fixed-count loop: one graph per shape
         Loop L{c, &b, v, 0, max_it, max_it, false};
         const std::vector<int64_t> key = {1, (int64_t)sizeof(T), w, v.pc, max_it, (int64_t)(uintptr_t)v.cb,
-                                          (int64_t)(uintptr_t)v.D, (int64_t)(uintptr_t)b.Z};
+                                          (int64_t)(uintptr_t)v.D, (int64_t)(uintptr_t)b.Z, c->prm.pcg_pc,
+                                          (int64_t)(uintptr_t)c->sep.pbuf};
         int rc;
         if ((rc = run_graph(c, key, iterate_pcg, &L))) return rc;
         c->pcg_cols_total += (int64_t)w * max_it;
@@ -700,7 +703,7 @@ void ofks_default_params(ofks_params *p) {
     p->pcg_staged = 0;
     p->sweep_pc32 = 1;
     p->method = OFKS_METHOD_PCAL;
-    p->learned_loss = 1; p->learned_retry = 64;
+    p->learned_loss = 1; p->learned_retry = 64; p->pcg_pc = OFKS_PCGPC_JACOBI;
 }
 
 int ofks_create(ofks_ctx **out, int device) {
@@ -802,7 +805,8 @@ int ofks_set_params(ofks_ctx *c, const ofks_params *prm) {
         prm->multipole_lmax < -1 || prm->multipole_lmax > 2 || !(prm->poisson_tol > 0) ||
         prm->poisson_max_iter < 1 || prm->poisson_pc < 0 || prm->poisson_pc > OFKS_HPC_SEPARABLE || (prm->eta_rule == OFKS_ETA_FIXED && !(prm->eta_fixed > 0)) ||
         prm->method < OFKS_METHOD_PCAL || prm->method > OFKS_METHOD_MOPTQR ||
-        prm->learned_loss < 0 || prm->learned_loss > 1 || prm->learned_retry < 0)
+        prm->learned_loss < 0 || prm->learned_loss > 1 || prm->learned_retry < 0 ||
+        prm->pcg_pc < OFKS_PCGPC_JACOBI || prm->pcg_pc > OFKS_PCGPC_SEPARABLE)
         return ofks_fail(c, OFKS_EINVAL, "set_params: a parameter is out of range");
     cudaSetDevice(c->device);
     const bool mixed = prm->precision == OFKS_MIXED;

@@ -650,6 +650,83 @@ __global__ void __launch_bounds__(256) k_pcg_update_s(int64_t ns, int pc, int w,
     cols_out(w, csw, part);                                  // rzn
 }
 
+// The separable preconditioner of the float32 PCG (lattice meshes): R (chunk-major) -> the bf16
+// tensor [k][a][b][c~] of the contractions (free row r = (a ny + b) nz + c; columns k >= pc and
+// padding rows are zero), then after the passes Z <- the tensor (chunk-major) with the column
+// sums rz = R.Z as per-block partials (as k_pcg_update_s writes them).  Items (row, 4-column
+// chunk) as in the other chunk-major kernels.
+__global__ void __launch_bounds__(256) k_psep_gather(int64_t n, int64_t ns, int pc, int w, int nz, int pz,
+                                                     int64_t blk, const float *__restrict__ R, __nv_bfloat16 *t) {
+    const int64_t total = ns * (w >> 2);
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(idx / ns);
+        const int64_t r = idx - (int64_t)q * ns;
+        if (r >= n) continue;
+        const float4 v = *reinterpret_cast<const float4 *>(R + (idx << 2));
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+        const int64_t pos = (r / nz) * pz + r % nz;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = 4 * q + i;
+            t[(int64_t)k * blk + pos] = __float2bfloat16(k < pc ? vv[i] : 0.f);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_psep_scatter(int64_t n, int64_t ns, int pc, int w, int nz, int pz,
+                                                      int64_t blk, const __nv_bfloat16 *__restrict__ t,
+                                                      const float *__restrict__ R, float *Z, double *part) {
+    __shared__ float csw[8][MAXLD];
+    for (int k = threadIdx.x; k < 8 * MAXLD; k += blockDim.x) csw[k / MAXLD][k % MAXLD] = 0.f;
+    __syncthreads();
+    const int64_t total = ns * (w >> 2);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;    // a multiple of 32
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx - (threadIdx.x & 31) < total;
+         idx += stride) {
+        // the warp's first item decides for the whole warp (total is a multiple of 32)
+        const int q = (int)(idx / ns);
+        const int64_t r = idx - (int64_t)q * ns;
+        float zv[4] = {0.f, 0.f, 0.f, 0.f}, acc[4] = {0.f, 0.f, 0.f, 0.f};
+        if (r < n) {
+            const float4 rv = *reinterpret_cast<const float4 *>(R + (idx << 2));
+            const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
+            const int64_t pos = (r / nz) * pz + r % nz;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int k = 4 * q + i;
+                zv[i] = k < pc ? __bfloat162float(t[(int64_t)k * blk + pos]) : 0.f;
+                acc[i] = rr[i] * zv[i];
+            }
+        }
+        if (idx < total) *reinterpret_cast<float4 *>(Z + (idx << 2)) = make_float4(zv[0], zv[1], zv[2], zv[3]);
+        flush_cols(acc, q, csw);
+    }
+    cols_out(w, csw, part);                                  // rz
+}
+
+// the same for row-major PCG blocks of width ld (element type T)
+template <class T>
+__global__ void __launch_bounds__(256) k_psep_gather_n(int64_t n, int ld, int64_t stride, int pc, int nz, int pz,
+                                                       int64_t blk, const T *__restrict__ R, __nv_bfloat16 *t) {
+    ELEM_BEGIN
+        t[(int64_t)j * blk + (r / nz) * pz + r % nz] = __float2bfloat16(j < pc ? (float)R[e] : 0.f);
+    ELEM_END
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_psep_scatter_n(int64_t n, int ld, int64_t stride, int pc, int nz, int pz,
+                                                        int64_t blk, const __nv_bfloat16 *__restrict__ t,
+                                                        const T *__restrict__ R, T *Z, double *part) {
+    T acc = T(0);
+    ELEM_BEGIN
+        const T z = j < pc ? (T)__bfloat162float(t[(int64_t)j * blk + (r / nz) * pz + r % nz]) : T(0);
+        Z[e] = z;
+        acc = fma(R[e], z, acc);
+    ELEM_END
+    col_partial((double)acc, gid < stride, ld, ld, part);      // rz
+}
+
 // D (row-major, pitch ld) from the chunk-major PCG result: column j takes compact column cpos[j]
 // of Dc, G when inactive (cpos[j] = -1: T = I in Eq. precondition-T), and keeps its D when
 // cpos[j] = -2 (a learned direction the judge accepted)
@@ -947,14 +1024,53 @@ void launch_pcg_init(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v, bool warm) 
                 c->n, c->n_slots, v.pc, w, (const float *)b.G[c->cur], (const float *)Qn, (const float *)Dn, c->ld,
                 v.cmap, c->d_dL, c->d_dB, v.cb, (float *)b.W, (float *)v.D, (float *)b.R, (float *)b.Z, (float *)b.P,
                 warm ? nullptr : (float *)b.Q, c->d_cpart);
-            launch_col_fin(c, v.pc, w, grid, c->d_cpart, v.cb + CB_RZ * w);
+            unsigned units = grid;
+            if (c->prm.pcg_pc == OFKS_PCGPC_SEPARABLE && launch_pcg_sep(c, b, v)) units = (unsigned)c->rz_units;
+            launch_col_fin(c, v.pc, w, units, c->d_cpart, v.cb + CB_RZ * w);
             return;
         }
     }
     const ElemGrid g = elem_grid(c->n, w);
     k_pcg_init<T><<<g.blocks, 256, 0, c->stream>>>(c->n, v.pc, w, g.stride, b.G[c->cur], c->ld, v.cmap, Qn, Dn,
                                                    c->d_dL, c->d_dB, v.cb, b.W, v.D, b.R, b.Z, c->d_cpart);
-    launch_col_fin(c, v.pc, w, g.blocks, c->d_cpart, v.cb + CB_RZ * w);
+    unsigned units = g.blocks;
+    if (c->prm.pcg_pc == OFKS_PCGPC_SEPARABLE && launch_pcg_sep(c, b, v)) units = (unsigned)c->rz_units;
+    launch_col_fin(c, v.pc, w, units, c->d_cpart, v.cb + CB_RZ * w);
+}
+
+// z = T_sep^-1 r for the float32 PCG's w columns (chunk-major R, Z): the rz partials replace
+// those of the Jacobi step (rz_units = this grid); false when the form does not apply (not a
+// lattice mesh with the tensor-core separable operator, or not the chunk-major float32 blocks)
+template <class T>
+bool launch_pcg_sep(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v) {
+    const int w = v.w;
+    if (!sep_pcg_ready(c, w)) return false;
+    const SepState &S = c->sep;
+    const int nx = S.n[0], ny = S.n[1], nz = S.n[2], pz = (nz + 15) / 16 * 16;
+    if ((int64_t)nx * ny * nz != c->n) return false;
+    const int64_t blk = (int64_t)nx * ny * pz;
+    __nv_bfloat16 *t = S.pbuf + S.poff[0];
+    if constexpr (sizeof(T) == 4) {
+        if (pcg_zc<T>(c, w)) {
+            const int64_t total = c->n_slots * (w >> 2);
+            const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8);
+            k_psep_gather<<<grid, 256, 0, c->stream>>>(c->n, c->n_slots, v.pc, w, nz, pz, blk, (const float *)b.R, t);
+            sep_pcg_passes(c, w, v.cb + CB_SHIFT * w);
+            k_psep_scatter<<<grid, 256, 0, c->stream>>>(c->n, c->n_slots, v.pc, w, nz, pz, blk, t,
+                                                        (const float *)b.R, (float *)b.Z, c->d_cpart);
+            c->rz_units = grid;
+            c->kernels += 2;
+            return true;
+        }
+    }
+    const ElemGrid g = elem_grid(c->n, w);
+    k_psep_gather_n<T><<<g.blocks, 256, 0, c->stream>>>(c->n, w, g.stride, v.pc, nz, pz, blk, b.R, t);
+    sep_pcg_passes(c, w, v.cb + CB_SHIFT * w);
+    k_psep_scatter_n<T><<<g.blocks, 256, 0, c->stream>>>(c->n, w, g.stride, v.pc, nz, pz, blk, t, b.R, b.Z,
+                                                         c->d_cpart);
+    c->rz_units = g.blocks;
+    c->kernels += 2;
+    return true;
 }
 
 template <class T>
@@ -1126,6 +1242,7 @@ void launch_convert(ofks_ctx *c, const S *src, T *dst, int64_t count) {
     template void launch_pcg_update<T>(ofks_ctx *, Blocks<T> &, const PcgView<T> &, bool);           \
     template void launch_direction_expand<T>(ofks_ctx *, Blocks<T> &, const PcgView<T> &);           \
     template void launch_judge<T>(ofks_ctx *, Blocks<T> &);                                          \
+    template bool launch_pcg_sep<T>(ofks_ctx *, Blocks<T> &, const PcgView<T> &);                    \
     template void launch_direction_select<T>(ofks_ctx *, Blocks<T> &);                               \
     template void launch_bb_dots<T>(ofks_ctx *, Blocks<T> &, bool);                                  \
     template void launch_step_y<T>(ofks_ctx *, Blocks<T> &, T *);                                    \

@@ -115,6 +115,9 @@ struct SepState {
     __nv_bfloat16 *hS[3] = {nullptr, nullptr, nullptr}, *hSt[3] = {nullptr, nullptr, nullptr};  // bf16, padded
     __nv_bfloat16 *hbuf = nullptr;               // six padded bf16 tensors (input, intermediates)
     int64_t hoff[6] = {0, 0, 0, 0, 0, 0};
+    __nv_bfloat16 *pbuf = nullptr;               // the same six tensors for pw PCG columns
+    int64_t poff[6] = {0, 0, 0, 0, 0, 0};
+    int pw = 0;
 };
 
 struct ofks_ctx {
@@ -293,6 +296,8 @@ void launch_stencil_jacobi(ofks_ctx *c, const double *x, const double *b, double
 int sep_setup(ofks_ctx *c, const double *xyz, const uint8_t *dirichlet);
 void sep_cg_step(ofks_ctx *c, int it, int slot, int first);    // fused CG update + z = A_sep^-1 r + r.z
 void sep_free(ofks_ctx *c);
+bool sep_pcg_ready(ofks_ctx *c, int w);                        // separable PCG buffers for width w
+void sep_pcg_passes(ofks_ctx *c, int w, const double *shift);  // z = T_sep^-1 r on the PCG tensor
 
 // ---- fields.cu (density, potentials, Hamiltonian refresh, Poisson)
 int hartree_pc(ofks_ctx *c);                    // OFKS_HPC_* the next Hartree solve uses (builds the
@@ -344,6 +349,9 @@ template <class T> void launch_pcg_init(ofks_ctx *c, Blocks<T> &b, const PcgView
 // last: the final iteration, after which only D is read
 template <class T> void launch_pcg_update(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v, bool last);
 template <class T> void launch_judge(ofks_ctx *c, Blocks<T> &b);
+// Z = T_sep^-1 R (separable preconditioner of the PCG, float32 chunk-major blocks on lattice
+// meshes) with the rz partials; false when that form does not apply
+template <class T> bool launch_pcg_sep(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v);
 template <class T> void launch_direction_select(ofks_ctx *c, Blocks<T> &b);
 // D = the compact PCG result on the active columns, G on the others
 template <class T> void launch_direction_expand(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v);

@@ -268,7 +268,13 @@ struct SepPass {
     int NS;                        // output columns per CTA (NP / gridDim.y, a multiple of 16)
     __nv_bfloat16 *out;            // element (n, m) at (n M1 + m / M2) KPo + m % M2
     int M1, M2, KPo;
-    const float *lr, *lc;          // SCALE: multiply by 1 / (lr[n] + lc[m])
+    const float *lr, *lc;          // SCALE: multiply by f / (lr[n] + lc[m] + h_b)
+    // batches of Mb rows (Mb = 0: one batch of M): row m is row m' = m mod Mb of batch
+    // b = m / Mb, whose output starts at b * ob; in the scaling h_b = -2 shd[b] (shd null: 0)
+    int Mb;
+    int64_t ob;
+    const double *shd;
+    float f;
     int *err;
 };
 
@@ -340,8 +346,10 @@ __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
     if (!abort_flag) {
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int m = m0 + warp * 32 + lane;
-        const int m1 = m / P.M2, m2 = m - m1 * P.M2;
-        const float lcm = (SCALE && m < P.M) ? P.lc[m] : 0.f;
+        const int bt = P.Mb ? m / P.Mb : 0, mm = m - bt * P.Mb;
+        const int m1 = mm / P.M2, m2 = mm - m1 * P.M2;
+        const float lcm = (SCALE && m < P.M) ? P.lc[mm] + (P.shd ? (float)(-2.0 * P.shd[bt]) : 0.f) : 0.f;
+        __nv_bfloat16 *outb = P.out + (int64_t)bt * P.ob;
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
         for (int cb = 0; cb < P.NS; cb += 16) {
             uint32_t v[16];
@@ -358,8 +366,8 @@ __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
                 const int n = n0 + cb + q;
                 if (n >= P.N) break;
                 float x = __uint_as_float(v[q]);
-                if (SCALE) x = __fdividef(x, P.lr[n] + lcm);
-                P.out[((int64_t)n * P.M1 + m1) * P.KPo + m2] = __float2bfloat16(x);
+                if (SCALE) x = __fdividef(P.f * x, P.lr[n] + lcm);
+                outb[((int64_t)n * P.M1 + m1) * P.KPo + m2] = __float2bfloat16(x);
             }
         }
     }
@@ -402,7 +410,7 @@ void sep_free(ofks_ctx *c) {
     for (float *p : {S.S[0], S.S[1], S.S[2], S.St[0], S.St[1], S.St[2], S.lx, S.lyz, S.t0, S.t1})
         if (p) cudaFree(p);
     for (void *p : {(void *)S.hS[0], (void *)S.hS[1], (void *)S.hS[2], (void *)S.hSt[0], (void *)S.hSt[1],
-                    (void *)S.hSt[2], (void *)S.hbuf})
+                    (void *)S.hSt[2], (void *)S.hbuf, (void *)S.pbuf})
         if (p) cudaFree(p);
     S = SepState{};
 }
@@ -508,6 +516,7 @@ void sep_cg_step(ofks_ctx *c, int it, int slot, int first) {
         __nv_bfloat16 *B[6];
         for (int q = 0; q < 6; ++q) B[q] = S.hbuf + S.hoff[q];
         SepPass P{};
+        P.f = 1.f;
         auto pass = [&](const __nv_bfloat16 *A, const __nv_bfloat16 *Bt, int M, int K, int N, __nv_bfloat16 *out,
                         int M1, int M2, int KPo) {
             P.A = A; P.Bt = Bt; P.M = M; P.K = K; P.KP = pad16(K); P.N = N; P.NP = pad16(N);
@@ -552,4 +561,66 @@ void sep_cg_step(ofks_ctx *c, int it, int slot, int first) {
     k_sep_scatter<float><<<g, 256, 0, c->stream>>>(nx, ny, nz, nz, c->st.Ly, c->st.Lz, S.t0, c->d_cr, c->d_cz,
                                                    first ? c->d_cp : nullptr, sc, slot, c->d_gpart, c->d_gcount);
     c->kernels += 2;
+}
+
+// ---- the PCG of Eq. (precondition-T) preconditioned by the separable operator
+//
+// T_k = L/2 - shift_k B is approximated, like the Hartree stiffness above, by
+//     T_sep,k = A_sep / 2 - shift_k B_sep,   B_sep = Mx (x) My (x) Mz,
+// which the same modes diagonalize (S^T A_sep S = diag(lam), S^T B_sep S = I):
+//     T_sep,k^-1 = S diag(2 / (lam_x,i + lam_y,j + lam_z,k - 2 shift_k)) S^T.
+// The w columns of a PCG block go through the six contractions at once: column b's tensors are
+// consecutive blocks, so each pass is one GEMM over w times the rows (batches of Mb rows, the
+// output of batch b at b * ob), and the scaling adds -2 shift_b of its batch.  Six bf16 tensors
+// per column, zero-initialized, padding never written (as for the Hartree solve).
+
+// buffers for PCG blocks of width w (kept for smaller w); false when the form does not apply
+bool sep_pcg_ready(ofks_ctx *c, int w) {
+    SepState &S = c->sep;
+    if (!S.on || !S.tc) return false;
+    if (S.pbuf && S.pw >= w) return true;
+    if (S.pbuf) cudaFree(S.pbuf);
+    S.pbuf = nullptr;
+    S.pw = 0;
+    const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
+    const int64_t len[6] = {(int64_t)nx * ny * pad16(nz), (int64_t)nz * nx * pad16(ny), (int64_t)ny * nz * pad16(nx),
+                            (int64_t)nx * ny * pad16(nz), (int64_t)nz * nx * pad16(ny), (int64_t)ny * nz * pad16(nx)};
+    int64_t tot = 0;
+    for (int q = 0; q < 6; ++q) { S.poff[q] = tot; tot += (len[q] * w + 63) / 64 * 64; }
+    if (cudaMalloc((void **)&S.pbuf, sizeof(__nv_bfloat16) * tot) != cudaSuccess) { S.pbuf = nullptr; return false; }
+    if (cudaMemset(S.pbuf, 0, sizeof(__nv_bfloat16) * tot) != cudaSuccess) return false;
+    S.pw = w;
+    return true;
+}
+
+// z = T_sep^-1 r for the w columns in the input tensor (buffer 0, [b][a][b][c~]), result in the
+// same buffer; shift: the PCG's per-column shifts (w doubles)
+void sep_pcg_passes(ofks_ctx *c, int w, const double *shift) {
+    SepState &S = c->sep;
+    const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
+    const int px = pad16(nx), py = pad16(ny), pz = pad16(nz);
+    __nv_bfloat16 *B[6];
+    for (int q = 0; q < 6; ++q) B[q] = S.pbuf + S.poff[q];
+    SepPass P{};
+    P.f = 1.f;
+    auto pass = [&](const __nv_bfloat16 *A, const __nv_bfloat16 *Bt, int Mb, int K, int N, __nv_bfloat16 *out,
+                    int M1, int M2, int KPo) {
+        P.A = A; P.Bt = Bt; P.M = w * Mb; P.K = K; P.KP = pad16(K); P.N = N; P.NP = pad16(N);
+        P.out = out; P.M1 = M1; P.M2 = M2; P.KPo = KPo;
+        P.Mb = Mb; P.ob = (int64_t)N * M1 * KPo;
+    };
+    pass(B[0], S.hSt[2], nx * ny, nz, nz, B[1], nx, ny, py);           // [a][b][c] -> [k][a][b]
+    sep_tc_launch<0>(c, P);
+    pass(B[1], S.hSt[1], nz * nx, ny, ny, B[2], nz, nx, px);           // -> [j][k][a]
+    sep_tc_launch<0>(c, P);
+    pass(B[2], S.hSt[0], ny * nz, nx, nx, B[3], ny, nz, pz);           // -> [i][j][k] scaled
+    P.lr = S.lx; P.lc = S.lyz; P.shd = shift; P.f = 2.f;
+    sep_tc_launch<1>(c, P);
+    P.shd = nullptr; P.f = 1.f;
+    pass(B[3], S.hS[2], nx * ny, nz, nz, B[4], nx, ny, py);            // -> [c][i][j]
+    sep_tc_launch<0>(c, P);
+    pass(B[4], S.hS[1], nz * nx, ny, ny, B[5], nz, nx, px);            // -> [b][c][i]
+    sep_tc_launch<0>(c, P);
+    pass(B[5], S.hS[0], ny * nz, nx, nx, B[0], ny, nz, pz);            // -> [a][b][c]
+    sep_tc_launch<0>(c, P);
 }

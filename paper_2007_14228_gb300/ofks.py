@@ -23,6 +23,7 @@ HPC_NAMES = {v: k for k, v in HPC.items()}
 FIELDS = {"rho_q": 0, "vh_q": 1, "vxc_q": 2, "exc_q": 3, "U": 4, "HX": 5, "BX": 6, "G": 7, "D": 8,
           "Lambda0": 9, "S": 10, "Lambda": 11, "vext_q": 12}
 MATS = {"L": 0, "B": 1, "H": 2}
+PCGPC = {"jacobi": 0, "separable": 1}
 STATIC_NUCLEI_MAX = 1024          # OFKS_STATIC_NUCLEI_MAX
 SYMBOLS = ("ofks_default_params", "ofks_create", "ofks_destroy", "ofks_last_error", "ofks_set_mesh",
            "ofks_set_nuclei", "ofks_set_nuclei_static", "ofks_set_params", "ofks_init_orbitals", "ofks_set_orbitals",
@@ -51,7 +52,7 @@ class Params(C.Structure):
                 ("gram_tc", C.c_int32), ("spmm_f32_rows", C.c_int32), ("poisson_sep_tc", C.c_int32),
                 ("pcg_compact", C.c_int32), ("cuda_graphs", C.c_int32), ("pcg_staged", C.c_int32),
                 ("sweep_pc32", C.c_int32), ("method", C.c_int32), ("learned_loss", C.c_int32),
-                ("learned_retry", C.c_int32)]
+                ("learned_retry", C.c_int32), ("pcg_pc", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -148,6 +149,8 @@ def updated_params(base: Params, **overrides) -> Params:
             v = HPC[v]
         if k == "method" and isinstance(v, str):
             v = METHOD[v]
+        if k == "pcg_pc" and isinstance(v, str):
+            v = PCGPC[v]
         if isinstance(v, bool):
             v = int(v)
         setattr(prm, k, v)

@@ -71,15 +71,19 @@ def config_of(args, s, sizes):
             "beta": 10.0,
             "form": ("learned-preconditioner mixed form: float32 iterations with the graph network (bf16 weights, "
                      "float32 activations) in place of the PCG; each column judged by its residual in the PCG's "
-                     "M^-1 norm: accepted, or PCG x8 from the network's direction (residual below that of zero) "
+                     "M^-1 norm: accepted, or the PCG from the network's direction (residual below that of zero) "
                      "or from zero; the network pauses 1, 2, 4, .. 64 calls after calls in which the judge took "
                      "none of its directions; float64 p x p / energy / tests; plain float64 and mixed + PCG beside it"),
-            "precond": "learned (width 64, committed weights, energy-norm loss), PCG x8 fallback (Eq. precondition-T)",
+            "precond": (f"learned (width 64, committed weights, energy-norm loss), PCG x{args.extra['pcg_iters']} "
+                        f"fallback (Eq. precondition-T) with the "
+                        f"{'separable (fast diagonalization)' if args.extra['pcg_pc'] else 'Jacobi'} "
+                        f"preconditioner inside, the same PCG in every form"),
             "eta": "BB2",
             "hartree": ("CG on the lattice-stencil stiffness, separable (fast-diagonalization) preconditioner, "
                         "tolerance max(1e-12, min(1e-4, 0.01 (kkt+fea)/kkt0)) in both forms"),
             "l2": "inputs larger than L2 (working set ~7 GB)", "parallelism": f"replicas x{args.gpus}",
-            "start": f"iterate {args.start} of the seeded run (prepared untimed)"}
+            "start": f"iterate {args.start} of the seeded run (prepared untimed)",
+            **({"params": args.extra} if getattr(args, "extra", None) else {})}
 
 
 class Clocks:
@@ -185,12 +189,13 @@ def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, spmv_model=(0, 0), ele
     """Dominant kernel family by time: algorithmic bytes and flops per launch / mean duration.
 
     Every family is one kernel launch per timed scope except "poisson" (the whole Hartree
-    solve), "poisson_vec" (two vector kernels per CG iteration) and "gcn" (one application of the
-    learned preconditioner's network, a dozen kernels), which are left out of the choice; the
-    solve's SpMV kernel is the "poisson_spmv" family.  The PCG apply works on the
+    solve), "poisson_vec" (two vector kernels per CG iteration), "gcn" (one application of the
+    learned preconditioner's network, a dozen kernels) and "pcg_sep" (one application of the
+    PCG's separable preconditioner: gather, six tensor-core contractions, scatter), which are left
+    out of the choice; the solve's SpMV kernel is the "poisson_spmv" family.  The PCG apply works on the
     active columns only (their count rounded up to 4): pcg_w is its mean block width over the
     timed launches."""
-    leaves = {k: v for k, v in prof.items() if k not in ("poisson", "poisson_vec", "gcn") and v["launches"]}
+    leaves = {k: v for k, v in prof.items() if k not in ("poisson", "poisson_vec", "gcn", "pcg_sep") and v["launches"]}
     fam = max(leaves, key=lambda k: leaves[k]["ms"])
     st = prof[fam]
     per = st["ms"] / max(st["launches"], 1) * 1e-3
@@ -320,7 +325,7 @@ def run_form(ofks, s, m, V, budget_s, chunk=100, E_star=None, tol=1e-10, learned
             "learned_calls": r["learned_calls"] if r else 0, "learned_warm": r["learned_warm"] if r else 0}
 
 
-def time_to_target(ofks, I, system, budgets, chunk=100, forms=("fp64", "mixed", "learned")):
+def time_to_target(ofks, I, system, budgets, chunk=100, forms=("fp64", "mixed", "learned"), extra=None):
     """Wall time from the initial guess to the first iterate with |E - E*| <= 1e-6 Ha and
     fea <= 1e-7 (seconds since ofks_init_orbitals, as the library's history records them), for the
     plain float64 form, the mixed form with the paper's PCG and the mixed form with the learned
@@ -330,7 +335,8 @@ def time_to_target(ofks, I, system, budgets, chunk=100, forms=("fp64", "mixed", 
     seconds = None with the iterations and time it ran and its last |E - E*|."""
     m = I.make_mesh(system)
     V = I.initial_block(m.n_free, system.p, 0)
-    ref = run_form(ofks, system, m, V, budgets["mixed"], chunk, None, 1e-10, precision="mixed")
+    extra = extra or {}
+    ref = run_form(ofks, system, m, V, budgets["mixed"], chunk, None, 1e-10, precision="mixed", **extra)
     out = {"workload": f"{system.name}: {len(system.Z)} nuclei, {'x'.join(map(str, system.cells))} cells, "
                        f"n = {m.n_free}, p = {system.p}",
            "target": "|E - E*| <= 1e-6 Ha and fea <= 1e-7", "E_star_from": "mixed form to tol 1e-10",
@@ -353,7 +359,7 @@ def time_to_target(ofks, I, system, budgets, chunk=100, forms=("fp64", "mixed", 
         if form == "mixed":
             continue
         rec = run_form(ofks, system, m, V, budgets[form], chunk, E_star, 1e-12,
-                       learned=(form == "learned"), precision="fp64" if form == "fp64" else "mixed")
+                       learned=(form == "learned"), precision="fp64" if form == "fp64" else "mixed", **extra)
         out[form] = {k: rec[k] for k in ("seconds", "iters", "ran_iters", "ran_seconds")}
         out[form]["dE_last"] = abs(rec["E_last"] - E_star)
         if form == "learned":
@@ -449,8 +455,15 @@ def main():
                     help="state file of the start iterate: loaded if it exists, else written (profiling runs)")
     ap.add_argument("--params", default="",
                     help="extra ofks_params for every context, e.g. spmm_f32_rows=1,gram_tc=0 (profiling runs)")
+    ap.add_argument("--pcg", default="separable:4",
+                    help="the PCG of Eq. precondition-T in every form: 'separable:K' (the separable "
+                         "preconditioner inside, K iterations; default K = 4) or 'jacobi:K' (the diagonal, "
+                         "the paper's reading with K = 8)")
     args = ap.parse_args()
-    args.extra = {}
+    kind, _, its = args.pcg.partition(":")
+    if kind not in ("separable", "jacobi"):
+        raise SystemExit(f"--pcg {args.pcg}: separable:K or jacobi:K")
+    args.extra = {"pcg_pc": 1 if kind == "separable" else 0, "pcg_iters": int(its or (4 if kind == "separable" else 8))}
     for kv in filter(None, args.params.split(",")):
         k, v = kv.split("=")
         args.extra[k] = float(v) if "." in v or "e" in v else int(v)
@@ -599,8 +612,12 @@ def main():
     ttc = None
     if not args.no_ttc:
         budgets = {"mixed": args.ttt_budget[0], "fp64": args.ttt_budget[1], "learned": args.ttt_budget[2]}
-        ttc = {"chain": time_to_target(ofks, I, s, budgets, chunk=100) if args.workload == "chain" else None,
-               "lih": time_to_target(ofks, I, I.lih(), {"mixed": 60, "fp64": 60, "learned": 60}, chunk=100)}
+        ttc = {"chain": time_to_target(ofks, I, s, budgets, chunk=100, extra=args.extra)
+                        if args.workload == "chain" else None,
+               "lih": time_to_target(ofks, I, I.lih(), {"mixed": 60, "fp64": 60, "learned": 60}, chunk=100,
+                                     extra=args.extra)}
+        if args.extra:
+            ttc["params"] = args.extra
     methods = None
     if not args.no_ttc:
         try:

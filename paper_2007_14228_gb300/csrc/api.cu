@@ -22,7 +22,7 @@
 
 static const char *kPfNames[PF_COUNT] = {"density", "poisson", "potential", "spmm_h", "gram", "small",
                                          "grad", "pcg_spmm", "pcg_update", "bb", "step", "spmm_b", "other",
-                                         "poisson_spmv", "gcn", "poisson_vec", "poisson_pc"};
+                                         "poisson_spmv", "gcn", "poisson_vec", "poisson_pc", "pcg_sep"};
 
 int ofks_fail(ofks_ctx *c, int code, const char *fmt, ...) {
     char buf[512];
@@ -463,10 +463,17 @@ static int precondition_t(ofks_ctx *c) {
             warm = nwarm > 0;
         }
     }
+    const bool sep = c->prm.pcg_pc == OFKS_PCGPC_SEPARABLE;
     if (run_pcg) {
-        ProfScope ps(c, PF_PCG_UPDATE);
-        launch_pcg_init(c, b, v, warm);
-        cudaMemsetAsync(v.cb + CB_PQ * v.w, 0, sizeof(double) * v.w, c->stream);
+        {
+            ProfScope ps(c, PF_PCG_UPDATE);
+            launch_pcg_init(c, b, v, warm);
+            cudaMemsetAsync(v.cb + CB_PQ * v.w, 0, sizeof(double) * v.w, c->stream);
+        }
+        if (sep) {     // Z = T_sep^-1 R replaces the Jacobi start's Z and r.z
+            ProfScope ps(c, PF_PCG_SEP);
+            if (launch_pcg_sep(c, b, v)) launch_col_fin(c, v.pc, v.w, c->rz_units, c->d_cpart, v.cb + CB_RZ * v.w);
+        }
     }
     const bool exact = c->prm.precond == OFKS_PC_EXACT;
     const int max_it = !run_pcg ? 0 : exact ? 5000 : c->prm.pcg_iters;
@@ -492,12 +499,18 @@ static int precondition_t(ofks_ctx *c) {
                 launch_pcg_apply(c, vals_L<T>(c), vals_B<T>(c), (const T *)b.Z, pcg_zc<T>(c, w) ? 1 : 0, b.P, b.Q,
                                  v.cb + CB_BETA * w, v.cb + CB_SHIFT * w, v.cb + CB_PQ * w, it == 0 ? 1 : 0, w, v.pc);
             }
+            const bool last = !L.exact && it + 1 == L.max_it;
             {
                 ProfScope ps(c, PF_PCG_UPDATE);
-                const bool last = !L.exact && it + 1 == L.max_it;
                 launch_pcg_alpha(c, w, v.pc, v.cb);
                 launch_pcg_update(c, b, v, last);
-                if (!last && c->prm.pcg_pc == OFKS_PCGPC_SEPARABLE) launch_pcg_sep(c, b, v);
+            }
+            if (!last && c->prm.pcg_pc == OFKS_PCGPC_SEPARABLE) {
+                ProfScope ps(c, PF_PCG_SEP);
+                launch_pcg_sep(c, b, v);          // Z and r.z of the separable preconditioner
+            }
+            {
+                ProfScope ps(c, PF_PCG_UPDATE);
                 launch_pcg_beta(c, w, v.pc, v.cb);
             }
         }

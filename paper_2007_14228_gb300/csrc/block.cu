@@ -1024,18 +1024,14 @@ void launch_pcg_init(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v, bool warm) 
                 c->n, c->n_slots, v.pc, w, (const float *)b.G[c->cur], (const float *)Qn, (const float *)Dn, c->ld,
                 v.cmap, c->d_dL, c->d_dB, v.cb, (float *)b.W, (float *)v.D, (float *)b.R, (float *)b.Z, (float *)b.P,
                 warm ? nullptr : (float *)b.Q, c->d_cpart);
-            unsigned units = grid;
-            if (c->prm.pcg_pc == OFKS_PCGPC_SEPARABLE && launch_pcg_sep(c, b, v)) units = (unsigned)c->rz_units;
-            launch_col_fin(c, v.pc, w, units, c->d_cpart, v.cb + CB_RZ * w);
+            launch_col_fin(c, v.pc, w, grid, c->d_cpart, v.cb + CB_RZ * w);
             return;
         }
     }
     const ElemGrid g = elem_grid(c->n, w);
     k_pcg_init<T><<<g.blocks, 256, 0, c->stream>>>(c->n, v.pc, w, g.stride, b.G[c->cur], c->ld, v.cmap, Qn, Dn,
                                                    c->d_dL, c->d_dB, v.cb, b.W, v.D, b.R, b.Z, c->d_cpart);
-    unsigned units = g.blocks;
-    if (c->prm.pcg_pc == OFKS_PCGPC_SEPARABLE && launch_pcg_sep(c, b, v)) units = (unsigned)c->rz_units;
-    launch_col_fin(c, v.pc, w, units, c->d_cpart, v.cb + CB_RZ * w);
+    launch_col_fin(c, v.pc, w, g.blocks, c->d_cpart, v.cb + CB_RZ * w);
 }
 
 // z = T_sep^-1 r for the float32 PCG's w columns (chunk-major R, Z): the rz partials replace

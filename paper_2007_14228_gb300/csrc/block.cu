@@ -571,48 +571,59 @@ __global__ void __launch_bounds__(256) k_pcg_init_s(int64_t n, int64_t ns, int p
                                                     const float *__restrict__ Dn, int ld, const int *__restrict__ cmap,
                                                     const double *__restrict__ dL, const double *__restrict__ dB,
                                                     const double *__restrict__ cb, float *W, float *D, float *R,
-                                                    float *Z, float *P, float *Q, double *part) {
+                                                    float *Z, float *P, float *Q, double *part, int jac) {
     __shared__ float csw[8][MAXLD];
+    __shared__ int scol[MAXLD];
+    __shared__ float ssh[MAXLD];
+    __shared__ unsigned char swarm[MAXLD];
     for (int k = threadIdx.x; k < 8 * MAXLD; k += blockDim.x) csw[k / MAXLD][k % MAXLD] = 0.f;
+    for (int k = threadIdx.x; k < w; k += blockDim.x) {
+        scol[k] = k < pc ? cmap[k] : -1;
+        ssh[k] = (float)cb[CB_SHIFT * w + k];
+        swarm[k] = (Qn && cb[CB_WARM * w + k] != 0.0) ? 1 : 0;
+    }
     __syncthreads();
-    const int64_t total = ns * (w >> 2);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;    // a multiple of 32
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx - (threadIdx.x & 31) < total;
-         idx += stride) {
-        // the warp's first item decides for the whole warp (total is a multiple of 32)
-        const int q = (int)(idx / ns);
-        const int64_t r = idx - (int64_t)q * ns;
-        const int64_t nat = r < n ? r : -1;
-        float wv[4], rv[4], zv[4], dv[4], acc[4];
+    // one row per item, all its chunks in turn: the row of G (and of Q, D when warm) is read once
+    // and the chunk-major writes of one chunk stay contiguous across the warp
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r - (threadIdx.x & 31) < ns; r += stride) {
+        const bool real = r < n;
+        const float dl = real ? 0.5f * (float)dL[r] : 0.f, db = real ? (float)dB[r] : 0.f;
+        for (int q = 0; q < (w >> 2); ++q) {
+            float wv[4], rv[4], zv[4], dv[4], acc[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int k = 4 * q + i;
-            const int col = k < pc ? cmap[k] : -1;
-            float g = 0.f, d = 0.f, ww = 0.f;
-            if (nat >= 0) {
-                const float sh = (float)cb[CB_SHIFT * w + k];
-                ww = 1.f / (0.5f * (float)dL[nat] - sh * (float)dB[nat]);
-                if (col >= 0) {
-                    const int64_t e = nat * ld + col;
-                    g = G[e];
-                    if (Qn && cb[CB_WARM * w + k] != 0.0) { g -= Qn[e]; d = Dn[e]; }
+            for (int i = 0; i < 4; ++i) {
+                const int k = 4 * q + i;
+                const int col = scol[k];
+                float g = 0.f, d = 0.f, ww = 0.f;
+                if (real) {
+                    if (jac) ww = 1.f / (dl - ssh[k] * db);
+                    if (col >= 0) {
+                        const int64_t e = r * ld + col;
+                        g = G[e];
+                        if (swarm[k]) { g -= Qn[e]; d = Dn[e]; }
+                    }
+                }
+                wv[i] = ww; rv[i] = g; zv[i] = g * ww; dv[i] = d;
+                acc[i] = g * zv[i];
+            }
+            if (r < ns) {
+                const int64_t o = (q * ns + r) << 2;           // sidx(r, 4 q, ns)
+                *reinterpret_cast<float4 *>(R + o) = make_float4(rv[0], rv[1], rv[2], rv[3]);
+                *reinterpret_cast<float4 *>(D + o) = make_float4(dv[0], dv[1], dv[2], dv[3]);
+                if (jac) {
+                    *reinterpret_cast<float4 *>(W + o) = make_float4(wv[0], wv[1], wv[2], wv[3]);
+                    *reinterpret_cast<float4 *>(Z + o) = make_float4(zv[0], zv[1], zv[2], zv[3]);
+                }
+                if (!real) {                                 // padding rows: the apply never writes their P, Q
+                    *reinterpret_cast<float4 *>(P + o) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (Q) *reinterpret_cast<float4 *>(Q + o) = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
-            wv[i] = ww; rv[i] = g; zv[i] = g * ww; dv[i] = d;
-            acc[i] = g * zv[i];
+            if (jac) flush_cols(acc, q, csw);
         }
-        const int64_t o = idx << 2;                  // sidx(r, 4 q, ns)
-        *reinterpret_cast<float4 *>(W + o) = make_float4(wv[0], wv[1], wv[2], wv[3]);
-        *reinterpret_cast<float4 *>(R + o) = make_float4(rv[0], rv[1], rv[2], rv[3]);
-        *reinterpret_cast<float4 *>(Z + o) = make_float4(zv[0], zv[1], zv[2], zv[3]);
-        *reinterpret_cast<float4 *>(D + o) = make_float4(dv[0], dv[1], dv[2], dv[3]);
-        if (nat < 0) {                               // padding rows: the apply never writes their P, Q
-            *reinterpret_cast<float4 *>(P + o) = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (Q) *reinterpret_cast<float4 *>(Q + o) = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        flush_cols(acc, q, csw);
     }
-    cols_out(w, csw, part);                                  // rz
+    if (jac) cols_out(w, csw, part);                         // rz
 }
 
 // alpha = rz/pq; D += alpha P; R -= alpha Q; Z = R W; rzn += R Z, per float4 of one row and
@@ -620,7 +631,7 @@ __global__ void __launch_bounds__(256) k_pcg_init_s(int64_t n, int64_t ns, int p
 __global__ void __launch_bounds__(256) k_pcg_update_s(int64_t ns, int pc, int w, const double *__restrict__ cb,
                                                       const float *__restrict__ W, const float *__restrict__ P,
                                                       const float *__restrict__ Q, float *D, float *R, float *Z,
-                                                      double *part, int last) {
+                                                      double *part, int last, int jac) {
     __shared__ float csw[8][MAXLD], al[MAXLD];
     for (int k = threadIdx.x; k < 8 * MAXLD; k += blockDim.x) csw[k / MAXLD][k % MAXLD] = 0.f;
     for (int k = threadIdx.x; k < w; k += blockDim.x) al[k] = (float)cb[CB_ALPHA * w + k];
@@ -637,16 +648,18 @@ __global__ void __launch_bounds__(256) k_pcg_update_s(int64_t ns, int pc, int w,
         d4.x = fmaf(a0, p4.x, d4.x); d4.y = fmaf(a1, p4.y, d4.y); d4.z = fmaf(a2, p4.z, d4.z); d4.w = fmaf(a3, p4.w, d4.w);
         *reinterpret_cast<float4 *>(D + o) = d4;
         if (last) continue;
-        const float4 q4 = *reinterpret_cast<const float4 *>(Q + o), w4 = *reinterpret_cast<const float4 *>(W + o);
+        const float4 q4 = *reinterpret_cast<const float4 *>(Q + o);
         float4 r4 = *reinterpret_cast<const float4 *>(R + o);
         r4.x = fmaf(-a0, q4.x, r4.x); r4.y = fmaf(-a1, q4.y, r4.y); r4.z = fmaf(-a2, q4.z, r4.z); r4.w = fmaf(-a3, q4.w, r4.w);
-        const float4 z4 = make_float4(r4.x * w4.x, r4.y * w4.y, r4.z * w4.z, r4.w * w4.w);
         *reinterpret_cast<float4 *>(R + o) = r4;
+        if (!jac) continue;                      // Z and r.z come from the separable preconditioner
+        const float4 w4 = *reinterpret_cast<const float4 *>(W + o);
+        const float4 z4 = make_float4(r4.x * w4.x, r4.y * w4.y, r4.z * w4.z, r4.w * w4.w);
         *reinterpret_cast<float4 *>(Z + o) = z4;
         const float acc[4] = {r4.x * z4.x, r4.y * z4.y, r4.z * z4.z, r4.w * z4.w};
         flush_cols(acc, q, csw);
     }
-    if (last) return;
+    if (last || !jac) return;
     cols_out(w, csw, part);                                  // rzn
 }
 
@@ -1020,11 +1033,13 @@ void launch_pcg_init(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v, bool warm) 
             // the padding rows add nothing
             const int64_t total = c->n_slots * (w >> 2);
             const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8);
-            k_pcg_init_s<<<grid, 256, 0, c->stream>>>(
+            const bool jac = !pcg_sep_active(c, w);      // else Z and r.z come from the separable step
+            const unsigned rgrid = (unsigned)std::min<int64_t>((c->n_slots + 255) / 256, 152 * 8);
+            k_pcg_init_s<<<rgrid, 256, 0, c->stream>>>(
                 c->n, c->n_slots, v.pc, w, (const float *)b.G[c->cur], (const float *)Qn, (const float *)Dn, c->ld,
                 v.cmap, c->d_dL, c->d_dB, v.cb, (float *)b.W, (float *)v.D, (float *)b.R, (float *)b.Z, (float *)b.P,
-                warm ? nullptr : (float *)b.Q, c->d_cpart);
-            launch_col_fin(c, v.pc, w, grid, c->d_cpart, v.cb + CB_RZ * w);
+                warm ? nullptr : (float *)b.Q, c->d_cpart, jac ? 1 : 0);
+            if (jac) launch_col_fin(c, v.pc, w, rgrid, c->d_cpart, v.cb + CB_RZ * w);
             return;
         }
     }
@@ -1037,13 +1052,20 @@ void launch_pcg_init(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v, bool warm) 
 // z = T_sep^-1 r for the float32 PCG's w columns (chunk-major R, Z): the rz partials replace
 // those of the Jacobi step (rz_units = this grid); false when the form does not apply (not a
 // lattice mesh with the tensor-core separable operator, or not the chunk-major float32 blocks)
+// the PCG of width w runs with the separable preconditioner (its buffers are allocated here,
+// outside any graph capture, by the PCG start)
+bool pcg_sep_active(ofks_ctx *c, int w) {
+    if (c->prm.pcg_pc != OFKS_PCGPC_SEPARABLE || !sep_pcg_ready(c, w)) return false;
+    const SepState &S = c->sep;
+    return (int64_t)S.n[0] * S.n[1] * S.n[2] == c->n;
+}
+
 template <class T>
 bool launch_pcg_sep(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v) {
     const int w = v.w;
-    if (!sep_pcg_ready(c, w)) return false;
+    if (!pcg_sep_active(c, w)) return false;
     const SepState &S = c->sep;
     const int nx = S.n[0], ny = S.n[1], nz = S.n[2], pz = (nz + 15) / 16 * 16;
-    if ((int64_t)nx * ny * nz != c->n) return false;
     const int64_t blk = (int64_t)nx * ny * pz;
     __nv_bfloat16 *t = S.pbuf + S.poff[0];
     if constexpr (sizeof(T) == 4) {
@@ -1096,7 +1118,7 @@ void launch_pcg_update(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v, bool last
             const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8);
             k_pcg_update_s<<<grid, 256, 0, c->stream>>>(
                 c->n_slots, v.pc, w, cb, (const float *)b.W, (const float *)b.P, (const float *)b.Q, (float *)v.D,
-                (float *)b.R, (float *)b.Z, c->d_cpart, last ? 1 : 0);
+                (float *)b.R, (float *)b.Z, c->d_cpart, last ? 1 : 0, pcg_sep_active(c, w) ? 0 : 1);
             c->rz_units = grid;
             return;
         }

@@ -121,6 +121,23 @@ struct SepState {
     int pw = 0;
 };
 
+// Stencil form of L and B on the free nodes of a lattice mesh whose Dirichlet nodes are the
+// lattice's faces (pcg_stencil.cu): node type t = parity triple of the lattice coordinates
+// (bits a b c), the type's K[t] neighbour offsets in [-2, 2]^3, and per type and offset one
+// float32 array over the type's interior sub-lattice (zero where the neighbour is not free)
+constexpr int PS_KMAX = 65;
+struct PcgStencil {
+    bool on = false;
+    int Lx = 0, Ly = 0, Lz = 0;                  // full lattice
+    int K[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int first[8][3] = {};                        // first interior coordinate of each type per axis
+    int dims[8][3] = {};                         // the type's sub-lattice extents
+    int64_t base[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // start of the type's K x n_t values
+    int *d_off = nullptr;                        // 8 x PS_KMAX offsets (da + 2) * 25 + (db + 2) * 5 + dc + 2
+    float *d_L = nullptr, *d_B = nullptr;
+    int64_t len = 0;
+};
+
 struct ofks_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -146,6 +163,7 @@ struct ofks_ctx {
     // row stride of the float32 PCG's chunk-major blocks: n rounded up to 32 (= 32 n_tslices)
     int64_t n_slots = 0;
     float *d_tvalL = nullptr, *d_tvalB = nullptr;
+    PcgStencil ps;                               // stencil form of L and B for the float32 PCG
     double *d_valL = nullptr, *d_valB = nullptr, *d_valH = nullptr;
     double *d_dL = nullptr, *d_dB = nullptr;     // diagonals of L and B (free)
     // full-node stiffness for the Hartree Poisson problem (CSR)
@@ -284,6 +302,15 @@ int setup_nuclei_static(ofks_ctx *c, int M, const double *Z, const double *R);
 cudaError_t static_stage_lookup(ofks_ctx *c);
 void free_mesh(ofks_ctx *c);
 
+// ---- pcg_stencil.cu (stencil form of the float32 PCG apply)
+int pcg_stencil_setup(ofks_ctx *c, const std::vector<int> &fidx, const std::vector<int64_t> &rptr,
+                      const std::vector<int> &rcol, const std::vector<int> &inv, const std::vector<int> &slice_ptr);
+void pcg_stencil_free(ofks_ctx *c);
+// T Z with the fused P, Q updates and the P.Q partials on chunk-major blocks of width w; false
+// when the stencil form is not available
+bool launch_pcg_apply_st(ofks_ctx *c, int w, int pc, const float *Zc, float *P, float *Q, const double *beta_col,
+                         const double *shift, int first);
+
 // ---- stencil.cu (lattice form of the Hartree stiffness)
 int stencil_setup(ofks_ctx *c, int64_t N, const double *xyz, const int64_t *fptr, const int *fcol,
                   const uint8_t *dirichlet);
@@ -353,6 +380,7 @@ template <class T> void launch_judge(ofks_ctx *c, Blocks<T> &b);
 // Z = T_sep^-1 R (separable preconditioner of the PCG, float32 chunk-major blocks on lattice
 // meshes) with the rz partials; false when that form does not apply
 template <class T> bool launch_pcg_sep(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v);
+bool pcg_sep_active(ofks_ctx *c, int w);
 template <class T> void launch_direction_select(ofks_ctx *c, Blocks<T> &b);
 // D = the compact PCG result on the active columns, G on the others
 template <class T> void launch_direction_expand(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v);

@@ -387,7 +387,10 @@ void sep_tc_launch(ofks_ctx *c, SepPass P) {
     for (int cand = 1; cand <= nb; ++cand) {
         if (nb % cand) continue;
         d = cand;
-        if ((int64_t)ctas * cand >= 152) break;
+        // enough CTAs for the SMs, and at most 128 output columns per CTA: 128 tensor-memory
+        // columns let three CTAs share an SM (256 would leave it one, with nothing to overlap its
+        // tile loads with another CTA's MMAs and epilogue)
+        if ((int64_t)ctas * cand >= 152 && P.NP / cand <= 128) break;
     }
     P.NS = P.NP / d;
     P.tcols = P.NS <= 32 ? 32 : (P.NS <= 64 ? 64 : (P.NS <= 128 ? 128 : 256));

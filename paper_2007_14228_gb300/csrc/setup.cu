@@ -227,6 +227,7 @@ void dev_free(T *&p) {
 
 void free_mesh(ofks_ctx *c) {
     clear_graphs(c);
+    pcg_stencil_free(c);
     dev_free(c->d_slice_ptr); dev_free(c->d_slice_w); dev_free(c->d_cols); dev_free(c->d_perm);
     dev_free(c->d_valL); dev_free(c->d_valB); dev_free(c->d_valH); dev_free(c->d_dL); dev_free(c->d_dB);
     dev_free(c->d_fptr); dev_free(c->d_fcol); dev_free(c->d_fval); dev_free(c->d_minv);
@@ -558,6 +559,13 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
                 k_tsell_values<<<(unsigned)((acc2 + 255) / 256), 256, 0, c->stream>>>(acc2, d_tpos, c->d_valL, c->d_valB,
                                                                                      c->d_tvalL, c->d_tvalB);
                 cudaStreamSynchronize(c->stream);
+                if ((rc = pcg_stencil_setup(c, fidx, rptr, rcol, inv, slice_ptr)) != OFKS_OK) {
+                    dev_free(d_tpos);
+                    dev_free(d_xyz); dev_free(d_lloc); dev_free(d_gptr); dev_free(d_glist); dev_free(d_dpos); dev_free(d_fdiag); dev_free(d_interior);
+                    dev_free(d_flag);
+                    free_mesh(c);
+                    return rc;
+                }
                 dev_free(d_tpos);
                 c->n_tslices = nts;
                 c->n_slots = (int64_t)nts * SELL_C;

@@ -714,6 +714,8 @@ void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, i
             return;
         }
         if (zc) {
+            if (launch_pcg_apply_st(c, w, pc, (const float *)Zin, (float *)P, (float *)Q, beta_col, shift, first))
+                return;                                   // the stencil form (pq_units set there)
             const int nch = w / 4;
             const int spw = spw_for((int64_t)c->n_tslices * nch);
             const int64_t nsg = ((int64_t)c->n_tslices + spw - 1) / spw, nw = nsg * nch;

@@ -391,3 +391,34 @@ def test_separable_pcg_in_float64(ofks):
         err[pc] = float(np.max(np.linalg.norm(D[:, act] - Dx[:, act], axis=0) / np.linalg.norm(Dx[:, act], axis=0)))
     assert err["separable"] < 0.1 * err["jacobi"], err
     ctx.close()
+
+
+@pytest.mark.parametrize("pc", ["jacobi", "separable"])
+def test_stencil_pcg_apply_matches_the_sell_apply(ofks, pc):
+    # the float32 PCG with its operator applied on the stencil form of L and B (tiles of Z in
+    # shared memory, no column ids) against the type-grouped SELL apply: the same operator in the
+    # same per-row order, so only the grouping of the P.Q column sums differs (the stencil form is
+    # the option pcg_stencil = 1, measured slower than the SELL apply on the chain)
+    s = I.chain(cells=(26, 14, 8))
+    m = I.make_mesh(s)
+    ctx = ofks.context_for(s, m, beta=10.0, precision="mixed", pcg_pc=pc)
+    ctx.init_orbitals(I.initial_block(m.n_free, s.p, 0))
+    ctx.step(120)
+    ctx.evaluate()
+    G = ctx.get_field("G")
+    lam = np.diag(ctx.get_field("Lambda")).copy()
+    assert (lam < 0).sum() >= 5                      # a block of at least two chunk groups
+    out = {}
+    for st in (0, 1):
+        ctx.set_params(pcg_stencil=st, pcg_iters=8)
+        out[st] = ctx.precondition("pcg", G, lam)
+    scale = np.max(np.abs(out[0]))
+    assert np.max(np.abs(out[1] - out[0])) < 1e-4 * scale, np.max(np.abs(out[1] - out[0])) / scale
+    # and the full width (every column, 11 chunks: four groups of up to three)
+    lam_all = np.where(lam < 0, lam, -0.5)
+    for st in (0, 1):
+        ctx.set_params(pcg_stencil=st)
+        out[st] = ctx.precondition("pcg", G, lam_all)
+    scale = np.max(np.abs(out[0]))
+    assert np.max(np.abs(out[1] - out[0])) < 1e-4 * scale
+    ctx.close()

@@ -380,6 +380,32 @@ def time_to_target(ofks, I, system, budgets, chunk=100, forms=("fp64", "mixed", 
     return out
 
 
+def mixed_errors(ofks, I, system, extra, tol=1e-10):
+    """The mixed form's errors against the float64 form on the same system: both solved from the
+    seeded start to (kkt + fea)/kkt0 < tol, and the mixed form once more stopped at its hand-over
+    to the float64 sweep (tol = mixed_tol: the first float64 evaluation of the last float32
+    iterate).  Energies, the Rayleigh-Ritz eigenvalues and ||X^T B X - I||_F."""
+    import numpy as np
+    m = I.make_mesh(system)
+    V = I.initial_block(m.n_free, system.p, 0)
+    runs = {}
+    for name, prec, t in (("fp64", "fp64", tol), ("mixed", "mixed", tol), ("float32_phase", "mixed", 1e-6)):
+        ctx = ofks.context_for(system, m, beta=10.0, tol=t, max_iter=10 ** 6, poisson_adaptive=1, precision=prec,
+                               **extra)
+        ctx.init_orbitals(V)
+        r = ctx.solve(allow_notconv=True)
+        runs[name] = {"iters": r["iters"], "converged": bool(r["converged"]), "E": r["e_total"], "fea": r["fea"],
+                      "eig": ctx.rayleigh_ritz()}
+        ctx.close()
+    ref = runs["fp64"]
+    out = {"workload": system.name, "tol": tol, "fp64": {k: v for k, v in ref.items() if k != "eig"}}
+    for name in ("mixed", "float32_phase"):
+        r = runs[name]
+        out[name] = {"iters": r["iters"], "converged": r["converged"], "dE": abs(r["E"] - ref["E"]),
+                     "deig_max": float(np.max(np.abs(r["eig"] - ref["eig"]))), "fea": r["fea"]}
+    return out
+
+
 def compare_methods(ofks, I, tol=1e-8, max_iter=6000):
     """Iterations and device seconds to (kkt + fea)/kkt0 < tol on LiH (24^3 cells, p = 2, float64)
     for the step-size rules of Sec. 4.4 (the shape of the paper's ABB comparison) and for the three
@@ -468,6 +494,9 @@ def main():
                     help="the PCG of Eq. precondition-T in every form: 'separable:K' (the separable "
                          "preconditioner inside, K iterations; default K = 4) or 'jacobi:K' (the diagonal, "
                          "the paper's reading with K = 8)")
+    ap.add_argument("--mixed-errors", action="store_true",
+                    help="only the mixed form's errors against the float64 form (energy, eigenvalues, "
+                         "||X^T B X - I||) on the workload, one JSON line")
     args = ap.parse_args()
     kind, _, its = args.pcg.partition(":")
     if kind not in ("separable", "jacobi"):
@@ -480,6 +509,12 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.mixed_errors:
+        from paper_2007_14228_gb300 import build, inputs as I, ofks
+        build.build()
+        print(json.dumps({"mixed_errors": mixed_errors(ofks, I, workload(args.workload), args.extra),
+                          "params": args.extra}), flush=True)
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

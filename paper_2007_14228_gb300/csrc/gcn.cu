@@ -570,7 +570,17 @@ static int gcn_buffers(ofks_ctx *c) {
         alloc(&g.colf, 3 * 256) ||
         cudaMalloc((void **)&g.stats, sizeof(double) * 2 * c->p) != cudaSuccess ||
         cudaMalloc((void **)&g.lacc, sizeof(double) * 2 * c->p) != cudaSuccess)
+    {
+        cudaGetLastError();                    // the failed allocation's error is reported here, once
+        for (float **q : {&g.F, &g.H1, &g.H2, &g.Z1, &g.Z2, &g.AH, &g.y, &g.scale, &g.Dn, &g.Ds, &g.dA, &g.dB2,
+                          &g.G32, &g.colf}) {
+            if (*q) cudaFree(*q);
+            *q = nullptr;
+        }
+        for (double **q : {&g.stats, &g.lacc}) { if (*q) cudaFree(*q); *q = nullptr; }
+        g.rows = 0;
         return ofks_fail(c, OFKS_ENOMEM, "learned preconditioner: activations for %lld rows", (long long)rows);
+    }
     g.rows = rows;
     return OFKS_OK;
 }

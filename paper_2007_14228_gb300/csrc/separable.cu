@@ -590,8 +590,19 @@ bool sep_pcg_ready(ofks_ctx *c, int w) {
                             (int64_t)nx * ny * pad16(nz), (int64_t)nz * nx * pad16(ny), (int64_t)ny * nz * pad16(nx)};
     int64_t tot = 0;
     for (int q = 0; q < 6; ++q) { S.poff[q] = tot; tot += (len[q] * w + 63) / 64 * 64; }
-    if (cudaMalloc((void **)&S.pbuf, sizeof(__nv_bfloat16) * tot) != cudaSuccess) { S.pbuf = nullptr; return false; }
-    if (cudaMemset(S.pbuf, 0, sizeof(__nv_bfloat16) * tot) != cudaSuccess) return false;
+    // without room for the buffers the PCG keeps the Jacobi preconditioner (the failed call's
+    // error is cleared so that no later check reports it)
+    if (cudaMalloc((void **)&S.pbuf, sizeof(__nv_bfloat16) * tot) != cudaSuccess) {
+        cudaGetLastError();
+        S.pbuf = nullptr;
+        return false;
+    }
+    if (cudaMemset(S.pbuf, 0, sizeof(__nv_bfloat16) * tot) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(S.pbuf);
+        S.pbuf = nullptr;
+        return false;
+    }
     S.pw = w;
     return true;
 }

@@ -183,13 +183,9 @@ def separable_model(pinfo):
 # traffic is this ratio times its own algorithmic bytes (the column ids, values and the Z, P, Q
 # pieces all grow with the launch).
 PCG_F32_DRAM_PER_ALG = 418.2e6 / (12 * 12201095 + 20 * 442323 * 24)
-# The same for the stencil form of the apply (no column ids: 8 nnz + 20 n w algorithmic bytes);
-# None until a capture of it is at hand
-PCG_ST_DRAM_PER_ALG = None
 
 
-def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, spmv_model=(0, 0), elem=8, pc_model=(0, 0), pcg_w=None,
-             pcg_stencil=False):
+def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, spmv_model=(0, 0), elem=8, pc_model=(0, 0), pcg_w=None):
     """Dominant kernel family by time: algorithmic bytes and flops per launch / mean duration.
 
     Every family is one kernel launch per timed scope except "poisson" (the whole Hartree
@@ -198,9 +194,7 @@ def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, spmv_model=(0, 0), ele
     PCG's separable preconditioner: gather, six tensor-core contractions, scatter), which are left
     out of the choice; the solve's SpMV kernel is the "poisson_spmv" family.  The PCG apply works on the
     active columns only (their count rounded up to 4): pcg_w is its mean block width over the
-    timed launches.  With pcg_stencil (the float32 apply on the stencil form of L and B) no
-    column ids are read: its algorithmic bytes are the two values per stored entry and the block
-    pieces, 2 s nnz + 5 s n w."""
+    timed launches."""
     leaves = {k: v for k, v in prof.items() if k not in ("poisson", "poisson_vec", "gcn", "pcg_sep") and v["launches"]}
     fam = max(leaves, key=lambda k: leaves[k]["ms"])
     st = prof[fam]
@@ -208,7 +202,7 @@ def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, spmv_model=(0, 0), ele
     s = elem
     pw = p if pcg_w is None else pcg_w
     model = {
-        "pcg_spmm": (((2 * s) if pcg_stencil else (4 + 2 * s)) * nnz + 5 * s * n * pw, 4 * nnz * pw + 6 * n * pw),
+        "pcg_spmm": ((4 + 2 * s) * nnz + 5 * s * n * pw, 4 * nnz * pw + 6 * n * pw),
         "spmm_h": ((4 + s) * nnz + 2 * s * n * p, 2 * nnz * p),
         "spmm_b": ((4 + s) * nnz + 3 * s * n * p, 2 * nnz * p + 2 * n * p),
         "gram": (3 * s * n * p, 2 * n * p * p),
@@ -225,11 +219,9 @@ def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, spmv_model=(0, 0), ele
     extra = {"pcg_block_width": round(pw, 2)} if fam == "pcg_spmm" else {}
     traffic = None
     if fam == "pcg_spmm" and elem == 4:
-        ratio = PCG_ST_DRAM_PER_ALG if pcg_stencil else PCG_F32_DRAM_PER_ALG
-        if ratio:
-            traffic = int(bytes_ * ratio)
+        if PCG_F32_DRAM_PER_ALG:
+            traffic = int(bytes_ * PCG_F32_DRAM_PER_ALG)
             extra["traffic_source"] = "ncu DRAM bytes of the 60x32x30 chain's launch, scaled by algorithmic bytes"
-        extra["pcg_apply"] = "stencil" if pcg_stencil else "sell"
     alu_peak = ALU_PEAKS["fp32"] if fp32 else ALU_PEAKS["fp64"]
     f_alu = tflops / alu_peak
     if f_alu >= f_hbm:
@@ -647,13 +639,10 @@ def main():
         return
     hbm_peak, hbm_kind = peaks()
     sm, pm = poisson_spmv_model(sizes, pinfo), separable_model(pinfo)
-    # the stencil apply runs with pcg_stencil = 1 where the separable operator does (a lattice
-    # whose faces are the Dirichlet nodes)
-    stc = pinfo.get("precond") == "separable" and args.extra.get("pcg_stencil", 0) == 1
     roof = roofline(prof, sizes["n_free"], s.p, sizes["nnz"], sizes["n_tets"], hbm_peak, hbm_kind, sm, 4, pm,
-                    res["pcg_width"], stc)
+                    res["pcg_width"])
     roofm = roofline(profm, sizes["n_free"], s.p, sizes["nnz"], sizes["n_tets"], hbm_peak, hbm_kind, sm, 4, pm,
-                     resm["pcg_width"], stc)
+                     resm["pcg_width"])
     roof64 = roofline(prof64, sizes["n_free"], s.p, sizes["nnz"], sizes["n_tets"], hbm_peak, hbm_kind, sm, 8, pm,
                       res64["pcg_width"])
     ttc = None

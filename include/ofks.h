@@ -179,11 +179,6 @@ typedef struct {
                                the PCG from zero; 0: the network runs on every call */
     int32_t pcg_pc;         /* OFKS_PCGPC_JACOBI (default) or OFKS_PCGPC_SEPARABLE: the preconditioner
                                inside the PCG (only the accuracy of D changes, never T or the fixed point) */
-    int32_t pcg_stencil;    /* float32 PCG on lattice meshes whose Dirichlet nodes are the lattice's faces:
-                               1 the operator apply on the stencil form of L and B (per node type and offset,
-                               tiles of Z staged through shared memory, no column ids); 0 (default, measured
-                               1.4x faster on the chain) the type-grouped SELL.  Same operator, same summation
-                               order per row */
 } ofks_params;
 
 typedef struct {
@@ -214,7 +209,7 @@ typedef struct {
  * poisson_tol 1e-12, poisson_max_iter 20000, poisson_pc OFKS_HPC_SEPARABLE, mixed_tol 1e-6, poisson_tol_mixed
  * 1e-8, judge_tau 0.5, learned_tc 1, poisson_adaptive 0, poisson_csr 0, gram_tc 1, spmm_f32_rows 0,
  * poisson_sep_tc 1, pcg_compact 1, cuda_graphs 1, pcg_staged 0, sweep_pc32 1, method OFKS_METHOD_PCAL,
- * learned_loss 1, learned_retry 64, pcg_pc OFKS_PCGPC_JACOBI, pcg_stencil 0.  p is set to 1. */
+ * learned_loss 1, learned_retry 64, pcg_pc OFKS_PCGPC_JACOBI.  p is set to 1. */
 void ofks_default_params(ofks_params *prm);
 
 /* Create a context on CUDA device `device`.  *out receives the context (NULL on failure).

@@ -716,7 +716,7 @@ void ofks_default_params(ofks_params *p) {
     p->pcg_staged = 0;
     p->sweep_pc32 = 1;
     p->method = OFKS_METHOD_PCAL;
-    p->learned_loss = 1; p->learned_retry = 64; p->pcg_pc = OFKS_PCGPC_JACOBI; p->pcg_stencil = 0;
+    p->learned_loss = 1; p->learned_retry = 64; p->pcg_pc = OFKS_PCGPC_JACOBI;
 }
 
 int ofks_create(ofks_ctx **out, int device) {
@@ -819,8 +819,7 @@ int ofks_set_params(ofks_ctx *c, const ofks_params *prm) {
         prm->poisson_max_iter < 1 || prm->poisson_pc < 0 || prm->poisson_pc > OFKS_HPC_SEPARABLE || (prm->eta_rule == OFKS_ETA_FIXED && !(prm->eta_fixed > 0)) ||
         prm->method < OFKS_METHOD_PCAL || prm->method > OFKS_METHOD_MOPTQR ||
         prm->learned_loss < 0 || prm->learned_loss > 1 || prm->learned_retry < 0 ||
-        prm->pcg_pc < OFKS_PCGPC_JACOBI || prm->pcg_pc > OFKS_PCGPC_SEPARABLE || prm->pcg_stencil < 0 ||
-        prm->pcg_stencil > 1)
+        prm->pcg_pc < OFKS_PCGPC_JACOBI || prm->pcg_pc > OFKS_PCGPC_SEPARABLE)
         return ofks_fail(c, OFKS_EINVAL, "set_params: a parameter is out of range");
     cudaSetDevice(c->device);
     const bool mixed = prm->precision == OFKS_MIXED;

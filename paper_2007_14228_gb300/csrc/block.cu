@@ -570,8 +570,9 @@ __global__ void __launch_bounds__(256) k_pcg_init_s(int64_t n, int64_t ns, int p
                                                     const float *__restrict__ G, const float *__restrict__ Qn,
                                                     const float *__restrict__ Dn, int ld, const int *__restrict__ cmap,
                                                     const double *__restrict__ dL, const double *__restrict__ dB,
-                                                    const double *__restrict__ cb, float *W, float *D, float *R,
-                                                    float *Z, float *P, float *Q, double *part, int jac) {
+                                                    const double *__restrict__ cb, const int *__restrict__ tmap,
+                                                    float *W, float *D, float *R, float *Z, float *P, float *Q,
+                                                    double *part, int jac) {
     __shared__ float csw[8][MAXLD];
     __shared__ int scol[MAXLD];
     __shared__ float ssh[MAXLD];
@@ -584,10 +585,12 @@ __global__ void __launch_bounds__(256) k_pcg_init_s(int64_t n, int64_t ns, int p
     }
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;    // a multiple of 32
-    // one row per item, all its chunks in turn: the row of G (and of Q, D when warm) is read once
-    // and the chunk-major writes of one chunk stay contiguous across the warp
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r - (threadIdx.x & 31) < ns; r += stride) {
-        const bool real = r < n;
+    // one block row (type order) per item, all its chunks in turn: the free row tmap[t] of G (and
+    // of Q, D when warm) is read once and the chunk-major writes of one chunk stay contiguous
+    // across the warp
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t - (threadIdx.x & 31) < ns; t += stride) {
+        const int64_t r = t < ns ? tmap[t] : -1;
+        const bool real = r >= 0;
         const float dl = real ? 0.5f * (float)dL[r] : 0.f, db = real ? (float)dB[r] : 0.f;
         for (int q = 0; q < (w >> 2); ++q) {
             float wv[4], rv[4], zv[4], dv[4], acc[4];
@@ -607,8 +610,8 @@ __global__ void __launch_bounds__(256) k_pcg_init_s(int64_t n, int64_t ns, int p
                 wv[i] = ww; rv[i] = g; zv[i] = g * ww; dv[i] = d;
                 acc[i] = g * zv[i];
             }
-            if (r < ns) {
-                const int64_t o = (q * ns + r) << 2;           // sidx(r, 4 q, ns)
+            if (t < ns) {
+                const int64_t o = (q * ns + t) << 2;           // sidx(t, 4 q, ns)
                 *reinterpret_cast<float4 *>(R + o) = make_float4(rv[0], rv[1], rv[2], rv[3]);
                 *reinterpret_cast<float4 *>(D + o) = make_float4(dv[0], dv[1], dv[2], dv[3]);
                 if (jac) {
@@ -663,19 +666,20 @@ __global__ void __launch_bounds__(256) k_pcg_update_s(int64_t ns, int pc, int w,
     cols_out(w, csw, part);                                  // rzn
 }
 
-// The separable preconditioner of the float32 PCG (lattice meshes): R (chunk-major) -> the bf16
-// tensor [k][a][b][c~] of the contractions (free row r = (a ny + b) nz + c; columns k >= pc and
-// padding rows are zero), then after the passes Z <- the tensor (chunk-major) with the column
-// sums rz = R.Z as per-block partials (as k_pcg_update_s writes them).  Items (row, 4-column
-// chunk) as in the other chunk-major kernels.
-__global__ void __launch_bounds__(256) k_psep_gather(int64_t n, int64_t ns, int pc, int w, int nz, int pz,
-                                                     int64_t blk, const float *__restrict__ R, __nv_bfloat16 *t) {
+// The separable preconditioner of the float32 PCG (lattice meshes): R (chunk-major, type-ordered
+// rows) -> the bf16 tensor [k][a][b][c~] of the contractions (free row r = (a ny + b) nz + c;
+// columns k >= pc are zero), then after the passes Z <- the tensor (chunk-major) with the column
+// sums rz = R.Z as per-block partials (as k_pcg_update_s writes them).  Items (block row, 4-column
+// chunk) as in the other chunk-major kernels; tmap gives a block row's free row (-1: padding).
+__global__ void __launch_bounds__(256) k_psep_gather(int64_t ns, int pc, int w, int nz, int pz, int64_t blk,
+                                                     const int *__restrict__ tmap, const float *__restrict__ R,
+                                                     __nv_bfloat16 *t) {
     const int64_t total = ns * (w >> 2);
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int q = (int)(idx / ns);
-        const int64_t r = idx - (int64_t)q * ns;
-        if (r >= n) continue;
+        const int64_t r = tmap[idx - (int64_t)q * ns];
+        if (r < 0) continue;
         const float4 v = *reinterpret_cast<const float4 *>(R + (idx << 2));
         const float vv[4] = {v.x, v.y, v.z, v.w};
         const int64_t pos = (r / nz) * pz + r % nz;
@@ -687,8 +691,8 @@ __global__ void __launch_bounds__(256) k_psep_gather(int64_t n, int64_t ns, int 
     }
 }
 
-__global__ void __launch_bounds__(256) k_psep_scatter(int64_t n, int64_t ns, int pc, int w, int nz, int pz,
-                                                      int64_t blk, const __nv_bfloat16 *__restrict__ t,
+__global__ void __launch_bounds__(256) k_psep_scatter(int64_t ns, int pc, int w, int nz, int pz, int64_t blk,
+                                                      const int *__restrict__ tmap, const __nv_bfloat16 *__restrict__ t,
                                                       const float *__restrict__ R, float *Z, double *part) {
     __shared__ float csw[8][MAXLD];
     for (int k = threadIdx.x; k < 8 * MAXLD; k += blockDim.x) csw[k / MAXLD][k % MAXLD] = 0.f;
@@ -699,9 +703,9 @@ __global__ void __launch_bounds__(256) k_psep_scatter(int64_t n, int64_t ns, int
          idx += stride) {
         // the warp's first item decides for the whole warp (total is a multiple of 32)
         const int q = (int)(idx / ns);
-        const int64_t r = idx - (int64_t)q * ns;
+        const int64_t r = idx < total ? tmap[idx - (int64_t)q * ns] : -1;
         float zv[4] = {0.f, 0.f, 0.f, 0.f}, acc[4] = {0.f, 0.f, 0.f, 0.f};
-        if (r < n) {
+        if (r >= 0) {
             const float4 rv = *reinterpret_cast<const float4 *>(R + (idx << 2));
             const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
             const int64_t pos = (r / nz) * pz + r % nz;
@@ -740,15 +744,15 @@ __global__ void __launch_bounds__(256) k_psep_scatter_n(int64_t n, int ld, int64
     col_partial((double)acc, gid < stride, ld, ld, part);      // rz
 }
 
-// D (row-major, pitch ld) from the chunk-major PCG result: column j takes compact column cpos[j]
-// of Dc, G when inactive (cpos[j] = -1: T = I in Eq. precondition-T), and keeps its D when
-// cpos[j] = -2 (a learned direction the judge accepted)
+// D (row-major, pitch ld) from the chunk-major PCG result (free row r at block row tinv[r]):
+// column j takes compact column cpos[j] of Dc, G when inactive (cpos[j] = -1: T = I in Eq.
+// precondition-T), and keeps its D when cpos[j] = -2 (a learned direction the judge accepted)
 __global__ void __launch_bounds__(256) k_expand_s(int64_t n, int ld, int64_t stride, int64_t ns,
-                                                  const int *__restrict__ cpos, const float *__restrict__ G,
-                                                  const float *__restrict__ Dc, float *D) {
+                                                  const int *__restrict__ cpos, const int *__restrict__ tinv,
+                                                  const float *__restrict__ G, const float *__restrict__ Dc, float *D) {
     ELEM_BEGIN
         const int k = cpos[j];
-        if (k >= 0) D[e] = Dc[sidx(r, k, ns)];
+        if (k >= 0) D[e] = Dc[sidx(tinv[r], k, ns)];
         else if (k == -1) D[e] = G[e];
     ELEM_END
 }
@@ -1037,7 +1041,7 @@ void launch_pcg_init(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v, bool warm) 
             const unsigned rgrid = (unsigned)std::min<int64_t>((c->n_slots + 255) / 256, 152 * 8);
             k_pcg_init_s<<<rgrid, 256, 0, c->stream>>>(
                 c->n, c->n_slots, v.pc, w, (const float *)b.G[c->cur], (const float *)Qn, (const float *)Dn, c->ld,
-                v.cmap, c->d_dL, c->d_dB, v.cb, (float *)b.W, (float *)v.D, (float *)b.R, (float *)b.Z, (float *)b.P,
+                v.cmap, c->d_dL, c->d_dB, v.cb, c->d_tmap, (float *)b.W, (float *)v.D, (float *)b.R, (float *)b.Z, (float *)b.P,
                 warm ? nullptr : (float *)b.Q, c->d_cpart, jac ? 1 : 0);
             if (jac) launch_col_fin(c, v.pc, w, rgrid, c->d_cpart, v.cb + CB_RZ * w);
             return;
@@ -1072,9 +1076,10 @@ bool launch_pcg_sep(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v) {
         if (pcg_zc<T>(c, w)) {
             const int64_t total = c->n_slots * (w >> 2);
             const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8);
-            k_psep_gather<<<grid, 256, 0, c->stream>>>(c->n, c->n_slots, v.pc, w, nz, pz, blk, (const float *)b.R, t);
+            k_psep_gather<<<grid, 256, 0, c->stream>>>(c->n_slots, v.pc, w, nz, pz, blk, c->d_tmap, (const float *)b.R,
+                                                       t);
             sep_pcg_passes(c, w, v.cb + CB_SHIFT * w);
-            k_psep_scatter<<<grid, 256, 0, c->stream>>>(c->n, c->n_slots, v.pc, w, nz, pz, blk, t,
+            k_psep_scatter<<<grid, 256, 0, c->stream>>>(c->n_slots, v.pc, w, nz, pz, blk, c->d_tmap, t,
                                                         (const float *)b.R, (float *)b.Z, c->d_cpart);
             c->rz_units = grid;
             c->kernels += 2;
@@ -1135,7 +1140,7 @@ void launch_direction_expand(ofks_ctx *c, Blocks<T> &b, const PcgView<T> &v) {
     const ElemGrid g = elem_grid(c->n, c->ld);
     if constexpr (sizeof(T) == 4) {
         if (pcg_zc<T>(c, v.w)) {
-            k_expand_s<<<g.blocks, 256, 0, c->stream>>>(c->n, c->ld, g.stride, c->n_slots, v.cpos,
+            k_expand_s<<<g.blocks, 256, 0, c->stream>>>(c->n, c->ld, g.stride, c->n_slots, v.cpos, c->d_tinv,
                                                         (const float *)b.G[c->cur], (const float *)v.D,
                                                         (float *)b.D[c->cur]);
             return;

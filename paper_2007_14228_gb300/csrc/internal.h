@@ -121,23 +121,6 @@ struct SepState {
     int pw = 0;
 };
 
-// Stencil form of L and B on the free nodes of a lattice mesh whose Dirichlet nodes are the
-// lattice's faces (pcg_stencil.cu): node type t = parity triple of the lattice coordinates
-// (bits a b c), the type's K[t] neighbour offsets in [-2, 2]^3, and per type and offset one
-// float32 array over the type's interior sub-lattice (zero where the neighbour is not free)
-constexpr int PS_KMAX = 65;
-struct PcgStencil {
-    bool on = false;
-    int Lx = 0, Ly = 0, Lz = 0;                  // full lattice
-    int K[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int first[8][3] = {};                        // first interior coordinate of each type per axis
-    int dims[8][3] = {};                         // the type's sub-lattice extents
-    int64_t base[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // start of the type's K x n_t values
-    int *d_off = nullptr;                        // 8 x PS_KMAX offsets (da + 2) * 25 + (db + 2) * 5 + dc + 2
-    float *d_L = nullptr, *d_B = nullptr;
-    int64_t len = 0;
-};
-
 struct ofks_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -154,16 +137,19 @@ struct ofks_ctx {
     int *d_cols = nullptr;                       // sell_len free column ids
     int *d_perm = nullptr;                       // n_slices*32 -> free row id or -1
     int max_slice_w = 0;                         // widest slice (entries per row)
-    // type-grouped SELL of L and B (float32 values) for the float32 PCG on lattice meshes: slices
-    // of 32 free rows of one lattice node type, two lattice steps apart along the third axis, so
-    // the neighbour rows of a slice at one offset are two rows apart
+    // type-grouped SELL of L and B (float32 values) for the float32 PCG on lattice meshes.  Its
+    // rows, and the rows of the PCG's chunk-major blocks, are the free nodes in type order: node
+    // type (parity triple of the lattice coordinates) first, then lattice order, so slice s is
+    // rows 32 s .. 32 s + 31 of one type along the third axis and its neighbours at one offset
+    // are consecutive rows of another type.  d_tmap: type-ordered row -> free row (-1 past n),
+    // d_tinv: free row -> type-ordered row; d_tcols holds type-ordered column ids
     int n_tslices = 0;
     int64_t tsell_len = 0;
-    int *d_tslice_ptr = nullptr, *d_tslice_w = nullptr, *d_tcols = nullptr, *d_tperm = nullptr;
+    int *d_tslice_ptr = nullptr, *d_tslice_w = nullptr, *d_tcols = nullptr;
+    int *d_tmap = nullptr, *d_tinv = nullptr;
     // row stride of the float32 PCG's chunk-major blocks: n rounded up to 32 (= 32 n_tslices)
     int64_t n_slots = 0;
     float *d_tvalL = nullptr, *d_tvalB = nullptr;
-    PcgStencil ps;                               // stencil form of L and B for the float32 PCG
     double *d_valL = nullptr, *d_valB = nullptr, *d_valH = nullptr;
     double *d_dL = nullptr, *d_dB = nullptr;     // diagonals of L and B (free)
     // full-node stiffness for the Hartree Poisson problem (CSR)
@@ -302,14 +288,6 @@ int setup_nuclei_static(ofks_ctx *c, int M, const double *Z, const double *R);
 cudaError_t static_stage_lookup(ofks_ctx *c);
 void free_mesh(ofks_ctx *c);
 
-// ---- pcg_stencil.cu (stencil form of the float32 PCG apply)
-int pcg_stencil_setup(ofks_ctx *c, const std::vector<int> &fidx, const std::vector<int64_t> &rptr,
-                      const std::vector<int> &rcol, const std::vector<int> &inv, const std::vector<int> &slice_ptr);
-void pcg_stencil_free(ofks_ctx *c);
-// T Z with the fused P, Q updates and the P.Q partials on chunk-major blocks of width w; false
-// when the stencil form is not available
-bool launch_pcg_apply_st(ofks_ctx *c, int w, int pc, const float *Zc, float *P, float *Q, const double *beta_col,
-                         const double *shift, int first);
 
 // ---- stencil.cu (lattice form of the Hartree stiffness)
 int stencil_setup(ofks_ctx *c, int64_t N, const double *xyz, const int64_t *fptr, const int *fcol,

@@ -227,7 +227,6 @@ void dev_free(T *&p) {
 
 void free_mesh(ofks_ctx *c) {
     clear_graphs(c);
-    pcg_stencil_free(c);
     dev_free(c->d_slice_ptr); dev_free(c->d_slice_w); dev_free(c->d_cols); dev_free(c->d_perm);
     dev_free(c->d_valL); dev_free(c->d_valB); dev_free(c->d_valH); dev_free(c->d_dL); dev_free(c->d_dB);
     dev_free(c->d_fptr); dev_free(c->d_fcol); dev_free(c->d_fval); dev_free(c->d_minv);
@@ -241,7 +240,8 @@ void free_mesh(ofks_ctx *c) {
     gcn_free(c);
     stencil_free(c);
     sep_free(c);
-    dev_free(c->d_tslice_ptr); dev_free(c->d_tslice_w); dev_free(c->d_tcols); dev_free(c->d_tperm);
+    dev_free(c->d_tslice_ptr); dev_free(c->d_tslice_w); dev_free(c->d_tcols);
+    dev_free(c->d_tmap); dev_free(c->d_tinv);
     dev_free(c->d_tvalL); dev_free(c->d_tvalB);
     c->n_tslices = 0; c->n_slots = 0; c->tsell_len = 0;
     c->amg_tried = false;
@@ -495,8 +495,10 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
     }
     c->n_nodes = N;
     stencil_fill(c);
-    // type-grouped SELL for the float32 PCG (lattice meshes): rows of each lattice node type in
-    // lattice order, so a slice is 32 rows of one type two steps apart along the third axis
+    // type-grouped SELL for the float32 PCG (lattice meshes): the free rows in type order (the
+    // lattice node types in turn, each in lattice order), which is also the row order of the
+    // PCG's chunk-major blocks, so the 32 rows of a slice and their neighbours at one offset are
+    // consecutive rows
     if (c->st.on) {
         const int Lx = c->st.Lx, Ly = c->st.Ly, Lz = c->st.Lz;
         std::vector<int> tp;
@@ -510,14 +512,16 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
                     }
         if ((int64_t)tp.size() == n) {
             const int nts = (int)((n + SELL_C - 1) / SELL_C);
-            std::vector<int> tptr(nts + 1, 0), tw(nts, 0), tperm((int64_t)nts * SELL_C, -1);
+            std::vector<int> tinv(n, -1), tmap((int64_t)nts * SELL_C, -1);
+            for (int64_t k = 0; k < n; ++k) { tinv[tp[k]] = (int)k; tmap[k] = tp[k]; }
+            std::vector<int> tptr(nts + 1, 0), tw(nts, 0);
             int64_t acc2 = 0;
             bool fits = true;
             for (int s = 0; s < nts; ++s) {
                 int w = 0;
                 for (int l = 0; l < SELL_C; ++l) {
                     const int64_t k = (int64_t)s * SELL_C + l;
-                    if (k < n) { tperm[k] = tp[k]; w = std::max(w, rowlen[tp[k]]); }
+                    if (k < n) w = std::max(w, rowlen[tp[k]]);
                 }
                 tw[s] = w;
                 if (acc2 >= ((int64_t)1 << 31)) fits = false;
@@ -538,7 +542,7 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
                             for (int j = 0; j < tw[s]; ++j) {
                                 const int jj = std::min(j, len - 1);
                                 const int64_t e = tptr[s] + (int64_t)j * SELL_C + l;
-                                tcol[e] = rcol[rptr[r] + jj];
+                                tcol[e] = tinv[rcol[rptr[r] + jj]];
                                 if (j < len) tpos[e] = (int)(slice_ptr[sp / SELL_C] + (int64_t)j * SELL_C + sp % SELL_C);
                             }
                         }
@@ -546,7 +550,8 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
                 int *d_tpos = nullptr;
                 if ((rc = dev_upload(c, &c->d_tslice_ptr, tptr.data(), tptr.size())) ||
                     (rc = dev_upload(c, &c->d_tslice_w, tw.data(), tw.size())) ||
-                    (rc = dev_upload(c, &c->d_tperm, tperm.data(), tperm.size())) ||
+                    (rc = dev_upload(c, &c->d_tmap, tmap.data(), tmap.size())) ||
+                    (rc = dev_upload(c, &c->d_tinv, tinv.data(), tinv.size())) ||
                     (rc = dev_upload(c, &c->d_tcols, tcol.data(), tcol.size())) ||
                     (rc = dev_upload(c, &d_tpos, tpos.data(), tpos.size())) ||
                     (rc = dev_zeros(c, &c->d_tvalL, acc2)) || (rc = dev_zeros(c, &c->d_tvalB, acc2))) {
@@ -559,13 +564,6 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
                 k_tsell_values<<<(unsigned)((acc2 + 255) / 256), 256, 0, c->stream>>>(acc2, d_tpos, c->d_valL, c->d_valB,
                                                                                      c->d_tvalL, c->d_tvalB);
                 cudaStreamSynchronize(c->stream);
-                if ((rc = pcg_stencil_setup(c, fidx, rptr, rcol, inv, slice_ptr)) != OFKS_OK) {
-                    dev_free(d_tpos);
-                    dev_free(d_xyz); dev_free(d_lloc); dev_free(d_gptr); dev_free(d_glist); dev_free(d_dpos); dev_free(d_fdiag); dev_free(d_interior);
-                    dev_free(d_flag);
-                    free_mesh(c);
-                    return rc;
-                }
                 dev_free(d_tpos);
                 c->n_tslices = nts;
                 c->n_slots = (int64_t)nts * SELL_C;

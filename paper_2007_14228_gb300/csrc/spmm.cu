@@ -204,19 +204,15 @@ __global__ void __launch_bounds__(256) k_pcg_apply(int64_t nwarps, int nchunks, 
 }
 
 // The float32 PCG apply on the type-grouped SELL with every PCG block chunk-major: element
-// (r, c) at ((c / 4) ns + r) 4 + c % 4 (ns = n rounded up to 32).  A warp takes spw consecutive
-// slices in turn for one 4-column chunk and writes its column sums P.Q once at the end.  Its lanes are
-// 32 rows of one lattice node type two lattice steps apart, so for one entry index their neighbour
-// rows are (mostly) two rows apart too: the 32 16-byte gathers fall in ~8 lines of the chunk's
-// ns x 16 B array, and the rows' 27 neighbourhoods overlap, so most of them hit L1.  The lanes'
-// own P and Q pieces lie in the same ~8 lines.  (Storing the blocks in the slices' own order made
-// the gathers contiguous but spread each neighbourhood over the eight node types' ranges: L1 hits
-// fell from 63 % to 48 % and the launch took 40 % longer.)
+// (r, c) at ((c / 4) ns + r) 4 + c % 4 (ns = n rounded up to 32), rows in type order.  A warp
+// takes spw consecutive slices in turn for one 4-column chunk and writes its column sums P.Q once
+// at the end.  Its lanes are 32 consecutive rows of one lattice node type, so for one entry index
+// their neighbours are (mostly) 32 consecutive rows of one type: each 16-byte gather of the warp
+// reads 512 contiguous bytes, and the lanes' own P and Q pieces are contiguous too.
 __global__ void __launch_bounds__(256, 4) k_pcg_apply_zc(int64_t nwarps, int nchunks, int64_t n_slices, int spw, int p,
-                                                      int64_t ns, const int *__restrict__ slice_ptr,
+                                                      int64_t n, int64_t ns, const int *__restrict__ slice_ptr,
                                                       const int *__restrict__ slice_w,
                                                       const int *__restrict__ cols,
-                                                      const int *__restrict__ perm,
                                                       const float *__restrict__ valL,
                                                       const float *__restrict__ valB,
                                                       const float *__restrict__ Zc, float *P, float *Q,
@@ -241,7 +237,7 @@ __global__ void __launch_bounds__(256, 4) k_pcg_apply_zc(int64_t nwarps, int nch
     float contrib[4] = {0.f, 0.f, 0.f, 0.f};
     for (int64_t s = s0; s < s1; ++s) {
         const int base = slice_ptr[s], width = slice_w[s];
-        const int r = perm[s * SELL_C + lane];
+        const int64_t r = s * SELL_C + lane;
         float aL[4] = {0.f, 0.f, 0.f, 0.f}, aB[4] = {0.f, 0.f, 0.f, 0.f};
         // four entries per pass with all their loads issued before the first multiply-add: four
         // gathers in flight per lane (with the register cap of four CTAs per SM this measured
@@ -272,8 +268,8 @@ __global__ void __launch_bounds__(256, 4) k_pcg_apply_zc(int64_t nwarps, int nch
             aL[0] = fmaf(vl, x.x, aL[0]); aL[1] = fmaf(vl, x.y, aL[1]); aL[2] = fmaf(vl, x.z, aL[2]); aL[3] = fmaf(vl, x.w, aL[3]);
             aB[0] = fmaf(vb, x.x, aB[0]); aB[1] = fmaf(vb, x.y, aB[1]); aB[2] = fmaf(vb, x.z, aB[2]); aB[3] = fmaf(vb, x.w, aB[3]);
         }
-        if (r < 0) continue;
-        const int64_t o = (int64_t)r * 4;
+        if (r >= n) continue;
+        const int64_t o = r * 4;
         const float4 z4 = __ldg(reinterpret_cast<const float4 *>(Zk + o));
         const float zr[4] = {z4.x, z4.y, z4.z, z4.w};
         float pr[4] = {0.f, 0.f, 0.f, 0.f}, qr[4] = {0.f, 0.f, 0.f, 0.f};
@@ -714,14 +710,12 @@ void launch_pcg_apply(ofks_ctx *c, const T *valL, const T *valB, const T *Zin, i
             return;
         }
         if (zc) {
-            if (launch_pcg_apply_st(c, w, pc, (const float *)Zin, (float *)P, (float *)Q, beta_col, shift, first))
-                return;                                   // the stencil form (pq_units set there)
             const int nch = w / 4;
             const int spw = spw_for((int64_t)c->n_tslices * nch);
             const int64_t nsg = ((int64_t)c->n_tslices + spw - 1) / spw, nw = nsg * nch;
             k_pcg_apply_zc<<<(unsigned)((nw * 32 + 255) / 256), 256, 0, c->stream>>>(
-                nw, nch, (int64_t)c->n_tslices, spw, pc, c->n_slots, c->d_tslice_ptr, c->d_tslice_w, c->d_tcols,
-                c->d_tperm, c->d_tvalL, c->d_tvalB, (const float *)Zin, (float *)P, (float *)Q, beta_col, shift,
+                nw, nch, (int64_t)c->n_tslices, spw, pc, c->n, c->n_slots, c->d_tslice_ptr, c->d_tslice_w, c->d_tcols,
+                c->d_tvalL, c->d_tvalB, (const float *)Zin, (float *)P, (float *)Q, beta_col, shift,
                 c->d_cpart, first);
             c->kernels += 1;
             c->pq_units = nsg;

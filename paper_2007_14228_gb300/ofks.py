@@ -52,7 +52,7 @@ class Params(C.Structure):
                 ("gram_tc", C.c_int32), ("spmm_f32_rows", C.c_int32), ("poisson_sep_tc", C.c_int32),
                 ("pcg_compact", C.c_int32), ("cuda_graphs", C.c_int32), ("pcg_staged", C.c_int32),
                 ("sweep_pc32", C.c_int32), ("method", C.c_int32), ("learned_loss", C.c_int32),
-                ("learned_retry", C.c_int32), ("pcg_pc", C.c_int32), ("pcg_stencil", C.c_int32)]
+                ("learned_retry", C.c_int32), ("pcg_pc", C.c_int32)]
 
 
 class Result(C.Structure):

@@ -24,17 +24,6 @@ def test_pcg_roofline_is_algorithmic_bytes_over_launch_time():
     assert 1.0 < bench.PCG_F32_DRAM_PER_ALG < 1.3    # the mid-size capture moved 1.17x its algorithmic bytes
 
 
-def test_stencil_pcg_roofline_counts_no_column_ids():
-    n, nnz, w = 1175805, 32817315, 24.0
-    prof = {"pcg_spmm": {"ms": 20.0, "launches": 80}}
-    r = bench.roofline(prof, n, 41, nnz, 908160, 6756.8, "measured", elem=4, pcg_w=w, pcg_stencil=True)
-    alg = 8 * nnz + 20 * n * w                        # 2 s nnz + 5 s n w at s = 4
-    assert r["achieved"] == pytest.approx(alg / (20e-3 / 80) / 1e9, abs=0.05)
-    assert r["pcg_apply"] == "stencil"
-    if bench.PCG_ST_DRAM_PER_ALG is None:
-        assert r["traffic"] is None
-
-
 def test_float64_pcg_roofline_is_against_the_fp64_rate():
     bench.ALU_PEAKS.update({"fp64": 1.25, "fp32": 78.0, "kind": "test"})
     prof = {"pcg_spmm": {"ms": 243.0, "launches": 80}}

@@ -164,18 +164,6 @@ def poisson_spmv_model(sizes, pinfo):
     return 12 * nnz_full + 32 * n_nodes, 2 * nnz_full
 
 
-def separable_model(pinfo):
-    """One application of the separable preconditioner: six float32 axis contractions of the
-    interior tensor (2 n_t n_d flops each, both directions) plus gather and scatter; bytes: the
-    tensor read and written by each pass (4 B) and the float64 vectors it starts and ends on."""
-    lat = pinfo.get("lattice") if pinfo else None
-    if not lat or not all(lat):
-        return 0, 0
-    nx, ny, nz = (d - 2 for d in lat)
-    nt = nx * ny * nz
-    return nt * (6 * 8 + 12 + 12) + 8 * (nx * nx + ny * ny + nz * nz), 4 * nt * (nx + ny + nz)
-
-
 # DRAM bytes per algorithmic byte of the float32 PCG apply (k_pcg_apply_zc), measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the chain at 60 x 32 x 30 cells: 418.2 MB per
 # launch at n = 442,323, width 24 and 12,201,095 stored entries, whose algorithmic bytes are
@@ -185,17 +173,19 @@ def separable_model(pinfo):
 PCG_F32_DRAM_PER_ALG = 418.2e6 / (12 * 12201095 + 20 * 442323 * 24)
 
 
-def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, spmv_model=(0, 0), elem=8, pc_model=(0, 0), pcg_w=None):
+def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, spmv_model=(0, 0), elem=8, pcg_w=None):
     """Dominant kernel family by time: algorithmic bytes and flops per launch / mean duration.
 
     Every family is one kernel launch per timed scope except "poisson" (the whole Hartree
-    solve), "poisson_vec" (two vector kernels per CG iteration), "gcn" (one application of the
-    learned preconditioner's network, a dozen kernels) and "pcg_sep" (one application of the
-    PCG's separable preconditioner: gather, six tensor-core contractions, scatter), which are left
-    out of the choice; the solve's SpMV kernel is the "poisson_spmv" family.  The PCG apply works on the
+    solve), "poisson_vec" (two vector kernels per CG iteration), "poisson_pc" (one application of
+    the Hartree CG's preconditioner: the CG update with the gather, six contractions, the scatter),
+    "gcn" (one application of the learned preconditioner's network, a dozen kernels) and
+    "pcg_sep" (the same separable application inside the PCG), which are left out of the choice;
+    the solve's SpMV kernel is the "poisson_spmv" family.  The PCG apply works on the
     active columns only (their count rounded up to 4): pcg_w is its mean block width over the
     timed launches."""
-    leaves = {k: v for k, v in prof.items() if k not in ("poisson", "poisson_vec", "gcn", "pcg_sep") and v["launches"]}
+    multi = ("poisson", "poisson_vec", "poisson_pc", "gcn", "pcg_sep")
+    leaves = {k: v for k, v in prof.items() if k not in multi and v["launches"]}
     fam = max(leaves, key=lambda k: leaves[k]["ms"])
     st = prof[fam]
     per = st["ms"] / max(st["launches"], 1) * 1e-3
@@ -209,13 +199,12 @@ def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, spmv_model=(0, 0), ele
         "grad": (3 * s * n * p, 4 * n * p * p),
         "density": (s * n * p + n_tets * (40 + 32), n_tets * 4 * (20 * p + 2 * p)),
         "poisson_spmv": spmv_model,
-        "poisson_pc": pc_model,
     }
     bytes_, flops = model.get(fam, (0, 0))
     gbs = bytes_ / per / 1e9
     tflops = flops / per / 1e12
     f_hbm = gbs / hbm_peak
-    fp32 = fam == "poisson_pc" or (elem == 4 and fam != "poisson_spmv")
+    fp32 = elem == 4 and fam != "poisson_spmv"
     extra = {"pcg_block_width": round(pw, 2)} if fam == "pcg_spmm" else {}
     traffic = None
     if fam == "pcg_spmm" and elem == 4:
@@ -482,9 +471,9 @@ def main():
                     help="state file of the start iterate: loaded if it exists, else written (profiling runs)")
     ap.add_argument("--params", default="",
                     help="extra ofks_params for every context, e.g. spmm_f32_rows=1,gram_tc=0 (profiling runs)")
-    ap.add_argument("--pcg", default="separable:4",
+    ap.add_argument("--pcg", default="separable:1",
                     help="the PCG of Eq. precondition-T in every form: 'separable:K' (the separable "
-                         "preconditioner inside, K iterations; default K = 4) or 'jacobi:K' (the diagonal, "
+                         "preconditioner inside, K iterations; default K = 1) or 'jacobi:K' (the diagonal, "
                          "the paper's reading with K = 8)")
     ap.add_argument("--mixed-errors", action="store_true",
                     help="only the mixed form's errors against the float64 form (energy, eigenvalues, "
@@ -493,7 +482,7 @@ def main():
     kind, _, its = args.pcg.partition(":")
     if kind not in ("separable", "jacobi"):
         raise SystemExit(f"--pcg {args.pcg}: separable:K or jacobi:K")
-    args.extra = {"pcg_pc": 1 if kind == "separable" else 0, "pcg_iters": int(its or (4 if kind == "separable" else 8))}
+    args.extra = {"pcg_pc": 1 if kind == "separable" else 0, "pcg_iters": int(its or (1 if kind == "separable" else 8))}
     for kv in filter(None, args.params.split(",")):
         k, v = kv.split("=")
         args.extra[k] = float(v) if "." in v or "e" in v else int(v)
@@ -638,12 +627,12 @@ def main():
     if rank != 0:
         return
     hbm_peak, hbm_kind = peaks()
-    sm, pm = poisson_spmv_model(sizes, pinfo), separable_model(pinfo)
-    roof = roofline(prof, sizes["n_free"], s.p, sizes["nnz"], sizes["n_tets"], hbm_peak, hbm_kind, sm, 4, pm,
+    sm = poisson_spmv_model(sizes, pinfo)
+    roof = roofline(prof, sizes["n_free"], s.p, sizes["nnz"], sizes["n_tets"], hbm_peak, hbm_kind, sm, 4,
                     res["pcg_width"])
-    roofm = roofline(profm, sizes["n_free"], s.p, sizes["nnz"], sizes["n_tets"], hbm_peak, hbm_kind, sm, 4, pm,
+    roofm = roofline(profm, sizes["n_free"], s.p, sizes["nnz"], sizes["n_tets"], hbm_peak, hbm_kind, sm, 4,
                      resm["pcg_width"])
-    roof64 = roofline(prof64, sizes["n_free"], s.p, sizes["nnz"], sizes["n_tets"], hbm_peak, hbm_kind, sm, 8, pm,
+    roof64 = roofline(prof64, sizes["n_free"], s.p, sizes["nnz"], sizes["n_tets"], hbm_peak, hbm_kind, sm, 8,
                       res64["pcg_width"])
     ttc = None
     if not args.no_ttc:

@@ -301,18 +301,29 @@ inline int chunk_width(int ld) { return (ld % 4 == 0) ? 4 : (ld % 2 == 0 ? 2 : 1
 
 // ---- float32 SpMM with the neighbour rows staged through shared memory (ld = 4 NC <= 64)
 //
-// One warp per SELL slice (lane = row).  For each entry index j the warp loads the 32 neighbour
-// rows X[c_l, 0:ld] cooperatively: flat item i = (row k, 16-byte chunk q) with consecutive lanes
-// on consecutive chunks of one row, so one load instruction covers about three whole rows (~6
-// cache lines) instead of 32 rows' pieces; the rows go to the warp's shared tile (row stride
-// XS_STRIDE(NC) floats: an odd multiple of 4 modulo 32 words, so the 16-byte reads of 8 lanes at
-// a time hit distinct banks) and each lane then multiplies its own row.  Column ids and values are
-// read once per slice.  The result rows leave through the same tile as whole-row coalesced
-// stores.  MODE 1 also forms the column sums X[r,c] Y[r,c] of the slice (per warp, in lane
-// order) into part[c * n_slices + slice].
+// One warp per SELL slice (lane = row).  For each entry index j the warp copies the 32 neighbour
+// rows X[c_l, 0:ld] into a shared tile with 16-byte asynchronous copies (cp.async, straight from
+// L2 into shared memory): flat item i = (row k, 16-byte chunk q) with consecutive lanes on
+// consecutive chunks of one row, so one copy instruction covers about three whole rows (~6 cache
+// lines) instead of 32 rows' pieces; each lane then multiplies its own row from the tile.  The
+// copies run WS_STAGES - 1 entries ahead of the multiply-adds (a ring of WS_STAGES tiles per
+// warp, row stride ws_stride(NC) floats: an odd multiple of 4 modulo 32 words, so the 16-byte
+// reads of 8 lanes at a time hit distinct banks), and the column ids and values of 8 entries
+// are loaded together.  The result rows leave through a tile as whole-row coalesced stores.
+// MODE 1 also forms the column sums X[r,c] Y[r,c] of the slice (per warp, in lane order) into
+// part[c * n_slices + slice].
 constexpr int WS_WARPS = 4;                       // warps per block
+constexpr int WS_STAGES = 3;                      // tiles in flight per warp
+constexpr int WS_BATCH = 8;                       // entries whose column ids and values load together
 
 __host__ __device__ constexpr int ws_stride(int nc) { return (nc % 2 == 1) ? 4 * nc : 4 * nc + 4; }
+// shared memory of one block: per warp WS_STAGES tiles of 32 rows and WS_STAGES x 32 values
+__host__ __device__ constexpr int ws_smem(int nc) { return WS_WARPS * WS_STAGES * 32 * (ws_stride(nc) + 1) * 4; }
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
 
 template <int NC, int MODE>
 __global__ void __launch_bounds__(WS_WARPS * 32) k_spmm_ws(int64_t n_slices, int p, const int *__restrict__ slice_ptr,
@@ -320,39 +331,63 @@ __global__ void __launch_bounds__(WS_WARPS * 32) k_spmm_ws(int64_t n_slices, int
                                                           const int *__restrict__ perm, const float *__restrict__ val,
                                                           const float *__restrict__ X, float *__restrict__ Y,
                                                           double *part) {
-    constexpr int LD = 4 * NC, STR = ws_stride(NC);
-    __shared__ __align__(16) float tile[WS_WARPS][32 * STR];
+    constexpr int LD = 4 * NC, STR = ws_stride(NC), TS = 32 * STR;
+    extern __shared__ __align__(16) float wsm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t s = blockIdx.x * (int64_t)WS_WARPS + warp;
     if (s >= n_slices) return;                      // whole warp leaves together
-    float *T = tile[warp];
+    float *T = wsm + (size_t)warp * WS_STAGES * (TS + 32);
+    float *V = T + WS_STAGES * TS;                  // the lane's value of each staged entry
     const int base = slice_ptr[s], width = slice_w[s];
     const int r = perm[s * SELL_C + lane];
     float acc[LD];
 #pragma unroll
     for (int k = 0; k < LD; ++k) acc[k] = 0.f;
-    for (int j = 0; j < width; ++j) {
-        const int e = base + j * SELL_C + lane;
-        const int cl = __ldg(cols + e);
-        const float vl = __ldg(val + e);
-        // stage the 32 neighbour rows (NC chunks each)
+    // iteration j copies entry j's rows and multiplies entry j - (WS_STAGES - 1); the copy groups
+    // are committed one per iteration (empty past the last entry), so waiting until at most
+    // WS_STAGES - 1 groups are pending completes the group of the entry multiplied
+    for (int j0 = 0; j0 < width + WS_STAGES - 1; j0 += WS_BATCH) {
+        int cc[WS_BATCH];
+        float vv[WS_BATCH];
 #pragma unroll
-        for (int it = 0; it < NC; ++it) {
-            const int i = it * 32 + lane, k = i / NC, q = i - k * NC;
-            const int ck = __shfl_sync(0xffffffffu, cl, k);
-            const float4 v = __ldg(reinterpret_cast<const float4 *>(X + (int64_t)ck * LD) + q);
-            *reinterpret_cast<float4 *>(T + k * STR + 4 * q) = v;
+        for (int u = 0; u < WS_BATCH; ++u) {
+            const int j = j0 + u;
+            cc[u] = j < width ? __ldg(cols + base + j * SELL_C + lane) : 0;
+            vv[u] = j < width ? __ldg(val + base + j * SELL_C + lane) : 0.f;
         }
-        __syncwarp();
 #pragma unroll
-        for (int q = 0; q < NC; ++q) {
-            const float4 x = *reinterpret_cast<const float4 *>(T + lane * STR + 4 * q);
-            acc[4 * q] = fmaf(vl, x.x, acc[4 * q]);
-            acc[4 * q + 1] = fmaf(vl, x.y, acc[4 * q + 1]);
-            acc[4 * q + 2] = fmaf(vl, x.z, acc[4 * q + 2]);
-            acc[4 * q + 3] = fmaf(vl, x.w, acc[4 * q + 3]);
+        for (int u = 0; u < WS_BATCH; ++u) {
+            const int j = j0 + u;
+            if (j >= width + WS_STAGES - 1) break;  // warp-uniform
+            if (j < width) {
+                const int st = j % WS_STAGES;
+                float *Ts = T + st * TS;
+                V[st * 32 + lane] = vv[u];
+#pragma unroll
+                for (int it = 0; it < NC; ++it) {
+                    const int i = it * 32 + lane, k = i / NC, q = i - k * NC;
+                    const int ck = __shfl_sync(0xffffffffu, cc[u], k);
+                    cp_async16(Ts + k * STR + 4 * q, X + (int64_t)ck * LD + 4 * q);
+                }
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            const int jc = j - (WS_STAGES - 1);
+            if (jc < 0) continue;
+            asm volatile("cp.async.wait_group %0;" ::"n"(WS_STAGES - 1) : "memory");
+            __syncwarp();
+            const int st = jc % WS_STAGES;
+            const float *Ts = T + st * TS;
+            const float vl = V[st * 32 + lane];
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+                const float4 x = *reinterpret_cast<const float4 *>(Ts + lane * STR + 4 * q);
+                acc[4 * q] = fmaf(vl, x.x, acc[4 * q]);
+                acc[4 * q + 1] = fmaf(vl, x.y, acc[4 * q + 1]);
+                acc[4 * q + 2] = fmaf(vl, x.z, acc[4 * q + 2]);
+                acc[4 * q + 3] = fmaf(vl, x.w, acc[4 * q + 3]);
+            }
+            __syncwarp();                           // the tile is refilled WS_STAGES entries later
         }
-        __syncwarp();
     }
     // the slice's rows out through the tile as whole-row stores
 #pragma unroll
@@ -493,8 +528,9 @@ template <int MODE>
 bool launch_spmm_ws(ofks_ctx *c, int ld, const float *val, const float *X, float *Y, double *colsum) {
     if (ld % 4 || ld < 8 || ld > 64) return false;
     const unsigned grid = (unsigned)((c->n_slices + WS_WARPS - 1) / WS_WARPS);
-#define WS_(nc) k_spmm_ws<nc, MODE><<<grid, WS_WARPS * 32, 0, c->stream>>>(c->n_slices, c->p, c->d_slice_ptr, \
-        c->d_slice_w, c->d_cols, c->d_perm, val, X, Y, c->d_cpart)
+#define WS_(nc) { cudaFuncSetAttribute(k_spmm_ws<nc, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, ws_smem(nc)); \
+        k_spmm_ws<nc, MODE><<<grid, WS_WARPS * 32, ws_smem(nc), c->stream>>>(c->n_slices, c->p, c->d_slice_ptr, \
+        c->d_slice_w, c->d_cols, c->d_perm, val, X, Y, c->d_cpart); }
     switch (ld / 4) {
         case 2: WS_(2); break; case 3: WS_(3); break; case 4: WS_(4); break; case 5: WS_(5); break;
         case 6: WS_(6); break; case 7: WS_(7); break; case 8: WS_(8); break; case 9: WS_(9); break;

@@ -115,6 +115,7 @@ struct SepState {
     bool tc = false;                             // tensor-core form available (every axis <= 256)
     __nv_bfloat16 *hS[3] = {nullptr, nullptr, nullptr}, *hSt[3] = {nullptr, nullptr, nullptr};  // bf16, padded
     __nv_bfloat16 *hbuf = nullptr;               // six padded bf16 tensors (input, intermediates)
+    __nv_bfloat16 *hlo = nullptr;                // their low parts: value = hbuf + hlo (same layout)
     int64_t hoff[6] = {0, 0, 0, 0, 0, 0};
     __nv_bfloat16 *pbuf = nullptr;               // the same six tensors for pw PCG columns
     int64_t poff[6] = {0, 0, 0, 0, 0, 0};

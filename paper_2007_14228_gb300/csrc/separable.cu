@@ -99,14 +99,15 @@ bool axis_modes(const std::vector<double> &x, std::vector<double> &S, std::vecto
 }
 
 // Interior lattice tensor (a, b, c) <- the CG residual (element type E, innermost axis stored
-// with stride ldc >= nz).  With it >= 0 the CG update of iteration it is fused in first (the
+// with stride ldc >= nz; with tlo the value is split in two, t + tlo, the low part the rounding
+// error of the high one).  With it >= 0 the CG update of iteration it is fused in first (the
 // scalars protocol of the Hartree CG in fields.cu): alpha = rz/pq, U += alpha p, r -= alpha q,
 // rr' += r.r, and the next pq slot is cleared.
 template <class E>
 __global__ void __launch_bounds__(256) k_sep_gather(int nx, int ny, int nz, int ldc, int Ly, int Lz,
                                                     const double *__restrict__ pv, const double *__restrict__ qv,
-                                                    double *U, double *r, E *t, double *sc, int it, double *gpart,
-                                                    unsigned *gcount) {
+                                                    double *U, double *r, E *t, E *tlo, double *sc, int it,
+                                                    double *gpart, unsigned *gcount) {
     __shared__ double sh[8];
     __shared__ double s_alpha;
     if (threadIdx.x == 0) {
@@ -130,7 +131,9 @@ __global__ void __launch_bounds__(256) k_sep_gather(int nx, int ny, int nz, int 
             r[i] = ri;
             rr = fma(ri, ri, rr);
         }
-        t[ab * ldc + c] = (E)(float)ri;
+        const E hi = (E)(float)ri;
+        t[ab * ldc + c] = hi;
+        if (tlo) tlo[ab * ldc + c] = (E)((float)ri - (float)hi);
     }
     if (it >= 0) {
         if (threadIdx.x == 0 && blockIdx.x == 0) sc[2 + ((it + 1) & 1)] = 0.0;
@@ -139,19 +142,20 @@ __global__ void __launch_bounds__(256) k_sep_gather(int nx, int ny, int nz, int 
     }
 }
 
-// z <- the interior tensor (float64), rz[slot] += r.z; with pv also p = z (CG start)
+// z <- the interior tensor (float64; t + tlo when tlo is given), rz[slot] += r.z; with pv also
+// p = z (CG start)
 template <class E>
 __global__ void __launch_bounds__(256) k_sep_scatter(int nx, int ny, int nz, int ldc, int Ly, int Lz,
-                                                     const E *__restrict__ t, const double *__restrict__ r, double *z,
-                                                     double *pv, double *sc, int slot, double *gpart,
-                                                     unsigned *gcount) {
+                                                     const E *__restrict__ t, const E *__restrict__ tlo,
+                                                     const double *__restrict__ r, double *z, double *pv, double *sc,
+                                                     int slot, double *gpart, unsigned *gcount) {
     __shared__ double sh[8];
     const int64_t n = (int64_t)nx * ny * nz;
     double rz = 0.0;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t ab = q / nz, c = q - ab * nz, a = ab / ny, b = ab - a * ny;
         const int64_t i = ((a + 1) * Ly + (b + 1)) * Lz + (c + 1);
-        const double zi = (double)(float)t[ab * ldc + c];
+        const double zi = (double)(float)t[ab * ldc + c] + (tlo ? (double)(float)tlo[ab * ldc + c] : 0.0);
         z[i] = zi;
         if (pv) pv[i] = zi;
         rz = fma(r[i], zi, rz);
@@ -263,10 +267,12 @@ __device__ __forceinline__ void cp16(void *dst, const void *src, int src_bytes) 
 
 struct SepPass {
     const __nv_bfloat16 *A;        // M x KP row-major (zero padding beyond K)
+    const __nv_bfloat16 *Alo;      // SPLIT: the low parts of A (A + Alo is the operand)
     const __nv_bfloat16 *Bt;       // NP x KP row-major, zero padded
     int M, K, KP, N, NP, tcols;    // tcols: tensor-memory columns (power of two >= NS)
     int NS;                        // output columns per CTA (NP / gridDim.y, a multiple of 16)
     __nv_bfloat16 *out;            // element (n, m) at (n M1 + m / M2) KPo + m % M2
+    __nv_bfloat16 *outlo;          // SPLIT: the low parts of the output (same layout)
     int M1, M2, KPo;
     const float *lr, *lc;          // SCALE: multiply by f / (lr[n] + lc[m] + h_b)
     // batches of Mb rows (Mb = 0: one batch of M): row m is row m' = m mod Mb of batch
@@ -278,11 +284,13 @@ struct SepPass {
     int *err;
 };
 
-template <int SCALE>
+// SPLIT: the A operand and the output are pairs of bf16 parts (high + low), and the MMAs add
+// both parts' products with Bt, so the passes carry ~16 significant bits instead of 8
+template <int SCALE, int SPLIT>
 __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
     extern __shared__ __align__(128) unsigned char dsm[];
-    __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(dsm);     // STM x KP
-    __nv_bfloat16 *sB = sA + STM * P.KP;                             // NS x KP
+    __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(dsm);     // STM x KP (then its low part)
+    __nv_bfloat16 *sB = sA + (SPLIT ? 2 : 1) * STM * P.KP;           // NS x KP
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
@@ -310,7 +318,9 @@ __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
     for (int e = tid; e < STM * kc8; e += blockDim.x) {
         const int rr = e / kc8, k = (e - rr * kc8) * 8;
         const bool in = m0 + rr < P.M;
-        cp16(sA + coff(rr, k, P.KP), P.A + (in ? (int64_t)(m0 + rr) * P.KP + k : 0), in ? 16 : 0);
+        const int64_t off = in ? (int64_t)(m0 + rr) * P.KP + k : 0;
+        cp16(sA + coff(rr, k, P.KP), P.A + off, in ? 16 : 0);
+        if (SPLIT) cp16(sA + STM * P.KP + coff(rr, k, P.KP), P.Alo + off, in ? 16 : 0);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
     asm volatile("cp.async.wait_all;" ::: "memory");
@@ -323,15 +333,16 @@ __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(P.NS >> 3) << 17) |
                                ((uint32_t)(STM >> 4) << 24);
         const uint32_t a0 = su32(sA), b0 = su32(sB), sbo = (uint32_t)(P.KP >> 3) * 128u;
-        for (int kk = 0; kk < P.KP / 16; ++kk) {
-            const uint64_t ad = sdesc(a0 + kk * 256, 128, sbo);
-            const uint64_t bd = sdesc(b0 + kk * 256, 128, sbo);
-            const uint32_t accum = kk > 0 ? 1u : 0u;
-            asm volatile(
-                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
-        }
+        for (int part = 0; part < (SPLIT ? 2 : 1); ++part)
+            for (int kk = 0; kk < P.KP / 16; ++kk) {
+                const uint64_t ad = sdesc(a0 + (uint32_t)(part * STM * P.KP * 2) + kk * 256, 128, sbo);
+                const uint64_t bd = sdesc(b0 + kk * 256, 128, sbo);
+                const uint32_t accum = (part > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+            }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&mbar)));
     }
     uint32_t done = 0;
@@ -350,6 +361,7 @@ __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
         const int m1 = mm / P.M2, m2 = mm - m1 * P.M2;
         const float lcm = (SCALE && m < P.M) ? P.lc[mm] + (P.shd ? (float)(-2.0 * P.shd[bt]) : 0.f) : 0.f;
         __nv_bfloat16 *outb = P.out + (int64_t)bt * P.ob;
+        __nv_bfloat16 *outl = SPLIT ? P.outlo + (int64_t)bt * P.ob : nullptr;
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
         for (int cb = 0; cb < P.NS; cb += 16) {
             uint32_t v[16];
@@ -367,7 +379,10 @@ __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
                 if (n >= P.N) break;
                 float x = __uint_as_float(v[q]);
                 if (SCALE) x = __fdividef(P.f * x, P.lr[n] + lcm);
-                outb[((int64_t)n * P.M1 + m1) * P.KPo + m2] = __float2bfloat16(x);
+                const int64_t o = ((int64_t)n * P.M1 + m1) * P.KPo + m2;
+                const __nv_bfloat16 hi = __float2bfloat16(x);
+                outb[o] = hi;
+                if (SPLIT) outl[o] = __float2bfloat16(x - __bfloat162float(hi));
             }
         }
     }
@@ -378,7 +393,7 @@ __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P.tcols));
 }
 
-template <int SCALE>
+template <int SCALE, int SPLIT = 0>
 void sep_tc_launch(ofks_ctx *c, SepPass P) {
     // the output columns split over gridDim.y CTAs (each a multiple of 16) until the grid covers
     // the 152 SMs: the passes are latency-bound, and short axes give few 128-row tiles
@@ -397,11 +412,11 @@ void sep_tc_launch(ofks_ctx *c, SepPass P) {
     P.err = c->d_flag + 1;
     // shared memory of at least 228 KB * tcols / 512 per CTA keeps the CTAs resident on one SM
     // within its 512 tensor-memory columns, so no allocation ever has to wait
-    const int need = (STM + P.NS) * P.KP * (int)sizeof(__nv_bfloat16);
+    const int need = ((SPLIT ? 2 : 1) * STM + P.NS) * P.KP * (int)sizeof(__nv_bfloat16);
     const int floor_ = 228 * 1024 / (512 / P.tcols) + 1024;
     const int smem = std::min(227 * 1024, std::max(need, floor_));
-    cudaFuncSetAttribute(k_sep_tc<SCALE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_sep_tc<SCALE><<<dim3((unsigned)ctas, (unsigned)d), 128, smem, c->stream>>>(P);
+    cudaFuncSetAttribute(k_sep_tc<SCALE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_sep_tc<SCALE, SPLIT><<<dim3((unsigned)ctas, (unsigned)d), 128, smem, c->stream>>>(P);
     c->kernels += 1;
 }
 
@@ -413,7 +428,7 @@ void sep_free(ofks_ctx *c) {
     for (float *p : {S.S[0], S.S[1], S.S[2], S.St[0], S.St[1], S.St[2], S.lx, S.lyz, S.t0, S.t1})
         if (p) cudaFree(p);
     for (void *p : {(void *)S.hS[0], (void *)S.hS[1], (void *)S.hS[2], (void *)S.hSt[0], (void *)S.hSt[1],
-                    (void *)S.hSt[2], (void *)S.hbuf, (void *)S.pbuf})
+                    (void *)S.hSt[2], (void *)S.hbuf, (void *)S.hlo, (void *)S.pbuf})
         if (p) cudaFree(p);
     S = SepState{};
 }
@@ -490,6 +505,8 @@ int sep_setup(ofks_ctx *c, const double *xyz, const uint8_t *dirichlet) {
         for (int q = 0; q < 6; ++q) { S.hoff[q] = tot; tot += (len[q] + 63) / 64 * 64; }
         if (e == cudaSuccess) e = cudaMalloc((void **)&S.hbuf, sizeof(__nv_bfloat16) * tot);
         if (e == cudaSuccess) e = cudaMemset(S.hbuf, 0, sizeof(__nv_bfloat16) * tot);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&S.hlo, sizeof(__nv_bfloat16) * tot);
+        if (e == cudaSuccess) e = cudaMemset(S.hlo, 0, sizeof(__nv_bfloat16) * tot);
     }
     if (e == cudaSuccess) e = cudaMalloc((void **)&S.t0, sizeof(float) * nt);
     if (e == cudaSuccess) e = cudaMalloc((void **)&S.t1, sizeof(float) * nt);
@@ -515,40 +532,41 @@ void sep_cg_step(ofks_ctx *c, int it, int slot, int first) {
     const unsigned g = (unsigned)std::min<int64_t>((nt + 255) / 256, 152 * 8);
     double *sc = c->d_sc + SC_CG;
     if (S.tc && c->prm.poisson_sep_tc) {
+        // every tensor as a high and a low bf16 part: the rounding of the intermediates to 8 bits
+        // made the preconditioner visibly nonlinear and cost the CG about a quarter more iterations
         const int px = pad16(nx), py = pad16(ny), pz = pad16(nz);
-        __nv_bfloat16 *B[6];
-        for (int q = 0; q < 6; ++q) B[q] = S.hbuf + S.hoff[q];
+        __nv_bfloat16 *B[6], *Bl[6];
+        for (int q = 0; q < 6; ++q) { B[q] = S.hbuf + S.hoff[q]; Bl[q] = S.hlo + S.hoff[q]; }
         SepPass P{};
         P.f = 1.f;
-        auto pass = [&](const __nv_bfloat16 *A, const __nv_bfloat16 *Bt, int M, int K, int N, __nv_bfloat16 *out,
-                        int M1, int M2, int KPo) {
-            P.A = A; P.Bt = Bt; P.M = M; P.K = K; P.KP = pad16(K); P.N = N; P.NP = pad16(N);
-            P.out = out; P.M1 = M1; P.M2 = M2; P.KPo = KPo;
+        auto pass = [&](int q, const __nv_bfloat16 *Bt, int M, int K, int N, int qo, int M1, int M2, int KPo) {
+            P.A = B[q]; P.Alo = Bl[q]; P.Bt = Bt; P.M = M; P.K = K; P.KP = pad16(K); P.N = N; P.NP = pad16(N);
+            P.out = B[qo]; P.outlo = Bl[qo]; P.M1 = M1; P.M2 = M2; P.KPo = KPo;
         };
         k_sep_gather<__nv_bfloat16><<<g, 256, 0, c->stream>>>(nx, ny, nz, pz, c->st.Ly, c->st.Lz, c->d_cp, c->d_cq,
-                                                              c->d_U, c->d_cr, B[0], sc, it, c->d_gpart,
+                                                              c->d_U, c->d_cr, B[0], Bl[0], sc, it, c->d_gpart,
                                                               c->d_gcount);
-        pass(B[0], S.hSt[2], nx * ny, nz, nz, B[1], nx, ny, py);           // [a][b][c] -> [k][a][b]
-        sep_tc_launch<0>(c, P);
-        pass(B[1], S.hSt[1], nz * nx, ny, ny, B[2], nz, nx, px);           // -> [j][k][a]
-        sep_tc_launch<0>(c, P);
-        pass(B[2], S.hSt[0], ny * nz, nx, nx, B[3], ny, nz, pz);           // -> [i][j][k] / lam
+        pass(0, S.hSt[2], nx * ny, nz, nz, 1, nx, ny, py);                 // [a][b][c] -> [k][a][b]
+        sep_tc_launch<0, 1>(c, P);
+        pass(1, S.hSt[1], nz * nx, ny, ny, 2, nz, nx, px);                 // -> [j][k][a]
+        sep_tc_launch<0, 1>(c, P);
+        pass(2, S.hSt[0], ny * nz, nx, nx, 3, ny, nz, pz);                 // -> [i][j][k] / lam
         P.lr = S.lx; P.lc = S.lyz;
-        sep_tc_launch<1>(c, P);
-        pass(B[3], S.hS[2], nx * ny, nz, nz, B[4], nx, ny, py);            // -> [c][i][j]
-        sep_tc_launch<0>(c, P);
-        pass(B[4], S.hS[1], nz * nx, ny, ny, B[5], nz, nx, px);            // -> [b][c][i]
-        sep_tc_launch<0>(c, P);
-        pass(B[5], S.hS[0], ny * nz, nx, nx, B[0], ny, nz, pz);            // -> [a][b][c]
-        sep_tc_launch<0>(c, P);
-        k_sep_scatter<__nv_bfloat16><<<g, 256, 0, c->stream>>>(nx, ny, nz, pz, c->st.Ly, c->st.Lz, B[0], c->d_cr,
-                                                               c->d_cz, first ? c->d_cp : nullptr, sc, slot,
+        sep_tc_launch<1, 1>(c, P);
+        pass(3, S.hS[2], nx * ny, nz, nz, 4, nx, ny, py);                  // -> [c][i][j]
+        sep_tc_launch<0, 1>(c, P);
+        pass(4, S.hS[1], nz * nx, ny, ny, 5, nz, nx, px);                  // -> [b][c][i]
+        sep_tc_launch<0, 1>(c, P);
+        pass(5, S.hS[0], ny * nz, nx, nx, 0, ny, nz, pz);                  // -> [a][b][c]
+        sep_tc_launch<0, 1>(c, P);
+        k_sep_scatter<__nv_bfloat16><<<g, 256, 0, c->stream>>>(nx, ny, nz, pz, c->st.Ly, c->st.Lz, B[0], Bl[0],
+                                                               c->d_cr, c->d_cz, first ? c->d_cp : nullptr, sc, slot,
                                                                c->d_gpart, c->d_gcount);
         c->kernels += 2;
         return;
     }
     k_sep_gather<float><<<g, 256, 0, c->stream>>>(nx, ny, nz, nz, c->st.Ly, c->st.Lz, c->d_cp, c->d_cq, c->d_U,
-                                                  c->d_cr, S.t0, sc, it, c->d_gpart, c->d_gcount);
+                                                  c->d_cr, S.t0, nullptr, sc, it, c->d_gpart, c->d_gcount);
     // forward: T1[ab][k] = sum_c R[ab][c] Sz[c][k]
     gemm(c, 1, nx * ny, nz, nz, S.t0, 0, S.S[2], 0, S.t1, 0);
     // T2[a][j][k] = sum_b Sy^T[j][b] T1[a][b][k]
@@ -561,7 +579,7 @@ void sep_cg_step(ofks_ctx *c, int it, int slot, int first) {
     gemm(c, nx, ny, nz, ny, S.S[1], 0, S.t0, (int64_t)ny * nz, S.t1, (int64_t)ny * nz);
     // Z[ab][c] = sum_k U2[ab][k] Sz^T[k][c]
     gemm(c, 1, nx * ny, nz, nz, S.t1, 0, S.St[2], 0, S.t0, 0);
-    k_sep_scatter<float><<<g, 256, 0, c->stream>>>(nx, ny, nz, nz, c->st.Ly, c->st.Lz, S.t0, c->d_cr, c->d_cz,
+    k_sep_scatter<float><<<g, 256, 0, c->stream>>>(nx, ny, nz, nz, c->st.Ly, c->st.Lz, S.t0, nullptr, c->d_cr, c->d_cz,
                                                    first ? c->d_cp : nullptr, sc, slot, c->d_gpart, c->d_gcount);
     c->kernels += 2;
 }

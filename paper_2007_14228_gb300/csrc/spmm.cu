@@ -312,7 +312,7 @@ inline int chunk_width(int ld) { return (ld % 4 == 0) ? 4 : (ld % 2 == 0 ? 2 : 1
 // are loaded together.  The result rows leave through a tile as whole-row coalesced stores.
 // MODE 1 also forms the column sums X[r,c] Y[r,c] of the slice (per warp, in lane order) into
 // part[c * n_slices + slice].
-constexpr int WS_WARPS = 4;                       // warps per block
+constexpr int WS_WARPS = 2;                       // warps per block
 constexpr int WS_STAGES = 3;                      // tiles in flight per warp
 constexpr int WS_BATCH = 8;                       // entries whose column ids and values load together
 

@@ -419,8 +419,9 @@ def test_hartree_on_renumbered_mesh_uses_csr(ofks, pc, used):
 
 @pytest.mark.parametrize("case", ["lih10", "chain_p41"])
 def test_separable_preconditioner_tensor_cores_match_cuda_cores(ofks, case):
-    # the bf16 tensor-core contractions and the float32 CUDA-core ones precondition the same CG:
-    # both reach the oracle's potential in nearly the same number of iterations
+    # the tensor-core contractions (bf16 operands, every intermediate tensor as a high and a low
+    # bf16 part) and the float32 CUDA-core ones precondition the same CG: both reach the oracle's
+    # potential in nearly the same number of iterations
     s = CASES[case]()
     iters = {}
     for tc in (1, 0):

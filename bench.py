@@ -179,12 +179,13 @@ def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, spmv_model=(0, 0), ele
     Every family is one kernel launch per timed scope except "poisson" (the whole Hartree
     solve), "poisson_vec" (two vector kernels per CG iteration), "poisson_pc" (one application of
     the Hartree CG's preconditioner: the CG update with the gather, six contractions, the scatter),
-    "gcn" (one application of the learned preconditioner's network, a dozen kernels) and
-    "pcg_sep" (the same separable application inside the PCG), which are left out of the choice;
+    "gcn" (one application of the learned preconditioner's network, a dozen kernels), "judge"
+    (the product T D of the network's directions and their residual sums) and "pcg_sep" (the
+    same separable application inside the PCG), which are left out of the choice;
     the solve's SpMV kernel is the "poisson_spmv" family.  The PCG apply works on the
     active columns only (their count rounded up to 4): pcg_w is its mean block width over the
     timed launches."""
-    multi = ("poisson", "poisson_vec", "poisson_pc", "gcn", "pcg_sep")
+    multi = ("poisson", "poisson_vec", "poisson_pc", "gcn", "pcg_sep", "judge")
     leaves = {k: v for k, v in prof.items() if k not in multi and v["launches"]}
     fam = max(leaves, key=lambda k: leaves[k]["ms"])
     st = prof[fam]

@@ -22,7 +22,8 @@
 
 static const char *kPfNames[PF_COUNT] = {"density", "poisson", "potential", "spmm_h", "gram", "small",
                                          "grad", "pcg_spmm", "pcg_update", "bb", "step", "spmm_b", "other",
-                                         "poisson_spmv", "gcn", "poisson_vec", "poisson_pc", "pcg_sep"};
+                                         "poisson_spmv", "gcn", "poisson_vec", "poisson_pc", "pcg_sep",
+                                         "judge"};
 
 int ofks_fail(ofks_ctx *c, int code, const char *fmt, ...) {
     char buf[512];
@@ -418,11 +419,12 @@ static int precondition_t(ofks_ctx *c) {
         if (rc) return rc;
         c->learned_calls++;
         {
-            ProfScope ps(c, PF_PCG_SPMM);
+            // the network's directions judged: T D on every column, then the residual sums
+            ProfScope ps(c, PF_JUDGE);
             launch_pcg_apply(c, vals_L<T>(c), vals_B<T>(c), (const T *)D, 0, b.P, b.Q, c->d_colA + CB_BETA * ld,
                              c->d_colA + CB_SHIFT * ld, c->d_colA + CB_PQ * ld, 1, ld, c->p);
+            launch_judge(c, b);
         }
-        launch_judge(c, b);
         std::vector<double> h(3 * (size_t)ld);
         cudaMemcpyAsync(h.data(), c->d_colA + CB_RZ * ld, sizeof(double) * 3 * ld, cudaMemcpyDeviceToHost, c->stream);
         cudaError_t e = cudaStreamSynchronize(c->stream);

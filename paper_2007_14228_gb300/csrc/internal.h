@@ -37,7 +37,7 @@ enum { CB_SHIFT = 0, CB_ACTIVE = 1, CB_RZ = 2, CB_RZN = 3, CB_PQ = 4, CB_BETA = 
 enum {
     PF_DENSITY = 0, PF_POISSON, PF_POTENTIAL, PF_SPMM_H, PF_GRAM, PF_SMALL, PF_GRAD,
     PF_PCG_SPMM, PF_PCG_UPDATE, PF_BB, PF_STEP, PF_SPMM_B, PF_OTHER, PF_POISSON_SPMV, PF_GCN, PF_POISSON_VEC, PF_POISSON_PC,
-    PF_PCG_SEP, PF_COUNT
+    PF_PCG_SEP, PF_JUDGE, PF_COUNT
 };
 
 // one level of the algebraic multigrid hierarchy of the Hartree Poisson operator (device CSR)

@@ -606,23 +606,25 @@ bool sep_pcg_ready(ofks_ctx *c, int w) {
     const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
     const int64_t len[6] = {(int64_t)nx * ny * pad16(nz), (int64_t)nz * nx * pad16(ny), (int64_t)ny * nz * pad16(nx),
                             (int64_t)nx * ny * pad16(nz), (int64_t)nz * nx * pad16(ny), (int64_t)ny * nz * pad16(nx)};
-    int64_t tot = 0;
-    for (int q = 0; q < 6; ++q) { S.poff[q] = tot; tot += (len[q] * w + 63) / 64 * 64; }
+    // room for the widest block (ld columns) at once, so that a growing active set neither
+    // reallocates (a device-wide synchronization) nor invalidates the captured PCG graphs; the
+    // exact width when that does not fit
+    for (const int wa : {std::max(w, c->ld), w}) {
+        int64_t tot = 0;
+        for (int q = 0; q < 6; ++q) { S.poff[q] = tot; tot += (len[q] * wa + 63) / 64 * 64; }
+        if (cudaMalloc((void **)&S.pbuf, sizeof(__nv_bfloat16) * tot) == cudaSuccess) {
+            if (cudaMemset(S.pbuf, 0, sizeof(__nv_bfloat16) * tot) == cudaSuccess) {
+                S.pw = wa;
+                return true;
+            }
+            cudaFree(S.pbuf);
+        }
+        cudaGetLastError();
+        S.pbuf = nullptr;
+    }
     // without room for the buffers the PCG keeps the Jacobi preconditioner (the failed call's
     // error is cleared so that no later check reports it)
-    if (cudaMalloc((void **)&S.pbuf, sizeof(__nv_bfloat16) * tot) != cudaSuccess) {
-        cudaGetLastError();
-        S.pbuf = nullptr;
-        return false;
-    }
-    if (cudaMemset(S.pbuf, 0, sizeof(__nv_bfloat16) * tot) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(S.pbuf);
-        S.pbuf = nullptr;
-        return false;
-    }
-    S.pw = w;
-    return true;
+    return false;
 }
 
 // z = T_sep^-1 r for the w columns in the input tensor (buffer 0, [b][a][b][c~]), result in the

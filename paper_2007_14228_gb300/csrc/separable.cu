@@ -281,22 +281,32 @@ struct SepPass {
     int64_t ob;
     const double *shd;
     float f;
+    int nst;                       // A stages in shared memory (1 or 2)
     int *err;
 };
 
 // SPLIT: the A operand and the output are pairs of bf16 parts (high + low), and the MMAs add
-// both parts' products with Bt, so the passes carry ~16 significant bits instead of 8
+// both parts' products with Bt, so the passes carry ~16 significant bits instead of 8.
+//
+// Persistent: CTA (x, y) takes the 128-row tiles x, x + gridDim.x, ... of output columns
+// [y NS, (y + 1) NS).  Bt's NS x KP slice is loaded once; the A tiles go through P.nst stages
+// (two: the next tile's copies are issued before this tile's MMAs, so they overlap the MMAs and
+// the epilogue; one: issued once this tile's MMAs are done, overlapping the epilogue).  One
+// thread issues each tile's MMAs into the tensor-memory accumulator and commits them to the
+// mbarrier (one phase per tile); the four warps read their 32 rows back after the wait.
 template <int SCALE, int SPLIT>
 __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
     extern __shared__ __align__(128) unsigned char dsm[];
-    __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(dsm);     // STM x KP (then its low part)
-    __nv_bfloat16 *sB = sA + (SPLIT ? 2 : 1) * STM * P.KP;           // NS x KP
+    constexpr int NA = SPLIT ? 2 : 1;                                // parts of A
+    const int KP = P.KP, kc8 = KP >> 3;
+    __nv_bfloat16 *sB = reinterpret_cast<__nv_bfloat16 *>(dsm);     // NS x KP
+    __nv_bfloat16 *sA = sB + P.NS * KP;                              // nst stages of NA x STM x KP
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * STM;
     const int n0 = blockIdx.y * P.NS;                                // this CTA's output columns
+    const int ntiles = (P.M + STM - 1) / STM;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
@@ -308,55 +318,77 @@ __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
         asm volatile("fence.mbarrier_init.release.cluster;");
         abort_flag = 0;
     }
-    // operands: rows of 8 elements (16 B) copied asynchronously into their core-matrix rows,
-    // all of a thread's copies in flight at once
-    const int kc8 = P.KP >> 3;
+    // operands: rows of 8 elements (16 B) copied asynchronously into their core-matrix rows
+    auto load_a = [&](int tile, int stage) {
+        const int m0 = tile * STM;
+        __nv_bfloat16 *dst = sA + (size_t)stage * NA * STM * KP;
+        for (int e = tid; e < STM * kc8; e += blockDim.x) {
+            const int rr = e / kc8, k = (e - rr * kc8) * 8;
+            const bool in = m0 + rr < P.M;
+            const int64_t off = in ? (int64_t)(m0 + rr) * KP + k : 0;
+            cp16(dst + coff(rr, k, KP), P.A + off, in ? 16 : 0);
+            if (SPLIT) cp16(dst + STM * KP + coff(rr, k, KP), P.Alo + off, in ? 16 : 0);
+        }
+    };
     for (int e = tid; e < P.NS * kc8; e += blockDim.x) {
         const int n = e / kc8, k = (e - n * kc8) * 8;
-        cp16(sB + coff(n, k, P.KP), P.Bt + (int64_t)(n0 + n) * P.KP + k, 16);
+        cp16(sB + coff(n, k, KP), P.Bt + (int64_t)(n0 + n) * KP + k, 16);
     }
-    for (int e = tid; e < STM * kc8; e += blockDim.x) {
-        const int rr = e / kc8, k = (e - rr * kc8) * 8;
-        const bool in = m0 + rr < P.M;
-        const int64_t off = in ? (int64_t)(m0 + rr) * P.KP + k : 0;
-        cp16(sA + coff(rr, k, P.KP), P.A + off, in ? 16 : 0);
-        if (SPLIT) cp16(sA + STM * P.KP + coff(rr, k, P.KP), P.Alo + off, in ? 16 : 0);
-    }
+    int tile = blockIdx.x;
+    if (tile < ntiles) load_a(tile, 0);
     asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
-    if (tid == 0) {
-        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(P.NS >> 3) << 17) |
-                               ((uint32_t)(STM >> 4) << 24);
-        const uint32_t a0 = su32(sA), b0 = su32(sB), sbo = (uint32_t)(P.KP >> 3) * 128u;
-        for (int part = 0; part < (SPLIT ? 2 : 1); ++part)
-            for (int kk = 0; kk < P.KP / 16; ++kk) {
-                const uint64_t ad = sdesc(a0 + (uint32_t)(part * STM * P.KP * 2) + kk * 256, 128, sbo);
-                const uint64_t bd = sdesc(b0 + kk * 256, 128, sbo);
-                const uint32_t accum = (part > 0 || kk > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
-            }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&mbar)));
-    }
-    uint32_t done = 0;
-    for (long long w = 0; w < SEP_WAIT && !done; ++w) {
-        asm volatile(
-            "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
-            : "=r"(done)
-            : "r"(su32(&mbar)), "r"(0u));
-    }
-    if (!done) abort_flag = 1;
-    __syncthreads();
-    if (!abort_flag) {
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(P.NS >> 3) << 17) |
+                           ((uint32_t)(STM >> 4) << 24);
+    const uint32_t sbo = (uint32_t)kc8 * 128u;
+    for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
+        const int st = P.nst == 2 ? (i & 1) : 0;
+        const int next = tile + gridDim.x;
+        if (P.nst == 2) {
+            if (next < ntiles) load_a(next, st ^ 1);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const int m = m0 + warp * 32 + lane;
+        if (tid == 0) {
+            const uint32_t a0 = su32(sA + (size_t)st * NA * STM * KP), b0 = su32(sB);
+            for (int part = 0; part < NA; ++part)
+                for (int kk = 0; kk < KP / 16; ++kk) {
+                    const uint64_t ad = sdesc(a0 + (uint32_t)(part * STM * KP * 2) + kk * 256, 128, sbo);
+                    const uint64_t bd = sdesc(b0 + kk * 256, 128, sbo);
+                    const uint32_t accum = (part > 0 || kk > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                su32(&mbar)));
+        }
+        uint32_t done = 0;
+        for (long long w = 0; w < SEP_WAIT && !done; ++w) {
+            asm volatile(
+                "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
+                : "=r"(done)
+                : "r"(su32(&mbar)), "r"((uint32_t)(i & 1)));
+        }
+        if (!done) abort_flag = 1;
+        __syncthreads();
+        if (abort_flag) break;                                       // uniform: read after the barrier
+        if (P.nst == 1) {                                            // the stage is free again
+            if (next < ntiles) load_a(next, 0);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int m = tile * STM + warp * 32 + lane;
         const int bt = P.Mb ? m / P.Mb : 0, mm = m - bt * P.Mb;
         const int m1 = mm / P.M2, m2 = mm - m1 * P.M2;
         const float lcm = (SCALE && m < P.M) ? P.lc[mm] + (P.shd ? (float)(-2.0 * P.shd[bt]) : 0.f) : 0.f;
@@ -385,8 +417,11 @@ __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
                 if (SPLIT) outl[o] = __float2bfloat16(x - __bfloat162float(hi));
             }
         }
+        // the accumulator is read: the next tile's MMAs (issued after the next barrier) may overwrite it
+        asm volatile("tcgen05.fence::before_thread_sync;");
     }
     if (abort_flag && tid == 0) atomicExch(P.err, 1);
+    asm volatile("cp.async.wait_all;" ::: "memory");                 // no copy left in flight
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0)
@@ -395,28 +430,41 @@ __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
 
 template <int SCALE, int SPLIT = 0>
 void sep_tc_launch(ofks_ctx *c, SepPass P) {
-    // the output columns split over gridDim.y CTAs (each a multiple of 16) until the grid covers
-    // the 152 SMs: the passes are latency-bound, and short axes give few 128-row tiles
-    const int ctas = (P.M + STM - 1) / STM, nb = P.NP / 16;
+    // the output columns split over gridDim.y (each a multiple of 16) until the tiles cover the
+    // 152 SMs: the passes are latency-bound, and short axes give few 128-row tiles
+    const int tiles = (P.M + STM - 1) / STM, nb = P.NP / 16;
     int d = 1;
     for (int cand = 1; cand <= nb; ++cand) {
         if (nb % cand) continue;
         d = cand;
-        // enough CTAs for the SMs, and at most 128 output columns per CTA: 128 tensor-memory
-        // columns let three CTAs share an SM (256 would leave it one, with nothing to overlap its
-        // tile loads with another CTA's MMAs and epilogue)
-        if ((int64_t)ctas * cand >= 152 && P.NP / cand <= 128) break;
+        // enough tiles for the SMs, and at most 128 output columns per CTA: 128 tensor-memory
+        // columns let several CTAs share an SM
+        if ((int64_t)tiles * cand >= 152 && P.NP / cand <= 128) break;
     }
     P.NS = P.NP / d;
     P.tcols = P.NS <= 32 ? 32 : (P.NS <= 64 ? 64 : (P.NS <= 128 ? 128 : 256));
     P.err = c->d_flag + 1;
+    const int NA = SPLIT ? 2 : 1, kmax = 227 * 1024;
     // shared memory of at least 228 KB * tcols / 512 per CTA keeps the CTAs resident on one SM
     // within its 512 tensor-memory columns, so no allocation ever has to wait
-    const int need = ((SPLIT ? 2 : 1) * STM + P.NS) * P.KP * (int)sizeof(__nv_bfloat16);
     const int floor_ = 228 * 1024 / (512 / P.tcols) + 1024;
-    const int smem = std::min(227 * 1024, std::max(need, floor_));
+    auto need = [&](int nst) { return (P.NS + nst * NA * STM) * P.KP * (int)sizeof(__nv_bfloat16); };
+    auto smem_for = [&](int nst) { return std::min(kmax, std::max(need(nst), floor_)); };
+    // persistent CTAs: one wave over the SMs, each walking its share of the tiles
+    auto grid_for = [&](int smem) {
+        const int per_sm = std::max(1, std::min(512 / P.tcols, 228 * 1024 / (smem + 1024)));
+        return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (152LL * per_sm + d - 1) / d));
+    };
+    // a second A stage only where a CTA has more than one tile (it costs residency)
+    P.nst = 1;
+    int smem = smem_for(1), gx = grid_for(smem);
+    if (tiles > gx && need(2) <= kmax) {
+        P.nst = 2;
+        smem = smem_for(2);
+        gx = grid_for(smem);
+    }
     cudaFuncSetAttribute(k_sep_tc<SCALE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_sep_tc<SCALE, SPLIT><<<dim3((unsigned)ctas, (unsigned)d), 128, smem, c->stream>>>(P);
+    k_sep_tc<SCALE, SPLIT><<<dim3((unsigned)gx, (unsigned)d), 128, smem, c->stream>>>(P);
     c->kernels += 1;
 }
 

@@ -165,12 +165,12 @@ def poisson_spmv_model(sizes, pinfo):
 
 
 # DRAM bytes per algorithmic byte of the float32 PCG apply (k_pcg_apply_zc), measured by ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum) on the chain at 60 x 32 x 30 cells: 418.2 MB per
-# launch at n = 442,323, width 24 and 12,201,095 stored entries, whose algorithmic bytes are
-# 12 nnz + 20 n w = 358.7 MB.  The 80 x 44 x 43 workload is too large for that capture, so its
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the chain at 60 x 32 x 30 cells: 380.0 MB per
+# launch at n = 442,323, width 28 and 12,201,095 stored entries, whose algorithmic bytes are
+# 12 nnz + 20 n w = 394.1 MB.  The 80 x 44 x 43 workload is too large for that capture, so its
 # traffic is this ratio times its own algorithmic bytes (the column ids, values and the Z, P, Q
 # pieces all grow with the launch).
-PCG_F32_DRAM_PER_ALG = 418.2e6 / (12 * 12201095 + 20 * 442323 * 24)
+PCG_F32_DRAM_PER_ALG = 380.0e6 / (12 * 12201095 + 20 * 442323 * 28)
 
 
 def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, spmv_model=(0, 0), elem=8, pcg_w=None):

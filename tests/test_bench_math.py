@@ -21,7 +21,7 @@ def test_pcg_roofline_is_algorithmic_bytes_over_launch_time():
     assert r["achieved"] == pytest.approx(alg / per / 1e9, abs=0.05)
     assert r["frac"] == pytest.approx(r["achieved"] / 6756.8, abs=1e-4)
     assert r["traffic"] == int(alg * bench.PCG_F32_DRAM_PER_ALG)
-    assert 1.0 < bench.PCG_F32_DRAM_PER_ALG < 1.3    # the mid-size capture moved 1.17x its algorithmic bytes
+    assert 0.9 < bench.PCG_F32_DRAM_PER_ALG < 1.1    # the mid-size capture moved 0.96x its algorithmic bytes
 
 
 def test_float64_pcg_roofline_is_against_the_fp64_rate():

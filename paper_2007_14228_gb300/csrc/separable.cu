@@ -344,6 +344,7 @@ __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(P.NS >> 3) << 17) |
                            ((uint32_t)(STM >> 4) << 24);
     const uint32_t sbo = (uint32_t)kc8 * 128u;
+    int last = -1;                                                   // iteration of the last commit
     for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
         const int st = P.nst == 2 ? (i & 1) : 0;
         const int next = tile + gridDim.x;
@@ -373,6 +374,7 @@ __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 su32(&mbar)));
         }
+        last = i;
         uint32_t done = 0;
         for (long long w = 0; w < SEP_WAIT && !done; ++w) {
             asm volatile(
@@ -420,7 +422,17 @@ __global__ void __launch_bounds__(128, 1) k_sep_tc(const SepPass P) {
         // the accumulator is read: the next tile's MMAs (issued after the next barrier) may overwrite it
         asm volatile("tcgen05.fence::before_thread_sync;");
     }
-    if (abort_flag && tid == 0) atomicExch(P.err, 1);
+    if (abort_flag && tid == 0) {
+        atomicExch(P.err, 1);
+        // the MMAs of the last commit may still be running: wait for them once more (bounded)
+        // before the tensor memory is released
+        uint32_t done = 0;
+        for (long long w = 0; w < SEP_WAIT && !done && last >= 0; ++w)
+            asm volatile(
+                "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
+                : "=r"(done)
+                : "r"(su32(&mbar)), "r"((uint32_t)(last & 1)));
+    }
     asm volatile("cp.async.wait_all;" ::: "memory");                 // no copy left in flight
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();

@@ -44,7 +44,9 @@ def test_multi_kernel_families_are_not_the_dominant_kernel():
     # the Hartree preconditioner's scope (gather, six contractions, scatter) outweighs every
     # single kernel here, but the roofline names the largest one-launch family, the SpMM of B
     prof = {"poisson_pc": {"ms": 9.0, "launches": 76}, "spmm_b": {"ms": 8.6, "launches": 10},
-            "spmm_h": {"ms": 7.3, "launches": 10}, "pcg_sep": {"ms": 5.7, "launches": 10}}
+            "spmm_h": {"ms": 7.3, "launches": 10}, "pcg_sep": {"ms": 5.7, "launches": 10},
+            "gcn": {"ms": 35.0, "launches": 2}, "judge": {"ms": 9.9, "launches": 2},
+            "poisson": {"ms": 20.0, "launches": 10}}
     r = bench.roofline(prof, 1175805, 41, 32817315, 908160, 6756.8, "measured", elem=4)
     assert r["kernel"] == "spmm_b"
     alg = (4 + 4) * 32817315 + 3 * 4 * 1175805 * 41

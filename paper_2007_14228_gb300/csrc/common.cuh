@@ -9,6 +9,12 @@
 // Rows per SELL slice (one warp covers the rows of a slice).
 #define SELL_C 32
 
+// a float64 value as the float32 pair (hi, lo) with hi + lo ~ v to ~48 significant bits
+__device__ __forceinline__ float2 ff_split(double v) {
+    const float hi = __double2float_rn(v);
+    return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

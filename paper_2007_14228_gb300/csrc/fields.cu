@@ -389,7 +389,8 @@ __global__ void __launch_bounds__(256) k_cg_rz(int64_t N, const double *__restri
 }
 
 // beta = rz'/rz; p = z + beta p
-__global__ void k_cg_dir(int64_t N, const double *__restrict__ z, double *pv, const double *sc, int it) {
+// p = z + beta p (beta = rz'/rz); with pf also p as float32 pairs
+__global__ void k_cg_dir(int64_t N, const double *__restrict__ z, double *pv, float2 *pf, const double *sc, int it) {
     __shared__ double s_beta;
     if (threadIdx.x == 0) {
         const double rz = sc[it & 1], rz2 = sc[(it + 1) & 1];
@@ -397,8 +398,11 @@ __global__ void k_cg_dir(int64_t N, const double *__restrict__ z, double *pv, co
     }
     __syncthreads();
     const double beta = s_beta;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        pv[i] = z[i] + beta * pv[i];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = z[i] + beta * pv[i];
+        pv[i] = v;
+        if (pf) pf[i] = ff_split(v);
+    }
 }
 
 // Per tetrahedron: V_H(x_q) from the nodal U, LDA at rho_q, V_q = V_ext + V_H + V_xc, the
@@ -579,6 +583,9 @@ int run_hartree(ofks_ctx *c) {
     };
     const bool sep = pc == OFKS_HPC_SEPARABLE;
     const bool lat = c->st.on && !c->prm.poisson_csr;
+    // during the float32 iterations the lattice SpMV of the separable CG runs in float-float
+    // arithmetic (~48 bits, its tolerance is at least poisson_tol_mixed); float64 otherwise
+    c->hartree_ff = sep && lat && c->phase == 32 && c->st.valff != nullptr;
     auto spmv = [&](int it) {
         ProfScope pv(c, PF_POISSON_SPMV);
         if (lat) { launch_stencil_spmv(c, c->d_cp, c->d_cq, sc, it); return; }
@@ -637,15 +644,16 @@ int run_hartree(ofks_ctx *c) {
             // `chunk` CG iterations between residual checks; their kernels use the iteration
             // number only through its parity (it >= 0), so one captured graph per chunk length
             // and parity of its first iteration serves every chunk
-            struct Chunk { ofks_ctx *c; int it0, n; bool lat; unsigned gN, gU; int64_t N; double *sc; };
-            Chunk C{c, it, chunk, lat, gN, gU, N, sc};
+            struct Chunk { ofks_ctx *c; int it0, n; bool lat, ff; unsigned gN, gU; int64_t N; double *sc; };
+            Chunk C{c, it, chunk, lat, c->hartree_ff, gN, gU, N, sc};
             auto body = [](void *a) {
                 Chunk &K = *static_cast<Chunk *>(a);
                 ofks_ctx *c = K.c;
                 for (int it = K.it0; it < K.it0 + K.n; ++it) {
                     {
                         ProfScope pv(c, PF_POISSON_SPMV);
-                        if (K.lat) launch_stencil_spmv(c, c->d_cp, c->d_cq, K.sc, it);
+                        if (K.ff) launch_stencil_spmv_ff(c, c->d_cpff, c->d_cp, c->d_cq, K.sc, it);
+                        else if (K.lat) launch_stencil_spmv(c, c->d_cp, c->d_cq, K.sc, it);
                         else {
                             k_cg_spmv<<<K.gN, 256, 0, c->stream>>>(K.N, c->d_fptr, c->d_fcol, c->d_fval, c->d_minv,
                                                                    c->d_cp, c->d_cq, K.sc, it, c->d_gpart,
@@ -659,13 +667,14 @@ int run_hartree(ofks_ctx *c) {
                     }
                     {
                         ProfScope pu(c, PF_POISSON_VEC);
-                        k_cg_dir<<<K.gU, 256, 0, c->stream>>>(K.N, c->d_cz, c->d_cp, K.sc, it);
+                        k_cg_dir<<<K.gU, 256, 0, c->stream>>>(K.N, c->d_cz, c->d_cp, K.ff ? c->d_cpff : nullptr, K.sc, it);
                     }
                     c->kernels += 1;
                 }
             };
             int rc;
-            if ((rc = run_graph(c, {2, chunk, it & 1, lat ? 1 : 0, (c->sep.tc && c->prm.poisson_sep_tc) ? 1 : 0},
+            if ((rc = run_graph(c, {2, chunk, it & 1, lat ? 1 : 0, (c->sep.tc && c->prm.poisson_sep_tc) ? 1 : 0,
+                                    c->hartree_ff ? 1 : 0},
                                 body, &C)))
                 return rc;
             it += chunk;
@@ -682,7 +691,7 @@ int run_hartree(ofks_ctx *c) {
                 ProfScope pu(c, PF_POISSON_VEC);
                 k_cg_rz<<<gU, 256, 0, c->stream>>>(N, c->d_cr, c->d_cz, c->d_cp, sc, (it + 1) & 1, 0, c->d_gpart,
                                                    c->d_gcount);
-                k_cg_dir<<<gU, 256, 0, c->stream>>>(N, c->d_cz, c->d_cp, sc, it);
+                k_cg_dir<<<gU, 256, 0, c->stream>>>(N, c->d_cz, c->d_cp, nullptr, sc, it);
             }
             c->kernels += 3;
         }
@@ -692,7 +701,7 @@ int run_hartree(ofks_ctx *c) {
                 ProfScope pu(c, PF_POISSON_VEC);
                 k_cg_update<<<gU, 256, 0, c->stream>>>(N, c->d_minv, c->d_cp, c->d_cq, c->d_U, c->d_cr,
                                                        c->d_cz, sc, it, c->d_gpart, c->d_gcount);
-                k_cg_dir<<<gU, 256, 0, c->stream>>>(N, c->d_cz, c->d_cp, sc, it);
+                k_cg_dir<<<gU, 256, 0, c->stream>>>(N, c->d_cz, c->d_cp, nullptr, sc, it);
             }
             c->kernels += 2;
         }

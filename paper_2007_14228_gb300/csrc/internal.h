@@ -99,6 +99,7 @@ struct Stencil {
     int Lx = 0, Ly = 0, Lz = 0, blocks = 0;
     int64_t len = 0, rows = 0;                   // stored values, rows the SpMV computes
     double *val = nullptr;
+    float2 *valff = nullptr;                     // val as float32 pairs (float-float SpMV)
     StencilType *d_type = nullptr;
     StencilEntry *d_ent = nullptr;               // 8 x ST_MAXE
     int *d_slot = nullptr;                       // 8 x 125 offset code -> own slot or -1
@@ -189,6 +190,7 @@ struct ofks_ctx {
     double *d_ve = nullptr;                      // T x 4 weighted potentials w V_q (float32 or float64)
     double *d_U = nullptr, *d_rhs = nullptr, *d_cr = nullptr, *d_cz = nullptr, *d_cp = nullptr,
            *d_cq = nullptr;
+    float2 *d_cpff = nullptr;                    // the CG direction p as float32 pairs
 
     // ---- blocks n x ld: float64 set (plain form, refinement sweep) and float32 set (mixed form)
     int p = 0, ld = 0;
@@ -230,6 +232,7 @@ struct ofks_ctx {
     double cg_rate = 0.0;                        // per-iteration factor of the squared Hartree CG residual
                                                  // observed in the last solve (0: none yet)
     double hartree_tol = 0.0;                    // > 0: tolerance of the next Hartree solve (adaptive mode)
+    bool hartree_ff = false;                     // this Hartree solve keeps p as float32 pairs (d_cpff) too
     int64_t cg_total = 0;                        // ... summed since the counter was cleared
     double kkt0 = 0.0, eta = 0.0;
     bool converged = false;
@@ -296,6 +299,8 @@ int stencil_setup(ofks_ctx *c, int64_t N, const double *xyz, const int64_t *fptr
 void stencil_fill(ofks_ctx *c);
 void stencil_free(ofks_ctx *c);
 void launch_stencil_spmv(ofks_ctx *c, const double *p, double *q, double *sc, int it);
+// the same in float-float arithmetic from p as float32 pairs (pf); pq += p.q in float64
+void launch_stencil_spmv_ff(ofks_ctx *c, const float2 *pf, const double *p, double *q, double *sc, int it);
 void launch_stencil_residual(ofks_ctx *c, const double *x, const double *b, double *r);     // r = b - L x
 void launch_stencil_jacobi(ofks_ctx *c, const double *x, const double *b, double w, double *y); // y = x + w minv (b - L x)
 

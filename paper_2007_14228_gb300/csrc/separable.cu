@@ -143,12 +143,12 @@ __global__ void __launch_bounds__(256) k_sep_gather(int nx, int ny, int nz, int 
 }
 
 // z <- the interior tensor (float64; t + tlo when tlo is given), rz[slot] += r.z; with pv also
-// p = z (CG start)
+// p = z (CG start), and with pf p as float32 pairs too
 template <class E>
 __global__ void __launch_bounds__(256) k_sep_scatter(int nx, int ny, int nz, int ldc, int Ly, int Lz,
                                                      const E *__restrict__ t, const E *__restrict__ tlo,
-                                                     const double *__restrict__ r, double *z, double *pv, double *sc,
-                                                     int slot, double *gpart, unsigned *gcount) {
+                                                     const double *__restrict__ r, double *z, double *pv, float2 *pf,
+                                                     double *sc, int slot, double *gpart, unsigned *gcount) {
     __shared__ double sh[8];
     const int64_t n = (int64_t)nx * ny * nz;
     double rz = 0.0;
@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(256) k_sep_scatter(int nx, int ny, int nz, int
         const double zi = (double)(float)t[ab * ldc + c] + (tlo ? (double)(float)tlo[ab * ldc + c] : 0.0);
         z[i] = zi;
         if (pv) pv[i] = zi;
+        if (pf) pf[i] = ff_split(zi);
         rz = fma(r[i], zi, rz);
     }
     const double tot[1] = {block_sum(rz, sh)};
@@ -620,7 +621,8 @@ void sep_cg_step(ofks_ctx *c, int it, int slot, int first) {
         pass(5, S.hS[0], ny * nz, nx, nx, 0, ny, nz, pz);                  // -> [a][b][c]
         sep_tc_launch<0, 1>(c, P);
         k_sep_scatter<__nv_bfloat16><<<g, 256, 0, c->stream>>>(nx, ny, nz, pz, c->st.Ly, c->st.Lz, B[0], Bl[0],
-                                                               c->d_cr, c->d_cz, first ? c->d_cp : nullptr, sc, slot,
+                                                               c->d_cr, c->d_cz, first ? c->d_cp : nullptr,
+                                                               first && c->hartree_ff ? c->d_cpff : nullptr, sc, slot,
                                                                c->d_gpart, c->d_gcount);
         c->kernels += 2;
         return;
@@ -640,7 +642,8 @@ void sep_cg_step(ofks_ctx *c, int it, int slot, int first) {
     // Z[ab][c] = sum_k U2[ab][k] Sz^T[k][c]
     gemm(c, 1, nx * ny, nz, nz, S.t1, 0, S.St[2], 0, S.t0, 0);
     k_sep_scatter<float><<<g, 256, 0, c->stream>>>(nx, ny, nz, nz, c->st.Ly, c->st.Lz, S.t0, nullptr, c->d_cr, c->d_cz,
-                                                   first ? c->d_cp : nullptr, sc, slot, c->d_gpart, c->d_gcount);
+                                                   first ? c->d_cp : nullptr, first && c->hartree_ff ? c->d_cpff : nullptr,
+                                                   sc, slot, c->d_gpart, c->d_gcount);
     c->kernels += 2;
 }
 

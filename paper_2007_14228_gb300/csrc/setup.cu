@@ -234,7 +234,7 @@ void free_mesh(ofks_ctx *c) {
     dev_free(c->d_nlist); dev_free(c->d_wq); dev_free(c->d_yq);
     dev_free(c->d_vext); dev_free(c->d_bnd); dev_free(c->d_bxyz); dev_free(c->d_ynode);
     dev_free(c->d_rho); dev_free(c->d_vh); dev_free(c->d_vxc); dev_free(c->d_exc); dev_free(c->d_ve);
-    dev_free(c->d_U); dev_free(c->d_rhs); dev_free(c->d_cr); dev_free(c->d_cz); dev_free(c->d_cp);
+    dev_free(c->d_U); dev_free(c->d_rhs); dev_free(c->d_cr); dev_free(c->d_cz); dev_free(c->d_cp); dev_free(c->d_cpff);
     dev_free(c->d_cq);
     amg_free(c);
     gcn_free(c);
@@ -464,7 +464,7 @@ int setup_mesh(ofks_ctx *c, int64_t n_nodes, const double *xyz, int64_t n_tets, 
         (rc = dev_zeros(c, &c->d_vxc, T * 4)) || (rc = dev_zeros(c, &c->d_exc, T * 4)) ||
         (rc = dev_zeros(c, &c->d_U, N)) || (rc = dev_zeros(c, &c->d_rhs, N)) ||
         (rc = dev_zeros(c, &c->d_cr, N)) || (rc = dev_zeros(c, &c->d_cz, N)) ||
-        (rc = dev_zeros(c, &c->d_cp, N)) || (rc = dev_zeros(c, &c->d_cq, N)) ||
+        (rc = dev_zeros(c, &c->d_cp, N)) || (rc = dev_zeros(c, &c->d_cq, N)) || (rc = dev_zeros(c, &c->d_cpff, N)) ||
         (rc = dev_upload(c, &d_xyz, xyz, (size_t)N * 3)) ||
         (rc = dev_upload(c, &d_dpos, dpos.data(), dpos.size())) ||
         (rc = dev_upload(c, &d_fdiag, fdiag.data(), fdiag.size())) ||

@@ -111,10 +111,98 @@ __global__ void __launch_bounds__(256) k_st_apply(int Ly, int Lz, const StencilT
     }
 }
 
+// ---- float-float form of the MODE 0 apply (the Hartree CG during the float32 iterations)
+//
+// A value v is carried as the float32 pair (hi, lo) with v ~ hi + lo (hi = fl(v), lo = fl(v - hi):
+// ~48 significant bits); a product a x adds hi_a hi_x exactly (its rounding error by an FMA,
+// Dekker's product), plus hi_a lo_x + lo_a hi_x, to the row sum kept as a pair by Knuth's
+// two-sum, on the FP32 pipes (the float64 form keeps the FP64 pipe ~77 % busy).  Intrinsics keep
+// the compiler from contracting or reordering.  The loads of eight entries are issued before
+// their products (the float64 form waits on its loads about as long as on the FP64 pipe).
+__device__ __forceinline__ void ff_madd(float &sh, float &sl, const float2 a, const float2 x) {
+    const float p = __fmul_rn(a.x, x.x);
+    float e = __fmaf_rn(a.x, x.x, -p);
+    e = __fmaf_rn(a.x, x.y, e);
+    e = __fmaf_rn(a.y, x.x, e);
+    const float t = __fadd_rn(sh, p);
+    const float bv = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+constexpr int FF_B = 8;                           // entries whose loads are issued together
+
+__global__ void __launch_bounds__(256) k_st_apply_ff(int Ly, int Lz, const StencilType *__restrict__ types,
+                                                     const StencilEntry *__restrict__ ents,
+                                                     const float2 *__restrict__ val, const double *__restrict__ minv,
+                                                     const float2 *__restrict__ xf, const double *__restrict__ xv,
+                                                     double *yv, double *sc, int it, double *gpart,
+                                                     unsigned *gcount) {
+    __shared__ StencilType st[8];
+    __shared__ StencilEntry se[ST_MAXE];
+    __shared__ double sh[8];
+    if (threadIdx.x < 8) st[threadIdx.x] = types[threadIdx.x];
+    __syncthreads();
+    int t = 0;
+    while (t < 7 && (int)blockIdx.x >= st[t + 1].blk0) ++t;
+    const StencilType T = st[t];
+    for (int e = threadIdx.x; e < T.nent; e += blockDim.x) se[e] = ents[t * ST_MAXE + e];
+    __syncthreads();
+    const int64_t idx = (int64_t)((int)blockIdx.x - T.blk0) * blockDim.x + threadIdx.x;
+    double pq = 0.0;
+    if (idx < T.n) {
+        const int64_t nyz = (int64_t)T.ny * T.nz;
+        const int ia = (int)(idx / nyz);
+        const int64_t rem = idx - (int64_t)ia * nyz;
+        const int ib = (int)(rem / T.nz), ic = (int)(rem - (int64_t)ib * T.nz);
+        const int a = 2 * ia + T.px, b = 2 * ib + T.py, c = 2 * ic + T.pz;
+        const int64_t row = ((int64_t)a * Ly + b) * Lz + c;
+        if (minv[row] != 0.0) {
+            float s_hi = 0.f, s_lo = 0.f;
+            // entry e's value: own slots (e < nown) at this row's index, mirrored ones at the
+            // neighbour's index in its type's arrays
+            auto vaddr = [&](int e) -> const float2 * {
+                const StencilEntry E = se[e];
+                if (e < T.nown) return val + T.base + (int64_t)E.slot * T.n + idx;
+                const StencilType &S = st[E.tp];
+                const int64_t j = ((int64_t)((a + E.oa) >> 1) * S.ny + ((b + E.ob) >> 1)) * S.nz + ((c + E.oc) >> 1);
+                return val + S.base + (int64_t)E.slot * S.n + j;
+            };
+            int e = 0;
+            for (; e + FF_B <= T.nent; e += FF_B) {
+                float2 v[FF_B], x[FF_B];
+#pragma unroll
+                for (int u = 0; u < FF_B; ++u) {
+                    v[u] = __ldg(vaddr(e + u));
+                    x[u] = __ldg(xf + row + se[e + u].lin);
+                }
+#pragma unroll
+                for (int u = 0; u < FF_B; ++u) ff_madd(s_hi, s_lo, v[u], x[u]);
+            }
+            for (; e < T.nent; ++e) ff_madd(s_hi, s_lo, __ldg(vaddr(e)), __ldg(xf + row + se[e].lin));
+            const double s = (double)s_hi + (double)s_lo;
+            yv[row] = s;
+            pq = xv[row] * s;
+        }
+    }
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        sc[0 + ((it + 1) & 1)] = 0.0;
+        sc[4 + ((it + 1) & 1)] = 0.0;
+    }
+    const double tot[1] = {block_sum(pq, sh)};
+    grid_accumulate<1>(tot, gpart, gcount, [&](int, double v) { sc[2 + (it & 1)] += v; });
+}
+
+__global__ void k_st_split(int64_t len, const double *__restrict__ v, float2 *vf) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < len) vf[i] = ff_split(v[i]);
+}
+
 }  // namespace
 
 void stencil_free(ofks_ctx *c) {
-    cudaFree(c->st.val); cudaFree(c->st.d_type); cudaFree(c->st.d_ent); cudaFree(c->st.d_slot);
+    cudaFree(c->st.val); cudaFree(c->st.valff); cudaFree(c->st.d_type); cudaFree(c->st.d_ent); cudaFree(c->st.d_slot);
     c->st = Stencil{};
 }
 
@@ -245,6 +333,7 @@ int stencil_setup(ofks_ctx *c, int64_t N, const double *xyz, const int64_t *fptr
 
     Stencil &S = c->st;
     cudaError_t e = cudaMalloc(&S.val, sizeof(double) * std::max<int64_t>(len, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&S.valff, sizeof(float2) * std::max<int64_t>(len, 1));
     if (e == cudaSuccess) e = cudaMalloc(&S.d_type, sizeof(types));
     if (e == cudaSuccess) e = cudaMalloc(&S.d_ent, sizeof(StencilEntry) * ents.size());
     if (e == cudaSuccess) e = cudaMalloc(&S.d_slot, sizeof(int) * slot.size());
@@ -275,12 +364,23 @@ void stencil_fill(ofks_ctx *c) {
     k_st_fill<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(N, c->st.Ly, c->st.Lz, c->d_fptr, c->d_fcol,
                                                                   c->d_fval, c->st.d_type, c->st.d_slot, c->st.val);
     c->kernels += 1;
+    if (c->st.valff) {
+        k_st_split<<<(unsigned)((c->st.len + 255) / 256), 256, 0, c->stream>>>(c->st.len, c->st.val, c->st.valff);
+        c->kernels += 1;
+    }
 }
 
 void launch_stencil_spmv(ofks_ctx *c, const double *p, double *q, double *sc, int it) {
     k_st_apply<0><<<(unsigned)c->st.blocks, 256, 0, c->stream>>>(c->st.Ly, c->st.Lz, c->st.d_type, c->st.d_ent,
                                                                 c->st.val, c->d_minv, p, nullptr, 0.0, q, sc, it,
                                                                 c->d_gpart, c->d_gcount);
+    c->kernels += 1;
+}
+
+void launch_stencil_spmv_ff(ofks_ctx *c, const float2 *pf, const double *p, double *q, double *sc, int it) {
+    k_st_apply_ff<<<(unsigned)c->st.blocks, 256, 0, c->stream>>>(c->st.Ly, c->st.Lz, c->st.d_type, c->st.d_ent,
+                                                                c->st.valff, c->d_minv, pf, p, q, sc, it, c->d_gpart,
+                                                                c->d_gcount);
     c->kernels += 1;
 }
 

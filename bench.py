@@ -205,7 +205,9 @@ def roofline(prof, n, p, nnz, n_tets, hbm_peak, hbm_kind, spmv_model=(0, 0), ele
     gbs = bytes_ / per / 1e9
     tflops = flops / per / 1e12
     f_hbm = gbs / hbm_peak
-    fp32 = elem == 4 and fam != "poisson_spmv"
+    # float32 forms: every family on the FP32 pipes, the Hartree SpMV included (float-float
+    # products, ~12 FP32 operations per stored product, far below that rate: HBM bounds it)
+    fp32 = elem == 4
     extra = {"pcg_block_width": round(pw, 2)} if fam == "pcg_spmm" else {}
     traffic = None
     if fam == "pcg_spmm" and elem == 4:

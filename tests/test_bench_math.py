@@ -51,3 +51,16 @@ def test_multi_kernel_families_are_not_the_dominant_kernel():
     assert r["kernel"] == "spmm_b"
     alg = (4 + 4) * 32817315 + 3 * 4 * 1175805 * 41
     assert r["achieved"] == pytest.approx(alg / (8.6e-3 / 10) / 1e9, abs=0.05)
+
+
+def test_float32_hartree_spmv_is_against_hbm():
+    # in the float32 forms the Hartree CG's SpMV runs in float-float on the FP32 pipes: its
+    # algorithmic flops are far below the FP32 rate, so its roofline is the HBM one
+    bench.ALU_PEAKS.update({"fp64": 1.25, "fp32": 78.0, "kind": "test"})
+    prof = {"poisson_spmv": {"ms": 6.3, "launches": 57}, "spmm_b": {"ms": 6.0, "launches": 10}}
+    model = (8 * 18648214 + 24 * 1175805, 2 * 35120623)
+    r = bench.roofline(prof, 1175805, 41, 32817315, 908160, 6756.8, "measured", model, elem=4)
+    assert r["kernel"] == "poisson_spmv" and r["bound"] == "hbm"
+    assert r["achieved"] == pytest.approx(model[0] / (6.3e-3 / 57) / 1e9, abs=0.05)
+    r64 = bench.roofline(prof, 1175805, 41, 32817315, 908160, 6756.8, "measured", model, elem=8)
+    assert r64["bound"] == "alu" and r64["unit"] == "TFLOP/s (fp64)"

@@ -64,3 +64,18 @@ def test_float32_hartree_spmv_is_against_hbm():
     assert r["achieved"] == pytest.approx(model[0] / (6.3e-3 / 57) / 1e9, abs=0.05)
     r64 = bench.roofline(prof, 1175805, 41, 32817315, 908160, 6756.8, "measured", model, elem=8)
     assert r64["bound"] == "alu" and r64["unit"] == "TFLOP/s (fp64)"
+
+
+def test_time_to_target_needs_both_energy_and_feasibility():
+    # history rows (k, seconds, E, kkt, fea, eta): the target is the first row with |E - E*| <=
+    # 1e-6 Ha AND fea <= 1e-7; an energy that passes through E* while still infeasible, or a
+    # feasible row still 2e-6 Ha away, does not count
+    E = -276.85
+    hist = [(0, 0.0, E + 1.0, 1.0, 1e-2, 1.0),
+            (1, 0.5, E + 5e-7, 1e-3, 1e-5, 1.0),      # close in energy, infeasible
+            (2, 1.0, E - 2e-6, 1e-4, 1e-8, 1.0),      # feasible, 2e-6 Ha away
+            (3, 1.25, E + 9e-7, 1e-5, 5e-8, 1.0),     # the first hit
+            (4, 1.5, E, 1e-6, 1e-9, 1.0)]
+    assert bench.first_hit(hist, E) == (1.25, 3)
+    assert bench.first_hit(hist[:3], E) == (None, None)
+    assert bench.first_hit(hist, E, target=1e-5, fea_max=1e-4) == (0.5, 1)

@@ -130,7 +130,9 @@ typedef struct {
     int32_t poisson_pc;     /* Hartree CG preconditioner: OFKS_HPC_JACOBI, OFKS_HPC_MULTIGRID or
                                OFKS_HPC_SEPARABLE (falls back to Jacobi where the mesh has none) */
     double  mixed_tol;      /* OFKS_MIXED: hand over to float64 once (kkt+fea)/kkt0 < mixed_tol (or on a stall) */
-    double  poisson_tol_mixed; /* Hartree CG tolerance during the float32 iterations */
+    double  poisson_tol_mixed; /* Hartree CG tolerance during the float32 iterations (whose lattice
+                                  SpMV, with the separable preconditioner, runs in float-float
+                                  arithmetic: float32 pairs, ~48 bits) */
     double  judge_tau;      /* OFKS_PC_LEARNED: accept the network's column D if G.D > 0 and
                                |G - T D|_{M^-1} <= judge_tau |G|_{M^-1} (M the Jacobi diagonal of T,
                                |r|_{M^-1}^2 = r^T M^-1 r, the PCG's residual measure); a rejected column
@@ -147,8 +149,8 @@ typedef struct {
     int32_t spmm_f32_rows;  /* float32 block SpMMs (mixed form): 1 half a warp per row (lanes split the
                                columns), 0 (default) one lane per row and 4-column chunks */
     int32_t poisson_sep_tc; /* OFKS_HPC_SEPARABLE: 1 (default) the six axis contractions on the tensor
-                               cores with bf16 operands (axes up to 256 interior points), 0 float32 on
-                               the CUDA cores */
+                               cores with bf16 operands, every intermediate tensor as a high and a low
+                               bf16 part (axes up to 256 interior points), 0 float32 on the CUDA cores */
     int32_t pcg_compact;    /* OFKS_PC_PCG / OFKS_PC_EXACT: 1 (default) the PCG runs on the active
                                columns only (Lambda_ii < 0), gathered into a block of their count
                                rounded up to 4; the other columns take D = G (T = I) as always.
